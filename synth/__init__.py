@@ -1,0 +1,257 @@
+"""Seeded synthetic inputs shared by the FP64 oracle and the CUDA path.
+
+Holds none of the method's arithmetic: graph topology, atom types, random
+targets, random parameter vectors, and the packed graph-store file writer.
+The generators live in ``synth.c`` (splitmix64 streams + Box-Muller), built
+to ``libsynth.so`` beside it.
+
+Packed store file (one file, global arrays; the single-file analogue of the
+paper's schema of one global array per graph attribute, Section 4, Table 1):
+
+    offset  type        field
+    0       char[8]     magic "GCNNPKD1"
+    8       u32         version (1)
+    12      u32         number of atom types
+    16      i64         G  graphs
+    24      i64         N  nodes
+    32      i64         E  directed edges
+    40      i64         byte offset of node_ptr  (i64[G+1])
+    48      i64         byte offset of edge_ptr  (i64[G+1])
+    56      i64         byte offset of types     (u8[N])
+    64      i64         byte offset of edges     (u8[2E], local (src, dst) pairs)
+    72      i64         byte offset of y         (f32[G])
+    80      i64         file size in bytes
+    88..127 zero
+Every array starts on a 64-byte boundary.  Node and edge ids inside a graph
+are local (0..n-1), so a graph is a contiguous slice of each array.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "synth.c")
+_SO = os.path.join(_HERE, "libsynth.so")
+_lib = None
+
+N_TYPES = 7
+STORE_MAGIC = b"GCNNPKD1"
+HEADER_BYTES = 128
+
+
+def build(force: bool = False) -> str:
+    """Compile synth.c into libsynth.so (plain C, portable flags)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        i64, i32, u64, dbl, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
+        L.synth_stream_first.restype = u64
+        L.synth_stream_first.argtypes = [u64, u64, u64]
+        L.synth_node_counts.restype = i32
+        L.synth_node_counts.argtypes = [u64, i64, i64, i32, i32, i32, dbl, dbl, vp]
+        L.synth_max_directed_edges.restype = i64
+        L.synth_max_directed_edges.argtypes = [i32, dbl]
+        L.synth_topology.restype = i64
+        L.synth_topology.argtypes = [u64, i64, i64, vp, i32, dbl, vp, vp, vp, vp, i64]
+        L.synth_uniform_targets.restype = None
+        L.synth_uniform_targets.argtypes = [u64, i64, i64, dbl, dbl, vp]
+        L.synth_normal.restype = None
+        L.synth_normal.argtypes = [u64, i64, i64, dbl, vp]
+        L.synth_uniform.restype = None
+        L.synth_uniform.argtypes = [u64, i64, i64, dbl, dbl, vp]
+        L.synth_param_count.restype = i64
+        L.synth_param_count.argtypes = [i32, i32, i32, i32]
+        L.synth_init_params.restype = None
+        L.synth_init_params.argtypes = [u64, i32, i32, i32, i32, vp]
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray) -> int:
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+# ---------------------------------------------------------------- scalars
+
+def node_counts_uniform(seed: int, g0: int, G: int, lo: int, hi: int) -> np.ndarray:
+    out = np.empty(G, np.int32)
+    rc = lib().synth_node_counts(seed, g0, G, 0, lo, hi, 0.0, 0.0, _p(out))
+    if rc:
+        raise ValueError(f"synth_node_counts failed ({rc})")
+    return out
+
+
+def node_counts_lognormal(seed: int, g0: int, G: int, mu: float, sigma: float, lo: int, hi: int) -> np.ndarray:
+    out = np.empty(G, np.int32)
+    rc = lib().synth_node_counts(seed, g0, G, 1, lo, hi, mu, sigma, _p(out))
+    if rc:
+        raise ValueError(f"synth_node_counts failed ({rc})")
+    return out
+
+
+def lognormal_mu(mean: float = 18.0, sigma: float = 0.45, lo: int = 3, hi: int = 51) -> float:
+    """Location mu such that round(exp(N(mu, sigma^2))) truncated to [lo, hi]
+    has the requested mean (exact discrete mean, bisection)."""
+    def tmean(mu: float) -> float:
+        def cdf(x: float) -> float:
+            return 0.5 * (1.0 + math.erf((math.log(x) - mu) / (sigma * math.sqrt(2.0))))
+        num = den = 0.0
+        for k in range(lo, hi + 1):
+            p = cdf(k + 0.5) - cdf(max(k - 0.5, 1e-300))
+            num += k * p
+            den += p
+        return num / den
+    a, b = math.log(lo), math.log(hi)
+    for _ in range(200):
+        m = 0.5 * (a + b)
+        if tmean(m) < mean:
+            a = m
+        else:
+            b = m
+    return 0.5 * (a + b)
+
+
+def uniform_targets(seed: int, g0: int, G: int, lo: float, hi: float) -> np.ndarray:
+    out = np.empty(G, np.float32)
+    lib().synth_uniform_targets(seed, g0, G, lo, hi, _p(out))
+    return out
+
+
+def normal(seed: int, i0: int, n: int, sigma: float = 1.0) -> np.ndarray:
+    out = np.empty(n, np.float64)
+    lib().synth_normal(seed, i0, n, sigma, _p(out))
+    return out
+
+
+def uniform(seed: int, i0: int, n: int, lo: float, hi: float) -> np.ndarray:
+    out = np.empty(n, np.float64)
+    lib().synth_uniform(seed, i0, n, lo, hi, _p(out))
+    return out
+
+
+def param_count(H: int, L: int, T: int = N_TYPES, Hh: int | None = None) -> int:
+    return int(lib().synth_param_count(H, L, T, H if Hh is None else Hh))
+
+
+def init_params(seed: int, H: int, L: int, T: int = N_TYPES, Hh: int | None = None) -> np.ndarray:
+    Hh = H if Hh is None else Hh
+    out = np.empty(param_count(H, L, T, Hh), np.float32)
+    lib().synth_init_params(seed, H, L, T, Hh, _p(out))
+    return out
+
+
+# ---------------------------------------------------------------- graphs
+
+@dataclass
+class GraphSet:
+    """A set of graphs as global arrays (the packed-store layout in memory)."""
+    node_ptr: np.ndarray  # int64 [G+1]
+    edge_ptr: np.ndarray  # int64 [G+1]
+    types: np.ndarray     # uint8 [N]
+    edges: np.ndarray     # uint8 [E, 2]  local (src, dst)
+    y: np.ndarray         # float32 [G]
+
+    @property
+    def n_graphs(self) -> int:
+        return len(self.node_ptr) - 1
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.node_ptr[-1])
+
+    @property
+    def n_edges(self) -> int:
+        return int(self.edge_ptr[-1])
+
+    def subset(self, ids) -> "GraphSet":
+        """Graphs ids[0], ids[1], ... as a new set (local ids are unchanged)."""
+        ids = np.asarray(ids, np.int64)
+        n = self.node_ptr[ids + 1] - self.node_ptr[ids]
+        e = self.edge_ptr[ids + 1] - self.edge_ptr[ids]
+        node_ptr = np.zeros(len(ids) + 1, np.int64)
+        edge_ptr = np.zeros(len(ids) + 1, np.int64)
+        node_ptr[1:] = np.cumsum(n)
+        edge_ptr[1:] = np.cumsum(e)
+        types = np.concatenate([self.types[self.node_ptr[g]:self.node_ptr[g + 1]] for g in ids]) if len(ids) else np.zeros(0, np.uint8)
+        edges = np.concatenate([self.edges[self.edge_ptr[g]:self.edge_ptr[g + 1]] for g in ids]) if len(ids) else np.zeros((0, 2), np.uint8)
+        return GraphSet(node_ptr, edge_ptr, np.ascontiguousarray(types), np.ascontiguousarray(edges), self.y[ids].copy())
+
+
+def make_graphs(seed: int, counts: np.ndarray, g0: int = 0, max_deg: int = 4, edge_factor: float = 1.1) -> GraphSet:
+    """Topology + atom types for graphs g0.. with the given node counts; y = 0."""
+    counts = np.ascontiguousarray(counts, np.int32)
+    G = len(counts)
+    L = lib()
+    # capacity: per-count maximum times multiplicity
+    uniq, mult = np.unique(counts, return_counts=True)
+    cap = int(sum(int(L.synth_max_directed_edges(int(n), edge_factor)) * int(m) for n, m in zip(uniq, mult)))
+    node_ptr = np.zeros(G + 1, np.int64)
+    edge_ptr = np.zeros(G + 1, np.int64)
+    types = np.zeros(int(counts.sum()), np.uint8)
+    edges = np.zeros((max(cap, 1), 2), np.uint8)
+    ne = L.synth_topology(seed, g0, G, _p(counts), max_deg, edge_factor, _p(node_ptr), _p(edge_ptr),
+                          _p(types), _p(edges), cap)
+    if ne < 0:
+        raise ValueError(f"synth_topology failed ({ne})")
+    return GraphSet(node_ptr, edge_ptr, types, np.ascontiguousarray(edges[:ne]), np.zeros(G, np.float32))
+
+
+def molecules_uniform(seed: int, G: int, lo: int, hi: int, g0: int = 0) -> GraphSet:
+    """G molecule-shaped graphs with n ~ U{lo..hi} nodes (y = 0)."""
+    return make_graphs(seed, node_counts_uniform(seed, g0, G, lo, hi), g0=g0)
+
+
+def molecules_lognormal(seed: int, G: int, mean: float = 18.0, sigma: float = 0.45, lo: int = 3,
+                        hi: int = 51, g0: int = 0) -> GraphSet:
+    """G molecule-shaped graphs, n = round(exp(N(mu, sigma^2))) in [lo, hi], mu set for the mean."""
+    mu = lognormal_mu(mean, sigma, lo, hi)
+    return make_graphs(seed, node_counts_lognormal(seed, g0, G, mu, sigma, lo, hi), g0=g0)
+
+
+# ---------------------------------------------------------------- store file
+
+def _align(x: int, a: int = 64) -> int:
+    return (x + a - 1) // a * a
+
+
+def write_store(path: str, gs: GraphSet) -> None:
+    """Write a GraphSet as one packed store file (layout in the module docstring)."""
+    G, N, E = gs.n_graphs, gs.n_nodes, gs.n_edges
+    offs = []
+    pos = HEADER_BYTES
+    for nbytes in [(G + 1) * 8, (G + 1) * 8, N, 2 * E, 4 * G]:
+        pos = _align(pos)
+        offs.append(pos)
+        pos += nbytes
+    total = _align(pos)
+    buf = np.zeros(total, np.uint8)
+    hdr = np.zeros(HEADER_BYTES, np.uint8)
+    hdr[0:8] = np.frombuffer(STORE_MAGIC, np.uint8)
+    hdr[8:16] = np.array([1, N_TYPES], "<u4").view(np.uint8)
+    hdr[16:88] = np.array([G, N, E] + offs + [total], "<i8").view(np.uint8)
+    buf[:HEADER_BYTES] = hdr
+    arrays = [np.ascontiguousarray(gs.node_ptr, "<i8"), np.ascontiguousarray(gs.edge_ptr, "<i8"),
+              np.ascontiguousarray(gs.types, np.uint8), np.ascontiguousarray(gs.edges, np.uint8).reshape(-1),
+              np.ascontiguousarray(gs.y, "<f4")]
+    for off, arr in zip(offs, arrays):
+        b = arr.view(np.uint8).reshape(-1)
+        buf[off:off + b.size] = b
+    tmp = path + f".tmp{os.getpid()}"
+    buf.tofile(tmp)
+    os.replace(tmp, path)
