@@ -1,0 +1,239 @@
+/*
+ * gcnn.h -- C ABI of the GB300 (sm_103a) GCNN training / inference library.
+ *
+ * The library implements one training step of the graph convolutional neural
+ * network of HydraGNN (Choi et al., arXiv 2207.11333) over a collated batch
+ * of molecular graphs: data loading from a packed store (Sec. 4, Table 1),
+ * batch collation, PNA graph convolutions (Sec. 3.1; 6 layers in Sec. 5.1),
+ * global mean pooling (Sec. 3.1), a fully connected head (Sec. 3.1), the MSE
+ * loss, the backward pass and the optimizer step (Sec. 3.2, Fig. 3; AdamW with
+ * learning rate 1e-3 in Sec. 5.1), plus an inference server for the paper's
+ * screening use (Sec. 1, Sec. 6).
+ *
+ * Conventions
+ *   - Every function returns an int status: GCNN_OK (0) or a negative GCNN_E*
+ *     code; gcnn_last_error() gives a message for the calling thread.  No
+ *     function aborts, traps or throws across this boundary.
+ *   - "stream" arguments are cudaStream_t values passed as void*; NULL is the
+ *     legacy default stream.  GPU work is asynchronous on the stream unless a
+ *     function says otherwise.
+ *   - Pointers marked (device) are CUDA device pointers; (host) pointers are
+ *     ordinary host memory.  The caller owns every buffer it passes; the
+ *     library owns the objects it creates until the matching destroy call.
+ *   - Matrices are row-major.  H = hidden width, Hh = head hidden width,
+ *     T = number of atom types, L = number of convolution layers,
+ *     G / N / E = graphs / nodes / directed edges of a batch.
+ *
+ * Model (PNA layer, the published definition with one linear message layer
+ * and one linear update layer; the paper names PNA without printing it):
+ *   x0_i          = emb[type_i]
+ *   m_ij          = W_M [x_i ; x_j] + b_M               for each edge j -> i
+ *   a_i           = sum, mean, min, max, std of m_ij over j in N(i)   (5H)
+ *   s_i           = [1, log(d_i+1)/delta, delta/log(d_i+1)]          (scalers)
+ *   x_i'          = ReLU(W_U [x_i ; s_i (x) a_i] + b_U)               (16H -> H)
+ *   g             = mean of x^L over the graph's nodes
+ *   yhat          = w2 . ReLU(W1 g + b1) + b2
+ *   loss          = (1/G) sum_g (yhat_g - y_g)^2
+ * with std = sqrt(ReLU(var) + std_eps), var two-pass; d_i = 0 gives zero
+ * aggregates; the scalers use max(d_i, 1); min/max ties share the gradient
+ * equally; ReLU'(0) = 0.
+ *
+ * Flat parameter layout (float32), in this order:
+ *   emb[T][H]
+ *   per layer: msg_w[H][2H] (columns 0..H-1 act on x_i, H..2H-1 on x_j),
+ *              msg_b[H],
+ *              upd_w[16H][H] (rows 0..H-1 act on x_i, then 15 blocks of H
+ *                 rows, scaler-major: identity{sum,mean,min,max,std},
+ *                 amplification{...}, attenuation{...}),
+ *              upd_b[H]
+ *   head: w1[H][Hh], b1[Hh], w2[Hh], b2[1]
+ */
+#ifndef GCNN_H_
+#define GCNN_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GCNN_OK 0
+#define GCNN_EINVAL (-1)    /* bad argument or unsupported size               */
+#define GCNN_ENOMEM (-2)    /* host or device allocation failed               */
+#define GCNN_ECUDA (-3)     /* a CUDA runtime call failed                     */
+#define GCNN_EFORMAT (-4)   /* the store file is malformed                    */
+#define GCNN_EDEVICE (-5)   /* a device-side bounds check fired               */
+#define GCNN_ETIMEDOUT (-6) /* a bounded wait ran out                         */
+#define GCNN_EAGAIN (-7)    /* result not ready / queue full: call again      */
+#define GCNN_ESTATE (-8)    /* call out of order (e.g. backward w/o forward)  */
+
+#define GCNN_PREC_FP32 0    /* FP32 everywhere (SIMT FFMA GEMMs)              */
+#define GCNN_PREC_BF16 1    /* BF16 tensor-core GEMMs, FP32 accumulate        */
+
+/* Message for the last failing call on this thread (never NULL). */
+const char *gcnn_last_error(void);
+/* Library version, major * 10000 + minor * 100 + patch. */
+int gcnn_version(void);
+
+/* ------------------------------------------------------------------ store
+ * Packed graph store: one file holding every graph attribute as a global
+ * array (the single-file analogue of the paper's schema, Sec. 4, Table 1):
+ * node_ptr[G+1], edge_ptr[G+1] (int64 offsets), types[N] (uint8 atom type),
+ * edges[E][2] (uint8 local source, destination), y[G] (float32 target).
+ * Graphs must have 1..255 nodes and at most 1024 directed edges, local ids
+ * < n; each undirected bond is stored as two directed edges.  The file is
+ * validated once at open (GCNN_EFORMAT on any violation).  A store is
+ * read-only after open except for gcnn_store_set_targets, and may be shared
+ * by several contexts on one device.
+ */
+typedef struct gcnn_store gcnn_store;
+
+/* Open and validate a store file; *out owns a host copy in pinned memory. */
+int gcnn_store_open(const char *path, gcnn_store **out);
+int gcnn_store_close(gcnn_store *st);
+/* Totals of the whole store. */
+int gcnn_store_info(const gcnn_store *st, int64_t *n_graphs, int64_t *n_nodes, int64_t *n_edges);
+/* Node and edge totals of the batch graph_ids[0..n) (host ids). */
+int gcnn_store_batch_size(const gcnn_store *st, const int64_t *graph_ids, int64_t n,
+                          int64_t *n_nodes, int64_t *n_edges);
+/* PNA degree normaliser delta = mean over all nodes of graphs ids[0..n)
+ * (ids NULL: every graph) of log(in-degree + 1), in FP64. */
+int gcnn_store_delta(const gcnn_store *st, const int64_t *graph_ids, int64_t n, double *delta);
+/* Replace the targets y[0..n) (host, n = number of graphs); updates the
+ * device copy too when one exists (synchronously). */
+int gcnn_store_set_targets(gcnn_store *st, const float *y, int64_t n);
+/* Copy the store's arrays into device memory of the current device so that
+ * collation reads them there (the "resident" mode).  Synchronous. */
+int gcnn_store_to_device(gcnn_store *st);
+
+/* ------------------------------------------------------------------ context */
+typedef struct gcnn_config {
+  int32_t hidden;       /* H, a multiple of 8, 8..1024                         */
+  int32_t layers;       /* L >= 1 convolution layers                           */
+  int32_t n_types;      /* T atom types (7)                                    */
+  int32_t head_hidden;  /* Hh, 1..1024                                         */
+  int32_t max_graphs;   /* batch capacity: graphs                              */
+  int32_t max_nodes;    /* batch capacity: nodes                               */
+  int32_t max_edges;    /* batch capacity: directed edges                      */
+  int32_t precision;    /* GCNN_PREC_FP32 or GCNN_PREC_BF16                    */
+  int32_t recompute;    /* 1: do not keep aggregates in forward; recompute
+                           them per layer in backward (saves 5*N*H floats per
+                           layer)                                              */
+  int32_t reserved;
+  double delta;         /* PNA degree normaliser (gcnn_store_delta)            */
+  double std_eps;       /* epsilon inside the std aggregator (1e-5)            */
+  double beta1, beta2;  /* Adam moment decays (0.9, 0.999)                     */
+  double adam_eps;      /* Adam epsilon (1e-8)                                 */
+  double weight_decay;  /* decoupled (AdamW) weight decay (0)                  */
+} gcnn_config;
+
+typedef struct gcnn_ctx gcnn_ctx;
+
+/* Fill *cfg with the defaults above for the given sizes. */
+int gcnn_config_default(gcnn_config *cfg, int32_t hidden, int32_t layers, int32_t max_graphs,
+                        int32_t max_nodes, int32_t max_edges);
+/* Create a context on the current device: allocates parameters (zeroed),
+ * gradients, Adam moments and an activation arena sized by the capacities.
+ * All later GPU work of this context runs on `stream`. */
+int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out);
+int gcnn_destroy(gcnn_ctx *ctx);
+/* Number of float32 parameters (layout in the file header). */
+int gcnn_param_count(const gcnn_ctx *ctx, int64_t *n);
+/* Copy n = gcnn_param_count floats in or out; on_device says whether the
+ * caller's pointer is device (1) or host (0) memory.  Synchronous. */
+int gcnn_set_params(gcnn_ctx *ctx, const float *src, int64_t n, int on_device);
+int gcnn_get_params(gcnn_ctx *ctx, float *dst, int64_t n, int on_device);
+int gcnn_get_grads(gcnn_ctx *ctx, float *dst, int64_t n, int on_device);
+/* Zero Adam's moments and step counter. */
+int gcnn_reset_optimizer(gcnn_ctx *ctx);
+/* Checkpoint: parameters, Adam moments and step counter in one binary file. */
+int gcnn_save(gcnn_ctx *ctx, const char *path);
+int gcnn_load(gcnn_ctx *ctx, const char *path);
+/* Device error word (bounds checks in kernels); synchronises the stream.
+ * Returns GCNN_EDEVICE and clears the word if a check fired. */
+int gcnn_check(gcnn_ctx *ctx);
+
+/* ------------------------------------------------------------------ batches
+ * A collated batch: device views into the context's arena, valid until the
+ * next collate on the same context.  Edges are grouped by destination in
+ * CSR form (row_ptr/col, col = source node), each row sorted by source.
+ */
+typedef struct gcnn_batch {
+  int32_t n_graphs, n_nodes, n_edges, reserved;
+  const int32_t *node_off;  /* (device) [G+1] first node of each graph         */
+  const int32_t *edge_off;  /* (device) [G+1] first edge slot of each graph    */
+  const int32_t *graph_id;  /* (device) [N]   graph of each node               */
+  const int32_t *row_ptr;   /* (device) [N+1] CSR offsets by destination       */
+  const int32_t *col;       /* (device) [E]   source node of each edge slot    */
+  const int32_t *rev;       /* (device) [E]   slot of the reverse edge         */
+  const int32_t *deg;       /* (device) [N]   in-degree                        */
+  const float *amp;         /* (device) [N]   log(max(d,1)+1)/delta as float   */
+  const float *att;         /* (device) [N]   delta/log(max(d,1)+1) as float   */
+  const uint8_t *types;     /* (device) [N]   atom type                        */
+  const float *y;           /* (device) [G]   target                           */
+} gcnn_batch;
+
+/* Collate graphs graph_ids[0..n_graphs) (host ids) of `st` on the device.
+ * Resident store: the collator reads the device copy; otherwise the graphs'
+ * slices are gathered into pinned staging memory and copied in one transfer.
+ * GCNN_EINVAL if the batch exceeds the context's capacities. */
+int gcnn_collate(gcnn_ctx *ctx, const gcnn_store *st, const int64_t *graph_ids, int32_t n_graphs,
+                 gcnn_batch *out);
+/* Upload an order of graph ids (host, n) once; gcnn_collate_range then
+ * collates order[first .. first+count) reading the ids on the device
+ * (resident stores only). */
+int gcnn_set_order(gcnn_ctx *ctx, const gcnn_store *st, const int64_t *order, int64_t n);
+int gcnn_collate_range(gcnn_ctx *ctx, const gcnn_store *st, int64_t first, int32_t count,
+                       gcnn_batch *out);
+/* Copy a batch's arrays to host buffers (any may be NULL).  Synchronous. */
+int gcnn_batch_export(gcnn_ctx *ctx, const gcnn_batch *b, int32_t *node_off, int32_t *graph_id,
+                      int32_t *row_ptr, int32_t *col, int32_t *rev, int32_t *deg, float *amp,
+                      float *att, uint8_t *types, float *y);
+
+/* ------------------------------------------------------------------ training */
+/* Forward pass; pred (device, G floats) may be NULL.  train = 1 keeps what
+ * backward needs. */
+int gcnn_forward(gcnn_ctx *ctx, const gcnn_batch *b, float *pred, int train);
+/* Backward of the last forward(train = 1) on the same batch.  dpred (device,
+ * G) = dL/dyhat, or NULL for the MSE loss against the batch targets.
+ * Gradients overwrite the context's gradient buffer.  loss_accum (device,
+ * 3 doubles, may be NULL): += sum (yhat-y)^2, += sum |yhat-y|, += G. */
+int gcnn_backward(gcnn_ctx *ctx, const gcnn_batch *b, const float *dpred, double *loss_accum);
+/* AdamW step over all parameters with learning rate lr. */
+int gcnn_step(gcnn_ctx *ctx, float lr);
+/* forward(train) + backward(MSE) + step; replays a captured CUDA graph per
+ * batch graph count after the first call with that count. */
+int gcnn_train_step(gcnn_ctx *ctx, const gcnn_batch *b, float lr, double *loss_accum);
+/* Copy x^l (l = 0..L, N x H floats) of the last forward to host.  Sync. */
+int gcnn_get_activation(gcnn_ctx *ctx, int32_t layer, float *dst, int64_t n);
+
+/* ------------------------------------------------------------------ operators
+ * Single steps of the path on caller-owned device buffers, for composing the
+ * layer from PyTorch (torch.autograd.Function) and for unit tests.
+ */
+/* agg[i] = [sum, mean, min, max, std] over edges j->i of m_ij = P_i + Q_j,
+ * where PQ (N x 2H) holds P in columns 0..H-1 and Q in H..2H-1.
+ * agg is N x 5H.  (Sec. 3.1 message passing; PNA aggregators.) */
+int gcnn_op_aggregate_fwd(int32_t n_nodes, int32_t hidden, const int32_t *row_ptr,
+                          const int32_t *col, const float *PQ, float *agg, float std_eps,
+                          void *stream);
+/* Gradient of gcnn_op_aggregate_fwd: from dagg (N x 5H) and the forward's
+ * PQ and agg, writes dPQ (N x 2H: dP = sum over the row, dQ_j = sum over the
+ * edges leaving j).  scratch (device) holds n_edges * hidden floats.  Min/max
+ * ties share the gradient equally; no atomics (deterministic). */
+int gcnn_op_aggregate_bwd(int32_t n_nodes, int32_t n_edges, int32_t hidden, const int32_t *row_ptr,
+                          const int32_t *col, const int32_t *rev, const float *PQ,
+                          const float *agg, const float *dagg, float *dPQ, float *scratch,
+                          float std_eps, void *stream);
+/* pooled[g] = mean of x over nodes node_off[g]..node_off[g+1]-1 (Sec. 3.1). */
+int gcnn_op_pool_fwd(int32_t n_graphs, int32_t hidden, const int32_t *node_off, const float *x,
+                     float *pooled, void *stream);
+/* dx[i] = dpooled[graph_id[i]] / n_graph. */
+int gcnn_op_pool_bwd(int32_t n_graphs, int32_t n_nodes, int32_t hidden, const int32_t *node_off,
+                     const int32_t *graph_id, const float *dpooled, float *dx, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GCNN_H_ */

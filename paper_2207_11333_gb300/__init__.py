@@ -1,0 +1,380 @@
+"""Python binding of libgcnn (include/gcnn.h): argument marshalling only.
+
+Every step of the GCNN training / inference path runs in the library's CUDA
+kernels; this module converts numpy arrays / torch tensors to pointers,
+passes torch's current CUDA stream, and turns status codes into exceptions.
+There is no fallback: if libgcnn.so is missing or cannot be loaded, importing
+this package raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgcnn.so")
+
+PREC_FP32 = 0
+PREC_BF16 = 1
+
+_ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EFORMAT", -5: "EDEVICE", -6: "ETIMEDOUT",
+           -7: "EAGAIN", -8: "ESTATE"}
+
+
+class GcnnError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("hidden", ctypes.c_int32), ("layers", ctypes.c_int32), ("n_types", ctypes.c_int32),
+                ("head_hidden", ctypes.c_int32), ("max_graphs", ctypes.c_int32), ("max_nodes", ctypes.c_int32),
+                ("max_edges", ctypes.c_int32), ("precision", ctypes.c_int32), ("recompute", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("delta", ctypes.c_double), ("std_eps", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("adam_eps", ctypes.c_double),
+                ("weight_decay", ctypes.c_double)]
+
+
+class BatchStruct(ctypes.Structure):
+    _fields_ = [("n_graphs", ctypes.c_int32), ("n_nodes", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)] + [(n, ctypes.c_void_p) for n in (
+                    "node_off", "edge_off", "graph_id", "row_ptr", "col", "rev", "deg", "amp", "att", "types", "y")]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_2207_11333_gb300.build.build() "
+                          "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    i32, i64, f32, f64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double, ctypes.c_void_p
+    P = ctypes.POINTER
+    sig = {
+        "gcnn_last_error": (ctypes.c_char_p, []),
+        "gcnn_version": (i32, []),
+        "gcnn_store_open": (i32, [ctypes.c_char_p, P(vp)]),
+        "gcnn_store_close": (i32, [vp]),
+        "gcnn_store_info": (i32, [vp, P(i64), P(i64), P(i64)]),
+        "gcnn_store_batch_size": (i32, [vp, vp, i64, P(i64), P(i64)]),
+        "gcnn_store_delta": (i32, [vp, vp, i64, P(f64)]),
+        "gcnn_store_set_targets": (i32, [vp, vp, i64]),
+        "gcnn_store_to_device": (i32, [vp]),
+        "gcnn_config_default": (i32, [P(Config), i32, i32, i32, i32, i32]),
+        "gcnn_create": (i32, [P(Config), vp, P(vp)]),
+        "gcnn_destroy": (i32, [vp]),
+        "gcnn_param_count": (i32, [vp, P(i64)]),
+        "gcnn_set_params": (i32, [vp, vp, i64, i32]),
+        "gcnn_get_params": (i32, [vp, vp, i64, i32]),
+        "gcnn_get_grads": (i32, [vp, vp, i64, i32]),
+        "gcnn_reset_optimizer": (i32, [vp]),
+        "gcnn_save": (i32, [vp, ctypes.c_char_p]),
+        "gcnn_load": (i32, [vp, ctypes.c_char_p]),
+        "gcnn_check": (i32, [vp]),
+        "gcnn_collate": (i32, [vp, vp, vp, i32, P(BatchStruct)]),
+        "gcnn_set_order": (i32, [vp, vp, vp, i64]),
+        "gcnn_collate_range": (i32, [vp, vp, i64, i32, P(BatchStruct)]),
+        "gcnn_batch_export": (i32, [vp, P(BatchStruct)] + [vp] * 10),
+        "gcnn_forward": (i32, [vp, P(BatchStruct), vp, i32]),
+        "gcnn_backward": (i32, [vp, P(BatchStruct), vp, vp]),
+        "gcnn_step": (i32, [vp, f32]),
+        "gcnn_train_step": (i32, [vp, P(BatchStruct), f32, vp]),
+        "gcnn_get_activation": (i32, [vp, i32, vp, i64]),
+        "gcnn_op_aggregate_fwd": (i32, [i32, i32, vp, vp, vp, vp, f32, vp]),
+        "gcnn_op_aggregate_bwd": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, f32, vp]),
+        "gcnn_op_pool_fwd": (i32, [i32, i32, vp, vp, vp, vp]),
+        "gcnn_op_pool_bwd": (i32, [i32, i32, i32, vp, vp, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def _check(rc: int) -> None:
+    if rc != 0:
+        raise GcnnError(rc, lib.gcnn_last_error().decode(errors="replace"))
+
+
+def _np_ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+    return a.ctypes.data
+
+
+def _stream(stream=None):
+    """cudaStream_t of torch's current stream (or the given torch stream / raw handle)."""
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- store
+
+class Store:
+    """Packed graph store (gcnn_store_*)."""
+
+    def __init__(self, path: str):
+        self._h = ctypes.c_void_p()
+        _check(lib.gcnn_store_open(path.encode(), ctypes.byref(self._h)))
+        g, n, e = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.gcnn_store_info(self._h, ctypes.byref(g), ctypes.byref(n), ctypes.byref(e)))
+        self.n_graphs, self.n_nodes, self.n_edges = g.value, n.value, e.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self) -> None:
+        if self._h:
+            _check(lib.gcnn_store_close(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def batch_size(self, ids) -> tuple[int, int]:
+        ids = np.ascontiguousarray(ids, np.int64)
+        n, e = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.gcnn_store_batch_size(self._h, _np_ptr(ids), len(ids), ctypes.byref(n), ctypes.byref(e)))
+        return n.value, e.value
+
+    def delta(self, ids=None) -> float:
+        d = ctypes.c_double()
+        if ids is None:
+            _check(lib.gcnn_store_delta(self._h, None, 0, ctypes.byref(d)))
+        else:
+            ids = np.ascontiguousarray(ids, np.int64)
+            _check(lib.gcnn_store_delta(self._h, _np_ptr(ids), len(ids), ctypes.byref(d)))
+        return d.value
+
+    def set_targets(self, y) -> None:
+        y = np.ascontiguousarray(y, np.float32)
+        _check(lib.gcnn_store_set_targets(self._h, _np_ptr(y), len(y)))
+
+    def to_device(self) -> None:
+        _check(lib.gcnn_store_to_device(self._h))
+
+
+# ---------------------------------------------------------------- context
+
+def make_config(hidden: int, layers: int, max_graphs: int, max_nodes: int, max_edges: int, **kw) -> Config:
+    c = Config()
+    _check(lib.gcnn_config_default(ctypes.byref(c), hidden, layers, max_graphs, max_nodes, max_edges))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise AttributeError(k)
+        setattr(c, k, v)
+    return c
+
+
+@dataclass
+class Batch:
+    s: BatchStruct
+    owner: "Context"
+
+    @property
+    def n_graphs(self) -> int:
+        return self.s.n_graphs
+
+    @property
+    def n_nodes(self) -> int:
+        return self.s.n_nodes
+
+    @property
+    def n_edges(self) -> int:
+        return self.s.n_edges
+
+    def export(self) -> dict:
+        G, N, E = self.n_graphs, self.n_nodes, self.n_edges
+        out = {"node_off": np.zeros(G + 1, np.int32), "graph_id": np.zeros(N, np.int32),
+               "row_ptr": np.zeros(N + 1, np.int32), "col": np.zeros(E, np.int32), "rev": np.zeros(E, np.int32),
+               "deg": np.zeros(N, np.int32), "amp": np.zeros(N, np.float32), "att": np.zeros(N, np.float32),
+               "types": np.zeros(N, np.uint8), "y": np.zeros(G, np.float32)}
+        _check(lib.gcnn_batch_export(self.owner._h, ctypes.byref(self.s), *[_np_ptr(out[k]) for k in (
+            "node_off", "graph_id", "row_ptr", "col", "rev", "deg", "amp", "att", "types", "y")]))
+        return out
+
+    def tensor(self, name: str):
+        """A torch view of one of the batch's device arrays (valid until the next collate)."""
+        import torch
+        G, N, E = self.n_graphs, self.n_nodes, self.n_edges
+        spec = {"node_off": (G + 1, torch.int32), "edge_off": (G + 1, torch.int32), "graph_id": (N, torch.int32),
+                "row_ptr": (N + 1, torch.int32), "col": (E, torch.int32), "rev": (E, torch.int32),
+                "deg": (N, torch.int32), "amp": (N, torch.float32), "att": (N, torch.float32),
+                "types": (N, torch.uint8), "y": (G, torch.float32)}[name]
+        return _wrap_device(getattr(self.s, name), spec[0], spec[1])
+
+
+def _wrap_device(ptr: int, n: int, dtype):
+    """Zero-copy torch tensor over library-owned device memory (via DLPack-free __cuda_array_interface__)."""
+    import torch
+    typestr = {torch.int32: "<i4", torch.float32: "<f4", torch.uint8: "|u1", torch.int64: "<i8"}[dtype]
+
+    class _A:
+        __cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr or 0, False), "version": 2}
+    if n == 0:
+        return torch.zeros(0, dtype=dtype, device="cuda")
+    return torch.as_tensor(_A(), device="cuda")
+
+
+class Context:
+    """A training context (gcnn_create): parameters, Adam state, activation arena."""
+
+    def __init__(self, cfg: Config, stream=None):
+        self.cfg = cfg
+        self._h = ctypes.c_void_p()
+        _check(lib.gcnn_create(ctypes.byref(cfg), _stream(stream), ctypes.byref(self._h)))
+        n = ctypes.c_int64()
+        _check(lib.gcnn_param_count(self._h, ctypes.byref(n)))
+        self.n_params = n.value
+
+    def close(self) -> None:
+        if self._h:
+            _check(lib.gcnn_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # parameters
+    def set_params(self, p) -> None:
+        if isinstance(p, np.ndarray):
+            p = np.ascontiguousarray(p, np.float32)
+            _check(lib.gcnn_set_params(self._h, _np_ptr(p), p.size, 0))
+        else:
+            _check(lib.gcnn_set_params(self._h, _dev_ptr(p, None), p.numel(), 1))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        _check(lib.gcnn_get_params(self._h, _np_ptr(out), out.size, 0))
+        return out
+
+    def get_grads(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        _check(lib.gcnn_get_grads(self._h, _np_ptr(out), out.size, 0))
+        return out
+
+    def reset_optimizer(self) -> None:
+        _check(lib.gcnn_reset_optimizer(self._h))
+
+    def save(self, path: str) -> None:
+        _check(lib.gcnn_save(self._h, path.encode()))
+
+    def load(self, path: str) -> None:
+        _check(lib.gcnn_load(self._h, path.encode()))
+
+    def check(self) -> None:
+        _check(lib.gcnn_check(self._h))
+
+    # batches
+    def collate(self, store: Store, ids) -> Batch:
+        ids = np.ascontiguousarray(ids, np.int64)
+        b = BatchStruct()
+        _check(lib.gcnn_collate(self._h, store.handle, _np_ptr(ids), len(ids), ctypes.byref(b)))
+        return Batch(b, self)
+
+    def set_order(self, store: Store, order) -> None:
+        order = np.ascontiguousarray(order, np.int64)
+        _check(lib.gcnn_set_order(self._h, store.handle, _np_ptr(order), len(order)))
+
+    def collate_range(self, store: Store, first: int, count: int) -> Batch:
+        b = BatchStruct()
+        _check(lib.gcnn_collate_range(self._h, store.handle, first, count, ctypes.byref(b)))
+        return Batch(b, self)
+
+    # training
+    def forward(self, batch: Batch, pred=None, train: bool = True) -> None:
+        _check(lib.gcnn_forward(self._h, ctypes.byref(batch.s), _dev_ptr(pred), int(train)))
+
+    def backward(self, batch: Batch, dpred=None, loss_accum=None) -> None:
+        _check(lib.gcnn_backward(self._h, ctypes.byref(batch.s), _dev_ptr(dpred), _dev_ptr(loss_accum)))
+
+    def step(self, lr: float) -> None:
+        _check(lib.gcnn_step(self._h, lr))
+
+    def train_step(self, batch: Batch, lr: float, loss_accum=None) -> None:
+        _check(lib.gcnn_train_step(self._h, ctypes.byref(batch.s), lr, _dev_ptr(loss_accum)))
+
+    def activation(self, layer: int) -> np.ndarray:
+        n = self._last_nodes * self.cfg.hidden
+        out = np.empty(n, np.float32)
+        _check(lib.gcnn_get_activation(self._h, layer, _np_ptr(out), n))
+        return out.reshape(self._last_nodes, self.cfg.hidden)
+
+    def activations(self, batch: Batch) -> list[np.ndarray]:
+        self._last_nodes = batch.n_nodes
+        return [self.activation(l) for l in range(self.cfg.layers + 1)]
+
+
+# ---------------------------------------------------------------- operators
+
+def aggregate_fwd(PQ, row_ptr, col, std_eps: float = 1e-5, stream=None):
+    """agg (N x 5H) = [sum, mean, min, max, std] of P_i + Q_j over each CSR row (gcnn_op_aggregate_fwd)."""
+    import torch
+    N, H2 = PQ.shape
+    H = H2 // 2
+    agg = torch.empty(N, 5 * H, device=PQ.device, dtype=torch.float32)
+    _check(lib.gcnn_op_aggregate_fwd(N, H, _dev_ptr(row_ptr, torch.int32), _dev_ptr(col, torch.int32),
+                                     _dev_ptr(PQ, torch.float32), _dev_ptr(agg), std_eps, _stream(stream)))
+    return agg
+
+
+def aggregate_bwd(PQ, agg, dagg, row_ptr, col, rev, std_eps: float = 1e-5, stream=None):
+    """dPQ (N x 2H) from dagg (gcnn_op_aggregate_bwd)."""
+    import torch
+    N, H2 = PQ.shape
+    H = H2 // 2
+    E = col.numel()
+    dPQ = torch.empty_like(PQ)
+    scratch = torch.empty(max(E, 1) * H, device=PQ.device, dtype=torch.float32)
+    _check(lib.gcnn_op_aggregate_bwd(N, E, H, _dev_ptr(row_ptr, torch.int32), _dev_ptr(col, torch.int32),
+                                     _dev_ptr(rev, torch.int32), _dev_ptr(PQ, torch.float32),
+                                     _dev_ptr(agg, torch.float32), _dev_ptr(dagg.contiguous(), torch.float32),
+                                     _dev_ptr(dPQ), _dev_ptr(scratch), std_eps, _stream(stream)))
+    return dPQ
+
+
+def pool_fwd(x, node_off, stream=None):
+    import torch
+    G = node_off.numel() - 1
+    H = x.shape[1]
+    out = torch.empty(G, H, device=x.device, dtype=torch.float32)
+    _check(lib.gcnn_op_pool_fwd(G, H, _dev_ptr(node_off, torch.int32), _dev_ptr(x, torch.float32), _dev_ptr(out),
+                                _stream(stream)))
+    return out
+
+
+def pool_bwd(dpooled, node_off, graph_id, n_nodes: int, stream=None):
+    import torch
+    G, H = dpooled.shape
+    dx = torch.empty(n_nodes, H, device=dpooled.device, dtype=torch.float32)
+    _check(lib.gcnn_op_pool_bwd(G, n_nodes, H, _dev_ptr(node_off, torch.int32), _dev_ptr(graph_id, torch.int32),
+                                _dev_ptr(dpooled.contiguous(), torch.float32), _dev_ptr(dx), _stream(stream)))
+    return dx

@@ -1,0 +1,207 @@
+// Gather + multi-aggregator message passing of the PNA layer (Sec. 3.1, the
+// graph-convolution step), and its backward.
+//
+// By linearity of the one-layer message function, m_ij = W_M [x_i ; x_j] + b_M
+// equals P_i + Q_j with P = x A + b_M and Q = x B (A, B the two halves of
+// W_M), so the per-edge message never has to be stored: the forward kernel
+// gathers Q rows over each destination's CSR row and reduces them on the fly.
+//
+// Forward:  one thread per (node, 4 channels); FP32; two passes over the row
+//           (the second re-reads Q rows from L1) for a two-pass variance.
+// Backward: kernel 1, one thread per (node i, 4 channels), recomputes m_ij,
+//           routes dagg to every edge (sum: 1, mean: 1/d, min/max: shared
+//           equally among exact ties, std: (m - mean) / (d std)), writes
+//           dP_i and stores each dm_ij at the slot of the reverse edge;
+//           kernel 2, one thread per (node j, 4 channels), sums its own row of
+//           that buffer into dQ_j.  No atomics: the result is deterministic.
+#include <cfloat>
+
+#include "kernels.cuh"
+
+namespace gcnn {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void flag(unsigned *err, unsigned bits) {
+  if (err) atomicOr(err, bits);
+}
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// Sum of squared deviations from `mean` over the row (second pass).
+__device__ __forceinline__ float4 sq_dev(const float *__restrict__ PQ, const int *__restrict__ col,
+                                         int r0, int r1, int H, int c, float4 P, float4 mean) {
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int e = r0; e < r1; ++e) {
+    const float4 m = add4(P, ld4(PQ + (size_t)col[e] * 2 * H + H + c));
+    const float tx = m.x - mean.x, ty = m.y - mean.y, tz = m.z - mean.z, tw = m.w - mean.w;
+    v.x += tx * tx; v.y += ty * ty; v.z += tz * tz; v.w += tw * tw;
+  }
+  return v;
+}
+
+// true iff every source index of the row is in [0, N)
+__device__ __forceinline__ bool row_ok(const int *__restrict__ col, int r0, int r1, int N) {
+  for (int e = r0; e < r1; ++e) {
+    const int j = col[e];
+    if (j < 0 || j >= N) return false;
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(kThreads)
+aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row_ptr,
+                     const int *__restrict__ col, const float *__restrict__ PQ,
+                     float *__restrict__ agg, float eps, unsigned *err) {
+  const int H4 = H >> 2;
+  const int N = min(n_cap, dims.nodes(n_cap));
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)N * H4) return;
+  const int i = (int)(t / H4), c = (int)(t % H4) * 4;
+  const int r0 = row_ptr[i], r1 = row_ptr[i + 1];
+  float *out = agg + (size_t)i * kAgg * H + c;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (r1 <= r0 || !row_ok(col, r0, r1, N)) {
+    if (r1 < r0 || !row_ok(col, r0, r1, N)) flag(err, kErrIndex);
+#pragma unroll
+    for (int a = 0; a < kAgg; ++a) st4(out + a * H, z);
+    return;
+  }
+  const float4 P = ld4(PQ + (size_t)i * 2 * H + c);
+  float4 s = z;
+  float4 mn = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX);
+  float4 mx = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX);
+  for (int e = r0; e < r1; ++e) {
+    const float4 m = add4(P, ld4(PQ + (size_t)col[e] * 2 * H + H + c));
+    s = add4(s, m);
+    mn.x = fminf(mn.x, m.x); mn.y = fminf(mn.y, m.y); mn.z = fminf(mn.z, m.z); mn.w = fminf(mn.w, m.w);
+    mx.x = fmaxf(mx.x, m.x); mx.y = fmaxf(mx.y, m.y); mx.z = fmaxf(mx.z, m.z); mx.w = fmaxf(mx.w, m.w);
+  }
+  const float d = (float)(r1 - r0);
+  const float4 mean = make_float4(s.x / d, s.y / d, s.z / d, s.w / d);
+  const float4 v = sq_dev(PQ, col, r0, r1, H, c, P, mean);
+  float4 sd;
+  sd.x = sqrtf(fmaxf(v.x / d, 0.f) + eps);
+  sd.y = sqrtf(fmaxf(v.y / d, 0.f) + eps);
+  sd.z = sqrtf(fmaxf(v.z / d, 0.f) + eps);
+  sd.w = sqrtf(fmaxf(v.w / d, 0.f) + eps);
+  st4(out + 0 * H, s);
+  st4(out + 1 * H, mean);
+  st4(out + 2 * H, mn);
+  st4(out + 3 * H, mx);
+  st4(out + 4 * H, sd);
+}
+
+__device__ __forceinline__ float route(float m, float base, float mn, float dmin, float nmin,
+                                       float mx, float dmax, float nmax, float var, float mean,
+                                       float dstd, float d, float sd) {
+  float g = base;
+  if (m == mn) g += dmin / nmin;
+  if (m == mx) g += dmax / nmax;
+  if (var > 0.f) g += dstd * (m - mean) / (d * sd);
+  return g;
+}
+
+__global__ void __launch_bounds__(kThreads)
+aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *__restrict__ row_ptr,
+                          const int *__restrict__ col, const int *__restrict__ rev,
+                          const float *__restrict__ PQ, const float *__restrict__ agg,
+                          const float *__restrict__ dagg, float *__restrict__ dPQ,
+                          float *__restrict__ dm, unsigned *err) {
+  const int H4 = H >> 2;
+  const int N = min(n_cap, dims.nodes(n_cap));
+  const int E = min(e_cap, dims.edges(e_cap));
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)N * H4) return;
+  const int i = (int)(t / H4), c = (int)(t % H4) * 4;
+  const int r0 = row_ptr[i], r1 = row_ptr[i + 1];
+  float4 dP = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (r1 <= r0 || r1 > E || !row_ok(col, r0, r1, N)) {
+    if (r1 < r0 || r1 > E || !row_ok(col, r0, r1, N)) flag(err, kErrIndex);
+    st4(dPQ + (size_t)i * 2 * H + c, dP);
+    return;
+  }
+  const float d = (float)(r1 - r0);
+  const float *a = agg + (size_t)i * kAgg * H + c;
+  const float *da = dagg + (size_t)i * kAgg * H + c;
+  const float4 P = ld4(PQ + (size_t)i * 2 * H + c);
+  const float4 mean = ld4(a + 1 * H), mn = ld4(a + 2 * H), mx = ld4(a + 3 * H), sd = ld4(a + 4 * H);
+  const float4 dsum = ld4(da + 0 * H), dmean = ld4(da + 1 * H), dmin = ld4(da + 2 * H);
+  const float4 dmax = ld4(da + 3 * H), dstd = ld4(da + 4 * H);
+  float4 nmin = make_float4(0.f, 0.f, 0.f, 0.f), nmax = nmin;
+  for (int e = r0; e < r1; ++e) {
+    const float4 m = add4(P, ld4(PQ + (size_t)col[e] * 2 * H + H + c));
+    nmin.x += (m.x == mn.x); nmin.y += (m.y == mn.y); nmin.z += (m.z == mn.z); nmin.w += (m.w == mn.w);
+    nmax.x += (m.x == mx.x); nmax.y += (m.y == mx.y); nmax.z += (m.z == mx.z); nmax.w += (m.w == mx.w);
+  }
+  float4 var = sq_dev(PQ, col, r0, r1, H, c, P, mean);
+  var.x /= d; var.y /= d; var.z /= d; var.w /= d;
+  const float4 base = make_float4(dsum.x + dmean.x / d, dsum.y + dmean.y / d, dsum.z + dmean.z / d,
+                                  dsum.w + dmean.w / d);
+  for (int e = r0; e < r1; ++e) {
+    const float4 m = add4(P, ld4(PQ + (size_t)col[e] * 2 * H + H + c));
+    float4 g;
+    g.x = route(m.x, base.x, mn.x, dmin.x, nmin.x, mx.x, dmax.x, nmax.x, var.x, mean.x, dstd.x, d, sd.x);
+    g.y = route(m.y, base.y, mn.y, dmin.y, nmin.y, mx.y, dmax.y, nmax.y, var.y, mean.y, dstd.y, d, sd.y);
+    g.z = route(m.z, base.z, mn.z, dmin.z, nmin.z, mx.z, dmax.z, nmax.z, var.z, mean.z, dstd.z, d, sd.z);
+    g.w = route(m.w, base.w, mn.w, dmin.w, nmin.w, mx.w, dmax.w, nmax.w, var.w, mean.w, dstd.w, d, sd.w);
+    dP = add4(dP, g);
+    const int re = rev[e];
+    if (re >= 0 && re < E) st4(dm + (size_t)re * H + c, g);
+    else flag(err, kErrIndex);
+  }
+  st4(dPQ + (size_t)i * 2 * H + c, dP);
+}
+
+__global__ void __launch_bounds__(kThreads)
+aggregate_bwd_gather_kernel(int n_cap, int e_cap, int H, DevDims dims,
+                            const int *__restrict__ row_ptr, const float *__restrict__ dm,
+                            float *__restrict__ dPQ, unsigned *err) {
+  const int H4 = H >> 2;
+  const int N = min(n_cap, dims.nodes(n_cap));
+  const int E = min(e_cap, dims.edges(e_cap));
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)N * H4) return;
+  const int j = (int)(t / H4), c = (int)(t % H4) * 4;
+  int r0 = row_ptr[j], r1 = row_ptr[j + 1];
+  if (r1 < r0 || r0 < 0 || r1 > E) { flag(err, kErrIndex); r1 = r0; }
+  float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int e = r0; e < r1; ++e) q = add4(q, ld4(dm + (size_t)e * H + c));
+  st4(dPQ + (size_t)j * 2 * H + H + c, q);
+}
+
+}  // namespace
+
+int launch_aggregate_fwd(int n_nodes, int H, DevDims dims, const int *row_ptr, const int *col,
+                         const float *PQ, float *agg, float eps, unsigned *err, cudaStream_t s) {
+  if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
+  if (n_nodes <= 0) return GCNN_OK;
+  const long long work = (long long)n_nodes * (H / 4);
+  aggregate_fwd_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(n_nodes, H, dims, row_ptr, col,
+                                                                      PQ, agg, eps, err);
+  GCNN_LAUNCH_CHECK();
+  return GCNN_OK;
+}
+
+int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const int *row_ptr,
+                         const int *col, const int *rev, const float *PQ, const float *agg,
+                         const float *dagg, float *dPQ, float *scratch, float eps, unsigned *err,
+                         cudaStream_t s) {
+  (void)eps;
+  if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
+  if (n_nodes <= 0) return GCNN_OK;
+  const long long work = (long long)n_nodes * (H / 4);
+  aggregate_bwd_edge_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(
+      n_nodes, n_edges, H, dims, row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, err);
+  GCNN_LAUNCH_CHECK();
+  aggregate_bwd_gather_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(n_nodes, n_edges, H, dims,
+                                                                            row_ptr, scratch, dPQ, err);
+  GCNN_LAUNCH_CHECK();
+  return GCNN_OK;
+}
+
+}  // namespace gcnn

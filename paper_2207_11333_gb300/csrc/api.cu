@@ -1,0 +1,524 @@
+// C ABI (include/gcnn.h): argument checking, context lifetime, the arena,
+// collation staging, CUDA-graph capture of the training step, checkpoints.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "context.h"
+
+using namespace gcnn;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+struct Carve {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t n) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    const size_t at = off;
+    off += std::max<size_t>(n, 1) * sizeof(T);
+    return at;
+  }
+};
+
+int64_t layer_size_of(int64_t H) { return 2 * H * H + H + 16 * H * H + H; }
+
+int64_t param_count_of(const gcnn_config &c) {
+  const int64_t H = c.hidden, Hh = c.head_hidden;
+  return (int64_t)c.n_types * H + (int64_t)c.layers * layer_size_of(H) + H * Hh + 2 * Hh + 1;
+}
+
+int check_config(const gcnn_config *c) {
+  if (!c) return set_error(GCNN_EINVAL, "null config");
+  if (c->hidden < 8 || c->hidden > 1024 || c->hidden % 8)
+    return set_error(GCNN_EINVAL, "hidden must be a multiple of 8 in [8, 1024] (got %d)", c->hidden);
+  if (c->layers < 1 || c->layers > 64) return set_error(GCNN_EINVAL, "layers must be in [1, 64]");
+  if (c->n_types < 1 || c->n_types > 16) return set_error(GCNN_EINVAL, "n_types must be in [1, 16]");
+  if (c->head_hidden < 1 || c->head_hidden > 1024) return set_error(GCNN_EINVAL, "head_hidden must be in [1, 1024]");
+  if (c->max_graphs < 1 || c->max_nodes < 1 || c->max_edges < 0)
+    return set_error(GCNN_EINVAL, "capacities must be positive");
+  if ((int64_t)c->max_nodes * c->hidden * 16 > (int64_t)1 << 31 ||
+      (int64_t)c->max_edges * c->hidden > (int64_t)1 << 31)
+    return set_error(GCNN_EINVAL, "capacity too large for 32-bit indexing");
+  if (c->precision != GCNN_PREC_FP32)
+    return set_error(GCNN_EINVAL, "precision %d is not available in this build", c->precision);
+  if (!(c->delta > 0.0) || !(c->std_eps >= 0.0)) return set_error(GCNN_EINVAL, "delta must be > 0, std_eps >= 0");
+  return GCNN_OK;
+}
+
+int make_scaler_table(gcnn_ctx *c) {
+  std::vector<float> tab(2 * (kMaxGraphEdges + 1));
+  for (int d = 0; d <= kMaxGraphEdges; ++d) {
+    const double dd = d > 1 ? (double)d : 1.0;
+    tab[2 * d] = (float)(std::log(dd + 1.0) / c->cfg.delta);
+    tab[2 * d + 1] = (float)(c->cfg.delta / std::log(dd + 1.0));
+  }
+  GCNN_CUDA_TRY(cudaMemcpy(c->scal_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return GCNN_OK;
+}
+
+size_t stage_bytes_of(int Gc, int Nc, int Ec) {
+  // mini-store: node_ptr, edge_ptr (i64 [G+1]), y (f32 [G]), types (u8 [N]), edges (u8 [2E]), ids
+  return 3 * 8 * (size_t)(Gc + 1) + 4 * (size_t)Gc + (size_t)Nc + 2 * (size_t)Ec + 4 * 64;
+}
+
+void destroy_ctx(gcnn_ctx *c) {
+  if (!c) return;
+  for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  for (int q = 0; q < 2; ++q) {
+    if (c->stage_host[q]) cudaFreeHost(c->stage_host[q]);
+    if (c->stage_ev[q]) cudaEventDestroy(c->stage_ev[q]);
+  }
+  if (c->lr_pinned) cudaFreeHost(c->lr_pinned);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->order_dev) cudaFree(c->order_dev);
+  if (c->dmem) cudaFree(c->dmem);
+  delete c;
+}
+
+int sync(gcnn_ctx *c) {
+  GCNN_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return GCNN_OK;
+}
+
+int same_batch(const gcnn_ctx *c, const gcnn_batch *b) {
+  if (!b) return set_error(GCNN_EINVAL, "null batch");
+  if (b->node_off != c->bb.node_off) return set_error(GCNN_EINVAL, "batch was not collated by this context");
+  if (b->n_graphs < 0 || b->n_graphs > c->Gc || b->n_nodes < 0 || b->n_nodes > c->Nc || b->n_edges < 0 ||
+      b->n_edges > c->Ec)
+    return set_error(GCNN_EINVAL, "batch exceeds the context capacity");
+  return GCNN_OK;
+}
+
+int set_lr(gcnn_ctx *c, float lr) {
+  if (!(lr >= 0.f) || !std::isfinite(lr)) return set_error(GCNN_EINVAL, "learning rate must be finite and >= 0");
+  if (lr != c->lr_host) {
+    *c->lr_pinned = lr;
+    GCNN_CUDA_TRY(cudaMemcpyAsync(c->lr_dev, c->lr_pinned, sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    // the pinned source must stay valid until the copy ran
+    GCNN_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->lr_host = lr;
+  }
+  return GCNN_OK;
+}
+
+int round_up(int v, int m, int cap) { return std::min(cap, (v + m - 1) / m * m); }
+
+// Launch grids cover the batch rounded up to a bucket; kernels read the true
+// sizes from the device, so one captured graph serves every batch in a bucket.
+int grid_nodes(const gcnn_ctx *c, const gcnn_batch *b) { return round_up(std::max(b->n_nodes, 1), 256, c->Nc); }
+int grid_edges(const gcnn_ctx *c, const gcnn_batch *b) { return round_up(std::max(b->n_edges, 1), 512, c->Ec); }
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+const char *gcnn_last_error(void) { return last_error(); }
+int gcnn_version(void) { return 100; }
+
+// ---------------------------------------------------------------- store
+int gcnn_store_open(const char *path, gcnn_store **out) { return store_open(path, out); }
+int gcnn_store_close(gcnn_store *st) { return store_close(st); }
+
+int gcnn_store_info(const gcnn_store *st, int64_t *g, int64_t *n, int64_t *e) {
+  if (!st) return set_error(GCNN_EINVAL, "null store");
+  if (g) *g = st->G;
+  if (n) *n = st->N;
+  if (e) *e = st->E;
+  return GCNN_OK;
+}
+
+int gcnn_store_batch_size(const gcnn_store *st, const int64_t *ids, int64_t n, int64_t *nn, int64_t *ne) {
+  if (!st || (!ids && n > 0) || n < 0 || !nn || !ne) return set_error(GCNN_EINVAL, "store_batch_size: bad arguments");
+  return store_batch_size(st, ids, n, nn, ne);
+}
+
+int gcnn_store_delta(const gcnn_store *st, const int64_t *ids, int64_t n, double *delta) {
+  if (!st || !delta || n < 0) return set_error(GCNN_EINVAL, "store_delta: bad arguments");
+  return store_delta(st, ids, n, delta);
+}
+
+int gcnn_store_set_targets(gcnn_store *st, const float *y, int64_t n) { return store_set_targets(st, y, n); }
+int gcnn_store_to_device(gcnn_store *st) { return store_to_device(st); }
+
+// ---------------------------------------------------------------- context
+int gcnn_config_default(gcnn_config *cfg, int32_t hidden, int32_t layers, int32_t max_graphs,
+                        int32_t max_nodes, int32_t max_edges) {
+  if (!cfg) return set_error(GCNN_EINVAL, "null config");
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->hidden = hidden;
+  cfg->layers = layers;
+  cfg->n_types = 7;
+  cfg->head_hidden = hidden;
+  cfg->max_graphs = max_graphs;
+  cfg->max_nodes = max_nodes;
+  cfg->max_edges = max_edges;
+  cfg->precision = GCNN_PREC_FP32;
+  cfg->recompute = 0;
+  cfg->delta = 1.0;
+  cfg->std_eps = 1e-5;
+  cfg->beta1 = 0.9;
+  cfg->beta2 = 0.999;
+  cfg->adam_eps = 1e-8;
+  cfg->weight_decay = 0.0;
+  return GCNN_OK;
+}
+
+int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
+  if (!out) return set_error(GCNN_EINVAL, "null output");
+  *out = nullptr;
+  GCNN_TRY(check_config(cfg));
+  gcnn_ctx *c = new gcnn_ctx();
+  c->cfg = *cfg;
+  c->stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e0 = cudaGetDevice(&c->device);
+  if (e0 != cudaSuccess) {
+    delete c;
+    return set_error(GCNN_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e0));
+  }
+  c->H = cfg->hidden; c->L = cfg->layers; c->T = cfg->n_types; c->Hh = cfg->head_hidden;
+  c->layer_size = layer_size_of(c->H);
+  c->P = param_count_of(*cfg);
+  c->Gc = cfg->max_graphs; c->Nc = cfg->max_nodes; c->Ec = cfg->max_edges;
+  const size_t H = c->H, Nc = c->Nc, Ec = c->Ec, Gc = c->Gc, L = c->L, Hh = c->Hh;
+  c->emb_chunks = (int)ceil_div(Nc, 64);
+  // split-K workspace: the largest of the step's GEMMs
+  // (over every node-count bucket a batch can launch with)
+  size_t wsf = 0;
+  for (int ng = 256;; ng += 256) {
+    const int n = std::min(ng, (int)Nc), h = (int)H;
+    wsf = std::max(wsf, gemm_simt_workspace_floats(n, 2 * h, h));
+    wsf = std::max(wsf, gemm_simt_workspace_floats(n, h, 16 * h));
+    wsf = std::max(wsf, gemm_simt_workspace_floats(16 * h + 1, h, n));
+    wsf = std::max(wsf, gemm_simt_workspace_floats(n, kAgg * h, 3 * h));
+    wsf = std::max(wsf, gemm_simt_workspace_floats(h + 1, 2 * h, n));
+    wsf = std::max(wsf, gemm_simt_workspace_floats(n, h, 3 * h));
+    if (n == (int)Nc) break;
+  }
+  // sizes of every buffer, carved from one allocation
+  Carve cv;
+  const size_t o_params = cv.take<float>(c->P), o_grads = cv.take<float>(c->P);
+  const size_t o_m = cv.take<float>(c->P), o_v = cv.take<float>(c->P);
+  const size_t o_opt = cv.take<int>(16), o_lr = cv.take<float>(4);
+  const size_t o_tab = cv.take<float>(2 * (kMaxGraphEdges + 1)), o_err = cv.take<unsigned>(4);
+  const size_t o_node_off = cv.take<int>(Gc + 1), o_edge_off = cv.take<int>(Gc + 1);
+  const size_t o_gid = cv.take<int>(Nc), o_rp = cv.take<int>(Nc + 1), o_col = cv.take<int>(Ec);
+  const size_t o_rev = cv.take<int>(Ec), o_deg = cv.take<int>(Nc), o_amp = cv.take<float>(Nc);
+  const size_t o_att = cv.take<float>(Nc), o_y = cv.take<float>(Gc), o_types = cv.take<uint8_t>(Nc);
+  const size_t o_dims = cv.take<int>(4), o_ids = cv.take<int64_t>(Gc);
+  c->stage_bytes = stage_bytes_of((int)Gc, (int)Nc, (int)Ec);
+  const size_t o_stage = cv.take<char>(c->stage_bytes);
+  const size_t o_xs = cv.take<float>((L + 1) * Nc * H), o_pq = cv.take<float>(L * Nc * 2 * H);
+  const size_t o_agg = cv.take<float>((cfg->recompute ? 1 : L) * Nc * kAgg * H);
+  const size_t o_pool = cv.take<float>(Gc * H), o_z1 = cv.take<float>(Gc * Hh), o_pred = cv.take<float>(Gc);
+  const size_t o_dpred = cv.take<float>(Gc), o_dz1 = cv.take<float>(Gc * Hh), o_dg = cv.take<float>(Gc * H);
+  const size_t o_dH = cv.take<float>(Nc * H), o_dX = cv.take<float>(Nc * H);
+  const size_t o_dagg = cv.take<float>(Nc * kAgg * H), o_dPQ = cv.take<float>(Nc * 2 * H);
+  const size_t o_dm = cv.take<float>(Ec * H);
+  const size_t o_embp = cv.take<float>((size_t)c->emb_chunks * c->T * H);
+  const size_t o_ws = cv.take<float>(wsf);
+  c->dbytes = cv.off;
+  cudaError_t e = cudaMalloc(&c->dmem, c->dbytes);
+  if (e != cudaSuccess) {
+    destroy_ctx(c);
+    return set_error(GCNN_ENOMEM, "cudaMalloc(%zu bytes): %s", c->dbytes, cudaGetErrorString(e));
+  }
+  char *b = c->dmem;
+  c->params = (float *)(b + o_params); c->grads = (float *)(b + o_grads);
+  c->adam_m = (float *)(b + o_m); c->adam_v = (float *)(b + o_v);
+  c->opt_state = (int *)(b + o_opt); c->lr_dev = (float *)(b + o_lr);
+  c->scal_tab = (float *)(b + o_tab); c->err = (unsigned *)(b + o_err);
+  c->bb.node_off = (int *)(b + o_node_off); c->bb.edge_off = (int *)(b + o_edge_off);
+  c->bb.graph_id = (int *)(b + o_gid); c->bb.row_ptr = (int *)(b + o_rp); c->bb.col = (int *)(b + o_col);
+  c->bb.rev = (int *)(b + o_rev); c->bb.deg = (int *)(b + o_deg); c->bb.amp = (float *)(b + o_amp);
+  c->bb.att = (float *)(b + o_att); c->bb.y = (float *)(b + o_y); c->bb.types = (uint8_t *)(b + o_types);
+  c->bb.dims = (int *)(b + o_dims); c->ids_dev = (int64_t *)(b + o_ids);
+  c->stage_dev = b + o_stage;
+  c->xs = (float *)(b + o_xs); c->PQ = (float *)(b + o_pq); c->agg = (float *)(b + o_agg);
+  c->pooled = (float *)(b + o_pool); c->z1 = (float *)(b + o_z1); c->pred = (float *)(b + o_pred);
+  c->dpred = (float *)(b + o_dpred); c->dz1 = (float *)(b + o_dz1); c->dg = (float *)(b + o_dg);
+  c->dH = (float *)(b + o_dH); c->dX = (float *)(b + o_dX); c->dagg = (float *)(b + o_dagg);
+  c->dPQ = (float *)(b + o_dPQ); c->dm = (float *)(b + o_dm); c->emb_partial = (float *)(b + o_embp);
+  c->ws.partial = (float *)(b + o_ws); c->ws.floats = wsf;
+  int rc = GCNN_OK;
+  if (cudaMemset(c->dmem, 0, c->dbytes) != cudaSuccess) rc = set_error(GCNN_ECUDA, "cudaMemset failed");
+  for (int q = 0; q < 2 && rc == GCNN_OK; ++q) {
+    if (cudaMallocHost(&c->stage_host[q], c->stage_bytes) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->stage_ev[q], cudaEventDisableTiming) != cudaSuccess)
+      rc = set_error(GCNN_ENOMEM, "cannot allocate pinned staging memory");
+  }
+  if (rc == GCNN_OK && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    rc = set_error(GCNN_ECUDA, "cannot create the capture stream");
+  if (rc == GCNN_OK && cudaMallocHost(&c->lr_pinned, sizeof(float)) != cudaSuccess)
+    rc = set_error(GCNN_ENOMEM, "cannot allocate pinned memory");
+  if (rc == GCNN_OK) rc = make_scaler_table(c);
+  if (rc == GCNN_OK) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  }
+  if (rc != GCNN_OK) {
+    destroy_ctx(c);
+    return rc;
+  }
+  *out = c;
+  return GCNN_OK;
+}
+
+int gcnn_destroy(gcnn_ctx *c) {
+  if (!c) return GCNN_OK;
+  cudaStreamSynchronize(c->stream);
+  destroy_ctx(c);
+  return GCNN_OK;
+}
+
+int gcnn_param_count(const gcnn_ctx *c, int64_t *n) {
+  if (!c || !n) return set_error(GCNN_EINVAL, "null argument");
+  *n = c->P;
+  return GCNN_OK;
+}
+
+static int copy_flat(gcnn_ctx *c, float *dev, const float *src, float *dst, int64_t n, int on_device) {
+  if (!c || n != c->P) return set_error(GCNN_EINVAL, "expected %lld floats", c ? (long long)c->P : 0LL);
+  const cudaMemcpyKind k = src ? (on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice)
+                               : (on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+  if (src) GCNN_CUDA_TRY(cudaMemcpyAsync(dev, src, n * sizeof(float), k, c->stream));
+  else GCNN_CUDA_TRY(cudaMemcpyAsync(dst, dev, n * sizeof(float), k, c->stream));
+  return sync(c);
+}
+
+int gcnn_set_params(gcnn_ctx *c, const float *src, int64_t n, int on_device) {
+  if (!src) return set_error(GCNN_EINVAL, "null source");
+  return copy_flat(c, c ? c->params : nullptr, src, nullptr, n, on_device);
+}
+int gcnn_get_params(gcnn_ctx *c, float *dst, int64_t n, int on_device) {
+  if (!dst) return set_error(GCNN_EINVAL, "null destination");
+  return copy_flat(c, c ? c->params : nullptr, nullptr, dst, n, on_device);
+}
+int gcnn_get_grads(gcnn_ctx *c, float *dst, int64_t n, int on_device) {
+  if (!dst) return set_error(GCNN_EINVAL, "null destination");
+  return copy_flat(c, c ? c->grads : nullptr, nullptr, dst, n, on_device);
+}
+
+int gcnn_reset_optimizer(gcnn_ctx *c) {
+  if (!c) return set_error(GCNN_EINVAL, "null context");
+  GCNN_CUDA_TRY(cudaMemsetAsync(c->adam_m, 0, c->P * sizeof(float), c->stream));
+  GCNN_CUDA_TRY(cudaMemsetAsync(c->adam_v, 0, c->P * sizeof(float), c->stream));
+  GCNN_CUDA_TRY(cudaMemsetAsync(c->opt_state, 0, 16 * sizeof(int), c->stream));
+  return sync(c);
+}
+
+int gcnn_save(gcnn_ctx *c, const char *path) {
+  if (!c || !path) return set_error(GCNN_EINVAL, "null argument");
+  std::vector<float> buf(3 * (size_t)c->P);
+  int step = 0;
+  GCNN_CUDA_TRY(cudaMemcpyAsync(buf.data(), c->params, c->P * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  GCNN_CUDA_TRY(cudaMemcpyAsync(buf.data() + c->P, c->adam_m, c->P * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  GCNN_CUDA_TRY(cudaMemcpyAsync(buf.data() + 2 * c->P, c->adam_v, c->P * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  GCNN_CUDA_TRY(cudaMemcpyAsync(&step, c->opt_state, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  GCNN_TRY(sync(c));
+  FILE *f = fopen(path, "wb");
+  if (!f) return set_error(GCNN_EINVAL, "cannot write %s", path);
+  const int64_t P = c->P;
+  bool ok = fwrite("GCNNCKP1", 8, 1, f) == 1 && fwrite(&P, sizeof(P), 1, f) == 1 &&
+            fwrite(&step, sizeof(step), 1, f) == 1 && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  ok = (fclose(f) == 0) && ok;
+  return ok ? GCNN_OK : set_error(GCNN_EINVAL, "short write to %s", path);
+}
+
+int gcnn_load(gcnn_ctx *c, const char *path) {
+  if (!c || !path) return set_error(GCNN_EINVAL, "null argument");
+  FILE *f = fopen(path, "rb");
+  if (!f) return set_error(GCNN_EINVAL, "cannot read %s", path);
+  char magic[8];
+  int64_t P = 0;
+  int step = 0;
+  std::vector<float> buf(3 * (size_t)c->P);
+  bool ok = fread(magic, 8, 1, f) == 1 && memcmp(magic, "GCNNCKP1", 8) == 0 && fread(&P, sizeof(P), 1, f) == 1 &&
+            P == c->P && fread(&step, sizeof(step), 1, f) == 1 &&
+            fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  fclose(f);
+  if (!ok) return set_error(GCNN_EFORMAT, "%s is not a checkpoint of this model", path);
+  GCNN_CUDA_TRY(cudaMemcpyAsync(c->params, buf.data(), c->P * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  GCNN_CUDA_TRY(cudaMemcpyAsync(c->adam_m, buf.data() + c->P, c->P * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  GCNN_CUDA_TRY(cudaMemcpyAsync(c->adam_v, buf.data() + 2 * c->P, c->P * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  GCNN_CUDA_TRY(cudaMemcpyAsync(c->opt_state, &step, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  return sync(c);
+}
+
+int gcnn_check(gcnn_ctx *c) {
+  if (!c) return set_error(GCNN_EINVAL, "null context");
+  unsigned w = 0;
+  GCNN_CUDA_TRY(cudaMemcpyAsync(&w, c->err, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
+  GCNN_TRY(sync(c));
+  if (w) {
+    GCNN_CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    GCNN_TRY(sync(c));
+    return set_error(GCNN_EDEVICE, "device bounds check fired (bits 0x%x)", w);
+  }
+  return GCNN_OK;
+}
+
+// ---------------------------------------------------------------- batches
+int gcnn_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n, gcnn_batch *out) {
+  if (!c || !st || !out || n < 0 || (n > 0 && !ids)) return set_error(GCNN_EINVAL, "collate: bad arguments");
+  return ctx_collate(c, st, ids, n, out);
+}
+
+int gcnn_set_order(gcnn_ctx *c, const gcnn_store *st, const int64_t *order, int64_t n) {
+  if (!c || !st || !order || n < 1) return set_error(GCNN_EINVAL, "set_order: bad arguments");
+  if (!st->dev) return set_error(GCNN_ESTATE, "set_order needs a device-resident store");
+  for (int64_t q = 0; q < n; ++q)
+    if (order[q] < 0 || order[q] >= st->G) return set_error(GCNN_EINVAL, "set_order: id out of range");
+  if (c->order_dev) {
+    GCNN_TRY(sync(c));
+    cudaFree(c->order_dev);
+    c->order_dev = nullptr;
+  }
+  GCNN_CUDA_TRY(cudaMalloc(&c->order_dev, n * sizeof(int64_t)));
+  GCNN_CUDA_TRY(cudaMemcpy(c->order_dev, order, n * sizeof(int64_t), cudaMemcpyHostToDevice));
+  c->order_host.assign(order, order + n);
+  c->order_store = st;
+  return GCNN_OK;
+}
+
+int gcnn_collate_range(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count, gcnn_batch *out) {
+  if (!c || !st || !out || count < 0) return set_error(GCNN_EINVAL, "collate_range: bad arguments");
+  return ctx_collate_range(c, st, first, count, out);
+}
+
+int gcnn_batch_export(gcnn_ctx *c, const gcnn_batch *b, int32_t *node_off, int32_t *graph_id, int32_t *row_ptr,
+                      int32_t *col, int32_t *rev, int32_t *deg, float *amp, float *att, uint8_t *types, float *y) {
+  if (!c) return set_error(GCNN_EINVAL, "null context");
+  GCNN_TRY(same_batch(c, b));
+  GCNN_TRY(sync(c));
+  const size_t G = b->n_graphs, N = b->n_nodes, E = b->n_edges;
+  struct Item { void *dst; const void *src; size_t bytes; } items[] = {
+      {node_off, b->node_off, (G + 1) * 4}, {graph_id, b->graph_id, N * 4}, {row_ptr, b->row_ptr, (N + 1) * 4},
+      {col, b->col, E * 4}, {rev, b->rev, E * 4}, {deg, b->deg, N * 4}, {amp, b->amp, N * 4},
+      {att, b->att, N * 4}, {types, b->types, N}, {y, b->y, G * 4}};
+  for (auto &it : items)
+    if (it.dst && it.bytes) GCNN_CUDA_TRY(cudaMemcpy(it.dst, it.src, it.bytes, cudaMemcpyDeviceToHost));
+  return GCNN_OK;
+}
+
+// ---------------------------------------------------------------- training
+int gcnn_forward(gcnn_ctx *c, const gcnn_batch *b, float *pred, int train) {
+  if (!c) return set_error(GCNN_EINVAL, "null context");
+  GCNN_TRY(same_batch(c, b));
+  // same grid buckets as the captured step, so both give bit-identical results
+  GCNN_TRY(ctx_forward(c, b->n_graphs, grid_nodes(c, b), grid_edges(c, b), train != 0));
+  if (pred && b->n_graphs > 0)
+    GCNN_CUDA_TRY(cudaMemcpyAsync(pred, c->pred, b->n_graphs * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+  c->have_fwd = train != 0;
+  c->fwd_G = b->n_graphs; c->fwd_N = b->n_nodes; c->fwd_E = b->n_edges;
+  return GCNN_OK;
+}
+
+int gcnn_backward(gcnn_ctx *c, const gcnn_batch *b, const float *dpred, double *loss_accum) {
+  if (!c) return set_error(GCNN_EINVAL, "null context");
+  GCNN_TRY(same_batch(c, b));
+  if (!c->have_fwd || c->fwd_G != b->n_graphs || c->fwd_N != b->n_nodes)
+    return set_error(GCNN_ESTATE, "backward needs a forward(train=1) on the same batch");
+  return ctx_backward(c, b->n_graphs, grid_nodes(c, b), grid_edges(c, b), dpred, loss_accum);
+}
+
+int gcnn_step(gcnn_ctx *c, float lr) {
+  if (!c) return set_error(GCNN_EINVAL, "null context");
+  GCNN_TRY(set_lr(c, lr));
+  return ctx_step(c);
+}
+
+int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_accum) {
+  if (!c) return set_error(GCNN_EINVAL, "null context");
+  GCNN_TRY(same_batch(c, b));
+  GCNN_TRY(set_lr(c, lr));
+  const int G = b->n_graphs;
+  const int Ng = grid_nodes(c, b), Eg = grid_edges(c, b);
+  auto key = std::make_tuple(G, Ng, Eg, (const double *)loss_accum);
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    // capture on the context's private stream (the legacy default stream
+    // cannot be captured); the graph is then launched on the caller's stream
+    cudaGraph_t graph = nullptr;
+    GCNN_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      c->stream = user;
+      return set_error(GCNN_ECUDA, "begin capture: %s", cudaGetErrorString(e));
+    }
+    int rc = ctx_forward(c, G, Ng, Eg, true);
+    if (rc == GCNN_OK) rc = ctx_backward(c, G, Ng, Eg, nullptr, loss_accum);
+    if (rc == GCNN_OK) rc = ctx_step(c);
+    e = cudaStreamEndCapture(c->stream, &graph);
+    c->stream = user;
+    if (rc != GCNN_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return set_error(GCNN_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return set_error(GCNN_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    it = c->graphs.emplace(key, exec).first;
+  }
+  GCNN_CUDA_TRY(cudaGraphLaunch(it->second, c->stream));
+  c->have_fwd = true;
+  c->fwd_G = b->n_graphs; c->fwd_N = b->n_nodes; c->fwd_E = b->n_edges;
+  return GCNN_OK;
+}
+
+int gcnn_get_activation(gcnn_ctx *c, int32_t layer, float *dst, int64_t n) {
+  if (!c || !dst || layer < 0 || layer > c->L) return set_error(GCNN_EINVAL, "get_activation: bad arguments");
+  if (n != (int64_t)c->fwd_N * c->H) return set_error(GCNN_EINVAL, "get_activation: expected N*H floats");
+  GCNN_CUDA_TRY(cudaMemcpyAsync(dst, c->xs + (size_t)layer * c->Nc * c->H, n * sizeof(float),
+                                cudaMemcpyDeviceToHost, c->stream));
+  return sync(c);
+}
+
+// ---------------------------------------------------------------- operators
+int gcnn_op_aggregate_fwd(int32_t n_nodes, int32_t hidden, const int32_t *row_ptr, const int32_t *col,
+                          const float *PQ, float *agg, float std_eps, void *stream) {
+  if (n_nodes < 0 || hidden <= 0 || hidden % 4 || (n_nodes > 0 && (!row_ptr || !col || !PQ || !agg)))
+    return set_error(GCNN_EINVAL, "aggregate_fwd: bad arguments (hidden must be a multiple of 4)");
+  if ((reinterpret_cast<uintptr_t>(PQ) | reinterpret_cast<uintptr_t>(agg)) % 16)
+    return set_error(GCNN_EINVAL, "aggregate_fwd: PQ and agg must be 16-byte aligned");
+  return launch_aggregate_fwd(n_nodes, hidden, DevDims{nullptr}, row_ptr, col, PQ, agg, std_eps, nullptr,
+                              static_cast<cudaStream_t>(stream));
+}
+
+int gcnn_op_aggregate_bwd(int32_t n_nodes, int32_t n_edges, int32_t hidden, const int32_t *row_ptr,
+                          const int32_t *col, const int32_t *rev, const float *PQ, const float *agg,
+                          const float *dagg, float *dPQ, float *scratch, float std_eps, void *stream) {
+  if (n_nodes < 0 || n_edges < 0 || hidden <= 0 || hidden % 4 ||
+      (n_nodes > 0 && (!row_ptr || !col || !rev || !PQ || !agg || !dagg || !dPQ || (n_edges > 0 && !scratch))))
+    return set_error(GCNN_EINVAL, "aggregate_bwd: bad arguments (hidden must be a multiple of 4)");
+  if ((reinterpret_cast<uintptr_t>(PQ) | reinterpret_cast<uintptr_t>(agg) | reinterpret_cast<uintptr_t>(dagg) |
+       reinterpret_cast<uintptr_t>(dPQ) | reinterpret_cast<uintptr_t>(scratch)) % 16)
+    return set_error(GCNN_EINVAL, "aggregate_bwd: float buffers must be 16-byte aligned");
+  return launch_aggregate_bwd(n_nodes, n_edges, hidden, DevDims{nullptr}, row_ptr, col, rev, PQ, agg, dagg, dPQ,
+                              scratch, std_eps, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+int gcnn_op_pool_fwd(int32_t n_graphs, int32_t hidden, const int32_t *node_off, const float *x, float *pooled,
+                     void *stream) {
+  if (n_graphs < 0 || hidden <= 0 || hidden % 4 || (n_graphs > 0 && (!node_off || !x || !pooled)))
+    return set_error(GCNN_EINVAL, "pool_fwd: bad arguments (hidden must be a multiple of 4)");
+  return launch_pool_fwd(n_graphs, hidden, DevDims{nullptr}, node_off, x, pooled, static_cast<cudaStream_t>(stream));
+}
+
+int gcnn_op_pool_bwd(int32_t n_graphs, int32_t n_nodes, int32_t hidden, const int32_t *node_off,
+                     const int32_t *graph_id, const float *dpooled, float *dx, void *stream) {
+  if (n_graphs < 0 || n_nodes < 0 || hidden <= 0 || hidden % 4 ||
+      (n_nodes > 0 && (!node_off || !graph_id || !dpooled || !dx)))
+    return set_error(GCNN_EINVAL, "pool_bwd: bad arguments (hidden must be a multiple of 4)");
+  return launch_pool_bwd(n_graphs, n_nodes, hidden, DevDims{nullptr}, node_off, graph_id, dpooled, dx,
+                         static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

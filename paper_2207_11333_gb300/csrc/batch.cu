@@ -1,0 +1,119 @@
+// Host side of batch collation: the per-batch read of the store (the paper's
+// data-loading phase, Sec. 4 and Fig. 5), either straight from a device-
+// resident store or through pinned staging memory and one host-to-device copy.
+#include <cstring>
+
+#include "context.h"
+
+namespace gcnn {
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+void fill_batch(const gcnn_ctx *c, int G, int64_t N, int64_t E, gcnn_batch *out) {
+  out->n_graphs = G;
+  out->n_nodes = (int32_t)N;
+  out->n_edges = (int32_t)E;
+  out->reserved = 0;
+  out->node_off = c->bb.node_off;
+  out->edge_off = c->bb.edge_off;
+  out->graph_id = c->bb.graph_id;
+  out->row_ptr = c->bb.row_ptr;
+  out->col = c->bb.col;
+  out->rev = c->bb.rev;
+  out->deg = c->bb.deg;
+  out->amp = c->bb.amp;
+  out->att = c->bb.att;
+  out->types = c->bb.types;
+  out->y = c->bb.y;
+}
+
+int check_caps(const gcnn_ctx *c, int64_t G, int64_t N, int64_t E) {
+  if (G > c->Gc || N > c->Nc || E > c->Ec)
+    return set_error(GCNN_EINVAL, "batch (%lld graphs, %lld nodes, %lld edges) exceeds capacity (%d, %d, %d)",
+                     (long long)G, (long long)N, (long long)E, c->Gc, c->Nc, c->Ec);
+  return GCNN_OK;
+}
+
+// Wait until the pinned staging buffer q is no longer read by a pending copy.
+int claim_stage(gcnn_ctx *c, int q) {
+  if (c->stage_used[q]) GCNN_CUDA_TRY(cudaEventSynchronize(c->stage_ev[q]));
+  c->stage_used[q] = false;
+  return GCNN_OK;
+}
+
+}  // namespace
+
+int ctx_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n, gcnn_batch *out) {
+  int64_t N = 0, E = 0;
+  GCNN_TRY(check_caps(c, n, 0, 0));
+  GCNN_TRY(store_batch_size(st, ids, n, &N, &E));
+  GCNN_TRY(check_caps(c, n, N, E));
+  const int q = c->stage_i;
+  c->stage_i ^= 1;
+  GCNN_TRY(claim_stage(c, q));
+  char *h = c->stage_host[q];
+  if (st->dev) {
+    // resident store: only the graph ids travel
+    memcpy(h, ids, sizeof(int64_t) * (size_t)n);
+    if (n > 0)
+      GCNN_CUDA_TRY(cudaMemcpyAsync(c->ids_dev, h, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+    GCNN_CUDA_TRY(cudaEventRecord(c->stage_ev[q], c->stream));
+    c->stage_used[q] = true;
+    GCNN_TRY(launch_collate(n, c->ids_dev, store_device_view(st), c->bb, c->scal_tab, c->Nc, c->Ec, c->err,
+                            c->stream));
+  } else {
+    // gather the graphs' slices into a mini-store in pinned memory, one copy
+    size_t o = 0;
+    const size_t o_np = o; o = align_up(o + 8 * (size_t)(n + 1), 16);
+    const size_t o_ep = o; o = align_up(o + 8 * (size_t)(n + 1), 16);
+    const size_t o_y = o;  o = align_up(o + 4 * (size_t)n, 16);
+    const size_t o_t = o;  o = align_up(o + (size_t)N, 16);
+    const size_t o_e = o;  o = align_up(o + 2 * (size_t)E, 16);
+    if (o > c->stage_bytes) return set_error(GCNN_EINVAL, "staging buffer too small");
+    int64_t *np = reinterpret_cast<int64_t *>(h + o_np), *ep = reinterpret_cast<int64_t *>(h + o_ep);
+    float *y = reinterpret_cast<float *>(h + o_y);
+    uint8_t *ty = reinterpret_cast<uint8_t *>(h + o_t), *ed = reinterpret_cast<uint8_t *>(h + o_e);
+    np[0] = 0;
+    ep[0] = 0;
+    for (int32_t g = 0; g < n; ++g) {
+      const int64_t id = ids[g];
+      const int64_t nn = st->node_ptr[id + 1] - st->node_ptr[id];
+      const int64_t ne = st->edge_ptr[id + 1] - st->edge_ptr[id];
+      memcpy(ty + np[g], st->types + st->node_ptr[id], (size_t)nn);
+      memcpy(ed + 2 * ep[g], st->edges + 2 * st->edge_ptr[id], 2 * (size_t)ne);
+      y[g] = st->y[id];
+      np[g + 1] = np[g] + nn;
+      ep[g + 1] = ep[g] + ne;
+    }
+    GCNN_CUDA_TRY(cudaMemcpyAsync(c->stage_dev, h, o, cudaMemcpyHostToDevice, c->stream));
+    GCNN_CUDA_TRY(cudaEventRecord(c->stage_ev[q], c->stream));
+    c->stage_used[q] = true;
+    const char *d = c->stage_dev;
+    StoreView v{reinterpret_cast<const int64_t *>(d + o_np), reinterpret_cast<const int64_t *>(d + o_ep),
+                reinterpret_cast<const uint8_t *>(d + o_t), reinterpret_cast<const uint8_t *>(d + o_e),
+                reinterpret_cast<const float *>(d + o_y)};
+    GCNN_TRY(launch_collate(n, nullptr, v, c->bb, c->scal_tab, c->Nc, c->Ec, c->err, c->stream));
+  }
+  fill_batch(c, n, N, E, out);
+  c->have_fwd = false;
+  return GCNN_OK;
+}
+
+int ctx_collate_range(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count, gcnn_batch *out) {
+  if (!c->order_dev || c->order_store != st) return set_error(GCNN_ESTATE, "collate_range: call gcnn_set_order first");
+  if (!st->dev) return set_error(GCNN_ESTATE, "collate_range needs a device-resident store");
+  if (first < 0 || first + count > (int64_t)c->order_host.size())
+    return set_error(GCNN_EINVAL, "collate_range: range outside the order");
+  int64_t N = 0, E = 0;
+  GCNN_TRY(check_caps(c, count, 0, 0));
+  GCNN_TRY(store_batch_size(st, c->order_host.data() + first, count, &N, &E));
+  GCNN_TRY(check_caps(c, count, N, E));
+  GCNN_TRY(launch_collate(count, c->order_dev + first, store_device_view(st), c->bb, c->scal_tab, c->Nc, c->Ec,
+                          c->err, c->stream));
+  fill_batch(c, count, N, E, out);
+  c->have_fwd = false;
+  return GCNN_OK;
+}
+
+}  // namespace gcnn

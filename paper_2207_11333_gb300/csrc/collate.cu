@@ -1,0 +1,176 @@
+// Device-side batch collation: the disjoint union of a batch of graphs read
+// from the packed store (global arrays, Sec. 4 Table 1), as the destination-
+// sorted CSR the aggregation kernels consume.
+//
+//   collate_scan_kernel   one block: per-graph node/edge counts, exclusive
+//                         scans -> node_off, edge_off, totals, targets
+//   collate_graph_kernel  one warp per graph: atom types, graph ids, in-degree
+//                         count (shared atomics), warp scan -> row_ptr, then a
+//                         rank sort of the graph's edges by (destination,
+//                         source, store order) -> col, and the reverse-edge
+//                         slot -> rev; degree scalers from a table
+//
+// Results are bit-identical to a sequential stable sort by (dst, src): every
+// position is computed from counts, never from the order of atomics.
+#include "kernels.cuh"
+
+namespace gcnn {
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kGraphWarps = 8;
+
+__global__ void __launch_bounds__(kScanThreads)
+collate_scan_kernel(int G, const int64_t *__restrict__ ids, StoreView st, BatchBuf b, int cap_nodes,
+                    int cap_edges, unsigned *err) {
+  __shared__ int warp_n[32], warp_e[32];
+  __shared__ int carry_n, carry_e;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) { carry_n = 0; carry_e = 0; }
+  __syncthreads();
+  for (int base = 0; base < G; base += kScanThreads) {
+    const int g = base + threadIdx.x;
+    int n = 0, e = 0;
+    if (g < G) {
+      const int64_t id = ids ? ids[g] : (int64_t)g;
+      n = (int)(st.node_ptr[id + 1] - st.node_ptr[id]);
+      e = (int)(st.edge_ptr[id + 1] - st.edge_ptr[id]);
+      b.y[g] = st.y[id];
+    }
+    int sn = n, se = e;  // inclusive warp scans
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int tn = __shfl_up_sync(0xffffffffu, sn, o);
+      const int te = __shfl_up_sync(0xffffffffu, se, o);
+      if (lane >= o) { sn += tn; se += te; }
+    }
+    if (lane == 31) { warp_n[w] = sn; warp_e[w] = se; }
+    __syncthreads();
+    if (w == 0) {
+      const int vn = warp_n[lane], ve = warp_e[lane];
+      int in = vn, ie = ve;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int tn = __shfl_up_sync(0xffffffffu, in, o);
+        const int te = __shfl_up_sync(0xffffffffu, ie, o);
+        if (lane >= o) { in += tn; ie += te; }
+      }
+      warp_n[lane] = in - vn;
+      warp_e[lane] = ie - ve;
+    }
+    __syncthreads();
+    const int ex_n = carry_n + warp_n[w] + sn - n;
+    const int ex_e = carry_e + warp_e[w] + se - e;
+    if (g < G) { b.node_off[g] = ex_n; b.edge_off[g] = ex_e; }
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) { carry_n = ex_n + n; carry_e = ex_e + e; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    b.node_off[G] = carry_n;
+    b.edge_off[G] = carry_e;
+    b.dims[0] = G;
+    b.dims[1] = carry_n;
+    b.dims[2] = carry_e;
+    b.dims[3] = 0;
+    if (carry_n > cap_nodes || carry_e > cap_edges) {
+      atomicOr(err, kErrCapacity);
+    } else {
+      b.row_ptr[carry_n] = carry_e;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kGraphWarps * 32)
+collate_graph_kernel(int G, const int64_t *__restrict__ ids, StoreView st, BatchBuf b,
+                     const float *__restrict__ scal_tab, int cap_nodes, int cap_edges,
+                     unsigned *err) {
+  __shared__ uint8_t s_src[kGraphWarps][kMaxGraphEdges];
+  __shared__ uint8_t s_dst[kGraphWarps][kMaxGraphEdges];
+  __shared__ int s_cnt[kGraphWarps][256];
+  __shared__ int s_start[kGraphWarps][256];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.x * kGraphWarps + w;
+  if (g >= G) return;  // warp-uniform; only warp-level synchronisation below
+  const int64_t id = ids ? ids[g] : (int64_t)g;
+  const int64_t np0 = st.node_ptr[id], ep0 = st.edge_ptr[id];
+  const int n = (int)(st.node_ptr[id + 1] - np0);
+  const int e = (int)(st.edge_ptr[id + 1] - ep0);
+  const int noff = b.node_off[g], eoff = b.edge_off[g];
+  if (n < 0 || n > kMaxGraphNodes || e < 0 || e > kMaxGraphEdges || noff < 0 || eoff < 0 ||
+      noff + n > cap_nodes || eoff + e > cap_edges) {
+    if (lane == 0) atomicOr(err, kErrCollateRange);
+    return;
+  }
+  for (int v = lane; v < 256; v += 32) s_cnt[w][v] = 0;
+  __syncwarp();
+  for (int v = lane; v < n; v += 32) {
+    b.types[noff + v] = st.types[np0 + v];
+    b.graph_id[noff + v] = g;
+  }
+  bool bad = false;
+  for (int k = lane; k < e; k += 32) {
+    int s = st.edges[2 * (ep0 + k)], d = st.edges[2 * (ep0 + k) + 1];
+    if (s >= n || d >= n) { bad = true; s = 0; d = 0; }
+    s_src[w][k] = (uint8_t)s;
+    s_dst[w][k] = (uint8_t)d;
+    atomicAdd(&s_cnt[w][d], 1);
+  }
+  if (__any_sync(0xffffffffu, bad)) {
+    if (lane == 0) atomicOr(err, kErrCollateRange);
+    return;
+  }
+  __syncwarp();
+  // exclusive scan of the in-degree counts, 8 entries per lane
+  int loc[8], tot = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { loc[q] = s_cnt[w][lane * 8 + q]; tot += loc[q]; }
+  int incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  int run = incl - tot;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) { s_start[w][lane * 8 + q] = run; run += loc[q]; }
+  __syncwarp();
+  for (int v = lane; v < n; v += 32) {
+    const int d = s_cnt[w][v];
+    b.row_ptr[noff + v] = eoff + s_start[w][v];
+    b.deg[noff + v] = d;
+    b.amp[noff + v] = scal_tab[2 * d];
+    b.att[noff + v] = scal_tab[2 * d + 1];
+  }
+  // rank of each edge inside its destination row: by source, then store order
+  for (int k = lane; k < e; k += 32) {
+    const int s = s_src[w][k], d = s_dst[w][k];
+    int rank = 0, rrank = 0, has_rev = 0;
+    for (int q = 0; q < e; ++q) {
+      const int sq = s_src[w][q], dq = s_dst[w][q];
+      rank += (dq == d) & ((sq < s) | ((sq == s) & (q < k)));
+      rrank += (dq == s) & (sq < d);
+      has_rev |= (dq == s) & (sq == d);
+    }
+    const int pos = eoff + s_start[w][d] + rank;
+    b.col[pos] = noff + s;
+    b.rev[pos] = has_rev ? eoff + s_start[w][s] + rrank : -1;
+  }
+}
+
+}  // namespace
+
+int launch_collate(int G, const int64_t *ids, StoreView st, BatchBuf b, const float *scal_tab,
+                   int cap_nodes, int cap_edges, unsigned *err, cudaStream_t s) {
+  if (G < 0) return set_error(GCNN_EINVAL, "collate: negative graph count");
+  collate_scan_kernel<<<1, kScanThreads, 0, s>>>(G, ids, st, b, cap_nodes, cap_edges, err);
+  GCNN_LAUNCH_CHECK();
+  if (G > 0) {
+    collate_graph_kernel<<<ceil_div(G, kGraphWarps), kGraphWarps * 32, 0, s>>>(
+        G, ids, st, b, scal_tab, cap_nodes, cap_edges, err);
+    GCNN_LAUNCH_CHECK();
+  }
+  return GCNN_OK;
+}
+
+}  // namespace gcnn

@@ -1,0 +1,56 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+
+#include "gcnn.h"
+
+namespace gcnn {
+
+// Thread-local error message; returns `code` so callers can `return set_error(...)`.
+int set_error(int code, const char *fmt, ...);
+
+#define GCNN_CUDA_TRY(expr)                                                                       \
+  do {                                                                                            \
+    cudaError_t e_ = (expr);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return ::gcnn::set_error(GCNN_ECUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                               __FILE__, __LINE__);                                               \
+  } while (0)
+
+#define GCNN_TRY(expr)              \
+  do {                              \
+    int r_ = (expr);                \
+    if (r_ != GCNN_OK) return r_;   \
+  } while (0)
+
+#define GCNN_LAUNCH_CHECK() GCNN_CUDA_TRY(cudaGetLastError())
+
+// Bits of the device error word (set with atomicOr by bounds checks; the
+// offending access is skipped).
+enum : unsigned {
+  kErrCollateRange = 1u,   // a graph violates the store limits or capacity
+  kErrCapacity = 2u,       // batch totals exceed the context's capacity
+  kErrIndex = 4u,          // an index read from memory is out of range
+};
+
+// Per-graph limits of the collator (a warp sorts one graph in shared memory).
+constexpr int kMaxGraphNodes = 255;
+constexpr int kMaxGraphEdges = 1024;
+
+constexpr int kAgg = 5;      // sum, mean, min, max, std
+constexpr int kScalers = 3;  // identity, amplification, attenuation
+
+// Device-side batch dimensions written by the collator: {G, N, E, 0}.
+struct DevDims {
+  const int *p;  // nullptr: use the host-side sizes
+  __device__ __forceinline__ int graphs(int h) const { return p ? p[0] : h; }
+  __device__ __forceinline__ int nodes(int h) const { return p ? p[1] : h; }
+  __device__ __forceinline__ int edges(int h) const { return p ? p[2] : h; }
+};
+
+inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace gcnn

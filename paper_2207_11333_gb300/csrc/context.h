@@ -1,0 +1,67 @@
+// Training context: parameters, optimiser state, batch and activation arena.
+#pragma once
+
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "store.h"
+
+struct gcnn_ctx {
+  gcnn_config cfg{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
+  int device = 0;
+  int H = 0, L = 0, T = 0, Hh = 0;
+  int64_t P = 0;       // parameter count
+  int64_t layer_size = 0;
+  int Gc = 0, Nc = 0, Ec = 0;  // capacities
+
+  char *dmem = nullptr;  // one device allocation for everything below
+  size_t dbytes = 0;
+
+  float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+  int *opt_state = nullptr;  // [0] step, [1..2] bias-correction factors (float bits)
+  float *lr_dev = nullptr;
+  float *scal_tab = nullptr;  // 2 * (kMaxGraphEdges + 1)
+  unsigned *err = nullptr;
+
+  gcnn::BatchBuf bb{};
+  int64_t *ids_dev = nullptr;
+  char *stage_dev = nullptr;
+  size_t stage_bytes = 0;
+  char *stage_host[2] = {nullptr, nullptr};
+  cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+  bool stage_used[2] = {false, false};
+  int stage_i = 0;
+
+  int64_t *order_dev = nullptr;  // gcnn_set_order
+  std::vector<int64_t> order_host;
+  const gcnn_store *order_store = nullptr;
+
+  // activations
+  float *xs = nullptr;   // (L+1) x Nc x H
+  float *PQ = nullptr;   // L x Nc x 2H
+  float *agg = nullptr;  // (recompute ? 1 : L) x Nc x 5H
+  float *pooled = nullptr, *z1 = nullptr, *pred = nullptr, *dpred = nullptr, *dz1 = nullptr;
+  float *dg = nullptr;
+  float *dH = nullptr, *dX = nullptr, *dagg = nullptr, *dPQ = nullptr, *dm = nullptr;
+  float *emb_partial = nullptr;
+  int emb_chunks = 0;
+  gcnn::GemmWorkspace ws{};
+
+  // host-side state
+  bool have_fwd = false;
+  int fwd_G = 0, fwd_N = 0, fwd_E = 0;
+  float lr_host = -1.f;
+  float *lr_pinned = nullptr;
+  std::map<std::tuple<int, int, int, const double *>, cudaGraphExec_t> graphs;
+};
+
+namespace gcnn {
+int ctx_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n, gcnn_batch *out);
+int ctx_collate_range(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count, gcnn_batch *out);
+int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train);
+int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, double *loss_accum);
+int ctx_step(gcnn_ctx *c);
+}  // namespace gcnn

@@ -1,0 +1,115 @@
+// Launchers of the library's CUDA kernels (one group per source file).
+#pragma once
+
+#include "common.cuh"
+
+namespace gcnn {
+
+// ---------------------------------------------------------------- collate.cu
+// Read view of a packed store (global arrays), host- or device-resident.
+struct StoreView {
+  const int64_t *node_ptr;  // [G+1]
+  const int64_t *edge_ptr;  // [G+1]
+  const uint8_t *types;     // [N]
+  const uint8_t *edges;     // [2E] local (src, dst)
+  const float *y;           // [G]
+};
+
+// Writable batch arrays in the context arena.
+struct BatchBuf {
+  int *node_off, *edge_off, *graph_id, *row_ptr, *col, *rev, *deg;
+  float *amp, *att, *y;
+  uint8_t *types;
+  int *dims;  // {G, N, E, 0}
+};
+
+// Collate graphs ids[0..G) (ids == nullptr: graphs 0..G-1) of `st`.
+// scal_tab[2*d], scal_tab[2*d+1] = amplification / attenuation of degree d
+// (d = 0..kMaxGraphEdges).
+int launch_collate(int G, const int64_t *ids, StoreView st, BatchBuf b, const float *scal_tab,
+                   int cap_nodes, int cap_edges, unsigned *err, cudaStream_t s);
+
+// ---------------------------------------------------------------- aggregate.cu
+// agg[i] = [sum, mean, min, max, std](P_i + Q_j, j in N(i)); PQ is N x 2H.
+int launch_aggregate_fwd(int n_nodes, int H, DevDims dims, const int *row_ptr, const int *col,
+                         const float *PQ, float *agg, float eps, unsigned *err, cudaStream_t s);
+// dPQ from dagg; scratch is E x H (per-edge message gradients).
+int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const int *row_ptr,
+                         const int *col, const int *rev, const float *PQ, const float *agg,
+                         const float *dagg, float *dPQ, float *scratch, float eps, unsigned *err,
+                         cudaStream_t s);
+
+// ---------------------------------------------------------------- small.cu
+int launch_embed(int n_nodes, int H, DevDims dims, const uint8_t *types, const float *emb,
+                 int n_types, float *x0, cudaStream_t s);
+// dEmb[t] = sum of dx0 over nodes of type t (deterministic two-stage sum).
+int launch_embed_bwd(int n_nodes, int H, DevDims dims, const uint8_t *types, const float *dx0,
+                     int n_types, float *partial, int max_chunks, float *demb, cudaStream_t s);
+int launch_pool_fwd(int G, int H, DevDims dims, const int *node_off, const float *x, float *pooled,
+                    cudaStream_t s);
+int launch_pool_bwd(int G, int n_nodes, int H, DevDims dims, const int *node_off,
+                    const int *graph_id, const float *dpooled, float *dx, cudaStream_t s);
+// Head forward: z1 = g W1 + b1, pred = ReLU(z1) . w2 + b2.
+int launch_head_fwd(int G, int H, int Hh, DevDims dims, const float *g, const float *w1,
+                    const float *b1, const float *w2, const float *b2, float *z1, float *pred,
+                    cudaStream_t s);
+// Head backward with the MSE loss (dpred_in == nullptr) or a given dL/dpred.
+// Writes grads of w1, b1, w2, b2 (contiguous, layout order) and dg.
+int launch_head_bwd(int G, int H, int Hh, DevDims dims, const float *g, const float *w1,
+                    const float *w2, const float *z1, const float *pred, const float *y,
+                    const float *dpred_in, float *dpred, float *dz1, float *grad_head, float *dg,
+                    double *loss_accum, cudaStream_t s);
+// AdamW over n floats; step counter and lr live in device memory.
+int launch_adam(int64_t n, float *param, const float *grad, float *m, float *v, int *step,
+                const float *lr, float beta1, float beta2, float eps, float wd, cudaStream_t s);
+
+// ---------------------------------------------------------------- gemm_simt.cu
+// C = op(A) . op(B) in FP32 on CUDA cores (FFMA), with operands assembled on
+// the fly from up to kMaxSeg segments along the feature dimension (each with
+// an optional per-node scale and an optional ReLU mask), optional bias and
+// ReLU in the epilogue, and split-K with a deterministic reduction.
+constexpr int kMaxSeg = 5;
+
+struct Seg {
+  int begin;              // first feature index of the segment
+  const float *ptr;       // nullptr: the constant 1
+  int ld;                 // leading dimension of ptr (and of mask)
+  const float *rowscale;  // per-node factor or nullptr
+  const float *mask;      // element kept iff mask > 0, or nullptr
+};
+
+struct Operand {
+  Seg seg[kMaxSeg];
+  int nseg;
+};
+
+// Which GEMM dimension runs over the batch's nodes (read from DevDims).
+enum NodeDim { kNodeNone = 0, kNodeM = 1, kNodeK = 2 };
+
+struct GemmDesc {
+  int M, N, K;          // K: capacity when node_dim == kNodeK
+  NodeDim node_dim;
+  // A is M x K: a_kcontig -> A(m,k) = seg.ptr[m*ld + k - begin] (segments along K)
+  //             else       -> A(m,k) = seg.ptr[k*ld + m - begin] (segments along M)
+  bool a_kcontig;
+  // B is K x N: b_ncontig -> B(k,n) = seg.ptr[(k - begin)*ld + n] (segments along K)
+  //             else       -> B(k,n) = seg.ptr[n*ld + k - begin] (segments along K)
+  bool b_ncontig;
+  Operand A, B;
+  float *C;
+  int ldc;
+  const float *bias;  // bias[n] for n < bias_n
+  int bias_n;
+  bool relu;
+  int last_row_cols;  // > 0: only the first last_row_cols columns of row M-1 are stored
+};
+
+struct GemmWorkspace {
+  float *partial;   // split-K partial sums
+  size_t floats;    // capacity
+};
+
+int run_gemm_simt(const GemmDesc &d, DevDims dims, const GemmWorkspace &ws, cudaStream_t s);
+size_t gemm_simt_workspace_floats(int M, int N, int K);
+
+}  // namespace gcnn

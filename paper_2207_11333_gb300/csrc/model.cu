@@ -1,0 +1,194 @@
+// The training step: forward (Sec. 3.2, Fig. 3: GC layers -> global mean
+// pooling -> FC layers -> MSE), the hand-written backward and the AdamW step,
+// as an ordered sequence of kernel launches on the context's stream.  Every
+// launch reads the batch's true sizes from the device ({G, N, E} written by
+// the collator), so one sequence captured in a CUDA graph serves every batch
+// whose sizes fit its grid.
+#include "context.h"
+
+namespace gcnn {
+namespace {
+
+struct LayerW {
+  float *msg_w, *msg_b, *upd_w, *upd_b;
+};
+
+LayerW layer_ptrs(float *base, const gcnn_ctx *c, int l) {
+  float *b = base + (int64_t)c->T * c->H + (int64_t)l * c->layer_size;
+  const int64_t H = c->H;
+  return LayerW{b, b + 2 * H * H, b + 2 * H * H + H, b + 2 * H * H + H + 16 * H * H};
+}
+
+float *head_ptr(float *base, const gcnn_ctx *c) {
+  return base + (int64_t)c->T * c->H + (int64_t)c->L * c->layer_size;
+}
+
+Seg seg(int begin, const float *ptr, int ld, const float *rowscale = nullptr,
+        const float *mask = nullptr) {
+  return Seg{begin, ptr, ld, rowscale, mask};
+}
+
+GemmDesc blank() {
+  GemmDesc d{};
+  d.last_row_cols = 0;
+  d.bias = nullptr;
+  d.relu = false;
+  return d;
+}
+
+float *xs_at(const gcnn_ctx *c, int l) { return c->xs + (size_t)l * c->Nc * c->H; }
+float *pq_at(const gcnn_ctx *c, int l) { return c->PQ + (size_t)l * c->Nc * 2 * c->H; }
+float *agg_at(const gcnn_ctx *c, int l) {
+  return c->agg + (c->cfg.recompute ? 0 : (size_t)l * c->Nc * kAgg * c->H);
+}
+
+int gemm(gcnn_ctx *c, const GemmDesc &d) {
+  return run_gemm_simt(d, DevDims{c->bb.dims}, c->ws, c->stream);
+}
+
+// PQ = x [A | B] + [b_M | 0]    (message layer, both halves at once)
+int gemm_message(gcnn_ctx *c, int Ngrid, int l) {
+  const int H = c->H;
+  LayerW w = layer_ptrs(c->params, c, l);
+  GemmDesc d = blank();
+  d.M = Ngrid; d.N = 2 * H; d.K = H; d.node_dim = kNodeM;
+  d.a_kcontig = true; d.b_ncontig = true;
+  d.A.nseg = 1; d.A.seg[0] = seg(0, xs_at(c, l), H);
+  d.B.nseg = 1; d.B.seg[0] = seg(0, w.msg_w, 2 * H);
+  d.C = pq_at(c, l); d.ldc = 2 * H;
+  d.bias = w.msg_b; d.bias_n = H;
+  return gemm(c, d);
+}
+
+// x' = ReLU([x ; agg ; amp*agg ; att*agg] W_U + b_U)
+int gemm_update(gcnn_ctx *c, int Ngrid, int l) {
+  const int H = c->H;
+  LayerW w = layer_ptrs(c->params, c, l);
+  const float *agg = agg_at(c, l);
+  GemmDesc d = blank();
+  d.M = Ngrid; d.N = H; d.K = 16 * H; d.node_dim = kNodeM;
+  d.a_kcontig = true; d.b_ncontig = true;
+  d.A.nseg = 4;
+  d.A.seg[0] = seg(0, xs_at(c, l), H);
+  d.A.seg[1] = seg(H, agg, kAgg * H);
+  d.A.seg[2] = seg(6 * H, agg, kAgg * H, c->bb.amp);
+  d.A.seg[3] = seg(11 * H, agg, kAgg * H, c->bb.att);
+  d.B.nseg = 1; d.B.seg[0] = seg(0, w.upd_w, H);
+  d.C = xs_at(c, l + 1); d.ldc = H;
+  d.bias = w.upd_b; d.bias_n = H; d.relu = true;
+  return gemm(c, d);
+}
+
+}  // namespace
+
+int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train) {
+  (void)Egrid;
+  const int H = c->H;
+  DevDims dims{c->bb.dims};
+  GCNN_TRY(launch_embed(Ngrid, H, dims, c->bb.types, c->params, c->T, xs_at(c, 0), c->stream));
+  for (int l = 0; l < c->L; ++l) {
+    GCNN_TRY(gemm_message(c, Ngrid, l));
+    GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq_at(c, l), agg_at(c, l),
+                                  (float)c->cfg.std_eps, c->err, c->stream));
+    GCNN_TRY(gemm_update(c, Ngrid, l));
+  }
+  GCNN_TRY(launch_pool_fwd(G, H, dims, c->bb.node_off, xs_at(c, c->L), c->pooled, c->stream));
+  float *hp = head_ptr(c->params, c);
+  const int64_t HHh = (int64_t)H * c->Hh;
+  GCNN_TRY(launch_head_fwd(G, H, c->Hh, dims, c->pooled, hp, hp + HHh, hp + HHh + c->Hh,
+                           hp + HHh + 2 * c->Hh, c->z1, c->pred, c->stream));
+  (void)train;
+  return GCNN_OK;
+}
+
+int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, double *loss_accum) {
+  const int H = c->H;
+  DevDims dims{c->bb.dims};
+  float *hp = head_ptr(c->params, c);
+  float *ghp = head_ptr(c->grads, c);
+  const int64_t HHh = (int64_t)H * c->Hh;
+  GCNN_TRY(launch_head_bwd(G, H, c->Hh, dims, c->pooled, hp, hp + HHh + c->Hh, c->z1, c->pred,
+                           c->bb.y, dpred, c->dpred, c->dz1, ghp, c->dg, loss_accum, c->stream));
+  GCNN_TRY(launch_pool_bwd(G, Ngrid, H, dims, c->bb.node_off, c->bb.graph_id, c->dg, c->dH, c->stream));
+  for (int l = c->L - 1; l >= 0; --l) {
+    LayerW w = layer_ptrs(c->params, c, l);
+    LayerW gw = layer_ptrs(c->grads, c, l);
+    const float *x = xs_at(c, l), *h = xs_at(c, l + 1), *pq = pq_at(c, l);
+    float *agg = agg_at(c, l);
+    if (c->cfg.recompute)
+      GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq, agg,
+                                    (float)c->cfg.std_eps, c->err, c->stream));
+    // dW_U (16H x H) and db_U: [x ; agg ; amp agg ; att agg ; 1]^T (dh * [h > 0])
+    {
+      GemmDesc d = blank();
+      d.M = 16 * H + 1; d.N = H; d.K = Ngrid; d.node_dim = kNodeK;
+      d.a_kcontig = false; d.b_ncontig = true;
+      d.A.nseg = 5;
+      d.A.seg[0] = seg(0, x, H);
+      d.A.seg[1] = seg(H, agg, kAgg * H);
+      d.A.seg[2] = seg(6 * H, agg, kAgg * H, c->bb.amp);
+      d.A.seg[3] = seg(11 * H, agg, kAgg * H, c->bb.att);
+      d.A.seg[4] = seg(16 * H, nullptr, 0);
+      d.B.nseg = 1; d.B.seg[0] = seg(0, c->dH, H, nullptr, h);
+      d.C = gw.upd_w; d.ldc = H;
+      GCNN_TRY(gemm(c, d));
+    }
+    // dagg = sum_s s_i (dh * [h > 0]) W_s^T, W_s = rows H + 5Hs .. of W_U
+    {
+      GemmDesc d = blank();
+      d.M = Ngrid; d.N = kAgg * H; d.K = 3 * H; d.node_dim = kNodeM;
+      d.a_kcontig = true; d.b_ncontig = false;
+      d.A.nseg = 3;
+      d.A.seg[0] = seg(0, c->dH, H, nullptr, h);
+      d.A.seg[1] = seg(H, c->dH, H, c->bb.amp, h);
+      d.A.seg[2] = seg(2 * H, c->dH, H, c->bb.att, h);
+      d.B.nseg = 3;
+      d.B.seg[0] = seg(0, w.upd_w + (size_t)H * H, H);
+      d.B.seg[1] = seg(H, w.upd_w + (size_t)6 * H * H, H);
+      d.B.seg[2] = seg(2 * H, w.upd_w + (size_t)11 * H * H, H);
+      d.C = c->dagg; d.ldc = kAgg * H;
+      GCNN_TRY(gemm(c, d));
+    }
+    GCNN_TRY(launch_aggregate_bwd(Ngrid, Egrid, H, dims, c->bb.row_ptr, c->bb.col, c->bb.rev, pq, agg,
+                                  c->dagg, c->dPQ, c->dm, (float)c->cfg.std_eps, c->err, c->stream));
+    // dW_M (H x 2H) and db_M: [x ; 1]^T dPQ  (bias row keeps the first H columns)
+    {
+      GemmDesc d = blank();
+      d.M = H + 1; d.N = 2 * H; d.K = Ngrid; d.node_dim = kNodeK;
+      d.a_kcontig = false; d.b_ncontig = true;
+      d.A.nseg = 2;
+      d.A.seg[0] = seg(0, x, H);
+      d.A.seg[1] = seg(H, nullptr, 0);
+      d.B.nseg = 1; d.B.seg[0] = seg(0, c->dPQ, 2 * H);
+      d.C = gw.msg_w; d.ldc = 2 * H; d.last_row_cols = H;
+      GCNN_TRY(gemm(c, d));
+    }
+    // dx = (dh * [h > 0]) W_x^T + [dP | dQ] [A | B]^T
+    {
+      GemmDesc d = blank();
+      d.M = Ngrid; d.N = H; d.K = 3 * H; d.node_dim = kNodeM;
+      d.a_kcontig = true; d.b_ncontig = false;
+      d.A.nseg = 2;
+      d.A.seg[0] = seg(0, c->dH, H, nullptr, h);
+      d.A.seg[1] = seg(H, c->dPQ, 2 * H);
+      d.B.nseg = 2;
+      d.B.seg[0] = seg(0, w.upd_w, H);
+      d.B.seg[1] = seg(H, w.msg_w, 2 * H);
+      d.C = c->dX; d.ldc = H;
+      GCNN_TRY(gemm(c, d));
+    }
+    std::swap(c->dH, c->dX);
+  }
+  // embedding: dEmb[t] = sum of dx0 over nodes of type t
+  GCNN_TRY(launch_embed_bwd(Ngrid, H, dims, c->bb.types, c->dH, c->T, c->emb_partial, c->emb_chunks,
+                            c->grads, c->stream));
+  return GCNN_OK;
+}
+
+int ctx_step(gcnn_ctx *c) {
+  return launch_adam(c->P, c->params, c->grads, c->adam_m, c->adam_v, c->opt_state, c->lr_dev,
+                     (float)c->cfg.beta1, (float)c->cfg.beta2, (float)c->cfg.adam_eps,
+                     (float)c->cfg.weight_decay, c->stream);
+}
+
+}  // namespace gcnn

@@ -1,0 +1,31 @@
+// Packed graph store (host side).
+#pragma once
+
+#include "kernels.cuh"
+
+struct gcnn_store {
+  void *host = nullptr;  // whole file (pinned when possible)
+  bool pinned = false;
+  size_t bytes = 0;
+  int64_t G = 0, N = 0, E = 0;
+  uint32_t n_types = 0;
+  int64_t off_node_ptr = 0, off_edge_ptr = 0, off_types = 0, off_edges = 0, off_y = 0;
+  const int64_t *node_ptr = nullptr;
+  const int64_t *edge_ptr = nullptr;
+  const uint8_t *types = nullptr;
+  const uint8_t *edges = nullptr;
+  float *y = nullptr;
+  void *dev = nullptr;  // device mirror of the whole file, or nullptr
+  int dev_id = -1;
+};
+
+namespace gcnn {
+const char *last_error();
+int store_open(const char *path, gcnn_store **out);
+int store_close(gcnn_store *st);
+int store_to_device(gcnn_store *st);
+StoreView store_device_view(const gcnn_store *st);
+int store_batch_size(const gcnn_store *st, const int64_t *ids, int64_t n, int64_t *nn, int64_t *ne);
+int store_delta(const gcnn_store *st, const int64_t *ids, int64_t n, double *delta);
+int store_set_targets(gcnn_store *st, const float *y, int64_t n);
+}  // namespace gcnn

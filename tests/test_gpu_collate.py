@@ -1,0 +1,65 @@
+"""Device collation against the oracle's collation: bit-exact integers and scalers."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import context, write_both
+
+pytestmark = pytest.mark.gpu
+
+
+def _compare(gb, ob):
+    e = gb.export()
+    assert np.array_equal(e["node_off"], ob.node_off.astype(np.int32))
+    for k in ("graph_id", "row_ptr", "col", "rev", "deg", "types"):
+        assert np.array_equal(e[k], getattr(ob, k)), k
+    for k in ("amp", "att", "y"):
+        assert np.array_equal(e[k].view(np.uint32), getattr(ob, k).view(np.uint32)), k
+
+
+@pytest.mark.parametrize("resident", [False, True])
+def test_collate_bit_exact(resident, tmp_path):
+    import paper_2207_11333_gb300 as g
+    gs = synth.molecules_uniform(1, 300, 1, 80)
+    gs.y = synth.uniform_targets(9, 0, 300, 1, 10)
+    path, ost = write_both(gs, str(tmp_path))
+    st = g.Store(path)
+    if resident:
+        st.to_device()
+    delta = st.delta()
+    ctx = context(32, 1, 256, 256 * 80, 256 * 200, delta)
+    rng = np.random.default_rng(3)
+    cases = [rng.integers(0, 300, 200), np.arange(300)[:256][::-1], np.array([7]), rng.integers(0, 300, 33),
+             np.array([0, 0, 0, 5, 5])]
+    for ids in cases:
+        gb = ctx.collate(st, ids)
+        ob = oracle.collate(ost, ids, delta)
+        assert (gb.n_graphs, gb.n_nodes, gb.n_edges) == (ob.G, ob.N, ob.E)
+        _compare(gb, ob)
+    ctx.check()
+
+
+def test_collate_edge_cases(tmp_path):
+    import paper_2207_11333_gb300 as g
+    from helpers import custom_set
+    big = synth.make_graphs(4, np.array([255, 254, 3], np.int32))        # largest graphs the store allows
+    tiny = custom_set([([2], []), ([0, 1], [(0, 1)])])                  # single atom (no edges), one bond
+    gs = synth.GraphSet(np.concatenate([big.node_ptr, big.node_ptr[-1] + tiny.node_ptr[1:]]),
+                        np.concatenate([big.edge_ptr, big.edge_ptr[-1] + tiny.edge_ptr[1:]]),
+                        np.concatenate([big.types, tiny.types]), np.concatenate([big.edges, tiny.edges]),
+                        np.arange(5, dtype=np.float32))
+    path, ost = write_both(gs, str(tmp_path))
+    st = g.Store(path)
+    delta = st.delta()
+    ctx = context(16, 1, 8, 1024, 4096, delta)
+    for ids in ([0, 1, 2, 3, 4], [3], [4, 3], [1]):
+        gb = ctx.collate(st, ids)
+        _compare(gb, oracle.collate(ost, ids, delta))
+    gb = ctx.collate(st, np.zeros(0, np.int64))                        # empty batch
+    assert (gb.n_graphs, gb.n_nodes, gb.n_edges) == (0, 0, 0)
+    with pytest.raises(g.GcnnError, match="capacity"):
+        ctx.collate(st, [0, 1, 2, 0, 1, 0])                               # 1276 > 1024 nodes
+    with pytest.raises(g.GcnnError, match="out of range"):
+        ctx.collate(st, [9])
+    ctx.check()

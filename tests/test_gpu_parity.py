@@ -1,0 +1,134 @@
+"""The CUDA training step against the FP64 oracle on the 64-graph parity workload
+(H = 32, L = 2) and ragged variants: forward within 1e-5, gradients within 1e-4
+(normwise relative, FP32 path), Adam step, graph-captured step == eager step."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import workloads
+from gpu_common import context, oracle_step, write_both
+from helpers import rel_max, rel_norm
+
+pytestmark = pytest.mark.gpu
+
+FWD_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+def _setup(tmp_path, G=64, lo=5, hi=30, H=32, L=2, recompute=False):
+    import paper_2207_11333_gb300 as g
+    d, gs, delta, student = workloads.small_parity(G=G, lo=lo, hi=hi, H=H, L=L)
+    path, ost = write_both(gs, str(tmp_path))
+    st = g.Store(path)
+    ctx = context(H, L, G, int(gs.n_nodes), int(gs.n_edges), delta, recompute=recompute)
+    ctx.set_params(student)
+    ids = np.arange(G)
+    b = ctx.collate(st, ids)
+    ob = oracle.collate(ost, ids, delta)
+    return d, ctx, st, b, ob, student
+
+
+@pytest.mark.parametrize("recompute", [False, True])
+def test_forward_backward_step_parity(tmp_path, recompute):
+    d, ctx, st, b, ob, student = _setup(tmp_path, recompute=recompute)
+    pred = torch.empty(b.n_graphs, device="cuda")
+    ctx.forward(b, pred, train=True)
+    acts = ctx.activations(b)
+    loss_acc = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ctx.backward(b, None, loss_acc)
+    grads = ctx.get_grads()
+    ctx.step(1e-3)
+    new_params = ctx.get_params()
+    ctx.check()
+
+    opred, oxs, _, _ = oracle.forward(d, student.astype(np.float64), ob, want_layers=True)
+    loss, ograd, _, oth = oracle_step(d, student, ob)
+    assert rel_norm(pred.cpu().numpy(), opred) < FWD_TOL
+    assert rel_max(pred.cpu().numpy(), opred) < 10 * FWD_TOL
+    for l in range(d.L + 1):
+        assert rel_norm(acts[l], oxs[l]) < FWD_TOL, l
+    la = loss_acc.cpu().numpy()
+    assert abs(la[0] / la[2] - loss) < FWD_TOL * loss and la[2] == b.n_graphs
+    assert abs(la[1] / la[2] - np.mean(np.abs(opred - ob.y))) < 1e-5 * la[1] / la[2]
+    gv, ov = oracle.split_params(d, grads), oracle.split_params(d, ograd)
+    for k in ov:
+        assert rel_norm(gv[k], ov[k]) < GRAD_TOL, (k, rel_norm(gv[k], ov[k]))
+    assert rel_norm(new_params - student, oth - student) < 1e-3
+    assert rel_norm(new_params, oth) < FWD_TOL
+
+
+@pytest.mark.parametrize("G,lo,hi,H,L", [(1, 5, 5, 8, 1), (7, 3, 51, 16, 3), (33, 1, 80, 24, 2)])
+def test_ragged_shapes(tmp_path, G, lo, hi, H, L):
+    d, ctx, st, b, ob, student = _setup(tmp_path, G=G, lo=lo, hi=hi, H=H, L=L)
+    pred = torch.empty(b.n_graphs, device="cuda")
+    ctx.forward(b, pred, train=True)
+    ctx.backward(b)
+    grads = ctx.get_grads()
+    ctx.check()
+    loss, ograd, opred, _ = oracle_step(d, student, ob)
+    assert rel_norm(pred.cpu().numpy(), opred) < FWD_TOL
+    gv, ov = oracle.split_params(d, grads), oracle.split_params(d, ograd)
+    for k in ov:
+        if np.linalg.norm(ov[k]) > 0:
+            assert rel_norm(gv[k], ov[k]) < GRAD_TOL, (k, rel_norm(gv[k], ov[k]))
+
+
+def test_captured_train_step_matches_eager(tmp_path):
+    d, ctx, st, b, ob, student = _setup(tmp_path)
+    ctx.forward(b, train=True)
+    ctx.backward(b)
+    ctx.step(1e-3)
+    eager = ctx.get_params()
+    ctx.set_params(student)
+    ctx.reset_optimizer()
+    b = ctx.collate(st, np.arange(64))
+    acc = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ctx.train_step(b, 1e-3, acc)
+    captured = ctx.get_params()
+    assert np.array_equal(eager, captured)
+    # replay on another batch of the same bucket, then redo that step eagerly
+    ckpt = str(tmp_path / "after1.bin")
+    ctx.save(ckpt)
+    ids = np.arange(64)[::-1].copy()
+    ctx.train_step(ctx.collate(st, ids), 1e-3, acc)
+    replay = ctx.get_params()
+    ctx.load(ckpt)
+    b = ctx.collate(st, ids)
+    ctx.forward(b, train=True)
+    ctx.backward(b)
+    ctx.step(1e-3)
+    assert np.array_equal(ctx.get_params(), replay)
+    ctx.check()
+
+
+def test_checkpoint_resume_bitwise(tmp_path):
+    d, ctx, st, b, ob, student = _setup(tmp_path)
+    rng = np.random.default_rng(0)
+    orders = [rng.permutation(64)[:48] for _ in range(4)]
+    for o in orders[:2]:
+        ctx.train_step(ctx.collate(st, o), 1e-3)
+    ckpt = str(tmp_path / "c.bin")
+    ctx.save(ckpt)
+    for o in orders[2:]:
+        ctx.train_step(ctx.collate(st, o), 1e-3)
+    straight = ctx.get_params()
+    ctx.set_params(student)
+    ctx.reset_optimizer()
+    ctx.load(ckpt)
+    for o in orders[2:]:
+        ctx.train_step(ctx.collate(st, o), 1e-3)
+    assert np.array_equal(ctx.get_params(), straight)
+
+
+def test_errors_are_reported(tmp_path):
+    import paper_2207_11333_gb300 as g
+    d, ctx, st, b, ob, student = _setup(tmp_path)
+    b2 = ctx.collate(st, np.arange(10))
+    with pytest.raises(g.GcnnError, match="ESTATE"):
+        ctx.backward(b2)
+    with pytest.raises(g.GcnnError, match="EINVAL"):
+        g.Context(g.make_config(30, 2, 4, 100, 100, delta=1.0))       # hidden not a multiple of 8
+    with pytest.raises(g.GcnnError, match="EINVAL"):
+        ctx.set_params(np.zeros(5, np.float32))

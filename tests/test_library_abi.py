@@ -1,0 +1,89 @@
+"""The C-ABI library loads, exports every declared entry point, and its host-side
+store reader agrees with the oracle (no GPU needed: no compute calls)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import custom_set
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "gcnn.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gcnn_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported():
+    import paper_2207_11333_gb300 as g
+    names = _declared()
+    assert len(names) >= 30
+    missing = [n for n in names if not hasattr(g.lib, n)]
+    assert not missing, missing
+
+
+def test_version_and_error_text():
+    import paper_2207_11333_gb300 as g
+    assert g.lib.gcnn_version() >= 100
+    assert isinstance(g.lib.gcnn_last_error(), bytes)
+
+
+def test_store_reader_matches_oracle(tmp_path):
+    import paper_2207_11333_gb300 as g
+    gs = synth.molecules_uniform(1, 80, 3, 60)
+    gs.y = synth.uniform_targets(5, 0, 80, 1, 10)
+    path = str(tmp_path / "s.gcnn")
+    synth.write_store(path, gs)
+    st = g.Store(path)
+    assert (st.n_graphs, st.n_nodes, st.n_edges) == (gs.n_graphs, gs.n_nodes, gs.n_edges)
+    ost = oracle.read_store(path)
+    assert st.delta() == oracle.delta_of(ost)            # same summation order: bitwise
+    ids = np.array([5, 3, 3, 79, 0])
+    assert st.batch_size(ids) == (int(np.sum(np.diff(gs.node_ptr)[ids])), int(np.sum(np.diff(gs.edge_ptr)[ids])))
+    assert abs(st.delta(ids) - oracle.delta_of(ost, ids)) <= 1e-15 * st.delta(ids)
+
+
+def _bad_store(tmp_path, gs, name):
+    path = str(tmp_path / name)
+    synth.write_store(path, gs)
+    return path
+
+
+def test_store_rejects_malformed_files(tmp_path):
+    import paper_2207_11333_gb300 as g
+    p = str(tmp_path / "junk")
+    open(p, "wb").write(b"not a store at all" * 10)
+    with pytest.raises(g.GcnnError, match="EFORMAT"):
+        g.Store(p)
+    # one direction of a bond missing
+    gs = custom_set([([0, 1, 2], [(0, 1), (1, 2)])])
+    gs.edges = gs.edges[:-1].copy()
+    gs.edge_ptr = np.array([0, 3], np.int64)
+    with pytest.raises(g.GcnnError, match="both directions"):
+        g.Store(_bad_store(tmp_path, gs, "asym"))
+    # atom type out of range
+    gs = custom_set([([0, 9], [(0, 1)])])
+    with pytest.raises(g.GcnnError, match="atom type"):
+        g.Store(_bad_store(tmp_path, gs, "type"))
+    # truncated file
+    gs = synth.molecules_uniform(2, 4, 5, 9)
+    path = _bad_store(tmp_path, gs, "trunc")
+    data = open(path, "rb").read()
+    open(path, "wb").write(data[:-70])
+    with pytest.raises(g.GcnnError, match="EFORMAT"):
+        g.Store(path)
+
+
+def test_store_rejects_oversized_graph(tmp_path):
+    import paper_2207_11333_gb300 as g
+    gs = synth.make_graphs(3, np.array([10], np.int32))
+    # claim 256 nodes for one graph
+    gs.node_ptr = np.array([0, 256], np.int64)
+    gs.types = np.zeros(256, np.uint8)
+    with pytest.raises(g.GcnnError, match="nodes"):
+        g.Store(_bad_store(tmp_path, gs, "big"))
