@@ -208,6 +208,32 @@ int gcnn_train_step(gcnn_ctx *ctx, const gcnn_batch *b, float lr, double *loss_a
 /* Copy x^l (l = 0..L, N x H floats) of the last forward to host.  Sync. */
 int gcnn_get_activation(gcnn_ctx *ctx, int32_t layer, float *dst, int64_t n);
 
+/* ------------------------------------------------------------------ timing
+ * Per-phase device time of the step (the paper's load / forward / backward /
+ * optimizer breakdown, Fig. 5, at kernel granularity).  While enabled, the
+ * library records a CUDA event pair on the context's stream around every
+ * kernel it launches outside graph capture, and gcnn_train_step runs eagerly.
+ */
+enum {
+  GCNN_PHASE_COLLATE = 0,   /* device collation                         */
+  GCNN_PHASE_EMBED = 1,     /* embedding lookup                         */
+  GCNN_PHASE_GEMM = 2,      /* dense node-wise GEMMs (fwd and bwd)      */
+  GCNN_PHASE_AGG_FWD = 3,   /* gather + aggregate (fwd, and recompute)  */
+  GCNN_PHASE_AGG_BWD = 4,   /* aggregate backward                       */
+  GCNN_PHASE_HEAD = 5,      /* pooling, head, loss (fwd and bwd)        */
+  GCNN_PHASE_EMBED_BWD = 6, /* embedding gradient                       */
+  GCNN_PHASE_ADAM = 7,      /* optimizer                                */
+  GCNN_NPHASE = 8
+};
+int gcnn_profile_enable(gcnn_ctx *ctx, int enable);
+/* Synchronises the stream; returns per-phase milliseconds and numbers of
+ * timed launches since the last read (host arrays of GCNN_NPHASE), then
+ * resets the counters. */
+int gcnn_profile_read(gcnn_ctx *ctx, double *ms, int64_t *launches);
+/* Kernels in the CUDA graph of the most recent gcnn_train_step (0 if it ran
+ * eagerly); the collation of a batch adds 2 more. */
+int gcnn_step_kernel_count(gcnn_ctx *ctx, int32_t *n);
+
 /* ------------------------------------------------------------------ operators
  * Single steps of the path on caller-owned device buffers, for composing the
  * layer from PyTorch (torch.autograd.Function) and for unit tests.

@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libgcnn.so")
 
 PREC_FP32 = 0
 PREC_BF16 = 1
+PHASES = ["collate", "embed", "gemm", "agg_fwd", "agg_bwd", "head", "embed_bwd", "adam"]
+NPHASE = len(PHASES)
 
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EFORMAT", -5: "EDEVICE", -6: "ETIMEDOUT",
            -7: "EAGAIN", -8: "ESTATE"}
@@ -82,6 +84,9 @@ def _load() -> ctypes.CDLL:
         "gcnn_step": (i32, [vp, f32]),
         "gcnn_train_step": (i32, [vp, P(BatchStruct), f32, vp]),
         "gcnn_get_activation": (i32, [vp, i32, vp, i64]),
+        "gcnn_profile_enable": (i32, [vp, i32]),
+        "gcnn_profile_read": (i32, [vp, vp, vp]),
+        "gcnn_step_kernel_count": (i32, [vp, P(i32)]),
         "gcnn_op_aggregate_fwd": (i32, [i32, i32, vp, vp, vp, vp, f32, vp]),
         "gcnn_op_aggregate_bwd": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, f32, vp]),
         "gcnn_op_pool_fwd": (i32, [i32, i32, vp, vp, vp, vp]),
@@ -321,6 +326,20 @@ class Context:
 
     def train_step(self, batch: Batch, lr: float, loss_accum=None) -> None:
         _check(lib.gcnn_train_step(self._h, ctypes.byref(batch.s), lr, _dev_ptr(loss_accum)))
+
+    def profile(self, enable: bool) -> None:
+        _check(lib.gcnn_profile_enable(self._h, int(enable)))
+
+    def profile_read(self) -> dict:
+        ms = np.zeros(NPHASE, np.float64)
+        n = np.zeros(NPHASE, np.int64)
+        _check(lib.gcnn_profile_read(self._h, _np_ptr(ms), _np_ptr(n)))
+        return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(PHASES)}
+
+    def step_kernel_count(self) -> int:
+        k = ctypes.c_int32()
+        _check(lib.gcnn_step_kernel_count(self._h, ctypes.byref(k)))
+        return k.value
 
     def activation(self, layer: int) -> np.ndarray:
         n = self._last_nodes * self.cfg.hidden

@@ -66,7 +66,8 @@ size_t stage_bytes_of(int Gc, int Nc, int Ec) {
 
 void destroy_ctx(gcnn_ctx *c) {
   if (!c) return;
-  for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   for (int q = 0; q < 2; ++q) {
     if (c->stage_host[q]) cudaFreeHost(c->stage_host[q]);
     if (c->stage_ev[q]) cudaEventDestroy(c->stage_ev[q]);
@@ -437,6 +438,15 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
   GCNN_TRY(set_lr(c, lr));
   const int G = b->n_graphs;
   const int Ng = grid_nodes(c, b), Eg = grid_edges(c, b);
+  if (c->prof_on) {  // eager, so every launch can be timed
+    GCNN_TRY(ctx_forward(c, G, Ng, Eg, true));
+    GCNN_TRY(ctx_backward(c, G, Ng, Eg, nullptr, loss_accum));
+    GCNN_TRY(ctx_step(c));
+    c->last_step_kernels = 0;
+    c->have_fwd = true;
+    c->fwd_G = b->n_graphs; c->fwd_N = b->n_nodes; c->fwd_E = b->n_edges;
+    return GCNN_OK;
+  }
   auto key = std::make_tuple(G, Ng, Eg, (const double *)loss_accum);
   auto it = c->graphs.find(key);
   if (it == c->graphs.end()) {
@@ -446,9 +456,11 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
     GCNN_CUDA_TRY(cudaStreamSynchronize(c->stream));
     cudaStream_t user = c->stream;
     c->stream = c->cap_stream;
+    c->capturing = true;
     cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
       c->stream = user;
+      c->capturing = false;
       return set_error(GCNN_ECUDA, "begin capture: %s", cudaGetErrorString(e));
     }
     int rc = ctx_forward(c, G, Ng, Eg, true);
@@ -456,18 +468,30 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
     if (rc == GCNN_OK) rc = ctx_step(c);
     e = cudaStreamEndCapture(c->stream, &graph);
     c->stream = user;
+    c->capturing = false;
     if (rc != GCNN_OK) {
       if (graph) cudaGraphDestroy(graph);
       return rc;
     }
     if (e != cudaSuccess) return set_error(GCNN_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    size_t n_nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &n_nodes);
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    int kernels = 0;
+    if (n_nodes && cudaGraphGetNodes(graph, nodes.data(), &n_nodes) == cudaSuccess) {
+      for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+      }
+    }
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return set_error(GCNN_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
-    it = c->graphs.emplace(key, exec).first;
+    it = c->graphs.emplace(key, gcnn_ctx::Graph{exec, kernels}).first;
   }
-  GCNN_CUDA_TRY(cudaGraphLaunch(it->second, c->stream));
+  GCNN_CUDA_TRY(cudaGraphLaunch(it->second.exec, c->stream));
+  c->last_step_kernels = it->second.kernels;
   c->have_fwd = true;
   c->fwd_G = b->n_graphs; c->fwd_N = b->n_nodes; c->fwd_E = b->n_edges;
   return GCNN_OK;
@@ -479,6 +503,33 @@ int gcnn_get_activation(gcnn_ctx *c, int32_t layer, float *dst, int64_t n) {
   GCNN_CUDA_TRY(cudaMemcpyAsync(dst, c->xs + (size_t)layer * c->Nc * c->H, n * sizeof(float),
                                 cudaMemcpyDeviceToHost, c->stream));
   return sync(c);
+}
+
+// ---------------------------------------------------------------- timing
+int gcnn_profile_enable(gcnn_ctx *c, int enable) {
+  if (!c) return set_error(GCNN_EINVAL, "null context");
+  c->prof_on = enable != 0;
+  return GCNN_OK;
+}
+
+int gcnn_profile_read(gcnn_ctx *c, double *ms, int64_t *launches) {
+  if (!c || !ms || !launches) return set_error(GCNN_EINVAL, "null argument");
+  GCNN_TRY(sync(c));
+  for (int q = 0; q < GCNN_NPHASE; ++q) { ms[q] = 0.0; launches[q] = 0; }
+  for (size_t k = 0; k < c->prof_used; ++k) {
+    float t = 0.f;
+    GCNN_CUDA_TRY(cudaEventElapsedTime(&t, c->prof_ev[2 * k], c->prof_ev[2 * k + 1]));
+    ms[c->prof_cls[k]] += t;
+    launches[c->prof_cls[k]] += 1;
+  }
+  c->prof_used = 0;
+  return GCNN_OK;
+}
+
+int gcnn_step_kernel_count(gcnn_ctx *c, int32_t *n) {
+  if (!c || !n) return set_error(GCNN_EINVAL, "null argument");
+  *n = c->last_step_kernels;
+  return GCNN_OK;
 }
 
 // ---------------------------------------------------------------- operators

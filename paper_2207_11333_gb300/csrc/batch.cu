@@ -60,6 +60,7 @@ int ctx_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n
       GCNN_CUDA_TRY(cudaMemcpyAsync(c->ids_dev, h, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
     GCNN_CUDA_TRY(cudaEventRecord(c->stage_ev[q], c->stream));
     c->stage_used[q] = true;
+    PhaseScope ps(c, GCNN_PHASE_COLLATE);
     GCNN_TRY(launch_collate(n, c->ids_dev, store_device_view(st), c->bb, c->scal_tab, c->Nc, c->Ec, c->err,
                             c->stream));
   } else {
@@ -93,6 +94,7 @@ int ctx_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n
     StoreView v{reinterpret_cast<const int64_t *>(d + o_np), reinterpret_cast<const int64_t *>(d + o_ep),
                 reinterpret_cast<const uint8_t *>(d + o_t), reinterpret_cast<const uint8_t *>(d + o_e),
                 reinterpret_cast<const float *>(d + o_y)};
+    PhaseScope ps(c, GCNN_PHASE_COLLATE);
     GCNN_TRY(launch_collate(n, nullptr, v, c->bb, c->scal_tab, c->Nc, c->Ec, c->err, c->stream));
   }
   fill_batch(c, n, N, E, out);
@@ -109,6 +111,7 @@ int ctx_collate_range(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t 
   GCNN_TRY(check_caps(c, count, 0, 0));
   GCNN_TRY(store_batch_size(st, c->order_host.data() + first, count, &N, &E));
   GCNN_TRY(check_caps(c, count, N, E));
+  PhaseScope ps(c, GCNN_PHASE_COLLATE);
   GCNN_TRY(launch_collate(count, c->order_dev + first, store_device_view(st), c->bb, c->scal_tab, c->Nc, c->Ec,
                           c->err, c->stream));
   fill_batch(c, count, N, E, out);

@@ -55,10 +55,34 @@ struct gcnn_ctx {
   int fwd_G = 0, fwd_N = 0, fwd_E = 0;
   float lr_host = -1.f;
   float *lr_pinned = nullptr;
-  std::map<std::tuple<int, int, int, const double *>, cudaGraphExec_t> graphs;
+  struct Graph {
+    cudaGraphExec_t exec;
+    int kernels;
+  };
+  std::map<std::tuple<int, int, int, const double *>, Graph> graphs;
+  int last_step_kernels = 0;
+  bool capturing = false;
+
+  // per-phase event timing (gcnn_profile_enable)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;  // pairs: [2k] start, [2k+1] end
+  std::vector<int> prof_cls;
+  size_t prof_used = 0;
 };
 
 namespace gcnn {
+// Event pair around the kernels launched in its lifetime (no-op unless
+// profiling is on and the stream is not being captured).
+class PhaseScope {
+ public:
+  PhaseScope(gcnn_ctx *c, int phase);
+  ~PhaseScope();
+
+ private:
+  gcnn_ctx *c_;
+  long idx_;
+};
+
 int ctx_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n, gcnn_batch *out);
 int ctx_collate_range(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count, gcnn_batch *out);
 int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train);

@@ -43,6 +43,7 @@ float *agg_at(const gcnn_ctx *c, int l) {
 }
 
 int gemm(gcnn_ctx *c, const GemmDesc &d) {
+  PhaseScope ps(c, GCNN_PHASE_GEMM);
   return run_gemm_simt(d, DevDims{c->bb.dims}, c->ws, c->stream);
 }
 
@@ -81,17 +82,46 @@ int gemm_update(gcnn_ctx *c, int Ngrid, int l) {
 
 }  // namespace
 
+PhaseScope::PhaseScope(gcnn_ctx *c, int phase) : c_(c), idx_(-1) {
+  if (!c->prof_on || c->capturing) return;
+  if (c->prof_used * 2 + 2 > c->prof_ev.size()) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      if (a) cudaEventDestroy(a);
+      cudaGetLastError();
+      return;
+    }
+    c->prof_ev.push_back(a);
+    c->prof_ev.push_back(b);
+    c->prof_cls.push_back(0);
+  }
+  idx_ = (long)c->prof_used++;
+  c->prof_cls[idx_] = phase;
+  cudaEventRecord(c->prof_ev[2 * idx_], c->stream);
+}
+
+PhaseScope::~PhaseScope() {
+  if (idx_ >= 0) cudaEventRecord(c_->prof_ev[2 * idx_ + 1], c_->stream);
+}
+
 int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train) {
   (void)Egrid;
   const int H = c->H;
   DevDims dims{c->bb.dims};
-  GCNN_TRY(launch_embed(Ngrid, H, dims, c->bb.types, c->params, c->T, xs_at(c, 0), c->stream));
+  {
+    PhaseScope ps(c, GCNN_PHASE_EMBED);
+    GCNN_TRY(launch_embed(Ngrid, H, dims, c->bb.types, c->params, c->T, xs_at(c, 0), c->stream));
+  }
   for (int l = 0; l < c->L; ++l) {
     GCNN_TRY(gemm_message(c, Ngrid, l));
-    GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq_at(c, l), agg_at(c, l),
-                                  (float)c->cfg.std_eps, c->err, c->stream));
+    {
+      PhaseScope ps(c, GCNN_PHASE_AGG_FWD);
+      GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq_at(c, l), agg_at(c, l),
+                                    (float)c->cfg.std_eps, c->err, c->stream));
+    }
     GCNN_TRY(gemm_update(c, Ngrid, l));
   }
+  PhaseScope ps(c, GCNN_PHASE_HEAD);
   GCNN_TRY(launch_pool_fwd(G, H, dims, c->bb.node_off, xs_at(c, c->L), c->pooled, c->stream));
   float *hp = head_ptr(c->params, c);
   const int64_t HHh = (int64_t)H * c->Hh;
@@ -107,17 +137,22 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
   float *hp = head_ptr(c->params, c);
   float *ghp = head_ptr(c->grads, c);
   const int64_t HHh = (int64_t)H * c->Hh;
+  {
+  PhaseScope ps(c, GCNN_PHASE_HEAD);
   GCNN_TRY(launch_head_bwd(G, H, c->Hh, dims, c->pooled, hp, hp + HHh + c->Hh, c->z1, c->pred,
                            c->bb.y, dpred, c->dpred, c->dz1, ghp, c->dg, loss_accum, c->stream));
   GCNN_TRY(launch_pool_bwd(G, Ngrid, H, dims, c->bb.node_off, c->bb.graph_id, c->dg, c->dH, c->stream));
+  }
   for (int l = c->L - 1; l >= 0; --l) {
     LayerW w = layer_ptrs(c->params, c, l);
     LayerW gw = layer_ptrs(c->grads, c, l);
     const float *x = xs_at(c, l), *h = xs_at(c, l + 1), *pq = pq_at(c, l);
     float *agg = agg_at(c, l);
-    if (c->cfg.recompute)
+    if (c->cfg.recompute) {
+      PhaseScope ps(c, GCNN_PHASE_AGG_FWD);
       GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq, agg,
                                     (float)c->cfg.std_eps, c->err, c->stream));
+    }
     // dW_U (16H x H) and db_U: [x ; agg ; amp agg ; att agg ; 1]^T (dh * [h > 0])
     {
       GemmDesc d = blank();
@@ -149,8 +184,11 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
       d.C = c->dagg; d.ldc = kAgg * H;
       GCNN_TRY(gemm(c, d));
     }
-    GCNN_TRY(launch_aggregate_bwd(Ngrid, Egrid, H, dims, c->bb.row_ptr, c->bb.col, c->bb.rev, pq, agg,
-                                  c->dagg, c->dPQ, c->dm, (float)c->cfg.std_eps, c->err, c->stream));
+    {
+      PhaseScope ps(c, GCNN_PHASE_AGG_BWD);
+      GCNN_TRY(launch_aggregate_bwd(Ngrid, Egrid, H, dims, c->bb.row_ptr, c->bb.col, c->bb.rev, pq, agg,
+                                    c->dagg, c->dPQ, c->dm, (float)c->cfg.std_eps, c->err, c->stream));
+    }
     // dW_M (H x 2H) and db_M: [x ; 1]^T dPQ  (bias row keeps the first H columns)
     {
       GemmDesc d = blank();
@@ -180,12 +218,14 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
     std::swap(c->dH, c->dX);
   }
   // embedding: dEmb[t] = sum of dx0 over nodes of type t
+  PhaseScope ps(c, GCNN_PHASE_EMBED_BWD);
   GCNN_TRY(launch_embed_bwd(Ngrid, H, dims, c->bb.types, c->dH, c->T, c->emb_partial, c->emb_chunks,
                             c->grads, c->stream));
   return GCNN_OK;
 }
 
 int ctx_step(gcnn_ctx *c) {
+  PhaseScope ps(c, GCNN_PHASE_ADAM);
   return launch_adam(c->P, c->params, c->grads, c->adam_m, c->adam_v, c->opt_state, c->lr_dev,
                      (float)c->cfg.beta1, (float)c->cfg.beta2, (float)c->cfg.adam_eps,
                      (float)c->cfg.weight_decay, c->stream);
