@@ -252,6 +252,23 @@ int gcnn_op_aggregate_bwd(int32_t n_nodes, int32_t n_edges, int32_t hidden, cons
                           const int32_t *col, const int32_t *rev, const float *PQ,
                           const float *agg, const float *dagg, float *dPQ, float *scratch,
                           float std_eps, void *stream);
+/* Same result as gcnn_op_aggregate_bwd, for callers that cannot allocate
+ * device memory where they need this gradient (a host framework whose caching
+ * allocator already holds the device's memory, or a latency-critical loop in
+ * which cudaMalloc/cudaFree, which can synchronise the device, are not
+ * allowed).  It allocates nothing: the per-edge scratch is a fixed array of
+ * 2^22 floats (16 MiB) inside the library, which every GPU that loads the
+ * library holds until the process exits.  n_edges * hidden above 2^22 returns
+ * GCNN_EINVAL.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the one array and each
+ * clears the part it uses, so calls whose GPU work overlaps (on different
+ * streams or host threads) race and must be serialised by the caller.  The
+ * paper has no counterpart of this entry point; it is a deployment variant. */
+int gcnn_op_aggregate_bwd_noalloc(int32_t n_nodes, int32_t n_edges, int32_t hidden, const int32_t *row_ptr,
+                                  const int32_t *col, const int32_t *rev, const float *PQ,
+                                  const float *agg, const float *dagg, float *dPQ, float std_eps,
+                                  void *stream);
 /* pooled[g] = mean of x over nodes node_off[g]..node_off[g+1]-1 (Sec. 3.1). */
 int gcnn_op_pool_fwd(int32_t n_graphs, int32_t hidden, const int32_t *node_off, const float *x,
                      float *pooled, void *stream);

@@ -89,6 +89,7 @@ def _load() -> ctypes.CDLL:
         "gcnn_step_kernel_count": (i32, [vp, P(i32)]),
         "gcnn_op_aggregate_fwd": (i32, [i32, i32, vp, vp, vp, vp, f32, vp]),
         "gcnn_op_aggregate_bwd": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, f32, vp]),
+        "gcnn_op_aggregate_bwd_noalloc": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, f32, vp]),
         "gcnn_op_pool_fwd": (i32, [i32, i32, vp, vp, vp, vp]),
         "gcnn_op_pool_bwd": (i32, [i32, i32, i32, vp, vp, vp, vp, vp]),
     }
