@@ -42,8 +42,8 @@ int check_config(const gcnn_config *c) {
   if ((int64_t)c->max_nodes * c->hidden * 16 > (int64_t)1 << 31 ||
       (int64_t)c->max_edges * c->hidden > (int64_t)1 << 31)
     return set_error(GCNN_EINVAL, "capacity too large for 32-bit indexing");
-  if (c->precision != GCNN_PREC_FP32)
-    return set_error(GCNN_EINVAL, "precision %d is not available in this build", c->precision);
+  if (c->precision != GCNN_PREC_FP32 && c->precision != GCNN_PREC_BF16)
+    return set_error(GCNN_EINVAL, "precision must be GCNN_PREC_FP32 or GCNN_PREC_BF16 (got %d)", c->precision);
   if (!(c->delta > 0.0) || !(c->std_eps >= 0.0)) return set_error(GCNN_EINVAL, "delta must be > 0, std_eps >= 0");
   return GCNN_OK;
 }
@@ -197,6 +197,14 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
     wsf = std::max(wsf, gemm_simt_workspace_floats(n, kAgg * h, 3 * h));
     wsf = std::max(wsf, gemm_simt_workspace_floats(h + 1, 2 * h, n));
     wsf = std::max(wsf, gemm_simt_workspace_floats(n, h, 3 * h));
+    if (cfg->precision == GCNN_PREC_BF16) {
+      wsf = std::max(wsf, gemm_tc_workspace_floats(n, 2 * h, h));
+      wsf = std::max(wsf, gemm_tc_workspace_floats(n, h, 16 * h));
+      wsf = std::max(wsf, gemm_tc_workspace_floats(16 * h + 1, h, n));
+      wsf = std::max(wsf, gemm_tc_workspace_floats(n, kAgg * h, 3 * h));
+      wsf = std::max(wsf, gemm_tc_workspace_floats(h + 1, 2 * h, n));
+      wsf = std::max(wsf, gemm_tc_workspace_floats(n, h, 3 * h));
+    }
     if (n == (int)Nc) break;
   }
   // sizes of every buffer, carved from one allocation
@@ -221,6 +229,11 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   const size_t o_dm = cv.take<float>(Ec * H);
   const size_t o_embp = cv.take<float>((size_t)c->emb_chunks * c->T * H);
   const size_t o_ws = cv.take<float>(wsf);
+  const bool bf = cfg->precision == GCNN_PREC_BF16;
+  const size_t o_wb = cv.take<uint16_t>(bf ? c->P : 0), o_xb = cv.take<uint16_t>(bf ? L * Nc * H : 0);
+  const size_t o_sb = cv.take<uint16_t>(bf ? (cfg->recompute ? 1 : L) * Nc * 15 * H : 0);
+  const size_t o_d30 = cv.take<uint16_t>(bf ? Nc * 3 * H : 0), o_d31 = cv.take<uint16_t>(bf ? Nc * 3 * H : 0);
+  const size_t o_pqb = cv.take<uint16_t>(bf ? Nc * 2 * H : 0);
   c->dbytes = cv.off;
   cudaError_t e = cudaMalloc(&c->dmem, c->dbytes);
   if (e != cudaSuccess) {
@@ -244,6 +257,10 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   c->dH = (float *)(b + o_dH); c->dX = (float *)(b + o_dX); c->dagg = (float *)(b + o_dagg);
   c->dPQ = (float *)(b + o_dPQ); c->dm = (float *)(b + o_dm); c->emb_partial = (float *)(b + o_embp);
   c->ws.partial = (float *)(b + o_ws); c->ws.floats = wsf;
+  if (bf) {
+    c->wb = (uint16_t *)(b + o_wb); c->xb = (uint16_t *)(b + o_xb); c->sb = (uint16_t *)(b + o_sb);
+    c->d3[0] = (uint16_t *)(b + o_d30); c->d3[1] = (uint16_t *)(b + o_d31); c->pqb = (uint16_t *)(b + o_pqb);
+  }
   int rc = GCNN_OK;
   if (cudaMemset(c->dmem, 0, c->dbytes) != cudaSuccess) rc = set_error(GCNN_ECUDA, "cudaMemset failed");
   for (int q = 0; q < 2 && rc == GCNN_OK; ++q) {
@@ -256,10 +273,7 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   if (rc == GCNN_OK && cudaMallocHost(&c->lr_pinned, sizeof(float)) != cudaSuccess)
     rc = set_error(GCNN_ENOMEM, "cannot allocate pinned memory");
   if (rc == GCNN_OK) rc = make_scaler_table(c);
-  if (rc == GCNN_OK) {
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  }
+  if (rc == GCNN_OK) (void)num_sms();  // cache the SM count outside any capture
   if (rc != GCNN_OK) {
     destroy_ctx(c);
     return rc;
@@ -290,9 +304,17 @@ static int copy_flat(gcnn_ctx *c, float *dev, const float *src, float *dst, int6
   return sync(c);
 }
 
+// Refresh the BF16 copy of the parameters (BF16 precision only).
+static int refresh_bf16(gcnn_ctx *c) {
+  if (!c->wb) return GCNN_OK;
+  GCNN_TRY(launch_cast_bf16(c->P, c->params, c->wb, c->stream));
+  return sync(c);
+}
+
 int gcnn_set_params(gcnn_ctx *c, const float *src, int64_t n, int on_device) {
   if (!src) return set_error(GCNN_EINVAL, "null source");
-  return copy_flat(c, c ? c->params : nullptr, src, nullptr, n, on_device);
+  GCNN_TRY(copy_flat(c, c ? c->params : nullptr, src, nullptr, n, on_device));
+  return refresh_bf16(c);
 }
 int gcnn_get_params(gcnn_ctx *c, float *dst, int64_t n, int on_device) {
   if (!dst) return set_error(GCNN_EINVAL, "null destination");
@@ -346,7 +368,8 @@ int gcnn_load(gcnn_ctx *c, const char *path) {
   GCNN_CUDA_TRY(cudaMemcpyAsync(c->adam_m, buf.data() + c->P, c->P * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   GCNN_CUDA_TRY(cudaMemcpyAsync(c->adam_v, buf.data() + 2 * c->P, c->P * sizeof(float), cudaMemcpyHostToDevice, c->stream));
   GCNN_CUDA_TRY(cudaMemcpyAsync(c->opt_state, &step, sizeof(int), cudaMemcpyHostToDevice, c->stream));
-  return sync(c);
+  GCNN_TRY(sync(c));
+  return refresh_bf16(c);
 }
 
 int gcnn_check(gcnn_ctx *c) {

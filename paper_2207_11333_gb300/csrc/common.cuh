@@ -34,6 +34,7 @@ enum : unsigned {
   kErrCollateRange = 1u,   // a graph violates the store limits or capacity
   kErrCapacity = 2u,       // batch totals exceed the context's capacity
   kErrIndex = 4u,          // an index read from memory is out of range
+  kErrTimeout = 8u,        // a bounded wait inside a kernel expired
 };
 
 // Per-graph limits of the collator (a warp sorts one graph in shared memory).
@@ -52,5 +53,17 @@ struct DevDims {
 };
 
 inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+// Two floats -> packed BF16 pair (round to nearest even), lo in the low half.
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
+// Four floats -> four BF16 at p (8-byte aligned).
+__device__ __forceinline__ void st_bf16x4(uint16_t *p, float a, float b, float c, float d) {
+  *reinterpret_cast<uint2 *>(p) = make_uint2(bf16x2(a, b), bf16x2(c, d));
+}
 
 }  // namespace gcnn

@@ -48,6 +48,13 @@ struct gcnn_ctx {
   float *dH = nullptr, *dX = nullptr, *dagg = nullptr, *dPQ = nullptr, *dm = nullptr;
   float *emb_partial = nullptr;
   int emb_chunks = 0;
+
+  // BF16 operands of the tensor-core GEMMs (precision == GCNN_PREC_BF16)
+  uint16_t *wb = nullptr;    // parameters cast to BF16 after every update
+  uint16_t *xb = nullptr;    // L x Nc x H      layer inputs
+  uint16_t *sb = nullptr;    // (recompute ? 1 : L) x Nc x 15H  scaled aggregates
+  uint16_t *d3[2] = {nullptr, nullptr};  // Nc x 3H  masked, scaled output gradients
+  uint16_t *pqb = nullptr;   // Nc x 2H         message gradients
   gcnn::GemmWorkspace ws{};
 
   // host-side state

@@ -268,6 +268,8 @@ splitk_reduce_kernel(GemmDesc d, DevDims dims, const float *__restrict__ partial
 
 int g_num_sms = 0;
 
+}  // namespace
+
 int num_sms() {
   if (g_num_sms == 0) {
     int dev = 0, n = 0;
@@ -279,6 +281,8 @@ int num_sms() {
   }
   return g_num_sms;
 }
+
+namespace {
 
 int choose_splits(int M, int N, int K) {
   const long long tiles = (long long)ceil_div(M, BM) * ceil_div(N, BN);
@@ -334,11 +338,14 @@ int run_gemm_simt(const GemmDesc &d, DevDims dims, const GemmWorkspace &ws, cuda
   else
     sgemm_kernel<false, false><<<grid, kThreads, 0, s>>>(d, dims, part, splits, kps);
   GCNN_LAUNCH_CHECK();
-  if (splits > 1) {
-    const long long work = (long long)d.M * (d.N / 4);
-    splitk_reduce_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(d, dims, part, splits);
-    GCNN_LAUNCH_CHECK();
-  }
+  if (splits > 1) GCNN_TRY(run_splitk_reduce(d, dims, part, splits, s));
+  return GCNN_OK;
+}
+
+int run_splitk_reduce(const GemmDesc &d, DevDims dims, const float *partial, int splits, cudaStream_t s) {
+  const long long work = (long long)d.M * (d.N / 4);
+  splitk_reduce_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(d, dims, partial, splits);
+  GCNN_LAUNCH_CHECK();
   return GCNN_OK;
 }
 

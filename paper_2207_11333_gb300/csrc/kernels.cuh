@@ -31,24 +31,31 @@ int launch_collate(int G, const int64_t *ids, StoreView st, BatchBuf b, const fl
 
 // ---------------------------------------------------------------- aggregate.cu
 // agg[i] = [sum, mean, min, max, std](P_i + Q_j, j in N(i)); PQ is N x 2H.
+// S16 (nullable, N x 15H BF16) additionally receives [agg, amp*agg, att*agg],
+// the scaled aggregates as the BF16 operand of the update GEMM.
 int launch_aggregate_fwd(int n_nodes, int H, DevDims dims, const int *row_ptr, const int *col,
-                         const float *PQ, float *agg, float eps, unsigned *err, cudaStream_t s);
+                         const float *PQ, float *agg, float eps, unsigned *err, cudaStream_t s,
+                         uint16_t *S16 = nullptr, const float *amp = nullptr, const float *att = nullptr);
 // dPQ from dagg; scratch is E x H (per-edge message gradients).
 int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const int *row_ptr,
                          const int *col, const int *rev, const float *PQ, const float *agg,
                          const float *dagg, float *dPQ, float *scratch, float eps, unsigned *err,
-                         cudaStream_t s);
+                         cudaStream_t s, uint16_t *dPQ16 = nullptr);
 
 // ---------------------------------------------------------------- small.cu
 int launch_embed(int n_nodes, int H, DevDims dims, const uint8_t *types, const float *emb,
-                 int n_types, float *x0, cudaStream_t s);
+                 int n_types, float *x0, cudaStream_t s, uint16_t *x0_16 = nullptr);
 // dEmb[t] = sum of dx0 over nodes of type t (deterministic two-stage sum).
 int launch_embed_bwd(int n_nodes, int H, DevDims dims, const uint8_t *types, const float *dx0,
                      int n_types, float *partial, int max_chunks, float *demb, cudaStream_t s);
 int launch_pool_fwd(int G, int H, DevDims dims, const int *node_off, const float *x, float *pooled,
                     cudaStream_t s);
+// D3 (nullable, N x 3H BF16) additionally receives [g, amp*g, att*g] with
+// g = dx * [h > 0] (the ReLU-masked, degree-scaled gradient of the last layer).
 int launch_pool_bwd(int G, int n_nodes, int H, DevDims dims, const int *node_off,
-                    const int *graph_id, const float *dpooled, float *dx, cudaStream_t s);
+                    const int *graph_id, const float *dpooled, float *dx, cudaStream_t s,
+                    uint16_t *D3 = nullptr, const float *h = nullptr, const float *amp = nullptr,
+                    const float *att = nullptr);
 // Head forward: z1 = g W1 + b1, pred = ReLU(z1) . w2 + b2.
 int launch_head_fwd(int G, int H, int Hh, DevDims dims, const float *g, const float *w1,
                     const float *b1, const float *w2, const float *b2, float *z1, float *pred,
@@ -111,5 +118,59 @@ struct GemmWorkspace {
 
 int run_gemm_simt(const GemmDesc &d, DevDims dims, const GemmWorkspace &ws, cudaStream_t s);
 size_t gemm_simt_workspace_floats(int M, int N, int K);
+// C = epilogue(sum over splits of partial[z]) in split order (deterministic).
+int run_splitk_reduce(const GemmDesc &d, DevDims dims, const float *partial, int splits, cudaStream_t s);
+int num_sms();
+
+// ---------------------------------------------------------------- gemm_tc.cu
+// C = A . B on the tensor cores: BF16 operands (stored as uint16_t bit
+// patterns), FP32 accumulation in TMEM.  Operands come from up to kMaxSeg
+// BF16 arrays along the feature dimension (ptr == nullptr: a constant-one
+// row, for bias gradients).
+struct TcSeg {
+  int begin;
+  const uint16_t *ptr;
+  int ld;
+};
+
+struct TcOperand {
+  TcSeg seg[kMaxSeg];
+  int nseg;
+  // A (M x K): false -> A(m,k) = ptr[m*ld + k - begin] (segments along K)
+  //            true  -> A(m,k) = ptr[k*ld + m - begin] (segments along M)
+  // B (K x N): false -> B(k,n) = ptr[n*ld + k - begin]
+  //            true  -> B(k,n) = ptr[(k - begin)*ld + n]  (segments along K)
+  bool mn_major;
+};
+
+struct TcEpilogue {
+  float *C;            // FP32 result (nullable)
+  int ldc;
+  const float *bias;   // bias[n] for n < bias_n
+  int bias_n;
+  bool relu;
+  int last_row_cols;   // > 0: row M-1 keeps only its first last_row_cols columns
+  uint16_t *C16;       // BF16 copy of the result (nullable)
+  int ld16;
+  // [v*[mask>0], amp*v*[mask>0], att*v*[mask>0]] as BF16 into D3 (nullable):
+  // the masked, degree-scaled output gradient consumed by the next backward GEMMs
+  uint16_t *D3;
+  int ld3;
+  const float *mask;
+  int ldm;
+  const float *amp, *att;
+};
+
+struct TcDesc {
+  int M, N, K;
+  NodeDim node_dim;
+  TcOperand A, B;
+  TcEpilogue ep;
+};
+
+int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned *err, cudaStream_t s);
+size_t gemm_tc_workspace_floats(int M, int N, int K);
+// dst[i] = bf16(src[i]) (round to nearest even)
+int launch_cast_bf16(int64_t n, const float *src, uint16_t *dst, cudaStream_t s);
 
 }  // namespace gcnn

@@ -47,6 +47,27 @@ int gemm(gcnn_ctx *c, const GemmDesc &d) {
   return run_gemm_simt(d, DevDims{c->bb.dims}, c->ws, c->stream);
 }
 
+int tc(gcnn_ctx *c, const TcDesc &d) {
+  PhaseScope ps(c, GCNN_PHASE_GEMM);
+  return run_gemm_tc(d, DevDims{c->bb.dims}, c->ws, c->err, c->stream);
+}
+
+bool bf16(const gcnn_ctx *c) { return c->cfg.precision == GCNN_PREC_BF16; }
+
+// BF16 views
+uint16_t *xb_at(const gcnn_ctx *c, int l) { return c->xb + (size_t)l * c->Nc * c->H; }
+uint16_t *sb_at(const gcnn_ctx *c, int l) {
+  return c->sb + (c->cfg.recompute ? 0 : (size_t)l * c->Nc * 15 * c->H);
+}
+const uint16_t *wb_of(const gcnn_ctx *c, const float *p) { return c->wb + (p - c->params); }
+
+TcSeg tseg(int begin, const uint16_t *ptr, int ld) { return TcSeg{begin, ptr, ld}; }
+
+TcDesc tblank() {
+  TcDesc d{};
+  return d;
+}
+
 // PQ = x [A | B] + [b_M | 0]    (message layer, both halves at once)
 int gemm_message(gcnn_ctx *c, int Ngrid, int l) {
   const int H = c->H;
@@ -80,6 +101,104 @@ int gemm_update(gcnn_ctx *c, int Ngrid, int l) {
   return gemm(c, d);
 }
 
+// BF16: PQ = x [A | B] + [b_M | 0]
+int tc_message(gcnn_ctx *c, int Ngrid, int l) {
+  const int H = c->H;
+  LayerW w = layer_ptrs(c->params, c, l);
+  TcDesc d = tblank();
+  d.M = Ngrid; d.N = 2 * H; d.K = H; d.node_dim = kNodeM;
+  d.A.nseg = 1; d.A.seg[0] = tseg(0, xb_at(c, l), H); d.A.mn_major = false;
+  d.B.nseg = 1; d.B.seg[0] = tseg(0, wb_of(c, w.msg_w), 2 * H); d.B.mn_major = true;
+  d.ep.C = pq_at(c, l); d.ep.ldc = 2 * H; d.ep.bias = w.msg_b; d.ep.bias_n = H;
+  return tc(c, d);
+}
+
+// BF16: x' = ReLU([x | agg | amp*agg | att*agg] W_U + b_U), also written as BF16
+int tc_update(gcnn_ctx *c, int Ngrid, int l) {
+  const int H = c->H;
+  LayerW w = layer_ptrs(c->params, c, l);
+  TcDesc d = tblank();
+  d.M = Ngrid; d.N = H; d.K = 16 * H; d.node_dim = kNodeM;
+  d.A.nseg = 2; d.A.seg[0] = tseg(0, xb_at(c, l), H); d.A.seg[1] = tseg(H, sb_at(c, l), 15 * H);
+  d.A.mn_major = false;
+  d.B.nseg = 1; d.B.seg[0] = tseg(0, wb_of(c, w.upd_w), H); d.B.mn_major = true;
+  d.ep.C = xs_at(c, l + 1); d.ep.ldc = H; d.ep.bias = w.upd_b; d.ep.bias_n = H; d.ep.relu = true;
+  if (l + 1 < c->L) { d.ep.C16 = xb_at(c, l + 1); d.ep.ld16 = H; }
+  return tc(c, d);
+}
+
+// BF16 backward of layer l; dH holds dL/dx_{l+1} and d3[cur] its masked,
+// scaled BF16 form.  Writes dX = dL/dx_l and, for l > 0, d3[cur ^ 1].
+int tc_backward_layer(gcnn_ctx *c, int Ngrid, int Egrid, int l, int cur) {
+  const int H = c->H;
+  DevDims dims{c->bb.dims};
+  LayerW w = layer_ptrs(c->params, c, l);
+  LayerW gw = layer_ptrs(c->grads, c, l);
+  const float *pq = pq_at(c, l);
+  float *agg = agg_at(c, l);
+  const uint16_t *d3 = c->d3[cur];
+  if (c->cfg.recompute) {
+    PhaseScope ps(c, GCNN_PHASE_AGG_FWD);
+    GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq, agg, (float)c->cfg.std_eps, c->err,
+                                  c->stream, sb_at(c, l), c->bb.amp, c->bb.att));
+  }
+  {  // dW_U, db_U = [x | scaled aggs | 1]^T dpre
+    TcDesc d = tblank();
+    d.M = 16 * H + 1; d.N = H; d.K = Ngrid; d.node_dim = kNodeK;
+    d.A.nseg = 3; d.A.mn_major = true;
+    d.A.seg[0] = tseg(0, xb_at(c, l), H);
+    d.A.seg[1] = tseg(H, sb_at(c, l), 15 * H);
+    d.A.seg[2] = tseg(16 * H, nullptr, 0);
+    d.B.nseg = 1; d.B.seg[0] = tseg(0, d3, 3 * H); d.B.mn_major = true;
+    d.ep.C = gw.upd_w; d.ep.ldc = H;
+    GCNN_TRY(tc(c, d));
+  }
+  {  // dagg = [dpre | amp dpre | att dpre] [W_id ; W_amp ; W_att]^T
+    TcDesc d = tblank();
+    d.M = Ngrid; d.N = kAgg * H; d.K = 3 * H; d.node_dim = kNodeM;
+    d.A.nseg = 1; d.A.seg[0] = tseg(0, d3, 3 * H); d.A.mn_major = false;
+    const uint16_t *wu = wb_of(c, w.upd_w);
+    d.B.nseg = 3; d.B.mn_major = false;
+    d.B.seg[0] = tseg(0, wu + (size_t)H * H, H);
+    d.B.seg[1] = tseg(H, wu + (size_t)6 * H * H, H);
+    d.B.seg[2] = tseg(2 * H, wu + (size_t)11 * H * H, H);
+    d.ep.C = c->dagg; d.ep.ldc = kAgg * H;
+    GCNN_TRY(tc(c, d));
+  }
+  {
+    PhaseScope ps(c, GCNN_PHASE_AGG_BWD);
+    GCNN_TRY(launch_aggregate_bwd(Ngrid, Egrid, H, dims, c->bb.row_ptr, c->bb.col, c->bb.rev, pq, agg, c->dagg,
+                                  c->dPQ, c->dm, (float)c->cfg.std_eps, c->err, c->stream, c->pqb));
+  }
+  {  // dW_M, db_M = [x | 1]^T dPQ
+    TcDesc d = tblank();
+    d.M = H + 1; d.N = 2 * H; d.K = Ngrid; d.node_dim = kNodeK;
+    d.A.nseg = 2; d.A.mn_major = true;
+    d.A.seg[0] = tseg(0, xb_at(c, l), H);
+    d.A.seg[1] = tseg(H, nullptr, 0);
+    d.B.nseg = 1; d.B.seg[0] = tseg(0, c->pqb, 2 * H); d.B.mn_major = true;
+    d.ep.C = gw.msg_w; d.ep.ldc = 2 * H; d.ep.last_row_cols = H;
+    GCNN_TRY(tc(c, d));
+  }
+  {  // dx = dpre W_x^T + [dP | dQ] [A | B]^T ; next layer's masked, scaled BF16 gradient
+    TcDesc d = tblank();
+    d.M = Ngrid; d.N = H; d.K = 3 * H; d.node_dim = kNodeM;
+    d.A.nseg = 2; d.A.mn_major = false;
+    d.A.seg[0] = tseg(0, d3, 3 * H);
+    d.A.seg[1] = tseg(H, c->pqb, 2 * H);
+    d.B.nseg = 2; d.B.mn_major = false;
+    d.B.seg[0] = tseg(0, wb_of(c, w.upd_w), H);
+    d.B.seg[1] = tseg(H, wb_of(c, w.msg_w), 2 * H);
+    d.ep.C = c->dX; d.ep.ldc = H;
+    if (l > 0) {
+      d.ep.D3 = c->d3[cur ^ 1]; d.ep.ld3 = 3 * H;
+      d.ep.mask = xs_at(c, l); d.ep.ldm = H; d.ep.amp = c->bb.amp; d.ep.att = c->bb.att;
+    }
+    GCNN_TRY(tc(c, d));
+  }
+  return GCNN_OK;
+}
+
 }  // namespace
 
 PhaseScope::PhaseScope(gcnn_ctx *c, int phase) : c_(c), idx_(-1) {
@@ -108,18 +227,23 @@ int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train) {
   (void)Egrid;
   const int H = c->H;
   DevDims dims{c->bb.dims};
+  const bool bf = bf16(c);
   {
     PhaseScope ps(c, GCNN_PHASE_EMBED);
-    GCNN_TRY(launch_embed(Ngrid, H, dims, c->bb.types, c->params, c->T, xs_at(c, 0), c->stream));
+    GCNN_TRY(launch_embed(Ngrid, H, dims, c->bb.types, c->params, c->T, xs_at(c, 0), c->stream,
+                          bf ? xb_at(c, 0) : nullptr));
   }
   for (int l = 0; l < c->L; ++l) {
-    GCNN_TRY(gemm_message(c, Ngrid, l));
+    if (bf) GCNN_TRY(tc_message(c, Ngrid, l));
+    else GCNN_TRY(gemm_message(c, Ngrid, l));
     {
       PhaseScope ps(c, GCNN_PHASE_AGG_FWD);
       GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq_at(c, l), agg_at(c, l),
-                                    (float)c->cfg.std_eps, c->err, c->stream));
+                                    (float)c->cfg.std_eps, c->err, c->stream, bf ? sb_at(c, l) : nullptr,
+                                    c->bb.amp, c->bb.att));
     }
-    GCNN_TRY(gemm_update(c, Ngrid, l));
+    if (bf) GCNN_TRY(tc_update(c, Ngrid, l));
+    else GCNN_TRY(gemm_update(c, Ngrid, l));
   }
   PhaseScope ps(c, GCNN_PHASE_HEAD);
   GCNN_TRY(launch_pool_fwd(G, H, dims, c->bb.node_off, xs_at(c, c->L), c->pooled, c->stream));
@@ -141,9 +265,18 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
   PhaseScope ps(c, GCNN_PHASE_HEAD);
   GCNN_TRY(launch_head_bwd(G, H, c->Hh, dims, c->pooled, hp, hp + HHh + c->Hh, c->z1, c->pred,
                            c->bb.y, dpred, c->dpred, c->dz1, ghp, c->dg, loss_accum, c->stream));
-  GCNN_TRY(launch_pool_bwd(G, Ngrid, H, dims, c->bb.node_off, c->bb.graph_id, c->dg, c->dH, c->stream));
+  GCNN_TRY(launch_pool_bwd(G, Ngrid, H, dims, c->bb.node_off, c->bb.graph_id, c->dg, c->dH, c->stream,
+                           bf16(c) ? c->d3[0] : nullptr, xs_at(c, c->L), c->bb.amp, c->bb.att));
   }
-  for (int l = c->L - 1; l >= 0; --l) {
+  if (bf16(c)) {
+    int cur = 0;
+    for (int l = c->L - 1; l >= 0; --l) {
+      GCNN_TRY(tc_backward_layer(c, Ngrid, Egrid, l, cur));
+      cur ^= 1;
+      std::swap(c->dH, c->dX);
+    }
+  }
+  for (int l = bf16(c) ? -1 : c->L - 1; l >= 0; --l) {
     LayerW w = layer_ptrs(c->params, c, l);
     LayerW gw = layer_ptrs(c->grads, c, l);
     const float *x = xs_at(c, l), *h = xs_at(c, l + 1), *pq = pq_at(c, l);
@@ -226,9 +359,11 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
 
 int ctx_step(gcnn_ctx *c) {
   PhaseScope ps(c, GCNN_PHASE_ADAM);
-  return launch_adam(c->P, c->params, c->grads, c->adam_m, c->adam_v, c->opt_state, c->lr_dev,
-                     (float)c->cfg.beta1, (float)c->cfg.beta2, (float)c->cfg.adam_eps,
-                     (float)c->cfg.weight_decay, c->stream);
+  GCNN_TRY(launch_adam(c->P, c->params, c->grads, c->adam_m, c->adam_v, c->opt_state, c->lr_dev,
+                       (float)c->cfg.beta1, (float)c->cfg.beta2, (float)c->cfg.adam_eps,
+                       (float)c->cfg.weight_decay, c->stream));
+  if (c->wb) GCNN_TRY(launch_cast_bf16(c->P, c->params, c->wb, c->stream));
+  return GCNN_OK;
 }
 
 }  // namespace gcnn

@@ -16,7 +16,8 @@ __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<floa
 
 // ---------------------------------------------------------------- embedding
 __global__ void embed_kernel(int n_cap, int H, DevDims dims, const uint8_t *__restrict__ types,
-                             const float *__restrict__ emb, int T, float *__restrict__ x0) {
+                             const float *__restrict__ emb, int T, float *__restrict__ x0,
+                             uint16_t *__restrict__ x0_16) {
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -25,6 +26,7 @@ __global__ void embed_kernel(int n_cap, int H, DevDims dims, const uint8_t *__re
   const int ty = types[i];
   const float4 v = ty < T ? ld4(emb + (size_t)ty * H + c) : make_float4(0.f, 0.f, 0.f, 0.f);
   st4(x0 + (size_t)i * H + c, v);
+  if (x0_16) st_bf16x4(x0_16 + (size_t)i * H + c, v.x, v.y, v.z, v.w);
 }
 
 constexpr int kEmbChunk = 64;   // nodes per partial sum
@@ -91,7 +93,8 @@ __global__ void pool_fwd_kernel(int g_cap, int H, DevDims dims, const int *__res
 
 __global__ void pool_bwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ node_off,
                                 const int *__restrict__ graph_id, const float *__restrict__ dpooled,
-                                float *__restrict__ dx) {
+                                float *__restrict__ dx, uint16_t *__restrict__ D3, const float *__restrict__ h,
+                                const float *__restrict__ amp, const float *__restrict__ att) {
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -100,7 +103,18 @@ __global__ void pool_bwd_kernel(int n_cap, int H, DevDims dims, const int *__res
   const int g = graph_id[i];
   const float n = (float)(node_off[g + 1] - node_off[g]);
   const float4 v = ld4(dpooled + (size_t)g * H + c);
-  st4(dx + (size_t)i * H + c, make_float4(v.x / n, v.y / n, v.z / n, v.w / n));
+  const float4 d = make_float4(v.x / n, v.y / n, v.z / n, v.w / n);
+  st4(dx + (size_t)i * H + c, d);
+  if (D3) {
+    const float4 m = ld4(h + (size_t)i * H + c);
+    const float gx = m.x > 0.f ? d.x : 0.f, gy = m.y > 0.f ? d.y : 0.f;
+    const float gz = m.z > 0.f ? d.z : 0.f, gw = m.w > 0.f ? d.w : 0.f;
+    const float a = amp[i], t = att[i];
+    uint16_t *o = D3 + (size_t)i * 3 * H + c;
+    st_bf16x4(o, gx, gy, gz, gw);
+    st_bf16x4(o + H, a * gx, a * gy, a * gz, a * gw);
+    st_bf16x4(o + 2 * H, t * gx, t * gy, t * gz, t * gw);
+  }
 }
 
 // ---------------------------------------------------------------- head
@@ -271,10 +285,10 @@ adam_kernel(int64_t n, float *__restrict__ p, const float *__restrict__ g, float
 }  // namespace
 
 int launch_embed(int n_nodes, int H, DevDims dims, const uint8_t *types, const float *emb,
-                 int n_types, float *x0, cudaStream_t s) {
+                 int n_types, float *x0, cudaStream_t s, uint16_t *x0_16) {
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
-  embed_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(n_nodes, H, dims, types, emb, n_types, x0);
+  embed_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(n_nodes, H, dims, types, emb, n_types, x0, x0_16);
   GCNN_LAUNCH_CHECK();
   return GCNN_OK;
 }
@@ -306,12 +320,13 @@ int launch_pool_fwd(int G, int H, DevDims dims, const int *node_off, const float
 }
 
 int launch_pool_bwd(int G, int n_nodes, int H, DevDims dims, const int *node_off,
-                    const int *graph_id, const float *dpooled, float *dx, cudaStream_t s) {
+                    const int *graph_id, const float *dpooled, float *dx, cudaStream_t s, uint16_t *D3,
+                    const float *h, const float *amp, const float *att) {
   (void)G;
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
   pool_bwd_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(n_nodes, H, dims, node_off, graph_id,
-                                                                 dpooled, dx);
+                                                                 dpooled, dx, D3, h, amp, att);
   GCNN_LAUNCH_CHECK();
   return GCNN_OK;
 }

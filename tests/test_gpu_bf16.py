@@ -1,0 +1,63 @@
+"""BF16 tensor-core GEMM path (tcgen05) against the FP64 oracle: forward within
+2e-2 relative (normwise) per output and per layer; gradient errors stated and
+bounded; the BF16 and FP32 paths agree to BF16 accuracy."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from gpu_common import context, oracle_step, write_both
+from helpers import rel_norm
+
+pytestmark = pytest.mark.gpu
+
+BF16_FWD_TOL = 2e-2
+
+
+def _run(tmp_path, precision, G=64, lo=5, hi=30, H=32, L=2, recompute=False):
+    import paper_2207_11333_gb300 as g
+    d, gs, delta, student = workloads.small_parity(G=G, lo=lo, hi=hi, H=H, L=L)
+    path, ost = write_both(gs, str(tmp_path))
+    st = g.Store(path)
+    ctx = context(H, L, G, int(gs.n_nodes), int(gs.n_edges), delta, precision=precision, recompute=recompute)
+    ctx.set_params(student)
+    b = ctx.collate(st, np.arange(G))
+    pred = torch.empty(G, device="cuda")
+    ctx.forward(b, pred, train=True)
+    acts = ctx.activations(b)
+    ctx.backward(b)
+    grads = ctx.get_grads()
+    ctx.check()
+    ob = oracle.collate(ost, np.arange(G), delta)
+    return d, student, ob, pred.cpu().numpy(), acts, grads
+
+
+@pytest.mark.parametrize("G,lo,hi,H,L", [(64, 5, 30, 32, 2), (13, 3, 51, 200, 2), (150, 3, 51, 64, 3)])
+def test_bf16_forward_and_gradients(tmp_path, G, lo, hi, H, L):
+    import paper_2207_11333_gb300 as g
+    d, student, ob, pred, acts, grads = _run(tmp_path, g.PREC_BF16, G, lo, hi, H, L)
+    opred, oxs, _, _ = oracle.forward(d, student.astype(np.float64), ob, want_layers=True)
+    _, ograd, _, _ = oracle_step(d, student, ob)
+    assert rel_norm(pred, opred) < BF16_FWD_TOL, rel_norm(pred, opred)
+    for l in range(1, d.L + 1):
+        assert rel_norm(acts[l], oxs[l]) < BF16_FWD_TOL, (l, rel_norm(acts[l], oxs[l]))
+    gv, ov = oracle.split_params(d, grads), oracle.split_params(d, ograd)
+    errs = {k: rel_norm(gv[k], ov[k]) for k in ov if np.linalg.norm(ov[k]) > 0}
+    print("bf16 gradient rel errors:", {k: f"{v:.2e}" for k, v in errs.items()})
+    assert max(errs.values()) < 0.1, errs
+
+
+def test_bf16_matches_fp32_path(tmp_path):
+    import paper_2207_11333_gb300 as g
+    _, _, _, p16, a16, g16 = _run(tmp_path, g.PREC_BF16)
+    _, _, _, p32, a32, g32 = _run(tmp_path, g.PREC_FP32)
+    assert rel_norm(p16, p32) < BF16_FWD_TOL
+    assert rel_norm(g16, g32) < 0.1
+
+
+def test_bf16_recompute_identical(tmp_path):
+    import paper_2207_11333_gb300 as g
+    _, _, _, p1, _, g1 = _run(tmp_path, g.PREC_BF16, recompute=False)
+    _, _, _, p2, _, g2 = _run(tmp_path, g.PREC_BF16, recompute=True)
+    assert np.array_equal(p1, p2) and np.array_equal(g1, g2)
