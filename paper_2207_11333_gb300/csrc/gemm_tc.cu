@@ -410,8 +410,9 @@ int choose(int M, int N, int K, int *BN, int *ntiles, int *splits) {
   *BN = ((N + *ntiles - 1) / *ntiles + 15) / 16 * 16;
   const long long tiles = (long long)*ntiles * ((M + BM - 1) / BM);
   const int ktiles = (K + BK - 1) / BK;
-  int s = (int)std::max<long long>(1, (num_sms() + tiles - 1) / tiles);
-  s = std::min(s, std::max(1, ktiles / 2));
+  // one wave (one 197 KB CTA per SM), at least 4 k-tiles per split
+  int s = (int)std::max<long long>(1, num_sms() / tiles);
+  s = std::min(s, std::max(1, ktiles / 4));
   *splits = std::min(s, 32);
   return ktiles;
 }
