@@ -224,6 +224,150 @@ def make_targets(g, st, delta, n_graphs, gpu_batch=2048):
     return (1.0 + 9.0 * (y - lo) / max(hi - lo, 1e-30)).astype(np.float32)
 
 
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+class Workload:
+    """The 200k-graph store (device-resident), its teacher targets, the epoch order, capacities."""
+
+    def __init__(self, g, rank: int):
+        gs = dataset()
+        self.tmp = tempfile.mkdtemp(prefix="gcnn_bench_")
+        self.path = os.path.join(self.tmp, "train.gcnn")
+        synth.write_store(self.path, gs)
+        self.st = g.Store(self.path)
+        self.st.to_device()
+        self.delta = self.st.delta(np.arange(N_TRAIN))
+        self.y = make_targets(g, self.st, self.delta, N_TRAIN + N_HELDOUT)
+        self.st.set_targets(self.y)
+        self.order = epoch_order(rank)
+        self.nb = (N_TRAIN + BATCH - 1) // BATCH
+        sizes = [self.st.batch_size(self.order[i * BATCH:(i + 1) * BATCH]) for i in range(self.nb)]
+        self.Nc = (max(s[0] for s in sizes) + 255) // 256 * 256
+        self.Ec = (max(s[1] for s in sizes) + 511) // 512 * 512
+
+
+def make_ctx(g, wl: Workload, precision: str):
+    prec = g.PREC_BF16 if precision == "bf16" else g.PREC_FP32
+    ctx = g.Context(g.make_config(H, L, BATCH, wl.Nc, wl.Ec, delta=wl.delta, precision=prec))
+    ctx.set_params(synth.init_params(SEED_STUDENT, H, L))
+    ctx.set_order(wl.st, wl.order)
+    return ctx
+
+
+def batch_at(ctx, wl: Workload, k: int):
+    i = k % wl.nb
+    return ctx.collate_range(wl.st, i * BATCH, min(BATCH, N_TRAIN - i * BATCH))
+
+
+def timed_steps(ctx, wl, steps, warmup, flush, loss_acc, dist=None, gpu_index=None):
+    """Device time of `steps` training steps (per-step CUDA events, L2 flushed between steps)."""
+    import torch
+    for k in range(warmup):
+        ctx.train_step(batch_at(ctx, wl, k), LR, loss_acc)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_index) if gpu_index is not None else None
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    graphs = 0
+    torch.cuda.nvtx.range_push("timed")
+    t_wall = time.perf_counter()
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record()
+        b = batch_at(ctx, wl, warmup + k)
+        ctx.train_step(b, LR, loss_acc)
+        evs[k][1].record()
+        graphs += b.n_graphs
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    torch.cuda.nvtx.range_pop()
+    clocks = sampler.stop() if sampler else None
+    dev_s = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    if dist:
+        tmax = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        gsum = torch.tensor([float(graphs)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(gsum, op=dist.ReduceOp.SUM)
+        dev_s, total = float(tmax.item()), float(gsum.item())
+    else:
+        total = float(graphs)
+    return {"value": total / dev_s, "dev_s": dev_s, "graphs": total, "wall_s": wall, "clocks": clocks,
+            "kernels_per_step": ctx.step_kernel_count() + 2}
+
+
+def kernel_profile(ctx, wl, n_steps, warmup, flush, loss_acc, precision):
+    """The same steps eagerly with CUDA events around every launch: per-phase ms and GEMM roofline."""
+    ctx.profile(True)
+    ctx.profile_read()
+    flops = agg_bytes = 0.0
+    for k in range(n_steps):
+        flush.zero_()
+        b = batch_at(ctx, wl, warmup + k)
+        ctx.train_step(b, LR, loss_acc)
+        flops += gemm_flops(b.n_nodes)
+        agg_bytes += L * agg_fwd_bytes(b.n_nodes, b.n_edges)
+    ph = ctx.profile_read()
+    ctx.profile(False)
+    out = {"phases_ms_per_step": {k: v[0] / n_steps for k, v in ph.items()}}
+    achieved = flops / (ph["gemm"][0] / 1e3) / 1e12
+    peaks = measured_peaks()
+    if precision == "bf16":
+        peak = float(peaks.get("bf16_tflops", 1900.0))
+        src = "measured (MEASURED_PEAKS.json bf16_tflops, burst)" if "bf16_tflops" in peaks else "fallback 1.9 PFLOP/s"
+        out["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                           "frac": achieved / peak, "traffic": None, "peak_source": src,
+                           "kernel": "tc_gemm_kernel + tc_reduce_kernel (all dense GEMMs of the step, "
+                                     "BF16 tcgen05, FP32 accumulate)"}
+    else:
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
+        out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                           "frac": achieved / peak, "traffic": None,
+                           "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)",
+                           "kernel": "sgemm_kernel + splitk_reduce (all dense GEMMs of the step, FP32 FFMA)"}
+    hbm, hbm_src = measured_hbm()
+    a_gbs = agg_bytes / (ph["agg_fwd"][0] / 1e3) / 1e9
+    out["roofline_aggregate"] = {"bound": "hbm", "achieved": a_gbs, "peak": hbm, "unit": "GB/s", "frac": a_gbs / hbm,
+                                 "traffic": None, "peak_source": hbm_src,
+                                 "note": "128-graph batches fit in L2; the HBM figure needs a >L2 batch"}
+    return out
+
+
+def e2e_steps(g, ctx, wl, steps, loss_acc):
+    """The same steps through the public API from a host store: pinned staging + H2D per batch, loss D2H."""
+    import torch
+    sh = g.Store(wl.path)          # host-resident twin
+    sh.set_targets(wl.y)
+    pinned = torch.zeros(3, dtype=torch.float64).pin_memory()
+    for k in range(3):
+        ctx.train_step(ctx.collate(sh, wl.order[k * BATCH:(k + 1) * BATCH]), LR, loss_acc)
+    torch.cuda.synchronize()
+    h2d = 0
+    n = 0
+    t0 = time.perf_counter()
+    for k in range(steps):
+        i = k % wl.nb
+        b = ctx.collate(sh, wl.order[i * BATCH:(i + 1) * BATCH])
+        ctx.train_step(b, LR, loss_acc)
+        pinned.copy_(loss_acc, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        _ = float(pinned[0])
+        n += b.n_graphs
+        h2d += 16 * (b.n_graphs + 1) + 4 * b.n_graphs + b.n_nodes + 2 * b.n_edges
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "graphs/s", "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": 24,
+            "steps": steps, "path": "gcnn_collate from a host store (pinned staging, one H2D) + gcnn_train_step "
+                                    "+ loss read back each step"}
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -237,147 +381,55 @@ def run_ours(args):
     import paper_2207_11333_gb300 as g
 
     t_setup = time.perf_counter()
-    gs = dataset()
-    tmp = tempfile.mkdtemp(prefix="gcnn_bench_")
-    path = os.path.join(tmp, "train.gcnn")
-    synth.write_store(path, gs)
-    st = g.Store(path)
-    st.to_device()
-    delta = st.delta(np.arange(N_TRAIN))
-    y = make_targets(g, st, delta, N_TRAIN + N_HELDOUT)
-    st.set_targets(y)
-    order = epoch_order(rank)
-    nb = (N_TRAIN + BATCH - 1) // BATCH
-    sizes = [st.batch_size(order[i * BATCH:(i + 1) * BATCH]) for i in range(nb)]
-    Nc = (max(s[0] for s in sizes) + 255) // 256 * 256
-    Ec = (max(s[1] for s in sizes) + 511) // 512 * 512
-    prec = g.PREC_BF16 if args.precision == "bf16" else g.PREC_FP32
-    ctx = g.Context(g.make_config(H, L, BATCH, Nc, Ec, delta=delta, precision=prec))
-    ctx.set_params(synth.init_params(SEED_STUDENT, H, L))
-    ctx.set_order(st, order)
-    loss_acc = torch.zeros(3, dtype=torch.float64, device="cuda")
+    wl = Workload(g, rank)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > 129 MB L2
-    log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s, capacity N={Nc} E={Ec}, delta={delta:.6f}")
+    loss_acc = torch.zeros(3, dtype=torch.float64, device="cuda")
+    log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s, capacity N={wl.Nc} E={wl.Ec}, delta={wl.delta:.6f}")
 
-    def batch_at(k):
-        i = k % nb
-        return ctx.collate_range(st, i * BATCH, min(BATCH, N_TRAIN - i * BATCH))
-
-    for k in range(args.warmup):
-        ctx.train_step(batch_at(k), LR, loss_acc)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    graphs = 0
-    torch.cuda.nvtx.range_push("timed")
-    t_wall = time.perf_counter()
-    for k in range(args.steps):
-        flush.zero_()
-        evs[k][0].record()
-        b = batch_at(args.warmup + k)
-        ctx.train_step(b, LR, loss_acc)
-        evs[k][1].record()
-        graphs += b.n_graphs
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - t_wall
-    torch.cuda.nvtx.range_pop()
-    clocks = sampler.stop()
-    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    kernels_per_step = ctx.step_kernel_count() + 2
-    if dist:
-        tt = torch.tensor([dev_ms / 1e3, float(graphs)], dtype=torch.float64, device="cuda")
-        tmax = tt[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        gsum = tt[1:].clone()
-        dist.all_reduce(gsum, op=dist.ReduceOp.SUM)
-        t_dev, total_graphs = float(tmax.item()), float(gsum.item())
-    else:
-        t_dev, total_graphs = dev_ms / 1e3, float(graphs)
-    value = total_graphs / t_dev
-    line = {"metric": METRIC, "value": value, "unit": "graphs/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec else "f32", "data": "synthetic",
+    ctx = make_ctx(g, wl, args.precision)
+    r = timed_steps(ctx, wl, args.steps, args.warmup, flush, loss_acc, dist, local)
+    line = {"metric": METRIC, "value": r["value"], "unit": "graphs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * r["dev_s"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "graphs": N_TRAIN, "batch_graphs": BATCH, "hidden": H, "layers": L,
                        "head": "200-200-1", "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "gemms": "BF16 tcgen05, FP32 accumulate; aggregation, scalers, std, pooling, loss FP32"
+                                if args.precision == "bf16" else "FP32 FFMA everywhere",
                        "l2": "256 MB buffer written between steps, outside the per-step CUDA events",
-                       "wall_ms_per_step_incl_flush": 1e3 * wall / args.steps},
-            "clocks": clocks, "gpu_launches": kernels_per_step * args.steps}
-
-    # end to end through the public API from host memory
+                       "wall_ms_per_step_incl_flush": 1e3 * r["wall_s"] / args.steps},
+            "clocks": r["clocks"], "gpu_launches": r["kernels_per_step"] * args.steps}
     if not args.no_e2e:
         try:
-            sh = g.Store(path)          # host-resident twin: collation stages through pinned memory
-            sh.set_targets(y)
-            pinned = torch.zeros(3, dtype=torch.float64).pin_memory()
-            k_e2e = args.steps
-            h2d = 0
-            for k in range(3):
-                i = k % nb
-                ctx.train_step(ctx.collate(sh, order[i * BATCH:(i + 1) * BATCH]), LR, loss_acc)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            n_e2e = 0
-            for k in range(k_e2e):
-                i = (args.warmup + k) % nb
-                ids = order[i * BATCH:(i + 1) * BATCH]
-                b = ctx.collate(sh, ids)
-                ctx.train_step(b, LR, loss_acc)
-                pinned.copy_(loss_acc, non_blocking=True)
-                torch.cuda.current_stream().synchronize()
-                _ = float(pinned[0])
-                n_e2e += b.n_graphs
-                h2d += 16 * (b.n_graphs + 1) + 4 * b.n_graphs + b.n_nodes + 2 * b.n_edges
-            dt = time.perf_counter() - t0
-            line["e2e"] = {"value": n_e2e / dt, "unit": "graphs/s", "h2d_bytes_per_step": h2d / k_e2e,
-                           "d2h_bytes_per_step": 24, "steps": k_e2e,
-                           "path": "gcnn_collate from a host store (pinned staging, one H2D) + gcnn_train_step "
-                                   "+ loss read back each step"}
+            line["e2e"] = e2e_steps(g, ctx, wl, args.steps, loss_acc)
         except Exception as e:  # noqa: BLE001
             line["e2e"] = {"error": repr(e)}
-
-    # kernel-level timing: the same steps eagerly, CUDA events around every launch
     try:
-        ctx.profile(True)
-        ctx.profile_read()
-        n_prof = min(args.steps, 100)
-        flops = 0.0
-        agg_bytes = 0.0
-        for k in range(n_prof):
-            flush.zero_()
-            b = batch_at(args.warmup + k)
-            ctx.train_step(b, LR, loss_acc)
-            flops += gemm_flops(b.n_nodes)
-            agg_bytes += L * agg_fwd_bytes(b.n_nodes, b.n_edges)
-        ph = ctx.profile_read()
-        ctx.profile(False)
-        line["phases_ms_per_step"] = {k: v[0] / n_prof for k, v in ph.items()}
-        gemm_ms = ph["gemm"][0]
-        sm_mhz = 2070.0
-        peak_alu = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-        achieved = flops / (gemm_ms / 1e3) / 1e12
-        line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-                            "frac": achieved / peak_alu, "traffic": None,
-                            "kernel": "sgemm_kernel + splitk_reduce (all dense GEMMs of the step, FP32 FFMA)",
-                            "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived; no measured FP32 peak)"}
-        agg_ms = ph["agg_fwd"][0]
-        hbm, hbm_src = measured_hbm()
-        a_gbs = agg_bytes / (agg_ms / 1e3) / 1e9
-        line["roofline_aggregate"] = {"bound": "hbm", "achieved": a_gbs, "peak": hbm, "unit": "GB/s",
-                                      "frac": a_gbs / hbm, "traffic": None, "peak_source": hbm_src,
-                                      "note": "batch working set fits in L2; the HBM figure needs a >L2 batch"}
+        line.update(kernel_profile(ctx, wl, min(args.steps, 100), args.warmup, flush, loss_acc, args.precision))
     except Exception as e:  # noqa: BLE001
         line["roofline"] = {"error": repr(e)}
-
+    ctx.check()
+    ctx.close()
+    if args.compare != "none" and args.compare != args.precision:
+        c2 = make_ctx(g, wl, args.compare)
+        r2 = timed_steps(c2, wl, args.steps, args.warmup, flush, loss_acc, dist)
+        cmp = {"value": r2["value"], "unit": "graphs/s", "ms_per_step": 1e3 * r2["dev_s"] / args.steps,
+               "precision": args.compare}
+        try:
+            prof = kernel_profile(c2, wl, min(args.steps, 50), args.warmup, flush, loss_acc, args.compare)
+            cmp["roofline"] = prof["roofline"]
+            cmp["phases_ms_per_step"] = prof["phases_ms_per_step"]
+        except Exception as e:  # noqa: BLE001
+            cmp["roofline"] = {"error": repr(e)}
+        c2.check()
+        c2.close()
+        line[f"{args.compare}_path"] = cmp
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             os.environ.setdefault("OMP_NUM_THREADS", str(len(os.sched_getaffinity(0))))
-            line["cpu_baseline"] = oracle_graphs_per_s(path, order, budget_s=args.cpu_seconds)
+            line["cpu_baseline"] = oracle_graphs_per_s(wl.path, wl.order, budget_s=args.cpu_seconds)
         except Exception as e:  # noqa: BLE001
             line["cpu_baseline"] = {"error": repr(e)}
-    ctx.check()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -392,7 +444,10 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="bf16",
+                    help="GEMM precision of the measured path (bf16: tensor cores, FP32 accumulate)")
+    ap.add_argument("--compare", choices=["none", "fp32", "bf16"], default="fp32",
+                    help="also time this path on the same workload (default: the plain FP32 path)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

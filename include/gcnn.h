@@ -71,6 +71,11 @@ extern "C" {
 #define GCNN_PREC_FP32 0    /* FP32 everywhere (SIMT FFMA GEMMs)              */
 #define GCNN_PREC_BF16 1    /* BF16 tensor-core GEMMs, FP32 accumulate        */
 
+/* Row-invariant arithmetic: no split-K in the GEMMs, so each node's and each
+ * graph's results depend only on its own graph, never on its batch-mates
+ * (bit-identical alone and in any batch).  Used by the inference server. */
+#define GCNN_FLAG_ROW_INVARIANT 1
+
 /* Message for the last failing call on this thread (never NULL). */
 const char *gcnn_last_error(void);
 /* Library version, major * 10000 + minor * 100 + patch. */
@@ -120,7 +125,7 @@ typedef struct gcnn_config {
   int32_t recompute;    /* 1: do not keep aggregates in forward; recompute
                            them per layer in backward (saves 5*N*H floats per
                            layer)                                              */
-  int32_t reserved;
+  int32_t flags;        /* GCNN_FLAG_* bits                                    */
   double delta;         /* PNA degree normaliser (gcnn_store_delta)            */
   double std_eps;       /* epsilon inside the std aggregator (1e-5)            */
   double beta1, beta2;  /* Adam moment decays (0.9, 0.999)                     */
@@ -233,6 +238,62 @@ int gcnn_profile_read(gcnn_ctx *ctx, double *ms, int64_t *launches);
 /* Kernels in the CUDA graph of the most recent gcnn_train_step (0 if it ran
  * eagerly); the collation of a batch adds 2 more. */
 int gcnn_step_kernel_count(gcnn_ctx *ctx, int32_t *n);
+
+/* ------------------------------------------------------------------ serving
+ * Inference server for the screening use of the trained model (Sec. 1:
+ * surrogate screening over streaming molecules; Sec. 6).  Requests of any
+ * number of molecules are queued on submit; a scheduler thread packs queued
+ * molecules (splitting requests when needed) into batches of the smallest
+ * node-count bucket that fits, and runs each batch on one of n_slots
+ * in-flight slots -- each with its own CUDA stream, device-resident copy of
+ * the weights and arena, and one captured CUDA graph per bucket -- so that
+ * batches overlap on the device and requests that arrive while others run
+ * are admitted as soon as a slot frees up (continuous batching).  Admission
+ * is by memory: submit returns GCNN_EAGAIN while the queued molecules would
+ * exceed queue_nodes.  Slots use GCNN_FLAG_ROW_INVARIANT, so a molecule's
+ * prediction is bit-identical alone and in any mix.
+ */
+typedef struct gcnn_server gcnn_server;
+
+typedef struct gcnn_serve_config {
+  int32_t n_slots;            /* batches in flight (1..16)                       */
+  int32_t n_buckets;          /* node-count buckets (1..8)                       */
+  int32_t bucket_nodes[8];    /* ascending node capacities, e.g. 1k,4k,16k,64k   */
+  int32_t max_graphs;         /* molecules per batch                             */
+  int32_t precision;          /* GCNN_PREC_FP32 or GCNN_PREC_BF16                */
+  int64_t queue_nodes;        /* admission limit: atoms queued and not started   */
+} gcnn_serve_config;
+
+typedef struct gcnn_request {
+  int32_t n_mol;              /* molecules in the request                        */
+  int32_t reserved;
+  const int32_t *n_nodes;     /* (host) [n_mol] atoms per molecule (1..255)      */
+  const int32_t *n_edges;     /* (host) [n_mol] directed edges per molecule      */
+  const uint8_t *types;       /* (host) atom types, molecules concatenated       */
+  const uint8_t *edges;       /* (host) local (src, dst) pairs, concatenated;
+                                 each bond stored in both directions             */
+} gcnn_request;
+
+/* Create a server for the model in `model` (its current parameters are copied
+ * to every slot; later changes to `model` are not seen).  Starts the
+ * scheduler thread. */
+int gcnn_serve_create(const gcnn_ctx *model, const gcnn_serve_config *cfg, gcnn_server **out);
+/* Queue a request (the library copies it; the caller may free it on return).
+ * GCNN_EAGAIN: admission refused (queue full), retry later. */
+int gcnn_serve_submit(gcnn_server *srv, const gcnn_request *req, uint64_t *ticket);
+/* Non-blocking: GCNN_EAGAIN until every molecule of the request is done;
+ * then writes n_mol predictions to out (host), the latency from submit to
+ * completion in microseconds to latency_us (may be NULL), and forgets the
+ * ticket. */
+int gcnn_serve_poll(gcnn_server *srv, uint64_t ticket, float *out, double *latency_us);
+/* Blocking variant with a timeout (GCNN_ETIMEDOUT when it expires). */
+int gcnn_serve_wait(gcnn_server *srv, uint64_t ticket, float *out, double *latency_us, int64_t timeout_us);
+/* Counters since creation: requests done, molecules done, batches run,
+ * submissions refused. */
+int gcnn_serve_stats(gcnn_server *srv, int64_t *requests, int64_t *molecules, int64_t *batches,
+                     int64_t *refused);
+/* Stop the scheduler (finishing batches in flight) and free everything. */
+int gcnn_serve_destroy(gcnn_server *srv);
 
 /* ------------------------------------------------------------------ operators
  * Single steps of the path on caller-owned device buffers, for composing the

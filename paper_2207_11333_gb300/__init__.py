@@ -36,7 +36,7 @@ class Config(ctypes.Structure):
     _fields_ = [("hidden", ctypes.c_int32), ("layers", ctypes.c_int32), ("n_types", ctypes.c_int32),
                 ("head_hidden", ctypes.c_int32), ("max_graphs", ctypes.c_int32), ("max_nodes", ctypes.c_int32),
                 ("max_edges", ctypes.c_int32), ("precision", ctypes.c_int32), ("recompute", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("delta", ctypes.c_double), ("std_eps", ctypes.c_double),
+                ("flags", ctypes.c_int32), ("delta", ctypes.c_double), ("std_eps", ctypes.c_double),
                 ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("adam_eps", ctypes.c_double),
                 ("weight_decay", ctypes.c_double)]
 
@@ -45,6 +45,16 @@ class BatchStruct(ctypes.Structure):
     _fields_ = [("n_graphs", ctypes.c_int32), ("n_nodes", ctypes.c_int32), ("n_edges", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)] + [(n, ctypes.c_void_p) for n in (
                     "node_off", "edge_off", "graph_id", "row_ptr", "col", "rev", "deg", "amp", "att", "types", "y")]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int32), ("n_buckets", ctypes.c_int32), ("bucket_nodes", ctypes.c_int32 * 8),
+                ("max_graphs", ctypes.c_int32), ("precision", ctypes.c_int32), ("queue_nodes", ctypes.c_int64)]
+
+
+class RequestStruct(ctypes.Structure):
+    _fields_ = [("n_mol", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n_nodes", ctypes.c_void_p),
+                ("n_edges", ctypes.c_void_p), ("types", ctypes.c_void_p), ("edges", ctypes.c_void_p)]
 
 
 def _load() -> ctypes.CDLL:
@@ -87,6 +97,12 @@ def _load() -> ctypes.CDLL:
         "gcnn_profile_enable": (i32, [vp, i32]),
         "gcnn_profile_read": (i32, [vp, vp, vp]),
         "gcnn_step_kernel_count": (i32, [vp, P(i32)]),
+        "gcnn_serve_create": (i32, [vp, P(ServeConfig), P(vp)]),
+        "gcnn_serve_submit": (i32, [vp, P(RequestStruct), P(ctypes.c_uint64)]),
+        "gcnn_serve_poll": (i32, [vp, ctypes.c_uint64, vp, P(f64)]),
+        "gcnn_serve_wait": (i32, [vp, ctypes.c_uint64, vp, P(f64), i64]),
+        "gcnn_serve_stats": (i32, [vp, P(i64), P(i64), P(i64), P(i64)]),
+        "gcnn_serve_destroy": (i32, [vp]),
         "gcnn_op_aggregate_fwd": (i32, [i32, i32, vp, vp, vp, vp, f32, vp]),
         "gcnn_op_aggregate_bwd": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, f32, vp]),
         "gcnn_op_aggregate_bwd_noalloc": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, f32, vp]),
@@ -398,3 +414,79 @@ def pool_bwd(dpooled, node_off, graph_id, n_nodes: int, stream=None):
     _check(lib.gcnn_op_pool_bwd(G, n_nodes, H, _dev_ptr(node_off, torch.int32), _dev_ptr(graph_id, torch.int32),
                                 _dev_ptr(dpooled.contiguous(), torch.float32), _dev_ptr(dx), _stream(stream)))
     return dx
+
+
+# ---------------------------------------------------------------- serving
+
+class Server:
+    """Continuous-batching inference server (gcnn_serve_*) over a trained Context."""
+
+    def __init__(self, model: Context, n_slots: int = 4, buckets=(1024, 4096, 16384, 65536), max_graphs: int = 4096,
+                 precision: int = PREC_FP32, queue_nodes: int = 1 << 22):
+        cfg = ServeConfig()
+        cfg.n_slots, cfg.n_buckets, cfg.max_graphs = n_slots, len(buckets), max_graphs
+        for i, b in enumerate(buckets):
+            cfg.bucket_nodes[i] = b
+        cfg.precision, cfg.queue_nodes = precision, queue_nodes
+        self._h = ctypes.c_void_p()
+        _check(lib.gcnn_serve_create(model._h, ctypes.byref(cfg), ctypes.byref(self._h)))
+        self._n = {}
+
+    def submit(self, n_nodes, n_edges, types, edges):
+        """Queue one request; returns a ticket, or None when admission is refused (queue full)."""
+        nn = np.ascontiguousarray(n_nodes, np.int32)
+        ne = np.ascontiguousarray(n_edges, np.int32)
+        ty = np.ascontiguousarray(types, np.uint8)
+        ed = np.ascontiguousarray(edges, np.uint8).reshape(-1)
+        q = RequestStruct(len(nn), 0, _np_ptr(nn), _np_ptr(ne), _np_ptr(ty), _np_ptr(ed) if ed.size else _np_ptr(ty))
+        t = ctypes.c_uint64()
+        rc = lib.gcnn_serve_submit(self._h, ctypes.byref(q), ctypes.byref(t))
+        if rc == -7:
+            return None
+        _check(rc)
+        self._n[t.value] = len(nn)
+        return t.value
+
+    def poll(self, ticket: int):
+        """(predictions, latency_us) when done, else None."""
+        out = np.empty(self._n[ticket], np.float32)
+        lat = ctypes.c_double()
+        rc = lib.gcnn_serve_poll(self._h, ticket, _np_ptr(out), ctypes.byref(lat))
+        if rc == -7:
+            return None
+        del self._n[ticket]
+        _check(rc)
+        return out, lat.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0):
+        out = np.empty(self._n[ticket], np.float32)
+        lat = ctypes.c_double()
+        rc = lib.gcnn_serve_wait(self._h, ticket, _np_ptr(out), ctypes.byref(lat), int(timeout_s * 1e6))
+        if rc != -6:
+            del self._n[ticket]
+        _check(rc)
+        return out, lat.value
+
+    def stats(self) -> dict:
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(lib.gcnn_serve_stats(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("requests", "molecules", "batches", "refused"), (x.value for x in v)))
+
+    def close(self) -> None:
+        if self._h:
+            _check(lib.gcnn_serve_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def request_arrays(gs, first: int, count: int):
+    """(n_nodes, n_edges, types, edges) of graphs first..first+count-1 of a synth.GraphSet."""
+    a, b = gs.node_ptr[first], gs.node_ptr[first + count]
+    c, d = gs.edge_ptr[first], gs.edge_ptr[first + count]
+    return (np.diff(gs.node_ptr[first:first + count + 1]).astype(np.int32),
+            np.diff(gs.edge_ptr[first:first + count + 1]).astype(np.int32), gs.types[a:b], gs.edges[c:d])

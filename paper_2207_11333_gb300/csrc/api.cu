@@ -257,6 +257,7 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   c->dH = (float *)(b + o_dH); c->dX = (float *)(b + o_dX); c->dagg = (float *)(b + o_dagg);
   c->dPQ = (float *)(b + o_dPQ); c->dm = (float *)(b + o_dm); c->emb_partial = (float *)(b + o_embp);
   c->ws.partial = (float *)(b + o_ws); c->ws.floats = wsf;
+  c->ws.max_splits = (cfg->flags & GCNN_FLAG_ROW_INVARIANT) ? 1 : 32;
   if (bf) {
     c->wb = (uint16_t *)(b + o_wb); c->xb = (uint16_t *)(b + o_xb); c->sb = (uint16_t *)(b + o_sb);
     c->d3[0] = (uint16_t *)(b + o_d30); c->d3[1] = (uint16_t *)(b + o_d31); c->pqb = (uint16_t *)(b + o_pqb);

@@ -323,7 +323,7 @@ int run_gemm_simt(const GemmDesc &d, DevDims dims, const GemmWorkspace &ws, cuda
     return set_error(GCNN_EINVAL, "gemm: bad operand segments (alignment / order)");
   for (int q = 0; q < d.B.nseg; ++q)
     if (!d.B.seg[q].ptr) return set_error(GCNN_EINVAL, "gemm: B segments need data");
-  int splits = choose_splits(d.M, d.N, d.K);
+  int splits = std::min(choose_splits(d.M, d.N, d.K), ws.max_splits);
   if (splits > 1 && (size_t)splits * d.M * d.N > ws.floats) splits = 1;
   int kps = (int)(ceil_div(d.K, (long long)splits * BK) * BK);
   if (kps == 0) kps = BK;

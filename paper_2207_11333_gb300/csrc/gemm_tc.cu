@@ -446,6 +446,7 @@ int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
   }
   int BN, ntiles, splits;
   const int ktiles = choose(d.M, d.N, d.K, &BN, &ntiles, &splits);
+  splits = std::min(splits, ws.max_splits);
   if (splits > 1 && (size_t)splits * d.M * d.N > ws.floats) splits = 1;
   const int kps = (ktiles + splits - 1) / splits * BK;
   dim3 grid(ntiles, (d.M + BM - 1) / BM, splits);

@@ -112,8 +112,9 @@ struct GemmDesc {
 };
 
 struct GemmWorkspace {
-  float *partial;   // split-K partial sums
-  size_t floats;    // capacity
+  float *partial;      // split-K partial sums
+  size_t floats;       // capacity
+  int max_splits = 32; // 1: row-invariant (no split-K)
 };
 
 int run_gemm_simt(const GemmDesc &d, DevDims dims, const GemmWorkspace &ws, cudaStream_t s);

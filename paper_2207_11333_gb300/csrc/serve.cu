@@ -1,0 +1,460 @@
+// Inference server: continuous batching of screening requests (Sec. 1 and
+// Sec. 6: the trained GCNN as a fast surrogate over streams of molecules).
+//
+// submit() validates and copies a request into host memory and queues it;
+// admission is refused (GCNN_EAGAIN) while the atoms waiting to start would
+// exceed queue_nodes.  One scheduler thread loops over the slots:
+//   - a busy slot whose completion event fired is retired: its predictions
+//     (pinned memory) are scattered to their requests, finished requests are
+//     stamped and waiters woken;
+//   - a free slot takes queued molecules in FIFO order (splitting requests
+//     across batches) up to the largest bucket and the slot's molecule and
+//     edge capacities, picks the smallest bucket that fits, writes the batch
+//     as a packed mini-store into pinned memory, and enqueues on its own
+//     stream: one host-to-device copy, the device collator, the captured
+//     forward graph of that bucket, and one device-to-host copy of the
+//     predictions, followed by its completion event.
+// Slots run with GCNN_FLAG_ROW_INVARIANT, so results do not depend on which
+// molecules share a batch.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "context.h"
+
+using namespace gcnn;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+struct Request {
+  uint64_t ticket = 0;
+  int n_mol = 0;
+  std::vector<int32_t> n_nodes, n_edges;
+  std::vector<int64_t> node_off, edge_off;  // prefix sums into types / edges
+  std::vector<uint8_t> types, edges;
+  std::vector<float> out;
+  int next = 0;          // first molecule not yet placed in a batch
+  int remaining = 0;     // molecules not yet finished
+  int status = GCNN_OK;  // sticky failure
+  bool done = false;
+  Clock::time_point t_submit, t_done;
+};
+
+struct Piece {
+  Request *r;
+  int first, count;
+};
+
+struct Slot {
+  gcnn_ctx *ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  float *pin_out = nullptr;
+  bool busy = false;
+  std::vector<Piece> pieces;
+  int graphs = 0;
+  std::vector<cudaGraphExec_t> exec;  // per bucket, captured lazily
+};
+
+}  // namespace
+
+struct gcnn_server {
+  gcnn_serve_config cfg{};
+  std::vector<Slot> slots;
+  int max_edges = 0;
+  std::mutex mu;
+  std::condition_variable work_cv, done_cv;
+  std::deque<Request *> pending;
+  std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+  uint64_t next_ticket = 1;
+  int64_t queued_nodes = 0;
+  std::atomic<bool> stop{false};
+  int fatal = GCNN_OK;
+  char fatal_msg[256] = "";
+  int64_t n_requests = 0, n_molecules = 0, n_batches = 0, n_refused = 0;
+  std::thread worker;
+  int device = 0;
+};
+
+namespace {
+
+size_t align16(size_t v) { return (v + 15) / 16 * 16; }
+
+int capture_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, cudaGraphExec_t *out) {
+  cudaGraph_t graph = nullptr;
+  cudaStream_t user = c->stream;
+  c->stream = c->cap_stream;
+  c->capturing = true;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  int rc = e == cudaSuccess ? ctx_forward(c, G, Ngrid, Egrid, false)
+                            : set_error(GCNN_ECUDA, "begin capture: %s", cudaGetErrorString(e));
+  if (e == cudaSuccess) {
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+    if (rc == GCNN_OK && e2 != cudaSuccess) rc = set_error(GCNN_ECUDA, "end capture: %s", cudaGetErrorString(e2));
+  }
+  c->stream = user;
+  c->capturing = false;
+  if (rc == GCNN_OK) {
+    e = cudaGraphInstantiate(out, graph, 0);
+    if (e != cudaSuccess) rc = set_error(GCNN_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  if (graph) cudaGraphDestroy(graph);
+  return rc;
+}
+
+void fail_all(gcnn_server *s, int code) {
+  // caller holds s->mu
+  for (auto &kv : s->reqs) {
+    Request *r = kv.second.get();
+    if (!r->done) {
+      r->status = code;
+      r->done = true;
+      r->t_done = Clock::now();
+    }
+  }
+  s->pending.clear();
+  s->done_cv.notify_all();
+}
+
+// Take molecules for one batch from the queue (caller holds s->mu).
+void form_batch(gcnn_server *s, Slot &sl, int64_t *nodes, int64_t *edges) {
+  const int64_t cap_nodes = s->cfg.bucket_nodes[s->cfg.n_buckets - 1];
+  int64_t N = 0, E = 0;
+  int G = 0;
+  sl.pieces.clear();
+  while (!s->pending.empty() && G < s->cfg.max_graphs) {
+    Request *r = s->pending.front();
+    int take = 0;
+    while (r->next + take < r->n_mol && G + take < s->cfg.max_graphs) {
+      const int m = r->next + take;
+      if (N + r->n_nodes[m] > cap_nodes || E + r->n_edges[m] > s->max_edges) break;
+      N += r->n_nodes[m];
+      E += r->n_edges[m];
+      ++take;
+    }
+    if (take == 0) break;
+    sl.pieces.push_back(Piece{r, r->next, take});
+    for (int m = r->next; m < r->next + take; ++m) s->queued_nodes -= r->n_nodes[m];
+    r->next += take;
+    G += take;
+    if (r->next == r->n_mol) s->pending.pop_front();
+    else break;  // batch full
+  }
+  sl.graphs = G;
+  *nodes = N;
+  *edges = E;
+}
+
+int launch_batch(gcnn_server *s, Slot &sl, int64_t N, int64_t E) {
+  gcnn_ctx *c = sl.ctx;
+  const int G = sl.graphs;
+  int b = 0;
+  while (b < s->cfg.n_buckets - 1 && s->cfg.bucket_nodes[b] < N) ++b;
+  const int Ng = s->cfg.bucket_nodes[b];
+  // packed mini-store in the slot context's pinned staging buffer (free: the
+  // slot's previous batch has completed)
+  char *h = c->stage_host[0];
+  size_t o = 0;
+  const size_t o_np = o; o = align16(o + 8 * (size_t)(G + 1));
+  const size_t o_ep = o; o = align16(o + 8 * (size_t)(G + 1));
+  const size_t o_y = o;  o = align16(o + 4 * (size_t)G);
+  const size_t o_t = o;  o = align16(o + (size_t)N);
+  const size_t o_e = o;  o = align16(o + 2 * (size_t)E);
+  if (o > c->stage_bytes) return set_error(GCNN_EINVAL, "serve: staging too small");
+  int64_t *np = reinterpret_cast<int64_t *>(h + o_np), *ep = reinterpret_cast<int64_t *>(h + o_ep);
+  float *y = reinterpret_cast<float *>(h + o_y);
+  uint8_t *ty = reinterpret_cast<uint8_t *>(h + o_t), *ed = reinterpret_cast<uint8_t *>(h + o_e);
+  np[0] = 0;
+  ep[0] = 0;
+  int g = 0;
+  for (const Piece &p : sl.pieces) {
+    const Request *r = p.r;
+    for (int m = p.first; m < p.first + p.count; ++m, ++g) {
+      memcpy(ty + np[g], r->types.data() + r->node_off[m], (size_t)r->n_nodes[m]);
+      memcpy(ed + 2 * ep[g], r->edges.data() + 2 * r->edge_off[m], 2 * (size_t)r->n_edges[m]);
+      y[g] = 0.f;
+      np[g + 1] = np[g] + r->n_nodes[m];
+      ep[g + 1] = ep[g] + r->n_edges[m];
+    }
+  }
+  GCNN_CUDA_TRY(cudaMemcpyAsync(c->stage_dev, h, o, cudaMemcpyHostToDevice, sl.stream));
+  const char *d = c->stage_dev;
+  StoreView v{reinterpret_cast<const int64_t *>(d + o_np), reinterpret_cast<const int64_t *>(d + o_ep),
+              reinterpret_cast<const uint8_t *>(d + o_t), reinterpret_cast<const uint8_t *>(d + o_e),
+              reinterpret_cast<const float *>(d + o_y)};
+  GCNN_TRY(launch_collate(G, nullptr, v, c->bb, c->scal_tab, c->Nc, c->Ec, c->err, sl.stream));
+  if (!sl.exec[b]) {
+    const int Eg = std::min(c->Ec, (int)((int64_t)Ng * s->max_edges / s->cfg.bucket_nodes[s->cfg.n_buckets - 1] + 512));
+    GCNN_TRY(capture_forward(c, s->cfg.max_graphs, Ng, std::max(Eg, 512), &sl.exec[b]));
+  }
+  GCNN_CUDA_TRY(cudaGraphLaunch(sl.exec[b], sl.stream));
+  GCNN_CUDA_TRY(cudaMemcpyAsync(sl.pin_out, c->pred, sizeof(float) * G, cudaMemcpyDeviceToHost, sl.stream));
+  GCNN_CUDA_TRY(cudaEventRecord(sl.done, sl.stream));
+  sl.busy = true;
+  return GCNN_OK;
+}
+
+void retire(gcnn_server *s, Slot &sl) {
+  // caller holds s->mu
+  int g = 0;
+  const auto now = Clock::now();
+  for (const Piece &p : sl.pieces) {
+    Request *r = p.r;
+    for (int m = p.first; m < p.first + p.count; ++m, ++g) r->out[m] = sl.pin_out[g];
+    r->remaining -= p.count;
+    s->n_molecules += p.count;
+    if (r->remaining == 0 && !r->done) {
+      r->done = true;
+      r->t_done = now;
+      s->n_requests += 1;
+    }
+  }
+  sl.pieces.clear();
+  sl.busy = false;
+  s->n_batches += 1;
+  s->done_cv.notify_all();
+}
+
+void worker_loop(gcnn_server *s) {
+  cudaSetDevice(s->device);
+  for (;;) {
+    bool progressed = false;
+    for (Slot &sl : s->slots) {
+      if (!sl.busy) continue;
+      const cudaError_t q = cudaEventQuery(sl.done);
+      if (q == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(s->mu);
+        retire(s, sl);
+        progressed = true;
+      } else if (q != cudaErrorNotReady) {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->fatal = GCNN_ECUDA;
+        snprintf(s->fatal_msg, sizeof(s->fatal_msg), "serve: batch failed: %s", cudaGetErrorString(q));
+        fail_all(s, GCNN_ECUDA);
+        sl.busy = false;
+      }
+    }
+    for (Slot &sl : s->slots) {
+      if (sl.busy) continue;
+      int64_t N = 0, E = 0;
+      {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->fatal != GCNN_OK || s->pending.empty()) break;
+        form_batch(s, sl, &N, &E);
+      }
+      if (sl.graphs == 0) break;
+      const int rc = launch_batch(s, sl, N, E);
+      progressed = true;
+      if (rc != GCNN_OK) {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->fatal = rc;
+        snprintf(s->fatal_msg, sizeof(s->fatal_msg), "%s", gcnn_last_error());
+        fail_all(s, rc);
+      }
+    }
+    bool any_busy = false;
+    for (Slot &sl : s->slots) any_busy |= sl.busy;
+    if (s->stop.load() && !any_busy) break;
+    if (!progressed) {
+      if (any_busy) {
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+      } else {
+        std::unique_lock<std::mutex> lock(s->mu);
+        s->work_cv.wait_for(lock, std::chrono::milliseconds(2),
+                            [s] { return s->stop.load() || (!s->pending.empty() && s->fatal == GCNN_OK); });
+      }
+    }
+  }
+}
+
+int validate(const gcnn_server *s, const gcnn_request *q, int64_t *nodes) {
+  if (!q || q->n_mol < 1 || !q->n_nodes || !q->n_edges || !q->types || !q->edges)
+    return set_error(GCNN_EINVAL, "serve_submit: empty or null request");
+  if (q->n_mol > (1 << 24)) return set_error(GCNN_EINVAL, "serve_submit: too many molecules");
+  int64_t nn = 0, ne = 0;
+  for (int m = 0; m < q->n_mol; ++m) {
+    if (q->n_nodes[m] < 1 || q->n_nodes[m] > kMaxGraphNodes || q->n_edges[m] < 0 ||
+        q->n_edges[m] > kMaxGraphEdges || q->n_edges[m] > s->max_edges)
+      return set_error(GCNN_EINVAL, "serve_submit: molecule %d has %d atoms / %d edges (1..%d / 0..%d)", m,
+                       q->n_nodes[m], q->n_edges[m], kMaxGraphNodes, kMaxGraphEdges);
+    for (int v = 0; v < q->n_nodes[m]; ++v)
+      if (q->types[nn + v] >= s->slots[0].ctx->T)
+        return set_error(GCNN_EINVAL, "serve_submit: molecule %d has an atom type out of range", m);
+    for (int k = 0; k < q->n_edges[m]; ++k) {
+      const uint8_t *e = q->edges + 2 * (ne + k);
+      if (e[0] >= q->n_nodes[m] || e[1] >= q->n_nodes[m])
+        return set_error(GCNN_EINVAL, "serve_submit: molecule %d has an edge to a missing atom", m);
+    }
+    nn += q->n_nodes[m];
+    ne += q->n_edges[m];
+  }
+  *nodes = nn;
+  return GCNN_OK;
+}
+
+void destroy_server(gcnn_server *s) {
+  for (Slot &sl : s->slots) {
+    for (auto e : sl.exec)
+      if (e) cudaGraphExecDestroy(e);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.pin_out) cudaFreeHost(sl.pin_out);
+    if (sl.ctx) gcnn_destroy(sl.ctx);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+  }
+  delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gcnn_serve_create(const gcnn_ctx *model, const gcnn_serve_config *cfg, gcnn_server **out) {
+  if (!model || !cfg || !out) return set_error(GCNN_EINVAL, "serve_create: null argument");
+  *out = nullptr;
+  if (cfg->n_slots < 1 || cfg->n_slots > 16 || cfg->n_buckets < 1 || cfg->n_buckets > 8 || cfg->max_graphs < 1 ||
+      cfg->queue_nodes < 1 || (cfg->precision != GCNN_PREC_FP32 && cfg->precision != GCNN_PREC_BF16))
+    return set_error(GCNN_EINVAL, "serve_create: bad configuration");
+  for (int b = 0; b < cfg->n_buckets; ++b)
+    if (cfg->bucket_nodes[b] < kMaxGraphNodes || (b > 0 && cfg->bucket_nodes[b] <= cfg->bucket_nodes[b - 1]))
+      return set_error(GCNN_EINVAL, "serve_create: buckets must ascend and hold at least %d atoms", kMaxGraphNodes);
+  gcnn_server *s = new gcnn_server();
+  s->cfg = *cfg;
+  cudaGetDevice(&s->device);
+  const int max_nodes = cfg->bucket_nodes[cfg->n_buckets - 1];
+  s->max_edges = (int)std::min<int64_t>((int64_t)max_nodes * 4 + kMaxGraphEdges, (int64_t)1 << 30);
+  gcnn_config sc = model->cfg;
+  sc.max_graphs = cfg->max_graphs;
+  sc.max_nodes = max_nodes;
+  sc.max_edges = s->max_edges;
+  sc.precision = cfg->precision;
+  sc.recompute = 1;  // inference: one aggregate buffer is enough
+  sc.flags |= GCNN_FLAG_ROW_INVARIANT;
+  s->slots.resize(cfg->n_slots);
+  int rc = GCNN_OK;
+  for (Slot &sl : s->slots) {
+    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost(&sl.pin_out, sizeof(float) * cfg->max_graphs) != cudaSuccess) {
+      rc = set_error(GCNN_ENOMEM, "serve_create: stream / event / pinned allocation failed");
+      break;
+    }
+    rc = gcnn_create(&sc, sl.stream, &sl.ctx);
+    if (rc != GCNN_OK) break;
+    rc = gcnn_set_params(sl.ctx, model->params, model->P, 1);
+    if (rc != GCNN_OK) break;
+    sl.exec.assign(cfg->n_buckets, nullptr);
+  }
+  if (rc != GCNN_OK) {
+    destroy_server(s);
+    return rc;
+  }
+  s->worker = std::thread(worker_loop, s);
+  *out = s;
+  return GCNN_OK;
+}
+
+int gcnn_serve_submit(gcnn_server *s, const gcnn_request *q, uint64_t *ticket) {
+  if (!s || !ticket) return set_error(GCNN_EINVAL, "serve_submit: null argument");
+  int64_t nodes = 0;
+  GCNN_TRY(validate(s, q, &nodes));
+  if (nodes > s->cfg.queue_nodes)
+    return set_error(GCNN_EINVAL, "serve_submit: request of %lld atoms exceeds queue_nodes", (long long)nodes);
+  auto r = std::make_unique<Request>();
+  r->n_mol = q->n_mol;
+  r->n_nodes.assign(q->n_nodes, q->n_nodes + q->n_mol);
+  r->n_edges.assign(q->n_edges, q->n_edges + q->n_mol);
+  r->node_off.resize(q->n_mol);
+  r->edge_off.resize(q->n_mol);
+  int64_t nn = 0, ne = 0;
+  for (int m = 0; m < q->n_mol; ++m) {
+    r->node_off[m] = nn;
+    r->edge_off[m] = ne;
+    nn += q->n_nodes[m];
+    ne += q->n_edges[m];
+  }
+  r->types.assign(q->types, q->types + nn);
+  r->edges.assign(q->edges, q->edges + 2 * ne);
+  r->out.assign(q->n_mol, 0.f);
+  r->remaining = q->n_mol;
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->fatal != GCNN_OK) return set_error(s->fatal, "%s", s->fatal_msg);
+    if (s->stop.load()) return set_error(GCNN_ESTATE, "serve_submit: server is stopping");
+    if (s->queued_nodes + nodes > s->cfg.queue_nodes) {
+      s->n_refused += 1;
+      return set_error(GCNN_EAGAIN, "serve_submit: queue full (%lld atoms waiting)", (long long)s->queued_nodes);
+    }
+    r->ticket = s->next_ticket++;
+    *ticket = r->ticket;
+    s->queued_nodes += nodes;
+    s->pending.push_back(r.get());
+    s->reqs.emplace(r->ticket, std::move(r));
+  }
+  s->work_cv.notify_one();
+  return GCNN_OK;
+}
+
+static int take_result(gcnn_server *s, std::unordered_map<uint64_t, std::unique_ptr<Request>>::iterator it, float *out,
+                       double *latency_us) {
+  Request *r = it->second.get();
+  const int st = r->status;
+  if (st == GCNN_OK && out) memcpy(out, r->out.data(), sizeof(float) * r->n_mol);
+  if (latency_us) latency_us[0] = std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count();
+  s->reqs.erase(it);
+  return st == GCNN_OK ? GCNN_OK : set_error(st, "serve: request failed: %s", s->fatal_msg);
+}
+
+int gcnn_serve_poll(gcnn_server *s, uint64_t ticket, float *out, double *latency_us) {
+  if (!s) return set_error(GCNN_EINVAL, "serve_poll: null server");
+  std::lock_guard<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return set_error(GCNN_EINVAL, "serve_poll: unknown ticket %llu", (unsigned long long)ticket);
+  if (!it->second->done) return set_error(GCNN_EAGAIN, "serve_poll: not ready");
+  return take_result(s, it, out, latency_us);
+}
+
+int gcnn_serve_wait(gcnn_server *s, uint64_t ticket, float *out, double *latency_us, int64_t timeout_us) {
+  if (!s) return set_error(GCNN_EINVAL, "serve_wait: null server");
+  std::unique_lock<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return set_error(GCNN_EINVAL, "serve_wait: unknown ticket %llu", (unsigned long long)ticket);
+  Request *r = it->second.get();
+  if (!s->done_cv.wait_for(lock, std::chrono::microseconds(std::max<int64_t>(timeout_us, 0)), [r] { return r->done; }))
+    return set_error(GCNN_ETIMEDOUT, "serve_wait: timed out");
+  return take_result(s, s->reqs.find(ticket), out, latency_us);
+}
+
+int gcnn_serve_stats(gcnn_server *s, int64_t *requests, int64_t *molecules, int64_t *batches, int64_t *refused) {
+  if (!s) return set_error(GCNN_EINVAL, "serve_stats: null server");
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (requests) *requests = s->n_requests;
+  if (molecules) *molecules = s->n_molecules;
+  if (batches) *batches = s->n_batches;
+  if (refused) *refused = s->n_refused;
+  return GCNN_OK;
+}
+
+int gcnn_serve_destroy(gcnn_server *s) {
+  if (!s) return GCNN_OK;
+  s->stop.store(true);
+  s->work_cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    fail_all(s, GCNN_ESTATE);
+  }
+  destroy_server(s);
+  return GCNN_OK;
+}
+
+}  // extern "C"
