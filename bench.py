@@ -368,6 +368,121 @@ def e2e_steps(g, ctx, wl, steps, loss_acc):
                                     "+ loss read back each step"}
 
 
+# ------------------------------------------------------------------ serving
+SERVE_POOL, SEED_SERVE = 100_000, 30
+
+
+def arrival_schedule(lam: float, seconds: float, n_pool: int, seed: int):
+    """Poisson arrivals at rate lam for `seconds`; request sizes log-uniform in 1..4096 molecules."""
+    rng = np.random.default_rng(seed)
+    n = max(1, int(lam * seconds))
+    t = np.cumsum(rng.exponential(1.0 / lam, n))
+    size = np.clip(np.floor(np.exp(rng.uniform(0.0, np.log(4097.0), n))), 1, 4096).astype(np.int64)
+    start = rng.integers(0, n_pool - 4096, n)
+    keep = t <= seconds
+    return t[keep], size[keep], start[keep]
+
+
+def summarize(lat_us, molecules, elapsed, offered, refused, lam):
+    lat = np.sort(np.asarray(lat_us, np.float64)) / 1e3
+    pct = (lambda q: float(lat[min(len(lat) - 1, int(q * len(lat)))]) if len(lat) else None)
+    return {"lambda_req_s": lam, "requests_done": len(lat), "requests_offered": offered, "refused": refused,
+            "served_graphs_per_s": molecules / elapsed if elapsed > 0 else 0.0, "p50_ms": pct(0.50),
+            "p99_ms": pct(0.99), "elapsed_s": elapsed}
+
+
+def serve_rates(g, model_ctx, pool, rates, seconds, precision):
+    """Continuous-batching server under Poisson load."""
+    prec = g.PREC_BF16 if precision == "bf16" else g.PREC_FP32
+    srv = g.Server(model_ctx, n_slots=4, buckets=(1024, 4096, 16384, 65536), max_graphs=4096, precision=prec,
+                   queue_nodes=1 << 22)
+    warm = srv.submit(*g.request_arrays(pool, 0, 4096))   # captures the bucket graphs
+    srv.wait(warm)
+    for b in (1, 60, 300):
+        srv.wait(srv.submit(*g.request_arrays(pool, 0, b)))
+    out = []
+    for r_i, lam in enumerate(rates):
+        t_arr, size, start = arrival_schedule(lam, seconds, pool.n_graphs, SEED_SERVE + r_i)
+        pending, lat, mols, refused = [], [], 0, 0
+        i = 0
+        t0 = time.perf_counter()
+        while i < len(t_arr) or pending:
+            now = time.perf_counter() - t0
+            while i < len(t_arr) and t_arr[i] <= now:
+                t = srv.submit(*g.request_arrays(pool, int(start[i]), int(size[i])))
+                if t is None:
+                    refused += 1
+                else:
+                    pending.append((t, int(size[i])))
+                i += 1
+            still = []
+            for t, n in pending:
+                r = srv.poll(t)
+                if r is None:
+                    still.append((t, n))
+                else:
+                    lat.append(r[1])
+                    mols += n
+            pending = still
+            if now > seconds + max(5.0, seconds):   # bounded drain
+                break
+            if not still and i < len(t_arr):
+                time.sleep(max(0.0, min(0.001, t_arr[i] - (time.perf_counter() - t0))))
+        elapsed = time.perf_counter() - t0
+        out.append(summarize(lat, mols, elapsed, len(t_arr), refused, lam))
+    stats = srv.stats()
+    srv.close()
+    return out, stats
+
+
+def baseline_rates(g, params, delta, pool_path, pool, rates, seconds):
+    """Plain FP32 path, one request per launch in arrival order (collate from host + forward + read back)."""
+    import torch
+    n_max = 4096 * 80
+    ctx = g.Context(g.make_config(H, L, 4096, n_max, 4 * n_max + 1024, delta=delta))
+    ctx.set_params(params)
+    st = g.Store(pool_path)
+    pred = torch.empty(4096, device="cuda")
+    host = torch.empty(4096, dtype=torch.float32).pin_memory()
+    out = []
+    for r_i, lam in enumerate(rates):
+        t_arr, size, start = arrival_schedule(lam, seconds, pool.n_graphs, SEED_SERVE + r_i)
+        lat, mols = [], 0
+        t0 = time.perf_counter()
+        for i in range(len(t_arr)):
+            now = time.perf_counter() - t0
+            if now < t_arr[i]:
+                time.sleep(t_arr[i] - now)
+            if time.perf_counter() - t0 > seconds + max(5.0, seconds):   # bounded drain
+                break
+            n = int(size[i])
+            b = ctx.collate(st, np.arange(start[i], start[i] + n))
+            ctx.forward(b, pred, train=False)
+            host[:n].copy_(pred[:n], non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            lat.append(1e6 * (time.perf_counter() - t0 - t_arr[i]))
+            mols += n
+        elapsed = time.perf_counter() - t0
+        out.append(summarize(lat, mols, elapsed, len(t_arr), 0, lam))
+    ctx.close()
+    return out
+
+
+def run_serving(g, model_ctx, delta, params, args):
+    pool = synth.molecules_uniform(SEED_SERVE, SERVE_POOL, 5, 80)
+    tmp = tempfile.mkdtemp(prefix="gcnn_serve_")
+    path = os.path.join(tmp, "pool.gcnn")
+    synth.write_store(path, pool)
+    rates = [float(x) for x in args.serve_rates.split(",")]
+    res, stats = serve_rates(g, model_ctx, pool, rates, args.serve_seconds, args.precision)
+    base = baseline_rates(g, params, delta, path, pool, rates, args.serve_seconds)
+    return {"workload": "Poisson arrivals; 1-4096 molecules per request (log-uniform), 5-80 atoms each; "
+                        f"{args.serve_seconds:g} s per rate",
+            "server": {"precision": args.precision, "slots": 4, "buckets_nodes": [1024, 4096, 16384, 65536],
+                       "rates": res, "totals": stats},
+            "baseline_fp32_one_request_per_launch": {"rates": base}}
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -409,6 +524,12 @@ def run_ours(args):
     except Exception as e:  # noqa: BLE001
         line["roofline"] = {"error": repr(e)}
     ctx.check()
+    if args.serve_seconds > 0 and world == 1:
+        try:
+            trained = ctx.get_params()
+            line["serving"] = run_serving(g, ctx, wl.delta, trained, args)
+        except Exception as e:  # noqa: BLE001
+            line["serving"] = {"error": repr(e)}
     ctx.close()
     if args.compare != "none" and args.compare != args.precision:
         c2 = make_ctx(g, wl, args.compare)
@@ -451,6 +572,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="seconds of Poisson load per arrival rate for the serving measurement (0: skip)")
+    ap.add_argument("--serve-rates", default="200,1000,2000", help="arrival rates, requests/s")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
