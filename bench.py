@@ -368,6 +368,100 @@ def e2e_steps(g, ctx, wl, steps, loss_acc):
                                     "+ loss read back each step"}
 
 
+# ------------------------------------------------------------------ large batches
+def aggregate_large(g, reps: int = 5):
+    """HBM throughput of the aggregation kernels on a batch far larger than L2.
+
+    60,000 molecules (about 1.1M atoms, 2.4M directed edges) collated on the device,
+    random P|Q rows at H = 200: forward reads P and Q and writes 5H aggregates per
+    node (7 GB), the backward reads 11H + 2 d H floats and writes 2H + d H per node.
+    """
+    import torch
+    G = 60_000
+    gs = synth.molecules_lognormal(SEED_DATA + 100, G)
+    tmp = tempfile.mkdtemp(prefix="gcnn_large_")
+    path = os.path.join(tmp, "large.gcnn")
+    synth.write_store(path, gs)
+    st = g.Store(path)
+    N, E = gs.n_nodes, gs.n_edges
+    c = g.Context(g.make_config(8, 1, G, N, E, delta=st.delta()))
+    b = c.collate(st, np.arange(G))
+    rp, col, rev = b.tensor("row_ptr"), b.tensor("col"), b.tensor("rev")
+    Hl = H
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    PQ = torch.randn(N, 2 * Hl, device="cuda", generator=gen)
+    agg = g.aggregate_fwd(PQ, rp, col)
+    dagg = torch.randn(N, 5 * Hl, device="cuda", generator=gen)
+    dPQ = g.aggregate_bwd(PQ, agg, dagg, rp, col, rev)
+    torch.cuda.synchronize()
+    fwd_bytes = N * (2 * Hl + 5 * Hl) * 4.0 + (N + 1 + E) * 4.0
+    bwd_bytes = N * (2 * Hl + 4 * Hl + 5 * Hl + 2 * Hl) * 4.0 + 2.0 * E * Hl * 4 + (N + 1 + 2 * E) * 4.0
+    out = {}
+    for name, fn, nbytes in (("forward", lambda: g.aggregate_fwd(PQ, rp, col), fwd_bytes),
+                             ("backward", lambda: g.aggregate_bwd(PQ, agg, dagg, rp, col, rev), bwd_bytes)):
+        fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        t = min(ts)
+        out[name] = {"ms": 1e3 * t, "algorithmic_bytes": nbytes, "GB_s": nbytes / t / 1e9}
+    hbm, src = measured_hbm()
+    for v in out.values():
+        v["frac_of_hbm"] = v["GB_s"] / hbm
+    out.update({"nodes": N, "edges": E, "hidden": Hl, "peak_GB_s": hbm, "peak_source": src,
+                "note": "gcnn_op_aggregate_fwd / _bwd through the C ABI; best of 5 launches, CUDA events"})
+    del PQ, agg, dagg, dPQ
+    c.close()
+    return out
+
+
+def recompute_study(g, precision: str, steps: int = 20):
+    """Per-layer recompute at H = 256, L = 6, 1024 graphs of 3-51 atoms per batch:
+    step time and device memory with and without it."""
+    import torch
+    Hr, Lr, Br = 256, 6, 1024
+    gs = synth.molecules_lognormal(SEED_DATA + 200, 16 * Br)
+    tmp = tempfile.mkdtemp(prefix="gcnn_recompute_")
+    path = os.path.join(tmp, "rc.gcnn")
+    synth.write_store(path, gs)
+    st = g.Store(path)
+    st.to_device()
+    delta = st.delta()
+    sizes = [st.batch_size(np.arange(i * Br, (i + 1) * Br)) for i in range(16)]
+    Nc = max(s[0] for s in sizes) + 256
+    Ec = max(s[1] for s in sizes) + 512
+    prec = g.PREC_BF16 if precision == "bf16" else g.PREC_FP32
+    out = {"hidden": Hr, "layers": Lr, "batch_graphs": Br, "precision": precision,
+           "mean_nodes_per_batch": float(np.mean([s[0] for s in sizes]))}
+    params = synth.init_params(SEED_STUDENT, Hr, Lr)
+    for rc in (0, 1):
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        c = g.Context(g.make_config(Hr, Lr, Br, Nc, Ec, delta=delta, precision=prec, recompute=rc))
+        free1 = torch.cuda.mem_get_info()[0]
+        c.set_params(params)
+        c.set_order(st, np.arange(16 * Br))
+        for k in range(3):
+            c.train_step(c.collate_range(st, (k % 16) * Br, Br), LR)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(steps):
+            c.train_step(c.collate_range(st, (k % 16) * Br, Br), LR)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out["recompute" if rc else "stored"] = {"ms_per_step": ms, "graphs_per_s": Br / (ms / 1e3),
+                                                "arena_bytes": c.memory_bytes(), "device_bytes_taken": free0 - free1}
+        c.close()
+    return out
+
+
 # ------------------------------------------------------------------ serving
 SERVE_POOL, SEED_SERVE = 100_000, 30
 
@@ -524,6 +618,13 @@ def run_ours(args):
     except Exception as e:  # noqa: BLE001
         line["roofline"] = {"error": repr(e)}
     ctx.check()
+    if args.studies and world == 1:
+        for key, fn in (("aggregate_large_batch", lambda: aggregate_large(g)),
+                        ("recompute", lambda: recompute_study(g, args.precision))):
+            try:
+                line[key] = fn()
+            except Exception as e:  # noqa: BLE001
+                line[key] = {"error": repr(e)}
     if args.serve_seconds > 0 and world == 1:
         try:
             trained = ctx.get_params()
@@ -575,6 +676,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="seconds of Poisson load per arrival rate for the serving measurement (0: skip)")
     ap.add_argument("--serve-rates", default="200,1000,2000", help="arrival rates, requests/s")
+    ap.add_argument("--no-studies", dest="studies", action="store_false",
+                    help="skip the large-batch aggregation and recompute measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

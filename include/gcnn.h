@@ -235,6 +235,9 @@ int gcnn_profile_enable(gcnn_ctx *ctx, int enable);
  * timed launches since the last read (host arrays of GCNN_NPHASE), then
  * resets the counters. */
 int gcnn_profile_read(gcnn_ctx *ctx, double *ms, int64_t *launches);
+/* Device bytes held by the context (parameters, optimiser state, batch,
+ * activations and workspace; one allocation made by gcnn_create). */
+int gcnn_memory(const gcnn_ctx *ctx, int64_t *arena_bytes);
 /* Kernels in the CUDA graph of the most recent gcnn_train_step (0 if it ran
  * eagerly); the collation of a batch adds 2 more. */
 int gcnn_step_kernel_count(gcnn_ctx *ctx, int32_t *n);

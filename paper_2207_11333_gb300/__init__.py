@@ -97,6 +97,7 @@ def _load() -> ctypes.CDLL:
         "gcnn_profile_enable": (i32, [vp, i32]),
         "gcnn_profile_read": (i32, [vp, vp, vp]),
         "gcnn_step_kernel_count": (i32, [vp, P(i32)]),
+        "gcnn_memory": (i32, [vp, P(i64)]),
         "gcnn_serve_create": (i32, [vp, P(ServeConfig), P(vp)]),
         "gcnn_serve_submit": (i32, [vp, P(RequestStruct), P(ctypes.c_uint64)]),
         "gcnn_serve_poll": (i32, [vp, ctypes.c_uint64, vp, P(f64)]),
@@ -352,6 +353,11 @@ class Context:
         n = np.zeros(NPHASE, np.int64)
         _check(lib.gcnn_profile_read(self._h, _np_ptr(ms), _np_ptr(n)))
         return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(PHASES)}
+
+    def memory_bytes(self) -> int:
+        n = ctypes.c_int64()
+        _check(lib.gcnn_memory(self._h, ctypes.byref(n)))
+        return n.value
 
     def step_kernel_count(self) -> int:
         k = ctypes.c_int32()

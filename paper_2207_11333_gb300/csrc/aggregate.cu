@@ -56,7 +56,7 @@ __device__ __forceinline__ bool row_ok(const int *__restrict__ col, int r0, int 
 __global__ void __launch_bounds__(kThreads)
 aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row_ptr,
                      const int *__restrict__ col, const float *__restrict__ PQ,
-                     float *__restrict__ agg, float eps, unsigned *err, uint16_t *__restrict__ S16,
+                     float *__restrict__ agg, float eps, unsigned *err, uint16_t *__restrict__ S16, int ld16,
                      const float *__restrict__ amp, const float *__restrict__ att) {
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
@@ -71,7 +71,7 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
 #pragma unroll
     for (int a = 0; a < kAgg; ++a) st4(out + a * H, z);
     if (S16)
-      for (int a = 0; a < kScalers * kAgg; ++a) st_bf16x4(S16 + (size_t)i * 15 * H + a * H + c, 0.f, 0.f, 0.f, 0.f);
+      for (int a = 0; a < kScalers * kAgg; ++a) st_bf16x4(S16 + (size_t)i * ld16 + a * H + c, 0.f, 0.f, 0.f, 0.f);
     return;
   }
   const float4 P = ld4(PQ + (size_t)i * 2 * H + c);
@@ -100,7 +100,7 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
   if (S16) {  // scaler-major: identity, amplification, attenuation
     const float4 v[kAgg] = {s, mean, mn, mx, sd};
     const float sc[kScalers] = {1.f, amp[i], att[i]};
-    uint16_t *o = S16 + (size_t)i * 15 * H + c;
+    uint16_t *o = S16 + (size_t)i * ld16 + c;
 #pragma unroll
     for (int q = 0; q < kScalers; ++q)
 #pragma unroll
@@ -124,7 +124,7 @@ aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *
                           const int *__restrict__ col, const int *__restrict__ rev,
                           const float *__restrict__ PQ, const float *__restrict__ agg,
                           const float *__restrict__ dagg, float *__restrict__ dPQ,
-                          float *__restrict__ dm, unsigned *err, uint16_t *__restrict__ dPQ16) {
+                          float *__restrict__ dm, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16) {
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const int E = min(e_cap, dims.edges(e_cap));
@@ -136,7 +136,7 @@ aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *
   if (r1 <= r0 || r1 > E || !row_ok(col, r0, r1, N)) {
     if (r1 < r0 || r1 > E || !row_ok(col, r0, r1, N)) flag(err, kErrIndex);
     st4(dPQ + (size_t)i * 2 * H + c, dP);
-    if (dPQ16) st_bf16x4(dPQ16 + (size_t)i * 2 * H + c, 0.f, 0.f, 0.f, 0.f);
+    if (dPQ16) st_bf16x4(dPQ16 + (size_t)i * ld16 + c, 0.f, 0.f, 0.f, 0.f);
     return;
   }
   const float d = (float)(r1 - r0);
@@ -169,13 +169,13 @@ aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *
     else flag(err, kErrIndex);
   }
   st4(dPQ + (size_t)i * 2 * H + c, dP);
-  if (dPQ16) st_bf16x4(dPQ16 + (size_t)i * 2 * H + c, dP.x, dP.y, dP.z, dP.w);
+  if (dPQ16) st_bf16x4(dPQ16 + (size_t)i * ld16 + c, dP.x, dP.y, dP.z, dP.w);
 }
 
 __global__ void __launch_bounds__(kThreads)
 aggregate_bwd_gather_kernel(int n_cap, int e_cap, int H, DevDims dims,
                             const int *__restrict__ row_ptr, const float *__restrict__ dm,
-                            float *__restrict__ dPQ, unsigned *err, uint16_t *__restrict__ dPQ16) {
+                            float *__restrict__ dPQ, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16) {
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const int E = min(e_cap, dims.edges(e_cap));
@@ -187,19 +187,19 @@ aggregate_bwd_gather_kernel(int n_cap, int e_cap, int H, DevDims dims,
   float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int e = r0; e < r1; ++e) q = add4(q, ld4(dm + (size_t)e * H + c));
   st4(dPQ + (size_t)j * 2 * H + H + c, q);
-  if (dPQ16) st_bf16x4(dPQ16 + (size_t)j * 2 * H + H + c, q.x, q.y, q.z, q.w);
+  if (dPQ16) st_bf16x4(dPQ16 + (size_t)j * ld16 + H + c, q.x, q.y, q.z, q.w);
 }
 
 }  // namespace
 
 int launch_aggregate_fwd(int n_nodes, int H, DevDims dims, const int *row_ptr, const int *col,
                          const float *PQ, float *agg, float eps, unsigned *err, cudaStream_t s,
-                         uint16_t *S16, const float *amp, const float *att) {
+                         uint16_t *S16, int ld16, const float *amp, const float *att) {
   if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
   aggregate_fwd_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(n_nodes, H, dims, row_ptr, col,
-                                                                      PQ, agg, eps, err, S16, amp, att);
+                                                                      PQ, agg, eps, err, S16, ld16, amp, att);
   GCNN_LAUNCH_CHECK();
   return GCNN_OK;
 }
@@ -207,16 +207,16 @@ int launch_aggregate_fwd(int n_nodes, int H, DevDims dims, const int *row_ptr, c
 int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const int *row_ptr,
                          const int *col, const int *rev, const float *PQ, const float *agg,
                          const float *dagg, float *dPQ, float *scratch, float eps, unsigned *err,
-                         cudaStream_t s, uint16_t *dPQ16) {
+                         cudaStream_t s, uint16_t *dPQ16, int ld16) {
   (void)eps;
   if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
   aggregate_bwd_edge_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(
-      n_nodes, n_edges, H, dims, row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, err, dPQ16);
+      n_nodes, n_edges, H, dims, row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, err, dPQ16, ld16);
   GCNN_LAUNCH_CHECK();
   aggregate_bwd_gather_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(n_nodes, n_edges, H, dims,
-                                                                            row_ptr, scratch, dPQ, err, dPQ16);
+                                                                            row_ptr, scratch, dPQ, err, dPQ16, ld16);
   GCNN_LAUNCH_CHECK();
   return GCNN_OK;
 }

@@ -185,7 +185,7 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   c->P = param_count_of(*cfg);
   c->Gc = cfg->max_graphs; c->Nc = cfg->max_nodes; c->Ec = cfg->max_edges;
   const size_t H = c->H, Nc = c->Nc, Ec = c->Ec, Gc = c->Gc, L = c->L, Hh = c->Hh;
-  c->emb_chunks = (int)ceil_div(Nc, 64);
+  c->emb_chunks = (int)ceil_div(Nc, 16);
   // split-K workspace: the largest of the step's GEMMs
   // (over every node-count bucket a batch can launch with)
   size_t wsf = 0;
@@ -198,12 +198,13 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
     wsf = std::max(wsf, gemm_simt_workspace_floats(h + 1, 2 * h, n));
     wsf = std::max(wsf, gemm_simt_workspace_floats(n, h, 3 * h));
     if (cfg->precision == GCNN_PREC_BF16) {
-      wsf = std::max(wsf, gemm_tc_workspace_floats(n, 2 * h, h));
-      wsf = std::max(wsf, gemm_tc_workspace_floats(n, h, 16 * h));
-      wsf = std::max(wsf, gemm_tc_workspace_floats(16 * h + 1, h, n));
-      wsf = std::max(wsf, gemm_tc_workspace_floats(n, kAgg * h, 3 * h));
-      wsf = std::max(wsf, gemm_tc_workspace_floats(h + 1, 2 * h, n));
-      wsf = std::max(wsf, gemm_tc_workspace_floats(n, h, 3 * h));
+      const int r64 = (h + 63) / 64 * 64, r3 = (3 * h + 63) / 64 * 64, r16 = (16 * h + 63) / 64 * 64;
+      wsf = std::max(wsf, gemm_tc_workspace_floats(n, 2 * h, r64));
+      wsf = std::max(wsf, gemm_tc_workspace_floats(n, h, r16));
+      wsf = std::max(wsf, gemm_tc_workspace_floats(16 * h, h, n));
+      wsf = std::max(wsf, gemm_tc_workspace_floats(n, kAgg * h, r3));
+      wsf = std::max(wsf, gemm_tc_workspace_floats(h, 2 * h, n));
+      wsf = std::max(wsf, gemm_tc_workspace_floats(n, h, r3));
     }
     if (n == (int)Nc) break;
   }
@@ -230,10 +231,11 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   const size_t o_embp = cv.take<float>((size_t)c->emb_chunks * c->T * H);
   const size_t o_ws = cv.take<float>(wsf);
   const bool bf = cfg->precision == GCNN_PREC_BF16;
-  const size_t o_wb = cv.take<uint16_t>(bf ? c->P : 0), o_xb = cv.take<uint16_t>(bf ? L * Nc * H : 0);
-  const size_t o_sb = cv.take<uint16_t>(bf ? (cfg->recompute ? 1 : L) * Nc * 15 * H : 0);
-  const size_t o_d30 = cv.take<uint16_t>(bf ? Nc * 3 * H : 0), o_d31 = cv.take<uint16_t>(bf ? Nc * 3 * H : 0);
-  const size_t o_pqb = cv.take<uint16_t>(bf ? Nc * 2 * H : 0);
+  const size_t o_wb = cv.take<uint16_t>(bf ? c->P : 0), o_wp = cv.take<uint16_t>(bf ? L * 18 * H * H : 0);
+  const size_t o_U = cv.take<uint16_t>(bf ? (cfg->recompute ? 1 : L) * Nc * 16 * H : 0);
+  const size_t o_Xb = cv.take<uint16_t>(bf && cfg->recompute ? L * Nc * H : 0);
+  const size_t o_g0 = cv.take<uint16_t>(bf ? Nc * 5 * H : 0), o_g1 = cv.take<uint16_t>(bf ? Nc * 5 * H : 0);
+  const size_t o_cp = cv.take<float>(bf ? ceil_div(Nc, 32) * 2 * H : 0);
   c->dbytes = cv.off;
   cudaError_t e = cudaMalloc(&c->dmem, c->dbytes);
   if (e != cudaSuccess) {
@@ -259,8 +261,9 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   c->ws.partial = (float *)(b + o_ws); c->ws.floats = wsf;
   c->ws.max_splits = (cfg->flags & GCNN_FLAG_ROW_INVARIANT) ? 1 : 32;
   if (bf) {
-    c->wb = (uint16_t *)(b + o_wb); c->xb = (uint16_t *)(b + o_xb); c->sb = (uint16_t *)(b + o_sb);
-    c->d3[0] = (uint16_t *)(b + o_d30); c->d3[1] = (uint16_t *)(b + o_d31); c->pqb = (uint16_t *)(b + o_pqb);
+    c->wb = (uint16_t *)(b + o_wb); c->wpack = (uint16_t *)(b + o_wp); c->U = (uint16_t *)(b + o_U);
+    if (cfg->recompute) c->Xb = (uint16_t *)(b + o_Xb);
+    c->G5[0] = (uint16_t *)(b + o_g0); c->G5[1] = (uint16_t *)(b + o_g1); c->colsum_partial = (float *)(b + o_cp);
   }
   int rc = GCNN_OK;
   if (cudaMemset(c->dmem, 0, c->dbytes) != cudaSuccess) rc = set_error(GCNN_ECUDA, "cudaMemset failed");
@@ -308,7 +311,7 @@ static int copy_flat(gcnn_ctx *c, float *dev, const float *src, float *dst, int6
 // Refresh the BF16 copy of the parameters (BF16 precision only).
 static int refresh_bf16(gcnn_ctx *c) {
   if (!c->wb) return GCNN_OK;
-  GCNN_TRY(launch_cast_bf16(c->P, c->params, c->wb, c->stream));
+  GCNN_TRY(ctx_refresh_bf16(c));
   return sync(c);
 }
 
@@ -547,6 +550,12 @@ int gcnn_profile_read(gcnn_ctx *c, double *ms, int64_t *launches) {
     launches[c->prof_cls[k]] += 1;
   }
   c->prof_used = 0;
+  return GCNN_OK;
+}
+
+int gcnn_memory(const gcnn_ctx *c, int64_t *arena_bytes) {
+  if (!c || !arena_bytes) return set_error(GCNN_EINVAL, "null argument");
+  *arena_bytes = (int64_t)c->dbytes;
   return GCNN_OK;
 }
 

@@ -50,11 +50,12 @@ struct gcnn_ctx {
   int emb_chunks = 0;
 
   // BF16 operands of the tensor-core GEMMs (precision == GCNN_PREC_BF16)
-  uint16_t *wb = nullptr;    // parameters cast to BF16 after every update
-  uint16_t *xb = nullptr;    // L x Nc x H      layer inputs
-  uint16_t *sb = nullptr;    // (recompute ? 1 : L) x Nc x 15H  scaled aggregates
-  uint16_t *d3[2] = {nullptr, nullptr};  // Nc x 3H  masked, scaled output gradients
-  uint16_t *pqb = nullptr;   // Nc x 2H         message gradients
+  uint16_t *wb = nullptr;     // parameters cast to BF16 after every update (same layout)
+  uint16_t *wpack = nullptr;  // per layer: Wd [5H][3H] then Wx [H][3H] (backward B operands)
+  uint16_t *U = nullptr;      // (recompute ? 1 : L) x Nc x 16H: [x_l | agg | amp*agg | att*agg]
+  uint16_t *Xb = nullptr;     // recompute only: L x Nc x H layer inputs (copied into U when needed)
+  uint16_t *G5[2] = {nullptr, nullptr};  // Nc x 5H: [amp*g | att*g | g | dP | dQ]
+  float *colsum_partial = nullptr;       // ceil(Nc/32) x 2H
   gcnn::GemmWorkspace ws{};
 
   // host-side state
@@ -78,6 +79,9 @@ struct gcnn_ctx {
 };
 
 namespace gcnn {
+// Refresh the BF16 copies of the parameters (BF16 precision; no-op otherwise).
+int ctx_refresh_bf16(gcnn_ctx *c);
+
 // Event pair around the kernels launched in its lifetime (no-op unless
 // profiling is on and the stream is not being captured).
 class PhaseScope {

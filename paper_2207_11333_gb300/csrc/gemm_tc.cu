@@ -1,24 +1,31 @@
-// BF16 GEMM on the Blackwell tensor cores (tcgen05, FP32 accumulator in TMEM)
-// for the dense node-wise layers of the PNA convolution and their gradients.
+// BF16 GEMM on the Blackwell tensor cores for the dense node-wise layers of
+// the PNA convolution and their gradients: TMA loads, tcgen05.mma with the
+// FP32 accumulator in TMEM, warp-specialised mbarrier pipeline.
 //
-// Operands are BF16 arrays written by the kernels that produce them (the
-// embedding, the update GEMM's epilogue, the aggregation kernels, the weight
-// cast after each optimizer step), possibly several along K ("segments", e.g.
-// [x | scaled aggregates]) or along M (the weight-gradient GEMMs append a row
-// of ones whose product is the bias gradient).  Staging is a pure copy:
-// 16-byte cp.async chunks into a 4-stage ring of 128-byte-swizzled shared-
-// memory tiles, K-major when the source is contiguous along K and MN-major
-// when it is contiguous along M / N (the weight-gradient GEMMs reduce over
-// nodes, and activations are stored node-major).
+// Each operand is one BF16 row-major array described by a TMA tensor map
+// (128-byte swizzle, 64-element boxes along the contiguous dimension):
+//   K-major  (contiguous along K): A tiles 128 rows x 64 k, B tiles BN x 64 k
+//   MN-major (contiguous along M/N, e.g. node-major activations in the
+//            weight-gradient GEMMs that reduce over nodes): boxes of
+//            64 M/N elements x 64 k rows
+// Zero fill past the array's extent pads K to a multiple of 64.  Rows past
+// the batch's true node count inside the array are cleared in shared memory
+// before the MMA when K runs over nodes.
 //
-// Per CTA: one 128 x BN output tile (BN <= 256, a multiple of 16), K in steps
-// of 64.  One thread issues four tcgen05.mma (M = 128, N = BN, K = 16) per
-// stage and commits them to the stage's mbarrier; the stage is refilled only
-// after that barrier fires.  The epilogue reads TMEM (tcgen05.ld) and applies
-// bias / ReLU, writing FP32 and optional BF16 side outputs, or split-K partials
-// that a second kernel sums in split order.  Every wait is bounded: on expiry
-// the kernel sets kErrTimeout in the device error word and skips its epilogue.
+// Roles (256 threads, one 128 x BN output tile per CTA, BN <= 256):
+//   warp 0   one lane issues the TMA loads of a stage after the stage's
+//            "empty" barrier fired, with the byte count on its "full" barrier
+//   warp 1   waits "full", issues four tcgen05.mma (K = 16 each) and commits
+//            them to the stage's "empty" barrier; after the last stage it
+//            commits to the "accumulator ready" barrier
+//   warps 4-7  wait for the accumulator, read TMEM (tcgen05.ld), apply bias /
+//            ReLU and write FP32 and BF16 outputs, or split-K partials
+// Every wait is bounded (~2 s): on expiry the kernel sets kErrTimeout in the
+// device error word, skips its epilogue and releases TMEM.
+#include <cuda.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "kernels.cuh"
 
@@ -32,26 +39,15 @@ constexpr int kBTileBytes = kMaxBN * BK * 2;    // 32 KB
 constexpr int kStageBytes = kATileBytes + kBTileBytes;
 constexpr int kSmemBytes = STAGES * kStageBytes + 1024 /* alignment slack */ + 256 /* barriers */;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
-constexpr uint32_t kMnAtomBytes = 64 * 128;      // one 64-wide MN atom over 64 K rows
+constexpr uint32_t kMnAtomBytes = 64 * 128;      // 64 M/N elements x 64 k rows
+
+struct TcMaps {
+  CUtensorMap a, b;
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
-  return r;
-}
-
-// ---------------------------------------------------------------- cp.async
-__device__ __forceinline__ void cp16(uint32_t dst, const void *src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // ---------------------------------------------------------------- mbarrier
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
@@ -70,13 +66,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (clock64() - t0 > kWaitCycles) return false;
   }
   return true;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// ---------------------------------------------------------------- TMA
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
 }
 
 // ---------------------------------------------------------------- tcgen05
@@ -94,10 +102,9 @@ __device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols) {
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor, 128-byte swizzle.  K-major tiles: 8-row
-// groups 1024 bytes apart (stride byte offset), leading offset unused.
-// MN-major tiles: 64-element MN atoms kMnAtomBytes apart (leading byte
-// offset), 8-row K groups 1024 bytes apart (stride byte offset).
+// Shared-memory matrix descriptor, 128-byte swizzle.  K-major: 8-row groups
+// 1024 bytes apart, leading offset unused.  MN-major: 64-element atoms
+// kMnAtomBytes apart (leading), 8-row k groups 1024 bytes apart (stride).
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, bool mn_major) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
@@ -130,19 +137,51 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                : "memory");
 }
 
-// 32 lanes x 8 consecutive 32-bit columns; thread t receives lane (base + t).
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
-  uint32_t r[8];
+// 32 lanes x 8 consecutive 32-bit columns (thread t: lane base + t); the
+// registers are valid after tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t r[8]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-// ---------------------------------------------------------------- staging
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---------------------------------------------------------------- epilogue
+__device__ __forceinline__ void finish8(const TcEpilogue &e, int n, float v[8]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (e.bias && n + q < e.bias_n) v[q] += e.bias[n + q];
+    if (e.relu) v[q] = fmaxf(v[q], 0.f);
+  }
+}
+
+__device__ __forceinline__ void st_bf16x8(uint16_t *p, const float v[8], float s) {
+  *reinterpret_cast<uint4 *>(p) = make_uint4(bf16x2(s * v[0], s * v[1]), bf16x2(s * v[2], s * v[3]),
+                                             bf16x2(s * v[4], s * v[5]), bf16x2(s * v[6], s * v[7]));
+}
+
+// Final value v of C(row, n..n+7) to every requested output.
+__device__ __forceinline__ void emit8(const TcEpilogue &e, int N, int row, int n, const float v[8]) {
+  if (e.C) {
+    float *c = e.C + (size_t)row * e.ldc + n;
+    *reinterpret_cast<float4 *>(c) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4 *>(c + 4) = make_float4(v[4], v[5], v[6], v[7]);
+  }
+  if (e.C16) st_bf16x8(e.C16 + (size_t)row * e.ld16 + n, v, 1.f);
+  if (e.D3) {  // [amp g | att g | g], g = v * [mask > 0]
+    float g[8];
+    const float *mk = e.mask + (size_t)row * e.ldm + n;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) g[q] = mk[q] > 0.f ? v[q] : 0.f;
+    uint16_t *o = e.D3 + (size_t)row * e.ld3 + n;
+    st_bf16x8(o, g, e.amp[row]);
+    st_bf16x8(o + N, g, e.att[row]);
+    st_bf16x8(o + 2 * N, g, 1.f);
+  }
+}
+
 struct Sizes {
   int M, K;
 };
@@ -154,132 +193,25 @@ __device__ __forceinline__ Sizes actual_sizes(const TcDesc &d, DevDims dims) {
   return s;
 }
 
-__device__ __forceinline__ int find_seg(const TcOperand &op, int f) {
-  int s = 0;
-#pragma unroll
-  for (int q = 1; q < kMaxSeg; ++q)
-    if (q < op.nseg && op.seg[q].begin <= f) s = q;
-  return s;
-}
-
-// byte offset of 16-byte chunk (row r, chunk c) in a K-major swizzled tile
-__device__ __forceinline__ uint32_t kmaj_off(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
-// byte offset of the chunk holding MN elements mn..mn+7 of K row kk in an MN-major tile
-__device__ __forceinline__ uint32_t mnmaj_off(int mn, int kk) {
-  return (uint32_t)((mn >> 6) * kMnAtomBytes + kk * 128 + ((((mn & 63) >> 3) ^ (kk & 7)) << 4));
-}
-
-// One 16-byte chunk of a "ones" segment: element i is 1 where mn + i == mn_one and valid.
-__device__ __forceinline__ void st_ones(uint8_t *dst, int mn, int M, bool kvalid) {
-  uint32_t w[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-    if (kvalid && mn + i < M) w[i >> 1] |= (i & 1) ? 0x3F800000u : 0x3F80u;
-  *reinterpret_cast<uint4 *>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-}
-
-// A tile (128 x 64) of k-tile k0 -> smem
-__device__ __forceinline__ void stage_a(const TcDesc &d, int M, int K, int m0, int k0, uint8_t *tile) {
-  const int tid = threadIdx.x;
-  const uint32_t base = smem_u32(tile);
-  if (!d.A.mn_major) {  // A(m,k) = ptr[m*ld + k - begin]
-#pragma unroll
-    for (int i = 0; i < (BM * 8) / kThreads; ++i) {
-      const int q = tid + i * kThreads;
-      const int r = q >> 3, c = q & 7;
-      const int m = m0 + r, k = k0 + c * 8;
-      const bool ok = m < M && k < K;
-      const TcSeg &sg = d.A.seg[find_seg(d.A, ok ? k : 0)];
-      if (sg.ptr) cp16(base + kmaj_off(r, c), ok ? sg.ptr + (size_t)m * sg.ld + (k - sg.begin) : sg.ptr, ok);
-      else st_ones(tile + kmaj_off(r, c), 0, 8, ok);
-    }
-  } else {  // A(m,k) = ptr[k*ld + m - begin]; consecutive threads walk m
-#pragma unroll
-    for (int i = 0; i < (BM * 8) / kThreads; ++i) {
-      const int q = tid + i * kThreads;
-      const int kk = q >> 4, c = q & 15;
-      const int ml = c * 8, m = m0 + ml, k = k0 + kk;
-      const bool ok = m < M && k < K;
-      const TcSeg &sg = d.A.seg[find_seg(d.A, ok ? m : 0)];
-      const uint32_t off = mnmaj_off(ml, kk);
-      if (sg.ptr) cp16(base + off, ok ? sg.ptr + (size_t)k * sg.ld + (m - sg.begin) : sg.ptr, ok);
-      else st_ones(tile + off, m, M, k < K);
-    }
-  }
-}
-
-// B tile (BN x 64; row n = output column) of k-tile k0 -> smem
-__device__ __forceinline__ void stage_b(const TcDesc &d, int N, int K, int BN, int n0, int k0, uint8_t *tile) {
-  const int tid = threadIdx.x;
-  const uint32_t base = smem_u32(tile);
-  const int chunks = BN * 8;
-  if (!d.B.mn_major) {  // B(k,n) = ptr[n*ld + k - begin]
-    for (int q = tid; q < chunks; q += kThreads) {
-      const int r = q >> 3, c = q & 7;
-      const int n = n0 + r, k = k0 + c * 8;
-      const bool ok = n < N && k < K;
-      const TcSeg &sg = d.B.seg[find_seg(d.B, ok ? k : 0)];
-      cp16(base + kmaj_off(r, c), ok ? sg.ptr + (size_t)n * sg.ld + (k - sg.begin) : sg.ptr, ok);
-    }
-  } else {  // B(k,n) = ptr[(k-begin)*ld + n]; consecutive threads walk n
-    const int cpr = BN >> 3;  // chunks per K row
-    for (int q = tid; q < chunks; q += kThreads) {
-      const int kk = q / cpr, c = q - kk * cpr;
-      const int nl = c * 8, n = n0 + nl, k = k0 + kk;
-      const bool ok = n < N && k < K;
-      const TcSeg &sg = d.B.seg[find_seg(d.B, ok ? k : 0)];
-      cp16(base + mnmaj_off(nl, kk), ok ? sg.ptr + (size_t)(k - sg.begin) * sg.ld + n : sg.ptr, ok);
-    }
-  }
-}
-
-// ---------------------------------------------------------------- epilogue
-// Final value v (bias and ReLU applied) of C(row, n..n+7) to every output.
-__device__ __forceinline__ void emit8(const TcEpilogue &e, int M, int N, int row, int n, const float v[8]) {
-  const int lim = (e.last_row_cols > 0 && row == M - 1) ? min(N, e.last_row_cols) : N;
-  if (e.C) {
-    float *c = e.C + (size_t)row * e.ldc + n;
-    if (n + 8 <= lim) {
-      *reinterpret_cast<float4 *>(c) = make_float4(v[0], v[1], v[2], v[3]);
-      *reinterpret_cast<float4 *>(c + 4) = make_float4(v[4], v[5], v[6], v[7]);
-    } else {
-      for (int q = 0; q < 8 && n + q < lim; ++q) c[q] = v[q];
-    }
-  }
-  if (e.C16 && n + 8 <= N) {
-    *reinterpret_cast<uint4 *>(e.C16 + (size_t)row * e.ld16 + n) =
-        make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
-  }
-  if (e.D3 && n + 8 <= N) {  // [v * [mask > 0], amp * (...), att * (...)]
-    float g[8];
-    const float *mk = e.mask + (size_t)row * e.ldm + n;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) g[q] = mk[q] > 0.f ? v[q] : 0.f;
-    const float a = e.amp[row], t = e.att[row];
-    uint16_t *o = e.D3 + (size_t)row * e.ld3 + n;
-    *reinterpret_cast<uint4 *>(o) =
-        make_uint4(pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), pack_bf16(g[4], g[5]), pack_bf16(g[6], g[7]));
-    *reinterpret_cast<uint4 *>(o + N) = make_uint4(pack_bf16(a * g[0], a * g[1]), pack_bf16(a * g[2], a * g[3]),
-                                                   pack_bf16(a * g[4], a * g[5]), pack_bf16(a * g[6], a * g[7]));
-    *reinterpret_cast<uint4 *>(o + 2 * N) = make_uint4(pack_bf16(t * g[0], t * g[1]), pack_bf16(t * g[2], t * g[3]),
-                                                       pack_bf16(t * g[4], t * g[5]), pack_bf16(t * g[6], t * g[7]));
-  }
-}
-
-__device__ __forceinline__ void finish8(const TcEpilogue &e, int n, float v[8]) {
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    if (e.bias && n + q < e.bias_n) v[q] += e.bias[n + q];
-    if (e.relu) v[q] = fmaxf(v[q], 0.f);
+// Clear k rows [from, 64) of an MN-major tile of `atoms` 64-wide atoms (lane-parallel).
+__device__ __forceinline__ void clear_k_rows(uint8_t *tile, int atoms, int from, int lane) {
+  const int rows = 64 - from;
+  for (int q = lane; q < atoms * rows * 8; q += 32) {
+    const int a = q / (rows * 8), r = from + (q / 8) % rows, c = q % 8;
+    *reinterpret_cast<uint4 *>(tile + a * kMnAtomBytes + r * 128 + c * 16) = make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-tc_gemm_kernel(TcDesc d, DevDims dims, float *__restrict__ partial, int splits, int kps, int BN, unsigned *err) {
+tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, float *__restrict__ partial, int splits,
+                int kps, int BN, unsigned *err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * kStageBytes);
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + STAGES);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * kStageBytes);
+  uint64_t *empty = full + STAGES;
+  uint64_t *acc_ready = empty + STAGES;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_ready + 1);
+  uint32_t *flag = tmem_slot + 1;
 
   const Sizes sz = actual_sizes(d, dims);
   const int M = sz.M, K = sz.K, N = d.N;
@@ -289,99 +221,140 @@ tc_gemm_kernel(TcDesc d, DevDims dims, float *__restrict__ partial, int splits, 
   const int kbeg = z * kps;
   const int kend = min(K, kbeg + kps);
   const int nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t ncols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+  const int b_atoms = (BN + 63) / 64;
+  const uint32_t a_bytes = kATileBytes;
+  const uint32_t b_bytes = d.B.mn_major ? (uint32_t)b_atoms * kMnAtomBytes : (uint32_t)BN * BK * 2;
 
   if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_ready, 1);
+    *flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b)) : "memory");
   }
   if (warp == 0) tmem_alloc(tmem_slot, ncols);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t idesc = instr_desc(BM, BN, d.A.mn_major, d.B.mn_major);
-  const uint32_t a_step = d.A.mn_major ? 2048u : 32u;  // bytes per K = 16 slice
-  const uint32_t b_step = d.B.mn_major ? 2048u : 32u;
 
-  auto load_stage = [&](int kt) {
-    uint8_t *a_tile = smem + (kt % STAGES) * kStageBytes;
-    const int k0 = kbeg + kt * BK;
-    stage_a(d, M, kend, m0, k0, a_tile);
-    stage_b(d, N, kend, BN, n0, k0, a_tile + kATileBytes);
-  };
-
-  // prologue: stages 0 .. STAGES-2 in flight
+  if (warp == 0) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt % STAGES;
+        if (kt >= STAGES && !mbar_wait(&empty[s], ((kt / STAGES) - 1) & 1)) {
+          atomicOr(flag, 1u);
+          break;
+        }
+        uint8_t *a_tile = smem + s * kStageBytes;
+        uint8_t *b_tile = a_tile + kATileBytes;
+        const int k0 = kbeg + kt * BK;
+        mbar_expect_tx(&full[s], a_bytes + b_bytes);
+        if (!d.A.mn_major) {
+          tma_load_2d(smem_u32(a_tile), &maps.a, k0, m0, &full[s]);
+        } else {
+          tma_load_2d(smem_u32(a_tile), &maps.a, m0, k0, &full[s]);
+          tma_load_2d(smem_u32(a_tile + kMnAtomBytes), &maps.a, m0 + 64, k0, &full[s]);
+        }
+        if (!d.B.mn_major) {
+          tma_load_2d(smem_u32(b_tile), &maps.b, k0, n0, &full[s]);
+        } else {
+          for (int j = 0; j < b_atoms; ++j)
+            tma_load_2d(smem_u32(b_tile + j * kMnAtomBytes), &maps.b, n0 + 64 * j, k0, &full[s]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer
+    const uint32_t idesc = instr_desc(BM, BN, d.A.mn_major, d.B.mn_major);
+    const uint32_t a_step = d.A.mn_major ? 2048u : 32u;
+    const uint32_t b_step = d.B.mn_major ? 2048u : 32u;
+    bool ok = true;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % STAGES;
+      if (!mbar_wait(&full[s], (kt / STAGES) & 1)) ok = false;
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) atomicOr(flag, 1u);
+        break;
+      }
+      uint8_t *a_tile = smem + s * kStageBytes;
+      uint8_t *b_tile = a_tile + kATileBytes;
+      const int k0 = kbeg + kt * BK;
+      if (d.node_dim == kNodeK && k0 + BK > K) {  // rows past the batch's nodes must not contribute
+        const int from = K - k0;
+        if (d.A.mn_major) clear_k_rows(a_tile, 2, from, lane);
+        if (d.B.mn_major) clear_k_rows(b_tile, b_atoms, from, lane);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+      }
+      if (lane == 0) {
+        fence_after_sync();
+        const uint32_t a_base = smem_u32(a_tile), b_base = smem_u32(b_tile);
 #pragma unroll
-  for (int p = 0; p < STAGES - 1; ++p) {
-    if (p < nk) load_stage(p);
-    cp_commit();
+        for (int j = 0; j < BK / 16; ++j)
+          mma_bf16(tmem, smem_desc(a_base + j * a_step, d.A.mn_major), smem_desc(b_base + j * b_step, d.B.mn_major),
+                   idesc, (kt > 0 || j > 0) ? 1u : 0u);
+        mma_commit(&empty[s]);
+      }
+      __syncwarp();
+    }
+    if (ok && nk > 0 && lane == 0) mma_commit(acc_ready);
   }
-  bool ok = true;
-  for (int kt = 0; kt < nk; ++kt) {
-    cp_wait<STAGES - 2>();  // this thread's copies of stage kt have landed
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+  // ------------------------------------------------ epilogue (all 8 warps)
+  // warp w reads TMEM lanes 32*(w%4).. (tile rows) and half w/4 of the columns
+  {
+    bool ok = true;
+    if (nk > 0) {
+      ok = mbar_wait(acc_ready, 0);
+      if (!ok && lane == 0) atomicOr(flag, 1u);
       fence_after_sync();
-      const uint32_t a_base = smem_u32(smem + (kt % STAGES) * kStageBytes);
-      const uint32_t b_base = a_base + kATileBytes;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (ok) {
+      const int lane_base = 32 * (warp & 3);
+      const int row = m0 + lane_base + lane;
+      const int groups = BN / 8, half = (groups + 1) / 2;
+      const int g0 = warp < 4 ? 0 : half, g1 = warp < 4 ? half : groups;
+      for (int gb = g0; gb < g1; gb += 4) {
+        uint32_t r[4][8];
+        const int cnt = min(4, g1 - gb);
+        if (nk > 0) {
 #pragma unroll
-      for (int j = 0; j < BK / 16; ++j)
-        mma_bf16(tmem, smem_desc(a_base + j * a_step, d.A.mn_major), smem_desc(b_base + j * b_step, d.B.mn_major),
-                 idesc, (kt > 0 || j > 0) ? 1u : 0u);
-      mma_commit(&bars[kt % STAGES]);
-    }
-    // refill the slot of k-tile kt-1 with k-tile kt+STAGES-1 once its MMAs are done
-    const int nxt = kt + STAGES - 1;
-    bool expired = false;
-    if (nxt < nk && kt >= 1) expired = !mbar_wait(&bars[(kt - 1) % STAGES], ((kt - 1) / STAGES) & 1);
-    if (__syncthreads_or(expired)) {  // block-uniform exit
-      ok = false;
-      break;
-    }
-    if (nxt < nk) load_stage(nxt);
-    cp_commit();
-  }
-  cp_wait<0>();
-  bool expired = false;
-  if (nk > 0 && ok) {
-    const int last = nk - 1;
-    expired = !mbar_wait(&bars[last % STAGES], (last / STAGES) & 1);
-  }
-  if (__syncthreads_or(expired)) ok = false;
-  fence_after_sync();
-
-  if (ok) {
-    const int lane_base = 32 * (warp & 3);
-    const int row = m0 + lane_base + (tid & 31);
-    const int ch = (BN / 8 + 1) / 2;
-    const int g0 = warp < 4 ? 0 : ch, g1 = warp < 4 ? ch : BN / 8;
-    for (int gq = g0; gq < g1; ++gq) {
-      float v[8];
-      if (nk > 0) {
-        tmem_ld8(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(gq * 8), v);
-      } else {
+          for (int u = 0; u < 4; ++u)
+            if (u < cnt) tmem_ld8(tmem + ((uint32_t)lane_base << 16) + (uint32_t)((gb + u) * 8), r[u]);
+          tmem_wait_ld();
+        }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = 0.f;
+        for (int u = 0; u < 4; ++u) {
+          if (u >= cnt) break;
+          float v[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) v[q] = nk > 0 ? __uint_as_float(r[u][q]) : 0.f;
+          const int n = n0 + (gb + u) * 8;
+          if (row >= M || n >= N) continue;
+          if (splits > 1) {
+            float *p = partial + ((size_t)z * d.M + row) * N + n;
+            *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4 *>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
+            continue;
+          }
+          finish8(d.ep, n, v);
+          emit8(d.ep, N, row, n, v);
+        }
       }
-      const int n = n0 + gq * 8;
-      if (row >= M || n >= N) continue;
-      if (splits > 1) {
-        float *p = partial + ((size_t)z * d.M + row) * N + n;
-        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-        *reinterpret_cast<float4 *>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
-        continue;
-      }
-      finish8(d.ep, n, v);
-      emit8(d.ep, M, N, row, n, v);
     }
-  } else if (tid == 0 && err) {
-    atomicOr(err, kErrTimeout);
   }
   fence_before_sync();
   __syncthreads();
+  if (tid == 0 && *flag && err) atomicOr(err, kErrTimeout);
   if (warp == 0) tmem_free(tmem, ncols);
 }
 
@@ -400,31 +373,59 @@ __global__ void __launch_bounds__(256) tc_reduce_kernel(TcDesc d, DevDims dims, 
     v[0] += a.x; v[1] += a.y; v[2] += a.z; v[3] += a.w; v[4] += b.x; v[5] += b.y; v[6] += b.z; v[7] += b.w;
   }
   finish8(d.ep, n, v);
-  emit8(d.ep, M, N, row, n, v);
+  emit8(d.ep, N, row, n, v);
+}
+
+// ---------------------------------------------------------------- host
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  });
+  return fn;
+}
+
+// Map of a row-major BF16 array [rows][cols] (row pitch ld elements), boxes of
+// 64 contiguous elements x box_rows rows, 128-byte swizzle, zero fill.
+int make_map(CUtensorMap *m, const TcMat &a, int box_rows) {
+  EncodeTiled enc = encoder();
+  if (!enc) return set_error(GCNN_ECUDA, "cuTensorMapEncodeTiled is not available");
+  if (!a.ptr || a.rows < 1 || a.cols < 1 || a.ld % 8 || a.cols > a.ld || reinterpret_cast<uintptr_t>(a.ptr) % 16)
+    return set_error(GCNN_EINVAL, "tc gemm: operand must be 16-byte aligned with ld a multiple of 8");
+  const cuuint64_t dim[2] = {(cuuint64_t)a.cols, (cuuint64_t)a.rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)a.ld * 2};
+  const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1u, 1u};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(a.ptr), dim, stride, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(GCNN_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return GCNN_OK;
 }
 
 int g_configured = 0;
 
-int choose(int M, int N, int K, int *BN, int *ntiles, int *splits) {
+// N tiles as few as possible (each <= 256 and a multiple of 16); splits of K
+// so that one wave (one CTA per SM) is filled, with >= 6 k-tiles per split.
+int choose(int M, int N, int K, int max_splits, int *BN, int *ntiles, int *splits) {
   *ntiles = (N + kMaxBN - 1) / kMaxBN;
   *BN = ((N + *ntiles - 1) / *ntiles + 15) / 16 * 16;
   const long long tiles = (long long)*ntiles * ((M + BM - 1) / BM);
   const int ktiles = (K + BK - 1) / BK;
-  // one wave (one 197 KB CTA per SM), at least 4 k-tiles per split
   int s = (int)std::max<long long>(1, num_sms() / tiles);
-  s = std::min(s, std::max(1, ktiles / 4));
-  *splits = std::min(s, 32);
+  s = std::min(s, std::max(1, ktiles / 6));
+  *splits = std::min(std::min(s, 32), max_splits);
   return ktiles;
-}
-
-bool seg_ok(const TcOperand &op) {
-  if (op.nseg < 1 || op.nseg > kMaxSeg || op.seg[0].begin != 0) return false;
-  for (int q = 0; q < op.nseg; ++q) {
-    const TcSeg &sg = op.seg[q];
-    if (sg.begin % 8 || (q > 0 && sg.begin <= op.seg[q - 1].begin)) return false;
-    if (sg.ptr && (sg.ld % 8 || reinterpret_cast<uintptr_t>(sg.ptr) % 16)) return false;
-  }
-  return true;
 }
 
 }  // namespace
@@ -436,21 +437,20 @@ int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
       (e.C16 && (e.ld16 % 8 || reinterpret_cast<uintptr_t>(e.C16) % 16)) ||
       (e.D3 && (e.ld3 % 8 || reinterpret_cast<uintptr_t>(e.D3) % 16 || !e.mask || !e.amp || !e.att)))
     return set_error(GCNN_EINVAL, "tc gemm: N must be a multiple of 8 and outputs 16-byte aligned");
-  if ((!d.A.mn_major || !d.B.mn_major) && d.K % 8) return set_error(GCNN_EINVAL, "tc gemm: K must be a multiple of 8");
-  if (!seg_ok(d.A) || !seg_ok(d.B)) return set_error(GCNN_EINVAL, "tc gemm: bad operand segments");
-  for (int q = 0; q < d.B.nseg; ++q)
-    if (!d.B.seg[q].ptr) return set_error(GCNN_EINVAL, "tc gemm: B segments need data");
+  int BN, ntiles, splits;
+  const int ktiles = choose(d.M, d.N, d.K, ws.max_splits, &BN, &ntiles, &splits);
+  TcMaps maps;
+  GCNN_TRY(make_map(&maps.a, d.A, d.A.mn_major ? 64 : BM));
+  GCNN_TRY(make_map(&maps.b, d.B, d.B.mn_major ? 64 : BN));
   if (!g_configured) {
-    GCNN_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    GCNN_CUDA_TRY(cudaFuncSetAttribute(tma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     g_configured = 1;
   }
-  int BN, ntiles, splits;
-  const int ktiles = choose(d.M, d.N, d.K, &BN, &ntiles, &splits);
-  splits = std::min(splits, ws.max_splits);
   if (splits > 1 && (size_t)splits * d.M * d.N > ws.floats) splits = 1;
   const int kps = (ktiles + splits - 1) / splits * BK;
   dim3 grid(ntiles, (d.M + BM - 1) / BM, splits);
-  tc_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(d, dims, splits > 1 ? ws.partial : nullptr, splits, kps, BN, err);
+  tma_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, d, dims, splits > 1 ? ws.partial : nullptr, splits, kps, BN,
+                                                     err);
   GCNN_LAUNCH_CHECK();
   if (splits > 1) {
     const long long work = (long long)d.M * (d.N / 8);
@@ -462,7 +462,7 @@ int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
 
 size_t gemm_tc_workspace_floats(int M, int N, int K) {
   int BN, ntiles, splits;
-  choose(M, N, K, &BN, &ntiles, &splits);
+  choose(M, N, K, 32, &BN, &ntiles, &splits);
   return splits > 1 ? (size_t)splits * M * N : 0;
 }
 
@@ -474,11 +474,31 @@ __global__ void cast_bf16_kernel(int64_t n, const float *__restrict__ src, uint1
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n8; q += stride) {
     const float4 a = reinterpret_cast<const float4 *>(src)[2 * q], b = reinterpret_cast<const float4 *>(src)[2 * q + 1];
     reinterpret_cast<uint4 *>(dst)[q] =
-        make_uint4(pack_bf16(a.x, a.y), pack_bf16(a.z, a.w), pack_bf16(b.x, b.y), pack_bf16(b.z, b.w));
+        make_uint4(bf16x2(a.x, a.y), bf16x2(a.z, a.w), bf16x2(b.x, b.y), bf16x2(b.z, b.w));
   }
   if (blockIdx.x == 0 && threadIdx.x < (int)(n - 8 * n8)) {
     const int64_t k = 8 * n8 + threadIdx.x;
-    dst[k] = (uint16_t)(pack_bf16(src[k], 0.f) & 0xFFFFu);
+    dst[k] = (uint16_t)(bf16x2(src[k], 0.f) & 0xFFFFu);
+  }
+}
+
+// Per layer: Wd[n][s*H + c] = W_U[H + blk(s)*5H + n][c] with the scaler order
+// (amplification, attenuation, identity) of the backward operand;
+// Wx[n] = [W_U[n][0..H) | W_M[n][0..2H)].
+__global__ void pack_layer_kernel(int H, const float *__restrict__ msg_w, const float *__restrict__ upd_w,
+                                  uint16_t *__restrict__ Wd, uint16_t *__restrict__ Wx) {
+  const long long nd = 15LL * H * H, nx = 3LL * H * H;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nd) {
+    const int n = (int)(t / (3 * H)), k = (int)(t % (3 * H));
+    const int s = k / H, c = k % H;
+    const int blk = s == 0 ? 1 : (s == 1 ? 2 : 0);
+    Wd[t] = (uint16_t)(bf16x2(upd_w[(size_t)(H + blk * 5 * H + n) * H + c], 0.f) & 0xFFFFu);
+  } else if (t < nd + nx) {
+    const long long u = t - nd;
+    const int n = (int)(u / (3 * H)), k = (int)(u % (3 * H));
+    const float v = k < H ? upd_w[(size_t)n * H + k] : msg_w[(size_t)n * 2 * H + (k - H)];
+    Wx[u] = (uint16_t)(bf16x2(v, 0.f) & 0xFFFFu);
   }
 }
 }  // namespace
@@ -489,6 +509,13 @@ int launch_cast_bf16(int64_t n, const float *src, uint16_t *dst, cudaStream_t s)
     return set_error(GCNN_EINVAL, "cast: buffers must be 16-byte aligned");
   const int blocks = (int)std::min<int64_t>((n / 8 + 255) / 256 + 1, (int64_t)num_sms() * 8);
   cast_bf16_kernel<<<blocks, 256, 0, s>>>(n, src, dst);
+  GCNN_LAUNCH_CHECK();
+  return GCNN_OK;
+}
+
+int launch_pack_layer(int H, const float *msg_w, const float *upd_w, uint16_t *Wd, uint16_t *Wx, cudaStream_t s) {
+  const long long work = 18LL * H * H;
+  pack_layer_kernel<<<ceil_div(work, 256), 256, 0, s>>>(H, msg_w, upd_w, Wd, Wx);
   GCNN_LAUNCH_CHECK();
   return GCNN_OK;
 }

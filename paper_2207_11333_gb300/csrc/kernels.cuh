@@ -31,30 +31,31 @@ int launch_collate(int G, const int64_t *ids, StoreView st, BatchBuf b, const fl
 
 // ---------------------------------------------------------------- aggregate.cu
 // agg[i] = [sum, mean, min, max, std](P_i + Q_j, j in N(i)); PQ is N x 2H.
-// S16 (nullable, N x 15H BF16) additionally receives [agg, amp*agg, att*agg],
-// the scaled aggregates as the BF16 operand of the update GEMM.
+// S16 (nullable, row pitch ld16) additionally receives [agg, amp*agg, att*agg]
+// (15H BF16), the scaled aggregates as the BF16 operand of the update GEMM.
 int launch_aggregate_fwd(int n_nodes, int H, DevDims dims, const int *row_ptr, const int *col,
                          const float *PQ, float *agg, float eps, unsigned *err, cudaStream_t s,
-                         uint16_t *S16 = nullptr, const float *amp = nullptr, const float *att = nullptr);
+                         uint16_t *S16 = nullptr, int ld16 = 0, const float *amp = nullptr,
+                         const float *att = nullptr);
 // dPQ from dagg; scratch is E x H (per-edge message gradients).
 int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const int *row_ptr,
                          const int *col, const int *rev, const float *PQ, const float *agg,
                          const float *dagg, float *dPQ, float *scratch, float eps, unsigned *err,
-                         cudaStream_t s, uint16_t *dPQ16 = nullptr);
+                         cudaStream_t s, uint16_t *dPQ16 = nullptr, int ld16 = 0);
 
 // ---------------------------------------------------------------- small.cu
 int launch_embed(int n_nodes, int H, DevDims dims, const uint8_t *types, const float *emb,
-                 int n_types, float *x0, cudaStream_t s, uint16_t *x0_16 = nullptr);
+                 int n_types, float *x0, cudaStream_t s, uint16_t *x0_16 = nullptr, int ld16 = 0);
 // dEmb[t] = sum of dx0 over nodes of type t (deterministic two-stage sum).
 int launch_embed_bwd(int n_nodes, int H, DevDims dims, const uint8_t *types, const float *dx0,
                      int n_types, float *partial, int max_chunks, float *demb, cudaStream_t s);
 int launch_pool_fwd(int G, int H, DevDims dims, const int *node_off, const float *x, float *pooled,
                     cudaStream_t s);
-// D3 (nullable, N x 3H BF16) additionally receives [g, amp*g, att*g] with
-// g = dx * [h > 0] (the ReLU-masked, degree-scaled gradient of the last layer).
+// D3 (nullable, row pitch ld3) additionally receives [amp*g, att*g, g] (3H
+// BF16) with g = dx * [h > 0], the masked, degree-scaled gradient of the last layer.
 int launch_pool_bwd(int G, int n_nodes, int H, DevDims dims, const int *node_off,
                     const int *graph_id, const float *dpooled, float *dx, cudaStream_t s,
-                    uint16_t *D3 = nullptr, const float *h = nullptr, const float *amp = nullptr,
+                    uint16_t *D3 = nullptr, int ld3 = 0, const float *h = nullptr, const float *amp = nullptr,
                     const float *att = nullptr);
 // Head forward: z1 = g W1 + b1, pred = ReLU(z1) . w2 + b2.
 int launch_head_fwd(int G, int H, int Hh, DevDims dims, const float *g, const float *w1,
@@ -124,23 +125,17 @@ int run_splitk_reduce(const GemmDesc &d, DevDims dims, const float *partial, int
 int num_sms();
 
 // ---------------------------------------------------------------- gemm_tc.cu
-// C = A . B on the tensor cores: BF16 operands (stored as uint16_t bit
-// patterns), FP32 accumulation in TMEM.  Operands come from up to kMaxSeg
-// BF16 arrays along the feature dimension (ptr == nullptr: a constant-one
-// row, for bias gradients).
-struct TcSeg {
-  int begin;
+// C = A . B on the tensor cores (TMA + tcgen05): BF16 operands stored as
+// uint16_t bit patterns, FP32 accumulation in TMEM.  Each operand is one
+// row-major BF16 array of `rows` x `cols` with row pitch `ld`:
+//   A (M x K): mn_major false -> A(m,k) = ptr[m*ld + k] (rows = M, cols = K)
+//              mn_major true  -> A(m,k) = ptr[k*ld + m] (rows = K, cols = M)
+//   B (K x N): mn_major false -> B(k,n) = ptr[n*ld + k] (rows = N, cols = K)
+//              mn_major true  -> B(k,n) = ptr[k*ld + n] (rows = K, cols = N)
+// Reads past cols / rows return zero, so K may be padded up to 64.
+struct TcMat {
   const uint16_t *ptr;
-  int ld;
-};
-
-struct TcOperand {
-  TcSeg seg[kMaxSeg];
-  int nseg;
-  // A (M x K): false -> A(m,k) = ptr[m*ld + k - begin] (segments along K)
-  //            true  -> A(m,k) = ptr[k*ld + m - begin] (segments along M)
-  // B (K x N): false -> B(k,n) = ptr[n*ld + k - begin]
-  //            true  -> B(k,n) = ptr[(k - begin)*ld + n]  (segments along K)
+  int ld, rows, cols;
   bool mn_major;
 };
 
@@ -150,11 +145,10 @@ struct TcEpilogue {
   const float *bias;   // bias[n] for n < bias_n
   int bias_n;
   bool relu;
-  int last_row_cols;   // > 0: row M-1 keeps only its first last_row_cols columns
   uint16_t *C16;       // BF16 copy of the result (nullable)
   int ld16;
-  // [v*[mask>0], amp*v*[mask>0], att*v*[mask>0]] as BF16 into D3 (nullable):
-  // the masked, degree-scaled output gradient consumed by the next backward GEMMs
+  // [amp*g | att*g | g] as BF16 into D3 (nullable), g = v*[mask > 0]: the
+  // ReLU-masked, degree-scaled output gradient used by the next backward GEMMs
   uint16_t *D3;
   int ld3;
   const float *mask;
@@ -163,9 +157,9 @@ struct TcEpilogue {
 };
 
 struct TcDesc {
-  int M, N, K;
+  int M, N, K;         // K: multiple of 64 (padded) or, with node_dim == kNodeK, the node capacity
   NodeDim node_dim;
-  TcOperand A, B;
+  TcMat A, B;
   TcEpilogue ep;
 };
 
@@ -173,5 +167,13 @@ int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
 size_t gemm_tc_workspace_floats(int M, int N, int K);
 // dst[i] = bf16(src[i]) (round to nearest even)
 int launch_cast_bf16(int64_t n, const float *src, uint16_t *dst, cudaStream_t s);
+// BF16 weight layouts of one layer for the backward GEMMs (see gemm_tc.cu)
+int launch_pack_layer(int H, const float *msg_w, const float *upd_w, uint16_t *Wd, uint16_t *Wx, cudaStream_t s);
+// Column sums over the batch's nodes of [a0 * [mask > 0] | a1] (cols0 + cols1
+// columns; mask and a1 nullable) into out0[cols0] and out1[cols1];
+// deterministic two-stage sum.  partial holds ceil(n_cap / 32) * (cols0 +
+// cols1) floats.
+int launch_colsum2(int n_cap, int cols0, int cols1, DevDims dims, const float *a0, int ld0, const float *mask,
+                   int ldm, const float *a1, int ld1, float *partial, float *out0, float *out1, cudaStream_t s);
 
 }  // namespace gcnn

@@ -55,13 +55,32 @@ int tc(gcnn_ctx *c, const TcDesc &d) {
 bool bf16(const gcnn_ctx *c) { return c->cfg.precision == GCNN_PREC_BF16; }
 
 // BF16 views
-uint16_t *xb_at(const gcnn_ctx *c, int l) { return c->xb + (size_t)l * c->Nc * c->H; }
-uint16_t *sb_at(const gcnn_ctx *c, int l) {
-  return c->sb + (c->cfg.recompute ? 0 : (size_t)l * c->Nc * 15 * c->H);
+// [x_l | scaled aggregates] operand of layer l (one shared buffer with recompute)
+uint16_t *U_at(const gcnn_ctx *c, int l) {
+  return c->U + (c->cfg.recompute ? 0 : (size_t)l * c->Nc * 16 * c->H);
+}
+// BF16 layer input x_l: columns [0, H) of U_at(l), or its own buffer with recompute
+uint16_t *X_at(const gcnn_ctx *c, int l) {
+  return c->cfg.recompute ? c->Xb + (size_t)l * c->Nc * c->H : U_at(c, l);
+}
+int X_ld(const gcnn_ctx *c) { return c->cfg.recompute ? c->H : 16 * c->H; }
+
+// With recompute, place x_l in the first H columns of the shared U buffer.
+int stage_x(gcnn_ctx *c, int Ngrid, int l) {
+  if (!c->cfg.recompute) return GCNN_OK;
+  const size_t w = (size_t)c->H * sizeof(uint16_t);
+  GCNN_CUDA_TRY(cudaMemcpy2DAsync(U_at(c, l), 16 * w, X_at(c, l), w, w, (size_t)Ngrid, cudaMemcpyDeviceToDevice,
+                                  c->stream));
+  return GCNN_OK;
 }
 const uint16_t *wb_of(const gcnn_ctx *c, const float *p) { return c->wb + (p - c->params); }
+const uint16_t *Wd_at(const gcnn_ctx *c, int l) { return c->wpack + (size_t)l * 18 * c->H * c->H; }
+const uint16_t *Wx_at(const gcnn_ctx *c, int l) { return Wd_at(c, l) + (size_t)15 * c->H * c->H; }
+int pad64(int k) { return (k + 63) / 64 * 64; }
 
-TcSeg tseg(int begin, const uint16_t *ptr, int ld) { return TcSeg{begin, ptr, ld}; }
+TcMat mat(const uint16_t *ptr, int ld, int rows, int cols, bool mn_major) {
+  return TcMat{ptr, ld, rows, cols, mn_major};
+}
 
 TcDesc tblank() {
   TcDesc d{};
@@ -106,92 +125,85 @@ int tc_message(gcnn_ctx *c, int Ngrid, int l) {
   const int H = c->H;
   LayerW w = layer_ptrs(c->params, c, l);
   TcDesc d = tblank();
-  d.M = Ngrid; d.N = 2 * H; d.K = H; d.node_dim = kNodeM;
-  d.A.nseg = 1; d.A.seg[0] = tseg(0, xb_at(c, l), H); d.A.mn_major = false;
-  d.B.nseg = 1; d.B.seg[0] = tseg(0, wb_of(c, w.msg_w), 2 * H); d.B.mn_major = true;
+  d.M = Ngrid; d.N = 2 * H; d.K = pad64(H); d.node_dim = kNodeM;
+  d.A = mat(X_at(c, l), X_ld(c), Ngrid, H, false);
+  d.B = mat(wb_of(c, w.msg_w), 2 * H, H, 2 * H, true);
   d.ep.C = pq_at(c, l); d.ep.ldc = 2 * H; d.ep.bias = w.msg_b; d.ep.bias_n = H;
   return tc(c, d);
 }
 
-// BF16: x' = ReLU([x | agg | amp*agg | att*agg] W_U + b_U), also written as BF16
+// BF16: x' = ReLU([x | agg | amp*agg | att*agg] W_U + b_U), also written as
+// the BF16 input of the next layer
 int tc_update(gcnn_ctx *c, int Ngrid, int l) {
   const int H = c->H;
   LayerW w = layer_ptrs(c->params, c, l);
+  GCNN_TRY(stage_x(c, Ngrid, l));
   TcDesc d = tblank();
-  d.M = Ngrid; d.N = H; d.K = 16 * H; d.node_dim = kNodeM;
-  d.A.nseg = 2; d.A.seg[0] = tseg(0, xb_at(c, l), H); d.A.seg[1] = tseg(H, sb_at(c, l), 15 * H);
-  d.A.mn_major = false;
-  d.B.nseg = 1; d.B.seg[0] = tseg(0, wb_of(c, w.upd_w), H); d.B.mn_major = true;
+  d.M = Ngrid; d.N = H; d.K = pad64(16 * H); d.node_dim = kNodeM;
+  d.A = mat(U_at(c, l), 16 * H, Ngrid, 16 * H, false);
+  d.B = mat(wb_of(c, w.upd_w), H, 16 * H, H, true);
   d.ep.C = xs_at(c, l + 1); d.ep.ldc = H; d.ep.bias = w.upd_b; d.ep.bias_n = H; d.ep.relu = true;
-  if (l + 1 < c->L) { d.ep.C16 = xb_at(c, l + 1); d.ep.ld16 = H; }
+  if (l + 1 < c->L) { d.ep.C16 = X_at(c, l + 1); d.ep.ld16 = X_ld(c); }
   return tc(c, d);
 }
 
-// BF16 backward of layer l; dH holds dL/dx_{l+1} and d3[cur] its masked,
-// scaled BF16 form.  Writes dX = dL/dx_l and, for l > 0, d3[cur ^ 1].
+// BF16 backward of layer l.  dH holds dL/dx_{l+1} (FP32) and G5[cur] its
+// masked, scaled BF16 form in columns [0, 3H).  Writes dX = dL/dx_l and, for
+// l > 0, columns [0, 3H) of G5[cur ^ 1].
 int tc_backward_layer(gcnn_ctx *c, int Ngrid, int Egrid, int l, int cur) {
   const int H = c->H;
   DevDims dims{c->bb.dims};
-  LayerW w = layer_ptrs(c->params, c, l);
   LayerW gw = layer_ptrs(c->grads, c, l);
-  const float *pq = pq_at(c, l);
+  const float *pq = pq_at(c, l), *h = xs_at(c, l + 1);
   float *agg = agg_at(c, l);
-  const uint16_t *d3 = c->d3[cur];
+  uint16_t *G = c->G5[cur];
   if (c->cfg.recompute) {
     PhaseScope ps(c, GCNN_PHASE_AGG_FWD);
     GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq, agg, (float)c->cfg.std_eps, c->err,
-                                  c->stream, sb_at(c, l), c->bb.amp, c->bb.att));
+                                  c->stream, U_at(c, l) + H, 16 * H, c->bb.amp, c->bb.att));
+    GCNN_TRY(stage_x(c, Ngrid, l));
   }
-  {  // dW_U, db_U = [x | scaled aggs | 1]^T dpre
+  {  // dW_U = [x | scaled aggs]^T dpre ; db_U = column sums of dpre
     TcDesc d = tblank();
-    d.M = 16 * H + 1; d.N = H; d.K = Ngrid; d.node_dim = kNodeK;
-    d.A.nseg = 3; d.A.mn_major = true;
-    d.A.seg[0] = tseg(0, xb_at(c, l), H);
-    d.A.seg[1] = tseg(H, sb_at(c, l), 15 * H);
-    d.A.seg[2] = tseg(16 * H, nullptr, 0);
-    d.B.nseg = 1; d.B.seg[0] = tseg(0, d3, 3 * H); d.B.mn_major = true;
+    d.M = 16 * H; d.N = H; d.K = Ngrid; d.node_dim = kNodeK;
+    d.A = mat(U_at(c, l), 16 * H, Ngrid, 16 * H, true);
+    d.B = mat(G + 2 * H, 5 * H, Ngrid, H, true);
     d.ep.C = gw.upd_w; d.ep.ldc = H;
     GCNN_TRY(tc(c, d));
   }
-  {  // dagg = [dpre | amp dpre | att dpre] [W_id ; W_amp ; W_att]^T
+  {  // dagg = [amp g | att g | g] [W_amp ; W_att ; W_id]^T
     TcDesc d = tblank();
-    d.M = Ngrid; d.N = kAgg * H; d.K = 3 * H; d.node_dim = kNodeM;
-    d.A.nseg = 1; d.A.seg[0] = tseg(0, d3, 3 * H); d.A.mn_major = false;
-    const uint16_t *wu = wb_of(c, w.upd_w);
-    d.B.nseg = 3; d.B.mn_major = false;
-    d.B.seg[0] = tseg(0, wu + (size_t)H * H, H);
-    d.B.seg[1] = tseg(H, wu + (size_t)6 * H * H, H);
-    d.B.seg[2] = tseg(2 * H, wu + (size_t)11 * H * H, H);
+    d.M = Ngrid; d.N = kAgg * H; d.K = pad64(3 * H); d.node_dim = kNodeM;
+    d.A = mat(G, 5 * H, Ngrid, 3 * H, false);
+    d.B = mat(Wd_at(c, l), 3 * H, kAgg * H, 3 * H, false);
     d.ep.C = c->dagg; d.ep.ldc = kAgg * H;
     GCNN_TRY(tc(c, d));
   }
   {
     PhaseScope ps(c, GCNN_PHASE_AGG_BWD);
     GCNN_TRY(launch_aggregate_bwd(Ngrid, Egrid, H, dims, c->bb.row_ptr, c->bb.col, c->bb.rev, pq, agg, c->dagg,
-                                  c->dPQ, c->dm, (float)c->cfg.std_eps, c->err, c->stream, c->pqb));
+                                  c->dPQ, c->dm, (float)c->cfg.std_eps, c->err, c->stream, G + 3 * H, 5 * H));
   }
-  {  // dW_M, db_M = [x | 1]^T dPQ
+  {  // dW_M = x^T [dP | dQ] ; db_M = column sums of dP
     TcDesc d = tblank();
-    d.M = H + 1; d.N = 2 * H; d.K = Ngrid; d.node_dim = kNodeK;
-    d.A.nseg = 2; d.A.mn_major = true;
-    d.A.seg[0] = tseg(0, xb_at(c, l), H);
-    d.A.seg[1] = tseg(H, nullptr, 0);
-    d.B.nseg = 1; d.B.seg[0] = tseg(0, c->pqb, 2 * H); d.B.mn_major = true;
-    d.ep.C = gw.msg_w; d.ep.ldc = 2 * H; d.ep.last_row_cols = H;
+    d.M = H; d.N = 2 * H; d.K = Ngrid; d.node_dim = kNodeK;
+    d.A = mat(X_at(c, l), X_ld(c), Ngrid, H, true);
+    d.B = mat(G + 3 * H, 5 * H, Ngrid, 2 * H, true);
+    d.ep.C = gw.msg_w; d.ep.ldc = 2 * H;
     GCNN_TRY(tc(c, d));
+    // bias gradients: db_U = sum of dpre, db_M = sum of dP (FP32, fixed order)
+    PhaseScope ps(c, GCNN_PHASE_GEMM);
+    GCNN_TRY(launch_colsum2(Ngrid, H, H, dims, c->dH, H, h, H, c->dPQ, 2 * H, c->colsum_partial, gw.upd_b, gw.msg_b,
+                            c->stream));
   }
-  {  // dx = dpre W_x^T + [dP | dQ] [A | B]^T ; next layer's masked, scaled BF16 gradient
+  {  // dx = [g | dP | dQ] [W_x | A | B]^T ; the next layer's masked, scaled BF16 gradient
     TcDesc d = tblank();
-    d.M = Ngrid; d.N = H; d.K = 3 * H; d.node_dim = kNodeM;
-    d.A.nseg = 2; d.A.mn_major = false;
-    d.A.seg[0] = tseg(0, d3, 3 * H);
-    d.A.seg[1] = tseg(H, c->pqb, 2 * H);
-    d.B.nseg = 2; d.B.mn_major = false;
-    d.B.seg[0] = tseg(0, wb_of(c, w.upd_w), H);
-    d.B.seg[1] = tseg(H, wb_of(c, w.msg_w), 2 * H);
+    d.M = Ngrid; d.N = H; d.K = pad64(3 * H); d.node_dim = kNodeM;
+    d.A = mat(G + 2 * H, 5 * H, Ngrid, 3 * H, false);
+    d.B = mat(Wx_at(c, l), 3 * H, H, 3 * H, false);
     d.ep.C = c->dX; d.ep.ldc = H;
     if (l > 0) {
-      d.ep.D3 = c->d3[cur ^ 1]; d.ep.ld3 = 3 * H;
+      d.ep.D3 = c->G5[cur ^ 1]; d.ep.ld3 = 5 * H;
       d.ep.mask = xs_at(c, l); d.ep.ldm = H; d.ep.amp = c->bb.amp; d.ep.att = c->bb.att;
     }
     GCNN_TRY(tc(c, d));
@@ -231,7 +243,7 @@ int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train) {
   {
     PhaseScope ps(c, GCNN_PHASE_EMBED);
     GCNN_TRY(launch_embed(Ngrid, H, dims, c->bb.types, c->params, c->T, xs_at(c, 0), c->stream,
-                          bf ? xb_at(c, 0) : nullptr));
+                          bf ? X_at(c, 0) : nullptr, X_ld(c)));
   }
   for (int l = 0; l < c->L; ++l) {
     if (bf) GCNN_TRY(tc_message(c, Ngrid, l));
@@ -239,8 +251,8 @@ int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train) {
     {
       PhaseScope ps(c, GCNN_PHASE_AGG_FWD);
       GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq_at(c, l), agg_at(c, l),
-                                    (float)c->cfg.std_eps, c->err, c->stream, bf ? sb_at(c, l) : nullptr,
-                                    c->bb.amp, c->bb.att));
+                                    (float)c->cfg.std_eps, c->err, c->stream, bf ? U_at(c, l) + H : nullptr,
+                                    16 * H, c->bb.amp, c->bb.att));
     }
     if (bf) GCNN_TRY(tc_update(c, Ngrid, l));
     else GCNN_TRY(gemm_update(c, Ngrid, l));
@@ -266,7 +278,7 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
   GCNN_TRY(launch_head_bwd(G, H, c->Hh, dims, c->pooled, hp, hp + HHh + c->Hh, c->z1, c->pred,
                            c->bb.y, dpred, c->dpred, c->dz1, ghp, c->dg, loss_accum, c->stream));
   GCNN_TRY(launch_pool_bwd(G, Ngrid, H, dims, c->bb.node_off, c->bb.graph_id, c->dg, c->dH, c->stream,
-                           bf16(c) ? c->d3[0] : nullptr, xs_at(c, c->L), c->bb.amp, c->bb.att));
+                           bf16(c) ? c->G5[0] : nullptr, 5 * H, xs_at(c, c->L), c->bb.amp, c->bb.att));
   }
   if (bf16(c)) {
     int cur = 0;
@@ -362,7 +374,18 @@ int ctx_step(gcnn_ctx *c) {
   GCNN_TRY(launch_adam(c->P, c->params, c->grads, c->adam_m, c->adam_v, c->opt_state, c->lr_dev,
                        (float)c->cfg.beta1, (float)c->cfg.beta2, (float)c->cfg.adam_eps,
                        (float)c->cfg.weight_decay, c->stream));
-  if (c->wb) GCNN_TRY(launch_cast_bf16(c->P, c->params, c->wb, c->stream));
+  if (c->wb) GCNN_TRY(ctx_refresh_bf16(c));
+  return GCNN_OK;
+}
+
+int ctx_refresh_bf16(gcnn_ctx *c) {
+  if (!c->wb) return GCNN_OK;
+  GCNN_TRY(launch_cast_bf16(c->P, c->params, c->wb, c->stream));
+  for (int l = 0; l < c->L; ++l) {
+    LayerW w = layer_ptrs(c->params, c, l);
+    uint16_t *wd = c->wpack + (size_t)l * 18 * c->H * c->H;
+    GCNN_TRY(launch_pack_layer(c->H, w.msg_w, w.upd_w, wd, wd + (size_t)15 * c->H * c->H, c->stream));
+  }
   return GCNN_OK;
 }
 

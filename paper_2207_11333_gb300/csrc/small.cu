@@ -4,6 +4,8 @@
 // gradient, and the AdamW update (Sec. 3.2; Sec. 5.1 uses AdamW, lr 1e-3).
 // All reductions run in a fixed order (no atomics), so results are
 // bit-reproducible run to run.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace gcnn {
@@ -17,7 +19,7 @@ __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<floa
 // ---------------------------------------------------------------- embedding
 __global__ void embed_kernel(int n_cap, int H, DevDims dims, const uint8_t *__restrict__ types,
                              const float *__restrict__ emb, int T, float *__restrict__ x0,
-                             uint16_t *__restrict__ x0_16) {
+                             uint16_t *__restrict__ x0_16, int ld16) {
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -26,10 +28,10 @@ __global__ void embed_kernel(int n_cap, int H, DevDims dims, const uint8_t *__re
   const int ty = types[i];
   const float4 v = ty < T ? ld4(emb + (size_t)ty * H + c) : make_float4(0.f, 0.f, 0.f, 0.f);
   st4(x0 + (size_t)i * H + c, v);
-  if (x0_16) st_bf16x4(x0_16 + (size_t)i * H + c, v.x, v.y, v.z, v.w);
+  if (x0_16) st_bf16x4(x0_16 + (size_t)i * ld16 + c, v.x, v.y, v.z, v.w);
 }
 
-constexpr int kEmbChunk = 64;   // nodes per partial sum
+constexpr int kEmbChunk = 16;   // nodes per partial sum
 constexpr int kMaxTypes = 16;
 
 // partial[ch][t][c] = sum over nodes of chunk ch with type t of dx0[., c]
@@ -93,7 +95,7 @@ __global__ void pool_fwd_kernel(int g_cap, int H, DevDims dims, const int *__res
 
 __global__ void pool_bwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ node_off,
                                 const int *__restrict__ graph_id, const float *__restrict__ dpooled,
-                                float *__restrict__ dx, uint16_t *__restrict__ D3, const float *__restrict__ h,
+                                float *__restrict__ dx, uint16_t *__restrict__ D3, int ld3, const float *__restrict__ h,
                                 const float *__restrict__ amp, const float *__restrict__ att) {
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
@@ -110,10 +112,10 @@ __global__ void pool_bwd_kernel(int n_cap, int H, DevDims dims, const int *__res
     const float gx = m.x > 0.f ? d.x : 0.f, gy = m.y > 0.f ? d.y : 0.f;
     const float gz = m.z > 0.f ? d.z : 0.f, gw = m.w > 0.f ? d.w : 0.f;
     const float a = amp[i], t = att[i];
-    uint16_t *o = D3 + (size_t)i * 3 * H + c;
-    st_bf16x4(o, gx, gy, gz, gw);
-    st_bf16x4(o + H, a * gx, a * gy, a * gz, a * gw);
-    st_bf16x4(o + 2 * H, t * gx, t * gy, t * gz, t * gw);
+    uint16_t *o = D3 + (size_t)i * ld3 + c;
+    st_bf16x4(o, a * gx, a * gy, a * gz, a * gw);
+    st_bf16x4(o + H, t * gx, t * gy, t * gz, t * gw);
+    st_bf16x4(o + 2 * H, gx, gy, gz, gw);
   }
 }
 
@@ -158,8 +160,14 @@ head_fwd_kernel(int g_cap, int H, int Hh, DevDims dims, const float *__restrict_
   __syncthreads();
   float part = 0.f;
   for (int c = threadIdx.x; c < Hh; c += blockDim.x) {
-    float acc = b1[c];
-    for (int k = 0; k < H; ++k) acc += sg[k] * w1[(size_t)k * Hh + c];
+    float a[4] = {b1[c], 0.f, 0.f, 0.f};  // four independent chains, summed in a fixed order
+    int k = 0;
+    for (; k + 4 <= H; k += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] += sg[k + u] * w1[(size_t)(k + u) * Hh + c];
+    }
+    for (; k < H; ++k) a[0] += sg[k] * w1[(size_t)k * Hh + c];
+    const float acc = (a[0] + a[1]) + (a[2] + a[3]);
     z1[(size_t)gr * Hh + c] = acc;
     part += fmaxf(acc, 0.f) * w2[c];
   }
@@ -167,13 +175,11 @@ head_fwd_kernel(int g_cap, int H, int Hh, DevDims dims, const float *__restrict_
   if (threadIdx.x == 0) pred[gr] = s + b2[0];
 }
 
-// one block: dL/dpred, loss sums, grad b2, dz1
+// one block: dL/dpred, the loss sums and the gradient of b2 (G values)
 __global__ void __launch_bounds__(kThreads)
-head_bwd_loss_kernel(int g_cap, int Hh, DevDims dims, const float *__restrict__ w2,
-                     const float *__restrict__ z1, const float *__restrict__ pred,
-                     const float *__restrict__ y, const float *__restrict__ dpred_in,
-                     float *__restrict__ dpred, float *__restrict__ dz1,
-                     float *__restrict__ grad_b2, double *__restrict__ loss_accum) {
+head_bwd_loss_kernel(int g_cap, DevDims dims, const float *__restrict__ pred, const float *__restrict__ y,
+                     const float *__restrict__ dpred_in, float *__restrict__ dpred, float *__restrict__ grad_b2,
+                     double *__restrict__ loss_accum) {
   __shared__ double redd[kThreads / 32];
   __shared__ float redf[kThreads / 32];
   const int G = min(g_cap, dims.graphs(g_cap));
@@ -198,32 +204,39 @@ head_bwd_loss_kernel(int g_cap, int Hh, DevDims dims, const float *__restrict__ 
       loss_accum[2] += (double)G;
     }
   }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < G * Hh; idx += blockDim.x) {
-    const int gr = idx / Hh, c = idx % Hh;
-    dz1[idx] = z1[idx] > 0.f ? dpred[gr] * w2[c] : 0.f;
-  }
 }
 
 // grads of w1 (H x Hh), b1, w2 and dg (G x H): one thread per output, sums
-// over graphs / head units in a fixed order
+// over graphs / head units in a fixed order; dz1 = [z1 > 0] dpred w2 inline
 __global__ void __launch_bounds__(kThreads)
 head_bwd_grad_kernel(int g_cap, int H, int Hh, DevDims dims, const float *__restrict__ g,
-                     const float *__restrict__ w1, const float *__restrict__ z1,
-                     const float *__restrict__ dpred, const float *__restrict__ dz1,
-                     float *__restrict__ grad_head, float *__restrict__ dg) {
+                     const float *__restrict__ w1, const float *__restrict__ w2, const float *__restrict__ z1,
+                     const float *__restrict__ dpred, float *__restrict__ grad_head, float *__restrict__ dg) {
   const int G = min(g_cap, dims.graphs(g_cap));
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long n_w1 = (long long)H * Hh;
   if (idx < n_w1) {
     const int k = (int)(idx / Hh), c = (int)(idx % Hh);
-    float s = 0.f;
-    for (int gr = 0; gr < G; ++gr) s += g[(size_t)gr * H + k] * dz1[(size_t)gr * Hh + c];
-    grad_head[idx] = s;
+    const float wc = w2[c];
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    int gr = 0;
+    for (; gr + 4 <= G; gr += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float z = z1[(size_t)(gr + u) * Hh + c];
+        a[u] += z > 0.f ? g[(size_t)(gr + u) * H + k] * (dpred[gr + u] * wc) : 0.f;
+      }
+    }
+    for (; gr < G; ++gr) {
+      const float z = z1[(size_t)gr * Hh + c];
+      a[0] += z > 0.f ? g[(size_t)gr * H + k] * (dpred[gr] * wc) : 0.f;
+    }
+    grad_head[idx] = (a[0] + a[1]) + (a[2] + a[3]);
   } else if (idx < n_w1 + Hh) {
     const int c = (int)(idx - n_w1);
+    const float wc = w2[c];
     float s = 0.f;
-    for (int gr = 0; gr < G; ++gr) s += dz1[(size_t)gr * Hh + c];
+    for (int gr = 0; gr < G; ++gr) s += z1[(size_t)gr * Hh + c] > 0.f ? dpred[gr] * wc : 0.f;
     grad_head[idx] = s;
   } else if (idx < n_w1 + 2 * Hh) {
     const int c = (int)(idx - n_w1 - Hh);
@@ -234,9 +247,21 @@ head_bwd_grad_kernel(int g_cap, int H, int Hh, DevDims dims, const float *__rest
     const long long r = idx - n_w1 - 2 * Hh;
     const int gr = (int)(r / H), k = (int)(r % H);
     if (gr >= G) return;
-    float s = 0.f;
-    for (int c = 0; c < Hh; ++c) s += w1[(size_t)k * Hh + c] * dz1[(size_t)gr * Hh + c];
-    dg[(size_t)gr * H + k] = s;
+    const float dp = dpred[gr];
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    int c = 0;
+    for (; c + 4 <= Hh; c += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float z = z1[(size_t)gr * Hh + c + u];
+        a[u] += z > 0.f ? w1[(size_t)k * Hh + c + u] * (dp * w2[c + u]) : 0.f;
+      }
+    }
+    for (; c < Hh; ++c) {
+      const float z = z1[(size_t)gr * Hh + c];
+      a[0] += z > 0.f ? w1[(size_t)k * Hh + c] * (dp * w2[c]) : 0.f;
+    }
+    dg[(size_t)gr * H + k] = (a[0] + a[1]) + (a[2] + a[3]);
   }
 }
 
@@ -282,13 +307,79 @@ adam_kernel(int64_t n, float *__restrict__ p, const float *__restrict__ g, float
   }
 }
 
+constexpr int kColChunk = 32;  // nodes per partial column sum
+
+// Column c < cols of the virtual matrix [a0 * [mask > 0] | a1] (a1 nullable):
+// partial[ch][c] = sum over the nodes of chunk ch.
+__global__ void colsum_partial_kernel(int n_cap, int cols0, int cols1, DevDims dims, const float *__restrict__ a0,
+                                      int ld0, const float *__restrict__ mask, int ldm, const float *__restrict__ a1,
+                                      int ld1, float *__restrict__ partial) {
+  const int N = min(n_cap, dims.nodes(n_cap));
+  const int cols = cols0 + cols1;
+  const int ch = blockIdx.y;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  const int i0 = ch * kColChunk;
+  float v[kColChunk];
+#pragma unroll
+  for (int q = 0; q < kColChunk; ++q) {
+    const int i = i0 + q;
+    float x = 0.f;
+    if (i < N) {
+      if (c < cols0) {
+        x = a0[(size_t)i * ld0 + c];
+        if (mask && !(mask[(size_t)i * ldm + c] > 0.f)) x = 0.f;
+      } else {
+        x = a1[(size_t)i * ld1 + (c - cols0)];
+      }
+    }
+    v[q] = x;
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int q = 0; q < kColChunk; ++q) sum += v[q];
+  partial[(size_t)ch * cols + c] = sum;
+}
+
+__global__ void colsum_reduce_kernel(int n_cap, int cols0, int cols1, DevDims dims, const float *__restrict__ partial,
+                                     float *__restrict__ out0, float *__restrict__ out1) {
+  const int N = min(n_cap, dims.nodes(n_cap));
+  const int cols = cols0 + cols1;
+  const int chunks = (N + kColChunk - 1) / kColChunk;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  float a[4] = {0.f, 0.f, 0.f, 0.f};
+  int ch = 0;
+  for (; ch + 4 <= chunks; ch += 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) a[u] += partial[(size_t)(ch + u) * cols + c];
+  }
+  for (; ch < chunks; ++ch) a[0] += partial[(size_t)ch * cols + c];
+  const float s = (a[0] + a[1]) + (a[2] + a[3]);
+  if (c < cols0) out0[c] = s;
+  else out1[c - cols0] = s;
+}
+
 }  // namespace
 
+int launch_colsum2(int n_cap, int cols0, int cols1, DevDims dims, const float *a0, int ld0, const float *mask,
+                   int ldm, const float *a1, int ld1, float *partial, float *out0, float *out1, cudaStream_t s) {
+  const int cols = cols0 + cols1;
+  if (cols <= 0) return GCNN_OK;
+  const int chunks = (int)ceil_div(std::max(n_cap, 1), kColChunk);
+  dim3 grid(ceil_div(cols, 128), chunks);
+  colsum_partial_kernel<<<grid, 128, 0, s>>>(n_cap, cols0, cols1, dims, a0, ld0, mask, ldm, a1, ld1, partial);
+  GCNN_LAUNCH_CHECK();
+  colsum_reduce_kernel<<<ceil_div(cols, 128), 128, 0, s>>>(n_cap, cols0, cols1, dims, partial, out0, out1);
+  GCNN_LAUNCH_CHECK();
+  return GCNN_OK;
+}
+
 int launch_embed(int n_nodes, int H, DevDims dims, const uint8_t *types, const float *emb,
-                 int n_types, float *x0, cudaStream_t s, uint16_t *x0_16) {
+                 int n_types, float *x0, cudaStream_t s, uint16_t *x0_16, int ld16) {
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
-  embed_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(n_nodes, H, dims, types, emb, n_types, x0, x0_16);
+  embed_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(n_nodes, H, dims, types, emb, n_types, x0, x0_16, ld16);
   GCNN_LAUNCH_CHECK();
   return GCNN_OK;
 }
@@ -321,12 +412,12 @@ int launch_pool_fwd(int G, int H, DevDims dims, const int *node_off, const float
 
 int launch_pool_bwd(int G, int n_nodes, int H, DevDims dims, const int *node_off,
                     const int *graph_id, const float *dpooled, float *dx, cudaStream_t s, uint16_t *D3,
-                    const float *h, const float *amp, const float *att) {
+                    int ld3, const float *h, const float *amp, const float *att) {
   (void)G;
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
   pool_bwd_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(n_nodes, H, dims, node_off, graph_id,
-                                                                 dpooled, dx, D3, h, amp, att);
+                                                                 dpooled, dx, D3, ld3, h, amp, att);
   GCNN_LAUNCH_CHECK();
   return GCNN_OK;
 }
@@ -344,13 +435,13 @@ int launch_head_bwd(int G, int H, int Hh, DevDims dims, const float *g, const fl
                     const float *w2, const float *z1, const float *pred, const float *y,
                     const float *dpred_in, float *dpred, float *dz1, float *grad_head, float *dg,
                     double *loss_accum, cudaStream_t s) {
+  (void)dz1;
   float *grad_b2 = grad_head + (size_t)H * Hh + 2 * Hh;
-  head_bwd_loss_kernel<<<1, kThreads, 0, s>>>(G, Hh, dims, w2, z1, pred, y, dpred_in, dpred, dz1,
-                                              grad_b2, loss_accum);
+  head_bwd_loss_kernel<<<1, kThreads, 0, s>>>(G, dims, pred, y, dpred_in, dpred, grad_b2, loss_accum);
   GCNN_LAUNCH_CHECK();
   const long long work = (long long)H * Hh + 2 * Hh + (long long)G * H;
-  head_bwd_grad_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(G, H, Hh, dims, g, w1, z1, dpred,
-                                                                      dz1, grad_head, dg);
+  head_bwd_grad_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(G, H, Hh, dims, g, w1, w2, z1, dpred,
+                                                                      grad_head, dg);
   GCNN_LAUNCH_CHECK();
   return GCNN_OK;
 }
