@@ -52,8 +52,8 @@ def dataset():
     return gs
 
 
-def epoch_order(rank: int = 0) -> np.ndarray:
-    return np.random.default_rng(SEED_ORDER + 1000 * rank).permutation(N_TRAIN).astype(np.int64)
+def epoch_order(epoch: int = 0) -> np.ndarray:
+    return np.random.default_rng(SEED_ORDER + 1000 * epoch).permutation(N_TRAIN).astype(np.int64)
 
 
 def gemm_flops(n_nodes: int) -> float:
@@ -236,7 +236,7 @@ def measured_peaks():
 class Workload:
     """The 200k-graph store (device-resident), its teacher targets, the epoch order, capacities."""
 
-    def __init__(self, g, rank: int):
+    def __init__(self, g, rank: int, world: int = 1):
         gs = dataset()
         self.tmp = tempfile.mkdtemp(prefix="gcnn_bench_")
         self.path = os.path.join(self.tmp, "train.gcnn")
@@ -246,8 +246,10 @@ class Workload:
         self.delta = self.st.delta(np.arange(N_TRAIN))
         self.y = make_targets(g, self.st, self.delta, N_TRAIN + N_HELDOUT)
         self.st.set_targets(self.y)
-        self.order = epoch_order(rank)
-        self.nb = (N_TRAIN + BATCH - 1) // BATCH
+        # replicas take disjoint shards of one seeded epoch order
+        self.order = np.ascontiguousarray(epoch_order(0)[rank::world])
+        self.n_train = len(self.order)
+        self.nb = (self.n_train + BATCH - 1) // BATCH
         sizes = [self.st.batch_size(self.order[i * BATCH:(i + 1) * BATCH]) for i in range(self.nb)]
         self.Nc = (max(s[0] for s in sizes) + 255) // 256 * 256
         self.Ec = (max(s[1] for s in sizes) + 511) // 512 * 512
@@ -263,7 +265,7 @@ def make_ctx(g, wl: Workload, precision: str):
 
 def batch_at(ctx, wl: Workload, k: int):
     i = k % wl.nb
-    return ctx.collate_range(wl.st, i * BATCH, min(BATCH, N_TRAIN - i * BATCH))
+    return ctx.collate_range(wl.st, i * BATCH, min(BATCH, wl.n_train - i * BATCH))
 
 
 def timed_steps(ctx, wl, steps, warmup, flush, loss_acc, dist=None, gpu_index=None):
@@ -590,7 +592,7 @@ def run_ours(args):
     import paper_2207_11333_gb300 as g
 
     t_setup = time.perf_counter()
-    wl = Workload(g, rank)
+    wl = Workload(g, rank, world)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > 129 MB L2
     loss_acc = torch.zeros(3, dtype=torch.float64, device="cuda")
     log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s, capacity N={wl.Nc} E={wl.Ec}, delta={wl.delta:.6f}")

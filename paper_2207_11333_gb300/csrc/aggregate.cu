@@ -6,8 +6,8 @@
 // W_M), so the per-edge message never has to be stored: the forward kernel
 // gathers Q rows over each destination's CSR row and reduces them on the fly.
 //
-// Forward:  one thread per (node, 4 channels); FP32; two passes over the row
-//           (the second re-reads Q rows from L1) for a two-pass variance.
+// Forward:  one thread per (node, 4 channels); FP32; the row's messages stay
+//           in registers (first 4 edges) for the two-pass variance.
 // Backward: kernel 1, one thread per (node i, 4 channels), recomputes m_ij,
 //           routes dagg to every edge (sum: 1, mean: 1/d, min/max: shared
 //           equally among exact ties, std: (m - mean) / (d std)), writes
@@ -32,28 +32,32 @@ __device__ __forceinline__ float4 add4(float4 a, float4 b) {
   return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
 
-// Sum of squared deviations from `mean` over the row (second pass).
-__device__ __forceinline__ float4 sq_dev(const float *__restrict__ PQ, const int *__restrict__ col,
-                                         int r0, int r1, int H, int c, float4 P, float4 mean) {
-  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int e = r0; e < r1; ++e) {
-    const float4 m = add4(P, ld4(PQ + (size_t)col[e] * 2 * H + H + c));
-    const float tx = m.x - mean.x, ty = m.y - mean.y, tz = m.z - mean.z, tw = m.w - mean.w;
-    v.x += tx * tx; v.y += ty * ty; v.z += tz * tz; v.w += tw * tw;
+// Messages of a row are kept in registers for its first kCache edges (the
+// degree of a molecule's atom is at most 4 in practice), so each Q row is
+// gathered once per pass structure; longer rows re-read the tail.
+constexpr int kCache = 4;
+
+// source of edge e, or -1 (and the error flag) when it is out of range
+__device__ __forceinline__ int source(const int *__restrict__ col, int e, int N, unsigned *err) {
+  const int j = col[e];
+  if (j < 0 || j >= N) {
+    flag(err, kErrIndex);
+    return -1;
   }
-  return v;
+  return j;
 }
 
-// true iff every source index of the row is in [0, N)
-__device__ __forceinline__ bool row_ok(const int *__restrict__ col, int r0, int r1, int N) {
-  for (int e = r0; e < r1; ++e) {
-    const int j = col[e];
-    if (j < 0 || j >= N) return false;
-  }
-  return true;
+// m_ij = P_i + Q_j for the 4 channels at c (Q taken as 0 for an invalid source)
+__device__ __forceinline__ float4 message(const float *__restrict__ PQ, int j, int H, int c, float4 P) {
+  return j >= 0 ? add4(P, ld4(PQ + (size_t)j * 2 * H + H + c)) : P;
 }
 
-__global__ void __launch_bounds__(kThreads)
+__device__ __forceinline__ void acc_sq(float4 &v, float4 m, float4 mean) {
+  const float tx = m.x - mean.x, ty = m.y - mean.y, tz = m.z - mean.z, tw = m.w - mean.w;
+  v.x += tx * tx; v.y += ty * ty; v.z += tz * tz; v.w += tw * tw;
+}
+
+__global__ void __launch_bounds__(kThreads, 4)
 aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row_ptr,
                      const int *__restrict__ col, const float *__restrict__ PQ,
                      float *__restrict__ agg, float eps, unsigned *err, uint16_t *__restrict__ S16, int ld16,
@@ -64,10 +68,11 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
   if (t >= (long long)N * H4) return;
   const int i = (int)(t / H4), c = (int)(t % H4) * 4;
   const int r0 = row_ptr[i], r1 = row_ptr[i + 1];
+  const int d = r1 - r0;
   float *out = agg + (size_t)i * kAgg * H + c;
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (r1 <= r0 || !row_ok(col, r0, r1, N)) {
-    if (r1 < r0 || !row_ok(col, r0, r1, N)) flag(err, kErrIndex);
+  if (d <= 0 || r0 < 0) {
+    if (d < 0 || r0 < 0) flag(err, kErrIndex);
 #pragma unroll
     for (int a = 0; a < kAgg; ++a) st4(out + a * H, z);
     if (S16)
@@ -78,34 +83,46 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
   float4 s = z;
   float4 mn = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX);
   float4 mx = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX);
-  for (int e = r0; e < r1; ++e) {
-    const float4 m = add4(P, ld4(PQ + (size_t)col[e] * 2 * H + H + c));
+  float4 mc[kCache];
+  auto take = [&](float4 m) {
     s = add4(s, m);
     mn.x = fminf(mn.x, m.x); mn.y = fminf(mn.y, m.y); mn.z = fminf(mn.z, m.z); mn.w = fminf(mn.w, m.w);
     mx.x = fmaxf(mx.x, m.x); mx.y = fmaxf(mx.y, m.y); mx.z = fmaxf(mx.z, m.z); mx.w = fmaxf(mx.w, m.w);
+  };
+#pragma unroll
+  for (int k = 0; k < kCache; ++k) {
+    if (k < d) {
+      mc[k] = message(PQ, source(col, r0 + k, N, err), H, c, P);
+      take(mc[k]);
+    }
   }
-  const float d = (float)(r1 - r0);
-  const float4 mean = make_float4(s.x / d, s.y / d, s.z / d, s.w / d);
-  const float4 v = sq_dev(PQ, col, r0, r1, H, c, P, mean);
+  for (int e = r0 + kCache; e < r1; ++e) take(message(PQ, source(col, e, N, err), H, c, P));
+  const float df = (float)d;
+  const float4 mean = make_float4(s.x / df, s.y / df, s.z / df, s.w / df);
+  float4 v = z;  // two-pass variance
+#pragma unroll
+  for (int k = 0; k < kCache; ++k)
+    if (k < d) acc_sq(v, mc[k], mean);
+  for (int e = r0 + kCache; e < r1; ++e) acc_sq(v, message(PQ, source(col, e, N, err), H, c, P), mean);
   float4 sd;
-  sd.x = sqrtf(fmaxf(v.x / d, 0.f) + eps);
-  sd.y = sqrtf(fmaxf(v.y / d, 0.f) + eps);
-  sd.z = sqrtf(fmaxf(v.z / d, 0.f) + eps);
-  sd.w = sqrtf(fmaxf(v.w / d, 0.f) + eps);
+  sd.x = sqrtf(fmaxf(v.x / df, 0.f) + eps);
+  sd.y = sqrtf(fmaxf(v.y / df, 0.f) + eps);
+  sd.z = sqrtf(fmaxf(v.z / df, 0.f) + eps);
+  sd.w = sqrtf(fmaxf(v.w / df, 0.f) + eps);
   st4(out + 0 * H, s);
   st4(out + 1 * H, mean);
   st4(out + 2 * H, mn);
   st4(out + 3 * H, mx);
   st4(out + 4 * H, sd);
   if (S16) {  // scaler-major: identity, amplification, attenuation
-    const float4 v[kAgg] = {s, mean, mn, mx, sd};
+    const float4 vv[kAgg] = {s, mean, mn, mx, sd};
     const float sc[kScalers] = {1.f, amp[i], att[i]};
     uint16_t *o = S16 + (size_t)i * ld16 + c;
 #pragma unroll
     for (int q = 0; q < kScalers; ++q)
 #pragma unroll
       for (int a = 0; a < kAgg; ++a)
-        st_bf16x4(o + (q * kAgg + a) * H, sc[q] * v[a].x, sc[q] * v[a].y, sc[q] * v[a].z, sc[q] * v[a].w);
+        st_bf16x4(o + (q * kAgg + a) * H, sc[q] * vv[a].x, sc[q] * vv[a].y, sc[q] * vv[a].z, sc[q] * vv[a].w);
   }
 }
 
@@ -132,42 +149,54 @@ aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *
   if (t >= (long long)N * H4) return;
   const int i = (int)(t / H4), c = (int)(t % H4) * 4;
   const int r0 = row_ptr[i], r1 = row_ptr[i + 1];
+  const int d = r1 - r0;
   float4 dP = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (r1 <= r0 || r1 > E || !row_ok(col, r0, r1, N)) {
-    if (r1 < r0 || r1 > E || !row_ok(col, r0, r1, N)) flag(err, kErrIndex);
+  if (d <= 0 || r0 < 0 || r1 > E) {
+    if (d < 0 || r0 < 0 || r1 > E) flag(err, kErrIndex);
     st4(dPQ + (size_t)i * 2 * H + c, dP);
     if (dPQ16) st_bf16x4(dPQ16 + (size_t)i * ld16 + c, 0.f, 0.f, 0.f, 0.f);
     return;
   }
-  const float d = (float)(r1 - r0);
+  const float df = (float)d;
   const float *a = agg + (size_t)i * kAgg * H + c;
   const float *da = dagg + (size_t)i * kAgg * H + c;
   const float4 P = ld4(PQ + (size_t)i * 2 * H + c);
   const float4 mean = ld4(a + 1 * H), mn = ld4(a + 2 * H), mx = ld4(a + 3 * H), sd = ld4(a + 4 * H);
   const float4 dsum = ld4(da + 0 * H), dmean = ld4(da + 1 * H), dmin = ld4(da + 2 * H);
   const float4 dmax = ld4(da + 3 * H), dstd = ld4(da + 4 * H);
-  float4 nmin = make_float4(0.f, 0.f, 0.f, 0.f), nmax = nmin;
-  for (int e = r0; e < r1; ++e) {
-    const float4 m = add4(P, ld4(PQ + (size_t)col[e] * 2 * H + H + c));
+  float4 nmin = make_float4(0.f, 0.f, 0.f, 0.f), nmax = nmin, var = nmin;
+  float4 mc[kCache];
+  auto count = [&](float4 m) {
     nmin.x += (m.x == mn.x); nmin.y += (m.y == mn.y); nmin.z += (m.z == mn.z); nmin.w += (m.w == mn.w);
     nmax.x += (m.x == mx.x); nmax.y += (m.y == mx.y); nmax.z += (m.z == mx.z); nmax.w += (m.w == mx.w);
+    acc_sq(var, m, mean);
+  };
+#pragma unroll
+  for (int k = 0; k < kCache; ++k) {
+    if (k < d) {
+      mc[k] = message(PQ, source(col, r0 + k, N, err), H, c, P);
+      count(mc[k]);
+    }
   }
-  float4 var = sq_dev(PQ, col, r0, r1, H, c, P, mean);
-  var.x /= d; var.y /= d; var.z /= d; var.w /= d;
-  const float4 base = make_float4(dsum.x + dmean.x / d, dsum.y + dmean.y / d, dsum.z + dmean.z / d,
-                                  dsum.w + dmean.w / d);
-  for (int e = r0; e < r1; ++e) {
-    const float4 m = add4(P, ld4(PQ + (size_t)col[e] * 2 * H + H + c));
+  for (int e = r0 + kCache; e < r1; ++e) count(message(PQ, source(col, e, N, err), H, c, P));
+  var.x /= df; var.y /= df; var.z /= df; var.w /= df;
+  const float4 base = make_float4(dsum.x + dmean.x / df, dsum.y + dmean.y / df, dsum.z + dmean.z / df,
+                                  dsum.w + dmean.w / df);
+  auto emit = [&](int e, float4 m) {
     float4 g;
-    g.x = route(m.x, base.x, mn.x, dmin.x, nmin.x, mx.x, dmax.x, nmax.x, var.x, mean.x, dstd.x, d, sd.x);
-    g.y = route(m.y, base.y, mn.y, dmin.y, nmin.y, mx.y, dmax.y, nmax.y, var.y, mean.y, dstd.y, d, sd.y);
-    g.z = route(m.z, base.z, mn.z, dmin.z, nmin.z, mx.z, dmax.z, nmax.z, var.z, mean.z, dstd.z, d, sd.z);
-    g.w = route(m.w, base.w, mn.w, dmin.w, nmin.w, mx.w, dmax.w, nmax.w, var.w, mean.w, dstd.w, d, sd.w);
+    g.x = route(m.x, base.x, mn.x, dmin.x, nmin.x, mx.x, dmax.x, nmax.x, var.x, mean.x, dstd.x, df, sd.x);
+    g.y = route(m.y, base.y, mn.y, dmin.y, nmin.y, mx.y, dmax.y, nmax.y, var.y, mean.y, dstd.y, df, sd.y);
+    g.z = route(m.z, base.z, mn.z, dmin.z, nmin.z, mx.z, dmax.z, nmax.z, var.z, mean.z, dstd.z, df, sd.z);
+    g.w = route(m.w, base.w, mn.w, dmin.w, nmin.w, mx.w, dmax.w, nmax.w, var.w, mean.w, dstd.w, df, sd.w);
     dP = add4(dP, g);
     const int re = rev[e];
     if (re >= 0 && re < E) st4(dm + (size_t)re * H + c, g);
     else flag(err, kErrIndex);
-  }
+  };
+#pragma unroll
+  for (int k = 0; k < kCache; ++k)
+    if (k < d) emit(r0 + k, mc[k]);
+  for (int e = r0 + kCache; e < r1; ++e) emit(e, message(PQ, source(col, e, N, err), H, c, P));
   st4(dPQ + (size_t)i * 2 * H + c, dP);
   if (dPQ16) st_bf16x4(dPQ16 + (size_t)i * ld16 + c, dP.x, dP.y, dP.z, dP.w);
 }
@@ -185,6 +214,7 @@ aggregate_bwd_gather_kernel(int n_cap, int e_cap, int H, DevDims dims,
   int r0 = row_ptr[j], r1 = row_ptr[j + 1];
   if (r1 < r0 || r0 < 0 || r1 > E) { flag(err, kErrIndex); r1 = r0; }
   float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
   for (int e = r0; e < r1; ++e) q = add4(q, ld4(dm + (size_t)e * H + c));
   st4(dPQ + (size_t)j * 2 * H + H + c, q);
   if (dPQ16) st_bf16x4(dPQ16 + (size_t)j * ld16 + H + c, q.x, q.y, q.z, q.w);
