@@ -464,6 +464,50 @@ def recompute_study(g, precision: str, steps: int = 20):
     return out
 
 
+# ------------------------------------------------------------------ precision study
+def precision_study(g, epochs: int, lr: float):
+    """FP32 and BF16 paths trained from the same initial parameters on the same epoch
+    orders of the 200k-graph set; training MSE per epoch and MAE on the held-out 20k."""
+    import torch
+    wl = Workload(g, 0, 1)
+    held = np.arange(N_TRAIN, N_TRAIN + N_HELDOUT, dtype=np.int64)
+    hs = [wl.st.batch_size(held[i:i + BATCH]) for i in range(0, N_HELDOUT, BATCH)]
+    Nc = max(wl.Nc, (max(s[0] for s in hs) + 255) // 256 * 256)
+    Ec = max(wl.Ec, (max(s[1] for s in hs) + 511) // 512 * 512)
+    y_held = wl.y[held].astype(np.float64)
+    out = {"epochs": epochs, "train_graphs": N_TRAIN, "heldout_graphs": N_HELDOUT, "batch": BATCH, "lr": lr}
+    for prec in ("fp32", "bf16"):
+        c = g.Context(g.make_config(H, L, BATCH, Nc, Ec, delta=wl.delta,
+                                    precision=g.PREC_BF16 if prec == "bf16" else g.PREC_FP32))
+        c.set_params(synth.init_params(SEED_STUDENT, H, L))
+        pred = torch.empty(N_HELDOUT, device="cuda")
+        hist = []
+        t0 = time.perf_counter()
+        for ep in range(epochs):
+            order = epoch_order(ep)
+            c.set_order(wl.st, order)
+            acc = torch.zeros(3, dtype=torch.float64, device="cuda")
+            for i in range(0, N_TRAIN, BATCH):
+                c.train_step(c.collate_range(wl.st, i, min(BATCH, N_TRAIN - i)), lr, acc)
+            a = acc.cpu().numpy()
+            for i in range(0, N_HELDOUT, BATCH):
+                b = c.collate(wl.st, held[i:i + BATCH])
+                c.forward(b, pred[i:i + b.n_graphs], train=False)
+            err = pred.cpu().numpy().astype(np.float64) - y_held
+            hist.append({"epoch": ep + 1, "train_mse": a[0] / a[2], "train_mae": a[1] / a[2],
+                         "heldout_mae": float(np.mean(np.abs(err))), "heldout_rmse": float(np.sqrt(np.mean(err ** 2)))})
+            log(f"[precision] {prec} epoch {ep + 1}: {hist[-1]}")
+        c.check()
+        out[prec] = {"history": hist, "seconds": time.perf_counter() - t0}
+        c.close()
+    h32, h16 = out["fp32"]["history"], out["bf16"]["history"]
+    out["final_train_mse_rel_diff"] = (h16[-1]["train_mse"] - h32[-1]["train_mse"]) / h32[-1]["train_mse"]
+    out["final_heldout_mae_rel_diff"] = (h16[-1]["heldout_mae"] - h32[-1]["heldout_mae"]) / h32[-1]["heldout_mae"]
+    b32, b16 = min(h["heldout_mae"] for h in h32), min(h["heldout_mae"] for h in h16)
+    out["best_heldout_mae_rel_diff"] = (b16 - b32) / b32
+    return out
+
+
 # ------------------------------------------------------------------ serving
 SERVE_POOL, SEED_SERVE = 100_000, 30
 
@@ -678,6 +722,10 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="seconds of Poisson load per arrival rate for the serving measurement (0: skip)")
     ap.add_argument("--serve-rates", default="200,1000,2000", help="arrival rates, requests/s")
+    ap.add_argument("--study", choices=["none", "precision"], default="none",
+                    help="precision: train FP32 and BF16 for --epochs and compare held-out MAE (no bench line)")
+    ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--lr", type=float, default=1e-4, help="learning rate of the precision study")
     ap.add_argument("--no-studies", dest="studies", action="store_false",
                     help="skip the large-batch aggregation and recompute measurements")
     args = ap.parse_args()
@@ -685,6 +733,12 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.study == "precision":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        import paper_2207_11333_gb300 as g
+        print(json.dumps({"study": "precision", **precision_study(g, args.epochs, args.lr)}), flush=True)
+        return 0
     return run_ours(args)
 
 
