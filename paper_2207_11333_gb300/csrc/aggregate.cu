@@ -62,6 +62,7 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
                      const int *__restrict__ col, const float *__restrict__ PQ,
                      float *__restrict__ agg, float eps, unsigned *err, uint16_t *__restrict__ S16, int ld16,
                      const float *__restrict__ amp, const float *__restrict__ att) {
+  pdl_entry();
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -142,6 +143,7 @@ aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *
                           const float *__restrict__ PQ, const float *__restrict__ agg,
                           const float *__restrict__ dagg, float *__restrict__ dPQ,
                           float *__restrict__ dm, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16) {
+  pdl_entry();
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const int E = min(e_cap, dims.edges(e_cap));
@@ -205,6 +207,7 @@ __global__ void __launch_bounds__(kThreads)
 aggregate_bwd_gather_kernel(int n_cap, int e_cap, int H, DevDims dims,
                             const int *__restrict__ row_ptr, const float *__restrict__ dm,
                             float *__restrict__ dPQ, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16) {
+  pdl_entry();
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const int E = min(e_cap, dims.edges(e_cap));
@@ -228,9 +231,8 @@ int launch_aggregate_fwd(int n_nodes, int H, DevDims dims, const int *row_ptr, c
   if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
-  aggregate_fwd_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(n_nodes, H, dims, row_ptr, col,
-                                                                      PQ, agg, eps, err, S16, ld16, amp, att);
-  GCNN_LAUNCH_CHECK();
+  GCNN_TRY(launch(aggregate_fwd_kernel, ceil_div(work, kThreads), kThreads, 0, s, n_nodes, H, dims, row_ptr, col, PQ,
+                  agg, eps, err, S16, ld16, amp, att));
   return GCNN_OK;
 }
 
@@ -242,12 +244,10 @@ int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const in
   if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
-  aggregate_bwd_edge_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(
-      n_nodes, n_edges, H, dims, row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, err, dPQ16, ld16);
-  GCNN_LAUNCH_CHECK();
-  aggregate_bwd_gather_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(n_nodes, n_edges, H, dims,
-                                                                            row_ptr, scratch, dPQ, err, dPQ16, ld16);
-  GCNN_LAUNCH_CHECK();
+  GCNN_TRY(launch(aggregate_bwd_edge_kernel, ceil_div(work, kThreads), kThreads, 0, s, n_nodes, n_edges, H, dims,
+                  row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, err, dPQ16, ld16));
+  GCNN_TRY(launch(aggregate_bwd_gather_kernel, ceil_div(work, kThreads), kThreads, 0, s, n_nodes, n_edges, H, dims,
+                  row_ptr, (const float *)scratch, dPQ, err, dPQ16, ld16));
   return GCNN_OK;
 }
 

@@ -185,7 +185,6 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   c->P = param_count_of(*cfg);
   c->Gc = cfg->max_graphs; c->Nc = cfg->max_nodes; c->Ec = cfg->max_edges;
   const size_t H = c->H, Nc = c->Nc, Ec = c->Ec, Gc = c->Gc, L = c->L, Hh = c->Hh;
-  c->emb_chunks = (int)ceil_div(Nc, 16);
   // split-K workspace: the largest of the step's GEMMs
   // (over every node-count bucket a batch can launch with)
   size_t wsf = 0;
@@ -228,14 +227,13 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   const size_t o_dH = cv.take<float>(Nc * H), o_dX = cv.take<float>(Nc * H);
   const size_t o_dagg = cv.take<float>(Nc * kAgg * H), o_dPQ = cv.take<float>(Nc * 2 * H);
   const size_t o_dm = cv.take<float>(Ec * H);
-  const size_t o_embp = cv.take<float>((size_t)c->emb_chunks * c->T * H);
+  const size_t o_tk = cv.take<unsigned>(16);
   const size_t o_ws = cv.take<float>(wsf);
   const bool bf = cfg->precision == GCNN_PREC_BF16;
   const size_t o_wb = cv.take<uint16_t>(bf ? c->P : 0), o_wp = cv.take<uint16_t>(bf ? L * 18 * H * H : 0);
   const size_t o_U = cv.take<uint16_t>(bf ? (cfg->recompute ? 1 : L) * Nc * 16 * H : 0);
   const size_t o_Xb = cv.take<uint16_t>(bf && cfg->recompute ? L * Nc * H : 0);
   const size_t o_g0 = cv.take<uint16_t>(bf ? Nc * 5 * H : 0), o_g1 = cv.take<uint16_t>(bf ? Nc * 5 * H : 0);
-  const size_t o_cp = cv.take<float>(bf ? ceil_div(Nc, 32) * 2 * H : 0);
   c->dbytes = cv.off;
   cudaError_t e = cudaMalloc(&c->dmem, c->dbytes);
   if (e != cudaSuccess) {
@@ -257,13 +255,13 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   c->pooled = (float *)(b + o_pool); c->z1 = (float *)(b + o_z1); c->pred = (float *)(b + o_pred);
   c->dpred = (float *)(b + o_dpred); c->dz1 = (float *)(b + o_dz1); c->dg = (float *)(b + o_dg);
   c->dH = (float *)(b + o_dH); c->dX = (float *)(b + o_dX); c->dagg = (float *)(b + o_dagg);
-  c->dPQ = (float *)(b + o_dPQ); c->dm = (float *)(b + o_dm); c->emb_partial = (float *)(b + o_embp);
+  c->dPQ = (float *)(b + o_dPQ); c->dm = (float *)(b + o_dm); c->tickets = (unsigned *)(b + o_tk);
   c->ws.partial = (float *)(b + o_ws); c->ws.floats = wsf;
   c->ws.max_splits = (cfg->flags & GCNN_FLAG_ROW_INVARIANT) ? 1 : 32;
   if (bf) {
     c->wb = (uint16_t *)(b + o_wb); c->wpack = (uint16_t *)(b + o_wp); c->U = (uint16_t *)(b + o_U);
     if (cfg->recompute) c->Xb = (uint16_t *)(b + o_Xb);
-    c->G5[0] = (uint16_t *)(b + o_g0); c->G5[1] = (uint16_t *)(b + o_g1); c->colsum_partial = (float *)(b + o_cp);
+    c->G5[0] = (uint16_t *)(b + o_g0); c->G5[1] = (uint16_t *)(b + o_g1);
   }
   int rc = GCNN_OK;
   if (cudaMemset(c->dmem, 0, c->dbytes) != cudaSuccess) rc = set_error(GCNN_ECUDA, "cudaMemset failed");
@@ -466,8 +464,11 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
   const int G = b->n_graphs;
   const int Ng = grid_nodes(c, b), Eg = grid_edges(c, b);
   if (c->prof_on) {  // eager, so every launch can be timed
-    GCNN_TRY(ctx_forward(c, G, Ng, Eg, true));
-    GCNN_TRY(ctx_backward(c, G, Ng, Eg, nullptr, loss_accum));
+    c->fuse_head = true;
+    int rc = ctx_forward(c, G, Ng, Eg, true);
+    if (rc == GCNN_OK) rc = ctx_backward(c, G, Ng, Eg, nullptr, loss_accum);
+    c->fuse_head = false;
+    GCNN_TRY(rc);
     GCNN_TRY(ctx_step(c));
     c->last_step_kernels = 0;
     c->have_fwd = true;
@@ -490,8 +491,10 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
       c->capturing = false;
       return set_error(GCNN_ECUDA, "begin capture: %s", cudaGetErrorString(e));
     }
+    c->fuse_head = true;
     int rc = ctx_forward(c, G, Ng, Eg, true);
     if (rc == GCNN_OK) rc = ctx_backward(c, G, Ng, Eg, nullptr, loss_accum);
+    c->fuse_head = false;
     if (rc == GCNN_OK) rc = ctx_step(c);
     e = cudaStreamEndCapture(c->stream, &graph);
     c->stream = user;

@@ -25,6 +25,7 @@ collate_scan_kernel(int G, const int64_t *__restrict__ ids, StoreView st, BatchB
                     int cap_edges, unsigned *err) {
   __shared__ int warp_n[32], warp_e[32];
   __shared__ int carry_n, carry_e;
+  pdl_entry();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (threadIdx.x == 0) { carry_n = 0; carry_e = 0; }
   __syncthreads();
@@ -89,6 +90,7 @@ collate_graph_kernel(int G, const int64_t *__restrict__ ids, StoreView st, Batch
   __shared__ uint8_t s_dst[kGraphWarps][kMaxGraphEdges];
   __shared__ int s_cnt[kGraphWarps][256];
   __shared__ int s_start[kGraphWarps][256];
+  pdl_entry();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = blockIdx.x * kGraphWarps + w;
   if (g >= G) return;  // warp-uniform; only warp-level synchronisation below
@@ -163,13 +165,10 @@ collate_graph_kernel(int G, const int64_t *__restrict__ ids, StoreView st, Batch
 int launch_collate(int G, const int64_t *ids, StoreView st, BatchBuf b, const float *scal_tab,
                    int cap_nodes, int cap_edges, unsigned *err, cudaStream_t s) {
   if (G < 0) return set_error(GCNN_EINVAL, "collate: negative graph count");
-  collate_scan_kernel<<<1, kScanThreads, 0, s>>>(G, ids, st, b, cap_nodes, cap_edges, err);
-  GCNN_LAUNCH_CHECK();
-  if (G > 0) {
-    collate_graph_kernel<<<ceil_div(G, kGraphWarps), kGraphWarps * 32, 0, s>>>(
-        G, ids, st, b, scal_tab, cap_nodes, cap_edges, err);
-    GCNN_LAUNCH_CHECK();
-  }
+  GCNN_TRY(launch(collate_scan_kernel, 1, kScanThreads, 0, s, G, ids, st, b, cap_nodes, cap_edges, err));
+  if (G > 0)
+    GCNN_TRY(launch(collate_graph_kernel, ceil_div(G, kGraphWarps), kGraphWarps * 32, 0, s, G, ids, st, b, scal_tab,
+                    cap_nodes, cap_edges, err));
   return GCNN_OK;
 }
 

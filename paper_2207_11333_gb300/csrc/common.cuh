@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
+#include <utility>
 
 #include "gcnn.h"
 
@@ -51,6 +53,53 @@ struct DevDims {
   __device__ __forceinline__ int nodes(int h) const { return p ? p[1] : h; }
   __device__ __forceinline__ int edges(int h) const { return p ? p[2] : h; }
 };
+
+// ---------------------------------------------------------------- launches
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialisation attribute may be scheduled while its predecessor in the
+// stream is still running, so every kernel of the library begins with
+// pdl_entry(): griddepcontrol.wait blocks until the predecessor grid has
+// completed and its writes are visible (a no-op for a normal launch), then
+// griddepcontrol.launch_dependents lets the successor be scheduled.  Every CTA
+// executes the wait before it can exit, so the completion of a grid implies the
+// completion of every earlier grid in the stream; only work that touches no
+// global memory (shared-memory barrier set-up, tensor-map prefetch) may come
+// before it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_entry() {
+  pdl_wait();
+  pdl_launch_dependents();
+}
+
+// Launches on the legacy or per-thread default stream keep full serialisation;
+// GCNN_PDL=0 in the environment turns the attribute off everywhere.
+inline bool pdl_enabled(cudaStream_t s) {
+  static const bool on = [] {
+    const char *v = std::getenv("GCNN_PDL");
+    return !(v && v[0] == '0');
+  }();
+  return on && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+}
+
+// kernel<<<grid, block, smem, s>>>(args...) with programmatic serialisation.
+template <typename... P, typename... A>
+int launch(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A &&...args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled(s) ? 1 : 0;
+  GCNN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...));
+  return GCNN_OK;
+}
 
 inline unsigned ceil_div(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 

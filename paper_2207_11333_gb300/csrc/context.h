@@ -46,8 +46,7 @@ struct gcnn_ctx {
   float *pooled = nullptr, *z1 = nullptr, *pred = nullptr, *dpred = nullptr, *dz1 = nullptr;
   float *dg = nullptr;
   float *dH = nullptr, *dX = nullptr, *dagg = nullptr, *dPQ = nullptr, *dm = nullptr;
-  float *emb_partial = nullptr;
-  int emb_chunks = 0;
+  unsigned *tickets = nullptr;  // zero-initialised completion counters of single-launch reductions
 
   // BF16 operands of the tensor-core GEMMs (precision == GCNN_PREC_BF16)
   uint16_t *wb = nullptr;     // parameters cast to BF16 after every update (same layout)
@@ -55,7 +54,6 @@ struct gcnn_ctx {
   uint16_t *U = nullptr;      // (recompute ? 1 : L) x Nc x 16H: [x_l | agg | amp*agg | att*agg]
   uint16_t *Xb = nullptr;     // recompute only: L x Nc x H layer inputs (copied into U when needed)
   uint16_t *G5[2] = {nullptr, nullptr};  // Nc x 5H: [amp*g | att*g | g | dP | dQ]
-  float *colsum_partial = nullptr;       // ceil(Nc/32) x 2H
   gcnn::GemmWorkspace ws{};
 
   // host-side state
@@ -70,6 +68,7 @@ struct gcnn_ctx {
   std::map<std::tuple<int, int, int, const double *>, Graph> graphs;
   int last_step_kernels = 0;
   bool capturing = false;
+  bool fuse_head = false;  // train step: head backward runs inside the forward's head kernel
 
   // per-phase event timing (gcnn_profile_enable)
   bool prof_on = false;

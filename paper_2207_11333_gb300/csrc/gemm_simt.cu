@@ -83,6 +83,7 @@ __device__ __forceinline__ float load_feat1(const Seg &sg, int node, int f) {
 template <bool AK, bool BNC>
 __global__ void __launch_bounds__(kThreads, 2)
 sgemm_kernel(GemmDesc d, DevDims dims, float *__restrict__ partial, int splits, int kps) {
+  pdl_entry();
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Bs[2][BK][BN];
   const Sizes sz = actual_sizes(d, dims);
@@ -236,6 +237,7 @@ sgemm_kernel(GemmDesc d, DevDims dims, float *__restrict__ partial, int splits, 
 // C = epilogue(sum_z partial[z]); one thread per 4 outputs
 __global__ void __launch_bounds__(kThreads)
 splitk_reduce_kernel(GemmDesc d, DevDims dims, const float *__restrict__ partial, int splits) {
+  pdl_entry();
   const Sizes sz = actual_sizes(d, dims);
   const int M = sz.M, N = d.N, N4 = N / 4;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -330,22 +332,20 @@ int run_gemm_simt(const GemmDesc &d, DevDims dims, const GemmWorkspace &ws, cuda
   dim3 grid(ceil_div(d.N, BN), ceil_div(d.M, BM), splits);
   float *part = splits > 1 ? ws.partial : nullptr;
   if (d.a_kcontig && d.b_ncontig)
-    sgemm_kernel<true, true><<<grid, kThreads, 0, s>>>(d, dims, part, splits, kps);
+    GCNN_TRY(launch(sgemm_kernel<true, true>, grid, kThreads, 0, s, d, dims, part, splits, kps));
   else if (d.a_kcontig && !d.b_ncontig)
-    sgemm_kernel<true, false><<<grid, kThreads, 0, s>>>(d, dims, part, splits, kps);
+    GCNN_TRY(launch(sgemm_kernel<true, false>, grid, kThreads, 0, s, d, dims, part, splits, kps));
   else if (!d.a_kcontig && d.b_ncontig)
-    sgemm_kernel<false, true><<<grid, kThreads, 0, s>>>(d, dims, part, splits, kps);
+    GCNN_TRY(launch(sgemm_kernel<false, true>, grid, kThreads, 0, s, d, dims, part, splits, kps));
   else
-    sgemm_kernel<false, false><<<grid, kThreads, 0, s>>>(d, dims, part, splits, kps);
-  GCNN_LAUNCH_CHECK();
+    GCNN_TRY(launch(sgemm_kernel<false, false>, grid, kThreads, 0, s, d, dims, part, splits, kps));
   if (splits > 1) GCNN_TRY(run_splitk_reduce(d, dims, part, splits, s));
   return GCNN_OK;
 }
 
 int run_splitk_reduce(const GemmDesc &d, DevDims dims, const float *partial, int splits, cudaStream_t s) {
   const long long work = (long long)d.M * (d.N / 4);
-  splitk_reduce_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(d, dims, partial, splits);
-  GCNN_LAUNCH_CHECK();
+  GCNN_TRY(launch(splitk_reduce_kernel, ceil_div(work, kThreads), kThreads, 0, s, d, dims, partial, splits));
   return GCNN_OK;
 }
 

@@ -18,8 +18,10 @@
 //   warp 1   waits "full", issues four tcgen05.mma (K = 16 each) and commits
 //            them to the stage's "empty" barrier; after the last stage it
 //            commits to the "accumulator ready" barrier
-//   warps 4-7  wait for the accumulator, read TMEM (tcgen05.ld), apply bias /
-//            ReLU and write FP32 and BF16 outputs, or split-K partials
+//   all 8    wait for the accumulator, drain TMEM (tcgen05.ld) into an FP32
+//            tile staged in the idle pipeline buffers, then write it
+//            row-contiguously: bias / ReLU, FP32 and BF16 outputs, the masked
+//            and scaled BF16 gradient blocks, or split-K partials
 // Every wait is bounded (~2 s): on expiry the kernel sets kErrTimeout in the
 // device error word, skips its epilogue and releases TMEM.
 #include <cuda.h>
@@ -171,8 +173,10 @@ __device__ __forceinline__ void emit8(const TcEpilogue &e, int N, int row, int n
   }
   if (e.C16) st_bf16x8(e.C16 + (size_t)row * e.ld16 + n, v, 1.f);
   if (e.D3) {  // [amp g | att g | g], g = v * [mask > 0]
+    const float4 m0 = *reinterpret_cast<const float4 *>(e.mask + (size_t)row * e.ldm + n);
+    const float4 m1 = *reinterpret_cast<const float4 *>(e.mask + (size_t)row * e.ldm + n + 4);
+    const float mk[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
     float g[8];
-    const float *mk = e.mask + (size_t)row * e.ldm + n;
 #pragma unroll
     for (int q = 0; q < 8; ++q) g[q] = mk[q] > 0.f ? v[q] : 0.f;
     uint16_t *o = e.D3 + (size_t)row * e.ld3 + n;
@@ -182,9 +186,31 @@ __device__ __forceinline__ void emit8(const TcEpilogue &e, int N, int row, int n
   }
 }
 
+// Final 4 columns (row, n..n+3) of the product: bias and ReLU already
+// applied (x), mask values mk and degree scalers am / at for D3.
+__device__ __forceinline__ void emit4(const TcEpilogue &e, int N, int row, int n, float4 x, float4 mk, float am,
+                                      float at) {
+  if (e.C) *reinterpret_cast<float4 *>(e.C + (size_t)row * e.ldc + n) = x;
+  if (e.C16) st_bf16x4(e.C16 + (size_t)row * e.ld16 + n, x.x, x.y, x.z, x.w);
+  if (e.D3) {  // [amp g | att g | g], g = x * [mask > 0]
+    const float gx = mk.x > 0.f ? x.x : 0.f, gy = mk.y > 0.f ? x.y : 0.f;
+    const float gz = mk.z > 0.f ? x.z : 0.f, gw = mk.w > 0.f ? x.w : 0.f;
+    uint16_t *o = e.D3 + (size_t)row * e.ld3 + n;
+    st_bf16x4(o, am * gx, am * gy, am * gz, am * gw);
+    st_bf16x4(o + N, at * gx, at * gy, at * gz, at * gw);
+    st_bf16x4(o + 2 * N, gx, gy, gz, gw);
+  }
+}
+
 struct Sizes {
   int M, K;
 };
+
+// Row stride (floats) of the staged FP32 output tile: consecutive rows shift
+// by 16 bytes modulo 128, so the row-per-thread TMEM drain stores 16-byte
+// vectors without shared-memory bank conflicts.
+__host__ __device__ constexpr int stage_stride(int BN) { return BN + (36 - BN % 32) % 32; }
+static_assert(BM * stage_stride(kMaxBN) * 4 <= STAGES * kStageBytes, "staged tile must fit the pipeline buffers");
 
 __device__ __forceinline__ Sizes actual_sizes(const TcDesc &d, DevDims dims) {
   Sizes s{d.M, d.K};
@@ -213,20 +239,8 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_ready + 1);
   uint32_t *flag = tmem_slot + 1;
 
-  const Sizes sz = actual_sizes(d, dims);
-  const int M = sz.M, K = sz.K, N = d.N;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int z = blockIdx.z;
-  if (m0 >= M) return;  // block-uniform, before any barrier or TMEM use
-  const int kbeg = z * kps;
-  const int kend = min(K, kbeg + kps);
-  const int nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t ncols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
-  const int b_atoms = (BN + 63) / 64;
-  const uint32_t a_bytes = kATileBytes;
-  const uint32_t b_bytes = d.B.mn_major ? (uint32_t)b_atoms * kMnAtomBytes : (uint32_t)BN * BK * 2;
-
+  // shared-memory set-up and descriptor prefetch overlap the previous kernel
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -238,6 +252,20 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b)) : "memory");
   }
+  pdl_entry();
+  const Sizes sz = actual_sizes(d, dims);
+  const int M = sz.M, K = sz.K, N = d.N;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int z = blockIdx.z;
+  if (m0 >= M) return;  // block-uniform, before any barrier wait or TMEM use
+  const int kbeg = z * kps;
+  const int kend = min(K, kbeg + kps);
+  const int nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+  const uint32_t ncols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+  const int b_atoms = (BN + 63) / 64;
+  const uint32_t a_bytes = kATileBytes;
+  const uint32_t b_bytes = d.B.mn_major ? (uint32_t)b_atoms * kMnAtomBytes : (uint32_t)BN * BK * 2;
+
   if (warp == 0) tmem_alloc(tmem_slot, ncols);
   fence_before_sync();
   __syncthreads();
@@ -309,7 +337,10 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
     if (ok && nk > 0 && lane == 0) mma_commit(acc_ready);
   }
   // ------------------------------------------------ epilogue (all 8 warps)
-  // warp w reads TMEM lanes 32*(w%4).. (tile rows) and half w/4 of the columns
+  // (1) warp w drains TMEM lanes 32*(w%4).. (tile rows) and half w/4 of the
+  //     columns into an FP32 tile staged in the idle pipeline buffers;
+  // (2) the warps write the tile row by row, each row's 4-column slices
+  //     spread over the lanes (coalesced stores).
   {
     bool ok = true;
     if (nk > 0) {
@@ -318,36 +349,96 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
       fence_after_sync();
     }
     ok = __all_sync(0xffffffffu, ok);
+    float *S = reinterpret_cast<float *>(smem);
+    const int RS = stage_stride(BN);
     if (ok) {
-      const int lane_base = 32 * (warp & 3);
-      const int row = m0 + lane_base + lane;
+      const int r = 32 * (warp & 3) + lane;
       const int groups = BN / 8, half = (groups + 1) / 2;
       const int g0 = warp < 4 ? 0 : half, g1 = warp < 4 ? half : groups;
-      for (int gb = g0; gb < g1; gb += 4) {
-        uint32_t r[4][8];
-        const int cnt = min(4, g1 - gb);
+      for (int gb = g0; gb < g1; gb += 8) {
+        uint32_t v[8][8];
+        const int cnt = min(8, g1 - gb);
         if (nk > 0) {
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (u < cnt) tmem_ld8(tmem + ((uint32_t)lane_base << 16) + (uint32_t)((gb + u) * 8), r[u]);
+          for (int u = 0; u < 8; ++u)
+            if (u < cnt) tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((gb + u) * 8), v[u]);
           tmem_wait_ld();
+        } else {
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[u][q] = 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (u >= cnt) break;
+          float *p = S + (size_t)r * RS + (gb + u) * 8;
+          *reinterpret_cast<uint4 *>(p) = make_uint4(v[u][0], v[u][1], v[u][2], v[u][3]);
+          *reinterpret_cast<uint4 *>(p + 4) = make_uint4(v[u][4], v[u][5], v[u][6], v[u][7]);
+        }
+      }
+    }
+    if (!__syncthreads_or(!ok)) {
+      // warp w writes rows w, w + 8, ..., four per batch with every load of
+      // the batch issued first; lane l owns the 4-column slices 4l and 128 + 4l
+      // a local copy: stores through the output pointers cannot alias it, so
+      // its fields stay in registers across the loop
+      const TcEpilogue e = d.ep;
+      const int rows = min(BM, M - m0);
+      int cn[2];
+      bool on[2];
+      float4 bias[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        cn[h] = 128 * h + 4 * lane;
+        on[h] = cn[h] < BN && n0 + cn[h] < N;
+        float b[4] = {0.f, 0.f, 0.f, 0.f};
+        if (splits == 1 && e.bias && on[h])
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (n0 + cn[h] + q < e.bias_n) b[q] = e.bias[n0 + cn[h] + q];
+        bias[h] = make_float4(b[0], b[1], b[2], b[3]);
+      }
+      for (int r0 = warp; r0 < rows; r0 += 32) {
+        float4 v[4][2], mk[4][2];
+        float am[4], at[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int r = r0 + 8 * u;
+          am[u] = at[u] = 0.f;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            v[u][h] = mk[u][h] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < rows && on[h]) {
+              v[u][h] = *reinterpret_cast<const float4 *>(S + (size_t)r * RS + cn[h]);
+              if (e.D3) mk[u][h] = *reinterpret_cast<const float4 *>(e.mask + (size_t)(m0 + r) * e.ldm + n0 + cn[h]);
+            }
+          }
+          if (e.D3 && r < rows) {
+            am[u] = e.amp[m0 + r];
+            at[u] = e.att[m0 + r];
+          }
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          if (u >= cnt) break;
-          float v[8];
+          const int r = r0 + 8 * u;
+          if (r >= rows) break;
+          const int row = m0 + r;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) v[q] = nk > 0 ? __uint_as_float(r[u][q]) : 0.f;
-          const int n = n0 + (gb + u) * 8;
-          if (row >= M || n >= N) continue;
-          if (splits > 1) {
-            float *p = partial + ((size_t)z * d.M + row) * N + n;
-            *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-            *reinterpret_cast<float4 *>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
-            continue;
+          for (int h = 0; h < 2; ++h) {
+            if (!on[h]) continue;
+            const int n = n0 + cn[h];
+            float4 x = v[u][h];
+            if (splits > 1) {
+              *reinterpret_cast<float4 *>(partial + ((size_t)z * d.M + row) * N + n) = x;
+              continue;
+            }
+            x.x += bias[h].x; x.y += bias[h].y; x.z += bias[h].z; x.w += bias[h].w;
+            if (e.relu) {
+              x.x = fmaxf(x.x, 0.f); x.y = fmaxf(x.y, 0.f); x.z = fmaxf(x.z, 0.f); x.w = fmaxf(x.w, 0.f);
+            }
+            emit4(e, N, row, n, x, mk[u][h], am[u], at[u]);
           }
-          finish8(d.ep, n, v);
-          emit8(d.ep, N, row, n, v);
         }
       }
     }
@@ -361,6 +452,7 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
 // C = epilogue(sum over splits); one thread per 8 outputs
 __global__ void __launch_bounds__(256) tc_reduce_kernel(TcDesc d, DevDims dims, const float *__restrict__ partial,
                                                        int splits) {
+  pdl_entry();
   const Sizes sz = actual_sizes(d, dims);
   const int M = sz.M, N = d.N, N8 = N / 8;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -372,8 +464,9 @@ __global__ void __launch_bounds__(256) tc_reduce_kernel(TcDesc d, DevDims dims, 
     const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
     v[0] += a.x; v[1] += a.y; v[2] += a.z; v[3] += a.w; v[4] += b.x; v[5] += b.y; v[6] += b.z; v[7] += b.w;
   }
-  finish8(d.ep, n, v);
-  emit8(d.ep, N, row, n, v);
+  const TcEpilogue e = d.ep;
+  finish8(e, n, v);
+  emit8(e, N, row, n, v);
 }
 
 // ---------------------------------------------------------------- host
@@ -415,17 +508,55 @@ int make_map(CUtensorMap *m, const TcMat &a, int box_rows) {
 
 int g_configured = 0;
 
-// N tiles as few as possible (each <= 256 and a multiple of 16); splits of K
-// so that one wave (one CTA per SM) is filled, with >= 6 k-tiles per split.
-int choose(int M, int N, int K, int max_splits, int *BN, int *ntiles, int *splits) {
-  *ntiles = (N + kMaxBN - 1) / kMaxBN;
-  *BN = ((N + *ntiles - 1) / *ntiles + 15) / 16 * 16;
-  const long long tiles = (long long)*ntiles * ((M + BM - 1) / BM);
-  const int ktiles = (K + BK - 1) / BK;
-  int s = (int)std::max<long long>(1, num_sms() / tiles);
-  s = std::min(s, std::max(1, ktiles / 6));
-  *splits = std::min(std::min(s, 32), max_splits);
-  return ktiles;
+struct Plan {
+  int BN, ntiles, splits;
+};
+
+// Tile width and split count of one launch.  A CTA's time is dominated by
+// the bytes it moves: operand tiles from L2 (~100 GB/s per SM), the FP32
+// accumulator tile and the epilogue outputs to memory (~40 GB/s per SM
+// sustained by one CTA), plus, for split-K, a reduction pass over the
+// partial tiles.  Among widths BN (multiple of 16, <= 256) and splits whose
+// grid fits one wave (one CTA per SM), take the smallest estimate; grids
+// larger than a wave use the widest tiles and no split.
+// out_bytes: epilogue bytes per output element; b_mn: B tiles are MN-major
+// (loaded in 64-column atoms).
+Plan choose(int M, int N, int K, int max_splits, double out_bytes, bool b_mn) {
+  const int sms = num_sms();
+  const long long mtiles = (M + BM - 1) / BM;
+  const int ktiles = std::max(1, (K + BK - 1) / BK);
+  Plan best{0, 0, 1};
+  double best_t = 1e30;
+  for (int bn = 16; bn <= kMaxBN; bn += 16) {
+    const int nt = (N + bn - 1) / bn;
+    if (nt > 1 && (long long)bn * (nt - 1) >= N) continue;
+    for (int sp = 1; sp <= std::min(max_splits, ktiles); ++sp) {
+      if (mtiles * nt * sp > sms) break;
+      const int kps = (ktiles + sp - 1) / sp;
+      const double b_tile = b_mn ? ((bn + 63) / 64) * 8192.0 : bn * 128.0;
+      const double t_load = kps * (kATileBytes + b_tile) / 1.0e5;          // us at 100 GB/s
+      const double t_out = BM * (double)bn * (sp > 1 ? 4.0 : out_bytes) / 4.0e4;  // us at 40 GB/s
+      const double t_red = sp > 1 ? 2.0 + (double)M * N * (4.0 * sp + out_bytes) / 5.0e6 : 0.0;
+      const double t = t_load + t_out + t_red;
+      if (t < best_t) {
+        best_t = t;
+        best = Plan{bn, nt, sp};
+      }
+    }
+  }
+  if (best.BN == 0) {  // more than one wave: widest tiles, no split
+    best.ntiles = (N + kMaxBN - 1) / kMaxBN;
+    best.BN = ((N + best.ntiles - 1) / best.ntiles + 15) / 16 * 16;
+    best.splits = 1;
+  }
+  return best;
+}
+
+// Upper bound of the split count choose() can return for these sizes.
+int max_splits_of(int M, int K) {
+  const long long mtiles = (M + BM - 1) / BM;
+  const int ktiles = std::max(1, (K + BK - 1) / BK);
+  return (int)std::max<long long>(1, std::min<long long>({32LL, (long long)ktiles, num_sms() / std::max(1LL, mtiles)}));
 }
 
 }  // namespace
@@ -435,10 +566,14 @@ int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
   const TcEpilogue &e = d.ep;
   if (d.N % 8 || (e.C && (e.ldc % 4 || reinterpret_cast<uintptr_t>(e.C) % 16)) ||
       (e.C16 && (e.ld16 % 8 || reinterpret_cast<uintptr_t>(e.C16) % 16)) ||
-      (e.D3 && (e.ld3 % 8 || reinterpret_cast<uintptr_t>(e.D3) % 16 || !e.mask || !e.amp || !e.att)))
+      (e.D3 && (e.ld3 % 8 || reinterpret_cast<uintptr_t>(e.D3) % 16 || !e.mask || !e.amp || !e.att ||
+                e.ldm % 4 || reinterpret_cast<uintptr_t>(e.mask) % 16)))
     return set_error(GCNN_EINVAL, "tc gemm: N must be a multiple of 8 and outputs 16-byte aligned");
-  int BN, ntiles, splits;
-  const int ktiles = choose(d.M, d.N, d.K, ws.max_splits, &BN, &ntiles, &splits);
+  const double out_bytes = (e.C ? 4.0 : 0.0) + (e.C16 ? 2.0 : 0.0) + (e.D3 ? 10.0 : 0.0);
+  const Plan plan = choose(d.M, d.N, d.K, ws.max_splits, out_bytes, d.B.mn_major);
+  const int BN = plan.BN, ntiles = plan.ntiles;
+  int splits = plan.splits;
+  const int ktiles = (d.K + BK - 1) / BK;
   TcMaps maps;
   GCNN_TRY(make_map(&maps.a, d.A, d.A.mn_major ? 64 : BM));
   GCNN_TRY(make_map(&maps.b, d.B, d.B.mn_major ? 64 : BN));
@@ -449,26 +584,24 @@ int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
   if (splits > 1 && (size_t)splits * d.M * d.N > ws.floats) splits = 1;
   const int kps = (ktiles + splits - 1) / splits * BK;
   dim3 grid(ntiles, (d.M + BM - 1) / BM, splits);
-  tma_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, d, dims, splits > 1 ? ws.partial : nullptr, splits, kps, BN,
-                                                     err);
-  GCNN_LAUNCH_CHECK();
+  GCNN_TRY(launch(tma_gemm_kernel, grid, kThreads, kSmemBytes, s, maps, d, dims, splits > 1 ? ws.partial : nullptr,
+                  splits, kps, BN, err));
   if (splits > 1) {
     const long long work = (long long)d.M * (d.N / 8);
-    tc_reduce_kernel<<<ceil_div(work, 256), 256, 0, s>>>(d, dims, ws.partial, splits);
-    GCNN_LAUNCH_CHECK();
+    GCNN_TRY(launch(tc_reduce_kernel, ceil_div(work, 256), 256, 0, s, d, dims, (const float *)ws.partial, splits));
   }
   return GCNN_OK;
 }
 
 size_t gemm_tc_workspace_floats(int M, int N, int K) {
-  int BN, ntiles, splits;
-  choose(M, N, K, 32, &BN, &ntiles, &splits);
-  return splits > 1 ? (size_t)splits * M * N : 0;
+  const int sp = max_splits_of(M, K);
+  return sp > 1 ? (size_t)sp * M * N : 0;
 }
 
 // ---------------------------------------------------------------- casts
 namespace {
 __global__ void cast_bf16_kernel(int64_t n, const float *__restrict__ src, uint16_t *__restrict__ dst) {
+  pdl_entry();
   const int64_t n8 = n / 8;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n8; q += stride) {
@@ -487,6 +620,7 @@ __global__ void cast_bf16_kernel(int64_t n, const float *__restrict__ src, uint1
 // Wx[n] = [W_U[n][0..H) | W_M[n][0..2H)].
 __global__ void pack_layer_kernel(int H, const float *__restrict__ msg_w, const float *__restrict__ upd_w,
                                   uint16_t *__restrict__ Wd, uint16_t *__restrict__ Wx) {
+  pdl_entry();
   const long long nd = 15LL * H * H, nx = 3LL * H * H;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < nd) {
@@ -508,15 +642,13 @@ int launch_cast_bf16(int64_t n, const float *src, uint16_t *dst, cudaStream_t s)
   if (reinterpret_cast<uintptr_t>(src) % 16 || reinterpret_cast<uintptr_t>(dst) % 16)
     return set_error(GCNN_EINVAL, "cast: buffers must be 16-byte aligned");
   const int blocks = (int)std::min<int64_t>((n / 8 + 255) / 256 + 1, (int64_t)num_sms() * 8);
-  cast_bf16_kernel<<<blocks, 256, 0, s>>>(n, src, dst);
-  GCNN_LAUNCH_CHECK();
+  GCNN_TRY(launch(cast_bf16_kernel, blocks, 256, 0, s, n, src, dst));
   return GCNN_OK;
 }
 
 int launch_pack_layer(int H, const float *msg_w, const float *upd_w, uint16_t *Wd, uint16_t *Wx, cudaStream_t s) {
   const long long work = 18LL * H * H;
-  pack_layer_kernel<<<ceil_div(work, 256), 256, 0, s>>>(H, msg_w, upd_w, Wd, Wx);
-  GCNN_LAUNCH_CHECK();
+  GCNN_TRY(launch(pack_layer_kernel, ceil_div(work, 256), 256, 0, s, H, msg_w, upd_w, Wd, Wx));
   return GCNN_OK;
 }
 

@@ -46,9 +46,9 @@ int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const in
 // ---------------------------------------------------------------- small.cu
 int launch_embed(int n_nodes, int H, DevDims dims, const uint8_t *types, const float *emb,
                  int n_types, float *x0, cudaStream_t s, uint16_t *x0_16 = nullptr, int ld16 = 0);
-// dEmb[t] = sum of dx0 over nodes of type t (deterministic two-stage sum).
-int launch_embed_bwd(int n_nodes, int H, DevDims dims, const uint8_t *types, const float *dx0,
-                     int n_types, float *partial, int max_chunks, float *demb, cudaStream_t s);
+// dEmb[t] = sum of dx0 over nodes of type t (fixed-order sum, one launch).
+int launch_embed_bwd(int n_nodes, int H, DevDims dims, const uint8_t *types, const float *dx0, int n_types,
+                     float *demb, cudaStream_t s);
 int launch_pool_fwd(int G, int H, DevDims dims, const int *node_off, const float *x, float *pooled,
                     cudaStream_t s);
 // D3 (nullable, row pitch ld3) additionally receives [amp*g, att*g, g] (3H
@@ -57,19 +57,47 @@ int launch_pool_bwd(int G, int n_nodes, int H, DevDims dims, const int *node_off
                     const int *graph_id, const float *dpooled, float *dx, cudaStream_t s,
                     uint16_t *D3 = nullptr, int ld3 = 0, const float *h = nullptr, const float *amp = nullptr,
                     const float *att = nullptr);
-// Head forward: z1 = g W1 + b1, pred = ReLU(z1) . w2 + b2.
-int launch_head_fwd(int G, int H, int Hh, DevDims dims, const float *g, const float *w1,
-                    const float *b1, const float *w2, const float *b2, float *z1, float *pred,
-                    cudaStream_t s);
-// Head backward with the MSE loss (dpred_in == nullptr) or a given dL/dpred.
-// Writes grads of w1, b1, w2, b2 (contiguous, layout order) and dg.
-int launch_head_bwd(int G, int H, int Hh, DevDims dims, const float *g, const float *w1,
-                    const float *w2, const float *z1, const float *pred, const float *y,
-                    const float *dpred_in, float *dpred, float *dz1, float *grad_head, float *dg,
-                    double *loss_accum, cudaStream_t s);
-// AdamW over n floats; step counter and lr live in device memory.
-int launch_adam(int64_t n, float *param, const float *grad, float *m, float *v, int *step,
-                const float *lr, float beta1, float beta2, float eps, float wd, cudaStream_t s);
+
+// Per-graph part of the head (one block per graph): forward = mean pooling,
+// z1 = g W1 + b1, pred = ReLU(z1) . w2 + b2; backward = dpred (dpred_in, or
+// the MSE gradient 2 (pred - y) / G), dz1, dg = W1 dz1 and the pooling
+// gradient on the graph's nodes (plus D3 as in launch_pool_bwd).
+struct HeadArgs {
+  int g_cap, H, Hh, rk;  // rk is set by the launcher
+  DevDims dims;
+  const int *node_off;
+  const float *x;
+  const float *w1, *b1, *w2, *b2;
+  float *pooled, *z1, *pred;
+  const float *y, *dpred_in;
+  float *dpred, *dz1, *dg, *dx;
+  uint16_t *D3;
+  int ld3;
+  const float *h, *amp, *att;
+};
+int launch_head_graph(HeadArgs a, bool fwd, bool bwd, cudaStream_t s);
+// Head parameter gradients (w1, b1, w2, b2, contiguous in layout order) summed
+// over the batch's graphs, and the FP64 loss sums into loss_accum (nullable).
+struct HeadGradArgs {
+  int g_cap, H, Hh;
+  DevDims dims;
+  const float *pooled, *z1, *dz1, *dpred, *pred, *y;
+  float *grad;
+  double *loss_accum;
+};
+int launch_head_grad(const HeadGradArgs &a, cudaStream_t s);
+
+// AdamW over n floats.  state[0] is the step counter (advanced by the kernel),
+// ticket a zero-initialised device word.  With wb non-null the updated
+// parameters are also written as BF16 (flat copy wb, and the packed backward
+// operands wpack of every layer when non-null).
+struct AdamPack {
+  int H, L;
+  long long layers_begin, layer_size;
+};
+int launch_adam(int64_t n, float *param, const float *grad, float *m, float *v, int *state, unsigned *ticket,
+                const float *lr, float beta1, float beta2, float eps, float wd, uint16_t *wb, uint16_t *wpack,
+                AdamPack pk, cudaStream_t s);
 
 // ---------------------------------------------------------------- gemm_simt.cu
 // C = op(A) . op(B) in FP32 on CUDA cores (FFMA), with operands assembled on
@@ -170,10 +198,9 @@ int launch_cast_bf16(int64_t n, const float *src, uint16_t *dst, cudaStream_t s)
 // BF16 weight layouts of one layer for the backward GEMMs (see gemm_tc.cu)
 int launch_pack_layer(int H, const float *msg_w, const float *upd_w, uint16_t *Wd, uint16_t *Wx, cudaStream_t s);
 // Column sums over the batch's nodes of [a0 * [mask > 0] | a1] (cols0 + cols1
-// columns; mask and a1 nullable) into out0[cols0] and out1[cols1];
-// deterministic two-stage sum.  partial holds ceil(n_cap / 32) * (cols0 +
-// cols1) floats.
+// columns, each a multiple of 4; mask and a1 nullable) into out0[cols0] and
+// out1[cols1]; fixed-order sum, one launch.
 int launch_colsum2(int n_cap, int cols0, int cols1, DevDims dims, const float *a0, int ld0, const float *mask,
-                   int ldm, const float *a1, int ld1, float *partial, float *out0, float *out1, cudaStream_t s);
+                   int ldm, const float *a1, int ld1, float *out0, float *out1, cudaStream_t s);
 
 }  // namespace gcnn

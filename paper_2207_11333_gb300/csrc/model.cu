@@ -42,6 +42,27 @@ float *agg_at(const gcnn_ctx *c, int l) {
   return c->agg + (c->cfg.recompute ? 0 : (size_t)l * c->Nc * kAgg * c->H);
 }
 
+bool bf16(const gcnn_ctx *c);
+
+// Arguments of the per-graph head kernel; its pooling gradient goes to dH
+// (and, with BF16 GEMMs, to the masked and scaled operand block G5[0]).
+HeadArgs head_args(gcnn_ctx *c, int G, const float *dpred_in) {
+  float *hp = head_ptr(c->params, c);
+  const int64_t HHh = (int64_t)c->H * c->Hh;
+  HeadArgs a{};
+  a.g_cap = G; a.H = c->H; a.Hh = c->Hh; a.dims = DevDims{c->bb.dims};
+  a.node_off = c->bb.node_off; a.x = xs_at(c, c->L);
+  a.w1 = hp; a.b1 = hp + HHh; a.w2 = hp + HHh + c->Hh; a.b2 = hp + HHh + 2 * c->Hh;
+  a.pooled = c->pooled; a.z1 = c->z1; a.pred = c->pred;
+  a.y = c->bb.y; a.dpred_in = dpred_in;
+  a.dpred = c->dpred; a.dz1 = c->dz1; a.dg = c->dg; a.dx = c->dH;
+  if (bf16(c)) {
+    a.D3 = c->G5[0]; a.ld3 = 5 * c->H;
+    a.h = xs_at(c, c->L); a.amp = c->bb.amp; a.att = c->bb.att;
+  }
+  return a;
+}
+
 int gemm(gcnn_ctx *c, const GemmDesc &d) {
   PhaseScope ps(c, GCNN_PHASE_GEMM);
   return run_gemm_simt(d, DevDims{c->bb.dims}, c->ws, c->stream);
@@ -193,8 +214,7 @@ int tc_backward_layer(gcnn_ctx *c, int Ngrid, int Egrid, int l, int cur) {
     GCNN_TRY(tc(c, d));
     // bias gradients: db_U = sum of dpre, db_M = sum of dP (FP32, fixed order)
     PhaseScope ps(c, GCNN_PHASE_GEMM);
-    GCNN_TRY(launch_colsum2(Ngrid, H, H, dims, c->dH, H, h, H, c->dPQ, 2 * H, c->colsum_partial, gw.upd_b, gw.msg_b,
-                            c->stream));
+    GCNN_TRY(launch_colsum2(Ngrid, H, H, dims, c->dH, H, h, H, c->dPQ, 2 * H, gw.upd_b, gw.msg_b, c->stream));
   }
   {  // dx = [g | dP | dQ] [W_x | A | B]^T ; the next layer's masked, scaled BF16 gradient
     TcDesc d = tblank();
@@ -258,27 +278,19 @@ int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train) {
     else GCNN_TRY(gemm_update(c, Ngrid, l));
   }
   PhaseScope ps(c, GCNN_PHASE_HEAD);
-  GCNN_TRY(launch_pool_fwd(G, H, dims, c->bb.node_off, xs_at(c, c->L), c->pooled, c->stream));
-  float *hp = head_ptr(c->params, c);
-  const int64_t HHh = (int64_t)H * c->Hh;
-  GCNN_TRY(launch_head_fwd(G, H, c->Hh, dims, c->pooled, hp, hp + HHh, hp + HHh + c->Hh,
-                           hp + HHh + 2 * c->Hh, c->z1, c->pred, c->stream));
-  (void)train;
+  GCNN_TRY(launch_head_graph(head_args(c, G, nullptr), true, train && c->fuse_head, c->stream));
   return GCNN_OK;
 }
 
 int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, double *loss_accum) {
   const int H = c->H;
   DevDims dims{c->bb.dims};
-  float *hp = head_ptr(c->params, c);
-  float *ghp = head_ptr(c->grads, c);
-  const int64_t HHh = (int64_t)H * c->Hh;
   {
-  PhaseScope ps(c, GCNN_PHASE_HEAD);
-  GCNN_TRY(launch_head_bwd(G, H, c->Hh, dims, c->pooled, hp, hp + HHh + c->Hh, c->z1, c->pred,
-                           c->bb.y, dpred, c->dpred, c->dz1, ghp, c->dg, loss_accum, c->stream));
-  GCNN_TRY(launch_pool_bwd(G, Ngrid, H, dims, c->bb.node_off, c->bb.graph_id, c->dg, c->dH, c->stream,
-                           bf16(c) ? c->G5[0] : nullptr, 5 * H, xs_at(c, c->L), c->bb.amp, c->bb.att));
+    PhaseScope ps(c, GCNN_PHASE_HEAD);
+    if (!c->fuse_head) GCNN_TRY(launch_head_graph(head_args(c, G, dpred), false, true, c->stream));
+    HeadGradArgs ga{G, H, c->Hh, dims, c->pooled, c->z1, c->dz1, c->dpred, c->pred, c->bb.y,
+                    head_ptr(c->grads, c), loss_accum};
+    GCNN_TRY(launch_head_grad(ga, c->stream));
   }
   if (bf16(c)) {
     int cur = 0;
@@ -364,17 +376,16 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
   }
   // embedding: dEmb[t] = sum of dx0 over nodes of type t
   PhaseScope ps(c, GCNN_PHASE_EMBED_BWD);
-  GCNN_TRY(launch_embed_bwd(Ngrid, H, dims, c->bb.types, c->dH, c->T, c->emb_partial, c->emb_chunks,
-                            c->grads, c->stream));
+  GCNN_TRY(launch_embed_bwd(Ngrid, H, dims, c->bb.types, c->dH, c->T, c->grads, c->stream));
   return GCNN_OK;
 }
 
 int ctx_step(gcnn_ctx *c) {
   PhaseScope ps(c, GCNN_PHASE_ADAM);
-  GCNN_TRY(launch_adam(c->P, c->params, c->grads, c->adam_m, c->adam_v, c->opt_state, c->lr_dev,
-                       (float)c->cfg.beta1, (float)c->cfg.beta2, (float)c->cfg.adam_eps,
-                       (float)c->cfg.weight_decay, c->stream));
-  if (c->wb) GCNN_TRY(ctx_refresh_bf16(c));
+  const AdamPack pk{c->H, c->L, (long long)c->T * c->H, (long long)c->layer_size};
+  GCNN_TRY(launch_adam(c->P, c->params, c->grads, c->adam_m, c->adam_v, c->opt_state, c->tickets, c->lr_dev,
+                       (float)c->cfg.beta1, (float)c->cfg.beta2, (float)c->cfg.adam_eps, (float)c->cfg.weight_decay,
+                       c->wb, c->wpack, pk, c->stream));
   return GCNN_OK;
 }
 

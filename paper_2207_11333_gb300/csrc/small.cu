@@ -20,6 +20,7 @@ __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<floa
 __global__ void embed_kernel(int n_cap, int H, DevDims dims, const uint8_t *__restrict__ types,
                              const float *__restrict__ emb, int T, float *__restrict__ x0,
                              uint16_t *__restrict__ x0_16, int ld16) {
+  pdl_entry();
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -31,50 +32,65 @@ __global__ void embed_kernel(int n_cap, int H, DevDims dims, const uint8_t *__re
   if (x0_16) st_bf16x4(x0_16 + (size_t)i * ld16 + c, v.x, v.y, v.z, v.w);
 }
 
-constexpr int kEmbChunk = 16;   // nodes per partial sum
 constexpr int kMaxTypes = 16;
+constexpr int kRedThreads = 256;
 
-// partial[ch][t][c] = sum over nodes of chunk ch with type t of dx0[., c]
-__global__ void embed_bwd_partial_kernel(int n_cap, int H, DevDims dims,
-                                         const uint8_t *__restrict__ types,
-                                         const float *__restrict__ dx0, int T,
-                                         float *__restrict__ partial) {
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// Butterfly sum over the warp (fixed order; every lane gets the total).
+__device__ __forceinline__ float4 warp_sum4(float4 a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+    a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+    a.z += __shfl_xor_sync(0xffffffffu, a.z, o);
+    a.w += __shfl_xor_sync(0xffffffffu, a.w, o);
+  }
+  return a;
+}
+
+// dEmb[t][c..c+3] = sum of dx0[i][c..c+3] over the nodes i of type t.  One
+// block per 4-column slice; nodes strided over the block's threads, then a
+// fixed-order reduction (warp butterflies, warps in index order).
+__global__ void __launch_bounds__(kRedThreads)
+embed_bwd_kernel(int n_cap, int H, DevDims dims, const uint8_t *__restrict__ types, const float *__restrict__ dx0,
+                 int T, float *__restrict__ demb) {
+  pdl_entry();
+  __shared__ float4 sh[kRedThreads / 32][kMaxTypes];
   const int N = min(n_cap, dims.nodes(n_cap));
-  const int ch = blockIdx.x;
-  const int i0 = ch * kEmbChunk;
-  const int H4 = H >> 2;
-  const int c4 = blockIdx.y * blockDim.x + threadIdx.x;
-  if (c4 >= H4) return;
+  const int c = blockIdx.x * 4;
   float4 acc[kMaxTypes];
 #pragma unroll
   for (int t = 0; t < kMaxTypes; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (i0 < N) {
-    const int i1 = min(N, i0 + kEmbChunk);
-    for (int i = i0; i < i1; ++i) {
-      const int ty = types[i];
-      const float4 v = ld4(dx0 + (size_t)i * H + c4 * 4);
+#pragma unroll 4
+  for (int i = threadIdx.x; i < N; i += kRedThreads) {
+    const int ty = types[i];
+    const float4 v = ld4(dx0 + (size_t)i * H + c);
 #pragma unroll
-      for (int t = 0; t < kMaxTypes; ++t)
-        if (t == ty) { acc[t].x += v.x; acc[t].y += v.y; acc[t].z += v.z; acc[t].w += v.w; }
-    }
+    for (int t = 0; t < kMaxTypes; ++t)
+      if (t == ty) acc[t] = add4(acc[t], v);
   }
-  for (int t = 0; t < T; ++t) st4(partial + ((size_t)ch * T + t) * H + c4 * 4, acc[t]);
-}
-
-__global__ void embed_bwd_reduce_kernel(int n_cap, int H, DevDims dims, int T,
-                                        const float *__restrict__ partial, float *__restrict__ demb) {
-  const int N = min(n_cap, dims.nodes(n_cap));
-  const int chunks = (N + kEmbChunk - 1) / kEmbChunk;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // over T * H
-  if (idx >= T * H) return;
-  float s = 0.f;
-  for (int ch = 0; ch < chunks; ++ch) s += partial[(size_t)ch * T * H + idx];
-  demb[idx] = s;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < kMaxTypes; ++t) {
+    if (t >= T) break;
+    const float4 a = warp_sum4(acc[t]);
+    if (lane == 0) sh[w][t] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < T) {
+    float4 sum = sh[0][threadIdx.x];
+    for (int q = 1; q < kRedThreads / 32; ++q) sum = add4(sum, sh[q][threadIdx.x]);
+    st4(demb + (size_t)threadIdx.x * H + c, sum);
+  }
 }
 
 // ---------------------------------------------------------------- pooling
 __global__ void pool_fwd_kernel(int g_cap, int H, DevDims dims, const int *__restrict__ node_off,
                                 const float *__restrict__ x, float *__restrict__ pooled) {
+  pdl_entry();
   const int H4 = H >> 2;
   const int G = min(g_cap, dims.graphs(g_cap));
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -97,6 +113,7 @@ __global__ void pool_bwd_kernel(int n_cap, int H, DevDims dims, const int *__res
                                 const int *__restrict__ graph_id, const float *__restrict__ dpooled,
                                 float *__restrict__ dx, uint16_t *__restrict__ D3, int ld3, const float *__restrict__ h,
                                 const float *__restrict__ amp, const float *__restrict__ att) {
+  pdl_entry();
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -120,160 +137,245 @@ __global__ void pool_bwd_kernel(int n_cap, int H, DevDims dims, const int *__res
 }
 
 // ---------------------------------------------------------------- head
-// Deterministic block sum of one float per thread (blockDim.x == kThreads).
-__device__ float block_sum(float v, float *sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+// Deterministic block sum of one value per thread (blockDim.x == NT): warp
+// butterflies, then the warps' sums in index order.  Valid in thread 0.
+template <int NT, typename F>
+__device__ F block_sum(F v, F *sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __syncthreads();
   if (lane == 0) sh[w] = v;
   __syncthreads();
-  float s = 0.f;
+  F s = F(0);
   if (threadIdx.x == 0)
-    for (int q = 0; q < kThreads / 32; ++q) s += sh[q];
-  return s;  // valid in thread 0
-}
-
-__device__ double block_sum_d(double v, double *sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int q = 0; q < kThreads / 32; ++q) s += sh[q];
+    for (int q = 0; q < NT / 32; ++q) s += sh[q];
   return s;
 }
 
-// one block per graph
-__global__ void __launch_bounds__(kThreads)
-head_fwd_kernel(int g_cap, int H, int Hh, DevDims dims, const float *__restrict__ g,
-                const float *__restrict__ w1, const float *__restrict__ b1,
-                const float *__restrict__ w2, const float *__restrict__ b2,
-                float *__restrict__ z1, float *__restrict__ pred) {
-  extern __shared__ float sg[];  // H floats
-  __shared__ float red[kThreads / 32];
-  const int G = min(g_cap, dims.graphs(g_cap));
+constexpr int kHeadThreads = 512;
+
+// Per-graph part of the head (one block per graph).  Forward: mean pooling of
+// the last layer's features, z1 = g W1 + b1, pred = ReLU(z1) w2 + b2.
+// Backward: dpred (given, or 2 (pred - y) / G), dz1 = [z1 > 0] dpred w2,
+// dg = W1 dz1 and the pooling gradient dx_i = dg / n_g on the graph's nodes,
+// optionally also as the BF16 blocks [amp g | att g | g], g = dx [h > 0].
+// W1 is staged in shared memory, rk rows at a time.
+
+template <bool kFwd, bool kBwd>
+__global__ void __launch_bounds__(kHeadThreads) head_graph_kernel(HeadArgs a) {
+  pdl_entry();
+  extern __shared__ float sm[];
+  __shared__ float red[kHeadThreads / 32];
+  __shared__ float s_pred, s_dp;
+  const int H = a.H, Hh = a.Hh, rk = a.rk;
+  float *Ws = sm;                     // rk x Hh
+  float *sv = Ws + (size_t)rk * Hh;   // H: pooled features, later dg
+  float *sz = sv + H;                 // Hh: z1
+  float *sd = sz + Hh;                // Hh: dz1
+  const int G = min(a.g_cap, a.dims.graphs(a.g_cap));
   const int gr = blockIdx.x;
   if (gr >= G) return;  // block-uniform
-  for (int k = threadIdx.x; k < H; k += blockDim.x) sg[k] = g[(size_t)gr * H + k];
-  __syncthreads();
-  float part = 0.f;
-  for (int c = threadIdx.x; c < Hh; c += blockDim.x) {
-    float a[4] = {b1[c], 0.f, 0.f, 0.f};  // four independent chains, summed in a fixed order
-    int k = 0;
-    for (; k + 4 <= H; k += 4) {
+  const int tid = threadIdx.x;
+  const int n0 = a.node_off[gr], n1 = a.node_off[gr + 1], nn = n1 - n0;
+  const int nchunks = (H + rk - 1) / rk;
+  int staged = -1;
+  auto stage = [&](int ch) {  // rows [ch * rk, ...) of W1 into Ws
+    __syncthreads();
+    const int k0 = ch * rk, cnt = min(rk, H - k0) * Hh;
+    const float4 *src = reinterpret_cast<const float4 *>(a.w1 + (size_t)k0 * Hh);
+    float4 *dst = reinterpret_cast<float4 *>(Ws);
+#pragma unroll 4
+    for (int q = tid; q < cnt / 4; q += kHeadThreads) dst[q] = src[q];
+    for (int q = cnt / 4 * 4 + tid; q < cnt; q += kHeadThreads) Ws[q] = a.w1[(size_t)k0 * Hh + q];
+    __syncthreads();
+    staged = ch;
+  };
+  if (kFwd) {
+    for (int k = tid; k < H; k += kHeadThreads) {
+      float s4[4] = {0.f, 0.f, 0.f, 0.f};
+      int i = n0;
+      for (; i + 4 <= n1; i += 4) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] += sg[k + u] * w1[(size_t)(k + u) * Hh + c];
+        for (int u = 0; u < 4; ++u) s4[u] += a.x[(size_t)(i + u) * H + k];
+      }
+      for (; i < n1; ++i) s4[0] += a.x[(size_t)i * H + k];
+      float v = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+      if (nn > 0) v /= (float)nn;
+      sv[k] = v;
+      a.pooled[(size_t)gr * H + k] = v;
     }
-    for (; k < H; ++k) a[0] += sg[k] * w1[(size_t)k * Hh + c];
-    const float acc = (a[0] + a[1]) + (a[2] + a[3]);
-    z1[(size_t)gr * Hh + c] = acc;
-    part += fmaxf(acc, 0.f) * w2[c];
-  }
-  const float s = block_sum(part, red);
-  if (threadIdx.x == 0) pred[gr] = s + b2[0];
-}
-
-// one block: dL/dpred, the loss sums and the gradient of b2 (G values)
-__global__ void __launch_bounds__(kThreads)
-head_bwd_loss_kernel(int g_cap, DevDims dims, const float *__restrict__ pred, const float *__restrict__ y,
-                     const float *__restrict__ dpred_in, float *__restrict__ dpred, float *__restrict__ grad_b2,
-                     double *__restrict__ loss_accum) {
-  __shared__ double redd[kThreads / 32];
-  __shared__ float redf[kThreads / 32];
-  const int G = min(g_cap, dims.graphs(g_cap));
-  double se = 0.0, ae = 0.0;
-  float db2 = 0.f;
-  for (int gr = threadIdx.x; gr < G; gr += blockDim.x) {
-    const float r = pred[gr] - y[gr];
-    const float dp = dpred_in ? dpred_in[gr] : 2.f * r / (float)G;
-    dpred[gr] = dp;
-    se += (double)r * (double)r;
-    ae += fabs((double)r);
-    db2 += dp;
-  }
-  const double sse = block_sum_d(se, redd);
-  const double sae = block_sum_d(ae, redd);
-  const float sdb2 = block_sum(db2, redf);
-  if (threadIdx.x == 0) {
-    grad_b2[0] = sdb2;
-    if (loss_accum) {
-      loss_accum[0] += sse;
-      loss_accum[1] += sae;
-      loss_accum[2] += (double)G;
-    }
-  }
-}
-
-// grads of w1 (H x Hh), b1, w2 and dg (G x H): one thread per output, sums
-// over graphs / head units in a fixed order; dz1 = [z1 > 0] dpred w2 inline
-__global__ void __launch_bounds__(kThreads)
-head_bwd_grad_kernel(int g_cap, int H, int Hh, DevDims dims, const float *__restrict__ g,
-                     const float *__restrict__ w1, const float *__restrict__ w2, const float *__restrict__ z1,
-                     const float *__restrict__ dpred, float *__restrict__ grad_head, float *__restrict__ dg) {
-  const int G = min(g_cap, dims.graphs(g_cap));
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n_w1 = (long long)H * Hh;
-  if (idx < n_w1) {
-    const int k = (int)(idx / Hh), c = (int)(idx % Hh);
-    const float wc = w2[c];
-    float a[4] = {0.f, 0.f, 0.f, 0.f};
-    int gr = 0;
-    for (; gr + 4 <= G; gr += 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float z = z1[(size_t)(gr + u) * Hh + c];
-        a[u] += z > 0.f ? g[(size_t)(gr + u) * H + k] * (dpred[gr + u] * wc) : 0.f;
+    for (int c = tid; c < Hh; c += kHeadThreads) sz[c] = a.b1[c];
+    for (int ch = 0; ch < nchunks; ++ch) {
+      stage(ch);
+      const int k0 = ch * rk, rows = min(rk, H - k0);
+      for (int c = tid; c < Hh; c += kHeadThreads) {
+        float acc = sz[c];
+#pragma unroll 8
+        for (int k = 0; k < rows; ++k) acc += sv[k0 + k] * Ws[(size_t)k * Hh + c];
+        sz[c] = acc;
       }
     }
-    for (; gr < G; ++gr) {
-      const float z = z1[(size_t)gr * Hh + c];
-      a[0] += z > 0.f ? g[(size_t)gr * H + k] * (dpred[gr] * wc) : 0.f;
+    __syncthreads();
+    float part = 0.f;
+    for (int c = tid; c < Hh; c += kHeadThreads) {
+      a.z1[(size_t)gr * Hh + c] = sz[c];
+      part += fmaxf(sz[c], 0.f) * a.w2[c];
     }
-    grad_head[idx] = (a[0] + a[1]) + (a[2] + a[3]);
-  } else if (idx < n_w1 + Hh) {
-    const int c = (int)(idx - n_w1);
-    const float wc = w2[c];
-    float s = 0.f;
-    for (int gr = 0; gr < G; ++gr) s += z1[(size_t)gr * Hh + c] > 0.f ? dpred[gr] * wc : 0.f;
-    grad_head[idx] = s;
-  } else if (idx < n_w1 + 2 * Hh) {
-    const int c = (int)(idx - n_w1 - Hh);
-    float s = 0.f;
-    for (int gr = 0; gr < G; ++gr) s += fmaxf(z1[(size_t)gr * Hh + c], 0.f) * dpred[gr];
-    grad_head[idx] = s;
-  } else if (idx < n_w1 + 2 * Hh + (long long)g_cap * H) {
-    const long long r = idx - n_w1 - 2 * Hh;
-    const int gr = (int)(r / H), k = (int)(r % H);
-    if (gr >= G) return;
-    const float dp = dpred[gr];
-    float a[4] = {0.f, 0.f, 0.f, 0.f};
-    int c = 0;
-    for (; c + 4 <= Hh; c += 4) {
+    const float s = block_sum<kHeadThreads>(part, red);
+    if (tid == 0) {
+      s_pred = s + a.b2[0];
+      a.pred[gr] = s_pred;
+    }
+  }
+  if (kBwd) {
+    if (!kFwd) {
+      for (int c = tid; c < Hh; c += kHeadThreads) sz[c] = a.z1[(size_t)gr * Hh + c];
+      if (tid == 0) s_pred = a.pred[gr];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const float r = s_pred - a.y[gr];
+      const float dp = a.dpred_in ? a.dpred_in[gr] : 2.f * r / (float)G;
+      a.dpred[gr] = dp;
+      s_dp = dp;
+    }
+    __syncthreads();
+    const float dp = s_dp;
+    for (int c = tid; c < Hh; c += kHeadThreads) {
+      const float d = sz[c] > 0.f ? dp * a.w2[c] : 0.f;
+      sd[c] = d;
+      a.dz1[(size_t)gr * Hh + c] = d;
+    }
+    // dg = W1 dz1, chunks in reverse order (the forward's last chunk is still staged)
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int ch = nchunks - 1; ch >= 0; --ch) {
+      if (staged != ch) stage(ch);
+      else __syncthreads();
+      const int k0 = ch * rk, rows = min(rk, H - k0);
+      for (int k = warp; k < rows; k += kHeadThreads / 32) {
+        float acc = 0.f;
+        for (int c = lane; c < Hh; c += 32) acc += Ws[(size_t)k * Hh + c] * sd[c];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float z = z1[(size_t)gr * Hh + c + u];
-        a[u] += z > 0.f ? w1[(size_t)k * Hh + c + u] * (dp * w2[c + u]) : 0.f;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+          sv[k0 + k] = acc;
+          a.dg[(size_t)gr * H + k0 + k] = acc;
+        }
       }
     }
-    for (; c < Hh; ++c) {
-      const float z = z1[(size_t)gr * Hh + c];
-      a[0] += z > 0.f ? w1[(size_t)k * Hh + c] * (dp * w2[c]) : 0.f;
+    __syncthreads();
+    // mean pooling backward on the graph's nodes
+    const float n = (float)nn;
+    const int H4 = H >> 2;
+    for (int q = tid; q < nn * H4; q += kHeadThreads) {
+      const int i = n0 + q / H4, c = (q % H4) * 4;
+      const float4 d = make_float4(sv[c] / n, sv[c + 1] / n, sv[c + 2] / n, sv[c + 3] / n);
+      st4(a.dx + (size_t)i * H + c, d);
+      if (a.D3) {
+        const float4 m = ld4(a.h + (size_t)i * H + c);
+        const float gx = m.x > 0.f ? d.x : 0.f, gy = m.y > 0.f ? d.y : 0.f;
+        const float gz = m.z > 0.f ? d.z : 0.f, gw = m.w > 0.f ? d.w : 0.f;
+        const float am = a.amp[i], at = a.att[i];
+        uint16_t *o = a.D3 + (size_t)i * a.ld3 + c;
+        st_bf16x4(o, am * gx, am * gy, am * gz, am * gw);
+        st_bf16x4(o + H, at * gx, at * gy, at * gz, at * gw);
+        st_bf16x4(o + 2 * H, gx, gy, gz, gw);
+      }
     }
-    dg[(size_t)gr * H + k] = (a[0] + a[1]) + (a[2] + a[3]);
+  }
+}
+
+// Head parameter gradients, summed over the batch's graphs in a fixed order:
+// W1 (H x Hh) = pooled^T dz1 in 32 x 32 tiles (grid.y < ceil(H / 32)); the last
+// row of blocks: b1 = sum dz1, w2 = sum ReLU(z1) dpred, and in block (0, .)
+// b2 = sum dpred and the FP64 loss sums (squared and absolute error, count).
+constexpr int kHT = 32, kHG = 64;
+
+
+__global__ void __launch_bounds__(kRedThreads) head_grad_kernel(HeadGradArgs a) {
+  pdl_entry();
+  __shared__ float sp[kHG][kHT + 1], sd[kHG][kHT + 1];
+  __shared__ double redd[kRedThreads / 32];
+  __shared__ float redf[kRedThreads / 32];
+  const int G = min(a.g_cap, a.dims.graphs(a.g_cap));
+  const int H = a.H, Hh = a.Hh, tid = threadIdx.x;
+  const int c0 = blockIdx.x * kHT;
+  const int tc = tid & 31, q8 = tid >> 5;
+  if ((int)blockIdx.y < (H + kHT - 1) / kHT) {
+    const int k0 = blockIdx.y * kHT;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int g0 = 0; g0 < G; g0 += kHG) {
+      const int gn = min(kHG, G - g0);
+      __syncthreads();
+      for (int q = tid; q < kHG * kHT; q += kRedThreads) {
+        const int gg = q / kHT, cc = q % kHT;
+        const bool in = gg < gn;
+        sp[gg][cc] = in && k0 + cc < H ? a.pooled[(size_t)(g0 + gg) * H + k0 + cc] : 0.f;
+        sd[gg][cc] = in && c0 + cc < Hh ? a.dz1[(size_t)(g0 + gg) * Hh + c0 + cc] : 0.f;
+      }
+      __syncthreads();
+      for (int gg = 0; gg < gn; ++gg) {
+        const float d = sd[gg][tc];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r] += sp[gg][q8 + 8 * r] * d;
+      }
+    }
+    const int c = c0 + tc;
+    if (c < Hh)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int k = k0 + q8 + 8 * r;
+        if (k < H) a.grad[(size_t)k * Hh + c] = acc[r];
+      }
+    return;
+  }
+  // b1 and w2 for columns c0 .. c0 + 31: graphs strided over the 8 warps
+  {
+    const int c = c0 + tc;
+    float sb = 0.f, sw = 0.f;
+    if (c < Hh)
+      for (int g = q8; g < G; g += kRedThreads / 32) {
+        sb += a.dz1[(size_t)g * Hh + c];
+        sw += fmaxf(a.z1[(size_t)g * Hh + c], 0.f) * a.dpred[g];
+      }
+    sp[q8][tc] = sb;
+    sd[q8][tc] = sw;
+    __syncthreads();
+    if (q8 == 0 && c < Hh) {
+      float tb = sp[0][tc], tw = sd[0][tc];
+      for (int q = 1; q < kRedThreads / 32; ++q) {
+        tb += sp[q][tc];
+        tw += sd[q][tc];
+      }
+      a.grad[(size_t)H * Hh + c] = tb;
+      a.grad[(size_t)H * Hh + Hh + c] = tw;
+    }
+  }
+  if (blockIdx.x == 0) {
+    double se = 0.0, ae = 0.0;
+    float db2 = 0.f;
+    for (int g = tid; g < G; g += kRedThreads) {
+      const float r = a.pred[g] - a.y[g];
+      se += (double)r * (double)r;
+      ae += fabs((double)r);
+      db2 += a.dpred[g];
+    }
+    const double sse = block_sum<kRedThreads>(se, redd);
+    const double sae = block_sum<kRedThreads>(ae, redd);
+    const float sdb2 = block_sum<kRedThreads>(db2, redf);
+    if (tid == 0) {
+      a.grad[(size_t)H * Hh + 2 * Hh] = sdb2;
+      if (a.loss_accum) {
+        a.loss_accum[0] += sse;
+        a.loss_accum[1] += sae;
+        a.loss_accum[2] += (double)G;
+      }
+    }
   }
 }
 
 // ---------------------------------------------------------------- AdamW
-// step[0]: step counter; coef[0] = 1/(1-beta1^t), coef[1] = 1/(1-beta2^t)
-__global__ void adam_tick_kernel(int *step, float *coef, float beta1, float beta2) {
-  const int t = step[0] + 1;
-  step[0] = t;
-  coef[0] = (float)(1.0 / (1.0 - pow((double)beta1, (double)t)));
-  coef[1] = (float)(1.0 / (1.0 - pow((double)beta2, (double)t)));
-}
-
 __device__ __forceinline__ void adam_one(float &p, float g, float &m, float &v, float lr, float c1,
                                          float c2, float b1, float b2, float eps, float wd) {
   if (wd > 0.f) p -= lr * wd * p;
@@ -282,11 +384,43 @@ __device__ __forceinline__ void adam_one(float &p, float g, float &m, float &v, 
   p -= lr * (m * c1) / (sqrtf(v * c2) + eps);
 }
 
+// Destination of parameter i (a multiple of 4) in the packed BF16 operands of
+// the backward GEMMs, or -1: per layer Wd[n][s*H + c] = W_U[H + blk(s)*5H + n][c]
+// (s = 0, 1, 2 for the amplification, attenuation and identity blocks) and
+// Wx[n] = [W_U[n][0..H) | W_M[n][0..2H)].
+__device__ __forceinline__ long long packed_index(long long i, const AdamPack &k) {
+  const long long H = k.H;
+  const long long o0 = i - k.layers_begin;
+  if (o0 < 0 || o0 >= (long long)k.L * k.layer_size) return -1;
+  const long long l = o0 / k.layer_size, o = o0 % k.layer_size;
+  const long long base = l * 18 * H * H, wx = base + 15 * H * H;
+  if (o < 2 * H * H) return wx + (o / (2 * H)) * 3 * H + H + o % (2 * H);  // W_M
+  const long long u = o - (2 * H * H + H);
+  if (u < 0 || u >= 16 * H * H) return -1;  // biases
+  const long long r = u / H, c = u % H;
+  if (r < H) return wx + r * 3 * H + c;
+  const long long rr = r - H, blk = rr / (5 * H), n = rr % (5 * H);
+  return base + n * 3 * H + ((blk + 2) % 3) * H + c;
+}
+
+// AdamW over the flat FP32 parameters.  The step counter state[0] is read by
+// every block and advanced by the last block to finish (ticket), so the
+// update of step t uses the bias corrections of t = state[0] + 1.  Optionally
+// writes the BF16 copies of the updated parameters (flat and packed).
 __global__ void __launch_bounds__(kThreads)
 adam_kernel(int64_t n, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
-            float *__restrict__ v, const float *__restrict__ coef, const float *__restrict__ lrp,
-            float b1, float b2, float eps, float wd) {
-  const float c1 = coef[0], c2 = coef[1], lr = lrp[0];
+            float *__restrict__ v, int *__restrict__ state, unsigned *__restrict__ ticket,
+            const float *__restrict__ lrp, float b1, float b2, float eps, float wd, uint16_t *__restrict__ wb,
+            uint16_t *__restrict__ wpack, AdamPack pk) {
+  pdl_entry();
+  __shared__ float s_c[2];
+  const int t = state[0] + 1;
+  if (threadIdx.x == 0) {
+    s_c[0] = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
+    s_c[1] = (float)(1.0 / (1.0 - pow((double)b2, (double)t)));
+  }
+  __syncthreads();
+  const float c1 = s_c[0], c2 = s_c[1], lr = lrp[0];
   const int64_t n4 = n / 4;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
@@ -298,80 +432,80 @@ adam_kernel(int64_t n, float *__restrict__ p, const float *__restrict__ g, float
     st4(p + 4 * q, P);
     st4(m + 4 * q, Mv);
     st4(v + 4 * q, V);
+    if (wb) {
+      st_bf16x4(wb + 4 * q, P.x, P.y, P.z, P.w);
+      const long long d = wpack ? packed_index(4 * q, pk) : -1;
+      if (d >= 0) st_bf16x4(wpack + d, P.x, P.y, P.z, P.w);
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x < (int)(n - 4 * n4)) {
     const int64_t k = 4 * n4 + threadIdx.x;
     float P = p[k], M = m[k], V = v[k];
     adam_one(P, g[k], M, V, lr, c1, c2, b1, b2, eps, wd);
     p[k] = P; m[k] = M; v[k] = V;
+    if (wb) wb[k] = (uint16_t)(bf16x2(P, 0.f) & 0xFFFFu);
   }
-}
-
-constexpr int kColChunk = 32;  // nodes per partial column sum
-
-// Column c < cols of the virtual matrix [a0 * [mask > 0] | a1] (a1 nullable):
-// partial[ch][c] = sum over the nodes of chunk ch.
-__global__ void colsum_partial_kernel(int n_cap, int cols0, int cols1, DevDims dims, const float *__restrict__ a0,
-                                      int ld0, const float *__restrict__ mask, int ldm, const float *__restrict__ a1,
-                                      int ld1, float *__restrict__ partial) {
-  const int N = min(n_cap, dims.nodes(n_cap));
-  const int cols = cols0 + cols1;
-  const int ch = blockIdx.y;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
-  const int i0 = ch * kColChunk;
-  float v[kColChunk];
-#pragma unroll
-  for (int q = 0; q < kColChunk; ++q) {
-    const int i = i0 + q;
-    float x = 0.f;
-    if (i < N) {
-      if (c < cols0) {
-        x = a0[(size_t)i * ld0 + c];
-        if (mask && !(mask[(size_t)i * ldm + c] > 0.f)) x = 0.f;
-      } else {
-        x = a1[(size_t)i * ld1 + (c - cols0)];
-      }
+  // the last block to finish advances the step counter
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ticket, 1u) == gridDim.x - 1) {
+      state[0] = t;
+      *ticket = 0u;
     }
-    v[q] = x;
   }
-  float sum = 0.f;
-#pragma unroll
-  for (int q = 0; q < kColChunk; ++q) sum += v[q];
-  partial[(size_t)ch * cols + c] = sum;
 }
 
-__global__ void colsum_reduce_kernel(int n_cap, int cols0, int cols1, DevDims dims, const float *__restrict__ partial,
-                                     float *__restrict__ out0, float *__restrict__ out1) {
+// out0[c] = sum_i a0[i][c] [mask[i][c] > 0] for c < cols0 and out1[c] =
+// sum_i a1[i][c] for c < cols1: one block per 4-column slice of [a0 | a1],
+// nodes strided over the block's threads, fixed-order reduction.
+__global__ void __launch_bounds__(kRedThreads)
+colsum_kernel(int n_cap, int cols0, DevDims dims, const float *__restrict__ a0, int ld0,
+              const float *__restrict__ mask, int ldm, const float *__restrict__ a1, int ld1,
+              float *__restrict__ out0, float *__restrict__ out1) {
+  pdl_entry();
+  __shared__ float4 sh[kRedThreads / 32];
   const int N = min(n_cap, dims.nodes(n_cap));
-  const int cols = cols0 + cols1;
-  const int chunks = (N + kColChunk - 1) / kColChunk;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
-  float a[4] = {0.f, 0.f, 0.f, 0.f};
-  int ch = 0;
-  for (; ch + 4 <= chunks; ch += 4) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) a[u] += partial[(size_t)(ch + u) * cols + c];
+  const int c = blockIdx.x * 4;
+  const bool first = c < cols0;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+  for (int i = threadIdx.x; i < N; i += kRedThreads) {
+    float4 x;
+    if (first) {
+      x = ld4(a0 + (size_t)i * ld0 + c);
+      if (mask) {
+        const float4 mk = ld4(mask + (size_t)i * ldm + c);
+        x.x = mk.x > 0.f ? x.x : 0.f;
+        x.y = mk.y > 0.f ? x.y : 0.f;
+        x.z = mk.z > 0.f ? x.z : 0.f;
+        x.w = mk.w > 0.f ? x.w : 0.f;
+      }
+    } else {
+      x = ld4(a1 + (size_t)i * ld1 + (c - cols0));
+    }
+    acc = add4(acc, x);
   }
-  for (; ch < chunks; ++ch) a[0] += partial[(size_t)ch * cols + c];
-  const float s = (a[0] + a[1]) + (a[2] + a[3]);
-  if (c < cols0) out0[c] = s;
-  else out1[c - cols0] = s;
+  acc = warp_sum4(acc);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float4 sum = sh[0];
+    for (int q = 1; q < kRedThreads / 32; ++q) sum = add4(sum, sh[q]);
+    st4(first ? out0 + c : out1 + (c - cols0), sum);
+  }
 }
 
 }  // namespace
 
 int launch_colsum2(int n_cap, int cols0, int cols1, DevDims dims, const float *a0, int ld0, const float *mask,
-                   int ldm, const float *a1, int ld1, float *partial, float *out0, float *out1, cudaStream_t s) {
+                   int ldm, const float *a1, int ld1, float *out0, float *out1, cudaStream_t s) {
   const int cols = cols0 + cols1;
-  if (cols <= 0) return GCNN_OK;
-  const int chunks = (int)ceil_div(std::max(n_cap, 1), kColChunk);
-  dim3 grid(ceil_div(cols, 128), chunks);
-  colsum_partial_kernel<<<grid, 128, 0, s>>>(n_cap, cols0, cols1, dims, a0, ld0, mask, ldm, a1, ld1, partial);
-  GCNN_LAUNCH_CHECK();
-  colsum_reduce_kernel<<<ceil_div(cols, 128), 128, 0, s>>>(n_cap, cols0, cols1, dims, partial, out0, out1);
-  GCNN_LAUNCH_CHECK();
+  if (cols <= 0 || n_cap <= 0) return GCNN_OK;
+  if (cols0 % 4 || cols1 % 4 || ld0 % 4 || ld1 % 4 || (mask && ldm % 4))
+    return set_error(GCNN_EINVAL, "colsum: widths and strides must be multiples of 4");
+  GCNN_TRY(launch(colsum_kernel, cols / 4, kRedThreads, 0, s, n_cap, cols0, dims, a0, ld0, mask, ldm, a1, ld1, out0,
+                  out1));
   return GCNN_OK;
 }
 
@@ -379,25 +513,17 @@ int launch_embed(int n_nodes, int H, DevDims dims, const uint8_t *types, const f
                  int n_types, float *x0, cudaStream_t s, uint16_t *x0_16, int ld16) {
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
-  embed_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(n_nodes, H, dims, types, emb, n_types, x0, x0_16, ld16);
-  GCNN_LAUNCH_CHECK();
+  GCNN_TRY(launch(embed_kernel, ceil_div(work, kThreads), kThreads, 0, s, n_nodes, H, dims, types, emb, n_types, x0,
+                  x0_16, ld16));
   return GCNN_OK;
 }
 
-int launch_embed_bwd(int n_nodes, int H, DevDims dims, const uint8_t *types, const float *dx0,
-                     int n_types, float *partial, int max_chunks, float *demb, cudaStream_t s) {
+int launch_embed_bwd(int n_nodes, int H, DevDims dims, const uint8_t *types, const float *dx0, int n_types,
+                     float *demb, cudaStream_t s) {
   if (n_types > kMaxTypes) return set_error(GCNN_EINVAL, "at most %d atom types", kMaxTypes);
-  const int chunks = (int)ceil_div(n_nodes, kEmbChunk);
-  if (chunks > max_chunks) return set_error(GCNN_EINVAL, "embedding workspace too small");
-  const int H4 = H / 4;
-  if (chunks > 0) {
-    dim3 grid(chunks, ceil_div(H4, 64));
-    embed_bwd_partial_kernel<<<grid, 64, 0, s>>>(n_nodes, H, dims, types, dx0, n_types, partial);
-    GCNN_LAUNCH_CHECK();
-  }
-  embed_bwd_reduce_kernel<<<ceil_div((long long)n_types * H, kThreads), kThreads, 0, s>>>(
-      n_nodes, H, dims, n_types, partial, demb);
-  GCNN_LAUNCH_CHECK();
+  if (H % 4) return set_error(GCNN_EINVAL, "embedding: hidden must be a multiple of 4");
+  GCNN_TRY(launch(embed_bwd_kernel, H / 4, kRedThreads, 0, s, std::max(n_nodes, 0), H, dims, types, dx0, n_types,
+                  demb));
   return GCNN_OK;
 }
 
@@ -405,8 +531,7 @@ int launch_pool_fwd(int G, int H, DevDims dims, const int *node_off, const float
                     cudaStream_t s) {
   if (G <= 0) return GCNN_OK;
   const long long work = (long long)G * (H / 4);
-  pool_fwd_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(G, H, dims, node_off, x, pooled);
-  GCNN_LAUNCH_CHECK();
+  GCNN_TRY(launch(pool_fwd_kernel, ceil_div(work, kThreads), kThreads, 0, s, G, H, dims, node_off, x, pooled));
   return GCNN_OK;
 }
 
@@ -416,45 +541,54 @@ int launch_pool_bwd(int G, int n_nodes, int H, DevDims dims, const int *node_off
   (void)G;
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
-  pool_bwd_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(n_nodes, H, dims, node_off, graph_id,
-                                                                 dpooled, dx, D3, ld3, h, amp, att);
-  GCNN_LAUNCH_CHECK();
+  GCNN_TRY(launch(pool_bwd_kernel, ceil_div(work, kThreads), kThreads, 0, s, n_nodes, H, dims, node_off, graph_id,
+                  dpooled, dx, D3, ld3, h, amp, att));
   return GCNN_OK;
 }
 
-int launch_head_fwd(int G, int H, int Hh, DevDims dims, const float *g, const float *w1,
-                    const float *b1, const float *w2, const float *b2, float *z1, float *pred,
-                    cudaStream_t s) {
-  if (G <= 0) return GCNN_OK;
-  head_fwd_kernel<<<G, kThreads, H * sizeof(float), s>>>(G, H, Hh, dims, g, w1, b1, w2, b2, z1, pred);
-  GCNN_LAUNCH_CHECK();
+namespace {
+constexpr int kHeadSmemFloats = 40 * 1024;  // 160 KB: W1 rows plus pooled / z1 / dz1 vectors
+
+template <bool F, bool B>
+int head_graph(HeadArgs a, cudaStream_t s) {
+  static bool configured = false;
+  const size_t bytes = sizeof(float) * ((size_t)a.rk * a.Hh + a.H + 2 * (size_t)a.Hh);
+  if (!configured) {
+    GCNN_CUDA_TRY(cudaFuncSetAttribute(head_graph_kernel<F, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float) * kHeadSmemFloats)));
+    configured = true;
+  }
+  GCNN_TRY(launch(head_graph_kernel<F, B>, a.g_cap, kHeadThreads, bytes, s, a));
+  return GCNN_OK;
+}
+}  // namespace
+
+int launch_head_graph(HeadArgs a, bool fwd, bool bwd, cudaStream_t s) {
+  if (a.g_cap <= 0 || (!fwd && !bwd)) return GCNN_OK;
+  if (a.H % 4 || a.H <= 0 || a.Hh <= 0) return set_error(GCNN_EINVAL, "head: hidden must be a positive multiple of 4");
+  const long long room = kHeadSmemFloats - a.H - 2LL * a.Hh;
+  long long rk = std::min<long long>(a.H, room / a.Hh) / 4 * 4;
+  if (rk < 4) return set_error(GCNN_EINVAL, "head: layer too wide for shared memory");
+  a.rk = (int)rk;
+  if (fwd && bwd) return head_graph<true, true>(a, s);
+  if (fwd) return head_graph<true, false>(a, s);
+  return head_graph<false, true>(a, s);
+}
+
+int launch_head_grad(const HeadGradArgs &a, cudaStream_t s) {
+  if (a.g_cap <= 0) return GCNN_OK;
+  dim3 grid(ceil_div(a.Hh, kHT), ceil_div(a.H, kHT) + 1);
+  GCNN_TRY(launch(head_grad_kernel, grid, kRedThreads, 0, s, a));
   return GCNN_OK;
 }
 
-int launch_head_bwd(int G, int H, int Hh, DevDims dims, const float *g, const float *w1,
-                    const float *w2, const float *z1, const float *pred, const float *y,
-                    const float *dpred_in, float *dpred, float *dz1, float *grad_head, float *dg,
-                    double *loss_accum, cudaStream_t s) {
-  (void)dz1;
-  float *grad_b2 = grad_head + (size_t)H * Hh + 2 * Hh;
-  head_bwd_loss_kernel<<<1, kThreads, 0, s>>>(G, dims, pred, y, dpred_in, dpred, grad_b2, loss_accum);
-  GCNN_LAUNCH_CHECK();
-  const long long work = (long long)H * Hh + 2 * Hh + (long long)G * H;
-  head_bwd_grad_kernel<<<ceil_div(work, kThreads), kThreads, 0, s>>>(G, H, Hh, dims, g, w1, w2, z1, dpred,
-                                                                      grad_head, dg);
-  GCNN_LAUNCH_CHECK();
-  return GCNN_OK;
-}
-
-int launch_adam(int64_t n, float *param, const float *grad, float *m, float *v, int *step,
-                const float *lr, float beta1, float beta2, float eps, float wd, cudaStream_t s) {
-  // coef lives right after the step counter (two floats)
-  float *coef = reinterpret_cast<float *>(step + 1);
-  adam_tick_kernel<<<1, 1, 0, s>>>(step, coef, beta1, beta2);
-  GCNN_LAUNCH_CHECK();
-  int blocks = (int)std::min<int64_t>((n / 4 + kThreads - 1) / kThreads + 1, 152 * 8);
-  adam_kernel<<<blocks, kThreads, 0, s>>>(n, param, grad, m, v, coef, lr, beta1, beta2, eps, wd);
-  GCNN_LAUNCH_CHECK();
+int launch_adam(int64_t n, float *param, const float *grad, float *m, float *v, int *state, unsigned *ticket,
+                const float *lr, float beta1, float beta2, float eps, float wd, uint16_t *wb, uint16_t *wpack,
+                AdamPack pk, cudaStream_t s) {
+  if (n <= 0) return GCNN_OK;
+  const int blocks = (int)std::min<int64_t>((n / 4 + kThreads - 1) / kThreads + 1, (int64_t)num_sms() * 8);
+  GCNN_TRY(launch(adam_kernel, blocks, kThreads, 0, s, n, param, grad, m, v, state, ticket, lr, beta1, beta2, eps, wd,
+                  wb, wpack, pk));
   return GCNN_OK;
 }
 
