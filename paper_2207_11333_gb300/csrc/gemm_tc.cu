@@ -39,7 +39,11 @@ constexpr int kMaxBN = 256;
 constexpr int kATileBytes = BM * BK * 2;        // 16 KB
 constexpr int kBTileBytes = kMaxBN * BK * 2;    // 32 KB
 constexpr int kStageBytes = kATileBytes + kBTileBytes;
-constexpr int kSmemBytes = STAGES * kStageBytes + 1024 /* alignment slack */ + 256 /* barriers */;
+// masked-gradient epilogue: ReLU-mask bits (8 words per tile row) and the
+// tile rows' degree scalers, prefetched during the main loop
+constexpr int kMaskWords = kMaxBN / 32;
+constexpr int kSideBytes = BM * kMaskWords * 4 + 2 * BM * 4;
+constexpr int kSmemBytes = STAGES * kStageBytes + 1024 /* alignment slack */ + 256 /* barriers */ + kSideBytes;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr uint32_t kMnAtomBytes = 64 * 128;      // 64 M/N elements x 64 k rows
 
@@ -186,19 +190,111 @@ __device__ __forceinline__ void emit8(const TcEpilogue &e, int N, int row, int n
   }
 }
 
-// Final 4 columns (row, n..n+3) of the product: bias and ReLU already
-// applied (x), mask values mk and degree scalers am / at for D3.
-__device__ __forceinline__ void emit4(const TcEpilogue &e, int N, int row, int n, float4 x, float4 mk, float am,
-                                      float at) {
-  if (e.C) *reinterpret_cast<float4 *>(e.C + (size_t)row * e.ldc + n) = x;
-  if (e.C16) st_bf16x4(e.C16 + (size_t)row * e.ld16 + n, x.x, x.y, x.z, x.w);
-  if (e.D3) {  // [amp g | att g | g], g = x * [mask > 0]
-    const float gx = mk.x > 0.f ? x.x : 0.f, gy = mk.y > 0.f ? x.y : 0.f;
-    const float gz = mk.z > 0.f ? x.z : 0.f, gw = mk.w > 0.f ? x.w : 0.f;
-    uint16_t *o = e.D3 + (size_t)row * e.ld3 + n;
-    st_bf16x4(o, am * gx, am * gy, am * gz, am * gw);
-    st_bf16x4(o + N, at * gx, at * gy, at * gz, at * gw);
-    st_bf16x4(o + 2 * N, gx, gy, gz, gw);
+// ---------------------------------------------------------------- tile stores
+// The FP32 tile staged in shared memory (row pitch RS floats) goes to global
+// memory row by row: warp w takes rows w, w + 8, ...; lane l the 4-column
+// slices 4l and 128 + 4l.  Four rows per batch, every load of a batch issued
+// before its stores.  One routine per epilogue kind keeps each kernel
+// instantiation's store loop small.
+enum EpiKind { kEpiPartial = 0, kEpiC = 1, kEpiD3 = 2 };
+
+// split-K partial tile: P[row][n] (pitch N), no epilogue
+__device__ __forceinline__ void store_partial(const float *S, int RS, int rows, int BN, int N, int m0, int n0,
+                                              float *__restrict__ P, int warp, int lane) {
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const int cn = 128 * h + 4 * lane;
+    if (cn >= BN || n0 + cn >= N) continue;
+    float *dst = P + (size_t)m0 * N + n0 + cn;
+    for (int r0 = warp; r0 < rows; r0 += 32) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        v[u] = r0 + 8 * u < rows ? *reinterpret_cast<const float4 *>(S + (size_t)(r0 + 8 * u) * RS + cn)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (r0 + 8 * u < rows) *reinterpret_cast<float4 *>(dst + (size_t)(r0 + 8 * u) * N) = v[u];
+    }
+  }
+}
+
+// C (FP32) and / or C16 (BF16) with optional bias and ReLU
+__device__ __forceinline__ void store_c(const float *S, int RS, int rows, int BN, int N, int m0, int n0,
+                                        const TcEpilogue e, int warp, int lane) {
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const int cn = 128 * h + 4 * lane;
+    const int n = n0 + cn;
+    if (cn >= BN || n >= N) continue;
+    float b[4] = {0.f, 0.f, 0.f, 0.f};
+    if (e.bias)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (n + q < e.bias_n) b[q] = e.bias[n + q];
+    for (int r0 = warp; r0 < rows; r0 += 32) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        v[u] = r0 + 8 * u < rows ? *reinterpret_cast<const float4 *>(S + (size_t)(r0 + 8 * u) * RS + cn)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (r0 + 8 * u >= rows) break;
+        const size_t row = (size_t)(m0 + r0 + 8 * u);
+        float4 x = make_float4(v[u].x + b[0], v[u].y + b[1], v[u].z + b[2], v[u].w + b[3]);
+        if (e.relu) {
+          x.x = fmaxf(x.x, 0.f); x.y = fmaxf(x.y, 0.f); x.z = fmaxf(x.z, 0.f); x.w = fmaxf(x.w, 0.f);
+        }
+        if (e.C) *reinterpret_cast<float4 *>(e.C + row * e.ldc + n) = x;
+        if (e.C16) st_bf16x4(e.C16 + row * e.ld16 + n, x.x, x.y, x.z, x.w);
+      }
+    }
+  }
+}
+
+// C (FP32, nullable) and the BF16 blocks [amp g | att g | g] of D3, g = v [mask > 0];
+// mask bits and degree scalers come from shared memory (prefetched)
+__device__ __forceinline__ void store_d3(const float *S, int RS, int rows, int BN, int N, int m0, int n0,
+                                         const TcEpilogue e, const uint32_t *mbits, const float *s_amp,
+                                         const float *s_att, int warp, int lane) {
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const int cn = 128 * h + 4 * lane;
+    const int n = n0 + cn;
+    if (cn >= BN || n >= N) continue;
+    const int word = cn / 32, shift = cn % 32;
+    for (int r0 = warp; r0 < rows; r0 += 32) {
+      float4 v[4];
+      uint32_t mk[4];
+      float am[4], at[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r0 + 8 * u;
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        mk[u] = 0u;
+        am[u] = at[u] = 0.f;
+        if (r < rows) {
+          v[u] = *reinterpret_cast<const float4 *>(S + (size_t)r * RS + cn);
+          mk[u] = mbits[r * kMaskWords + word] >> shift;
+          am[u] = s_amp[r];
+          at[u] = s_att[r];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (r0 + 8 * u >= rows) break;
+        const size_t row = (size_t)(m0 + r0 + 8 * u);
+        const float4 x = v[u];
+        if (e.C) *reinterpret_cast<float4 *>(e.C + row * e.ldc + n) = x;
+        const float gx = (mk[u] & 1u) ? x.x : 0.f, gy = (mk[u] & 2u) ? x.y : 0.f;
+        const float gz = (mk[u] & 4u) ? x.z : 0.f, gw = (mk[u] & 8u) ? x.w : 0.f;
+        uint16_t *o = e.D3 + row * e.ld3 + n;
+        st_bf16x4(o, am[u] * gx, am[u] * gy, am[u] * gz, am[u] * gw);
+        st_bf16x4(o + N, at[u] * gx, at[u] * gy, at[u] * gz, at[u] * gw);
+        st_bf16x4(o + 2 * N, gx, gy, gz, gw);
+      }
+    }
   }
 }
 
@@ -228,6 +324,7 @@ __device__ __forceinline__ void clear_k_rows(uint8_t *tile, int atoms, int from,
   }
 }
 
+template <int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
 tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, float *__restrict__ partial, int splits,
                 int kps, int BN, unsigned *err) {
@@ -238,6 +335,8 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
   uint64_t *acc_ready = empty + STAGES;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_ready + 1);
   uint32_t *flag = tmem_slot + 1;
+  uint32_t *mbits = reinterpret_cast<uint32_t *>(smem + STAGES * kStageBytes + 256);  // BM x kMaskWords
+  float *s_amp = reinterpret_cast<float *>(mbits + BM * kMaskWords), *s_att = s_amp + BM;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // shared-memory set-up and descriptor prefetch overlap the previous kernel
@@ -335,6 +434,33 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
       __syncwarp();
     }
     if (ok && nk > 0 && lane == 0) mma_commit(acc_ready);
+  } else if (EPI == kEpiD3) {
+    // ------------------------------------------------ epilogue inputs (warps 2-7)
+    // mask bit (row r, column 32 w + lane) = [mask > 0]; eight rows per batch
+    // with their loads issued together
+    const TcEpilogue e = d.ep;
+    const int rows = min(BM, M - m0), words = (BN + 31) / 32;
+    const int pw = warp - 2, npw = kThreads / 32 - 2;
+    for (int q0 = pw; q0 < BM * words; q0 += 8 * npw) {
+      bool bit[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * npw, r = q / words, c = 32 * (q % words) + lane;
+        bit[u] = false;
+        if (q < BM * words && r < rows && c < BN && n0 + c < N)
+          bit[u] = e.mask[(size_t)(m0 + r) * e.ldm + n0 + c] > 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * npw;
+        const uint32_t b = __ballot_sync(0xffffffffu, bit[u]);
+        if (lane == 0 && q < BM * words) mbits[(q / words) * kMaskWords + q % words] = b;
+      }
+    }
+    for (int r = tid - 64; r < BM; r += kThreads - 64) {
+      s_amp[r] = r < rows ? e.amp[m0 + r] : 0.f;
+      s_att[r] = r < rows ? e.att[m0 + r] : 0.f;
+    }
   }
   // ------------------------------------------------ epilogue (all 8 warps)
   // (1) warp w drains TMEM lanes 32*(w%4).. (tile rows) and half w/4 of the
@@ -379,68 +505,13 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
       }
     }
     if (!__syncthreads_or(!ok)) {
-      // warp w writes rows w, w + 8, ..., four per batch with every load of
-      // the batch issued first; lane l owns the 4-column slices 4l and 128 + 4l
-      // a local copy: stores through the output pointers cannot alias it, so
-      // its fields stay in registers across the loop
-      const TcEpilogue e = d.ep;
       const int rows = min(BM, M - m0);
-      int cn[2];
-      bool on[2];
-      float4 bias[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        cn[h] = 128 * h + 4 * lane;
-        on[h] = cn[h] < BN && n0 + cn[h] < N;
-        float b[4] = {0.f, 0.f, 0.f, 0.f};
-        if (splits == 1 && e.bias && on[h])
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (n0 + cn[h] + q < e.bias_n) b[q] = e.bias[n0 + cn[h] + q];
-        bias[h] = make_float4(b[0], b[1], b[2], b[3]);
-      }
-      for (int r0 = warp; r0 < rows; r0 += 32) {
-        float4 v[4][2], mk[4][2];
-        float am[4], at[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int r = r0 + 8 * u;
-          am[u] = at[u] = 0.f;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            v[u][h] = mk[u][h] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r < rows && on[h]) {
-              v[u][h] = *reinterpret_cast<const float4 *>(S + (size_t)r * RS + cn[h]);
-              if (e.D3) mk[u][h] = *reinterpret_cast<const float4 *>(e.mask + (size_t)(m0 + r) * e.ldm + n0 + cn[h]);
-            }
-          }
-          if (e.D3 && r < rows) {
-            am[u] = e.amp[m0 + r];
-            at[u] = e.att[m0 + r];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int r = r0 + 8 * u;
-          if (r >= rows) break;
-          const int row = m0 + r;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            if (!on[h]) continue;
-            const int n = n0 + cn[h];
-            float4 x = v[u][h];
-            if (splits > 1) {
-              *reinterpret_cast<float4 *>(partial + ((size_t)z * d.M + row) * N + n) = x;
-              continue;
-            }
-            x.x += bias[h].x; x.y += bias[h].y; x.z += bias[h].z; x.w += bias[h].w;
-            if (e.relu) {
-              x.x = fmaxf(x.x, 0.f); x.y = fmaxf(x.y, 0.f); x.z = fmaxf(x.z, 0.f); x.w = fmaxf(x.w, 0.f);
-            }
-            emit4(e, N, row, n, x, mk[u][h], am[u], at[u]);
-          }
-        }
-      }
+      if constexpr (EPI == kEpiPartial)
+        store_partial(S, RS, rows, BN, N, m0, n0, partial + (size_t)z * d.M * N, warp, lane);
+      else if constexpr (EPI == kEpiC)
+        store_c(S, RS, rows, BN, N, m0, n0, d.ep, warp, lane);
+      else
+        store_d3(S, RS, rows, BN, N, m0, n0, d.ep, mbits, s_amp, s_att, warp, lane);
     }
   }
   fence_before_sync();
@@ -567,7 +638,7 @@ int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
   if (d.N % 8 || (e.C && (e.ldc % 4 || reinterpret_cast<uintptr_t>(e.C) % 16)) ||
       (e.C16 && (e.ld16 % 8 || reinterpret_cast<uintptr_t>(e.C16) % 16)) ||
       (e.D3 && (e.ld3 % 8 || reinterpret_cast<uintptr_t>(e.D3) % 16 || !e.mask || !e.amp || !e.att ||
-                e.ldm % 4 || reinterpret_cast<uintptr_t>(e.mask) % 16)))
+                e.ldm % 4 || reinterpret_cast<uintptr_t>(e.mask) % 16 || e.bias || e.relu)))
     return set_error(GCNN_EINVAL, "tc gemm: N must be a multiple of 8 and outputs 16-byte aligned");
   const double out_bytes = (e.C ? 4.0 : 0.0) + (e.C16 ? 2.0 : 0.0) + (e.D3 ? 10.0 : 0.0);
   const Plan plan = choose(d.M, d.N, d.K, ws.max_splits, out_bytes, d.B.mn_major);
@@ -578,13 +649,17 @@ int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
   GCNN_TRY(make_map(&maps.a, d.A, d.A.mn_major ? 64 : BM));
   GCNN_TRY(make_map(&maps.b, d.B, d.B.mn_major ? 64 : BN));
   if (!g_configured) {
-    GCNN_CUDA_TRY(cudaFuncSetAttribute(tma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    GCNN_CUDA_TRY(cudaFuncSetAttribute(tma_gemm_kernel<kEpiPartial>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kSmemBytes));
+    GCNN_CUDA_TRY(cudaFuncSetAttribute(tma_gemm_kernel<kEpiC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    GCNN_CUDA_TRY(cudaFuncSetAttribute(tma_gemm_kernel<kEpiD3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     g_configured = 1;
   }
   if (splits > 1 && (size_t)splits * d.M * d.N > ws.floats) splits = 1;
   const int kps = (ktiles + splits - 1) / splits * BK;
   dim3 grid(ntiles, (d.M + BM - 1) / BM, splits);
-  GCNN_TRY(launch(tma_gemm_kernel, grid, kThreads, kSmemBytes, s, maps, d, dims, splits > 1 ? ws.partial : nullptr,
+  auto kernel = splits > 1 ? tma_gemm_kernel<kEpiPartial> : (e.D3 ? tma_gemm_kernel<kEpiD3> : tma_gemm_kernel<kEpiC>);
+  GCNN_TRY(launch(kernel, grid, kThreads, kSmemBytes, s, maps, d, dims, splits > 1 ? ws.partial : nullptr,
                   splits, kps, BN, err));
   if (splits > 1) {
     const long long work = (long long)d.M * (d.N / 8);
