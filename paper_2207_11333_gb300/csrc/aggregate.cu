@@ -70,12 +70,13 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
   const int i = (int)(t / H4), c = (int)(t % H4) * 4;
   const int r0 = row_ptr[i], r1 = row_ptr[i + 1];
   const int d = r1 - r0;
-  float *out = agg + (size_t)i * kAgg * H + c;
+  float *out = agg ? agg + (size_t)i * kAgg * H + c : nullptr;
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
   if (d <= 0 || r0 < 0) {
     if (d < 0 || r0 < 0) flag(err, kErrIndex);
+    if (out)
 #pragma unroll
-    for (int a = 0; a < kAgg; ++a) st4(out + a * H, z);
+      for (int a = 0; a < kAgg; ++a) st4(out + a * H, z);
     if (S16)
       for (int a = 0; a < kScalers * kAgg; ++a) st_bf16x4(S16 + (size_t)i * ld16 + a * H + c, 0.f, 0.f, 0.f, 0.f);
     return;
@@ -110,11 +111,13 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
   sd.y = sqrtf(fmaxf(v.y / df, 0.f) + eps);
   sd.z = sqrtf(fmaxf(v.z / df, 0.f) + eps);
   sd.w = sqrtf(fmaxf(v.w / df, 0.f) + eps);
-  st4(out + 0 * H, s);
-  st4(out + 1 * H, mean);
-  st4(out + 2 * H, mn);
-  st4(out + 3 * H, mx);
-  st4(out + 4 * H, sd);
+  if (out) {
+    st4(out + 0 * H, s);
+    st4(out + 1 * H, mean);
+    st4(out + 2 * H, mn);
+    st4(out + 3 * H, mx);
+    st4(out + 4 * H, sd);
+  }
   if (S16) {  // scaler-major: identity, amplification, attenuation
     const float4 vv[kAgg] = {s, mean, mn, mx, sd};
     const float sc[kScalers] = {1.f, amp[i], att[i]};
@@ -127,22 +130,23 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
   }
 }
 
-__device__ __forceinline__ float route(float m, float base, float mn, float dmin, float nmin,
-                                       float mx, float dmax, float nmax, float var, float mean,
-                                       float dstd, float d, float sd) {
+// dL/dm for one channel of one edge from its node's routing coefficients
+__device__ __forceinline__ float route(float m, float base, float mn, float cmin, float mx, float cmax, float mean,
+                                       float cstd) {
   float g = base;
-  if (m == mn) g += dmin / nmin;
-  if (m == mx) g += dmax / nmax;
-  if (var > 0.f) g += dstd * (m - mean) / (d * sd);
-  return g;
+  if (m == mn) g += cmin;
+  if (m == mx) g += cmax;
+  return g + cstd * (m - mean);
 }
 
-__global__ void __launch_bounds__(kThreads)
+constexpr int kEdgeThreads = 128;  // five blocks of 128 per SM at this kernel's register count
+
+__global__ void __launch_bounds__(kEdgeThreads)
 aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *__restrict__ row_ptr,
                           const int *__restrict__ col, const int *__restrict__ rev,
                           const float *__restrict__ PQ, const float *__restrict__ agg,
                           const float *__restrict__ dagg, float *__restrict__ dPQ,
-                          float *__restrict__ dm, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16) {
+                          float *__restrict__ dm, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16, float eps) {
   pdl_entry();
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
@@ -160,36 +164,66 @@ aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *
     return;
   }
   const float df = (float)d;
-  const float *a = agg + (size_t)i * kAgg * H + c;
-  const float *da = dagg + (size_t)i * kAgg * H + c;
   const float4 P = ld4(PQ + (size_t)i * 2 * H + c);
-  const float4 mean = ld4(a + 1 * H), mn = ld4(a + 2 * H), mx = ld4(a + 3 * H), sd = ld4(a + 4 * H);
-  const float4 dsum = ld4(da + 0 * H), dmean = ld4(da + 1 * H), dmin = ld4(da + 2 * H);
-  const float4 dmax = ld4(da + 3 * H), dstd = ld4(da + 4 * H);
-  float4 nmin = make_float4(0.f, 0.f, 0.f, 0.f), nmax = nmin, var = nmin;
   float4 mc[kCache];
+#pragma unroll
+  for (int k = 0; k < kCache; ++k)
+    if (k < d) mc[k] = message(PQ, source(col, r0 + k, N, err), H, c, P);
+  // the forward's statistics: stored, or recomputed in the forward's order
+  float4 mean, mn, mx, sd;
+  if (agg) {
+    const float *a = agg + (size_t)i * kAgg * H + c;
+    mean = ld4(a + 1 * H); mn = ld4(a + 2 * H); mx = ld4(a + 3 * H); sd = ld4(a + 4 * H);
+  } else {
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    mn = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX);
+    mx = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX);
+    auto take = [&](float4 m) {
+      s = add4(s, m);
+      mn.x = fminf(mn.x, m.x); mn.y = fminf(mn.y, m.y); mn.z = fminf(mn.z, m.z); mn.w = fminf(mn.w, m.w);
+      mx.x = fmaxf(mx.x, m.x); mx.y = fmaxf(mx.y, m.y); mx.z = fmaxf(mx.z, m.z); mx.w = fmaxf(mx.w, m.w);
+    };
+#pragma unroll
+    for (int k = 0; k < kCache; ++k)
+      if (k < d) take(mc[k]);
+    for (int e = r0 + kCache; e < r1; ++e) take(message(PQ, source(col, e, N, err), H, c, P));
+    mean = make_float4(s.x / df, s.y / df, s.z / df, s.w / df);
+  }
+  float4 nmin = make_float4(0.f, 0.f, 0.f, 0.f), nmax = nmin, var = nmin;
   auto count = [&](float4 m) {
     nmin.x += (m.x == mn.x); nmin.y += (m.y == mn.y); nmin.z += (m.z == mn.z); nmin.w += (m.w == mn.w);
     nmax.x += (m.x == mx.x); nmax.y += (m.y == mx.y); nmax.z += (m.z == mx.z); nmax.w += (m.w == mx.w);
     acc_sq(var, m, mean);
   };
 #pragma unroll
-  for (int k = 0; k < kCache; ++k) {
-    if (k < d) {
-      mc[k] = message(PQ, source(col, r0 + k, N, err), H, c, P);
-      count(mc[k]);
-    }
-  }
+  for (int k = 0; k < kCache; ++k)
+    if (k < d) count(mc[k]);
   for (int e = r0 + kCache; e < r1; ++e) count(message(PQ, source(col, e, N, err), H, c, P));
   var.x /= df; var.y /= df; var.z /= df; var.w /= df;
+  if (!agg) {
+    sd.x = sqrtf(fmaxf(var.x, 0.f) + eps);
+    sd.y = sqrtf(fmaxf(var.y, 0.f) + eps);
+    sd.z = sqrtf(fmaxf(var.z, 0.f) + eps);
+    sd.w = sqrtf(fmaxf(var.w, 0.f) + eps);
+  }
+  // per-node routing coefficients: every edge gets base = dsum + dmean / d,
+  // plus dmin / (number of minima) at a minimum, dmax / (number of maxima) at
+  // a maximum and dstd (m - mean) / (d std) where the variance is positive
+  const float *da = dagg + (size_t)i * kAgg * H + c;
+  const float4 dsum = ld4(da + 0 * H), dmean = ld4(da + 1 * H), dmin = ld4(da + 2 * H);
+  const float4 dmax = ld4(da + 3 * H), dstd = ld4(da + 4 * H);
   const float4 base = make_float4(dsum.x + dmean.x / df, dsum.y + dmean.y / df, dsum.z + dmean.z / df,
                                   dsum.w + dmean.w / df);
+  const float4 cmin = make_float4(dmin.x / nmin.x, dmin.y / nmin.y, dmin.z / nmin.z, dmin.w / nmin.w);
+  const float4 cmax = make_float4(dmax.x / nmax.x, dmax.y / nmax.y, dmax.z / nmax.z, dmax.w / nmax.w);
+  const float4 cstd = make_float4(var.x > 0.f ? dstd.x / (df * sd.x) : 0.f, var.y > 0.f ? dstd.y / (df * sd.y) : 0.f,
+                                  var.z > 0.f ? dstd.z / (df * sd.z) : 0.f, var.w > 0.f ? dstd.w / (df * sd.w) : 0.f);
   auto emit = [&](int e, float4 m) {
     float4 g;
-    g.x = route(m.x, base.x, mn.x, dmin.x, nmin.x, mx.x, dmax.x, nmax.x, var.x, mean.x, dstd.x, df, sd.x);
-    g.y = route(m.y, base.y, mn.y, dmin.y, nmin.y, mx.y, dmax.y, nmax.y, var.y, mean.y, dstd.y, df, sd.y);
-    g.z = route(m.z, base.z, mn.z, dmin.z, nmin.z, mx.z, dmax.z, nmax.z, var.z, mean.z, dstd.z, df, sd.z);
-    g.w = route(m.w, base.w, mn.w, dmin.w, nmin.w, mx.w, dmax.w, nmax.w, var.w, mean.w, dstd.w, df, sd.w);
+    g.x = route(m.x, base.x, mn.x, cmin.x, mx.x, cmax.x, mean.x, cstd.x);
+    g.y = route(m.y, base.y, mn.y, cmin.y, mx.y, cmax.y, mean.y, cstd.y);
+    g.z = route(m.z, base.z, mn.z, cmin.z, mx.z, cmax.z, mean.z, cstd.z);
+    g.w = route(m.w, base.w, mn.w, cmin.w, mx.w, cmax.w, mean.w, cstd.w);
     dP = add4(dP, g);
     const int re = rev[e];
     if (re >= 0 && re < E) st4(dm + (size_t)re * H + c, g);
@@ -240,12 +274,11 @@ int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const in
                          const int *col, const int *rev, const float *PQ, const float *agg,
                          const float *dagg, float *dPQ, float *scratch, float eps, unsigned *err,
                          cudaStream_t s, uint16_t *dPQ16, int ld16) {
-  (void)eps;
   if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
-  GCNN_TRY(launch(aggregate_bwd_edge_kernel, ceil_div(work, kThreads), kThreads, 0, s, n_nodes, n_edges, H, dims,
-                  row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, err, dPQ16, ld16));
+  GCNN_TRY(launch(aggregate_bwd_edge_kernel, ceil_div(work, kEdgeThreads), kEdgeThreads, 0, s, n_nodes, n_edges, H, dims,
+                  row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, err, dPQ16, ld16, eps));
   GCNN_TRY(launch(aggregate_bwd_gather_kernel, ceil_div(work, kThreads), kThreads, 0, s, n_nodes, n_edges, H, dims,
                   row_ptr, (const float *)scratch, dPQ, err, dPQ16, ld16));
   return GCNN_OK;

@@ -221,7 +221,8 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   c->stage_bytes = stage_bytes_of((int)Gc, (int)Nc, (int)Ec);
   const size_t o_stage = cv.take<char>(c->stage_bytes);
   const size_t o_xs = cv.take<float>((L + 1) * Nc * H), o_pq = cv.take<float>(L * Nc * 2 * H);
-  const size_t o_agg = cv.take<float>((cfg->recompute ? 1 : L) * Nc * kAgg * H);
+  const bool fp32_agg = cfg->precision != GCNN_PREC_BF16;  // the BF16 path recomputes them
+  const size_t o_agg = cv.take<float>(fp32_agg ? (cfg->recompute ? 1 : L) * Nc * kAgg * H : 0);
   const size_t o_pool = cv.take<float>(Gc * H), o_z1 = cv.take<float>(Gc * Hh), o_pred = cv.take<float>(Gc);
   const size_t o_dpred = cv.take<float>(Gc), o_dz1 = cv.take<float>(Gc * Hh), o_dg = cv.take<float>(Gc * H);
   const size_t o_dH = cv.take<float>(Nc * H), o_dX = cv.take<float>(Nc * H);
@@ -251,7 +252,7 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   c->bb.att = (float *)(b + o_att); c->bb.y = (float *)(b + o_y); c->bb.types = (uint8_t *)(b + o_types);
   c->bb.dims = (int *)(b + o_dims); c->ids_dev = (int64_t *)(b + o_ids);
   c->stage_dev = b + o_stage;
-  c->xs = (float *)(b + o_xs); c->PQ = (float *)(b + o_pq); c->agg = (float *)(b + o_agg);
+  c->xs = (float *)(b + o_xs); c->PQ = (float *)(b + o_pq); c->agg = fp32_agg ? (float *)(b + o_agg) : nullptr;
   c->pooled = (float *)(b + o_pool); c->z1 = (float *)(b + o_z1); c->pred = (float *)(b + o_pred);
   c->dpred = (float *)(b + o_dpred); c->dz1 = (float *)(b + o_dz1); c->dg = (float *)(b + o_dg);
   c->dH = (float *)(b + o_dH); c->dX = (float *)(b + o_dX); c->dagg = (float *)(b + o_dagg);

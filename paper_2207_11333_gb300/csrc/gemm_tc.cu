@@ -530,6 +530,7 @@ __global__ void __launch_bounds__(256) tc_reduce_kernel(TcDesc d, DevDims dims, 
   if (t >= (long long)M * N8) return;
   const int row = (int)(t / N8), n = (int)(t % N8) * 8;
   float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
   for (int z = 0; z < splits; ++z) {
     const float *p = partial + ((size_t)z * d.M + row) * N + n;
     const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);

@@ -31,13 +31,16 @@ int launch_collate(int G, const int64_t *ids, StoreView st, BatchBuf b, const fl
 
 // ---------------------------------------------------------------- aggregate.cu
 // agg[i] = [sum, mean, min, max, std](P_i + Q_j, j in N(i)); PQ is N x 2H.
-// S16 (nullable, row pitch ld16) additionally receives [agg, amp*agg, att*agg]
-// (15H BF16), the scaled aggregates as the BF16 operand of the update GEMM.
+// agg is nullable; S16 (nullable, row pitch ld16) receives [agg, amp*agg,
+// att*agg] (15H BF16), the scaled aggregates as the BF16 operand of the
+// update GEMM.
 int launch_aggregate_fwd(int n_nodes, int H, DevDims dims, const int *row_ptr, const int *col,
                          const float *PQ, float *agg, float eps, unsigned *err, cudaStream_t s,
                          uint16_t *S16 = nullptr, int ld16 = 0, const float *amp = nullptr,
                          const float *att = nullptr);
-// dPQ from dagg; scratch is E x H (per-edge message gradients).
+// dPQ from dagg; scratch is E x H (per-edge message gradients).  With agg
+// null the forward's statistics are recomputed from the messages in the
+// forward kernel's order (bit-identical).
 int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const int *row_ptr,
                          const int *col, const int *rev, const float *PQ, const float *agg,
                          const float *dagg, float *dPQ, float *scratch, float eps, unsigned *err,

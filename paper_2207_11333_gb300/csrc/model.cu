@@ -38,7 +38,10 @@ GemmDesc blank() {
 
 float *xs_at(const gcnn_ctx *c, int l) { return c->xs + (size_t)l * c->Nc * c->H; }
 float *pq_at(const gcnn_ctx *c, int l) { return c->PQ + (size_t)l * c->Nc * 2 * c->H; }
+// FP32 aggregates of layer l; the BF16 path keeps none (its backward
+// recomputes the statistics from the messages)
 float *agg_at(const gcnn_ctx *c, int l) {
+  if (!c->agg) return nullptr;
   return c->agg + (c->cfg.recompute ? 0 : (size_t)l * c->Nc * kAgg * c->H);
 }
 
