@@ -63,9 +63,11 @@ def gemm_flops(n_nodes: int) -> float:
     return L * per_layer
 
 
-def agg_fwd_bytes(n_nodes: int, n_edges: int) -> float:
-    """Compulsory bytes of one aggregation launch: P and Q rows read once, 5H written, CSR read."""
-    return n_nodes * (2 * H + 5 * H) * 4.0 + (n_nodes + 1 + n_edges) * 4.0
+def agg_fwd_bytes(n_nodes: int, n_edges: int, precision: str = "fp32") -> float:
+    """Compulsory bytes of one aggregation launch: P and Q rows read once, the CSR read, and the
+    aggregates written (FP32 path: 5H FP32; BF16 path: the 15H scaled BF16 operand block)."""
+    out = 15 * H * 2.0 if precision == "bf16" else 5 * H * 4.0
+    return n_nodes * (2 * H * 4.0 + out) + (n_nodes + 1 + n_edges) * 4.0
 
 
 def measured_hbm():
@@ -306,39 +308,77 @@ def timed_steps(ctx, wl, steps, warmup, flush, loss_acc, dist=None, gpu_index=No
             "kernels_per_step": ctx.step_kernel_count() + 2}
 
 
-def kernel_profile(ctx, wl, n_steps, warmup, flush, loss_acc, precision):
-    """The same steps eagerly with CUDA events around every launch: per-phase ms and GEMM roofline."""
-    ctx.profile(True)
-    ctx.profile_read()
+def gemm_traffic():
+    """DRAM bytes per GEMM launch from the committed ncu summary, or None when
+    the GEMM kernel's source has changed since those counters were taken."""
+    import hashlib
+    import re
+    try:
+        with open(os.path.join(ROOT, "profiles", "tma_gemm_bf16_train_step_200k.md")) as f:
+            m = re.search(r"bench: kernel=tma_gemm source_sha256=([0-9a-f]{64}) dram_bytes_per_launch=(\d+)", f.read())
+        with open(os.path.join(ROOT, "paper_2207_11333_gb300", "csrc", "gemm_tc.cu"), "rb") as f:
+            src = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return float(m.group(2)) if m and m.group(1) == src else None
+
+
+def kernel_profile(g, ctx, wl, n_steps, warmup, flush, loss_acc, precision):
+    """Per-kernel durations inside the captured step, from the library's kernel timeline.
+
+    Every library kernel records the device clock once its dependency on the
+    previous kernel is satisfied (the previous kernel's completion), so in the
+    serial graph the difference of consecutive records is a kernel's duration
+    as it runs in the step.  The last kernel of a step (the optimiser) has no
+    successor record and is left out; the collation kernels run before the
+    graph launch, so their durations include that host gap."""
+    import torch
+    from collections import Counter, defaultdict
+    ctx.timeline_enable(256 * n_steps)
+    ctx.timeline_read()
     flops = agg_bytes = 0.0
+    dur, cnt = defaultdict(float), Counter()
     for k in range(n_steps):
         flush.zero_()
         b = batch_at(ctx, wl, warmup + k)
         ctx.train_step(b, LR, loss_acc)
+        torch.cuda.synchronize()
+        ids, t = ctx.timeline_read()
+        for i in range(len(ids) - 1):
+            name = g.KERNELS.get(int(ids[i]), str(int(ids[i])))
+            dur[name] += (t[i + 1] - t[i]) * 1e-9
+            cnt[name] += 1
         flops += gemm_flops(b.n_nodes)
-        agg_bytes += L * agg_fwd_bytes(b.n_nodes, b.n_edges)
-    ph = ctx.profile_read()
-    ctx.profile(False)
-    out = {"phases_ms_per_step": {k: v[0] / n_steps for k, v in ph.items()}}
-    achieved = flops / (ph["gemm"][0] / 1e3) / 1e12
+        agg_bytes += L * agg_fwd_bytes(b.n_nodes, b.n_edges, precision)
+    ctx.timeline_enable(0)
+    out = {"kernel_ms_per_step": {k: {"ms": 1e3 * v / n_steps, "launches": cnt[k] // n_steps}
+                                  for k, v in sorted(dur.items(), key=lambda x: -x[1])},
+           "kernel_timing": "library kernel timeline (device clock at each kernel's start after its dependency "
+                            "wait), inside the captured step; L2 flushed before each step"}
     peaks = measured_peaks()
     if precision == "bf16":
+        gemm_s = sum(v for k, v in dur.items() if k.startswith("gemm_tc"))
+        launches = sum(c for k, c in cnt.items() if k.startswith("gemm_tc_") and k != "gemm_tc_reduce") / n_steps
+        achieved = flops / gemm_s / 1e12
         peak = float(peaks.get("bf16_tflops", 1900.0))
         src = "measured (MEASURED_PEAKS.json bf16_tflops, burst)" if "bf16_tflops" in peaks else "fallback 1.9 PFLOP/s"
         out["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                           "frac": achieved / peak, "traffic": None, "peak_source": src,
-                           "kernel": "tc_gemm_kernel + tc_reduce_kernel (all dense GEMMs of the step, "
+                           "frac": achieved / peak, "traffic": gemm_traffic(), "traffic_unit": "DRAM bytes per launch",
+                           "peak_source": src, "launches_per_step": launches,
+                           "kernel": "tma_gemm_kernel<epilogue> + tc_reduce_kernel (all dense GEMMs of the step, "
                                      "BF16 tcgen05, FP32 accumulate)"}
     else:
+        gemm_s = sum(v for k, v in dur.items() if k.startswith("gemm_simt"))
+        achieved = flops / gemm_s / 1e12
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
         out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                            "frac": achieved / peak, "traffic": None,
                            "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)",
                            "kernel": "sgemm_kernel + splitk_reduce (all dense GEMMs of the step, FP32 FFMA)"}
     hbm, hbm_src = measured_hbm()
-    a_gbs = agg_bytes / (ph["agg_fwd"][0] / 1e3) / 1e9
+    a_gbs = agg_bytes / dur["agg_fwd"] / 1e9
     out["roofline_aggregate"] = {"bound": "hbm", "achieved": a_gbs, "peak": hbm, "unit": "GB/s", "frac": a_gbs / hbm,
-                                 "traffic": None, "peak_source": hbm_src,
+                                 "traffic": None, "peak_source": hbm_src, "kernel": "aggregate_fwd_kernel",
                                  "note": "128-graph batches fit in L2; the HBM figure needs a >L2 batch"}
     return out
 
@@ -660,7 +700,7 @@ def run_ours(args):
         except Exception as e:  # noqa: BLE001
             line["e2e"] = {"error": repr(e)}
     try:
-        line.update(kernel_profile(ctx, wl, min(args.steps, 100), args.warmup, flush, loss_acc, args.precision))
+        line.update(kernel_profile(g, ctx, wl, min(args.steps, 100), args.warmup, flush, loss_acc, args.precision))
     except Exception as e:  # noqa: BLE001
         line["roofline"] = {"error": repr(e)}
     ctx.check()
@@ -684,9 +724,9 @@ def run_ours(args):
         cmp = {"value": r2["value"], "unit": "graphs/s", "ms_per_step": 1e3 * r2["dev_s"] / args.steps,
                "precision": args.compare}
         try:
-            prof = kernel_profile(c2, wl, min(args.steps, 50), args.warmup, flush, loss_acc, args.compare)
+            prof = kernel_profile(g, c2, wl, min(args.steps, 50), args.warmup, flush, loss_acc, args.compare)
             cmp["roofline"] = prof["roofline"]
-            cmp["phases_ms_per_step"] = prof["phases_ms_per_step"]
+            cmp["kernel_ms_per_step"] = prof["kernel_ms_per_step"]
         except Exception as e:  # noqa: BLE001
             cmp["roofline"] = {"error": repr(e)}
         c2.check()

@@ -230,6 +230,10 @@ enum {
   GCNN_PHASE_ADAM = 7,      /* optimizer                                */
   GCNN_NPHASE = 8
 };
+/* With profiling on, gcnn_train_step replays a separately captured graph that
+ * carries event-record nodes around every phase (so the kernels are timed as
+ * they run inside a graph) and synchronises the stream after each step;
+ * other calls time their launches with eager events. */
 int gcnn_profile_enable(gcnn_ctx *ctx, int enable);
 /* Synchronises the stream; returns per-phase milliseconds and numbers of
  * timed launches since the last read (host arrays of GCNN_NPHASE), then
@@ -241,6 +245,48 @@ int gcnn_memory(const gcnn_ctx *ctx, int64_t *arena_bytes);
 /* Kernels in the CUDA graph of the most recent gcnn_train_step (0 if it ran
  * eagerly); the collation of a batch adds 2 more. */
 int gcnn_step_kernel_count(gcnn_ctx *ctx, int32_t *n);
+
+/* Kernel timeline.  While enabled, block 0 of every kernel of the library
+ * appends one record (kernel id, device clock in ns) right after the kernel's
+ * dependency on the previous work in its stream is satisfied.  Inside a
+ * serial stream or graph that moment is the completion of the previous
+ * kernel, so consecutive records give each kernel's in-stream duration.  The
+ * timeline is process-wide on the calling thread's device (every context's
+ * kernels append) and holds at most `capacity` records; records past it are
+ * dropped.  Not a paper operation: measurement support.
+ *   gcnn_timeline_enable: capacity > 0 allocates (or resizes) the device
+ *     buffer and clears it; 0 disables recording and frees it.  Call it with
+ *     no library kernel in flight.
+ *   gcnn_timeline_read: synchronises the device, copies up to `max` records
+ *     (ids into `ids`, times into `t_ns`, both host arrays) in append order,
+ *     sets *n to the number copied and clears the buffer.  GCNN_ESTATE when
+ *     the timeline is not enabled. */
+enum {
+  GCNN_K_COLLATE_SCAN = 1,
+  GCNN_K_COLLATE_GRAPH = 2,
+  GCNN_K_EMBED = 3,
+  GCNN_K_EMBED_BWD = 4,
+  GCNN_K_AGG_FWD = 5,
+  GCNN_K_AGG_BWD_EDGE = 6,
+  GCNN_K_AGG_BWD_GATHER = 7,
+  GCNN_K_GEMM_TC_PARTIAL = 8,   /* tensor-core GEMM writing split-K partials   */
+  GCNN_K_GEMM_TC_C = 9,         /* tensor-core GEMM, C / C16 epilogue          */
+  GCNN_K_GEMM_TC_D3 = 10,       /* tensor-core GEMM, masked gradient epilogue  */
+  GCNN_K_GEMM_TC_REDUCE = 11,   /* split-K reduction and epilogue              */
+  GCNN_K_GEMM_SIMT = 12,
+  GCNN_K_GEMM_SIMT_REDUCE = 13,
+  GCNN_K_POOL_FWD = 14,
+  GCNN_K_POOL_BWD = 15,
+  GCNN_K_HEAD_GRAPH = 16,
+  GCNN_K_HEAD_GRAD = 17,
+  GCNN_K_COLSUM = 18,
+  GCNN_K_ADAM = 19,
+  GCNN_K_CAST_BF16 = 20,
+  GCNN_K_PACK_LAYER = 21,
+  GCNN_NKERNEL = 22
+};
+int gcnn_timeline_enable(gcnn_ctx *ctx, int32_t capacity);
+int gcnn_timeline_read(gcnn_ctx *ctx, int32_t *ids, int64_t *t_ns, int32_t max, int32_t *n);
 
 /* ------------------------------------------------------------------ serving
  * Inference server for the screening use of the trained model (Sec. 1:

@@ -21,6 +21,11 @@ PREC_FP32 = 0
 PREC_BF16 = 1
 PHASES = ["collate", "embed", "gemm", "agg_fwd", "agg_bwd", "head", "embed_bwd", "adam"]
 NPHASE = len(PHASES)
+# kernel identifiers of the timeline records (GCNN_K_* in gcnn.h)
+KERNELS = {1: "collate_scan", 2: "collate_graph", 3: "embed", 4: "embed_bwd", 5: "agg_fwd", 6: "agg_bwd_edge",
+           7: "agg_bwd_gather", 8: "gemm_tc_partial", 9: "gemm_tc_c", 10: "gemm_tc_d3", 11: "gemm_tc_reduce",
+           12: "gemm_simt", 13: "gemm_simt_reduce", 14: "pool_fwd", 15: "pool_bwd", 16: "head_graph",
+           17: "head_grad", 18: "colsum", 19: "adam", 20: "cast_bf16", 21: "pack_layer"}
 
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EFORMAT", -5: "EDEVICE", -6: "ETIMEDOUT",
            -7: "EAGAIN", -8: "ESTATE"}
@@ -97,6 +102,8 @@ def _load() -> ctypes.CDLL:
         "gcnn_profile_enable": (i32, [vp, i32]),
         "gcnn_profile_read": (i32, [vp, vp, vp]),
         "gcnn_step_kernel_count": (i32, [vp, P(i32)]),
+        "gcnn_timeline_enable": (i32, [vp, i32]),
+        "gcnn_timeline_read": (i32, [vp, vp, vp, i32, P(i32)]),
         "gcnn_memory": (i32, [vp, P(i64)]),
         "gcnn_serve_create": (i32, [vp, P(ServeConfig), P(vp)]),
         "gcnn_serve_submit": (i32, [vp, P(RequestStruct), P(ctypes.c_uint64)]),
@@ -353,6 +360,18 @@ class Context:
         n = np.zeros(NPHASE, np.int64)
         _check(lib.gcnn_profile_read(self._h, _np_ptr(ms), _np_ptr(n)))
         return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(PHASES)}
+
+    def timeline_enable(self, capacity: int) -> None:
+        """Record (kernel id, device ns) at the start of every library kernel; 0 disables."""
+        _check(lib.gcnn_timeline_enable(self._h, int(capacity)))
+
+    def timeline_read(self, max_records: int = 1 << 16):
+        """Records since the last read: (kernel ids int32[n], device times in ns int64[n])."""
+        ids = np.zeros(max_records, np.int32)
+        t = np.zeros(max_records, np.int64)
+        n = ctypes.c_int32()
+        _check(lib.gcnn_timeline_read(self._h, _np_ptr(ids), _np_ptr(t), int(max_records), ctypes.byref(n)))
+        return ids[:n.value].copy(), t[:n.value].copy()
 
     def memory_bytes(self) -> int:
         n = ctypes.c_int64()

@@ -62,7 +62,7 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
                      const int *__restrict__ col, const float *__restrict__ PQ,
                      float *__restrict__ agg, float eps, unsigned *err, uint16_t *__restrict__ S16, int ld16,
                      const float *__restrict__ amp, const float *__restrict__ att) {
-  pdl_entry();
+  pdl_entry(GCNN_K_AGG_FWD);
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -147,7 +147,7 @@ aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *
                           const float *__restrict__ PQ, const float *__restrict__ agg,
                           const float *__restrict__ dagg, float *__restrict__ dPQ,
                           float *__restrict__ dm, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16, float eps) {
-  pdl_entry();
+  pdl_entry(GCNN_K_AGG_BWD_EDGE);
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const int E = min(e_cap, dims.edges(e_cap));
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kThreads)
 aggregate_bwd_gather_kernel(int n_cap, int e_cap, int H, DevDims dims,
                             const int *__restrict__ row_ptr, const float *__restrict__ dm,
                             float *__restrict__ dPQ, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16) {
-  pdl_entry();
+  pdl_entry(GCNN_K_AGG_BWD_GATHER);
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const int E = min(e_cap, dims.edges(e_cap));
@@ -283,5 +283,7 @@ int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const in
                   row_ptr, (const float *)scratch, dPQ, err, dPQ16, ld16));
   return GCNN_OK;
 }
+
+GCNN_TIMELINE_ATTACH(aggregate)
 
 }  // namespace gcnn

@@ -3,12 +3,32 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "context.h"
 
 using namespace gcnn;
 
 namespace {
+
+// process-wide kernel timeline (gcnn_timeline_*)
+struct TimelineHost {
+  char *buf = nullptr;
+  unsigned cap = 0;
+  size_t off_t = 0, off_id = 0;
+};
+TimelineHost g_tl;
+std::mutex g_tl_mu;
+
+int timeline_attach_all(void *tl) {
+  GCNN_TRY(timeline_attach_collate(tl));
+  GCNN_TRY(timeline_attach_aggregate(tl));
+  GCNN_TRY(timeline_attach_small(tl));
+  GCNN_TRY(timeline_attach_gemm_simt(tl));
+  GCNN_TRY(timeline_attach_gemm_tc(tl));
+  return GCNN_OK;
+}
 
 constexpr size_t kAlign = 256;
 
@@ -66,7 +86,17 @@ size_t stage_bytes_of(int Gc, int Nc, int Ec) {
 
 void destroy_ctx(gcnn_ctx *c) {
   if (!c) return;
-  for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  for (auto &kv : c->graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    for (auto &pe : kv.second.ev) {
+      cudaEventDestroy(pe.a);
+      cudaEventDestroy(pe.b);
+    }
+  }
+  for (auto &pe : c->cap_ev) {
+    cudaEventDestroy(pe.a);
+    cudaEventDestroy(pe.b);
+  }
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   for (int q = 0; q < 2; ++q) {
     if (c->stage_host[q]) cudaFreeHost(c->stage_host[q]);
@@ -464,19 +494,9 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
   GCNN_TRY(set_lr(c, lr));
   const int G = b->n_graphs;
   const int Ng = grid_nodes(c, b), Eg = grid_edges(c, b);
-  if (c->prof_on) {  // eager, so every launch can be timed
-    c->fuse_head = true;
-    int rc = ctx_forward(c, G, Ng, Eg, true);
-    if (rc == GCNN_OK) rc = ctx_backward(c, G, Ng, Eg, nullptr, loss_accum);
-    c->fuse_head = false;
-    GCNN_TRY(rc);
-    GCNN_TRY(ctx_step(c));
-    c->last_step_kernels = 0;
-    c->have_fwd = true;
-    c->fwd_G = b->n_graphs; c->fwd_N = b->n_nodes; c->fwd_E = b->n_edges;
-    return GCNN_OK;
-  }
-  auto key = std::make_tuple(G, Ng, Eg, (const double *)loss_accum);
+  // with profiling on, a separate graph carries event-record nodes around
+  // every phase; each of its replays is synchronised and accumulated
+  auto key = std::make_tuple(G, Ng, Eg, (const double *)loss_accum, c->prof_on);
   auto it = c->graphs.find(key);
   if (it == c->graphs.end()) {
     // capture on the context's private stream (the legacy default stream
@@ -486,6 +506,7 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
     cudaStream_t user = c->stream;
     c->stream = c->cap_stream;
     c->capturing = true;
+    c->cap_ev.clear();
     cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
       c->stream = user;
@@ -500,11 +521,23 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
     e = cudaStreamEndCapture(c->stream, &graph);
     c->stream = user;
     c->capturing = false;
+    std::vector<gcnn_ctx::ProfEvent> ev;
+    ev.swap(c->cap_ev);
+    auto drop_events = [&ev] {
+      for (auto &pe : ev) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+      }
+    };
     if (rc != GCNN_OK) {
       if (graph) cudaGraphDestroy(graph);
+      drop_events();
       return rc;
     }
-    if (e != cudaSuccess) return set_error(GCNN_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+      drop_events();
+      return set_error(GCNN_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    }
     size_t n_nodes = 0;
     cudaGraphGetNodes(graph, nullptr, &n_nodes);
     std::vector<cudaGraphNode_t> nodes(n_nodes);
@@ -518,10 +551,22 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return set_error(GCNN_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
-    it = c->graphs.emplace(key, gcnn_ctx::Graph{exec, kernels}).first;
+    if (e != cudaSuccess) {
+      drop_events();
+      return set_error(GCNN_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+    it = c->graphs.emplace(key, gcnn_ctx::Graph{exec, kernels, std::move(ev)}).first;
   }
   GCNN_CUDA_TRY(cudaGraphLaunch(it->second.exec, c->stream));
+  if (!it->second.ev.empty()) {
+    GCNN_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (auto &pe : it->second.ev) {
+      float t = 0.f;
+      GCNN_CUDA_TRY(cudaEventElapsedTime(&t, pe.a, pe.b));
+      c->prof_ms[pe.phase] += t;
+      c->prof_n[pe.phase] += 1;
+    }
+  }
   c->last_step_kernels = it->second.kernels;
   c->have_fwd = true;
   c->fwd_G = b->n_graphs; c->fwd_N = b->n_nodes; c->fwd_E = b->n_edges;
@@ -546,7 +591,12 @@ int gcnn_profile_enable(gcnn_ctx *c, int enable) {
 int gcnn_profile_read(gcnn_ctx *c, double *ms, int64_t *launches) {
   if (!c || !ms || !launches) return set_error(GCNN_EINVAL, "null argument");
   GCNN_TRY(sync(c));
-  for (int q = 0; q < GCNN_NPHASE; ++q) { ms[q] = 0.0; launches[q] = 0; }
+  for (int q = 0; q < GCNN_NPHASE; ++q) {
+    ms[q] = c->prof_ms[q];
+    launches[q] = c->prof_n[q];
+    c->prof_ms[q] = 0.0;
+    c->prof_n[q] = 0;
+  }
   for (size_t k = 0; k < c->prof_used; ++k) {
     float t = 0.f;
     GCNN_CUDA_TRY(cudaEventElapsedTime(&t, c->prof_ev[2 * k], c->prof_ev[2 * k + 1]));
@@ -566,6 +616,63 @@ int gcnn_memory(const gcnn_ctx *c, int64_t *arena_bytes) {
 int gcnn_step_kernel_count(gcnn_ctx *c, int32_t *n) {
   if (!c || !n) return set_error(GCNN_EINVAL, "null argument");
   *n = c->last_step_kernels;
+  return GCNN_OK;
+}
+
+int gcnn_timeline_enable(gcnn_ctx *c, int32_t capacity) {
+  if (!c || capacity < 0) return set_error(GCNN_EINVAL, "timeline: null context or negative capacity");
+  std::lock_guard<std::mutex> lock(g_tl_mu);
+  GCNN_CUDA_TRY(cudaDeviceSynchronize());
+  if (g_tl.buf) {
+    GCNN_TRY(timeline_attach_all(nullptr));
+    cudaFree(g_tl.buf);
+    g_tl = TimelineHost{};
+  }
+  if (capacity == 0) return GCNN_OK;
+  TimelineHost h;
+  h.cap = (unsigned)capacity;
+  h.off_t = 256;
+  h.off_id = h.off_t + sizeof(unsigned long long) * h.cap;
+  const size_t bytes = h.off_id + sizeof(unsigned) * h.cap;
+  if (cudaMalloc(&h.buf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(GCNN_ENOMEM, "timeline: cannot allocate %zu bytes", bytes);
+  }
+  const Timeline head{0u, h.cap, reinterpret_cast<unsigned long long *>(h.buf + h.off_t),
+                      reinterpret_cast<unsigned *>(h.buf + h.off_id)};
+  int rc = cudaMemcpy(h.buf, &head, sizeof(head), cudaMemcpyHostToDevice) == cudaSuccess
+               ? GCNN_OK
+               : set_error(GCNN_ECUDA, "timeline: header copy failed");
+  if (rc == GCNN_OK) rc = timeline_attach_all(h.buf);
+  if (rc != GCNN_OK) {
+    timeline_attach_all(nullptr);
+    cudaFree(h.buf);
+    return rc;
+  }
+  g_tl = h;
+  return GCNN_OK;
+}
+
+int gcnn_timeline_read(gcnn_ctx *c, int32_t *ids, int64_t *t_ns, int32_t max, int32_t *n) {
+  if (!c || !n || max < 0 || (max > 0 && (!ids || !t_ns))) return set_error(GCNN_EINVAL, "timeline: bad arguments");
+  std::lock_guard<std::mutex> lock(g_tl_mu);
+  if (!g_tl.buf) return set_error(GCNN_ESTATE, "timeline is not enabled");
+  GCNN_CUDA_TRY(cudaDeviceSynchronize());
+  unsigned count = 0;
+  GCNN_CUDA_TRY(cudaMemcpy(&count, g_tl.buf, sizeof(count), cudaMemcpyDeviceToHost));
+  const unsigned k = std::min<unsigned>(std::min(count, g_tl.cap), (unsigned)max);
+  if (k > 0) {
+    std::vector<unsigned long long> t(k);
+    std::vector<unsigned> id(k);
+    GCNN_CUDA_TRY(cudaMemcpy(t.data(), g_tl.buf + g_tl.off_t, sizeof(unsigned long long) * k, cudaMemcpyDeviceToHost));
+    GCNN_CUDA_TRY(cudaMemcpy(id.data(), g_tl.buf + g_tl.off_id, sizeof(unsigned) * k, cudaMemcpyDeviceToHost));
+    for (unsigned q = 0; q < k; ++q) {
+      ids[q] = (int32_t)id[q];
+      t_ns[q] = (int64_t)t[q];
+    }
+  }
+  GCNN_CUDA_TRY(cudaMemset(g_tl.buf, 0, sizeof(unsigned)));
+  *n = (int32_t)k;
   return GCNN_OK;
 }
 

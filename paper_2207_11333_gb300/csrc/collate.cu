@@ -25,7 +25,7 @@ collate_scan_kernel(int G, const int64_t *__restrict__ ids, StoreView st, BatchB
                     int cap_edges, unsigned *err) {
   __shared__ int warp_n[32], warp_e[32];
   __shared__ int carry_n, carry_e;
-  pdl_entry();
+  pdl_entry(GCNN_K_COLLATE_SCAN);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (threadIdx.x == 0) { carry_n = 0; carry_e = 0; }
   __syncthreads();
@@ -90,7 +90,7 @@ collate_graph_kernel(int G, const int64_t *__restrict__ ids, StoreView st, Batch
   __shared__ uint8_t s_dst[kGraphWarps][kMaxGraphEdges];
   __shared__ int s_cnt[kGraphWarps][256];
   __shared__ int s_start[kGraphWarps][256];
-  pdl_entry();
+  pdl_entry(GCNN_K_COLLATE_GRAPH);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = blockIdx.x * kGraphWarps + w;
   if (g >= G) return;  // warp-uniform; only warp-level synchronisation below
@@ -171,5 +171,7 @@ int launch_collate(int G, const int64_t *ids, StoreView st, BatchBuf b, const fl
                     cap_nodes, cap_edges, err));
   return GCNN_OK;
 }
+
+GCNN_TIMELINE_ATTACH(collate)
 
 }  // namespace gcnn

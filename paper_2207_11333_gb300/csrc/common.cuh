@@ -69,10 +69,44 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
-__device__ __forceinline__ void pdl_entry() {
+// Kernel timeline (gcnn_timeline_*): a device buffer of (clock, kernel id)
+// records.  Each translation unit has its own copy of the pointer below,
+// set by its timeline_attach_* function (the device code is not linked
+// across units).
+struct Timeline {
+  unsigned n, cap;
+  unsigned long long *t;
+  unsigned *id;
+};
+static __device__ Timeline *g_timeline = nullptr;
+
+__device__ __forceinline__ void timeline_stamp(unsigned kid) {
+  if (threadIdx.x == 0 && threadIdx.y == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) {
+    Timeline *tl = g_timeline;
+    if (tl) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      const unsigned k = atomicAdd(&tl->n, 1u);
+      if (k < tl->cap) {
+        tl->t[k] = t;
+        tl->id[k] = kid;
+      }
+    }
+  }
+}
+
+// kid: the kernel's GCNN_K_* identifier (timeline records)
+__device__ __forceinline__ void pdl_entry(unsigned kid) {
   pdl_wait();
   pdl_launch_dependents();
+  timeline_stamp(kid);
 }
+
+#define GCNN_TIMELINE_ATTACH(unit)                                                        \
+  int timeline_attach_##unit(void *tl) {                                                  \
+    GCNN_CUDA_TRY(cudaMemcpyToSymbol(g_timeline, &tl, sizeof(tl)));                       \
+    return GCNN_OK;                                                                       \
+  }
 
 // Launches on the legacy or per-thread default stream keep full serialisation;
 // GCNN_PDL=0 in the environment turns the attribute off everywhere.

@@ -61,20 +61,29 @@ struct gcnn_ctx {
   int fwd_G = 0, fwd_N = 0, fwd_E = 0;
   float lr_host = -1.f;
   float *lr_pinned = nullptr;
+  struct ProfEvent {
+    int phase;
+    cudaEvent_t a, b;
+  };
   struct Graph {
     cudaGraphExec_t exec;
     int kernels;
+    std::vector<ProfEvent> ev;  // profiling graphs: event-record nodes around each phase
   };
-  std::map<std::tuple<int, int, int, const double *>, Graph> graphs;
+  // key: grid (graphs, node bucket, edge bucket), loss accumulator, profiling graph
+  std::map<std::tuple<int, int, int, const double *, bool>, Graph> graphs;
   int last_step_kernels = 0;
   bool capturing = false;
   bool fuse_head = false;  // train step: head backward runs inside the forward's head kernel
 
   // per-phase event timing (gcnn_profile_enable)
   bool prof_on = false;
-  std::vector<cudaEvent_t> prof_ev;  // pairs: [2k] start, [2k+1] end
+  std::vector<cudaEvent_t> prof_ev;  // eager launches: pairs [2k] start, [2k+1] end
   std::vector<int> prof_cls;
   size_t prof_used = 0;
+  std::vector<ProfEvent> cap_ev;     // events recorded into the graph being captured
+  double prof_ms[GCNN_NPHASE] = {};  // accumulated from profiling-graph replays
+  int64_t prof_n[GCNN_NPHASE] = {};
 };
 
 namespace gcnn {

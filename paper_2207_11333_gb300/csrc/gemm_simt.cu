@@ -83,7 +83,7 @@ __device__ __forceinline__ float load_feat1(const Seg &sg, int node, int f) {
 template <bool AK, bool BNC>
 __global__ void __launch_bounds__(kThreads, 2)
 sgemm_kernel(GemmDesc d, DevDims dims, float *__restrict__ partial, int splits, int kps) {
-  pdl_entry();
+  pdl_entry(GCNN_K_GEMM_SIMT);
   __shared__ __align__(16) float As[2][BK][BM];
   __shared__ __align__(16) float Bs[2][BK][BN];
   const Sizes sz = actual_sizes(d, dims);
@@ -237,7 +237,7 @@ sgemm_kernel(GemmDesc d, DevDims dims, float *__restrict__ partial, int splits, 
 // C = epilogue(sum_z partial[z]); one thread per 4 outputs
 __global__ void __launch_bounds__(kThreads)
 splitk_reduce_kernel(GemmDesc d, DevDims dims, const float *__restrict__ partial, int splits) {
-  pdl_entry();
+  pdl_entry(GCNN_K_GEMM_SIMT_REDUCE);
   const Sizes sz = actual_sizes(d, dims);
   const int M = sz.M, N = d.N, N4 = N / 4;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -348,5 +348,7 @@ int run_splitk_reduce(const GemmDesc &d, DevDims dims, const float *partial, int
   GCNN_TRY(launch(splitk_reduce_kernel, ceil_div(work, kThreads), kThreads, 0, s, d, dims, partial, splits));
   return GCNN_OK;
 }
+
+GCNN_TIMELINE_ATTACH(gemm_simt)
 
 }  // namespace gcnn

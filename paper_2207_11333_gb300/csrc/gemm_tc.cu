@@ -351,7 +351,7 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b)) : "memory");
   }
-  pdl_entry();
+  pdl_entry(EPI == kEpiPartial ? GCNN_K_GEMM_TC_PARTIAL : (EPI == kEpiC ? GCNN_K_GEMM_TC_C : GCNN_K_GEMM_TC_D3));
   const Sizes sz = actual_sizes(d, dims);
   const int M = sz.M, K = sz.K, N = d.N;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -523,7 +523,7 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
 // C = epilogue(sum over splits); one thread per 8 outputs
 __global__ void __launch_bounds__(256) tc_reduce_kernel(TcDesc d, DevDims dims, const float *__restrict__ partial,
                                                        int splits) {
-  pdl_entry();
+  pdl_entry(GCNN_K_GEMM_TC_REDUCE);
   const Sizes sz = actual_sizes(d, dims);
   const int M = sz.M, N = d.N, N8 = N / 8;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -677,7 +677,7 @@ size_t gemm_tc_workspace_floats(int M, int N, int K) {
 // ---------------------------------------------------------------- casts
 namespace {
 __global__ void cast_bf16_kernel(int64_t n, const float *__restrict__ src, uint16_t *__restrict__ dst) {
-  pdl_entry();
+  pdl_entry(GCNN_K_CAST_BF16);
   const int64_t n8 = n / 8;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n8; q += stride) {
@@ -696,7 +696,7 @@ __global__ void cast_bf16_kernel(int64_t n, const float *__restrict__ src, uint1
 // Wx[n] = [W_U[n][0..H) | W_M[n][0..2H)].
 __global__ void pack_layer_kernel(int H, const float *__restrict__ msg_w, const float *__restrict__ upd_w,
                                   uint16_t *__restrict__ Wd, uint16_t *__restrict__ Wx) {
-  pdl_entry();
+  pdl_entry(GCNN_K_PACK_LAYER);
   const long long nd = 15LL * H * H, nx = 3LL * H * H;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < nd) {
@@ -727,5 +727,7 @@ int launch_pack_layer(int H, const float *msg_w, const float *upd_w, uint16_t *W
   GCNN_TRY(launch(pack_layer_kernel, ceil_div(work, 256), 256, 0, s, H, msg_w, upd_w, Wd, Wx));
   return GCNN_OK;
 }
+
+GCNN_TIMELINE_ATTACH(gemm_tc)
 
 }  // namespace gcnn

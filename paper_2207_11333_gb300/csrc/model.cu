@@ -237,7 +237,19 @@ int tc_backward_layer(gcnn_ctx *c, int Ngrid, int Egrid, int l, int cur) {
 }  // namespace
 
 PhaseScope::PhaseScope(gcnn_ctx *c, int phase) : c_(c), idx_(-1) {
-  if (!c->prof_on || c->capturing) return;
+  if (!c->prof_on) return;
+  if (c->capturing) {  // event-record nodes of a profiling graph
+    gcnn_ctx::ProfEvent pe{phase, nullptr, nullptr};
+    if (cudaEventCreate(&pe.a) != cudaSuccess || cudaEventCreate(&pe.b) != cudaSuccess) {
+      if (pe.a) cudaEventDestroy(pe.a);
+      cudaGetLastError();
+      return;
+    }
+    c->cap_ev.push_back(pe);
+    idx_ = (long)c->cap_ev.size() - 1;
+    cudaEventRecordWithFlags(pe.a, c->stream, cudaEventRecordExternal);
+    return;
+  }
   if (c->prof_used * 2 + 2 > c->prof_ev.size()) {
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
@@ -255,7 +267,9 @@ PhaseScope::PhaseScope(gcnn_ctx *c, int phase) : c_(c), idx_(-1) {
 }
 
 PhaseScope::~PhaseScope() {
-  if (idx_ >= 0) cudaEventRecord(c_->prof_ev[2 * idx_ + 1], c_->stream);
+  if (idx_ < 0) return;
+  if (c_->capturing) cudaEventRecordWithFlags(c_->cap_ev[idx_].b, c_->stream, cudaEventRecordExternal);
+  else cudaEventRecord(c_->prof_ev[2 * idx_ + 1], c_->stream);
 }
 
 int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train) {

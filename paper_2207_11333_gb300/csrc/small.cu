@@ -20,7 +20,7 @@ __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<floa
 __global__ void embed_kernel(int n_cap, int H, DevDims dims, const uint8_t *__restrict__ types,
                              const float *__restrict__ emb, int T, float *__restrict__ x0,
                              uint16_t *__restrict__ x0_16, int ld16) {
-  pdl_entry();
+  pdl_entry(GCNN_K_EMBED);
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -34,6 +34,8 @@ __global__ void embed_kernel(int n_cap, int H, DevDims dims, const uint8_t *__re
 
 constexpr int kMaxTypes = 16;
 constexpr int kRedThreads = 256;
+constexpr int kEmbBwdThreads = 512;   // one block per 4-column slice: nodes strided over the block
+constexpr int kColsumThreads = 1024;
 
 __device__ __forceinline__ float4 add4(float4 a, float4 b) {
   return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
@@ -54,18 +56,18 @@ __device__ __forceinline__ float4 warp_sum4(float4 a) {
 // dEmb[t][c..c+3] = sum of dx0[i][c..c+3] over the nodes i of type t.  One
 // block per 4-column slice; nodes strided over the block's threads, then a
 // fixed-order reduction (warp butterflies, warps in index order).
-__global__ void __launch_bounds__(kRedThreads)
+__global__ void __launch_bounds__(kEmbBwdThreads)
 embed_bwd_kernel(int n_cap, int H, DevDims dims, const uint8_t *__restrict__ types, const float *__restrict__ dx0,
                  int T, float *__restrict__ demb) {
-  pdl_entry();
-  __shared__ float4 sh[kRedThreads / 32][kMaxTypes];
+  pdl_entry(GCNN_K_EMBED_BWD);
+  __shared__ float4 sh[kEmbBwdThreads / 32][kMaxTypes];
   const int N = min(n_cap, dims.nodes(n_cap));
   const int c = blockIdx.x * 4;
   float4 acc[kMaxTypes];
 #pragma unroll
   for (int t = 0; t < kMaxTypes; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
-  for (int i = threadIdx.x; i < N; i += kRedThreads) {
+  for (int i = threadIdx.x; i < N; i += kEmbBwdThreads) {
     const int ty = types[i];
     const float4 v = ld4(dx0 + (size_t)i * H + c);
 #pragma unroll
@@ -82,7 +84,7 @@ embed_bwd_kernel(int n_cap, int H, DevDims dims, const uint8_t *__restrict__ typ
   __syncthreads();
   if (threadIdx.x < T) {
     float4 sum = sh[0][threadIdx.x];
-    for (int q = 1; q < kRedThreads / 32; ++q) sum = add4(sum, sh[q][threadIdx.x]);
+    for (int q = 1; q < kEmbBwdThreads / 32; ++q) sum = add4(sum, sh[q][threadIdx.x]);
     st4(demb + (size_t)threadIdx.x * H + c, sum);
   }
 }
@@ -90,7 +92,7 @@ embed_bwd_kernel(int n_cap, int H, DevDims dims, const uint8_t *__restrict__ typ
 // ---------------------------------------------------------------- pooling
 __global__ void pool_fwd_kernel(int g_cap, int H, DevDims dims, const int *__restrict__ node_off,
                                 const float *__restrict__ x, float *__restrict__ pooled) {
-  pdl_entry();
+  pdl_entry(GCNN_K_POOL_FWD);
   const int H4 = H >> 2;
   const int G = min(g_cap, dims.graphs(g_cap));
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -113,7 +115,7 @@ __global__ void pool_bwd_kernel(int n_cap, int H, DevDims dims, const int *__res
                                 const int *__restrict__ graph_id, const float *__restrict__ dpooled,
                                 float *__restrict__ dx, uint16_t *__restrict__ D3, int ld3, const float *__restrict__ h,
                                 const float *__restrict__ amp, const float *__restrict__ att) {
-  pdl_entry();
+  pdl_entry(GCNN_K_POOL_BWD);
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -164,7 +166,7 @@ constexpr int kHeadThreads = 512;
 
 template <bool kFwd, bool kBwd>
 __global__ void __launch_bounds__(kHeadThreads) head_graph_kernel(HeadArgs a) {
-  pdl_entry();
+  pdl_entry(GCNN_K_HEAD_GRAPH);
   extern __shared__ float sm[];
   __shared__ float red[kHeadThreads / 32];
   __shared__ float s_pred, s_dp;
@@ -294,7 +296,7 @@ constexpr int kHT = 32, kHG = 64;
 
 
 __global__ void __launch_bounds__(kRedThreads) head_grad_kernel(HeadGradArgs a) {
-  pdl_entry();
+  pdl_entry(GCNN_K_HEAD_GRAD);
   __shared__ float sp[kHG][kHT + 1], sd[kHG][kHT + 1];
   __shared__ double redd[kRedThreads / 32];
   __shared__ float redf[kRedThreads / 32];
@@ -412,7 +414,7 @@ adam_kernel(int64_t n, float *__restrict__ p, const float *__restrict__ g, float
             float *__restrict__ v, int *__restrict__ state, unsigned *__restrict__ ticket,
             const float *__restrict__ lrp, float b1, float b2, float eps, float wd, uint16_t *__restrict__ wb,
             uint16_t *__restrict__ wpack, AdamPack pk) {
-  pdl_entry();
+  pdl_entry(GCNN_K_ADAM);
   __shared__ float s_c[2];
   const int t = state[0] + 1;
   if (threadIdx.x == 0) {
@@ -459,18 +461,18 @@ adam_kernel(int64_t n, float *__restrict__ p, const float *__restrict__ g, float
 // out0[c] = sum_i a0[i][c] [mask[i][c] > 0] for c < cols0 and out1[c] =
 // sum_i a1[i][c] for c < cols1: one block per 4-column slice of [a0 | a1],
 // nodes strided over the block's threads, fixed-order reduction.
-__global__ void __launch_bounds__(kRedThreads)
+__global__ void __launch_bounds__(kColsumThreads)
 colsum_kernel(int n_cap, int cols0, DevDims dims, const float *__restrict__ a0, int ld0,
               const float *__restrict__ mask, int ldm, const float *__restrict__ a1, int ld1,
               float *__restrict__ out0, float *__restrict__ out1) {
-  pdl_entry();
-  __shared__ float4 sh[kRedThreads / 32];
+  pdl_entry(GCNN_K_COLSUM);
+  __shared__ float4 sh[kColsumThreads / 32];
   const int N = min(n_cap, dims.nodes(n_cap));
   const int c = blockIdx.x * 4;
   const bool first = c < cols0;
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
-  for (int i = threadIdx.x; i < N; i += kRedThreads) {
+  for (int i = threadIdx.x; i < N; i += kColsumThreads) {
     float4 x;
     if (first) {
       x = ld4(a0 + (size_t)i * ld0 + c);
@@ -491,7 +493,7 @@ colsum_kernel(int n_cap, int cols0, DevDims dims, const float *__restrict__ a0, 
   __syncthreads();
   if (threadIdx.x == 0) {
     float4 sum = sh[0];
-    for (int q = 1; q < kRedThreads / 32; ++q) sum = add4(sum, sh[q]);
+    for (int q = 1; q < kColsumThreads / 32; ++q) sum = add4(sum, sh[q]);
     st4(first ? out0 + c : out1 + (c - cols0), sum);
   }
 }
@@ -504,7 +506,7 @@ int launch_colsum2(int n_cap, int cols0, int cols1, DevDims dims, const float *a
   if (cols <= 0 || n_cap <= 0) return GCNN_OK;
   if (cols0 % 4 || cols1 % 4 || ld0 % 4 || ld1 % 4 || (mask && ldm % 4))
     return set_error(GCNN_EINVAL, "colsum: widths and strides must be multiples of 4");
-  GCNN_TRY(launch(colsum_kernel, cols / 4, kRedThreads, 0, s, n_cap, cols0, dims, a0, ld0, mask, ldm, a1, ld1, out0,
+  GCNN_TRY(launch(colsum_kernel, cols / 4, kColsumThreads, 0, s, n_cap, cols0, dims, a0, ld0, mask, ldm, a1, ld1, out0,
                   out1));
   return GCNN_OK;
 }
@@ -522,7 +524,7 @@ int launch_embed_bwd(int n_nodes, int H, DevDims dims, const uint8_t *types, con
                      float *demb, cudaStream_t s) {
   if (n_types > kMaxTypes) return set_error(GCNN_EINVAL, "at most %d atom types", kMaxTypes);
   if (H % 4) return set_error(GCNN_EINVAL, "embedding: hidden must be a multiple of 4");
-  GCNN_TRY(launch(embed_bwd_kernel, H / 4, kRedThreads, 0, s, std::max(n_nodes, 0), H, dims, types, dx0, n_types,
+  GCNN_TRY(launch(embed_bwd_kernel, H / 4, kEmbBwdThreads, 0, s, std::max(n_nodes, 0), H, dims, types, dx0, n_types,
                   demb));
   return GCNN_OK;
 }
@@ -591,5 +593,7 @@ int launch_adam(int64_t n, float *param, const float *grad, float *m, float *v, 
                   wb, wpack, pk));
   return GCNN_OK;
 }
+
+GCNN_TIMELINE_ATTACH(small)
 
 }  // namespace gcnn

@@ -103,6 +103,58 @@ def test_captured_train_step_matches_eager(tmp_path):
     ctx.check()
 
 
+def test_profiled_step_matches_and_times_phases(tmp_path):
+    """With profiling on, train_step replays a graph with event-record nodes
+    around every phase: same parameters bit for bit, every phase timed."""
+    d, ctx, st, b, ob, student = _setup(tmp_path)
+    acc = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ctx.train_step(b, 1e-3, acc)
+    plain = ctx.get_params()
+    ctx.set_params(student)
+    ctx.reset_optimizer()
+    ctx.profile(True)
+    ctx.profile_read()
+    b = ctx.collate(st, np.arange(64))
+    ctx.train_step(b, 1e-3, acc)
+    ph = ctx.profile_read()
+    ctx.profile(False)
+    assert np.array_equal(ctx.get_params(), plain)
+    for k in ("collate", "embed", "gemm", "agg_fwd", "agg_bwd", "head", "embed_bwd", "adam"):
+        assert ph[k][0] > 0 and ph[k][1] > 0, (k, ph[k])
+    assert ph["gemm"][1] == 6 * d.L  # message, update and four backward GEMMs per layer
+    ctx.check()
+
+
+def test_kernel_timeline_of_a_train_step(tmp_path):
+    """The kernel timeline records every launch of a collated train step in
+    order (FP32 path here: collation, embedding, per-layer GEMMs and
+    aggregations, head, backward, embedding gradient, optimiser), with
+    non-decreasing device times, and nothing once disabled."""
+    import paper_2207_11333_gb300 as g
+    d, ctx, st, b, ob, student = _setup(tmp_path)
+    acc = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ctx.timeline_enable(1024)
+    try:
+        ctx.timeline_read()
+        b = ctx.collate(st, np.arange(64))
+        ctx.train_step(b, 1e-3, acc)
+        ids, t = ctx.timeline_read()
+        names = [g.KERNELS[int(i)] for i in ids]
+        assert names[:3] == ["collate_scan", "collate_graph", "embed"]
+        assert names[-1] == "adam" and names[-2] == "embed_bwd"
+        assert names.count("agg_fwd") == d.L and names.count("agg_bwd_edge") == d.L
+        assert names.count("head_graph") == 1 and names.count("head_grad") == 1
+        assert names.count("gemm_simt") == 6 * d.L
+        assert np.all(np.diff(t) >= 0)
+        ctx.timeline_read()
+    finally:
+        ctx.timeline_enable(0)
+    ctx.train_step(ctx.collate(st, np.arange(64)), 1e-3, acc)
+    with pytest.raises(g.GcnnError):
+        ctx.timeline_read()
+    ctx.check()
+
+
 def test_checkpoint_resume_bitwise(tmp_path):
     d, ctx, st, b, ob, student = _setup(tmp_path)
     rng = np.random.default_rng(0)
