@@ -257,9 +257,9 @@ class Workload:
         self.Ec = (max(s[1] for s in sizes) + 511) // 512 * 512
 
 
-def make_ctx(g, wl: Workload, precision: str):
+def make_ctx(g, wl: Workload, precision: str, flags: int = 0):
     prec = g.PREC_BF16 if precision == "bf16" else g.PREC_FP32
-    ctx = g.Context(g.make_config(H, L, BATCH, wl.Nc, wl.Ec, delta=wl.delta, precision=prec))
+    ctx = g.Context(g.make_config(H, L, BATCH, wl.Nc, wl.Ec, delta=wl.delta, precision=prec, flags=flags))
     ctx.set_params(synth.init_params(SEED_STUDENT, H, L))
     ctx.set_order(wl.st, wl.order)
     return ctx
@@ -323,17 +323,24 @@ def gemm_traffic():
     return float(m.group(2)) if m and m.group(1) == src else None
 
 
-def kernel_profile(g, ctx, wl, n_steps, warmup, flush, loss_acc, precision):
+def kernel_profile(g, wl, n_steps, warmup, flush, loss_acc, precision):
     """Per-kernel durations inside the captured step, from the library's kernel timeline.
 
     Every library kernel records the device clock once its dependency on the
-    previous kernel is satisfied (the previous kernel's completion), so in the
+    previous kernel is satisfied (the previous kernel's completion), so in a
     serial graph the difference of consecutive records is a kernel's duration
-    as it runs in the step.  The last kernel of a step (the optimiser) has no
-    successor record and is left out; the collation kernels run before the
-    graph launch, so their durations include that host gap."""
+    as it runs in the step.  The timed step overlaps the BF16 weight-gradient
+    work on a second stream; these durations come from the same step on one
+    stream (GCNN_FLAG_SERIAL, same kernels and launch shapes).  The last
+    kernel of a step (the optimiser) has no successor record and is left
+    out; the collation kernels run before the graph launch, so their
+    durations include that host gap."""
     import torch
     from collections import Counter, defaultdict
+    ctx = make_ctx(g, wl, precision, g.FLAG_SERIAL)
+    for k in range(warmup):
+        ctx.train_step(batch_at(ctx, wl, k), LR, loss_acc)
+    torch.cuda.synchronize()
     ctx.timeline_enable(256 * n_steps)
     ctx.timeline_read()
     flops = agg_bytes = 0.0
@@ -351,10 +358,12 @@ def kernel_profile(g, ctx, wl, n_steps, warmup, flush, loss_acc, precision):
         flops += gemm_flops(b.n_nodes)
         agg_bytes += L * agg_fwd_bytes(b.n_nodes, b.n_edges, precision)
     ctx.timeline_enable(0)
+    ctx.check()
+    ctx.close()
     out = {"kernel_ms_per_step": {k: {"ms": 1e3 * v / n_steps, "launches": cnt[k] // n_steps}
                                   for k, v in sorted(dur.items(), key=lambda x: -x[1])},
            "kernel_timing": "library kernel timeline (device clock at each kernel's start after its dependency "
-                            "wait), inside the captured step; L2 flushed before each step"}
+                            "wait) over the step on one stream; L2 flushed before each step"}
     peaks = measured_peaks()
     if precision == "bf16":
         gemm_s = sum(v for k, v in dur.items() if k.startswith("gemm_tc"))
@@ -700,7 +709,7 @@ def run_ours(args):
         except Exception as e:  # noqa: BLE001
             line["e2e"] = {"error": repr(e)}
     try:
-        line.update(kernel_profile(g, ctx, wl, min(args.steps, 100), args.warmup, flush, loss_acc, args.precision))
+        line.update(kernel_profile(g, wl, min(args.steps, 100), args.warmup, flush, loss_acc, args.precision))
     except Exception as e:  # noqa: BLE001
         line["roofline"] = {"error": repr(e)}
     ctx.check()
@@ -724,7 +733,7 @@ def run_ours(args):
         cmp = {"value": r2["value"], "unit": "graphs/s", "ms_per_step": 1e3 * r2["dev_s"] / args.steps,
                "precision": args.compare}
         try:
-            prof = kernel_profile(g, c2, wl, min(args.steps, 50), args.warmup, flush, loss_acc, args.compare)
+            prof = kernel_profile(g, wl, min(args.steps, 50), args.warmup, flush, loss_acc, args.compare)
             cmp["roofline"] = prof["roofline"]
             cmp["kernel_ms_per_step"] = prof["kernel_ms_per_step"]
         except Exception as e:  # noqa: BLE001

@@ -75,6 +75,12 @@ extern "C" {
  * graph's results depend only on its own graph, never on its batch-mates
  * (bit-identical alone and in any batch).  Used by the inference server. */
 #define GCNN_FLAG_ROW_INVARIANT 1
+/* One stream for the whole step.  By default the BF16 backward (without
+ * recompute) runs each layer's weight- and bias-gradient GEMMs and sums on a
+ * second stream, overlapped with the data-gradient chain of the layers below
+ * (same kernels, same results bit for bit); this flag keeps every kernel on
+ * the caller's stream, in order, e.g. to time kernels one by one. */
+#define GCNN_FLAG_SERIAL 2
 
 /* Message for the last failing call on this thread (never NULL). */
 const char *gcnn_last_error(void);

@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libgcnn.so")
 
 PREC_FP32 = 0
 PREC_BF16 = 1
+FLAG_ROW_INVARIANT = 1
+FLAG_SERIAL = 2
 PHASES = ["collate", "embed", "gemm", "agg_fwd", "agg_bwd", "head", "embed_bwd", "adam"]
 NPHASE = len(PHASES)
 # kernel identifiers of the timeline records (GCNN_K_* in gcnn.h)

@@ -104,6 +104,8 @@ void destroy_ctx(gcnn_ctx *c) {
   }
   if (c->lr_pinned) cudaFreeHost(c->lr_pinned);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side) cudaStreamDestroy(c->side);
+  for (cudaEvent_t e : c->side_ev) cudaEventDestroy(e);
   if (c->order_dev) cudaFree(c->order_dev);
   if (c->dmem) cudaFree(c->dmem);
   delete c;
@@ -261,6 +263,10 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   const size_t o_tk = cv.take<unsigned>(16);
   const size_t o_ws = cv.take<float>(wsf);
   const bool bf = cfg->precision == GCNN_PREC_BF16;
+  // BF16 without recompute: weight gradients overlap on a second stream,
+  // with their own split-K workspace and a second [dP | dQ] buffer
+  const bool side = bf && !cfg->recompute;
+  const size_t o_ws2 = cv.take<float>(side ? wsf : 0), o_dPQ2 = cv.take<float>(side ? Nc * 2 * H : 0);
   const size_t o_wb = cv.take<uint16_t>(bf ? c->P : 0), o_wp = cv.take<uint16_t>(bf ? L * 18 * H * H : 0);
   const size_t o_U = cv.take<uint16_t>(bf ? (cfg->recompute ? 1 : L) * Nc * 16 * H : 0);
   const size_t o_Xb = cv.take<uint16_t>(bf && cfg->recompute ? L * Nc * H : 0);
@@ -289,6 +295,11 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   c->dPQ = (float *)(b + o_dPQ); c->dm = (float *)(b + o_dm); c->tickets = (unsigned *)(b + o_tk);
   c->ws.partial = (float *)(b + o_ws); c->ws.floats = wsf;
   c->ws.max_splits = (cfg->flags & GCNN_FLAG_ROW_INVARIANT) ? 1 : 32;
+  if (side) {
+    c->ws_side = c->ws;
+    c->ws_side.partial = (float *)(b + o_ws2);
+    c->dPQ2 = (float *)(b + o_dPQ2);
+  }
   if (bf) {
     c->wb = (uint16_t *)(b + o_wb); c->wpack = (uint16_t *)(b + o_wp); c->U = (uint16_t *)(b + o_U);
     if (cfg->recompute) c->Xb = (uint16_t *)(b + o_Xb);
@@ -303,6 +314,17 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   }
   if (rc == GCNN_OK && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     rc = set_error(GCNN_ECUDA, "cannot create the capture stream");
+  if (rc == GCNN_OK && side) {
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess)
+      rc = set_error(GCNN_ECUDA, "cannot create the side stream");
+    for (int q = 0; q < 3 * c->L && rc == GCNN_OK; ++q) {
+      cudaEvent_t ev = nullptr;
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+        rc = set_error(GCNN_ECUDA, "cannot create events");
+      else
+        c->side_ev.push_back(ev);
+    }
+  }
   if (rc == GCNN_OK && cudaMallocHost(&c->lr_pinned, sizeof(float)) != cudaSuccess)
     rc = set_error(GCNN_ENOMEM, "cannot allocate pinned memory");
   if (rc == GCNN_OK) rc = make_scaler_table(c);

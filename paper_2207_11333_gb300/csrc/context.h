@@ -11,6 +11,8 @@ struct gcnn_ctx {
   gcnn_config cfg{};
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
+  cudaStream_t side = nullptr;        // BF16 backward: weight-gradient work off the critical path
+  std::vector<cudaEvent_t> side_ev;   // 3 per layer: fork, aggregate gradient done, side work done
   int device = 0;
   int H = 0, L = 0, T = 0, Hh = 0;
   int64_t P = 0;       // parameter count
@@ -46,6 +48,7 @@ struct gcnn_ctx {
   float *pooled = nullptr, *z1 = nullptr, *pred = nullptr, *dpred = nullptr, *dz1 = nullptr;
   float *dg = nullptr;
   float *dH = nullptr, *dX = nullptr, *dagg = nullptr, *dPQ = nullptr, *dm = nullptr;
+  float *dPQ2 = nullptr;  // BF16: second [dP | dQ] buffer, alternating by layer
   unsigned *tickets = nullptr;  // zero-initialised completion counters of single-launch reductions
 
   // BF16 operands of the tensor-core GEMMs (precision == GCNN_PREC_BF16)
@@ -55,6 +58,7 @@ struct gcnn_ctx {
   uint16_t *Xb = nullptr;     // recompute only: L x Nc x H layer inputs (copied into U when needed)
   uint16_t *G5[2] = {nullptr, nullptr};  // Nc x 5H: [amp*g | att*g | g | dP | dQ]
   gcnn::GemmWorkspace ws{};
+  gcnn::GemmWorkspace ws_side{};  // split-K partials of the GEMMs on the side stream
 
   // host-side state
   bool have_fwd = false;

@@ -76,6 +76,25 @@ int tc(gcnn_ctx *c, const TcDesc &d) {
   return run_gemm_tc(d, DevDims{c->bb.dims}, c->ws, c->err, c->stream);
 }
 
+// The stream (and split-K workspace) of a layer's weight- and bias-gradient
+// work: a second stream that overlaps the data-gradient chain, or the main
+// stream when the step runs serially.
+struct Lane {
+  cudaStream_t s;
+  const GemmWorkspace *ws;
+};
+
+int tc_on(gcnn_ctx *c, const TcDesc &d, Lane lane) {
+  PhaseScope ps(c, GCNN_PHASE_GEMM);
+  return run_gemm_tc(d, DevDims{c->bb.dims}, *lane.ws, c->err, lane.s);
+}
+
+// BF16 backward without recompute overlaps unless asked not to (profiling
+// times phases on the main stream, so it runs serially too)
+bool overlapped(const gcnn_ctx *c) {
+  return c->side && !(c->cfg.flags & GCNN_FLAG_SERIAL) && !c->prof_on && !c->cfg.recompute;
+}
+
 bool bf16(const gcnn_ctx *c) { return c->cfg.precision == GCNN_PREC_BF16; }
 
 // BF16 views
@@ -173,27 +192,43 @@ int tc_update(gcnn_ctx *c, int Ngrid, int l) {
 
 // BF16 backward of layer l.  dH holds dL/dx_{l+1} (FP32) and G5[cur] its
 // masked, scaled BF16 form in columns [0, 3H).  Writes dX = dL/dx_l and, for
-// l > 0, columns [0, 3H) of G5[cur ^ 1].
-int tc_backward_layer(gcnn_ctx *c, int Ngrid, int Egrid, int l, int cur) {
+// l > 0, columns [0, 3H) of G5[cur ^ 1]; [dP | dQ] goes to dPQ (FP32) and to
+// columns [3H, 5H) of G5[cur].
+//
+// Critical path on the main stream: dagg -> aggregate backward -> dx.  The
+// weight and bias gradients (dW_U, dW_M, their split-K reductions and the
+// bias column sums) go to the side lane: dW_U once G5[cur] is final (event
+// `fork`), dW_M and the sums once [dP | dQ] is (event `mid`); event `done`
+// marks the lane's work of the layer.  dx(l) overwrites G5[cur ^ 1] and the
+// FP32 gradient the previous layer's sums read, so it waits for `done` of
+// layer l + 1; dPQ alternates between two buffers by layer.
+int tc_backward_layer(gcnn_ctx *c, int Ngrid, int Egrid, int l, int cur, float *dPQ, bool ov) {
   const int H = c->H;
   DevDims dims{c->bb.dims};
   LayerW gw = layer_ptrs(c->grads, c, l);
   const float *pq = pq_at(c, l), *h = xs_at(c, l + 1);
   float *agg = agg_at(c, l);
   uint16_t *G = c->G5[cur];
+  const Lane lane = ov ? Lane{c->side, &c->ws_side} : Lane{c->stream, &c->ws};
+  cudaEvent_t fork = ov ? c->side_ev[3 * l] : nullptr, mid = ov ? c->side_ev[3 * l + 1] : nullptr;
+  cudaEvent_t done = ov ? c->side_ev[3 * l + 2] : nullptr;
   if (c->cfg.recompute) {
     PhaseScope ps(c, GCNN_PHASE_AGG_FWD);
     GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq, agg, (float)c->cfg.std_eps, c->err,
                                   c->stream, U_at(c, l) + H, 16 * H, c->bb.amp, c->bb.att));
     GCNN_TRY(stage_x(c, Ngrid, l));
   }
-  {  // dW_U = [x | scaled aggs]^T dpre ; db_U = column sums of dpre
+  if (ov) {
+    GCNN_CUDA_TRY(cudaEventRecord(fork, c->stream));
+    GCNN_CUDA_TRY(cudaStreamWaitEvent(lane.s, fork, 0));
+  }
+  {  // dW_U = [x | scaled aggs]^T dpre
     TcDesc d = tblank();
     d.M = 16 * H; d.N = H; d.K = Ngrid; d.node_dim = kNodeK;
     d.A = mat(U_at(c, l), 16 * H, Ngrid, 16 * H, true);
     d.B = mat(G + 2 * H, 5 * H, Ngrid, H, true);
     d.ep.C = gw.upd_w; d.ep.ldc = H;
-    GCNN_TRY(tc(c, d));
+    GCNN_TRY(tc_on(c, d, lane));
   }
   {  // dagg = [amp g | att g | g] [W_amp ; W_att ; W_id]^T
     TcDesc d = tblank();
@@ -206,18 +241,26 @@ int tc_backward_layer(gcnn_ctx *c, int Ngrid, int Egrid, int l, int cur) {
   {
     PhaseScope ps(c, GCNN_PHASE_AGG_BWD);
     GCNN_TRY(launch_aggregate_bwd(Ngrid, Egrid, H, dims, c->bb.row_ptr, c->bb.col, c->bb.rev, pq, agg, c->dagg,
-                                  c->dPQ, c->dm, (float)c->cfg.std_eps, c->err, c->stream, G + 3 * H, 5 * H));
+                                  dPQ, c->dm, (float)c->cfg.std_eps, c->err, c->stream, G + 3 * H, 5 * H));
   }
-  {  // dW_M = x^T [dP | dQ] ; db_M = column sums of dP
+  if (ov) {
+    GCNN_CUDA_TRY(cudaEventRecord(mid, c->stream));
+    GCNN_CUDA_TRY(cudaStreamWaitEvent(lane.s, mid, 0));
+  }
+  {  // dW_M = x^T [dP | dQ]
     TcDesc d = tblank();
     d.M = H; d.N = 2 * H; d.K = Ngrid; d.node_dim = kNodeK;
     d.A = mat(X_at(c, l), X_ld(c), Ngrid, H, true);
     d.B = mat(G + 3 * H, 5 * H, Ngrid, 2 * H, true);
     d.ep.C = gw.msg_w; d.ep.ldc = 2 * H;
-    GCNN_TRY(tc(c, d));
+    GCNN_TRY(tc_on(c, d, lane));
     // bias gradients: db_U = sum of dpre, db_M = sum of dP (FP32, fixed order)
     PhaseScope ps(c, GCNN_PHASE_GEMM);
-    GCNN_TRY(launch_colsum2(Ngrid, H, H, dims, c->dH, H, h, H, c->dPQ, 2 * H, gw.upd_b, gw.msg_b, c->stream));
+    GCNN_TRY(launch_colsum2(Ngrid, H, H, dims, c->dH, H, h, H, dPQ, 2 * H, gw.upd_b, gw.msg_b, lane.s));
+  }
+  if (ov) {
+    GCNN_CUDA_TRY(cudaEventRecord(done, lane.s));
+    if (l + 1 < c->L) GCNN_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->side_ev[3 * (l + 1) + 2], 0));
   }
   {  // dx = [g | dP | dQ] [W_x | A | B]^T ; the next layer's masked, scaled BF16 gradient
     TcDesc d = tblank();
@@ -310,12 +353,16 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
     GCNN_TRY(launch_head_grad(ga, c->stream));
   }
   if (bf16(c)) {
+    const bool ov = overlapped(c);
     int cur = 0;
     for (int l = c->L - 1; l >= 0; --l) {
-      GCNN_TRY(tc_backward_layer(c, Ngrid, Egrid, l, cur));
+      float *dPQ = (ov && (l & 1)) ? c->dPQ2 : c->dPQ;
+      GCNN_TRY(tc_backward_layer(c, Ngrid, Egrid, l, cur, dPQ, ov));
       cur ^= 1;
       std::swap(c->dH, c->dX);
     }
+    // every gradient is complete before the embedding gradient and the optimiser
+    if (ov) GCNN_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->side_ev[2], 0));
   }
   for (int l = bf16(c) ? -1 : c->L - 1; l >= 0; --l) {
     LayerW w = layer_ptrs(c->params, c, l);

@@ -61,3 +61,33 @@ def test_bf16_recompute_identical(tmp_path):
     _, _, _, p1, _, g1 = _run(tmp_path, g.PREC_BF16, recompute=False)
     _, _, _, p2, _, g2 = _run(tmp_path, g.PREC_BF16, recompute=True)
     assert np.array_equal(p1, p2) and np.array_equal(g1, g2)
+
+
+def test_overlapped_backward_matches_serial(tmp_path):
+    """The BF16 backward's weight-gradient work on a second stream (default)
+    gives the same gradients and parameters, bit for bit, as the serial step
+    (GCNN_FLAG_SERIAL), over captured train steps and an eager backward."""
+    import paper_2207_11333_gb300 as g
+    G, H, L = 96, 64, 3
+    d, gs, delta, student = workloads.small_parity(G=G, lo=3, hi=51, H=H, L=L)
+    path, _ = write_both(gs, str(tmp_path))
+    st = g.Store(path)
+    res = []
+    for flags in (0, g.FLAG_SERIAL):
+        cfg = g.make_config(H, L, G, int(gs.n_nodes), int(gs.n_edges), delta=delta, precision=g.PREC_BF16,
+                            flags=flags, head_hidden=H)
+        ctx = g.Context(cfg)
+        ctx.set_params(student)
+        acc = torch.zeros(3, dtype=torch.float64, device="cuda")
+        for k in range(3):
+            ids = np.random.default_rng(k).permutation(G)
+            ctx.train_step(ctx.collate(st, ids), 1e-3, acc)
+        b = ctx.collate(st, np.arange(G))
+        ctx.forward(b, train=True)
+        ctx.backward(b)
+        res.append((ctx.get_params(), ctx.get_grads(), acc.cpu().numpy()))
+        ctx.check()
+        ctx.close()
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
+    assert np.array_equal(res[0][2], res[1][2])
