@@ -190,6 +190,37 @@ __device__ __forceinline__ void emit8(const TcEpilogue &e, int N, int row, int n
   }
 }
 
+// ---------------------------------------------------------------- cluster
+// barrier over every thread of every CTA of the cluster (release / acquire)
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// 16 bytes at shared-memory address a of cluster CTA `rank`
+__device__ __forceinline__ float4 ld_cluster4(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(r)
+               : "memory");
+  return v;
+}
+
+// Element p of the staged tile summed over the cluster's `ranks` CTAs in rank
+// order (the K-splits of one output tile), or the CTA's own value.
+__device__ __forceinline__ float4 tile_sum(const float *p, int ranks) {
+  if (ranks == 1) return *reinterpret_cast<const float4 *>(p);
+  const uint32_t a = smem_u32(p);
+  float4 s = ld_cluster4(a, 0);
+  for (int z = 1; z < ranks; ++z) {
+    const float4 t = ld_cluster4(a, z);
+    s.x += t.x; s.y += t.y; s.z += t.z; s.w += t.w;
+  }
+  return s;
+}
+
 // ---------------------------------------------------------------- tile stores
 // The FP32 tile staged in shared memory (row pitch RS floats) goes to global
 // memory row by row: warp w takes rows w, w + 8, ...; lane l the 4-column
@@ -219,9 +250,10 @@ __device__ __forceinline__ void store_partial(const float *S, int RS, int rows, 
   }
 }
 
-// C (FP32) and / or C16 (BF16) with optional bias and ReLU
-__device__ __forceinline__ void store_c(const float *S, int RS, int rows, int BN, int N, int m0, int n0,
-                                        const TcEpilogue e, int warp, int lane) {
+// C (FP32) and / or C16 (BF16) with optional bias and ReLU, tile rows [rb, re)
+// summed over `ranks` cluster CTAs
+__device__ __forceinline__ void store_c(const float *S, int RS, int rb, int re, int ranks, int BN, int N, int m0,
+                                        int n0, const TcEpilogue e, int warp, int lane) {
 #pragma unroll 1
   for (int h = 0; h < 2; ++h) {
     const int cn = 128 * h + 4 * lane;
@@ -232,15 +264,15 @@ __device__ __forceinline__ void store_c(const float *S, int RS, int rows, int BN
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (n + q < e.bias_n) b[q] = e.bias[n + q];
-    for (int r0 = warp; r0 < rows; r0 += 32) {
+    for (int r0 = rb + warp; r0 < re; r0 += 32) {
       float4 v[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        v[u] = r0 + 8 * u < rows ? *reinterpret_cast<const float4 *>(S + (size_t)(r0 + 8 * u) * RS + cn)
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[u] = r0 + 8 * u < re ? tile_sum(S + (size_t)(r0 + 8 * u) * RS + cn, ranks)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (r0 + 8 * u >= rows) break;
+        if (r0 + 8 * u >= re) break;
         const size_t row = (size_t)(m0 + r0 + 8 * u);
         float4 x = make_float4(v[u].x + b[0], v[u].y + b[1], v[u].z + b[2], v[u].w + b[3]);
         if (e.relu) {
@@ -253,10 +285,11 @@ __device__ __forceinline__ void store_c(const float *S, int RS, int rows, int BN
   }
 }
 
-// C (FP32, nullable) and the BF16 blocks [amp g | att g | g] of D3, g = v [mask > 0];
-// mask bits and degree scalers come from shared memory (prefetched)
-__device__ __forceinline__ void store_d3(const float *S, int RS, int rows, int BN, int N, int m0, int n0,
-                                         const TcEpilogue e, const uint32_t *mbits, const float *s_amp,
+// C (FP32, nullable) and the BF16 blocks [amp g | att g | g] of D3, g = v [mask > 0],
+// tile rows [rb, re) summed over `ranks` cluster CTAs; mask bits and degree
+// scalers come from shared memory (prefetched)
+__device__ __forceinline__ void store_d3(const float *S, int RS, int rb, int re, int ranks, int BN, int N, int m0,
+                                         int n0, const TcEpilogue e, const uint32_t *mbits, const float *s_amp,
                                          const float *s_att, int warp, int lane) {
 #pragma unroll 1
   for (int h = 0; h < 2; ++h) {
@@ -264,7 +297,7 @@ __device__ __forceinline__ void store_d3(const float *S, int RS, int rows, int B
     const int n = n0 + cn;
     if (cn >= BN || n >= N) continue;
     const int word = cn / 32, shift = cn % 32;
-    for (int r0 = warp; r0 < rows; r0 += 32) {
+    for (int r0 = rb + warp; r0 < re; r0 += 32) {
       float4 v[4];
       uint32_t mk[4];
       float am[4], at[4];
@@ -274,8 +307,8 @@ __device__ __forceinline__ void store_d3(const float *S, int RS, int rows, int B
         v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         mk[u] = 0u;
         am[u] = at[u] = 0.f;
-        if (r < rows) {
-          v[u] = *reinterpret_cast<const float4 *>(S + (size_t)r * RS + cn);
+        if (r < re) {
+          v[u] = tile_sum(S + (size_t)r * RS + cn, ranks);
           mk[u] = mbits[r * kMaskWords + word] >> shift;
           am[u] = s_amp[r];
           at[u] = s_att[r];
@@ -283,7 +316,7 @@ __device__ __forceinline__ void store_d3(const float *S, int RS, int rows, int B
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (r0 + 8 * u >= rows) break;
+        if (r0 + 8 * u >= re) break;
         const size_t row = (size_t)(m0 + r0 + 8 * u);
         const float4 x = v[u];
         if (e.C) *reinterpret_cast<float4 *>(e.C + row * e.ldc + n) = x;
@@ -324,7 +357,10 @@ __device__ __forceinline__ void clear_k_rows(uint8_t *tile, int atoms, int from,
   }
 }
 
-template <int EPI>
+// CL: the grid's z dimension (K-splits of one output tile) is a thread-block
+// cluster; the split-K partial tiles are summed through distributed shared
+// memory instead of a partial buffer and a reduction kernel.
+template <int EPI, bool CL>
 __global__ void __launch_bounds__(kThreads, 1)
 tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, float *__restrict__ partial, int splits,
                 int kps, int BN, unsigned *err) {
@@ -504,15 +540,25 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
         }
       }
     }
-    if (!__syncthreads_or(!ok)) {
+    const bool failed = __syncthreads_or(!ok);
+    if (CL) cluster_sync();  // every CTA's tile is staged (reached after a failure too)
+    if (!failed) {
       const int rows = min(BM, M - m0);
+      int rb = 0, re = rows, ranks = 1;
+      if (CL) {  // this CTA's share of the tile's rows, summed over the cluster
+        const int share = (rows + splits - 1) / splits;
+        rb = min(rows, z * share);
+        re = min(rows, rb + share);
+        ranks = splits;
+      }
       if constexpr (EPI == kEpiPartial)
         store_partial(S, RS, rows, BN, N, m0, n0, partial + (size_t)z * d.M * N, warp, lane);
       else if constexpr (EPI == kEpiC)
-        store_c(S, RS, rows, BN, N, m0, n0, d.ep, warp, lane);
+        store_c(S, RS, rb, re, ranks, BN, N, m0, n0, d.ep, warp, lane);
       else
-        store_d3(S, RS, rows, BN, N, m0, n0, d.ep, mbits, s_amp, s_att, warp, lane);
+        store_d3(S, RS, rb, re, ranks, BN, N, m0, n0, d.ep, mbits, s_amp, s_att, warp, lane);
     }
+    if (CL) cluster_sync();  // no CTA leaves while its tile may still be read
   }
   fence_before_sync();
   __syncthreads();
@@ -578,41 +624,104 @@ int make_map(CUtensorMap *m, const TcMat &a, int box_rows) {
   return GCNN_OK;
 }
 
-int g_configured = 0;
+constexpr int kMaxCluster = 6;  // largest split-K cluster (co-resident capacity falls beyond)
+
+template <int EPI, bool CL>
+void set_smem_attr(int *rc) {
+  if (*rc == GCNN_OK &&
+      cudaFuncSetAttribute(tma_gemm_kernel<EPI, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
+          cudaSuccess)
+    *rc = set_error(GCNN_ECUDA, "tc gemm: cannot set the shared-memory size");
+}
+
+// co-resident clusters of `size` CTAs of the cluster kernel of one epilogue kind
+template <int EPI>
+int cluster_capacity_of(int size) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = size;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(1, 1, size);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, (void *)tma_gemm_kernel<EPI, true>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+int g_rc = GCNN_OK;
+int g_capacity[2][kMaxCluster + 1];  // [masked-gradient kind][cluster size]
+
+// shared-memory attributes and cluster capacities, once per process
+int configure() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int rc = GCNN_OK;
+    set_smem_attr<kEpiPartial, false>(&rc);
+    set_smem_attr<kEpiC, false>(&rc);
+    set_smem_attr<kEpiD3, false>(&rc);
+    set_smem_attr<kEpiC, true>(&rc);
+    set_smem_attr<kEpiD3, true>(&rc);
+    for (int sz = 2; sz <= kMaxCluster && rc == GCNN_OK; ++sz) {
+      g_capacity[0][sz] = cluster_capacity_of<kEpiC>(sz);
+      g_capacity[1][sz] = cluster_capacity_of<kEpiD3>(sz);
+    }
+    g_rc = rc;
+  });
+  return g_rc;
+}
 
 struct Plan {
   int BN, ntiles, splits;
+  bool cluster;  // split-K summed in a cluster through distributed shared memory
 };
 
 // Tile width and split count of one launch.  A CTA's time is dominated by
 // the bytes it moves: operand tiles from L2 (~100 GB/s per SM), the FP32
 // accumulator tile and the epilogue outputs to memory (~40 GB/s per SM
-// sustained by one CTA), plus, for split-K, a reduction pass over the
-// partial tiles.  Among widths BN (multiple of 16, <= 256) and splits whose
-// grid fits one wave (one CTA per SM), take the smallest estimate; grids
-// larger than a wave use the widest tiles and no split.
+// sustained by one CTA), and for split-K either a reduction pass over partial
+// tiles in global memory (a separate kernel) or, with the splits of a tile
+// in one cluster, reads of the other CTAs' staged tiles (~50 GB/s per SM) and
+// two cluster barriers, each CTA then storing its share of the rows.  Among
+// widths BN (multiple of 16, <= 256) and splits whose grid fits one wave (one
+// CTA per SM; clusters within their co-resident capacity), take the smallest
+// estimate; grids larger than a wave use the widest tiles and no split.
 // out_bytes: epilogue bytes per output element; b_mn: B tiles are MN-major
-// (loaded in 64-column atoms).
-Plan choose(int M, int N, int K, int max_splits, double out_bytes, bool b_mn) {
+// (loaded in 64-column atoms); d3: masked-gradient epilogue.
+Plan choose(int M, int N, int K, int max_splits, double out_bytes, bool b_mn, bool d3) {
   const int sms = num_sms();
   const long long mtiles = (M + BM - 1) / BM;
   const int ktiles = std::max(1, (K + BK - 1) / BK);
-  Plan best{0, 0, 1};
+  Plan best{0, 0, 1, false};
   double best_t = 1e30;
   for (int bn = 16; bn <= kMaxBN; bn += 16) {
     const int nt = (N + bn - 1) / bn;
     if (nt > 1 && (long long)bn * (nt - 1) >= N) continue;
+    const double b_tile = b_mn ? ((bn + 63) / 64) * 8192.0 : bn * 128.0;
     for (int sp = 1; sp <= std::min(max_splits, ktiles); ++sp) {
       if (mtiles * nt * sp > sms) break;
       const int kps = (ktiles + sp - 1) / sp;
-      const double b_tile = b_mn ? ((bn + 63) / 64) * 8192.0 : bn * 128.0;
       const double t_load = kps * (kATileBytes + b_tile) / 1.0e5;          // us at 100 GB/s
       const double t_out = BM * (double)bn * (sp > 1 ? 4.0 : out_bytes) / 4.0e4;  // us at 40 GB/s
       const double t_red = sp > 1 ? 2.0 + (double)M * N * (4.0 * sp + out_bytes) / 5.0e6 : 0.0;
       const double t = t_load + t_out + t_red;
       if (t < best_t) {
         best_t = t;
-        best = Plan{bn, nt, sp};
+        best = Plan{bn, nt, sp, false};
+      }
+      if (sp >= 2 && sp <= kMaxCluster && mtiles * nt <= g_capacity[d3 ? 1 : 0][sp]) {
+        const double t_cl = t_load + BM * (double)bn * 4.0 / 5.0e4 + 0.5 + BM * (double)bn * out_bytes / sp / 4.0e4;
+        if (t_cl < best_t) {
+          best_t = t_cl;
+          best = Plan{bn, nt, sp, true};
+        }
       }
     }
   }
@@ -631,6 +740,35 @@ int max_splits_of(int M, int K) {
   return (int)std::max<long long>(1, std::min<long long>({32LL, (long long)ktiles, num_sms() / std::max(1LL, mtiles)}));
 }
 
+// kernel<<<grid, kThreads, kSmemBytes, s>>> as a cluster of (1, 1, cz) CTAs
+// (cz > 1), with programmatic serialisation like every launch of the library
+template <typename... P, typename... A>
+int launch_gemm(void (*kernel)(P...), dim3 grid, int cz, cudaStream_t s, A &&...args) {
+  cudaLaunchAttribute attr[2];
+  int n = 0;
+  if (cz > 1) {
+    attr[n].id = cudaLaunchAttributeClusterDimension;
+    attr[n].val.clusterDim.x = 1;
+    attr[n].val.clusterDim.y = 1;
+    attr[n].val.clusterDim.z = cz;
+    ++n;
+  }
+  if (pdl_enabled(s)) {
+    attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = kSmemBytes;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = n;
+  GCNN_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, std::forward<A>(args)...));
+  return GCNN_OK;
+}
+
 }  // namespace
 
 int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned *err, cudaStream_t s) {
@@ -641,27 +779,24 @@ int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
       (e.D3 && (e.ld3 % 8 || reinterpret_cast<uintptr_t>(e.D3) % 16 || !e.mask || !e.amp || !e.att ||
                 e.ldm % 4 || reinterpret_cast<uintptr_t>(e.mask) % 16 || e.bias || e.relu)))
     return set_error(GCNN_EINVAL, "tc gemm: N must be a multiple of 8 and outputs 16-byte aligned");
+  GCNN_TRY(configure());
   const double out_bytes = (e.C ? 4.0 : 0.0) + (e.C16 ? 2.0 : 0.0) + (e.D3 ? 10.0 : 0.0);
-  const Plan plan = choose(d.M, d.N, d.K, ws.max_splits, out_bytes, d.B.mn_major);
-  const int BN = plan.BN, ntiles = plan.ntiles;
-  int splits = plan.splits;
+  Plan plan = choose(d.M, d.N, d.K, ws.max_splits, out_bytes, d.B.mn_major, e.D3 != nullptr);
+  if (plan.splits > 1 && !plan.cluster && (size_t)plan.splits * d.M * d.N > ws.floats) plan.splits = 1;
+  const int BN = plan.BN, ntiles = plan.ntiles, splits = plan.splits;
   const int ktiles = (d.K + BK - 1) / BK;
   TcMaps maps;
   GCNN_TRY(make_map(&maps.a, d.A, d.A.mn_major ? 64 : BM));
   GCNN_TRY(make_map(&maps.b, d.B, d.B.mn_major ? 64 : BN));
-  if (!g_configured) {
-    GCNN_CUDA_TRY(cudaFuncSetAttribute(tma_gemm_kernel<kEpiPartial>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kSmemBytes));
-    GCNN_CUDA_TRY(cudaFuncSetAttribute(tma_gemm_kernel<kEpiC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    GCNN_CUDA_TRY(cudaFuncSetAttribute(tma_gemm_kernel<kEpiD3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    g_configured = 1;
-  }
-  if (splits > 1 && (size_t)splits * d.M * d.N > ws.floats) splits = 1;
   const int kps = (ktiles + splits - 1) / splits * BK;
   dim3 grid(ntiles, (d.M + BM - 1) / BM, splits);
-  auto kernel = splits > 1 ? tma_gemm_kernel<kEpiPartial> : (e.D3 ? tma_gemm_kernel<kEpiD3> : tma_gemm_kernel<kEpiC>);
-  GCNN_TRY(launch(kernel, grid, kThreads, kSmemBytes, s, maps, d, dims, splits > 1 ? ws.partial : nullptr,
-                  splits, kps, BN, err));
+  if (splits > 1 && plan.cluster) {
+    auto kernel = e.D3 ? tma_gemm_kernel<kEpiD3, true> : tma_gemm_kernel<kEpiC, true>;
+    return launch_gemm(kernel, grid, splits, s, maps, d, dims, (float *)nullptr, splits, kps, BN, err);
+  }
+  auto kernel = splits > 1 ? tma_gemm_kernel<kEpiPartial, false>
+                           : (e.D3 ? tma_gemm_kernel<kEpiD3, false> : tma_gemm_kernel<kEpiC, false>);
+  GCNN_TRY(launch_gemm(kernel, grid, 1, s, maps, d, dims, splits > 1 ? ws.partial : nullptr, splits, kps, BN, err));
   if (splits > 1) {
     const long long work = (long long)d.M * (d.N / 8);
     GCNN_TRY(launch(tc_reduce_kernel, ceil_div(work, 256), 256, 0, s, d, dims, (const float *)ws.partial, splits));
