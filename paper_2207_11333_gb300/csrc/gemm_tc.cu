@@ -695,8 +695,8 @@ struct Plan {
 // estimate; grids larger than a wave use the widest tiles and no split.
 // out_bytes: epilogue bytes per output element; b_mn: B tiles are MN-major
 // (loaded in 64-column atoms); d3: masked-gradient epilogue.
-Plan choose(int M, int N, int K, int max_splits, double out_bytes, bool b_mn, bool d3) {
-  const int sms = num_sms();
+Plan choose(int M, int N, int K, int max_splits, int max_ctas, double out_bytes, bool b_mn, bool d3) {
+  const int sms = max_ctas > 0 ? std::min(max_ctas, num_sms()) : num_sms();
   const long long mtiles = (M + BM - 1) / BM;
   const int ktiles = std::max(1, (K + BK - 1) / BK);
   Plan best{0, 0, 1, false};
@@ -716,7 +716,7 @@ Plan choose(int M, int N, int K, int max_splits, double out_bytes, bool b_mn, bo
         best_t = t;
         best = Plan{bn, nt, sp, false};
       }
-      if (sp >= 2 && sp <= kMaxCluster && mtiles * nt <= g_capacity[d3 ? 1 : 0][sp]) {
+      if (sp >= 2 && sp <= kMaxCluster && mtiles * nt <= g_capacity[d3 ? 1 : 0][sp] && mtiles * nt * sp <= sms) {
         const double t_cl = t_load + BM * (double)bn * 4.0 / 5.0e4 + 0.5 + BM * (double)bn * out_bytes / sp / 4.0e4;
         if (t_cl < best_t) {
           best_t = t_cl;
@@ -781,7 +781,7 @@ int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
     return set_error(GCNN_EINVAL, "tc gemm: N must be a multiple of 8 and outputs 16-byte aligned");
   GCNN_TRY(configure());
   const double out_bytes = (e.C ? 4.0 : 0.0) + (e.C16 ? 2.0 : 0.0) + (e.D3 ? 10.0 : 0.0);
-  Plan plan = choose(d.M, d.N, d.K, ws.max_splits, out_bytes, d.B.mn_major, e.D3 != nullptr);
+  Plan plan = choose(d.M, d.N, d.K, ws.max_splits, ws.max_ctas, out_bytes, d.B.mn_major, e.D3 != nullptr);
   if (plan.splits > 1 && !plan.cluster && (size_t)plan.splits * d.M * d.N > ws.floats) plan.splits = 1;
   const int BN = plan.BN, ntiles = plan.ntiles, splits = plan.splits;
   const int ktiles = (d.K + BK - 1) / BK;

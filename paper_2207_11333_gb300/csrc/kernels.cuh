@@ -147,6 +147,7 @@ struct GemmWorkspace {
   float *partial;      // split-K partial sums
   size_t floats;       // capacity
   int max_splits = 32; // 1: row-invariant (no split-K)
+  int max_ctas = 0;    // tensor-core GEMMs: grid limit (0: one CTA per SM), e.g. to share the GPU with a stream
 };
 
 int run_gemm_simt(const GemmDesc &d, DevDims dims, const GemmWorkspace &ws, cudaStream_t s);
