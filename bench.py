@@ -377,8 +377,8 @@ def kernel_profile(g, wl, n_steps, warmup, flush, loss_acc, precision):
         out["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                            "frac": achieved / peak, "traffic": gemm_traffic(), "traffic_unit": "DRAM bytes per launch",
                            "peak_source": src, "launches_per_step": launches,
-                           "kernel": "tma_gemm_kernel<epilogue> + tc_reduce_kernel (all dense GEMMs of the step, "
-                                     "BF16 tcgen05, FP32 accumulate)"}
+                           "kernel": "tma_gemm_kernel<epilogue, cluster> (all dense GEMMs of the step, BF16 tcgen05, "
+                                     "FP32 accumulate, split-K summed in thread-block clusters)"}
     else:
         gemm_s = sum(v for k, v in dur.items() if k.startswith("gemm_simt"))
         achieved = flops / gemm_s / 1e12
