@@ -322,7 +322,7 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   if (rc == GCNN_OK && side) {
     if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess)
       rc = set_error(GCNN_ECUDA, "cannot create the side stream");
-    for (int q = 0; q < 3 * c->L && rc == GCNN_OK; ++q) {
+    for (int q = 0; q < 3 * c->L + 1 && rc == GCNN_OK; ++q) {
       cudaEvent_t ev = nullptr;
       if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
         rc = set_error(GCNN_ECUDA, "cannot create events");

@@ -12,7 +12,8 @@ struct gcnn_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;  // private stream used only for graph capture
   cudaStream_t side = nullptr;        // BF16 backward: weight-gradient work off the critical path
-  std::vector<cudaEvent_t> side_ev;   // 3 per layer: fork, aggregate gradient done, side work done
+  std::vector<cudaEvent_t> side_ev;   // 3 per layer: fork, aggregate gradient done, side work done;
+                                      // then one for the head gradients
   int device = 0;
   int H = 0, L = 0, T = 0, Hh = 0;
   int64_t P = 0;       // parameter count

@@ -350,7 +350,16 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
     if (!c->fuse_head) GCNN_TRY(launch_head_graph(head_args(c, G, dpred), false, true, c->stream));
     HeadGradArgs ga{G, H, c->Hh, dims, c->pooled, c->z1, c->dz1, c->dpred, c->pred, c->bb.y,
                     head_ptr(c->grads, c), loss_accum};
-    GCNN_TRY(launch_head_grad(ga, c->stream));
+    // the head's parameter gradients and loss sums feed only the optimiser:
+    // on the side lane when the backward overlaps
+    cudaStream_t hs = c->stream;
+    if (bf16(c) && overlapped(c)) {
+      cudaEvent_t ev = c->side_ev[3 * c->L];
+      GCNN_CUDA_TRY(cudaEventRecord(ev, c->stream));
+      GCNN_CUDA_TRY(cudaStreamWaitEvent(c->side, ev, 0));
+      hs = c->side;
+    }
+    GCNN_TRY(launch_head_grad(ga, hs));
   }
   if (bf16(c)) {
     const bool ov = overlapped(c);

@@ -391,18 +391,22 @@ __device__ __forceinline__ void adam_one(float &p, float g, float &m, float &v, 
 // (s = 0, 1, 2 for the amplification, attenuation and identity blocks) and
 // Wx[n] = [W_U[n][0..H) | W_M[n][0..2H)].
 __device__ __forceinline__ long long packed_index(long long i, const AdamPack &k) {
-  const long long H = k.H;
-  const long long o0 = i - k.layers_begin;
-  if (o0 < 0 || o0 >= (long long)k.L * k.layer_size) return -1;
-  const long long l = o0 / k.layer_size, o = o0 % k.layer_size;
-  const long long base = l * 18 * H * H, wx = base + 15 * H * H;
-  if (o < 2 * H * H) return wx + (o / (2 * H)) * 3 * H + H + o % (2 * H);  // W_M
-  const long long u = o - (2 * H * H + H);
-  if (u < 0 || u >= 16 * H * H) return -1;  // biases
-  const long long r = u / H, c = u % H;
-  if (r < H) return wx + r * 3 * H + c;
-  const long long rr = r - H, blk = rr / (5 * H), n = rr % (5 * H);
-  return base + n * 3 * H + ((blk + 2) % 3) * H + c;
+  // 32-bit offsets: a layer's parameters and its packed operands hold < 2^31 elements
+  const long long o0l = i - k.layers_begin;
+  if (o0l < 0 || o0l >= (long long)k.L * k.layer_size) return -1;
+  const unsigned H = (unsigned)k.H, o0 = (unsigned)o0l, ls = (unsigned)k.layer_size;
+  const unsigned l = o0 / ls, o = o0 - l * ls;
+  const unsigned base = l * 18u * H * H, wx = base + 15u * H * H;
+  if (o < 2u * H * H) {  // W_M
+    const unsigned r = o / (2u * H);
+    return wx + r * 3u * H + H + (o - r * 2u * H);
+  }
+  if (o < 2u * H * H + H || o >= 18u * H * H + H) return -1;  // biases
+  const unsigned u = o - (2u * H * H + H);
+  const unsigned r = u / H, c = u - r * H;
+  if (r < H) return wx + r * 3u * H + c;
+  const unsigned rr = r - H, blk = rr / (5u * H), n = rr - blk * 5u * H;
+  return base + n * 3u * H + ((blk + 2u) % 3u) * H + c;
 }
 
 // AdamW over the flat FP32 parameters.  The step counter state[0] is read by
