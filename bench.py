@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -334,10 +335,14 @@ def kernel_profile(g, wl, n_steps, warmup, flush, loss_acc, precision):
     serial graph the difference of consecutive records is a kernel's duration
     as it runs in the step.  The timed step overlaps the BF16 weight-gradient
     work on a second stream; these durations come from the same step on one
-    stream (GCNN_FLAG_SERIAL, same kernels and launch shapes).  The last
-    kernel of a step (the optimiser) has no successor record and is left
-    out; the collation kernels run before the graph launch, so their
-    durations include that host gap."""
+    stream (GCNN_FLAG_SERIAL, same kernels and launch shapes).  The library
+    appends a one-thread marker kernel after the step while the timeline is
+    on, so the optimiser (the step's last kernel) is timed too, with the
+    graph's completion latency included; the collation kernels run before
+    the graph launch, so their durations include that host gap.  Phases
+    follow the launch order: collation, forward (embedding through the head
+    and loss), backward (head gradient through the embedding gradient) and
+    the optimiser."""
     import torch
     from collections import Counter, defaultdict
     ctx = make_ctx(g, wl, precision, g.FLAG_SERIAL)
@@ -347,17 +352,20 @@ def kernel_profile(g, wl, n_steps, warmup, flush, loss_acc, precision):
     ctx.timeline_enable(256 * n_steps)
     ctx.timeline_read()
     flops = agg_bytes = 0.0
-    dur, cnt = defaultdict(float), Counter()
+    dur, cnt, ph = defaultdict(float), Counter(), defaultdict(float)
     for k in range(n_steps):
         flush.zero_()
         b = batch_at(ctx, wl, warmup + k)
         ctx.train_step(b, LR, loss_acc)
         torch.cuda.synchronize()
         ids, t = ctx.timeline_read()
+        phase = "collate"
         for i in range(len(ids) - 1):
             name = g.KERNELS.get(int(ids[i]), str(int(ids[i])))
+            phase = {"embed": "forward", "head_grad": "backward", "adam": "optimizer"}.get(name, phase)
             dur[name] += (t[i + 1] - t[i]) * 1e-9
             cnt[name] += 1
+            ph[phase] += (t[i + 1] - t[i]) * 1e-9
         flops += gemm_flops(b.n_nodes)
         agg_bytes += L * agg_fwd_bytes(b.n_nodes, b.n_edges, precision)
     ctx.timeline_enable(0)
@@ -365,6 +373,7 @@ def kernel_profile(g, wl, n_steps, warmup, flush, loss_acc, precision):
     ctx.close()
     out = {"kernel_ms_per_step": {k: {"ms": 1e3 * v / n_steps, "launches": cnt[k] // n_steps}
                                   for k, v in sorted(dur.items(), key=lambda x: -x[1])},
+           "phase_us_per_step": {k: round(1e6 * v / n_steps, 1) for k, v in ph.items()},
            "kernel_timing": "library kernel timeline (device clock at each kernel's start after its dependency "
                             "wait) over the step on one stream; L2 flushed before each step"}
     peaks = measured_peaks()
@@ -382,10 +391,12 @@ def kernel_profile(g, wl, n_steps, warmup, flush, loss_acc, precision):
     else:
         gemm_s = sum(v for k, v in dur.items() if k.startswith("gemm_simt"))
         achieved = flops / gemm_s / 1e12
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
+        derived = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
+        peak = g.ffma_peak(8192)
         out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                            "frac": achieved / peak, "traffic": None,
-                           "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)",
+                           "peak_source": "measured live: gcnn_ffma_peak (independent FFMA chains on every SM); "
+                                          f"derived 152 SMs x 128 lanes x 2 FLOP x 2070 MHz = {derived:.1f}",
                            "kernel": "sgemm_kernel + splitk_reduce (all dense GEMMs of the step, FP32 FFMA)"}
     hbm, hbm_src = measured_hbm()
     a_gbs = agg_bytes / dur["agg_fwd"] / 1e9
@@ -423,7 +434,7 @@ def e2e_steps(g, ctx, wl, steps, loss_acc):
 
 
 # ------------------------------------------------------------------ large batches
-def aggregate_large(g, reps: int = 5):
+def aggregate_large(g, reps: int = 5, G: int = 60_000):
     """HBM throughput of the aggregation kernels on a batch far larger than L2.
 
     60,000 molecules (about 1.1M atoms, 2.4M directed edges) collated on the device,
@@ -431,7 +442,6 @@ def aggregate_large(g, reps: int = 5):
     node (7 GB), the backward reads 11H + 2 d H floats and writes 2H + d H per node.
     """
     import torch
-    G = 60_000
     gs = synth.molecules_lognormal(SEED_DATA + 100, G)
     tmp = tempfile.mkdtemp(prefix="gcnn_large_")
     path = os.path.join(tmp, "large.gcnn")
@@ -519,7 +529,10 @@ def recompute_study(g, precision: str, steps: int = 20):
 # ------------------------------------------------------------------ precision study
 def precision_study(g, epochs: int, lr: float):
     """FP32 and BF16 paths trained from the same initial parameters on the same epoch
-    orders of the 200k-graph set; training MSE per epoch and MAE on the held-out 20k."""
+    orders of the 200k-graph set, the learning rate decayed over the run by a half
+    cosine from `lr` to zero (so that the last epochs settle instead of moving with
+    the step size); training MSE per epoch and MAE on the held-out 20k, with the
+    mean over the last three epochs as the comparison figure."""
     import torch
     wl = Workload(g, 0, 1)
     held = np.arange(N_TRAIN, N_TRAIN + N_HELDOUT, dtype=np.int64)
@@ -527,7 +540,10 @@ def precision_study(g, epochs: int, lr: float):
     Nc = max(wl.Nc, (max(s[0] for s in hs) + 255) // 256 * 256)
     Ec = max(wl.Ec, (max(s[1] for s in hs) + 511) // 512 * 512)
     y_held = wl.y[held].astype(np.float64)
-    out = {"epochs": epochs, "train_graphs": N_TRAIN, "heldout_graphs": N_HELDOUT, "batch": BATCH, "lr": lr}
+    out = {"epochs": epochs, "train_graphs": N_TRAIN, "heldout_graphs": N_HELDOUT, "batch": BATCH, "lr": lr,
+           "lr_schedule": "half cosine from lr to 0 over all steps"}
+    steps_per_epoch = (N_TRAIN + BATCH - 1) // BATCH
+    total = epochs * steps_per_epoch
     for prec in ("fp32", "bf16"):
         c = g.Context(g.make_config(H, L, BATCH, Nc, Ec, delta=wl.delta,
                                     precision=g.PREC_BF16 if prec == "bf16" else g.PREC_FP32))
@@ -539,8 +555,9 @@ def precision_study(g, epochs: int, lr: float):
             order = epoch_order(ep)
             c.set_order(wl.st, order)
             acc = torch.zeros(3, dtype=torch.float64, device="cuda")
-            for i in range(0, N_TRAIN, BATCH):
-                c.train_step(c.collate_range(wl.st, i, min(BATCH, N_TRAIN - i)), lr, acc)
+            for j, i in enumerate(range(0, N_TRAIN, BATCH)):
+                lr_k = 0.5 * lr * (1.0 + math.cos(math.pi * (ep * steps_per_epoch + j) / total))
+                c.train_step(c.collate_range(wl.st, i, min(BATCH, N_TRAIN - i)), lr_k, acc)
             a = acc.cpu().numpy()
             for i in range(0, N_HELDOUT, BATCH):
                 b = c.collate(wl.st, held[i:i + BATCH])
@@ -557,6 +574,8 @@ def precision_study(g, epochs: int, lr: float):
     out["final_heldout_mae_rel_diff"] = (h16[-1]["heldout_mae"] - h32[-1]["heldout_mae"]) / h32[-1]["heldout_mae"]
     b32, b16 = min(h["heldout_mae"] for h in h32), min(h["heldout_mae"] for h in h16)
     out["best_heldout_mae_rel_diff"] = (b16 - b32) / b32
+    m32, m16 = (float(np.mean([h["heldout_mae"] for h in hh[-3:]])) for hh in (h32, h16))
+    out["last3_heldout_mae"] = {"fp32": m32, "bf16": m16, "rel_diff": (m16 - m32) / m32}
     return out
 
 
@@ -739,6 +758,7 @@ def run_ours(args):
             prof = kernel_profile(g, wl, min(args.steps, 50), args.warmup, flush, loss_acc, args.compare)
             cmp["roofline"] = prof["roofline"]
             cmp["kernel_ms_per_step"] = prof["kernel_ms_per_step"]
+            cmp["phase_us_per_step"] = prof["phase_us_per_step"]
         except Exception as e:  # noqa: BLE001
             cmp["roofline"] = {"error": repr(e)}
         c2.check()
@@ -774,8 +794,12 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="seconds of Poisson load per arrival rate for the serving measurement (0: skip)")
     ap.add_argument("--serve-rates", default="200,1000,2000", help="arrival rates, requests/s")
-    ap.add_argument("--study", choices=["none", "precision"], default="none",
-                    help="precision: train FP32 and BF16 for --epochs and compare held-out MAE (no bench line)")
+    ap.add_argument("--study", choices=["none", "precision", "aggregate"], default="none",
+                    help="precision: train FP32 and BF16 for --epochs and compare held-out MAE; aggregate: the "
+                         "aggregation operators alone on --molecules molecules, --reps timed launches each "
+                         "(no bench line)")
+    ap.add_argument("--molecules", type=int, default=60_000, help="batch of the aggregation study")
+    ap.add_argument("--reps", type=int, default=5, help="timed launches per operator in the aggregation study")
     ap.add_argument("--epochs", type=int, default=10)
     ap.add_argument("--lr", type=float, default=1e-4, help="learning rate of the precision study")
     ap.add_argument("--no-studies", dest="studies", action="store_false",
@@ -790,6 +814,12 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         import paper_2207_11333_gb300 as g
         print(json.dumps({"study": "precision", **precision_study(g, args.epochs, args.lr)}), flush=True)
+        return 0
+    if args.study == "aggregate":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        import paper_2207_11333_gb300 as g
+        print(json.dumps({"study": "aggregate", **aggregate_large(g, args.reps, args.molecules)}), flush=True)
         return 0
     return run_ours(args)
 

@@ -289,10 +289,18 @@ enum {
   GCNN_K_ADAM = 19,
   GCNN_K_CAST_BF16 = 20,
   GCNN_K_PACK_LAYER = 21,
-  GCNN_NKERNEL = 22
+  GCNN_K_STEP_END = 22,         /* marker after a train step (timeline on only) */
+  GCNN_NKERNEL = 23
 };
 int gcnn_timeline_enable(gcnn_ctx *ctx, int32_t capacity);
 int gcnn_timeline_read(gcnn_ctx *ctx, int32_t *ids, int64_t *t_ns, int32_t max, int32_t *n);
+
+/* FP32 FFMA throughput of the calling thread's device, in TFLOP/s: a kernel
+ * of independent fused multiply-add chains over every SM (full occupancy),
+ * timed with CUDA events over `iters` loop trips per thread after a warm-up
+ * launch; synchronous.  The roofline of the FP32 (CUDA-core) GEMM path.  Not a
+ * paper operation: measurement support.  GCNN_EINVAL for iters < 1. */
+int gcnn_ffma_peak(int32_t iters, double *tflops);
 
 /* ------------------------------------------------------------------ serving
  * Inference server for the screening use of the trained model (Sec. 1:

@@ -27,7 +27,7 @@ NPHASE = len(PHASES)
 KERNELS = {1: "collate_scan", 2: "collate_graph", 3: "embed", 4: "embed_bwd", 5: "agg_fwd", 6: "agg_bwd_edge",
            7: "agg_bwd_gather", 8: "gemm_tc_partial", 9: "gemm_tc_c", 10: "gemm_tc_d3", 11: "gemm_tc_reduce",
            12: "gemm_simt", 13: "gemm_simt_reduce", 14: "pool_fwd", 15: "pool_bwd", 16: "head_graph",
-           17: "head_grad", 18: "colsum", 19: "adam", 20: "cast_bf16", 21: "pack_layer"}
+           17: "head_grad", 18: "colsum", 19: "adam", 20: "cast_bf16", 21: "pack_layer", 22: "step_end"}
 
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EFORMAT", -5: "EDEVICE", -6: "ETIMEDOUT",
            -7: "EAGAIN", -8: "ESTATE"}
@@ -105,6 +105,7 @@ def _load() -> ctypes.CDLL:
         "gcnn_profile_read": (i32, [vp, vp, vp]),
         "gcnn_step_kernel_count": (i32, [vp, P(i32)]),
         "gcnn_timeline_enable": (i32, [vp, i32]),
+        "gcnn_ffma_peak": (i32, [i32, P(f64)]),
         "gcnn_timeline_read": (i32, [vp, vp, vp, i32, P(i32)]),
         "gcnn_memory": (i32, [vp, P(i64)]),
         "gcnn_serve_create": (i32, [vp, P(ServeConfig), P(vp)]),
@@ -212,6 +213,13 @@ class Store:
 
 
 # ---------------------------------------------------------------- context
+
+def ffma_peak(iters: int = 4096) -> float:
+    """FP32 FFMA throughput of the current device, TFLOP/s (measurement support)."""
+    t = ctypes.c_double()
+    _check(lib.gcnn_ffma_peak(int(iters), ctypes.byref(t)))
+    return t.value
+
 
 def make_config(hidden: int, layers: int, max_graphs: int, max_nodes: int, max_edges: int, **kw) -> Config:
     c = Config()

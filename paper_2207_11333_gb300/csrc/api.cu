@@ -585,6 +585,12 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
     it = c->graphs.emplace(key, gcnn_ctx::Graph{exec, kernels, std::move(ev)}).first;
   }
   GCNN_CUDA_TRY(cudaGraphLaunch(it->second.exec, c->stream));
+  bool tl_on;
+  {
+    std::lock_guard<std::mutex> lock(g_tl_mu);
+    tl_on = g_tl.buf != nullptr;
+  }
+  if (tl_on) GCNN_TRY(launch_step_end(c->stream));
   if (!it->second.ev.empty()) {
     GCNN_CUDA_TRY(cudaStreamSynchronize(c->stream));
     for (auto &pe : it->second.ev) {
@@ -678,6 +684,32 @@ int gcnn_timeline_enable(gcnn_ctx *c, int32_t capacity) {
   }
   g_tl = h;
   return GCNN_OK;
+}
+
+int gcnn_ffma_peak(int32_t iters, double *tflops) {
+  if (iters < 1 || !tflops) return set_error(GCNN_EINVAL, "ffma_peak: iters must be >= 1");
+  float *out = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = GCNN_OK;
+  double flop = 0.0;
+  if (cudaMalloc(&out, 4096 * sizeof(float)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    rc = set_error(GCNN_ECUDA, "ffma_peak: setup failed");
+  if (rc == GCNN_OK) rc = launch_ffma_peak(iters, out, s, &flop);  // warm-up
+  if (rc == GCNN_OK && cudaEventRecord(e0, s) != cudaSuccess) rc = set_error(GCNN_ECUDA, "ffma_peak: event");
+  if (rc == GCNN_OK) rc = launch_ffma_peak(iters, out, s, &flop);
+  if (rc == GCNN_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+    rc = set_error(GCNN_ECUDA, "ffma_peak: timing failed");
+  float ms = 0.f;
+  if (rc == GCNN_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = set_error(GCNN_ECUDA, "ffma_peak: timing");
+  if (rc == GCNN_OK) *tflops = ms > 0.f ? flop / (ms * 1e-3) / 1e12 : 0.0;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  if (out) cudaFree(out);
+  return rc;
 }
 
 int gcnn_timeline_read(gcnn_ctx *c, int32_t *ids, int64_t *t_ns, int32_t max, int32_t *n) {

@@ -207,6 +207,12 @@ int launch_pack_layer(int H, const float *msg_w, const float *upd_w, uint16_t *W
 int launch_colsum2(int n_cap, int cols0, int cols1, DevDims dims, const float *a0, int ld0, const float *mask,
                    int ldm, const float *a1, int ld1, float *out0, float *out1, cudaStream_t s);
 
+// Timeline marker after a train step: records the end of the step's last kernel.
+int launch_step_end(cudaStream_t s);
+
+// FP32 FFMA throughput probe over every SM; *flop receives the launch's FLOP.
+int launch_ffma_peak(int iters, float *out, cudaStream_t s, double *flop);
+
 // Point the kernels of each translation unit at the timeline buffer (or null).
 int timeline_attach_collate(void *tl);
 int timeline_attach_aggregate(void *tl);

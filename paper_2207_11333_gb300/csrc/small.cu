@@ -598,6 +598,44 @@ int launch_adam(int64_t n, float *param, const float *grad, float *m, float *v, 
   return GCNN_OK;
 }
 
+namespace {
+// FP32 FFMA throughput probe: 8 independent fused multiply-add chains per
+// thread (x = x * b + c), unrolled 16 deep; the sum is stored only under a
+// never-true condition so that the chains stay live.
+__global__ void __launch_bounds__(256) ffma_peak_kernel(int iters, float b, float c, float *out) {
+  float x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = 1e-3f * (float)threadIdx.x + (float)k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = fmaf(x[k], b, c);
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sum += x[k];
+  if (sum == -1.f) out[blockIdx.x] = sum;
+}
+}  // namespace
+
+namespace {
+__global__ void step_end_kernel() { pdl_entry(GCNN_K_STEP_END); }
+}  // namespace
+
+int launch_step_end(cudaStream_t s) {
+  GCNN_TRY(launch(step_end_kernel, 1, 32, 0, s));
+  return GCNN_OK;
+}
+
+int launch_ffma_peak(int iters, float *out, cudaStream_t s, double *flop) {
+  const int blocks = num_sms() * 8;
+  ffma_peak_kernel<<<blocks, 256, 0, s>>>(iters, 1.0000001f, 1e-7f, out);
+  GCNN_LAUNCH_CHECK();
+  *flop = 2.0 * 8 * 16 * (double)iters * blocks * 256;
+  return GCNN_OK;
+}
+
 GCNN_TIMELINE_ATTACH(small)
 
 }  // namespace gcnn

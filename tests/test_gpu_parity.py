@@ -128,8 +128,9 @@ def test_profiled_step_matches_and_times_phases(tmp_path):
 def test_kernel_timeline_of_a_train_step(tmp_path):
     """The kernel timeline records every launch of a collated train step in
     order (FP32 path here: collation, embedding, per-layer GEMMs and
-    aggregations, head, backward, embedding gradient, optimiser), with
-    non-decreasing device times, and nothing once disabled."""
+    aggregations, head, backward, embedding gradient, optimiser, then the
+    step-end marker), with non-decreasing device times, and nothing once
+    disabled."""
     import paper_2207_11333_gb300 as g
     d, ctx, st, b, ob, student = _setup(tmp_path)
     acc = torch.zeros(3, dtype=torch.float64, device="cuda")
@@ -141,7 +142,7 @@ def test_kernel_timeline_of_a_train_step(tmp_path):
         ids, t = ctx.timeline_read()
         names = [g.KERNELS[int(i)] for i in ids]
         assert names[:3] == ["collate_scan", "collate_graph", "embed"]
-        assert names[-1] == "adam" and names[-2] == "embed_bwd"
+        assert names[-3:] == ["embed_bwd", "adam", "step_end"]
         assert names.count("agg_fwd") == d.L and names.count("agg_bwd_edge") == d.L
         assert names.count("head_graph") == 1 and names.count("head_grad") == 1
         assert names.count("gemm_simt") == 6 * d.L
@@ -184,3 +185,14 @@ def test_errors_are_reported(tmp_path):
         g.Context(g.make_config(30, 2, 4, 100, 100, delta=1.0))       # hidden not a multiple of 8
     with pytest.raises(g.GcnnError, match="EINVAL"):
         ctx.set_params(np.zeros(5, np.float32))
+
+
+def test_ffma_peak_is_plausible():
+    """The FP32 FFMA probe (the roofline of the FP32 GEMM path) reports a rate
+    between a quarter of and just above 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz
+    (80.5 TFLOP/s); iters < 1 is rejected."""
+    import paper_2207_11333_gb300 as g
+    t = g.ffma_peak(2048)
+    assert 20.0 < t < 85.0, t
+    with pytest.raises(g.GcnnError, match="EINVAL"):
+        g.ffma_peak(0)
