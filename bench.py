@@ -438,8 +438,13 @@ def aggregate_large(g, reps: int = 5, G: int = 60_000):
     """HBM throughput of the aggregation kernels on a batch far larger than L2.
 
     60,000 molecules (about 1.1M atoms, 2.4M directed edges) collated on the device,
-    random P|Q rows at H = 200: forward reads P and Q and writes 5H aggregates per
-    node (7 GB), the backward reads 11H + 2 d H floats and writes 2H + d H per node.
+    random P|Q rows at H = 200.  Compulsory bytes: the forward reads P and Q and
+    writes 5H aggregates per node; the backward reads P|Q, the four stored
+    statistics and the 5H incoming gradient and writes dP|dQ (13H floats per node)
+    plus the CSR indices.  "backward" is the whole-graph entry point (fused over
+    chunks of graphs, per-edge gradients in shared memory); "backward_pair" is the
+    edge + gather pair, whose per-edge buffer (written and read back, 2 E H floats)
+    is counted on top for it.
     """
     import torch
     gs = synth.molecules_lognormal(SEED_DATA + 100, G)
@@ -450,19 +455,23 @@ def aggregate_large(g, reps: int = 5, G: int = 60_000):
     N, E = gs.n_nodes, gs.n_edges
     c = g.Context(g.make_config(8, 1, G, N, E, delta=st.delta()))
     b = c.collate(st, np.arange(G))
-    rp, col, rev = b.tensor("row_ptr"), b.tensor("col"), b.tensor("rev")
+    rp, col, rev, no = b.tensor("row_ptr"), b.tensor("col"), b.tensor("rev"), b.tensor("node_off")
     Hl = H
     gen = torch.Generator(device="cuda").manual_seed(5)
     PQ = torch.randn(N, 2 * Hl, device="cuda", generator=gen)
     agg = g.aggregate_fwd(PQ, rp, col)
     dagg = torch.randn(N, 5 * Hl, device="cuda", generator=gen)
-    dPQ = g.aggregate_bwd(PQ, agg, dagg, rp, col, rev)
+    dPQ = g.aggregate_bwd(PQ, agg, dagg, rp, col, rev, node_off=no)
+    same = bool(torch.equal(dPQ, g.aggregate_bwd(PQ, agg, dagg, rp, col, rev)))
     torch.cuda.synchronize()
     fwd_bytes = N * (2 * Hl + 5 * Hl) * 4.0 + (N + 1 + E) * 4.0
-    bwd_bytes = N * (2 * Hl + 4 * Hl + 5 * Hl + 2 * Hl) * 4.0 + 2.0 * E * Hl * 4 + (N + 1 + 2 * E) * 4.0
+    bwd_bytes = N * (2 * Hl + 4 * Hl + 5 * Hl + 2 * Hl) * 4.0 + (N + 1 + 2 * E + G + 1) * 4.0
+    pair_bytes = bwd_bytes + 2.0 * E * Hl * 4
     out = {}
     for name, fn, nbytes in (("forward", lambda: g.aggregate_fwd(PQ, rp, col), fwd_bytes),
-                             ("backward", lambda: g.aggregate_bwd(PQ, agg, dagg, rp, col, rev), bwd_bytes)):
+                             ("backward", lambda: g.aggregate_bwd(PQ, agg, dagg, rp, col, rev, node_off=no),
+                              bwd_bytes),
+                             ("backward_pair", lambda: g.aggregate_bwd(PQ, agg, dagg, rp, col, rev), pair_bytes)):
         fn()
         ts = []
         for _ in range(reps):
@@ -478,7 +487,9 @@ def aggregate_large(g, reps: int = 5, G: int = 60_000):
     for v in out.values():
         v["frac_of_hbm"] = v["GB_s"] / hbm
     out.update({"nodes": N, "edges": E, "hidden": Hl, "peak_GB_s": hbm, "peak_source": src,
-                "note": "gcnn_op_aggregate_fwd / _bwd through the C ABI; best of 5 launches, CUDA events"})
+                "backward_equals_pair_bitwise": same,
+                "note": "gcnn_op_aggregate_fwd / _bwd_graphs / _bwd through the C ABI; best of the timed launches, "
+                        "CUDA events; the scratch of the backward is allocated inside the timed call"})
     del PQ, agg, dagg, dPQ
     c.close()
     return out

@@ -290,7 +290,9 @@ enum {
   GCNN_K_CAST_BF16 = 20,
   GCNN_K_PACK_LAYER = 21,
   GCNN_K_STEP_END = 22,         /* marker after a train step (timeline on only) */
-  GCNN_NKERNEL = 23
+  GCNN_K_AGG_BWD_FUSED = 23,    /* aggregation backward over whole graphs      */
+  GCNN_K_AGG_BWD_CHUNKS = 24,   /* its partition of the batch into chunks      */
+  GCNN_NKERNEL = 25
 };
 int gcnn_timeline_enable(gcnn_ctx *ctx, int32_t capacity);
 int gcnn_timeline_read(gcnn_ctx *ctx, int32_t *ids, int64_t *t_ns, int32_t max, int32_t *n);
@@ -376,6 +378,22 @@ int gcnn_op_aggregate_bwd(int32_t n_nodes, int32_t n_edges, int32_t hidden, cons
                           const int32_t *col, const int32_t *rev, const float *PQ,
                           const float *agg, const float *dagg, float *dPQ, float *scratch,
                           float std_eps, void *stream);
+/* Same result as gcnn_op_aggregate_bwd (bitwise) for a batch of n_graphs whole
+ * graphs: node_off (device, n_graphs + 1 int32) gives each graph's first node,
+ * and no edge may leave its graph (as after gcnn_collate).  Batches of at
+ * least 2 x (SM count) x 128 edges run one fused kernel: the batch is cut into
+ * chunks of about 128 edges of whole graphs, and each block keeps its chunk's
+ * per-edge gradients in shared memory, so they never travel to device memory
+ * (graphs too large for that use scratch).  Smaller batches run the kernel
+ * pair of gcnn_op_aggregate_bwd.  scratch (device) holds
+ * n_edges * hidden + n_edges + 2 floats.  The operators carry no device
+ * error flag: an edge that leaves its graph, or an index out of range, is
+ * skipped (its gradient is lost) rather than read or written out of bounds.
+ * (Sec. 3.1 message passing; PNA aggregators; backward.) */
+int gcnn_op_aggregate_bwd_graphs(int32_t n_graphs, int32_t n_nodes, int32_t n_edges, int32_t hidden,
+                                 const int32_t *node_off, const int32_t *row_ptr, const int32_t *col,
+                                 const int32_t *rev, const float *PQ, const float *agg, const float *dagg,
+                                 float *dPQ, float *scratch, float std_eps, void *stream);
 /* Same result as gcnn_op_aggregate_bwd, for callers that cannot allocate
  * device memory where they need this gradient (a host framework whose caching
  * allocator already holds the device's memory, or a latency-critical loop in

@@ -27,7 +27,8 @@ NPHASE = len(PHASES)
 KERNELS = {1: "collate_scan", 2: "collate_graph", 3: "embed", 4: "embed_bwd", 5: "agg_fwd", 6: "agg_bwd_edge",
            7: "agg_bwd_gather", 8: "gemm_tc_partial", 9: "gemm_tc_c", 10: "gemm_tc_d3", 11: "gemm_tc_reduce",
            12: "gemm_simt", 13: "gemm_simt_reduce", 14: "pool_fwd", 15: "pool_bwd", 16: "head_graph",
-           17: "head_grad", 18: "colsum", 19: "adam", 20: "cast_bf16", 21: "pack_layer", 22: "step_end"}
+           17: "head_grad", 18: "colsum", 19: "adam", 20: "cast_bf16", 21: "pack_layer", 22: "step_end",
+           23: "agg_bwd_fused", 24: "agg_bwd_chunks"}
 
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EFORMAT", -5: "EDEVICE", -6: "ETIMEDOUT",
            -7: "EAGAIN", -8: "ESTATE"}
@@ -116,6 +117,7 @@ def _load() -> ctypes.CDLL:
         "gcnn_serve_destroy": (i32, [vp]),
         "gcnn_op_aggregate_fwd": (i32, [i32, i32, vp, vp, vp, vp, f32, vp]),
         "gcnn_op_aggregate_bwd": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, f32, vp]),
+        "gcnn_op_aggregate_bwd_graphs": (i32, [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, f32, vp]),
         "gcnn_op_aggregate_bwd_noalloc": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, f32, vp]),
         "gcnn_op_pool_fwd": (i32, [i32, i32, vp, vp, vp, vp]),
         "gcnn_op_pool_bwd": (i32, [i32, i32, i32, vp, vp, vp, vp, vp]),
@@ -417,18 +419,24 @@ def aggregate_fwd(PQ, row_ptr, col, std_eps: float = 1e-5, stream=None):
     return agg
 
 
-def aggregate_bwd(PQ, agg, dagg, row_ptr, col, rev, std_eps: float = 1e-5, stream=None):
-    """dPQ (N x 2H) from dagg (gcnn_op_aggregate_bwd)."""
+def aggregate_bwd(PQ, agg, dagg, row_ptr, col, rev, std_eps: float = 1e-5, stream=None, node_off=None):
+    """dPQ (N x 2H) from dagg: gcnn_op_aggregate_bwd, or gcnn_op_aggregate_bwd_graphs
+    when the graph offsets node_off (G + 1 int32) are given."""
     import torch
     N, H2 = PQ.shape
     H = H2 // 2
     E = col.numel()
     dPQ = torch.empty_like(PQ)
-    scratch = torch.empty(max(E, 1) * H, device=PQ.device, dtype=torch.float32)
-    _check(lib.gcnn_op_aggregate_bwd(N, E, H, _dev_ptr(row_ptr, torch.int32), _dev_ptr(col, torch.int32),
-                                     _dev_ptr(rev, torch.int32), _dev_ptr(PQ, torch.float32),
-                                     _dev_ptr(agg, torch.float32), _dev_ptr(dagg.contiguous(), torch.float32),
-                                     _dev_ptr(dPQ), _dev_ptr(scratch), std_eps, _stream(stream)))
+    ptrs = (_dev_ptr(row_ptr, torch.int32), _dev_ptr(col, torch.int32), _dev_ptr(rev, torch.int32),
+            _dev_ptr(PQ, torch.float32), _dev_ptr(agg, torch.float32), _dev_ptr(dagg.contiguous(), torch.float32),
+            _dev_ptr(dPQ))
+    if node_off is None:
+        scratch = torch.empty(max(E, 1) * H, device=PQ.device, dtype=torch.float32)
+        _check(lib.gcnn_op_aggregate_bwd(N, E, H, *ptrs, _dev_ptr(scratch), std_eps, _stream(stream)))
+    else:
+        scratch = torch.empty(E * H + E + 2, device=PQ.device, dtype=torch.float32)
+        _check(lib.gcnn_op_aggregate_bwd_graphs(node_off.numel() - 1, N, E, H, _dev_ptr(node_off, torch.int32),
+                                                *ptrs, _dev_ptr(scratch), std_eps, _stream(stream)))
     return dPQ
 
 

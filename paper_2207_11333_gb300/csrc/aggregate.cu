@@ -7,14 +7,18 @@
 // gathers Q rows over each destination's CSR row and reduces them on the fly.
 //
 // Forward:  one thread per (node, 4 channels); FP32; the row's messages stay
-//           in registers (first 4 edges) for the two-pass variance.
+//           in registers (first 4 edges) for the two-pass variance; all of a
+//           row's loads are issued before its arithmetic, so a thread has its
+//           P row and up to four Q rows in flight at once.
 // Backward: kernel 1, one thread per (node i, 4 channels), recomputes m_ij,
 //           routes dagg to every edge (sum: 1, mean: 1/d, min/max: shared
 //           equally among exact ties, std: (m - mean) / (d std)), writes
 //           dP_i and stores each dm_ij at the slot of the reverse edge;
 //           kernel 2, one thread per (node j, 4 channels), sums its own row of
 //           that buffer into dQ_j.  No atomics: the result is deterministic.
+#include <algorithm>
 #include <cfloat>
+#include <mutex>
 
 #include "kernels.cuh"
 
@@ -52,11 +56,31 @@ __device__ __forceinline__ float4 message(const float *__restrict__ PQ, int j, i
   return j >= 0 ? add4(P, ld4(PQ + (size_t)j * 2 * H + H + c)) : P;
 }
 
+// Messages of the first kCache edges of node i's row from their sources j[]:
+// every Q row is loaded unconditionally (row i stands in for a source out of
+// range, whose message is then P alone), so the loads are all in flight at
+// once; returns whether a source was out of range.
+__device__ __forceinline__ bool gather_first(const float *__restrict__ PQ, const int (&j)[kCache], int i, int N, int H,
+                                             int c, float4 P, float4 (&mc)[kCache]) {
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < kCache; ++k) {
+    const bool ok = j[k] >= 0 && j[k] < N;
+    bad |= !ok;
+    const float4 q = ld4(PQ + (size_t)(ok ? j[k] : i) * 2 * H + H + c);
+    mc[k] = ok ? add4(P, q) : P;
+  }
+  return bad;
+}
+
 __device__ __forceinline__ void acc_sq(float4 &v, float4 m, float4 mean) {
   const float tx = m.x - mean.x, ty = m.y - mean.y, tz = m.z - mean.z, tw = m.w - mean.w;
   v.x += tx * tx; v.y += ty * ty; v.z += tz * tz; v.w += tw * tw;
 }
 
+// F32 / B16: whether the FP32 aggregates / the BF16 scaled operand are
+// written (one instantiation per output set keeps the other's code out)
+template <bool F32, bool B16>
 __global__ void __launch_bounds__(kThreads, 4)
 aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row_ptr,
                      const int *__restrict__ col, const float *__restrict__ PQ,
@@ -70,34 +94,37 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
   const int i = (int)(t / H4), c = (int)(t % H4) * 4;
   const int r0 = row_ptr[i], r1 = row_ptr[i + 1];
   const int d = r1 - r0;
-  float *out = agg ? agg + (size_t)i * kAgg * H + c : nullptr;
+  float *out = F32 ? agg + (size_t)i * kAgg * H + c : nullptr;
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
   if (d <= 0 || r0 < 0) {
     if (d < 0 || r0 < 0) flag(err, kErrIndex);
-    if (out)
+    if (F32)
 #pragma unroll
       for (int a = 0; a < kAgg; ++a) st4(out + a * H, z);
-    if (S16)
+    if (B16)
       for (int a = 0; a < kScalers * kAgg; ++a) st_bf16x4(S16 + (size_t)i * ld16 + a * H + c, 0.f, 0.f, 0.f, 0.f);
     return;
   }
+  // every load of the row is issued before the arithmetic: the first kCache
+  // sources (indices clamped into the row, so short rows repeat their last
+  // edge and use only the first d), then P and the gathered Q rows
+  int j[kCache];
+#pragma unroll
+  for (int k = 0; k < kCache; ++k) j[k] = col[min(r0 + k, r1 - 1)];
   const float4 P = ld4(PQ + (size_t)i * 2 * H + c);
+  float4 mc[kCache];
+  if (gather_first(PQ, j, i, N, H, c, P, mc)) flag(err, kErrIndex);
   float4 s = z;
   float4 mn = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX);
   float4 mx = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX);
-  float4 mc[kCache];
   auto take = [&](float4 m) {
     s = add4(s, m);
     mn.x = fminf(mn.x, m.x); mn.y = fminf(mn.y, m.y); mn.z = fminf(mn.z, m.z); mn.w = fminf(mn.w, m.w);
     mx.x = fmaxf(mx.x, m.x); mx.y = fmaxf(mx.y, m.y); mx.z = fmaxf(mx.z, m.z); mx.w = fmaxf(mx.w, m.w);
   };
 #pragma unroll
-  for (int k = 0; k < kCache; ++k) {
-    if (k < d) {
-      mc[k] = message(PQ, source(col, r0 + k, N, err), H, c, P);
-      take(mc[k]);
-    }
-  }
+  for (int k = 0; k < kCache; ++k)
+    if (k < d) take(mc[k]);
   for (int e = r0 + kCache; e < r1; ++e) take(message(PQ, source(col, e, N, err), H, c, P));
   const float df = (float)d;
   const float4 mean = make_float4(s.x / df, s.y / df, s.z / df, s.w / df);
@@ -111,14 +138,14 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
   sd.y = sqrtf(fmaxf(v.y / df, 0.f) + eps);
   sd.z = sqrtf(fmaxf(v.z / df, 0.f) + eps);
   sd.w = sqrtf(fmaxf(v.w / df, 0.f) + eps);
-  if (out) {
+  if (F32) {
     st4(out + 0 * H, s);
     st4(out + 1 * H, mean);
     st4(out + 2 * H, mn);
     st4(out + 3 * H, mx);
     st4(out + 4 * H, sd);
   }
-  if (S16) {  // scaler-major: identity, amplification, attenuation
+  if (B16) {  // scaler-major: identity, amplification, attenuation
     const float4 vv[kAgg] = {s, mean, mn, mx, sd};
     const float sc[kScalers] = {1.f, amp[i], att[i]};
     uint16_t *o = S16 + (size_t)i * ld16 + c;
@@ -141,40 +168,49 @@ __device__ __forceinline__ float route(float m, float base, float mn, float cmin
 
 constexpr int kEdgeThreads = 128;  // five blocks of 128 per SM at this kernel's register count
 
-__global__ void __launch_bounds__(kEdgeThreads)
-aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *__restrict__ row_ptr,
-                          const int *__restrict__ col, const int *__restrict__ rev,
-                          const float *__restrict__ PQ, const float *__restrict__ agg,
-                          const float *__restrict__ dagg, float *__restrict__ dPQ,
-                          float *__restrict__ dm, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16, float eps) {
-  pdl_entry(GCNN_K_AGG_BWD_EDGE);
-  const int H4 = H >> 2;
-  const int N = min(n_cap, dims.nodes(n_cap));
-  const int E = min(e_cap, dims.edges(e_cap));
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)N * H4) return;
-  const int i = (int)(t / H4), c = (int)(t % H4) * 4;
+// Backward of one (node i, 4 channels at c): recomputes the row's messages,
+// takes the forward's statistics (stored in agg, or recomputed in the
+// forward's order when agg is null), routes dagg to every edge of the row
+// and hands each edge's gradient to to_slot(reverse slot, g); returns dP_i.
+// STATS: 1 = statistics stored in agg, 0 = recomputed, -1 = decided at run
+// time by agg != null (one code path for both, fewer registers)
+template <int STATS, class ToSlot>
+__device__ __forceinline__ float4 node_backward(int i, int c, int H, int N, int E, const int *__restrict__ row_ptr,
+                                                const int *__restrict__ col, const int *__restrict__ rev,
+                                                const float *__restrict__ PQ, const float *__restrict__ agg,
+                                                const float *__restrict__ dagg, float eps, unsigned *err,
+                                                ToSlot to_slot) {
+  const bool STORED = STATS < 0 ? agg != nullptr : STATS == 1;
   const int r0 = row_ptr[i], r1 = row_ptr[i + 1];
   const int d = r1 - r0;
   float4 dP = make_float4(0.f, 0.f, 0.f, 0.f);
   if (d <= 0 || r0 < 0 || r1 > E) {
     if (d < 0 || r0 < 0 || r1 > E) flag(err, kErrIndex);
-    st4(dPQ + (size_t)i * 2 * H + c, dP);
-    if (dPQ16) st_bf16x4(dPQ16 + (size_t)i * ld16 + c, 0.f, 0.f, 0.f, 0.f);
-    return;
+    return dP;
   }
   const float df = (float)d;
-  const float4 P = ld4(PQ + (size_t)i * 2 * H + c);
-  float4 mc[kCache];
+  // all loads of the row first (as in the forward): sources and reverse slots
+  // of the first kCache edges (clamped into the row), P, the stored statistics,
+  // the incoming gradient and the gathered Q rows
+  int j[kCache], re[kCache];
 #pragma unroll
-  for (int k = 0; k < kCache; ++k)
-    if (k < d) mc[k] = message(PQ, source(col, r0 + k, N, err), H, c, P);
-  // the forward's statistics: stored, or recomputed in the forward's order
+  for (int k = 0; k < kCache; ++k) {
+    j[k] = col[min(r0 + k, r1 - 1)];
+    re[k] = rev[min(r0 + k, r1 - 1)];
+  }
+  const float4 P = ld4(PQ + (size_t)i * 2 * H + c);
   float4 mean, mn, mx, sd;
-  if (agg) {
+  if (STORED) {
     const float *a = agg + (size_t)i * kAgg * H + c;
     mean = ld4(a + 1 * H); mn = ld4(a + 2 * H); mx = ld4(a + 3 * H); sd = ld4(a + 4 * H);
-  } else {
+  }
+  const float *da = dagg + (size_t)i * kAgg * H + c;
+  const float4 dsum = ld4(da + 0 * H), dmean = ld4(da + 1 * H), dmin = ld4(da + 2 * H);
+  const float4 dmax = ld4(da + 3 * H), dstd = ld4(da + 4 * H);
+  float4 mc[kCache];
+  if (gather_first(PQ, j, i, N, H, c, P, mc)) flag(err, kErrIndex);
+  // the forward's statistics: stored, or recomputed in the forward's order
+  if (!STORED) {
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
     mn = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX);
     mx = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX);
@@ -200,7 +236,7 @@ aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *
     if (k < d) count(mc[k]);
   for (int e = r0 + kCache; e < r1; ++e) count(message(PQ, source(col, e, N, err), H, c, P));
   var.x /= df; var.y /= df; var.z /= df; var.w /= df;
-  if (!agg) {
+  if (!STORED) {
     sd.x = sqrtf(fmaxf(var.x, 0.f) + eps);
     sd.y = sqrtf(fmaxf(var.y, 0.f) + eps);
     sd.z = sqrtf(fmaxf(var.z, 0.f) + eps);
@@ -209,32 +245,146 @@ aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *
   // per-node routing coefficients: every edge gets base = dsum + dmean / d,
   // plus dmin / (number of minima) at a minimum, dmax / (number of maxima) at
   // a maximum and dstd (m - mean) / (d std) where the variance is positive
-  const float *da = dagg + (size_t)i * kAgg * H + c;
-  const float4 dsum = ld4(da + 0 * H), dmean = ld4(da + 1 * H), dmin = ld4(da + 2 * H);
-  const float4 dmax = ld4(da + 3 * H), dstd = ld4(da + 4 * H);
   const float4 base = make_float4(dsum.x + dmean.x / df, dsum.y + dmean.y / df, dsum.z + dmean.z / df,
                                   dsum.w + dmean.w / df);
   const float4 cmin = make_float4(dmin.x / nmin.x, dmin.y / nmin.y, dmin.z / nmin.z, dmin.w / nmin.w);
   const float4 cmax = make_float4(dmax.x / nmax.x, dmax.y / nmax.y, dmax.z / nmax.z, dmax.w / nmax.w);
   const float4 cstd = make_float4(var.x > 0.f ? dstd.x / (df * sd.x) : 0.f, var.y > 0.f ? dstd.y / (df * sd.y) : 0.f,
                                   var.z > 0.f ? dstd.z / (df * sd.z) : 0.f, var.w > 0.f ? dstd.w / (df * sd.w) : 0.f);
-  auto emit = [&](int e, float4 m) {
+  auto emit = [&](int r, float4 m) {  // r: the reverse slot of the edge
     float4 g;
     g.x = route(m.x, base.x, mn.x, cmin.x, mx.x, cmax.x, mean.x, cstd.x);
     g.y = route(m.y, base.y, mn.y, cmin.y, mx.y, cmax.y, mean.y, cstd.y);
     g.z = route(m.z, base.z, mn.z, cmin.z, mx.z, cmax.z, mean.z, cstd.z);
     g.w = route(m.w, base.w, mn.w, cmin.w, mx.w, cmax.w, mean.w, cstd.w);
     dP = add4(dP, g);
-    const int re = rev[e];
-    if (re >= 0 && re < E) st4(dm + (size_t)re * H + c, g);
-    else flag(err, kErrIndex);
+    to_slot(r, g);
   };
 #pragma unroll
   for (int k = 0; k < kCache; ++k)
-    if (k < d) emit(r0 + k, mc[k]);
-  for (int e = r0 + kCache; e < r1; ++e) emit(e, message(PQ, source(col, e, N, err), H, c, P));
+    if (k < d) emit(re[k], mc[k]);
+  for (int e = r0 + kCache; e < r1; ++e) emit(rev[e], message(PQ, source(col, e, N, err), H, c, P));
+  return dP;
+}
+
+__global__ void __launch_bounds__(kEdgeThreads)
+aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *__restrict__ row_ptr,
+                          const int *__restrict__ col, const int *__restrict__ rev,
+                          const float *__restrict__ PQ, const float *__restrict__ agg,
+                          const float *__restrict__ dagg, float *__restrict__ dPQ,
+                          float *__restrict__ dm, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16, float eps) {
+  pdl_entry(GCNN_K_AGG_BWD_EDGE);
+  const int H4 = H >> 2;
+  const int N = min(n_cap, dims.nodes(n_cap));
+  const int E = min(e_cap, dims.edges(e_cap));
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)N * H4) return;
+  const int i = (int)(t / H4), c = (int)(t % H4) * 4;
+  const float4 dP = node_backward<-1>(i, c, H, N, E, row_ptr, col, rev, PQ, agg, dagg, eps, err, [&](int r, float4 g) {
+    if (r >= 0 && r < E) st4(dm + (size_t)r * H + c, g);
+    else flag(err, kErrIndex);
+  });
   st4(dPQ + (size_t)i * 2 * H + c, dP);
   if (dPQ16) st_bf16x4(dPQ16 + (size_t)i * ld16 + c, dP.x, dP.y, dP.z, dP.w);
+}
+
+// Fused backward over whole graphs: block (x, y) takes the graphs of chunk x
+// (a node range closed under the edges, since edges stay inside a graph) and
+// the channel slice of cs4 float4 columns starting at y cs4.  Pass 1 is
+// node_backward for every (node, channel) of the range with each edge's
+// gradient kept at its reverse slot in shared memory (in the global scratch
+// dm when the range has more than emax edges); after a block barrier pass 2
+// sums each node's own row of slots into dQ.  Same arithmetic and order as
+// the edge + gather pair, without the per-edge round trip through memory.
+constexpr int kFusedThreads = 512;
+constexpr int kChunkEdges = 128;  // edges per chunk on average (one window)
+constexpr int kChunkSlots = 192;  // edges a chunk keeps in shared memory (more costs L1)
+constexpr int kFusedSmem = 160 * 1024;  // shared-memory budget of one block
+
+// Work partition of the fused backward: chunk k holds the graphs whose first
+// edge lies in [k T, (k + 1) T); chunk_first[k] is its first graph (G when it
+// is empty), for k = 0..n_chunks.  Thread g (g = 0..G) is the first graph of
+// every window that starts after graph g - 1's first edge and no later than
+// its own, so each entry is written by exactly one thread.
+__global__ void __launch_bounds__(kThreads)
+aggregate_chunk_kernel(int g_cap, int n_cap, int n_chunks, int T, DevDims dims, const int *__restrict__ node_off,
+                       const int *__restrict__ row_ptr, int *__restrict__ chunk_first, unsigned *err) {
+  pdl_entry(GCNN_K_AGG_BWD_CHUNKS);
+  const int G = min(g_cap, dims.graphs(g_cap));
+  const int N = min(n_cap, dims.nodes(n_cap));
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g > G) return;
+  auto first_edge = [&](int h) {
+    const int n = node_off[h];
+    if (n < 0 || n > N) {
+      flag(err, kErrIndex);
+      return 0;
+    }
+    return row_ptr[n];
+  };
+  // the sentinel entry n_chunks is always G (a trailing graph without edges
+  // then belongs to the last chunk)
+  const int k0 = min(g == 0 ? 0 : first_edge(g - 1) / T + 1, n_chunks);
+  const int k1 = g == G ? n_chunks : min(n_chunks - 1, first_edge(g) / T);
+  for (int k = k0; k <= k1; ++k) chunk_first[k] = g;
+}
+
+template <bool STORED>
+__global__ void __launch_bounds__(kFusedThreads, 1)
+aggregate_bwd_fused_kernel(int g_cap, int n_cap, int e_cap, const int *__restrict__ chunk_first, int cs4, int emax,
+                           int H, DevDims dims, const int *__restrict__ node_off, const int *__restrict__ row_ptr,
+                           const int *__restrict__ col, const int *__restrict__ rev, const float *__restrict__ PQ,
+                           const float *__restrict__ agg, const float *__restrict__ dagg, float *__restrict__ dPQ,
+                           float *__restrict__ dm, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16, float eps) {
+  extern __shared__ float4 s_dm[];
+  pdl_entry(GCNN_K_AGG_BWD_FUSED);
+  const int G = min(g_cap, dims.graphs(g_cap));
+  const int N = min(n_cap, dims.nodes(n_cap));
+  const int E = min(e_cap, dims.edges(e_cap));
+  const int g0 = chunk_first[blockIdx.x], g1 = min(chunk_first[blockIdx.x + 1], G);
+  if (g0 < 0 || g0 >= g1) return;
+  const int n0 = node_off[g0], n1 = node_off[g1];
+  if (n0 < 0 || n1 < n0 || n1 > N) {
+    flag(err, kErrIndex);
+    return;
+  }
+  const int e0 = row_ptr[n0], e1 = row_ptr[n1];
+  if (e0 < 0 || e1 < e0 || e1 > E) {
+    flag(err, kErrIndex);
+    return;
+  }
+  const bool in_smem = e1 - e0 <= emax;
+  const int H4 = H >> 2;
+  const int c0 = blockIdx.y * cs4;
+  const int w = min(cs4, H4 - c0);
+  // each thread keeps one float4 column of the slice and strides over the
+  // chunk's nodes (kFusedThreads / w rows at a time; the remainder threads idle)
+  const int rows = kFusedThreads / w, row = threadIdx.x / w, cc = threadIdx.x % w, c = (c0 + cc) * 4;
+  const int n_end = row < rows ? n1 : n0;
+  for (int i = n0 + row; i < n_end; i += rows) {
+    const float4 dP = node_backward<STORED ? 1 : 0>(i, c, H, N, E, row_ptr, col, rev, PQ, agg, dagg, eps, err, [&](int r, float4 g) {
+      if (r < e0 || r >= e1) flag(err, kErrIndex);  // an edge leaving the graph
+      else if (in_smem) s_dm[(r - e0) * cs4 + cc] = g;
+      else st4(dm + (size_t)r * H + c, g);
+    });
+    st4(dPQ + (size_t)i * 2 * H + c, dP);
+    if (dPQ16) st_bf16x4(dPQ16 + (size_t)i * ld16 + c, dP.x, dP.y, dP.z, dP.w);
+  }
+  __syncthreads();
+  for (int j = n0 + row; j < n_end; j += rows) {
+    int r0 = row_ptr[j], r1 = row_ptr[j + 1];
+    if (r0 < e0 || r1 > e1 || r1 < r0) {
+      flag(err, kErrIndex);
+      r1 = r0;
+    }
+    float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (in_smem)
+      for (int e = r0; e < r1; ++e) q = add4(q, s_dm[(e - e0) * cs4 + cc]);
+    else
+      for (int e = r0; e < r1; ++e) q = add4(q, ld4(dm + (size_t)e * H + c));
+    st4(dPQ + (size_t)j * 2 * H + H + c, q);
+    if (dPQ16) st_bf16x4(dPQ16 + (size_t)j * ld16 + H + c, q.x, q.y, q.z, q.w);
+  }
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -265,8 +415,10 @@ int launch_aggregate_fwd(int n_nodes, int H, DevDims dims, const int *row_ptr, c
   if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
-  GCNN_TRY(launch(aggregate_fwd_kernel, ceil_div(work, kThreads), kThreads, 0, s, n_nodes, H, dims, row_ptr, col, PQ,
-                  agg, eps, err, S16, ld16, amp, att));
+  auto kernel = agg ? (S16 ? aggregate_fwd_kernel<true, true> : aggregate_fwd_kernel<true, false>)
+                    : (S16 ? aggregate_fwd_kernel<false, true> : aggregate_fwd_kernel<false, false>);
+  GCNN_TRY(launch(kernel, ceil_div(work, kThreads), kThreads, 0, s, n_nodes, H, dims, row_ptr, col, PQ, agg, eps, err,
+                  S16, ld16, amp, att));
   return GCNN_OK;
 }
 
@@ -281,6 +433,46 @@ int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const in
                   row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, err, dPQ16, ld16, eps));
   GCNN_TRY(launch(aggregate_bwd_gather_kernel, ceil_div(work, kThreads), kThreads, 0, s, n_nodes, n_edges, H, dims,
                   row_ptr, (const float *)scratch, dPQ, err, dPQ16, ld16));
+  return GCNN_OK;
+}
+
+int aggregate_chunk_capacity(int n_edges) { return ceil_div(std::max(n_edges, 1), kChunkEdges) + 1; }
+
+bool aggregate_bwd_uses_fused(int n_edges) {
+  return ceil_div(std::max(n_edges, 0), kChunkEdges) >= 2 * num_sms();
+}
+
+int launch_aggregate_bwd_graphs(int n_graphs, int n_nodes, int n_edges, int H, DevDims dims, const int *node_off,
+                                const int *row_ptr, const int *col, const int *rev, const float *PQ,
+                                const float *agg, const float *dagg, float *dPQ, float *scratch, int *chunks,
+                                float eps, unsigned *err, cudaStream_t s, uint16_t *dPQ16, int ld16) {
+  if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
+  if (n_nodes <= 0 || n_graphs <= 0) return GCNN_OK;
+  if (!aggregate_bwd_uses_fused(n_edges))
+    return launch_aggregate_bwd(n_nodes, n_edges, H, dims, row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, eps, err, s,
+                                dPQ16, ld16);
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(aggregate_bwd_fused_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kFusedSmem);
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(aggregate_bwd_fused_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kFusedSmem);
+  });
+  if (attr != cudaSuccess) return set_error(GCNN_ECUDA, "aggregate: %s", cudaGetErrorString(attr));
+  const int n_chunks = aggregate_chunk_capacity(n_edges) - 1;
+  // channel slices so that a chunk's kChunkSlots edges fit the budget
+  const int H4 = H / 4;
+  const int slices = ceil_div(kChunkSlots * H4 * 16, kFusedSmem);
+  const int cs4 = ceil_div(H4, slices);
+  GCNN_TRY(launch(aggregate_chunk_kernel, ceil_div(n_graphs + 1, kThreads), kThreads, 0, s, n_graphs, n_nodes,
+                  n_chunks, kChunkEdges, dims, node_off, row_ptr, chunks, err));
+  GCNN_TRY(launch(agg ? aggregate_bwd_fused_kernel<true> : aggregate_bwd_fused_kernel<false>,
+                  dim3(n_chunks, ceil_div(H4, cs4)), kFusedThreads,
+                  (size_t)kChunkSlots * cs4 * 16, s, n_graphs, n_nodes, n_edges, (const int *)chunks, cs4,
+                  kChunkSlots, H, dims, node_off, row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, err, dPQ16, ld16,
+                  eps));
   return GCNN_OK;
 }
 

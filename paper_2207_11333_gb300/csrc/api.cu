@@ -261,6 +261,7 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   const size_t o_dH = cv.take<float>(Nc * H), o_dX = cv.take<float>(Nc * H);
   const size_t o_dagg = cv.take<float>(Nc * kAgg * H), o_dPQ = cv.take<float>(Nc * 2 * H);
   const size_t o_dm = cv.take<float>(Ec * H);
+  const size_t o_chunks = cv.take<int>(aggregate_chunk_capacity((int)Ec));
   const size_t o_tk = cv.take<unsigned>(16);
   const size_t o_ws = cv.take<float>(wsf);
   const bool bf = cfg->precision == GCNN_PREC_BF16;
@@ -294,6 +295,7 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   c->dpred = (float *)(b + o_dpred); c->dz1 = (float *)(b + o_dz1); c->dg = (float *)(b + o_dg);
   c->dH = (float *)(b + o_dH); c->dX = (float *)(b + o_dX); c->dagg = (float *)(b + o_dagg);
   c->dPQ = (float *)(b + o_dPQ); c->dm = (float *)(b + o_dm); c->tickets = (unsigned *)(b + o_tk);
+  c->chunks = (int *)(b + o_chunks);
   c->ws.partial = (float *)(b + o_ws); c->ws.floats = wsf;
   c->ws.max_splits = (cfg->flags & GCNN_FLAG_ROW_INVARIANT) ? 1 : 32;
   if (side) {
@@ -757,6 +759,23 @@ int gcnn_op_aggregate_bwd(int32_t n_nodes, int32_t n_edges, int32_t hidden, cons
     return set_error(GCNN_EINVAL, "aggregate_bwd: float buffers must be 16-byte aligned");
   return launch_aggregate_bwd(n_nodes, n_edges, hidden, DevDims{nullptr}, row_ptr, col, rev, PQ, agg, dagg, dPQ,
                               scratch, std_eps, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+int gcnn_op_aggregate_bwd_graphs(int32_t n_graphs, int32_t n_nodes, int32_t n_edges, int32_t hidden,
+                                 const int32_t *node_off, const int32_t *row_ptr, const int32_t *col,
+                                 const int32_t *rev, const float *PQ, const float *agg, const float *dagg,
+                                 float *dPQ, float *scratch, float std_eps, void *stream) {
+  if (n_graphs < 0 || n_nodes < 0 || n_edges < 0 || hidden <= 0 || hidden % 4 ||
+      (n_nodes > 0 && (!node_off || !row_ptr || !col || !rev || !PQ || !agg || !dagg || !dPQ || !scratch)))
+    return set_error(GCNN_EINVAL, "aggregate_bwd_graphs: bad arguments (hidden must be a multiple of 4)");
+  if ((reinterpret_cast<uintptr_t>(PQ) | reinterpret_cast<uintptr_t>(agg) | reinterpret_cast<uintptr_t>(dagg) |
+       reinterpret_cast<uintptr_t>(dPQ) | reinterpret_cast<uintptr_t>(scratch)) % 16)
+    return set_error(GCNN_EINVAL, "aggregate_bwd_graphs: float buffers must be 16-byte aligned");
+  // the chunk partition follows the per-edge part of scratch
+  int *chunks = reinterpret_cast<int *>(scratch + (size_t)n_edges * hidden);
+  return launch_aggregate_bwd_graphs(n_graphs, n_nodes, n_edges, hidden, DevDims{nullptr}, node_off, row_ptr, col, rev,
+                                     PQ, agg, dagg, dPQ, scratch, chunks, std_eps, nullptr,
+                                     static_cast<cudaStream_t>(stream));
 }
 
 int gcnn_op_pool_fwd(int32_t n_graphs, int32_t hidden, const int32_t *node_off, const float *x, float *pooled,

@@ -49,6 +49,7 @@ struct gcnn_ctx {
   float *pooled = nullptr, *z1 = nullptr, *pred = nullptr, *dpred = nullptr, *dz1 = nullptr;
   float *dg = nullptr;
   float *dH = nullptr, *dX = nullptr, *dagg = nullptr, *dPQ = nullptr, *dm = nullptr;
+  int *chunks = nullptr;  // work partition of the fused aggregation backward
   float *dPQ2 = nullptr;  // BF16: second [dP | dQ] buffer, alternating by layer
   unsigned *tickets = nullptr;  // zero-initialised completion counters of single-launch reductions
 

@@ -46,6 +46,19 @@ int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const in
                          const float *dagg, float *dPQ, float *scratch, float eps, unsigned *err,
                          cudaStream_t s, uint16_t *dPQ16 = nullptr, int ld16 = 0);
 
+// The same gradient for a batch of whole graphs (node_off: G + 1 offsets;
+// no edge leaves its graph).  Batches of at least 2 x SMs x 128 edges take the
+// fused kernel: chunks of graphs of about 128 edges, each handled by one block
+// that keeps its per-edge gradients in shared memory; `chunks` holds
+// aggregate_chunk_capacity(n_edges) ints.  Smaller batches take the edge +
+// gather pair above (scratch as there).  Same result either way, bitwise.
+int launch_aggregate_bwd_graphs(int n_graphs, int n_nodes, int n_edges, int H, DevDims dims, const int *node_off,
+                                const int *row_ptr, const int *col, const int *rev, const float *PQ,
+                                const float *agg, const float *dagg, float *dPQ, float *scratch, int *chunks,
+                                float eps, unsigned *err, cudaStream_t s, uint16_t *dPQ16 = nullptr, int ld16 = 0);
+int aggregate_chunk_capacity(int n_edges);
+bool aggregate_bwd_uses_fused(int n_edges);
+
 // ---------------------------------------------------------------- small.cu
 int launch_embed(int n_nodes, int H, DevDims dims, const uint8_t *types, const float *emb,
                  int n_types, float *x0, cudaStream_t s, uint16_t *x0_16 = nullptr, int ld16 = 0);

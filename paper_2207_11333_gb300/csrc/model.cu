@@ -202,7 +202,7 @@ int tc_update(gcnn_ctx *c, int Ngrid, int l) {
 // marks the lane's work of the layer.  dx(l) overwrites G5[cur ^ 1] and the
 // FP32 gradient the previous layer's sums read, so it waits for `done` of
 // layer l + 1; dPQ alternates between two buffers by layer.
-int tc_backward_layer(gcnn_ctx *c, int Ngrid, int Egrid, int l, int cur, float *dPQ, bool ov) {
+int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur, float *dPQ, bool ov) {
   const int H = c->H;
   DevDims dims{c->bb.dims};
   LayerW gw = layer_ptrs(c->grads, c, l);
@@ -240,8 +240,9 @@ int tc_backward_layer(gcnn_ctx *c, int Ngrid, int Egrid, int l, int cur, float *
   }
   {
     PhaseScope ps(c, GCNN_PHASE_AGG_BWD);
-    GCNN_TRY(launch_aggregate_bwd(Ngrid, Egrid, H, dims, c->bb.row_ptr, c->bb.col, c->bb.rev, pq, agg, c->dagg,
-                                  dPQ, c->dm, (float)c->cfg.std_eps, c->err, c->stream, G + 3 * H, 5 * H));
+    GCNN_TRY(launch_aggregate_bwd_graphs(Gn, Ngrid, Egrid, H, dims, c->bb.node_off, c->bb.row_ptr, c->bb.col,
+                                         c->bb.rev, pq, agg, c->dagg, dPQ, c->dm, c->chunks,
+                                         (float)c->cfg.std_eps, c->err, c->stream, G + 3 * H, 5 * H));
   }
   if (ov) {
     GCNN_CUDA_TRY(cudaEventRecord(mid, c->stream));
@@ -366,7 +367,7 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
     int cur = 0;
     for (int l = c->L - 1; l >= 0; --l) {
       float *dPQ = (ov && (l & 1)) ? c->dPQ2 : c->dPQ;
-      GCNN_TRY(tc_backward_layer(c, Ngrid, Egrid, l, cur, dPQ, ov));
+      GCNN_TRY(tc_backward_layer(c, G, Ngrid, Egrid, l, cur, dPQ, ov));
       cur ^= 1;
       std::swap(c->dH, c->dX);
     }
@@ -416,8 +417,9 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
     }
     {
       PhaseScope ps(c, GCNN_PHASE_AGG_BWD);
-      GCNN_TRY(launch_aggregate_bwd(Ngrid, Egrid, H, dims, c->bb.row_ptr, c->bb.col, c->bb.rev, pq, agg,
-                                    c->dagg, c->dPQ, c->dm, (float)c->cfg.std_eps, c->err, c->stream));
+      GCNN_TRY(launch_aggregate_bwd_graphs(G, Ngrid, Egrid, H, dims, c->bb.node_off, c->bb.row_ptr, c->bb.col,
+                                           c->bb.rev, pq, agg, c->dagg, c->dPQ, c->dm, c->chunks,
+                                           (float)c->cfg.std_eps, c->err, c->stream));
     }
     // dW_M (H x 2H) and db_M: [x ; 1]^T dPQ  (bias row keeps the first H columns)
     {

@@ -54,6 +54,43 @@ def test_aggregate_function_matches_torch_fp64():
     assert rel_norm(x.grad.cpu().numpy(), ref_x.grad.cpu().numpy()) < 1e-5
 
 
+@pytest.mark.parametrize("G,lo,hi,H", [(20, 3, 40, 12), (900, 3, 60, 8), (400, 60, 120, 4)])
+def test_aggregate_bwd_over_graphs_matches_pair(G, lo, hi, H):
+    """gcnn_op_aggregate_bwd_graphs (fused over chunks of whole graphs once the
+    batch has more than 2 x SMs x 128 edges; graphs above a chunk's shared-memory
+    slots go through device memory) equals the edge + gather pair bitwise and
+    the FP64 torch gradient, with a trailing graph of isolated atoms.  P holds odd
+    and Q even multiples of 1/16, so every message P_i + Q_j is exact in FP32 and
+    FP64 (both sides take the same min/max decisions, exact ties included, on a
+    batch of tens of thousands of atoms) and never 0, the value torch's amax/amin
+    reference starts from and would count as a tie."""
+    import paper_2207_11333_gb300 as g
+    gs = synth.molecules_uniform(17, G, lo, hi)
+    _, b, delta = oracle_batch(gs)
+    extra = 3                                              # one more graph: 3 atoms, no edges
+    N = b.N + extra
+    row_ptr = np.concatenate([b.row_ptr, np.full(extra, b.row_ptr[-1], np.int32)]).astype(np.int32)
+    node_off = np.concatenate([b.node_off, [N]]).astype(np.int32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rp, col, rev, no = dev(row_ptr), dev(b.col), dev(b.rev), dev(node_off)
+    gen = torch.Generator(device="cuda").manual_seed(4)
+    k = torch.randint(-64, 64, (N, 2 * H), device="cuda", generator=gen).float()
+    PQ = torch.cat([2 * k[:, :H] + 1, 2 * k[:, H:]], 1) / 16
+    dagg = torch.randn(N, 5 * H, device="cuda", generator=gen)
+    agg = g.aggregate_fwd(PQ, rp, col)
+    pair = g.aggregate_bwd(PQ, agg, dagg, rp, col, rev)
+    fused = g.aggregate_bwd(PQ, agg, dagg, rp, col, rev, node_off=no)
+    torch.cuda.synchronize()
+    assert torch.equal(pair, fused)
+    bb = type("B", (), {})()
+    bb.N, bb.row_ptr, bb.col = N, row_ptr, b.col
+    bb.deg = np.diff(row_ptr)
+    ref_x = PQ.double().clone().requires_grad_(True)
+    (_torch_aggregate(ref_x, bb, H) * dagg.double()).sum().backward()
+    assert rel_norm(fused.cpu().numpy(), ref_x.grad.cpu().numpy()) < 1e-5
+    assert torch.count_nonzero(fused[b.N:]) == 0
+
+
 def test_aggregate_function_ties_match_torch():
     """Identical sources (as from equal atom types) tie in min/max; the split matches torch."""
     from paper_2207_11333_gb300.autograd import aggregate
