@@ -13,7 +13,8 @@
  *   batch collation of graphs into one disjoint-union graph         [Sec. 1, 4]
  *   atom-type embedding as node features                            [Sec. 3.1]
  *   L PNA graph-convolution layers (message passing)                [Sec. 3.1, 5.1]
- *       message     m_ij = W_M [x_i ; x_j] + b_M   on each edge j->i
+ *       message     m_ij = W_M [x_i ; x_j ; e_ij] + b_M   on each edge j->i
+ *                   (e_ij: the edge's F bond features, F = 0 without them)
  *       aggregators sum, mean, min, max, std over j in N(i)
  *       scalers     identity, amplification log(d+1)/delta,
  *                   attenuation delta/log(d+1)
@@ -25,7 +26,9 @@
  *   Adam / AdamW update                                             [Sec. 3.2, 5.1]
  * The paper names PNA (Corso et al. 2020) but does not print its equations;
  * the layer above is the published PNA definition with one linear message
- * layer, one linear update layer, no edge features and no towers.
+ * layer (over the two atoms' features and, when the data carry them, the
+ * bond's features: Sec. 3.1 and Table 1 name edge attributes), one linear
+ * update layer and no towers.
  *
  * Readings where the paper is silent (the same ones the library documents):
  *   std    = sqrt(ReLU(var) + eps), var = (1/d) sum_j (m_ij - mean)^2
@@ -41,8 +44,9 @@
  *              msg_b[H], upd_w[16H][H] (rows: x_i, then scaler-major blocks
  *              id{sum,mean,min,max,std}, amp{...}, att{...}), upd_b[H]
  *   head: w1[H][Hh], b1[Hh], w2[Hh], b2
- * so that W_M(k, c) for the stacked input [x_i ; x_j] is msg_w[k][c] for
- * k < H and msg_w[k-H][H+c] for k >= H.
+ *   with F bond features, per layer: edge_w[F][H] (the bond rows of W_M)
+ * so that W_M(k, c) for the stacked input [x_i ; x_j ; e_ij] is msg_w[k][c]
+ * for k < H, msg_w[k-H][H+c] for H <= k < 2H and edge_w[k-2H][c] after.
  */
 #include <math.h>
 #include <stdint.h>
@@ -65,13 +69,16 @@
  *   deg[N]                         in-degree
  *   amp[N], att[N]                 degree scalers (FP64, rounded to float)
  *   types[N], y[G]                 gathered node types and targets
+ *   eattr[E][F]                    bond features of each edge, in the order
+ *                                  of col (F = 0: not used)
  */
 int oracle_collate(int64_t G, const int64_t *ids, const int64_t *st_node_ptr,
                    const int64_t *st_edge_ptr, const uint8_t *st_types,
                    const uint8_t *st_edges, const float *st_y, double delta,
                    int64_t *node_off, int64_t *edge_off, int32_t *graph_id,
                    int32_t *row_ptr, int32_t *col, int32_t *rev, int32_t *deg,
-                   float *amp, float *att, uint8_t *types, float *y) {
+                   float *amp, float *att, uint8_t *types, float *y, int F,
+                   const float *st_eattr, float *eattr) {
   node_off[0] = 0;
   edge_off[0] = 0;
   for (int64_t g = 0; g < G; ++g) {
@@ -82,7 +89,8 @@ int oracle_collate(int64_t G, const int64_t *ids, const int64_t *st_node_ptr,
   int64_t N = node_off[G], E = edge_off[G];
   int64_t *src = (int64_t *)malloc(sizeof(int64_t) * (E + 1));
   int64_t *dst = (int64_t *)malloc(sizeof(int64_t) * (E + 1));
-  if (!src || !dst) { free(src); free(dst); return -1; }
+  int64_t *sid = (int64_t *)malloc(sizeof(int64_t) * (E + 1));  /* store index of each edge */
+  if (!src || !dst || !sid) { free(src); free(dst); free(sid); return -1; }
 
   /* global node ids and node attributes */
   for (int64_t g = 0; g < G; ++g) {
@@ -97,6 +105,7 @@ int oracle_collate(int64_t G, const int64_t *ids, const int64_t *st_node_ptr,
       const uint8_t *pair = st_edges + 2 * (st_edge_ptr[id] + k);
       src[edge_off[g] + k] = node_off[g] + pair[0];
       dst[edge_off[g] + k] = node_off[g] + pair[1];
+      sid[edge_off[g] + k] = st_edge_ptr[id] + k;
     }
     y[g] = st_y[id];
   }
@@ -107,22 +116,29 @@ int oracle_collate(int64_t G, const int64_t *ids, const int64_t *st_node_ptr,
   row_ptr[0] = 0;
   for (int64_t i = 0; i < N; ++i) row_ptr[i + 1] = row_ptr[i] + deg[i];
 
-  /* place each edge in its destination's row, then sort the row by source */
+  /* place each edge in its destination's row, then sort the row by source
+     (a stable sort: edges with the same source keep their store order) */
   int32_t *fill = (int32_t *)calloc((size_t)(N + 1), sizeof(int32_t));
-  if (!fill) { free(src); free(dst); return -1; }
+  int64_t *pos_sid = (int64_t *)malloc(sizeof(int64_t) * (E + 1));
+  if (!fill || !pos_sid) { free(src); free(dst); free(sid); free(fill); free(pos_sid); return -1; }
   for (int64_t k = 0; k < E; ++k) {
     int64_t i = dst[k];
     col[row_ptr[i] + fill[i]] = (int32_t)src[k];
+    pos_sid[row_ptr[i] + fill[i]] = sid[k];
     fill[i] += 1;
   }
   for (int64_t i = 0; i < N; ++i) {
     for (int32_t a = row_ptr[i] + 1; a < row_ptr[i + 1]; ++a) { /* insertion sort */
       int32_t v = col[a];
+      int64_t vs = pos_sid[a];
       int32_t b = a - 1;
-      while (b >= row_ptr[i] && col[b] > v) { col[b + 1] = col[b]; --b; }
+      while (b >= row_ptr[i] && col[b] > v) { col[b + 1] = col[b]; pos_sid[b + 1] = pos_sid[b]; --b; }
       col[b + 1] = v;
+      pos_sid[b + 1] = vs;
     }
   }
+  for (int64_t p = 0; p < E; ++p)
+    for (int f = 0; f < F; ++f) eattr[p * F + f] = st_eattr[pos_sid[p] * F + f];
   /* reverse edge: the edge i -> j sits in row j with source i */
   for (int64_t i = 0; i < N; ++i) {
     for (int32_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
@@ -139,8 +155,10 @@ int oracle_collate(int64_t G, const int64_t *ids, const int64_t *st_node_ptr,
     att[i] = (float)(delta / log(d + 1.0));
   }
   free(fill);
+  free(pos_sid);
   free(src);
   free(dst);
+  free(sid);
   return 0;
 }
 
@@ -154,8 +172,9 @@ double oracle_delta(int64_t N, const int32_t *deg) {
 /* ------------------------------------------------------------ model */
 
 typedef struct {
-  int H, L, T, Hh;
+  int H, L, T, Hh, F;
   int64_t G, N, E;
+  const float *eattr;  /* E x F bond features in col order */
   const int64_t *node_off;
   const int32_t *graph_id, *row_ptr, *col, *deg;
   const float *amp, *att;
@@ -164,15 +183,17 @@ typedef struct {
 } net_t;
 
 typedef struct {
-  const double *msg_w, *msg_b, *upd_w, *upd_b;
+  const double *msg_w, *msg_b, *upd_w, *upd_b, *edge_w;
 } layer_t;
 
 static int64_t layer_size(int H) {
   return (int64_t)H * 2 * H + H + (int64_t)16 * H * H + H;
 }
 
-int64_t oracle_param_count(int H, int L, int T, int Hh) {
-  return (int64_t)T * H + L * layer_size(H) + (int64_t)H * Hh + Hh + Hh + 1;
+static int64_t head_size(int H, int Hh) { return (int64_t)H * Hh + Hh + Hh + 1; }
+
+int64_t oracle_param_count(int H, int L, int T, int Hh, int F) {
+  return (int64_t)T * H + L * layer_size(H) + head_size(H, Hh) + (int64_t)L * F * H;
 }
 
 static layer_t layer_at(const net_t *n, const double *p, int l) {
@@ -182,6 +203,8 @@ static layer_t layer_at(const net_t *n, const double *p, int l) {
   w.msg_b = w.msg_w + (int64_t)n->H * 2 * n->H;
   w.upd_w = w.msg_b + n->H;
   w.upd_b = w.upd_w + (int64_t)16 * n->H * n->H;
+  w.edge_w = p + (int64_t)n->T * n->H + n->L * layer_size(n->H) + head_size(n->H, n->Hh) +
+             (int64_t)l * n->F * n->H;
   return w;
 }
 
@@ -200,7 +223,7 @@ static double scaler(const net_t *n, int64_t i, int s) {
   return s == 0 ? 1.0 : (s == 1 ? (double)n->amp[i] : (double)n->att[i]);
 }
 
-/* m[e][c] = b_M[c] + sum_k W_M(k,c) [x_i ; x_j]_k for the edge e = (j -> i) */
+/* m[e][c] = b_M[c] + sum_k W_M(k,c) [x_i ; x_j ; e_ij]_k for the edge e = (j -> i) */
 static void messages(const net_t *n, const layer_t *w, const double *x, double *m) {
   int H = n->H;
 #pragma omp parallel for schedule(static)
@@ -211,6 +234,7 @@ static void messages(const net_t *n, const layer_t *w, const double *x, double *
         double acc = w->msg_b[c];
         for (int k = 0; k < H; ++k) acc += wm(n, w->msg_w, k, c) * x[i * H + k];
         for (int k = 0; k < H; ++k) acc += wm(n, w->msg_w, H + k, c) * x[j * H + k];
+        for (int f = 0; f < n->F; ++f) acc += w->edge_w[(int64_t)f * H + c] * (double)n->eattr[(int64_t)e * n->F + f];
         m[(int64_t)e * H + c] = acc;
       }
     }
@@ -318,11 +342,11 @@ static void embed(const net_t *n, const double *p, double *x0) {
     for (int k = 0; k < H; ++k) x0[i * H + k] = p[(int64_t)n->types[i] * H + k];
 }
 
-static void net_init(net_t *n, int H, int L, int T, int Hh, int64_t G, int64_t N, int64_t E,
+static void net_init(net_t *n, int H, int L, int T, int Hh, int F, int64_t G, int64_t N, int64_t E,
                      const int64_t *node_off, const int32_t *graph_id, const int32_t *row_ptr,
                      const int32_t *col, const int32_t *deg, const float *amp, const float *att,
-                     const uint8_t *types, double eps) {
-  n->H = H; n->L = L; n->T = T; n->Hh = Hh;
+                     const uint8_t *types, const float *eattr, double eps) {
+  n->H = H; n->L = L; n->T = T; n->Hh = Hh; n->F = F; n->eattr = eattr;
   n->G = G; n->N = N; n->E = E;
   n->node_off = node_off; n->graph_id = graph_id; n->row_ptr = row_ptr; n->col = col;
   n->deg = deg; n->amp = amp; n->att = att; n->types = types; n->eps = eps;
@@ -367,15 +391,15 @@ static void forward(const net_t *n, const double *p, const double *x0_in, fwd_t 
  * Optional outputs: xs_out ((L+1) x N x H, layer inputs/outputs),
  * agg_out (L x N x 5H), pooled_out (G x H).
  */
-int oracle_forward(int H, int L, int T, int Hh, const double *params, int64_t G, int64_t N,
+int oracle_forward(int H, int L, int T, int Hh, int F, const double *params, int64_t G, int64_t N,
                    int64_t E, const int64_t *node_off, const int32_t *graph_id,
                    const int32_t *row_ptr, const int32_t *col, const int32_t *deg,
-                   const float *amp, const float *att, const uint8_t *types,
+                   const float *amp, const float *att, const uint8_t *types, const float *eattr,
                    const double *x0_in, double eps, double *pred, double *xs_out,
                    double *agg_out, double *pooled_out) {
   net_t n;
   fwd_t f;
-  net_init(&n, H, L, T, Hh, G, N, E, node_off, graph_id, row_ptr, col, deg, amp, att, types, eps);
+  net_init(&n, H, L, T, Hh, F, G, N, E, node_off, graph_id, row_ptr, col, deg, amp, att, types, eattr, eps);
   if (fwd_alloc(&n, &f)) { fwd_free(&f); return -1; }
   forward(&n, params, x0_in, &f, pred);
   if (xs_out) memcpy(xs_out, f.xs, sizeof(double) * (size_t)((L + 1) * N * H));
@@ -391,17 +415,17 @@ int oracle_forward(int H, int L, int T, int Hh, const double *params, int64_t G,
  * otherwise dpred_in is used as dL/dpred and *loss is not written.
  * grad has the parameter layout; dx0 (N x H, optional) receives dL/dx0.
  */
-int oracle_backward(int H, int L, int T, int Hh, const double *params, int64_t G, int64_t N,
+int oracle_backward(int H, int L, int T, int Hh, int F, const double *params, int64_t G, int64_t N,
                     int64_t E, const int64_t *node_off, const int32_t *graph_id,
                     const int32_t *row_ptr, const int32_t *col, const int32_t *deg,
-                    const float *amp, const float *att, const uint8_t *types,
+                    const float *amp, const float *att, const uint8_t *types, const float *eattr,
                     const double *x0_in, double eps, const float *y, const double *dpred_in,
                     double *grad, double *dx0, double *loss, double *pred_out) {
   net_t n;
   fwd_t f;
-  net_init(&n, H, L, T, Hh, G, N, E, node_off, graph_id, row_ptr, col, deg, amp, att, types, eps);
+  net_init(&n, H, L, T, Hh, F, G, N, E, node_off, graph_id, row_ptr, col, deg, amp, att, types, eattr, eps);
   int64_t NH = N * H;
-  int64_t P = oracle_param_count(H, L, T, Hh);
+  int64_t P = oracle_param_count(H, L, T, Hh, F);
   double *pred = (double *)calloc((size_t)(G + 1), sizeof(double));
   double *dpred = (double *)calloc((size_t)(G + 1), sizeof(double));
   double *dx = (double *)calloc((size_t)(NH + 1), sizeof(double));      /* dL/dx_l   */
@@ -534,11 +558,20 @@ int oracle_backward(int H, int L, int T, int Hh, const double *params, int64_t G
       }
     }
 
-    /* message layer: m_ij = b_M + W_M^T [x_i ; x_j], edge e = (j -> i) in row i */
+    /* message layer: m_ij = b_M + W_M^T [x_i ; x_j ; e_ij], edge e = (j -> i) in row i */
     for (int c = 0; c < H; ++c) {
       double s = 0.0;
       for (int64_t e = 0; e < E; ++e) s += dm[e * H + c];
       g_msg_b[c] += s;
+    }
+    if (F > 0) {                                  /* bond rows: dW_E[f][c] = sum_e e_ij[f] dm_ij[c] */
+      double *g_edge_w = grad + (w.edge_w - params);
+      for (int fi = 0; fi < F; ++fi)
+        for (int c = 0; c < H; ++c) {
+          double s = 0.0;
+          for (int64_t e = 0; e < E; ++e) s += (double)eattr[e * F + fi] * dm[e * H + c];
+          g_edge_w[(int64_t)fi * H + c] += s;
+        }
     }
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < H; ++k) {                /* dW_M over all edges */

@@ -21,7 +21,11 @@ paper's schema of one global array per graph attribute, Section 4, Table 1):
     64      i64         byte offset of edges     (u8[2E], local (src, dst) pairs)
     72      i64         byte offset of y         (f32[G])
     80      i64         file size in bytes
-    88..127 zero
+    88      i64         F  bond features per edge      (version 2 only)
+    96      i64         byte offset of edge_attr (f32[E][F], version 2 only)
+    88..127 zero otherwise
+Version 2 adds the edges' features (Table 1's edge attributes), one row per
+stored directed edge in store order.
 Every array starts on a 64-byte boundary.  Node and edge ids inside a graph
 are local (0..n-1), so a graph is a contiguous slice of each array.
 """
@@ -145,15 +149,20 @@ def uniform(seed: int, i0: int, n: int, lo: float, hi: float) -> np.ndarray:
     return out
 
 
-def param_count(H: int, L: int, T: int = N_TYPES, Hh: int | None = None) -> int:
-    return int(lib().synth_param_count(H, L, T, H if Hh is None else Hh))
+def param_count(H: int, L: int, T: int = N_TYPES, Hh: int | None = None, F: int = 0) -> int:
+    return int(lib().synth_param_count(H, L, T, H if Hh is None else Hh)) + L * F * H
 
 
-def init_params(seed: int, H: int, L: int, T: int = N_TYPES, Hh: int | None = None) -> np.ndarray:
+def init_params(seed: int, H: int, L: int, T: int = N_TYPES, Hh: int | None = None, F: int = 0) -> np.ndarray:
+    """Flat parameters; with F bond features the L blocks of bond rows of the
+    message weights (F x H each) follow the head, U(+-1/sqrt(2H + F))."""
     Hh = H if Hh is None else Hh
-    out = np.empty(param_count(H, L, T, Hh), np.float32)
-    lib().synth_init_params(seed, H, L, T, Hh, _p(out))
-    return out
+    base = np.empty(param_count(H, L, T, Hh), np.float32)
+    lib().synth_init_params(seed, H, L, T, Hh, _p(base))
+    if F == 0:
+        return base
+    b = 1.0 / math.sqrt(2 * H + F)
+    return np.concatenate([base, uniform(seed, 0, L * F * H, -b, b).astype(np.float32)])
 
 
 # ---------------------------------------------------------------- graphs
@@ -166,6 +175,11 @@ class GraphSet:
     types: np.ndarray     # uint8 [N]
     edges: np.ndarray     # uint8 [E, 2]  local (src, dst)
     y: np.ndarray         # float32 [G]
+    eattr: np.ndarray | None = None   # float32 [E, F] bond features (store version 2)
+
+    @property
+    def F(self) -> int:
+        return 0 if self.eattr is None else int(self.eattr.shape[1])
 
     @property
     def n_graphs(self) -> int:
@@ -190,7 +204,23 @@ class GraphSet:
         edge_ptr[1:] = np.cumsum(e)
         types = np.concatenate([self.types[self.node_ptr[g]:self.node_ptr[g + 1]] for g in ids]) if len(ids) else np.zeros(0, np.uint8)
         edges = np.concatenate([self.edges[self.edge_ptr[g]:self.edge_ptr[g + 1]] for g in ids]) if len(ids) else np.zeros((0, 2), np.uint8)
-        return GraphSet(node_ptr, edge_ptr, np.ascontiguousarray(types), np.ascontiguousarray(edges), self.y[ids].copy())
+        eattr = None
+        if self.eattr is not None:
+            eattr = (np.concatenate([self.eattr[self.edge_ptr[g]:self.edge_ptr[g + 1]] for g in ids]) if len(ids)
+                     else np.zeros((0, self.F), np.float32))
+        return GraphSet(node_ptr, edge_ptr, np.ascontiguousarray(types), np.ascontiguousarray(edges), self.y[ids].copy(),
+                        None if eattr is None else np.ascontiguousarray(eattr))
+
+
+def bond_features(seed: int, gs: GraphSet, F: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    """F features per bond, U(lo, hi), the same for both stored directions.  The
+    generator stores each bond as two consecutive directed edges (u, v), (v, u);
+    bond k (0-based over the set) draws items k F .. k F + F - 1."""
+    e = gs.edges.reshape(-1, 2)
+    if e.shape[0] % 2 or not np.array_equal(e[0::2, 0], e[1::2, 1]) or not np.array_equal(e[0::2, 1], e[1::2, 0]):
+        raise ValueError("bond_features: edges are not stored as consecutive (u, v), (v, u) pairs")
+    per_bond = uniform(seed, 0, (e.shape[0] // 2) * F, lo, hi).astype(np.float32).reshape(-1, F)
+    return np.ascontiguousarray(np.repeat(per_bond, 2, axis=0))
 
 
 def make_graphs(seed: int, counts: np.ndarray, g0: int = 0, max_deg: int = 4, edge_factor: float = 1.1) -> GraphSet:
@@ -232,10 +262,11 @@ def _align(x: int, a: int = 64) -> int:
 
 def write_store(path: str, gs: GraphSet) -> None:
     """Write a GraphSet as one packed store file (layout in the module docstring)."""
-    G, N, E = gs.n_graphs, gs.n_nodes, gs.n_edges
+    G, N, E, F = gs.n_graphs, gs.n_nodes, gs.n_edges, gs.F
     offs = []
     pos = HEADER_BYTES
-    for nbytes in [(G + 1) * 8, (G + 1) * 8, N, 2 * E, 4 * G]:
+    sizes = [(G + 1) * 8, (G + 1) * 8, N, 2 * E, 4 * G] + ([4 * E * F] if gs.eattr is not None else [])
+    for nbytes in sizes:
         pos = _align(pos)
         offs.append(pos)
         pos += nbytes
@@ -243,12 +274,16 @@ def write_store(path: str, gs: GraphSet) -> None:
     buf = np.zeros(total, np.uint8)
     hdr = np.zeros(HEADER_BYTES, np.uint8)
     hdr[0:8] = np.frombuffer(STORE_MAGIC, np.uint8)
-    hdr[8:16] = np.array([1, N_TYPES], "<u4").view(np.uint8)
-    hdr[16:88] = np.array([G, N, E] + offs + [total], "<i8").view(np.uint8)
+    hdr[8:16] = np.array([1 if gs.eattr is None else 2, N_TYPES], "<u4").view(np.uint8)
+    hdr[16:88] = np.array([G, N, E] + offs[:5] + [total], "<i8").view(np.uint8)
+    if gs.eattr is not None:
+        hdr[88:104] = np.array([F, offs[5]], "<i8").view(np.uint8)
     buf[:HEADER_BYTES] = hdr
     arrays = [np.ascontiguousarray(gs.node_ptr, "<i8"), np.ascontiguousarray(gs.edge_ptr, "<i8"),
               np.ascontiguousarray(gs.types, np.uint8), np.ascontiguousarray(gs.edges, np.uint8).reshape(-1),
               np.ascontiguousarray(gs.y, "<f4")]
+    if gs.eattr is not None:
+        arrays.append(np.ascontiguousarray(gs.eattr, "<f4").reshape(-1))
     for off, arr in zip(offs, arrays):
         b = arr.view(np.uint8).reshape(-1)
         buf[off:off + b.size] = b

@@ -267,8 +267,141 @@ def pin_mse_gradient():
     assert rel_norm(grad2, grad) < 1e-14
 
 
+def _bond_model(seed: int, H: int, L: int, F: int):
+    d = oracle.Dims(H=H, L=L, F=F)
+    p = synth.init_params(seed, H, L, F=F).astype(np.float64)
+    return d, p
+
+
+def _with_bonds(gs, F, seed=31):
+    gs.eattr = synth.bond_features(seed, gs, F, -1.0, 1.0)
+    return gs
+
+
+def pin_bond_features_collated_with_their_edge():
+    """Each collated edge carries the features stored for that (source, destination) pair."""
+    gs = _with_bonds(graph_set(7, 10, 3, 30), 3)
+    ids = np.array([4, 1, 9, 1, 0], np.int64)
+    st, b, _ = oracle_batch(gs, ids)
+    stored = {}
+    off = 0
+    for g in ids:
+        e0, e1 = gs.edge_ptr[g], gs.edge_ptr[g + 1]
+        for k in range(e0, e1):
+            s_, t_ = (int(v) + off for v in gs.edges[k])
+            stored[(s_, t_)] = gs.eattr[k]
+        off += int(gs.node_ptr[g + 1] - gs.node_ptr[g])
+    dst = np.repeat(np.arange(b.N), np.diff(b.row_ptr))
+    for p_ in range(b.E):
+        assert np.array_equal(b.eattr[p_], stored[(int(b.col[p_]), int(dst[p_]))])
+
+
+def pin_bond_features_zero_weights():
+    """Zero bond rows: the model with bond features equals the model without them."""
+    d, p = _bond_model(3, 8, 2, 4)
+    d0, p0 = _model(3, 8, 2)
+    assert np.array_equal(p[:p0.size], p0)
+    q = p.copy()
+    q[p0.size:] = 0.0
+    gs = graph_set(8, 9, 5, 20)
+    gs.y = synth.uniform_targets(9, 0, gs.n_graphs, 1, 10)
+    _, b0, _ = oracle_batch(gs)
+    _, b, _ = oracle_batch(_with_bonds(gs, 4))
+    assert np.array_equal(oracle.forward(d, q, b), oracle.forward(d0, p0, b0))
+    l, g, _, _ = oracle.backward(d, q, b)
+    l0, g0, _, _ = oracle.backward(d0, p0, b0)
+    assert l == l0 and np.array_equal(g[:p0.size], g0)
+
+
+def pin_bond_features_constant_is_bias_shift():
+    """Every bond carrying the same features v is a shift of the message bias by v W_E."""
+    d, p = _bond_model(4, 8, 2, 3)
+    d0 = oracle.Dims(H=8, L=2)
+    gs = graph_set(10, 8, 5, 16)
+    v = np.array([0.5, -1.25, 2.0], np.float32)
+    gs.eattr = np.tile(v, (gs.n_edges, 1))
+    _, b, _ = oracle_batch(gs)
+    gs0 = graph_set(10, 8, 5, 16)
+    _, b0, _ = oracle_batch(gs0)
+    W = oracle.split_params(d, p)
+    q = p[:oracle.param_count(d0)].copy()
+    V = oracle.split_params(d0, q)
+    for l in range(d.L):
+        V[f"msg_b{l}"][:] += v.astype(np.float64) @ W[f"edge_w{l}"]
+    assert rel_norm(oracle.forward(d, p, b), oracle.forward(d0, q, b0)) < 1e-12
+
+
+def pin_bond_features_autograd():
+    """With bond features, gradients (bond rows included) equal torch autograd (FP64)."""
+    d, p = _bond_model(5, 8, 2, 4)
+    gs = _with_bonds(graph_set(21, 6, 5, 12), 4)
+    gs.y = synth.uniform_targets(22, 0, gs.n_graphs, 1, 10)
+    _, b, _ = oracle_batch(gs)
+    x0 = synth.normal(24, 0, b.N * d.H).reshape(b.N, d.H)
+    loss, grad, dx0, _ = oracle.backward(d, p, b, x0=x0)
+    rloss, rgrad, rdx0, _ = torch_ref.loss_and_grads(d, p, b, x0)
+    assert abs(loss - rloss) <= 1e-12 * abs(rloss)
+    views, rviews = oracle.split_params(d, grad), oracle.split_params(d, rgrad)
+    for k in views:
+        if k != "emb":
+            assert rel_norm(views[k], rviews[k]) < 1e-10, k
+    assert rel_norm(dx0, rdx0) < 1e-10
+
+
+def pin_bond_features_finite_differences():
+    """Central differences of the loss w.r.t. the bond rows and the message weights."""
+    d, p = _bond_model(6, 6, 2, 3)
+    gs = _with_bonds(graph_set(25, 8, 5, 12), 3)
+    gs.y = synth.uniform_targets(26, 0, gs.n_graphs, 1, 10)
+    _, b, _ = oracle_batch(gs)
+    x0 = synth.normal(27, 0, b.N * d.H).reshape(b.N, d.H)
+    loss0, grad, _, _ = oracle.backward(d, p, b, x0=x0)
+    base = oracle.param_count(oracle.Dims(H=d.H, L=d.L))
+    coords = np.concatenate([np.arange(base, p.size), np.arange(d.T * d.H, d.T * d.H + 40)])
+    h = 1e-6
+    fd = np.empty(len(coords))
+    for n, k in enumerate(coords):
+        q = p.copy()
+        q[k] += h
+        lp = oracle.backward(d, q, b, x0=x0)[0]
+        q[k] -= 2 * h
+        lm = oracle.backward(d, q, b, x0=x0)[0]
+        fd[n] = (lp - lm) / (2 * h)
+    floor = 20 * np.finfo(np.float64).eps * abs(loss0) / h
+    assert np.all(np.abs(fd - grad[coords]) <= 1e-6 * np.abs(grad[coords]) + floor)
+
+
+def pin_bond_features_permutation_invariance():
+    """Relabelling nodes (bond features travel with their bonds) and reordering graphs."""
+    d, p = _bond_model(7, 8, 2, 2)
+    gs = _with_bonds(graph_set(28, 10, 5, 20), 2)
+    _, b, _ = oracle_batch(gs)
+    pred = oracle.forward(d, p, b)
+    rng = np.random.default_rng(3)
+    graphs, attrs = [], []
+    for g in range(gs.n_graphs):
+        n = int(gs.node_ptr[g + 1] - gs.node_ptr[g])
+        perm = rng.permutation(n)
+        t = np.empty(n, np.uint8)
+        t[perm] = gs.types[gs.node_ptr[g]:gs.node_ptr[g + 1]]
+        e = gs.edges[gs.edge_ptr[g]:gs.edge_ptr[g + 1]].astype(np.int64)
+        a = gs.eattr[gs.edge_ptr[g]:gs.edge_ptr[g + 1]]
+        bonds = rng.permutation(len(e) // 2)
+        graphs.append((t.tolist(), [(perm[e[2 * k, 0]], perm[e[2 * k, 1]]) for k in bonds]))
+        attrs.append(np.repeat(a[2 * bonds], 2, axis=0))
+    gs2 = custom_set(graphs)
+    gs2.eattr = np.ascontiguousarray(np.concatenate(attrs))
+    order = rng.permutation(gs.n_graphs)
+    _, b2, _ = oracle_batch(gs2, order)
+    assert rel_norm(oracle.forward(d, p, b2), pred[order]) < 1e-12
+
+
+BOND_PINS = [pin_bond_features_collated_with_their_edge, pin_bond_features_zero_weights,
+             pin_bond_features_constant_is_bias_shift, pin_bond_features_autograd,
+             pin_bond_features_finite_differences, pin_bond_features_permutation_invariance]
+
 ALL_PINS = [pin_collation_lexsort, pin_sum_is_dense_adjacency_matmul, pin_aggregators_scatter_reduce,
             pin_scalers_cycle_closed_form, pin_scalers_star_closed_form, pin_permutation_invariance,
             pin_pool_of_constant_graph, pin_constant_messages, pin_gradients_autograd,
             pin_gradients_autograd_continuous, pin_finite_differences, pin_adam_first_step,
-            pin_adamw_decay, pin_mse_gradient]
+            pin_adamw_decay, pin_mse_gradient] + BOND_PINS

@@ -34,6 +34,12 @@ MUTATIONS = {
     "msg_bwd_source_uses_dest_weights": ("wm(&n, w.msg_w, H + k, c) * dm", "wm(&n, w.msg_w, k, c) * dm"),
     "pool_bwd_no_division": ("dx[i * H + k] = dg[g * H + k] / (double)(b - a);", "dx[i * H + k] = dg[g * H + k];"),
     "min_ties_counted_as_max": ("nmin += (v == mn);", "nmin += (v == mx);"),
+    "bond_message_feature_index": ("(double)n->eattr[(int64_t)e * n->F + f]", "(double)n->eattr[(int64_t)e * n->F]"),
+    "bond_grad_feature_index": ("(double)eattr[e * F + fi] * dm[e * H + c]", "(double)eattr[e * F] * dm[e * H + c]"),
+    "bond_attr_in_store_order": ("eattr[p * F + f] = st_eattr[pos_sid[p] * F + f];",
+                                 "eattr[p * F + f] = st_eattr[p * F + f];"),
+    "bond_attr_left_behind_by_sort": ("col[b + 1] = col[b]; pos_sid[b + 1] = pos_sid[b]; --b;",
+                                      "col[b + 1] = col[b]; --b;"),
 }
 
 

@@ -66,3 +66,25 @@ def test_param_init_ranges():
     assert abs(emb.mean()) < 0.3 and 0.6 < emb.std() < 1.4
     msg_w = p[7 * H:7 * H + 2 * H * H]
     assert np.abs(msg_w).max() <= 1 / np.sqrt(2 * H)
+
+
+def test_store_version2_round_trip_with_bond_features(tmp_path):
+    """A set with bond features is written as a version-2 store and read back unchanged;
+    both directions of a bond carry the same features."""
+    import oracle
+    gs = synth.molecules_uniform(3, 12, 3, 20)
+    gs.y = synth.uniform_targets(4, 0, 12, 1, 10)
+    gs.eattr = synth.bond_features(5, gs, 3)
+    assert gs.eattr.shape == (gs.n_edges, 3)
+    assert np.array_equal(gs.eattr[0::2], gs.eattr[1::2])
+    path = str(tmp_path / "b.gcnn")
+    synth.write_store(path, gs)
+    raw = np.fromfile(path, np.uint8)
+    assert raw[8:12].view("<u4")[0] == 2
+    st = oracle.read_store(path)
+    assert st.F == 3
+    assert np.array_equal(st.eattr, gs.eattr)
+    assert np.array_equal(st.edges, gs.edges.reshape(-1)) and np.array_equal(st.y, gs.y)
+    sub = gs.subset([5, 2])
+    assert np.array_equal(sub.eattr, np.concatenate([gs.eattr[gs.edge_ptr[5]:gs.edge_ptr[6]],
+                                                     gs.eattr[gs.edge_ptr[2]:gs.edge_ptr[3]]]))

@@ -30,6 +30,8 @@ def _views(d, p):
     take("b1", (Hh,))
     take("w2", (Hh,))
     take("b2", (1,))
+    for l in range(L if getattr(d, "F", 0) else 0):
+        take(f"edge_w{l}", (d.F, H))
     return out
 
 
@@ -52,7 +54,11 @@ def forward(d, params: torch.Tensor, b, x0: torch.Tensor | None = None, eps: flo
     for l in range(d.L):
         mw = W[f"msg_w{l}"]
         WM = torch.cat([mw[:, :H], mw[:, H:]], dim=0)            # (2H, H) acting on [x_i ; x_j]
-        m = torch.cat([x[dst], x[src]], dim=1) @ WM + W[f"msg_b{l}"]
+        inp = [x[dst], x[src]]
+        if getattr(d, "F", 0):                                   # bond features: [x_i ; x_j ; e_ij]
+            WM = torch.cat([WM, W[f"edge_w{l}"]], dim=0)
+            inp.append(torch.from_numpy(b.eattr.astype(np.float64)))
+        m = torch.cat(inp, dim=1) @ WM + W[f"msg_b{l}"]
         z = torch.zeros(N, H, dtype=x.dtype)
         s_sum = z.scatter_reduce(0, idx, m, "sum", include_self=False)
         s_mean = z.scatter_reduce(0, idx, m, "mean", include_self=False)
