@@ -27,7 +27,9 @@
  * Model (PNA layer, the published definition with one linear message layer
  * and one linear update layer; the paper names PNA without printing it):
  *   x0_i          = emb[type_i]
- *   m_ij          = W_M [x_i ; x_j] + b_M               for each edge j -> i
+ *   m_ij          = W_M [x_i ; x_j ; e_ij] + b_M        for each edge j -> i
+ *                   (e_ij: the bond's F features, Sec. 3.1 and Table 1's
+ *                   edge attributes; F = 0: no bond term)
  *   a_i           = sum, mean, min, max, std of m_ij over j in N(i)   (5H)
  *   s_i           = [1, log(d_i+1)/delta, delta/log(d_i+1)]          (scalers)
  *   x_i'          = ReLU(W_U [x_i ; s_i (x) a_i] + b_U)               (16H -> H)
@@ -47,6 +49,8 @@
  *                 amplification{...}, attenuation{...}),
  *              upd_b[H]
  *   head: w1[H][Hh], b1[Hh], w2[Hh], b2[1]
+ *   with F bond features: 0..3 unused floats up to the next multiple of 4,
+ *   then per layer edge_w[F][H] (the bond rows of W_M)
  */
 #ifndef GCNN_H_
 #define GCNN_H_
@@ -91,7 +95,9 @@ int gcnn_version(void);
  * Packed graph store: one file holding every graph attribute as a global
  * array (the single-file analogue of the paper's schema, Sec. 4, Table 1):
  * node_ptr[G+1], edge_ptr[G+1] (int64 offsets), types[N] (uint8 atom type),
- * edges[E][2] (uint8 local source, destination), y[G] (float32 target).
+ * edges[E][2] (uint8 local source, destination), y[G] (float32 target);
+ * version-2 files add edge_attr[E][F] (float32 bond features, F <= 16), and
+ * both directions of a bond must carry bitwise-equal features.
  * Graphs must have 1..255 nodes and at most 1024 directed edges, local ids
  * < n; each undirected bond is stored as two directed edges.  The file is
  * validated once at open (GCNN_EFORMAT on any violation).  A store is
@@ -105,6 +111,8 @@ int gcnn_store_open(const char *path, gcnn_store **out);
 int gcnn_store_close(gcnn_store *st);
 /* Totals of the whole store. */
 int gcnn_store_info(const gcnn_store *st, int64_t *n_graphs, int64_t *n_nodes, int64_t *n_edges);
+/* Bond features per edge (0 for a version-1 store). */
+int gcnn_store_edge_features(const gcnn_store *st, int32_t *n_features);
 /* Node and edge totals of the batch graph_ids[0..n) (host ids). */
 int gcnn_store_batch_size(const gcnn_store *st, const int64_t *graph_ids, int64_t n,
                           int64_t *n_nodes, int64_t *n_edges);
@@ -137,6 +145,9 @@ typedef struct gcnn_config {
   double beta1, beta2;  /* Adam moment decays (0.9, 0.999)                     */
   double adam_eps;      /* Adam epsilon (1e-8)                                 */
   double weight_decay;  /* decoupled (AdamW) weight decay (0)                  */
+  int32_t edge_features;  /* F bond features per edge, 0..16 (0); a store fed
+                             to the context must carry exactly F           */
+  int32_t reserved0;
 } gcnn_config;
 
 typedef struct gcnn_ctx gcnn_ctx;
@@ -183,6 +194,9 @@ typedef struct gcnn_batch {
   const float *att;         /* (device) [N]   delta/log(max(d,1)+1) as float   */
   const uint8_t *types;     /* (device) [N]   atom type                        */
   const float *y;           /* (device) [G]   target                           */
+  const float *edge_attr;   /* (device) [E] rows of bond features per edge
+                               slot, row stride F rounded up to a multiple
+                               of 4 floats (NULL when F = 0)                  */
 } gcnn_batch;
 
 /* Collate graphs graph_ids[0..n_graphs) (host ids) of `st` on the device.
@@ -341,7 +355,8 @@ typedef struct gcnn_request {
 
 /* Create a server for the model in `model` (its current parameters are copied
  * to every slot; later changes to `model` are not seen).  Starts the
- * scheduler thread. */
+ * scheduler thread.  Requests carry no bond features: a model with
+ * edge_features > 0 is refused (GCNN_EINVAL). */
 int gcnn_serve_create(const gcnn_ctx *model, const gcnn_serve_config *cfg, gcnn_server **out);
 /* Queue a request (the library copies it; the caller may free it on return).
  * GCNN_EAGAIN: admission refused (queue full), retry later. */

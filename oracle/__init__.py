@@ -263,7 +263,9 @@ def split_params(d: Dims, p):
     take("b1", (Hh,))
     take("w2", (Hh,))
     take("b2", (1,))
-    for l in range(L if d.F else 0):
-        take(f"edge_w{l}", (d.F, H))
+    if d.F:
+        k = (k + 3) // 4 * 4          # bond rows start at a multiple of 4 floats
+        for l in range(L):
+            take(f"edge_w{l}", (d.F, H))
     assert k == p.size
     return out

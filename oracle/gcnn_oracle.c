@@ -44,7 +44,8 @@
  *              msg_b[H], upd_w[16H][H] (rows: x_i, then scaler-major blocks
  *              id{sum,mean,min,max,std}, amp{...}, att{...}), upd_b[H]
  *   head: w1[H][Hh], b1[Hh], w2[Hh], b2
- *   with F bond features, per layer: edge_w[F][H] (the bond rows of W_M)
+ *   with F bond features: 0..3 unused floats up to the next multiple of 4,
+ *   then per layer edge_w[F][H] (the bond rows of W_M)
  * so that W_M(k, c) for the stacked input [x_i ; x_j ; e_ij] is msg_w[k][c]
  * for k < H, msg_w[k-H][H+c] for H <= k < 2H and edge_w[k-2H][c] after.
  */
@@ -192,8 +193,14 @@ static int64_t layer_size(int H) {
 
 static int64_t head_size(int H, int Hh) { return (int64_t)H * Hh + Hh + Hh + 1; }
 
+/* first bond row: after the head, rounded up to a multiple of 4 floats */
+static int64_t bonds_offset(int H, int L, int T, int Hh) {
+  return ((int64_t)T * H + L * layer_size(H) + head_size(H, Hh) + 3) / 4 * 4;
+}
+
 int64_t oracle_param_count(int H, int L, int T, int Hh, int F) {
-  return (int64_t)T * H + L * layer_size(H) + head_size(H, Hh) + (int64_t)L * F * H;
+  if (F == 0) return (int64_t)T * H + L * layer_size(H) + head_size(H, Hh);
+  return bonds_offset(H, L, T, Hh) + (int64_t)L * F * H;
 }
 
 static layer_t layer_at(const net_t *n, const double *p, int l) {
@@ -203,8 +210,7 @@ static layer_t layer_at(const net_t *n, const double *p, int l) {
   w.msg_b = w.msg_w + (int64_t)n->H * 2 * n->H;
   w.upd_w = w.msg_b + n->H;
   w.upd_b = w.upd_w + (int64_t)16 * n->H * n->H;
-  w.edge_w = p + (int64_t)n->T * n->H + n->L * layer_size(n->H) + head_size(n->H, n->Hh) +
-             (int64_t)l * n->F * n->H;
+  w.edge_w = p + bonds_offset(n->H, n->L, n->T, n->Hh) + (int64_t)l * n->F * n->H;
   return w;
 }
 

@@ -46,13 +46,14 @@ class Config(ctypes.Structure):
                 ("max_edges", ctypes.c_int32), ("precision", ctypes.c_int32), ("recompute", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("delta", ctypes.c_double), ("std_eps", ctypes.c_double),
                 ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("adam_eps", ctypes.c_double),
-                ("weight_decay", ctypes.c_double)]
+                ("weight_decay", ctypes.c_double), ("edge_features", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
 
 
 class BatchStruct(ctypes.Structure):
     _fields_ = [("n_graphs", ctypes.c_int32), ("n_nodes", ctypes.c_int32), ("n_edges", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)] + [(n, ctypes.c_void_p) for n in (
-                    "node_off", "edge_off", "graph_id", "row_ptr", "col", "rev", "deg", "amp", "att", "types", "y")]
+                    "node_off", "edge_off", "graph_id", "row_ptr", "col", "rev", "deg", "amp", "att", "types", "y",
+                    "edge_attr")]
 
 
 class ServeConfig(ctypes.Structure):
@@ -78,6 +79,7 @@ def _load() -> ctypes.CDLL:
         "gcnn_store_open": (i32, [ctypes.c_char_p, P(vp)]),
         "gcnn_store_close": (i32, [vp]),
         "gcnn_store_info": (i32, [vp, P(i64), P(i64), P(i64)]),
+        "gcnn_store_edge_features": (i32, [vp, P(i32)]),
         "gcnn_store_batch_size": (i32, [vp, vp, i64, P(i64), P(i64)]),
         "gcnn_store_delta": (i32, [vp, vp, i64, P(f64)]),
         "gcnn_store_set_targets": (i32, [vp, vp, i64]),
@@ -175,6 +177,9 @@ class Store:
         g, n, e = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(lib.gcnn_store_info(self._h, ctypes.byref(g), ctypes.byref(n), ctypes.byref(e)))
         self.n_graphs, self.n_nodes, self.n_edges = g.value, n.value, e.value
+        f = ctypes.c_int32()
+        _check(lib.gcnn_store_edge_features(self._h, ctypes.byref(f)))
+        self.edge_features = f.value
 
     @property
     def handle(self):
@@ -264,6 +269,10 @@ class Batch:
         """A torch view of one of the batch's device arrays (valid until the next collate)."""
         import torch
         G, N, E = self.n_graphs, self.n_nodes, self.n_edges
+        if name == "edge_attr":  # E rows of round_up(F, 4) floats; the first F columns hold the features
+            F = self.owner.cfg.edge_features
+            F4 = (F + 3) // 4 * 4
+            return _wrap_device(self.s.edge_attr, E * F4, torch.float32).view(E, F4)[:, :F]
         spec = {"node_off": (G + 1, torch.int32), "edge_off": (G + 1, torch.int32), "graph_id": (N, torch.int32),
                 "row_ptr": (N + 1, torch.int32), "col": (E, torch.int32), "rev": (E, torch.int32),
                 "deg": (N, torch.int32), "amp": (N, torch.float32), "att": (N, torch.float32),

@@ -51,17 +51,44 @@ __device__ __forceinline__ int source(const int *__restrict__ col, int e, int N,
   return j;
 }
 
-// m_ij = P_i + Q_j for the 4 channels at c (Q taken as 0 for an invalid source)
-__device__ __forceinline__ float4 message(const float *__restrict__ PQ, int j, int H, int c, float4 P) {
-  return j >= 0 ? add4(P, ld4(PQ + (size_t)j * 2 * H + H + c)) : P;
+// The bond term of the message (Sec. 3.1 bond properties; Table 1 edge
+// attributes): R_e = sum_f e_e[f] W_E[f] for edge slot e, with the edge
+// features in slot order (attr, E rows of round_up(F, 4) floats) and the
+// layer's bond rows of W_M (w, F x H).  F = 0 (EDGE = false) drops the term.
+struct Bonds {
+  const float *attr, *w;
+  int F;
+};
+
+// rows of attr are round_up(F, 4) floats apart
+__device__ __forceinline__ float4 bond_term(const Bonds &b, int H, int e, int c) {
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  const size_t row = (size_t)e * ((b.F + 3) & ~3);
+  for (int f = 0; f < b.F; ++f) {
+    const float a = b.attr[row + f];
+    const float4 w = ld4(b.w + (size_t)f * H + c);
+    r.x = fmaf(a, w.x, r.x); r.y = fmaf(a, w.y, r.y); r.z = fmaf(a, w.z, r.z); r.w = fmaf(a, w.w, r.w);
+  }
+  return r;
 }
 
-// Messages of the first kCache edges of node i's row from their sources j[]:
-// every Q row is loaded unconditionally (row i stands in for a source out of
-// range, whose message is then P alone), so the loads are all in flight at
-// once; returns whether a source was out of range.
+// m_ij = (P_i + Q_j) + R_e for the 4 channels at c, edge slot e (Q taken as 0
+// for an invalid source)
+template <bool EDGE>
+__device__ __forceinline__ float4 message(const float *__restrict__ PQ, int j, int H, int c, float4 P, const Bonds &b,
+                                          int e) {
+  const float4 m = j >= 0 ? add4(P, ld4(PQ + (size_t)j * 2 * H + H + c)) : P;
+  return EDGE ? add4(m, bond_term(b, H, e, c)) : m;
+}
+
+// Messages of the first kCache edges (slots r0 + k, clamped into the row) of
+// node i's row from their sources j[]: every Q row is loaded unconditionally
+// (row i stands in for a source out of range, whose message is then P alone,
+// plus its bond term), so the loads are all in flight at once; returns
+// whether a source was out of range.
+template <bool EDGE>
 __device__ __forceinline__ bool gather_first(const float *__restrict__ PQ, const int (&j)[kCache], int i, int N, int H,
-                                             int c, float4 P, float4 (&mc)[kCache]) {
+                                             int c, float4 P, float4 (&mc)[kCache], const Bonds &b, int r0, int r1) {
   bool bad = false;
 #pragma unroll
   for (int k = 0; k < kCache; ++k) {
@@ -69,6 +96,10 @@ __device__ __forceinline__ bool gather_first(const float *__restrict__ PQ, const
     bad |= !ok;
     const float4 q = ld4(PQ + (size_t)(ok ? j[k] : i) * 2 * H + H + c);
     mc[k] = ok ? add4(P, q) : P;
+  }
+  if (EDGE) {
+#pragma unroll
+    for (int k = 0; k < kCache; ++k) mc[k] = add4(mc[k], bond_term(b, H, min(r0 + k, r1 - 1), c));
   }
   return bad;
 }
@@ -80,12 +111,12 @@ __device__ __forceinline__ void acc_sq(float4 &v, float4 m, float4 mean) {
 
 // F32 / B16: whether the FP32 aggregates / the BF16 scaled operand are
 // written (one instantiation per output set keeps the other's code out)
-template <bool F32, bool B16>
+template <bool F32, bool B16, bool EDGE>
 __global__ void __launch_bounds__(kThreads, 4)
 aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row_ptr,
                      const int *__restrict__ col, const float *__restrict__ PQ,
                      float *__restrict__ agg, float eps, unsigned *err, uint16_t *__restrict__ S16, int ld16,
-                     const float *__restrict__ amp, const float *__restrict__ att) {
+                     const float *__restrict__ amp, const float *__restrict__ att, Bonds bonds) {
   pdl_entry(GCNN_K_AGG_FWD);
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
@@ -113,7 +144,7 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
   for (int k = 0; k < kCache; ++k) j[k] = col[min(r0 + k, r1 - 1)];
   const float4 P = ld4(PQ + (size_t)i * 2 * H + c);
   float4 mc[kCache];
-  if (gather_first(PQ, j, i, N, H, c, P, mc)) flag(err, kErrIndex);
+  if (gather_first<EDGE>(PQ, j, i, N, H, c, P, mc, bonds, r0, r1)) flag(err, kErrIndex);
   float4 s = z;
   float4 mn = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX);
   float4 mx = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX);
@@ -125,14 +156,15 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
 #pragma unroll
   for (int k = 0; k < kCache; ++k)
     if (k < d) take(mc[k]);
-  for (int e = r0 + kCache; e < r1; ++e) take(message(PQ, source(col, e, N, err), H, c, P));
+  for (int e = r0 + kCache; e < r1; ++e) take(message<EDGE>(PQ, source(col, e, N, err), H, c, P, bonds, e));
   const float df = (float)d;
   const float4 mean = make_float4(s.x / df, s.y / df, s.z / df, s.w / df);
   float4 v = z;  // two-pass variance
 #pragma unroll
   for (int k = 0; k < kCache; ++k)
     if (k < d) acc_sq(v, mc[k], mean);
-  for (int e = r0 + kCache; e < r1; ++e) acc_sq(v, message(PQ, source(col, e, N, err), H, c, P), mean);
+  for (int e = r0 + kCache; e < r1; ++e)
+    acc_sq(v, message<EDGE>(PQ, source(col, e, N, err), H, c, P, bonds, e), mean);
   float4 sd;
   sd.x = sqrtf(fmaxf(v.x / df, 0.f) + eps);
   sd.y = sqrtf(fmaxf(v.y / df, 0.f) + eps);
@@ -174,12 +206,12 @@ constexpr int kEdgeThreads = 128;  // five blocks of 128 per SM at this kernel's
 // and hands each edge's gradient to to_slot(reverse slot, g); returns dP_i.
 // STATS: 1 = statistics stored in agg, 0 = recomputed, -1 = decided at run
 // time by agg != null (one code path for both, fewer registers)
-template <int STATS, class ToSlot>
+template <int STATS, bool EDGE, class ToSlot>
 __device__ __forceinline__ float4 node_backward(int i, int c, int H, int N, int E, const int *__restrict__ row_ptr,
                                                 const int *__restrict__ col, const int *__restrict__ rev,
                                                 const float *__restrict__ PQ, const float *__restrict__ agg,
                                                 const float *__restrict__ dagg, float eps, unsigned *err,
-                                                ToSlot to_slot) {
+                                                const Bonds &bonds, ToSlot to_slot) {
   const bool STORED = STATS < 0 ? agg != nullptr : STATS == 1;
   const int r0 = row_ptr[i], r1 = row_ptr[i + 1];
   const int d = r1 - r0;
@@ -208,7 +240,7 @@ __device__ __forceinline__ float4 node_backward(int i, int c, int H, int N, int 
   const float4 dsum = ld4(da + 0 * H), dmean = ld4(da + 1 * H), dmin = ld4(da + 2 * H);
   const float4 dmax = ld4(da + 3 * H), dstd = ld4(da + 4 * H);
   float4 mc[kCache];
-  if (gather_first(PQ, j, i, N, H, c, P, mc)) flag(err, kErrIndex);
+  if (gather_first<EDGE>(PQ, j, i, N, H, c, P, mc, bonds, r0, r1)) flag(err, kErrIndex);
   // the forward's statistics: stored, or recomputed in the forward's order
   if (!STORED) {
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -222,7 +254,7 @@ __device__ __forceinline__ float4 node_backward(int i, int c, int H, int N, int 
 #pragma unroll
     for (int k = 0; k < kCache; ++k)
       if (k < d) take(mc[k]);
-    for (int e = r0 + kCache; e < r1; ++e) take(message(PQ, source(col, e, N, err), H, c, P));
+    for (int e = r0 + kCache; e < r1; ++e) take(message<EDGE>(PQ, source(col, e, N, err), H, c, P, bonds, e));
     mean = make_float4(s.x / df, s.y / df, s.z / df, s.w / df);
   }
   float4 nmin = make_float4(0.f, 0.f, 0.f, 0.f), nmax = nmin, var = nmin;
@@ -234,7 +266,7 @@ __device__ __forceinline__ float4 node_backward(int i, int c, int H, int N, int 
 #pragma unroll
   for (int k = 0; k < kCache; ++k)
     if (k < d) count(mc[k]);
-  for (int e = r0 + kCache; e < r1; ++e) count(message(PQ, source(col, e, N, err), H, c, P));
+  for (int e = r0 + kCache; e < r1; ++e) count(message<EDGE>(PQ, source(col, e, N, err), H, c, P, bonds, e));
   var.x /= df; var.y /= df; var.z /= df; var.w /= df;
   if (!STORED) {
     sd.x = sqrtf(fmaxf(var.x, 0.f) + eps);
@@ -263,16 +295,19 @@ __device__ __forceinline__ float4 node_backward(int i, int c, int H, int N, int 
 #pragma unroll
   for (int k = 0; k < kCache; ++k)
     if (k < d) emit(re[k], mc[k]);
-  for (int e = r0 + kCache; e < r1; ++e) emit(rev[e], message(PQ, source(col, e, N, err), H, c, P));
+  for (int e = r0 + kCache; e < r1; ++e)
+    emit(rev[e], message<EDGE>(PQ, source(col, e, N, err), H, c, P, bonds, e));
   return dP;
 }
 
+template <bool EDGE>
 __global__ void __launch_bounds__(kEdgeThreads)
 aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *__restrict__ row_ptr,
                           const int *__restrict__ col, const int *__restrict__ rev,
                           const float *__restrict__ PQ, const float *__restrict__ agg,
                           const float *__restrict__ dagg, float *__restrict__ dPQ,
-                          float *__restrict__ dm, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16, float eps) {
+                          float *__restrict__ dm, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16, float eps,
+                          Bonds bonds) {
   pdl_entry(GCNN_K_AGG_BWD_EDGE);
   const int H4 = H >> 2;
   const int N = min(n_cap, dims.nodes(n_cap));
@@ -280,7 +315,8 @@ aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)N * H4) return;
   const int i = (int)(t / H4), c = (int)(t % H4) * 4;
-  const float4 dP = node_backward<-1>(i, c, H, N, E, row_ptr, col, rev, PQ, agg, dagg, eps, err, [&](int r, float4 g) {
+  const float4 dP = node_backward<-1, EDGE>(i, c, H, N, E, row_ptr, col, rev, PQ, agg, dagg, eps, err, bonds,
+                                             [&](int r, float4 g) {
     if (r >= 0 && r < E) st4(dm + (size_t)r * H + c, g);
     else flag(err, kErrIndex);
   });
@@ -362,7 +398,8 @@ aggregate_bwd_fused_kernel(int g_cap, int n_cap, int e_cap, const int *__restric
   const int rows = kFusedThreads / w, row = threadIdx.x / w, cc = threadIdx.x % w, c = (c0 + cc) * 4;
   const int n_end = row < rows ? n1 : n0;
   for (int i = n0 + row; i < n_end; i += rows) {
-    const float4 dP = node_backward<STORED ? 1 : 0>(i, c, H, N, E, row_ptr, col, rev, PQ, agg, dagg, eps, err, [&](int r, float4 g) {
+    const float4 dP = node_backward<STORED ? 1 : 0, false>(i, c, H, N, E, row_ptr, col, rev, PQ, agg, dagg, eps, err,
+                                                           Bonds{nullptr, nullptr, 0}, [&](int r, float4 g) {
       if (r < e0 || r >= e1) flag(err, kErrIndex);  // an edge leaving the graph
       else if (in_smem) s_dm[(r - e0) * cs4 + cc] = g;
       else st4(dm + (size_t)r * H + c, g);
@@ -411,26 +448,35 @@ aggregate_bwd_gather_kernel(int n_cap, int e_cap, int H, DevDims dims,
 
 int launch_aggregate_fwd(int n_nodes, int H, DevDims dims, const int *row_ptr, const int *col,
                          const float *PQ, float *agg, float eps, unsigned *err, cudaStream_t s,
-                         uint16_t *S16, int ld16, const float *amp, const float *att) {
+                         uint16_t *S16, int ld16, const float *amp, const float *att, const float *eattr,
+                         const float *wE, int F) {
   if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
+  if (F < 0 || (F > 0 && (!eattr || !wE))) return set_error(GCNN_EINVAL, "aggregate: bond features without data");
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
-  auto kernel = agg ? (S16 ? aggregate_fwd_kernel<true, true> : aggregate_fwd_kernel<true, false>)
-                    : (S16 ? aggregate_fwd_kernel<false, true> : aggregate_fwd_kernel<false, false>);
+  using K = void (*)(int, int, DevDims, const int *, const int *, const float *, float *, float, unsigned *,
+                     uint16_t *, int, const float *, const float *, Bonds);
+  static const K table[8] = {aggregate_fwd_kernel<false, false, false>, aggregate_fwd_kernel<false, true, false>,
+                             aggregate_fwd_kernel<true, false, false>,  aggregate_fwd_kernel<true, true, false>,
+                             aggregate_fwd_kernel<false, false, true>,  aggregate_fwd_kernel<false, true, true>,
+                             aggregate_fwd_kernel<true, false, true>,   aggregate_fwd_kernel<true, true, true>};
+  const K kernel = table[(F > 0 ? 4 : 0) + (agg ? 2 : 0) + (S16 ? 1 : 0)];
   GCNN_TRY(launch(kernel, ceil_div(work, kThreads), kThreads, 0, s, n_nodes, H, dims, row_ptr, col, PQ, agg, eps, err,
-                  S16, ld16, amp, att));
+                  S16, ld16, amp, att, Bonds{eattr, wE, F}));
   return GCNN_OK;
 }
 
 int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const int *row_ptr,
                          const int *col, const int *rev, const float *PQ, const float *agg,
                          const float *dagg, float *dPQ, float *scratch, float eps, unsigned *err,
-                         cudaStream_t s, uint16_t *dPQ16, int ld16) {
+                         cudaStream_t s, uint16_t *dPQ16, int ld16, const float *eattr, const float *wE, int F) {
   if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
+  if (F < 0 || (F > 0 && (!eattr || !wE))) return set_error(GCNN_EINVAL, "aggregate: bond features without data");
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
-  GCNN_TRY(launch(aggregate_bwd_edge_kernel, ceil_div(work, kEdgeThreads), kEdgeThreads, 0, s, n_nodes, n_edges, H, dims,
-                  row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, err, dPQ16, ld16, eps));
+  GCNN_TRY(launch(F > 0 ? aggregate_bwd_edge_kernel<true> : aggregate_bwd_edge_kernel<false>, ceil_div(work, kEdgeThreads),
+                  kEdgeThreads, 0, s, n_nodes, n_edges, H, dims, row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, err,
+                  dPQ16, ld16, eps, Bonds{eattr, wE, F}));
   GCNN_TRY(launch(aggregate_bwd_gather_kernel, ceil_div(work, kThreads), kThreads, 0, s, n_nodes, n_edges, H, dims,
                   row_ptr, (const float *)scratch, dPQ, err, dPQ16, ld16));
   return GCNN_OK;
@@ -445,12 +491,14 @@ bool aggregate_bwd_uses_fused(int n_edges) {
 int launch_aggregate_bwd_graphs(int n_graphs, int n_nodes, int n_edges, int H, DevDims dims, const int *node_off,
                                 const int *row_ptr, const int *col, const int *rev, const float *PQ,
                                 const float *agg, const float *dagg, float *dPQ, float *scratch, int *chunks,
-                                float eps, unsigned *err, cudaStream_t s, uint16_t *dPQ16, int ld16) {
+                                float eps, unsigned *err, cudaStream_t s, uint16_t *dPQ16, int ld16,
+                                const float *eattr, const float *wE, int F) {
   if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
   if (n_nodes <= 0 || n_graphs <= 0) return GCNN_OK;
-  if (!aggregate_bwd_uses_fused(n_edges))
+  // with bond features the per-edge gradients are kept: their weight gradient reads them
+  if (F > 0 || !aggregate_bwd_uses_fused(n_edges))
     return launch_aggregate_bwd(n_nodes, n_edges, H, dims, row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, eps, err, s,
-                                dPQ16, ld16);
+                                dPQ16, ld16, eattr, wE, F);
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {

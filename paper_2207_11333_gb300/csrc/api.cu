@@ -48,7 +48,10 @@ int64_t layer_size_of(int64_t H) { return 2 * H * H + H + 16 * H * H + H; }
 
 int64_t param_count_of(const gcnn_config &c) {
   const int64_t H = c.hidden, Hh = c.head_hidden;
-  return (int64_t)c.n_types * H + (int64_t)c.layers * layer_size_of(H) + H * Hh + 2 * Hh + 1;
+  const int64_t base = (int64_t)c.n_types * H + (int64_t)c.layers * layer_size_of(H) + H * Hh + 2 * Hh + 1;
+  if (c.edge_features == 0) return base;
+  // bond rows start at a multiple of 4 floats (16-byte rows for vector loads)
+  return (base + 3) / 4 * 4 + (int64_t)c.layers * c.edge_features * H;
 }
 
 int check_config(const gcnn_config *c) {
@@ -66,6 +69,8 @@ int check_config(const gcnn_config *c) {
   if (c->precision != GCNN_PREC_FP32 && c->precision != GCNN_PREC_BF16)
     return set_error(GCNN_EINVAL, "precision must be GCNN_PREC_FP32 or GCNN_PREC_BF16 (got %d)", c->precision);
   if (!(c->delta > 0.0) || !(c->std_eps >= 0.0)) return set_error(GCNN_EINVAL, "delta must be > 0, std_eps >= 0");
+  if (c->edge_features < 0 || c->edge_features > 16)
+    return set_error(GCNN_EINVAL, "edge_features must be in [0, 16] (got %d)", c->edge_features);
   return GCNN_OK;
 }
 
@@ -80,9 +85,10 @@ int make_scaler_table(gcnn_ctx *c) {
   return GCNN_OK;
 }
 
-size_t stage_bytes_of(int Gc, int Nc, int Ec) {
-  // mini-store: node_ptr, edge_ptr (i64 [G+1]), y (f32 [G]), types (u8 [N]), edges (u8 [2E]), ids
-  return 3 * 8 * (size_t)(Gc + 1) + 4 * (size_t)Gc + (size_t)Nc + 2 * (size_t)Ec + 4 * 64;
+size_t stage_bytes_of(int Gc, int Nc, int Ec, int F) {
+  // mini-store: node_ptr, edge_ptr (i64 [G+1]), y (f32 [G]), types (u8 [N]), edges (u8 [2E]),
+  // bond features (f32 [E][F]), ids
+  return 3 * 8 * (size_t)(Gc + 1) + 4 * (size_t)Gc + (size_t)Nc + 2 * (size_t)Ec + 4 * (size_t)Ec * F + 5 * 64;
 }
 
 void destroy_ctx(gcnn_ctx *c) {
@@ -165,6 +171,12 @@ int gcnn_store_info(const gcnn_store *st, int64_t *g, int64_t *n, int64_t *e) {
   return GCNN_OK;
 }
 
+int gcnn_store_edge_features(const gcnn_store *st, int32_t *f) {
+  if (!st || !f) return set_error(GCNN_EINVAL, "null argument");
+  *f = st->F;
+  return GCNN_OK;
+}
+
 int gcnn_store_batch_size(const gcnn_store *st, const int64_t *ids, int64_t n, int64_t *nn, int64_t *ne) {
   if (!st || (!ids && n > 0) || n < 0 || !nn || !ne) return set_error(GCNN_EINVAL, "store_batch_size: bad arguments");
   return store_batch_size(st, ids, n, nn, ne);
@@ -229,6 +241,8 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
     wsf = std::max(wsf, gemm_simt_workspace_floats(n, kAgg * h, 3 * h));
     wsf = std::max(wsf, gemm_simt_workspace_floats(h + 1, 2 * h, n));
     wsf = std::max(wsf, gemm_simt_workspace_floats(n, h, 3 * h));
+    if (cfg->edge_features > 0)  // bond rows of W_M: e^T dm over the edges
+      wsf = std::max(wsf, gemm_simt_workspace_floats(cfg->edge_features, h, (int)Ec));
     if (cfg->precision == GCNN_PREC_BF16) {
       const int r64 = (h + 63) / 64 * 64, r3 = (3 * h + 63) / 64 * 64, r16 = (16 * h + 63) / 64 * 64;
       wsf = std::max(wsf, gemm_tc_workspace_floats(n, 2 * h, r64));
@@ -251,7 +265,9 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   const size_t o_rev = cv.take<int>(Ec), o_deg = cv.take<int>(Nc), o_amp = cv.take<float>(Nc);
   const size_t o_att = cv.take<float>(Nc), o_y = cv.take<float>(Gc), o_types = cv.take<uint8_t>(Nc);
   const size_t o_dims = cv.take<int>(4), o_ids = cv.take<int64_t>(Gc);
-  c->stage_bytes = stage_bytes_of((int)Gc, (int)Nc, (int)Ec);
+  const int F4 = (cfg->edge_features + 3) & ~3;  // 16-byte rows of bond features
+  const size_t o_eattr = cv.take<float>((size_t)Ec * F4);
+  c->stage_bytes = stage_bytes_of((int)Gc, (int)Nc, (int)Ec, cfg->edge_features);
   const size_t o_stage = cv.take<char>(c->stage_bytes);
   const size_t o_xs = cv.take<float>((L + 1) * Nc * H), o_pq = cv.take<float>(L * Nc * 2 * H);
   const bool fp32_agg = cfg->precision != GCNN_PREC_BF16;  // the BF16 path recomputes them
@@ -289,6 +305,8 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   c->bb.rev = (int *)(b + o_rev); c->bb.deg = (int *)(b + o_deg); c->bb.amp = (float *)(b + o_amp);
   c->bb.att = (float *)(b + o_att); c->bb.y = (float *)(b + o_y); c->bb.types = (uint8_t *)(b + o_types);
   c->bb.dims = (int *)(b + o_dims); c->ids_dev = (int64_t *)(b + o_ids);
+  c->bb.eattr = cfg->edge_features > 0 ? (float *)(b + o_eattr) : nullptr;
+  c->bb.eattr_ld = F4;
   c->stage_dev = b + o_stage;
   c->xs = (float *)(b + o_xs); c->PQ = (float *)(b + o_pq); c->agg = fp32_agg ? (float *)(b + o_agg) : nullptr;
   c->pooled = (float *)(b + o_pool); c->z1 = (float *)(b + o_z1); c->pred = (float *)(b + o_pred);

@@ -26,6 +26,13 @@ void fill_batch(const gcnn_ctx *c, int G, int64_t N, int64_t E, gcnn_batch *out)
   out->att = c->bb.att;
   out->types = c->bb.types;
   out->y = c->bb.y;
+  out->edge_attr = c->cfg.edge_features > 0 ? c->bb.eattr : nullptr;
+}
+
+int check_features(const gcnn_ctx *c, const gcnn_store *st) {
+  if (st->F != c->cfg.edge_features)
+    return set_error(GCNN_EINVAL, "store has %d bond features per edge, the model %d", st->F, c->cfg.edge_features);
+  return GCNN_OK;
 }
 
 int check_caps(const gcnn_ctx *c, int64_t G, int64_t N, int64_t E) {
@@ -46,6 +53,7 @@ int claim_stage(gcnn_ctx *c, int q) {
 
 int ctx_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n, gcnn_batch *out) {
   int64_t N = 0, E = 0;
+  GCNN_TRY(check_features(c, st));
   GCNN_TRY(check_caps(c, n, 0, 0));
   GCNN_TRY(store_batch_size(st, ids, n, &N, &E));
   GCNN_TRY(check_caps(c, n, N, E));
@@ -71,7 +79,10 @@ int ctx_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n
     const size_t o_y = o;  o = align_up(o + 4 * (size_t)n, 16);
     const size_t o_t = o;  o = align_up(o + (size_t)N, 16);
     const size_t o_e = o;  o = align_up(o + 2 * (size_t)E, 16);
+    const int F = st->F;
+    const size_t o_a = o;  o = align_up(o + 4 * (size_t)E * F, 16);
     if (o > c->stage_bytes) return set_error(GCNN_EINVAL, "staging buffer too small");
+    float *at = reinterpret_cast<float *>(h + o_a);
     int64_t *np = reinterpret_cast<int64_t *>(h + o_np), *ep = reinterpret_cast<int64_t *>(h + o_ep);
     float *y = reinterpret_cast<float *>(h + o_y);
     uint8_t *ty = reinterpret_cast<uint8_t *>(h + o_t), *ed = reinterpret_cast<uint8_t *>(h + o_e);
@@ -83,6 +94,7 @@ int ctx_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n
       const int64_t ne = st->edge_ptr[id + 1] - st->edge_ptr[id];
       memcpy(ty + np[g], st->types + st->node_ptr[id], (size_t)nn);
       memcpy(ed + 2 * ep[g], st->edges + 2 * st->edge_ptr[id], 2 * (size_t)ne);
+      if (F > 0) memcpy(at + ep[g] * F, st->eattr + st->edge_ptr[id] * F, sizeof(float) * (size_t)ne * F);
       y[g] = st->y[id];
       np[g + 1] = np[g] + nn;
       ep[g + 1] = ep[g] + ne;
@@ -93,7 +105,8 @@ int ctx_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n
     const char *d = c->stage_dev;
     StoreView v{reinterpret_cast<const int64_t *>(d + o_np), reinterpret_cast<const int64_t *>(d + o_ep),
                 reinterpret_cast<const uint8_t *>(d + o_t), reinterpret_cast<const uint8_t *>(d + o_e),
-                reinterpret_cast<const float *>(d + o_y)};
+                reinterpret_cast<const float *>(d + o_y), F > 0 ? reinterpret_cast<const float *>(d + o_a) : nullptr,
+                F};
     PhaseScope ps(c, GCNN_PHASE_COLLATE);
     GCNN_TRY(launch_collate(n, nullptr, v, c->bb, c->scal_tab, c->Nc, c->Ec, c->err, c->stream));
   }
@@ -108,6 +121,7 @@ int ctx_collate_range(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t 
   if (first < 0 || first + count > (int64_t)c->order_host.size())
     return set_error(GCNN_EINVAL, "collate_range: range outside the order");
   int64_t N = 0, E = 0;
+  GCNN_TRY(check_features(c, st));
   GCNN_TRY(check_caps(c, count, 0, 0));
   GCNN_TRY(store_batch_size(st, c->order_host.data() + first, count, &N, &E));
   GCNN_TRY(check_caps(c, count, N, E));

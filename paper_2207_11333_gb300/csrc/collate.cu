@@ -8,7 +8,8 @@
 //                         count (shared atomics), warp scan -> row_ptr, then a
 //                         rank sort of the graph's edges by (destination,
 //                         source, store order) -> col, and the reverse-edge
-//                         slot -> rev; degree scalers from a table
+//                         slot -> rev; degree scalers from a table; the
+//                         edges' bond features follow them to their slots
 //
 // Results are bit-identical to a sequential stable sort by (dst, src): every
 // position is computed from counts, never from the order of atomics.
@@ -157,6 +158,7 @@ collate_graph_kernel(int G, const int64_t *__restrict__ ids, StoreView st, Batch
     const int pos = eoff + s_start[w][d] + rank;
     b.col[pos] = noff + s;
     b.rev[pos] = has_rev ? eoff + s_start[w][s] + rrank : -1;
+    for (int f = 0; f < st.F; ++f) b.eattr[(size_t)pos * b.eattr_ld + f] = st.eattr[(ep0 + k) * st.F + f];
   }
 }
 

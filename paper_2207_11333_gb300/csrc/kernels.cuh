@@ -13,6 +13,8 @@ struct StoreView {
   const uint8_t *types;     // [N]
   const uint8_t *edges;     // [2E] local (src, dst)
   const float *y;           // [G]
+  const float *eattr;       // [E][F] bond features (F = 0: nullptr)
+  int F;
 };
 
 // Writable batch arrays in the context arena.
@@ -21,6 +23,8 @@ struct BatchBuf {
   float *amp, *att, *y;
   uint8_t *types;
   int *dims;  // {G, N, E, 0}
+  float *eattr;  // [E][eattr_ld] bond features in slot order (F = 0: unused)
+  int eattr_ld;  // row stride: F rounded up to a multiple of 4 (16-byte rows)
 };
 
 // Collate graphs ids[0..G) (ids == nullptr: graphs 0..G-1) of `st`.
@@ -34,28 +38,34 @@ int launch_collate(int G, const int64_t *ids, StoreView st, BatchBuf b, const fl
 // agg is nullable; S16 (nullable, row pitch ld16) receives [agg, amp*agg,
 // att*agg] (15H BF16), the scaled aggregates as the BF16 operand of the
 // update GEMM.
+// With F > 0 the message carries the bond term sum_f eattr[e][f] wE[f]
+// (eattr: E rows of stride round_up(F, 4) in slot order, wE: F x H).
 int launch_aggregate_fwd(int n_nodes, int H, DevDims dims, const int *row_ptr, const int *col,
                          const float *PQ, float *agg, float eps, unsigned *err, cudaStream_t s,
                          uint16_t *S16 = nullptr, int ld16 = 0, const float *amp = nullptr,
-                         const float *att = nullptr);
+                         const float *att = nullptr, const float *eattr = nullptr, const float *wE = nullptr,
+                         int F = 0);
 // dPQ from dagg; scratch is E x H (per-edge message gradients).  With agg
 // null the forward's statistics are recomputed from the messages in the
 // forward kernel's order (bit-identical).
 int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const int *row_ptr,
                          const int *col, const int *rev, const float *PQ, const float *agg,
                          const float *dagg, float *dPQ, float *scratch, float eps, unsigned *err,
-                         cudaStream_t s, uint16_t *dPQ16 = nullptr, int ld16 = 0);
+                         cudaStream_t s, uint16_t *dPQ16 = nullptr, int ld16 = 0, const float *eattr = nullptr,
+                         const float *wE = nullptr, int F = 0);
 
 // The same gradient for a batch of whole graphs (node_off: G + 1 offsets;
 // no edge leaves its graph).  Batches of at least 2 x SMs x 128 edges take the
 // fused kernel: chunks of graphs of about 128 edges, each handled by one block
 // that keeps its per-edge gradients in shared memory; `chunks` holds
-// aggregate_chunk_capacity(n_edges) ints.  Smaller batches take the edge +
-// gather pair above (scratch as there).  Same result either way, bitwise.
+// aggregate_chunk_capacity(n_edges) ints.  Smaller batches, and batches
+// with bond features (whose weight gradient reads the per-edge gradients in
+// scratch), take the edge + gather pair above.  Same result either way, bitwise.
 int launch_aggregate_bwd_graphs(int n_graphs, int n_nodes, int n_edges, int H, DevDims dims, const int *node_off,
                                 const int *row_ptr, const int *col, const int *rev, const float *PQ,
                                 const float *agg, const float *dagg, float *dPQ, float *scratch, int *chunks,
-                                float eps, unsigned *err, cudaStream_t s, uint16_t *dPQ16 = nullptr, int ld16 = 0);
+                                float eps, unsigned *err, cudaStream_t s, uint16_t *dPQ16 = nullptr, int ld16 = 0,
+                                const float *eattr = nullptr, const float *wE = nullptr, int F = 0);
 int aggregate_chunk_capacity(int n_edges);
 bool aggregate_bwd_uses_fused(int n_edges);
 
@@ -136,7 +146,9 @@ struct Operand {
 };
 
 // Which GEMM dimension runs over the batch's nodes (read from DevDims).
-enum NodeDim { kNodeNone = 0, kNodeM = 1, kNodeK = 2 };
+// which GEMM dimension runs over the batch's nodes (or, kEdgeK, edges), so
+// that its extent is read from the device-side batch sizes
+enum NodeDim { kNodeNone = 0, kNodeM = 1, kNodeK = 2, kEdgeK = 3 };
 
 struct GemmDesc {
   int M, N, K;          // K: capacity when node_dim == kNodeK

@@ -11,13 +11,18 @@ namespace {
 
 struct LayerW {
   float *msg_w, *msg_b, *upd_w, *upd_b;
+  float *edge_w;  // bond rows of W_M (F x H), after the head; nullptr when F = 0
 };
 
 LayerW layer_ptrs(float *base, const gcnn_ctx *c, int l) {
   float *b = base + (int64_t)c->T * c->H + (int64_t)l * c->layer_size;
-  const int64_t H = c->H;
-  return LayerW{b, b + 2 * H * H, b + 2 * H * H + H, b + 2 * H * H + H + 16 * H * H};
+  const int64_t H = c->H, F = c->cfg.edge_features;
+  // bond rows: after the head, from the next multiple of 4 floats (16-byte aligned)
+  const int64_t bonds = ((int64_t)c->T * H + (int64_t)c->L * c->layer_size + H * c->Hh + 2 * c->Hh + 1 + 3) / 4 * 4;
+  float *e = F > 0 ? base + bonds + l * F * H : nullptr;
+  return LayerW{b, b + 2 * H * H, b + 2 * H * H + H, b + 2 * H * H + H + 16 * H * H, e};
 }
+
 
 float *head_ptr(float *base, const gcnn_ctx *c) {
   return base + (int64_t)c->T * c->H + (int64_t)c->L * c->layer_size;
@@ -69,6 +74,20 @@ HeadArgs head_args(gcnn_ctx *c, int G, const float *dpred_in) {
 int gemm(gcnn_ctx *c, const GemmDesc &d) {
   PhaseScope ps(c, GCNN_PHASE_GEMM);
   return run_gemm_simt(d, DevDims{c->bb.dims}, c->ws, c->stream);
+}
+
+// Bond rows' gradient: dW_E = eattr^T dm over the batch's edges.  dm holds
+// each edge's message gradient at its reverse slot, and both directions of a
+// bond carry the same features (checked when the store is opened), so slot r
+// pairs dm[r] with eattr[r].
+int gemm_bond_rows(gcnn_ctx *c, int Egrid, float *g_edge_w) {
+  GemmDesc d = blank();
+  d.M = c->cfg.edge_features; d.N = c->H; d.K = Egrid; d.node_dim = kEdgeK;
+  d.a_kcontig = false; d.b_ncontig = true;
+  d.A.nseg = 1; d.A.seg[0] = seg(0, c->bb.eattr, c->bb.eattr_ld);
+  d.B.nseg = 1; d.B.seg[0] = seg(0, c->dm, c->H);
+  d.C = g_edge_w; d.ldc = c->H;
+  return gemm(c, d);
 }
 
 int tc(gcnn_ctx *c, const TcDesc &d) {
@@ -215,7 +234,8 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
   if (c->cfg.recompute) {
     PhaseScope ps(c, GCNN_PHASE_AGG_FWD);
     GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq, agg, (float)c->cfg.std_eps, c->err,
-                                  c->stream, U_at(c, l) + H, 16 * H, c->bb.amp, c->bb.att));
+                                  c->stream, U_at(c, l) + H, 16 * H, c->bb.amp, c->bb.att, c->bb.eattr,
+                                  layer_ptrs(c->params, c, l).edge_w, c->cfg.edge_features));
     GCNN_TRY(stage_x(c, Ngrid, l));
   }
   if (ov) {
@@ -242,8 +262,11 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
     PhaseScope ps(c, GCNN_PHASE_AGG_BWD);
     GCNN_TRY(launch_aggregate_bwd_graphs(Gn, Ngrid, Egrid, H, dims, c->bb.node_off, c->bb.row_ptr, c->bb.col,
                                          c->bb.rev, pq, agg, c->dagg, dPQ, c->dm, c->chunks,
-                                         (float)c->cfg.std_eps, c->err, c->stream, G + 3 * H, 5 * H));
+                                         (float)c->cfg.std_eps, c->err, c->stream, G + 3 * H, 5 * H, c->bb.eattr,
+                                         layer_ptrs(c->params, c, l).edge_w, c->cfg.edge_features));
   }
+  // before the next layer's aggregation backward reuses dm
+  if (c->cfg.edge_features > 0) GCNN_TRY(gemm_bond_rows(c, Egrid, gw.edge_w));
   if (ov) {
     GCNN_CUDA_TRY(cudaEventRecord(mid, c->stream));
     GCNN_CUDA_TRY(cudaStreamWaitEvent(lane.s, mid, 0));
@@ -333,7 +356,8 @@ int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train) {
       PhaseScope ps(c, GCNN_PHASE_AGG_FWD);
       GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq_at(c, l), agg_at(c, l),
                                     (float)c->cfg.std_eps, c->err, c->stream, bf ? U_at(c, l) + H : nullptr,
-                                    16 * H, c->bb.amp, c->bb.att));
+                                    16 * H, c->bb.amp, c->bb.att, c->bb.eattr, layer_ptrs(c->params, c, l).edge_w,
+                                    c->cfg.edge_features));
     }
     if (bf) GCNN_TRY(tc_update(c, Ngrid, l));
     else GCNN_TRY(gemm_update(c, Ngrid, l));
@@ -382,7 +406,8 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
     if (c->cfg.recompute) {
       PhaseScope ps(c, GCNN_PHASE_AGG_FWD);
       GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq, agg,
-                                    (float)c->cfg.std_eps, c->err, c->stream));
+                                    (float)c->cfg.std_eps, c->err, c->stream, nullptr, 0, nullptr, nullptr,
+                                    c->bb.eattr, w.edge_w, c->cfg.edge_features));
     }
     // dW_U (16H x H) and db_U: [x ; agg ; amp agg ; att agg ; 1]^T (dh * [h > 0])
     {
@@ -419,8 +444,10 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
       PhaseScope ps(c, GCNN_PHASE_AGG_BWD);
       GCNN_TRY(launch_aggregate_bwd_graphs(G, Ngrid, Egrid, H, dims, c->bb.node_off, c->bb.row_ptr, c->bb.col,
                                            c->bb.rev, pq, agg, c->dagg, c->dPQ, c->dm, c->chunks,
-                                           (float)c->cfg.std_eps, c->err, c->stream));
+                                           (float)c->cfg.std_eps, c->err, c->stream, nullptr, 0, c->bb.eattr,
+                                           w.edge_w, c->cfg.edge_features));
     }
+    if (c->cfg.edge_features > 0) GCNN_TRY(gemm_bond_rows(c, Egrid, gw.edge_w));
     // dW_M (H x 2H) and db_M: [x ; 1]^T dPQ  (bias row keeps the first H columns)
     {
       GemmDesc d = blank();

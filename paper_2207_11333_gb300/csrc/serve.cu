@@ -323,6 +323,9 @@ int gcnn_serve_create(const gcnn_ctx *model, const gcnn_serve_config *cfg, gcnn_
   if (cfg->n_slots < 1 || cfg->n_slots > 16 || cfg->n_buckets < 1 || cfg->n_buckets > 8 || cfg->max_graphs < 1 ||
       cfg->queue_nodes < 1 || (cfg->precision != GCNN_PREC_FP32 && cfg->precision != GCNN_PREC_BF16))
     return set_error(GCNN_EINVAL, "serve_create: bad configuration");
+  if (model->cfg.edge_features != 0)
+    return set_error(GCNN_EINVAL, "serve_create: requests carry no bond features (model has %d)",
+                     model->cfg.edge_features);
   for (int b = 0; b < cfg->n_buckets; ++b)
     if (cfg->bucket_nodes[b] < kMaxGraphNodes || (b > 0 && cfg->bucket_nodes[b] <= cfg->bucket_nodes[b - 1]))
       return set_error(GCNN_EINVAL, "serve_create: buckets must ascend and hold at least %d atoms", kMaxGraphNodes);

@@ -3,6 +3,7 @@
 // per graph attribute, like the paper's ADIOS schema (Sec. 4, Table 1), in a
 // single file instead of per-graph files.
 #include <cmath>
+#include <cstdint>
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
@@ -32,8 +33,10 @@ struct Header {
   char magic[8];
   uint32_t version, n_types;
   int64_t G, N, E, o_node_ptr, o_edge_ptr, o_types, o_edges, o_y, size;
+  int64_t F, o_eattr;  // version 2: bond features per edge and their offset
 };
-static_assert(sizeof(Header) == 88, "store header layout");
+static_assert(sizeof(Header) == 104, "store header layout");
+constexpr int kMaxEdgeFeatures = 16;
 
 bool range_ok(int64_t off, int64_t bytes, int64_t size) {
   return off >= 0 && bytes >= 0 && off <= size && bytes <= size - off;
@@ -43,7 +46,7 @@ int validate(const gcnn_store *st) {
   if (st->node_ptr[0] != 0 || st->edge_ptr[0] != 0 || st->node_ptr[st->G] != st->N ||
       st->edge_ptr[st->G] != st->E)
     return set_error(GCNN_EFORMAT, "store: offset arrays do not span the data");
-  std::vector<uint8_t> adj(256 * 256);
+  std::vector<int> adj(256 * 256, 0);  // 1 + store index of edge (s, d)
   for (int64_t g = 0; g < st->G; ++g) {
     const int64_t n = st->node_ptr[g + 1] - st->node_ptr[g];
     const int64_t e = st->edge_ptr[g + 1] - st->edge_ptr[g];
@@ -59,16 +62,26 @@ int validate(const gcnn_store *st) {
       if (s >= n || d >= n)
         return set_error(GCNN_EFORMAT, "store: graph %lld edge %lld has a node id >= %lld", (long long)g,
                          (long long)k, (long long)n);
-      adj[s * 256 + d] = 1;
+      adj[s * 256 + d] = (int)k + 1;
     }
-    bool sym = true;
+    bool sym = true, same = true;
     for (int64_t k = 0; k < e; ++k) {
       const int s = ed[2 * k], d = ed[2 * k + 1];
-      if (!adj[d * 256 + s]) sym = false;
+      const int r = adj[d * 256 + s];
+      if (!r) {
+        sym = false;
+      } else if (st->F > 0) {  // both directions of a bond carry the same features
+        const float *a = st->eattr + (st->edge_ptr[g] + k) * st->F;
+        const float *b = st->eattr + (st->edge_ptr[g] + r - 1) * st->F;
+        if (memcmp(a, b, sizeof(float) * st->F) != 0) same = false;
+      }
     }
     for (int64_t k = 0; k < e; ++k) adj[ed[2 * k] * 256 + ed[2 * k + 1]] = 0;
     if (!sym)
       return set_error(GCNN_EFORMAT, "store: graph %lld is not stored in both directions", (long long)g);
+    if (!same)
+      return set_error(GCNN_EFORMAT, "store: graph %lld has a bond whose two directions differ in features",
+                       (long long)g);
     const uint8_t *ty = st->types + st->node_ptr[g];
     for (int64_t v = 0; v < n; ++v)
       if (ty[v] >= st->n_types)
@@ -86,16 +99,22 @@ int store_open(const char *path, gcnn_store **out) {
   FILE *f = fopen(path, "rb");
   if (!f) return set_error(GCNN_EINVAL, "store_open: cannot open %s", path);
   Header h;
-  if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, "GCNNPKD1", 8) != 0 || h.version != 1) {
+  if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, "GCNNPKD1", 8) != 0 || (h.version != 1 && h.version != 2)) {
     fclose(f);
-    return set_error(GCNN_EFORMAT, "store_open: %s is not a packed graph store (v1)", path);
+    return set_error(GCNN_EFORMAT, "store_open: %s is not a packed graph store (v1 or v2)", path);
+  }
+  if (h.version == 1) {
+    h.F = 0;
+    h.o_eattr = 0;
   }
   fseek(f, 0, SEEK_END);
   const long long fsize = ftell(f);
   if (h.size != fsize || h.G < 0 || h.N < 0 || h.E < 0 || h.n_types < 1 || h.n_types > 16 ||
       !range_ok(h.o_node_ptr, 8 * (h.G + 1), h.size) || !range_ok(h.o_edge_ptr, 8 * (h.G + 1), h.size) ||
       !range_ok(h.o_types, h.N, h.size) || !range_ok(h.o_edges, 2 * h.E, h.size) ||
-      !range_ok(h.o_y, 4 * h.G, h.size) || h.o_node_ptr % 8 || h.o_edge_ptr % 8 || h.o_y % 4) {
+      !range_ok(h.o_y, 4 * h.G, h.size) || h.o_node_ptr % 8 || h.o_edge_ptr % 8 || h.o_y % 4 || h.F < 0 ||
+      h.F > kMaxEdgeFeatures || (h.F > 0 && (h.E > INT64_MAX / (4 * h.F) || !range_ok(h.o_eattr, 4 * h.E * h.F, h.size) ||
+                                             h.o_eattr % 16))) {
     fclose(f);
     return set_error(GCNN_EFORMAT, "store_open: inconsistent header in %s", path);
   }
@@ -120,11 +139,13 @@ int store_open(const char *path, gcnn_store **out) {
   st->G = h.G; st->N = h.N; st->E = h.E; st->n_types = h.n_types;
   st->off_node_ptr = h.o_node_ptr; st->off_edge_ptr = h.o_edge_ptr; st->off_types = h.o_types;
   st->off_edges = h.o_edges; st->off_y = h.o_y;
+  st->F = (int32_t)h.F; st->off_eattr = h.o_eattr;
   st->node_ptr = reinterpret_cast<const int64_t *>(b + h.o_node_ptr);
   st->edge_ptr = reinterpret_cast<const int64_t *>(b + h.o_edge_ptr);
   st->types = reinterpret_cast<const uint8_t *>(b + h.o_types);
   st->edges = reinterpret_cast<const uint8_t *>(b + h.o_edges);
   st->y = reinterpret_cast<float *>(b + h.o_y);
+  st->eattr = h.F > 0 ? reinterpret_cast<const float *>(b + h.o_eattr) : nullptr;
   int rc = got == st->bytes ? validate(st) : set_error(GCNN_EFORMAT, "store_open: short read");
   if (rc != GCNN_OK) {
     store_close(st);
@@ -166,7 +187,8 @@ StoreView store_device_view(const gcnn_store *st) {
                    reinterpret_cast<const int64_t *>(b + st->off_edge_ptr),
                    reinterpret_cast<const uint8_t *>(b + st->off_types),
                    reinterpret_cast<const uint8_t *>(b + st->off_edges),
-                   reinterpret_cast<const float *>(b + st->off_y)};
+                   reinterpret_cast<const float *>(b + st->off_y),
+                   st->F > 0 ? reinterpret_cast<const float *>(b + st->off_eattr) : nullptr, st->F};
 }
 
 int store_batch_size(const gcnn_store *st, const int64_t *ids, int64_t n, int64_t *nn, int64_t *ne) {

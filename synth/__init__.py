@@ -150,19 +150,22 @@ def uniform(seed: int, i0: int, n: int, lo: float, hi: float) -> np.ndarray:
 
 
 def param_count(H: int, L: int, T: int = N_TYPES, Hh: int | None = None, F: int = 0) -> int:
-    return int(lib().synth_param_count(H, L, T, H if Hh is None else Hh)) + L * F * H
+    base = int(lib().synth_param_count(H, L, T, H if Hh is None else Hh))
+    return base if F == 0 else (base + 3) // 4 * 4 + L * F * H
 
 
 def init_params(seed: int, H: int, L: int, T: int = N_TYPES, Hh: int | None = None, F: int = 0) -> np.ndarray:
-    """Flat parameters; with F bond features the L blocks of bond rows of the
-    message weights (F x H each) follow the head, U(+-1/sqrt(2H + F))."""
+    """Flat parameters; with F bond features, zero padding up to a multiple of 4
+    floats after the head, then the L blocks of bond rows of the message
+    weights (F x H each), U(+-1/sqrt(2H + F))."""
     Hh = H if Hh is None else Hh
     base = np.empty(param_count(H, L, T, Hh), np.float32)
     lib().synth_init_params(seed, H, L, T, Hh, _p(base))
     if F == 0:
         return base
     b = 1.0 / math.sqrt(2 * H + F)
-    return np.concatenate([base, uniform(seed, 0, L * F * H, -b, b).astype(np.float32)])
+    pad = np.zeros((base.size + 3) // 4 * 4 - base.size, np.float32)
+    return np.concatenate([base, pad, uniform(seed, 0, L * F * H, -b, b).astype(np.float32)])
 
 
 # ---------------------------------------------------------------- graphs

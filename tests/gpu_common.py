@@ -18,10 +18,10 @@ def write_both(gs: synth.GraphSet, tmpdir: str | None = None):
     return path, oracle.read_store(path)
 
 
-def context(H, L, G, N, E, delta, recompute=False, precision=0, Hh=None):
+def context(H, L, G, N, E, delta, recompute=False, precision=0, Hh=None, F=0):
     import paper_2207_11333_gb300 as g
     cfg = g.make_config(H, L, G, N, E, delta=delta, recompute=int(recompute), precision=precision,
-                        head_hidden=H if Hh is None else Hh)
+                        head_hidden=H if Hh is None else Hh, edge_features=F)
     return g.Context(cfg)
 
 

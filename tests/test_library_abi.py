@@ -87,3 +87,22 @@ def test_store_rejects_oversized_graph(tmp_path):
     gs.types = np.zeros(256, np.uint8)
     with pytest.raises(g.GcnnError, match="nodes"):
         g.Store(_bad_store(tmp_path, gs, "big"))
+
+
+def test_store_with_bond_features(tmp_path):
+    """Version-2 stores: the feature count is read back; a bond whose two directions
+    carry different features, or a feature count above 16, is rejected."""
+    import paper_2207_11333_gb300 as g
+    gs = synth.molecules_uniform(4, 10, 3, 20)
+    gs.eattr = synth.bond_features(6, gs, 4)
+    st = g.Store(_bad_store(tmp_path, gs, "bonds"))
+    assert st.edge_features == 4 and st.n_edges == gs.n_edges
+    assert g.Store(_bad_store(tmp_path, synth.molecules_uniform(4, 3, 3, 9), "plain")).edge_features == 0
+    bad = gs.eattr.copy()
+    bad[7, 2] += 1.0                     # one direction of one bond differs
+    gs.eattr = bad
+    with pytest.raises(g.GcnnError, match="differ in features"):
+        g.Store(_bad_store(tmp_path, gs, "asym_feat"))
+    gs.eattr = np.zeros((gs.n_edges, 17), np.float32)
+    with pytest.raises(g.GcnnError, match="EFORMAT"):
+        g.Store(_bad_store(tmp_path, gs, "too_many"))

@@ -30,8 +30,10 @@ def _views(d, p):
     take("b1", (Hh,))
     take("w2", (Hh,))
     take("b2", (1,))
-    for l in range(L if getattr(d, "F", 0) else 0):
-        take(f"edge_w{l}", (d.F, H))
+    if getattr(d, "F", 0):
+        k = (k + 3) // 4 * 4          # bond rows start at a multiple of 4 floats
+        for l in range(L):
+            take(f"edge_w{l}", (d.F, H))
     return out
 
 
