@@ -495,6 +495,63 @@ def aggregate_large(g, reps: int = 5, G: int = 60_000):
     return out
 
 
+def loading_study(g, n_graphs: int = 20_000, batches: int = 60):
+    """Data loading (Sec. 4, Fig. 5 bottom): one file per molecule against the packed
+    store of global arrays.  n_graphs molecules of the workload's size distribution are
+    written one file each, packed by gcnn_store_pack with 1 and with all host threads,
+    and `batches` random 128-graph batches are collated three ways, each followed by a
+    device synchronisation: from the files (gcnn_collate_files: one open + read per
+    molecule), from the packed store in pinned host memory (one copy per batch) and from
+    the device-resident store.  The files were just written, so they are read from the
+    page cache: the per-file figure is the file-system call overhead, not disk time."""
+    import shutil
+    import torch
+    gs = synth.molecules_lognormal(SEED_DATA + 300, n_graphs)
+    gs.y = synth.uniform_targets(SEED_DATA + 301, 0, n_graphs, 1.0, 10.0)
+    tmp = tempfile.mkdtemp(prefix="gcnn_files_")
+    out = {"graphs": n_graphs, "batch": BATCH, "batches": batches}
+    try:
+        t0 = time.perf_counter()
+        paths = synth.write_graph_files(os.path.join(tmp, "files"), gs)
+        out["write_files_s"] = time.perf_counter() - t0
+        cores = len(os.sched_getaffinity(0))
+        packed = os.path.join(tmp, "packed.gcnn")
+        for threads in sorted({1, cores}):
+            t0 = time.perf_counter()
+            g.store_pack(paths, packed, threads)
+            out[f"pack_s_{threads}_threads"] = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        st = g.Store(packed)
+        out["open_packed_s"] = time.perf_counter() - t0
+        rng = np.random.default_rng(7)
+        sets = [rng.integers(0, n_graphs, BATCH) for _ in range(batches)]
+        sizes = [st.batch_size(ids) for ids in sets]
+        Nc = (max(sz[0] for sz in sizes) + 255) // 256 * 256
+        Ec = (max(sz[1] for sz in sizes) + 511) // 512 * 512
+        ctx = g.Context(g.make_config(H, L, BATCH, Nc, Ec, delta=st.delta()))
+        ways = (("per_graph_files", lambda ids: ctx.collate_files([paths[i] for i in ids])),
+                ("packed_store_host", lambda ids: ctx.collate(st, ids)))
+        for name, fn in ways + (("packed_store_device", None),):
+            if name == "packed_store_device":
+                st.to_device()
+                fn = lambda ids: ctx.collate(st, ids)  # noqa: E731
+            fn(sets[0])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for ids in sets:
+                fn(ids)
+                torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            out[name] = {"ms_per_batch": 1e3 * dt / batches, "graphs_per_s": batches * BATCH / dt}
+        ctx.check()
+        ctx.close()
+        out["files_over_packed_host"] = out["per_graph_files"]["ms_per_batch"] / out["packed_store_host"]["ms_per_batch"]
+        out["note"] = "wall time per collated batch incl. device sync; files read from the page cache"
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+    return out
+
+
 def recompute_study(g, precision: str, steps: int = 20):
     """Per-layer recompute at H = 256, L = 6, 1024 graphs of 3-51 atoms per batch:
     step time and device memory with and without it."""
@@ -748,7 +805,8 @@ def run_ours(args):
     ctx.check()
     if args.studies and world == 1:
         for key, fn in (("aggregate_large_batch", lambda: aggregate_large(g)),
-                        ("recompute", lambda: recompute_study(g, args.precision))):
+                        ("recompute", lambda: recompute_study(g, args.precision)),
+                        ("data_loading", lambda: loading_study(g))):
             try:
                 line[key] = fn()
             except Exception as e:  # noqa: BLE001
@@ -805,7 +863,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="seconds of Poisson load per arrival rate for the serving measurement (0: skip)")
     ap.add_argument("--serve-rates", default="200,1000,2000", help="arrival rates, requests/s")
-    ap.add_argument("--study", choices=["none", "precision", "aggregate"], default="none",
+    ap.add_argument("--study", choices=["none", "precision", "aggregate", "loading"], default="none",
                     help="precision: train FP32 and BF16 for --epochs and compare held-out MAE; aggregate: the "
                          "aggregation operators alone on --molecules molecules, --reps timed launches each "
                          "(no bench line)")
@@ -825,6 +883,12 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         import paper_2207_11333_gb300 as g
         print(json.dumps({"study": "precision", **precision_study(g, args.epochs, args.lr)}), flush=True)
+        return 0
+    if args.study == "loading":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        import paper_2207_11333_gb300 as g
+        print(json.dumps({"study": "loading", **loading_study(g)}), flush=True)
         return 0
     if args.study == "aggregate":
         import torch

@@ -126,6 +126,21 @@ int gcnn_store_set_targets(gcnn_store *st, const float *y, int64_t n);
  * collation reads them there (the "resident" mode).  Synchronous. */
 int gcnn_store_to_device(gcnn_store *st);
 
+/* Per-graph files: one molecule per file, the layout the packed store
+ * replaces (Sec. 4: global arrays instead of one file per sample, to cut the
+ * data-loading time of Fig. 5).  Format: "GCNNGRF1", int32 n (atoms, 1..255),
+ * int32 e (directed edges, <= 1024), int32 F (bond features, 0..16),
+ * float32 y, uint8 types[n], uint8 edges[e][2] (local source, destination),
+ * zero padding to a multiple of 4 bytes, float32 edge_attr[e][F];
+ * little-endian.
+ * gcnn_store_pack reads paths[0..n_files) (host strings) with n_threads
+ * threads, checks each file (GCNN_EFORMAT names the first bad one; every file
+ * must have the same F), and writes one packed store to out_path (version 1,
+ * or 2 when F > 0; atom-type count max(7, largest type + 1)): graph q of the
+ * store is file q.  The bytes do not depend on n_threads.  Bond symmetry is
+ * checked when the store is opened. */
+int gcnn_store_pack(const char *const *paths, int64_t n_files, const char *out_path, int32_t n_threads);
+
 /* ------------------------------------------------------------------ context */
 typedef struct gcnn_config {
   int32_t hidden;       /* H, a multiple of 8, 8..1024                         */
@@ -205,6 +220,11 @@ typedef struct gcnn_batch {
  * GCNN_EINVAL if the batch exceeds the context's capacities. */
 int gcnn_collate(gcnn_ctx *ctx, const gcnn_store *st, const int64_t *graph_ids, int32_t n_graphs,
                  gcnn_batch *out);
+/* Collate graphs straight from per-graph files (host paths, read one after
+ * another into pinned staging memory, then one copy): the per-file loading
+ * path that the packed store replaces, kept for comparison.  Same batch as
+ * gcnn_collate on a store packed from the same files. */
+int gcnn_collate_files(gcnn_ctx *ctx, const char *const *paths, int32_t n_graphs, gcnn_batch *out);
 /* Upload an order of graph ids (host, n) once; gcnn_collate_range then
  * collates order[first .. first+count) reading the ids on the device
  * (resident stores only). */

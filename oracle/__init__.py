@@ -60,15 +60,15 @@ def load(path: str) -> ctypes.CDLL:
     L = ctypes.CDLL(path)
     i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
     L.oracle_collate.restype = i32
-    L.oracle_collate.argtypes = [i64, vp, vp, vp, vp, vp, vp, dbl] + [vp] * 11 + [i32, vp, vp]
+    L.oracle_collate.argtypes = [i64, vp, vp, vp, vp, vp, vp, dbl] + [vp] * 11 + [i32, vp, vp, vp, vp]
     L.oracle_delta.restype = dbl
     L.oracle_delta.argtypes = [i64, vp]
     L.oracle_param_count.restype = i64
-    L.oracle_param_count.argtypes = [i32, i32, i32, i32, i32]
+    L.oracle_param_count.argtypes = [i32, i32, i32, i32, i32, i32]
     L.oracle_forward.restype = i32
-    L.oracle_forward.argtypes = [i32, i32, i32, i32, i32, vp, i64, i64, i64] + [vp] * 10 + [dbl, vp, vp, vp, vp]
+    L.oracle_forward.argtypes = [i32, i32, i32, i32, i32, i32, vp, i64, i64, i64] + [vp] * 11 + [dbl, dbl] + [vp] * 5
     L.oracle_backward.restype = i32
-    L.oracle_backward.argtypes = [i32, i32, i32, i32, i32, vp, i64, i64, i64] + [vp] * 10 + [dbl, vp, vp, vp, vp, vp, vp]
+    L.oracle_backward.argtypes = [i32, i32, i32, i32, i32, i32, vp, i64, i64, i64] + [vp] * 11 + [dbl, dbl] + [vp] * 6
     L.oracle_adam.restype = None
     L.oracle_adam.argtypes = [i64, vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, dbl]
     return L
@@ -91,6 +91,7 @@ class Store:
     edges: np.ndarray   # uint8 [2E]
     y: np.ndarray
     eattr: np.ndarray | None = None   # float32 [E, F] bond features (version 2 stores)
+    ynode: np.ndarray | None = None   # float32 [N] node-level targets (version 2 stores)
 
     @property
     def F(self) -> int:
@@ -106,22 +107,26 @@ def read_store(path: str) -> Store:
     G, N, E, o_np, o_ep, o_t, o_e, o_y, size = raw[16:88].view("<i8").tolist()
     if size != raw.size or version not in (1, 2):
         raise ValueError("store size or version mismatch")
-    eattr = None
+    eattr = ynode = None
     if version == 2:
-        F, o_a = raw[88:104].view("<i8").tolist()
-        eattr = raw[o_a:o_a + 4 * E * F].view("<f4").reshape(E, F).copy()
+        F, o_a, o_yn = raw[88:112].view("<i8").tolist()
+        if F:
+            eattr = raw[o_a:o_a + 4 * E * F].view("<f4").reshape(E, F).copy()
+        if o_yn:
+            ynode = raw[o_yn:o_yn + 4 * N].view("<f4").copy()
     return Store(raw[o_np:o_np + 8 * (G + 1)].view("<i8").copy(),
                  raw[o_ep:o_ep + 8 * (G + 1)].view("<i8").copy(),
                  raw[o_t:o_t + N].copy(),
                  raw[o_e:o_e + 2 * E].copy(),
-                 raw[o_y:o_y + 4 * G].view("<f4").copy(), eattr)
+                 raw[o_y:o_y + 4 * G].view("<f4").copy(), eattr, ynode)
 
 
-def store_from_arrays(node_ptr, edge_ptr, types, edges, y, eattr=None) -> Store:
+def store_from_arrays(node_ptr, edge_ptr, types, edges, y, eattr=None, ynode=None) -> Store:
     return Store(np.ascontiguousarray(node_ptr, np.int64), np.ascontiguousarray(edge_ptr, np.int64),
                  np.ascontiguousarray(types, np.uint8), np.ascontiguousarray(edges, np.uint8).reshape(-1),
                  np.ascontiguousarray(y, np.float32),
-                 None if eattr is None else np.ascontiguousarray(eattr, np.float32))
+                 None if eattr is None else np.ascontiguousarray(eattr, np.float32),
+                 None if ynode is None else np.ascontiguousarray(ynode, np.float32))
 
 
 # ------------------------------------------------------------------ collation
@@ -143,6 +148,7 @@ class Batch:
     types: np.ndarray
     y: np.ndarray
     eattr: np.ndarray   # float32 [E, F] bond features in col order (F = 0: empty)
+    ynode: np.ndarray   # float32 [N] node-level targets (zeros when the store has none)
 
     @property
     def F(self) -> int:
@@ -159,11 +165,12 @@ def collate(st: Store, ids, delta: float) -> Batch:
               np.zeros(G + 1, np.int64), np.zeros(G + 1, np.int64), np.zeros(N, np.int32),
               np.zeros(N + 1, np.int32), np.zeros(E, np.int32), np.zeros(E, np.int32),
               np.zeros(N, np.int32), np.zeros(N, np.float32), np.zeros(N, np.float32),
-              np.zeros(N, np.uint8), np.zeros(G, np.float32), np.zeros((E, st.F), np.float32))
+              np.zeros(N, np.uint8), np.zeros(G, np.float32), np.zeros((E, st.F), np.float32),
+              np.zeros(N, np.float32))
     rc = lib().oracle_collate(G, _p(ids), _p(st.node_ptr), _p(st.edge_ptr), _p(st.types), _p(st.edges),
                               _p(st.y), float(delta), _p(b.node_off), _p(b.edge_off), _p(b.graph_id),
                               _p(b.row_ptr), _p(b.col), _p(b.rev), _p(b.deg), _p(b.amp), _p(b.att),
-                              _p(b.types), _p(b.y), st.F, _p(st.eattr), _p(b.eattr))
+                              _p(b.types), _p(b.y), st.F, _p(st.eattr), _p(b.eattr), _p(st.ynode), _p(b.ynode))
     if rc:
         raise MemoryError("oracle_collate failed")
     return b
@@ -186,6 +193,8 @@ class Dims:
     T: int = 7
     Hh: int | None = None
     F: int = 0   # bond features per edge
+    NH: int = 0  # node-level head (0/1)
+    node_weight: float = 1.0  # weight of the node-level MSE in the loss
 
     def __post_init__(self):
         if self.Hh is None:
@@ -193,18 +202,20 @@ class Dims:
 
 
 def param_count(d: Dims) -> int:
-    return int(lib().oracle_param_count(d.H, d.L, d.T, d.Hh, d.F))
+    return int(lib().oracle_param_count(d.H, d.L, d.T, d.Hh, d.F, d.NH))
 
 
 def _batch_args(d: Dims, b: Batch):
     if b.F != d.F:
         raise ValueError(f"batch has {b.F} bond features, the model {d.F}")
     return [b.G, b.N, b.E, _p(b.node_off), _p(b.graph_id), _p(b.row_ptr), _p(b.col), _p(b.deg),
-            _p(b.amp), _p(b.att), _p(b.types), _p(b.eattr)]
+            _p(b.amp), _p(b.att), _p(b.types), _p(b.eattr), _p(b.ynode)]
 
 
-def forward(d: Dims, params, b: Batch, x0=None, eps: float = 1e-5, want_layers: bool = False):
-    """Predictions (G,) in FP64; with want_layers also xs ((L+1),N,H), aggs (L,N,5H), pooled (G,H)."""
+def forward(d: Dims, params, b: Batch, x0=None, eps: float = 1e-5, want_layers: bool = False,
+            want_nodes: bool = False):
+    """Predictions (G,) in FP64; with want_layers also xs ((L+1),N,H), aggs (L,N,5H), pooled (G,H);
+    with want_nodes (node head) the node-level predictions (N,) are appended."""
     p = np.ascontiguousarray(params, np.float64)
     assert p.size == param_count(d)
     x0a = None if x0 is None else np.ascontiguousarray(x0, np.float64)
@@ -212,11 +223,15 @@ def forward(d: Dims, params, b: Batch, x0=None, eps: float = 1e-5, want_layers: 
     xs = np.zeros(((d.L + 1), b.N, d.H)) if want_layers else None
     ag = np.zeros((d.L, b.N, N_AGG * d.H)) if want_layers else None
     pooled = np.zeros((b.G, d.H)) if want_layers else None
-    rc = lib().oracle_forward(d.H, d.L, d.T, d.Hh, d.F, _p(p), *_batch_args(d, b), _p(x0a), eps, _p(pred),
-                              _p(xs), _p(ag), _p(pooled))
+    predn = np.zeros(b.N, np.float64) if want_nodes else None
+    rc = lib().oracle_forward(d.H, d.L, d.T, d.Hh, d.F, d.NH, _p(p), *_batch_args(d, b), _p(x0a), eps,
+                              float(d.node_weight), _p(pred), _p(xs), _p(ag), _p(pooled), _p(predn))
     if rc:
         raise MemoryError("oracle_forward failed")
-    return (pred, xs, ag, pooled) if want_layers else pred
+    out = (pred, xs, ag, pooled) if want_layers else (pred,)
+    if want_nodes:
+        out = out + (predn,)
+    return out if len(out) > 1 else out[0]
 
 
 def backward(d: Dims, params, b: Batch, x0=None, eps: float = 1e-5, dpred=None):
@@ -228,7 +243,8 @@ def backward(d: Dims, params, b: Batch, x0=None, eps: float = 1e-5, dpred=None):
     dx0 = np.zeros((b.N, d.H), np.float64)
     loss = np.zeros(1, np.float64)
     pred = np.zeros(b.G, np.float64)
-    rc = lib().oracle_backward(d.H, d.L, d.T, d.Hh, d.F, _p(p), *_batch_args(d, b), _p(x0a), eps, _p(b.y), _p(dp),
+    rc = lib().oracle_backward(d.H, d.L, d.T, d.Hh, d.F, d.NH, _p(p), *_batch_args(d, b), _p(x0a), eps,
+                               float(d.node_weight), _p(b.y), _p(dp),
                                _p(grad), _p(dx0), _p(loss), _p(pred))
     if rc:
         raise MemoryError("oracle_backward failed")
@@ -267,5 +283,11 @@ def split_params(d: Dims, p):
         k = (k + 3) // 4 * 4          # bond rows start at a multiple of 4 floats
         for l in range(L):
             take(f"edge_w{l}", (d.F, H))
+    if d.NH:
+        k = (k + 3) // 4 * 4          # node head likewise
+        take("w1n", (H, Hh))
+        take("b1n", (Hh,))
+        take("w2n", (Hh,))
+        take("b2n", (1,))
     assert k == p.size
     return out

@@ -21,7 +21,9 @@
  *       update      x_i' = ReLU(W_U [x_i ; scalers (x) aggregators] + b_U)
  *   global mean pooling per graph                                   [Sec. 3.1]
  *   fully connected head  y = W2 ReLU(W1 g + b1) + b2                [Sec. 3.1]
- *   MSE loss                                                        [Sec. 3.2]
+ *   optional node-level head (no pooling)                           [Sec. 3.1, Table 1]
+ *       yn_i = w2n . ReLU(W1n^T x_i + b1n) + b2n on the last layer
+ *   MSE loss (+ node_weight times the node-level MSE)               [Sec. 3.2]
  *   gradients of the loss w.r.t. every parameter (by hand)          [Sec. 3.2]
  *   Adam / AdamW update                                             [Sec. 3.2, 5.1]
  * The paper names PNA (Corso et al. 2020) but does not print its equations;
@@ -46,6 +48,8 @@
  *   head: w1[H][Hh], b1[Hh], w2[Hh], b2
  *   with F bond features: 0..3 unused floats up to the next multiple of 4,
  *   then per layer edge_w[F][H] (the bond rows of W_M)
+ *   with the node head: 0..3 unused floats up to the next multiple of 4,
+ *   then w1n[H][Hh], b1n[Hh], w2n[Hh], b2n
  * so that W_M(k, c) for the stacked input [x_i ; x_j ; e_ij] is msg_w[k][c]
  * for k < H, msg_w[k-H][H+c] for H <= k < 2H and edge_w[k-2H][c] after.
  */
@@ -72,6 +76,7 @@
  *   types[N], y[G]                 gathered node types and targets
  *   eattr[E][F]                    bond features of each edge, in the order
  *                                  of col (F = 0: not used)
+ *   ynode[N]                       node-level targets (when st_ynode != NULL)
  */
 int oracle_collate(int64_t G, const int64_t *ids, const int64_t *st_node_ptr,
                    const int64_t *st_edge_ptr, const uint8_t *st_types,
@@ -79,7 +84,7 @@ int oracle_collate(int64_t G, const int64_t *ids, const int64_t *st_node_ptr,
                    int64_t *node_off, int64_t *edge_off, int32_t *graph_id,
                    int32_t *row_ptr, int32_t *col, int32_t *rev, int32_t *deg,
                    float *amp, float *att, uint8_t *types, float *y, int F,
-                   const float *st_eattr, float *eattr) {
+                   const float *st_eattr, float *eattr, const float *st_ynode, float *ynode) {
   node_off[0] = 0;
   edge_off[0] = 0;
   for (int64_t g = 0; g < G; ++g) {
@@ -100,6 +105,7 @@ int oracle_collate(int64_t G, const int64_t *ids, const int64_t *st_node_ptr,
     for (int64_t v = 0; v < n; ++v) {
       graph_id[node_off[g] + v] = (int32_t)g;
       types[node_off[g] + v] = st_types[st_node_ptr[id] + v];
+      if (st_ynode) ynode[node_off[g] + v] = st_ynode[st_node_ptr[id] + v];
     }
     int64_t e = edge_off[g + 1] - edge_off[g];
     for (int64_t k = 0; k < e; ++k) {
@@ -173,9 +179,11 @@ double oracle_delta(int64_t N, const int32_t *deg) {
 /* ------------------------------------------------------------ model */
 
 typedef struct {
-  int H, L, T, Hh, F;
+  int H, L, T, Hh, F, NH;  /* NH: node-level head present (0/1) */
   int64_t G, N, E;
   const float *eattr;  /* E x F bond features in col order */
+  const float *ynode;  /* N node-level targets (NH = 1) */
+  double node_weight;  /* weight of the node-level MSE in the loss */
   const int64_t *node_off;
   const int32_t *graph_id, *row_ptr, *col, *deg;
   const float *amp, *att;
@@ -198,9 +206,19 @@ static int64_t bonds_offset(int H, int L, int T, int Hh) {
   return ((int64_t)T * H + L * layer_size(H) + head_size(H, Hh) + 3) / 4 * 4;
 }
 
-int64_t oracle_param_count(int H, int L, int T, int Hh, int F) {
+static int64_t trunk_end(int H, int L, int T, int Hh, int F) {
   if (F == 0) return (int64_t)T * H + L * layer_size(H) + head_size(H, Hh);
   return bonds_offset(H, L, T, Hh) + (int64_t)L * F * H;
+}
+
+/* node head: after the bond rows (or the head), from the next multiple of 4 */
+static int64_t node_head_offset(int H, int L, int T, int Hh, int F) {
+  return (trunk_end(H, L, T, Hh, F) + 3) / 4 * 4;
+}
+
+int64_t oracle_param_count(int H, int L, int T, int Hh, int F, int NH) {
+  if (!NH) return trunk_end(H, L, T, Hh, F);
+  return node_head_offset(H, L, T, Hh, F) + head_size(H, Hh);
 }
 
 static layer_t layer_at(const net_t *n, const double *p, int l) {
@@ -342,17 +360,37 @@ static void head(const net_t *n, const double *p, const double *g, double *z1, d
   }
 }
 
+/* node-level head on the last layer: zn_i = W1n^T x_i + b1n ;
+   predn_i = w2n . ReLU(zn_i) + b2n  (no pooling: one output per atom) */
+static void node_head(const net_t *n, const double *p, const double *x, double *zn, double *predn) {
+  int H = n->H, Hh = n->Hh;
+  const double *w1 = p + node_head_offset(H, n->L, n->T, Hh, n->F), *b1 = w1 + (int64_t)H * Hh;
+  const double *w2 = b1 + Hh, *b2 = w2 + Hh;
+  for (int64_t i = 0; i < n->N; ++i) {
+    double out = b2[0];
+    for (int c = 0; c < Hh; ++c) {
+      double z = b1[c];
+      for (int k = 0; k < H; ++k) z += x[i * H + k] * w1[(int64_t)k * Hh + c];
+      zn[i * Hh + c] = z;
+      out += (z > 0.0 ? z : 0.0) * w2[c];
+    }
+    predn[i] = out;
+  }
+}
+
 static void embed(const net_t *n, const double *p, double *x0) {
   int H = n->H;
   for (int64_t i = 0; i < n->N; ++i)
     for (int k = 0; k < H; ++k) x0[i * H + k] = p[(int64_t)n->types[i] * H + k];
 }
 
-static void net_init(net_t *n, int H, int L, int T, int Hh, int F, int64_t G, int64_t N, int64_t E,
+static void net_init(net_t *n, int H, int L, int T, int Hh, int F, int NH, int64_t G, int64_t N, int64_t E,
                      const int64_t *node_off, const int32_t *graph_id, const int32_t *row_ptr,
                      const int32_t *col, const int32_t *deg, const float *amp, const float *att,
-                     const uint8_t *types, const float *eattr, double eps) {
+                     const uint8_t *types, const float *eattr, const float *ynode, double node_weight,
+                     double eps) {
   n->H = H; n->L = L; n->T = T; n->Hh = Hh; n->F = F; n->eattr = eattr;
+  n->NH = NH; n->ynode = ynode; n->node_weight = node_weight;
   n->G = G; n->N = N; n->E = E;
   n->node_off = node_off; n->graph_id = graph_id; n->row_ptr = row_ptr; n->col = col;
   n->deg = deg; n->amp = amp; n->att = att; n->types = types; n->eps = eps;
@@ -360,7 +398,7 @@ static void net_init(net_t *n, int H, int L, int T, int Hh, int F, int64_t G, in
 
 /* Forward pass state: xs[(L+1)][N][H], pre[L][N][H], agg[L][N][5H], g, z1. */
 typedef struct {
-  double *xs, *pre, *agg, *msg, *g, *z1;
+  double *xs, *pre, *agg, *msg, *g, *z1, *zn, *predn;
 } fwd_t;
 
 static int fwd_alloc(const net_t *n, fwd_t *f) {
@@ -371,11 +409,13 @@ static int fwd_alloc(const net_t *n, fwd_t *f) {
   f->msg = (double *)calloc((size_t)(n->E * H + 1), sizeof(double));
   f->g = (double *)calloc((size_t)(n->G * H + 1), sizeof(double));
   f->z1 = (double *)calloc((size_t)(n->G * n->Hh + 1), sizeof(double));
-  return (f->xs && f->pre && f->agg && f->msg && f->g && f->z1) ? 0 : -1;
+  f->zn = (double *)calloc((size_t)(n->NH ? n->N * n->Hh + 1 : 1), sizeof(double));
+  f->predn = (double *)calloc((size_t)(n->N + 1), sizeof(double));
+  return (f->xs && f->pre && f->agg && f->msg && f->g && f->z1 && f->zn && f->predn) ? 0 : -1;
 }
 
 static void fwd_free(fwd_t *f) {
-  free(f->xs); free(f->pre); free(f->agg); free(f->msg); free(f->g); free(f->z1);
+  free(f->xs); free(f->pre); free(f->agg); free(f->msg); free(f->g); free(f->z1); free(f->zn); free(f->predn);
 }
 
 static void forward(const net_t *n, const double *p, const double *x0_in, fwd_t *f, double *pred) {
@@ -390,6 +430,7 @@ static void forward(const net_t *n, const double *p, const double *x0_in, fwd_t 
   }
   mean_pool(n, f->xs + n->L * NH, f->g);
   head(n, p, f->g, f->z1, pred);
+  if (n->NH) node_head(n, p, f->xs + n->L * NH, f->zn, f->predn);
 }
 
 /*
@@ -397,17 +438,19 @@ static void forward(const net_t *n, const double *p, const double *x0_in, fwd_t 
  * Optional outputs: xs_out ((L+1) x N x H, layer inputs/outputs),
  * agg_out (L x N x 5H), pooled_out (G x H).
  */
-int oracle_forward(int H, int L, int T, int Hh, int F, const double *params, int64_t G, int64_t N,
+int oracle_forward(int H, int L, int T, int Hh, int F, int NH, const double *params, int64_t G, int64_t N,
                    int64_t E, const int64_t *node_off, const int32_t *graph_id,
                    const int32_t *row_ptr, const int32_t *col, const int32_t *deg,
                    const float *amp, const float *att, const uint8_t *types, const float *eattr,
-                   const double *x0_in, double eps, double *pred, double *xs_out,
-                   double *agg_out, double *pooled_out) {
+                   const float *ynode, const double *x0_in, double eps, double node_weight, double *pred,
+                   double *xs_out, double *agg_out, double *pooled_out, double *predn_out) {
   net_t n;
   fwd_t f;
-  net_init(&n, H, L, T, Hh, F, G, N, E, node_off, graph_id, row_ptr, col, deg, amp, att, types, eattr, eps);
+  net_init(&n, H, L, T, Hh, F, NH, G, N, E, node_off, graph_id, row_ptr, col, deg, amp, att, types, eattr, ynode,
+           node_weight, eps);
   if (fwd_alloc(&n, &f)) { fwd_free(&f); return -1; }
   forward(&n, params, x0_in, &f, pred);
+  if (predn_out && NH) memcpy(predn_out, f.predn, sizeof(double) * (size_t)N);
   if (xs_out) memcpy(xs_out, f.xs, sizeof(double) * (size_t)((L + 1) * N * H));
   if (agg_out) memcpy(agg_out, f.agg, sizeof(double) * (size_t)(L * N * NAGG * H));
   if (pooled_out) memcpy(pooled_out, f.g, sizeof(double) * (size_t)(G * H));
@@ -421,17 +464,18 @@ int oracle_forward(int H, int L, int T, int Hh, int F, const double *params, int
  * otherwise dpred_in is used as dL/dpred and *loss is not written.
  * grad has the parameter layout; dx0 (N x H, optional) receives dL/dx0.
  */
-int oracle_backward(int H, int L, int T, int Hh, int F, const double *params, int64_t G, int64_t N,
+int oracle_backward(int H, int L, int T, int Hh, int F, int NHd, const double *params, int64_t G, int64_t N,
                     int64_t E, const int64_t *node_off, const int32_t *graph_id,
                     const int32_t *row_ptr, const int32_t *col, const int32_t *deg,
                     const float *amp, const float *att, const uint8_t *types, const float *eattr,
-                    const double *x0_in, double eps, const float *y, const double *dpred_in,
-                    double *grad, double *dx0, double *loss, double *pred_out) {
+                    const float *ynode, const double *x0_in, double eps, double node_weight, const float *y,
+                    const double *dpred_in, double *grad, double *dx0, double *loss, double *pred_out) {
   net_t n;
   fwd_t f;
-  net_init(&n, H, L, T, Hh, F, G, N, E, node_off, graph_id, row_ptr, col, deg, amp, att, types, eattr, eps);
+  net_init(&n, H, L, T, Hh, F, NHd, G, N, E, node_off, graph_id, row_ptr, col, deg, amp, att, types, eattr, ynode,
+           node_weight, eps);
   int64_t NH = N * H;
-  int64_t P = oracle_param_count(H, L, T, Hh, F);
+  int64_t P = oracle_param_count(H, L, T, Hh, F, NHd);
   double *pred = (double *)calloc((size_t)(G + 1), sizeof(double));
   double *dpred = (double *)calloc((size_t)(G + 1), sizeof(double));
   double *dx = (double *)calloc((size_t)(NH + 1), sizeof(double));      /* dL/dx_l   */
@@ -461,6 +505,18 @@ int oracle_backward(int H, int L, int T, int Hh, int F, const double *params, in
     }
     if (loss) *loss = G > 0 ? l / (double)G : 0.0;
   }
+  /* node-level MSE, weighted: node_weight (1/N) sum_i (predn_i - yn_i)^2 */
+  double *dpredn = (double *)calloc((size_t)(N + 1), sizeof(double));
+  if (!dpredn) { fwd_free(&f); free(pred); free(dpred); free(dx); free(dxn); free(dpre); free(dagg); free(dm); free(dg); free(tsrc); return -1; }
+  if (NHd) {
+    double l = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+      double r = f.predn[i] - (double)ynode[i];
+      l += r * r;
+      dpredn[i] = N > 0 ? node_weight * 2.0 * r / (double)N : 0.0;
+    }
+    if (loss && !dpred_in) *loss += N > 0 ? node_weight * l / (double)N : 0.0;
+  }
 
   /* head */
   {
@@ -487,6 +543,27 @@ int oracle_backward(int H, int L, int T, int Hh, int F, const double *params, in
     int64_t a = node_off[g], b = node_off[g + 1];
     for (int64_t i = a; i < b; ++i)
       for (int k = 0; k < H; ++k) dx[i * H + k] = dg[g * H + k] / (double)(b - a);
+  }
+
+  /* node head: predn_i = b2n + w2n . ReLU(zn_i), zn_i = b1n + W1n^T x_i */
+  if (NHd) {
+    const int64_t o = node_head_offset(H, L, T, Hh, F);
+    const double *w1 = params + o, *w2 = w1 + (int64_t)H * Hh + Hh;
+    double *gw1 = grad + o, *gb1 = gw1 + (int64_t)H * Hh, *gw2 = gb1 + Hh, *gb2 = gw2 + Hh;
+    const double *xl = f.xs + (int64_t)L * NH;
+    for (int64_t i = 0; i < N; ++i) {
+      gb2[0] += dpredn[i];
+      for (int c = 0; c < Hh; ++c) {
+        double z = f.zn[i * Hh + c];
+        gw2[c] += (z > 0.0 ? z : 0.0) * dpredn[i];
+        double dz = z > 0.0 ? dpredn[i] * w2[c] : 0.0;
+        gb1[c] += dz;
+        for (int k = 0; k < H; ++k) {
+          gw1[(int64_t)k * Hh + c] += xl[i * H + k] * dz;
+          dx[i * H + k] += w1[(int64_t)k * Hh + c] * dz;
+        }
+      }
+    }
   }
 
   /* conv layers, last to first */
@@ -623,7 +700,7 @@ int oracle_backward(int H, int L, int T, int Hh, int F, const double *params, in
       for (int k = 0; k < H; ++k) grad[(int64_t)types[i] * H + k] += dx[i * H + k];
 
   fwd_free(&f);
-  free(pred); free(dpred); free(dx); free(dxn); free(dpre); free(dagg); free(dm); free(dg); free(tsrc);
+  free(pred); free(dpred); free(dx); free(dxn); free(dpre); free(dagg); free(dm); free(dg); free(tsrc); free(dpredn);
   return 0;
 }
 

@@ -80,6 +80,8 @@ def _load() -> ctypes.CDLL:
         "gcnn_store_close": (i32, [vp]),
         "gcnn_store_info": (i32, [vp, P(i64), P(i64), P(i64)]),
         "gcnn_store_edge_features": (i32, [vp, P(i32)]),
+        "gcnn_store_pack": (i32, [vp, i64, ctypes.c_char_p, i32]),
+        "gcnn_collate_files": (i32, [vp, vp, i32, vp]),
         "gcnn_store_batch_size": (i32, [vp, vp, i64, P(i64), P(i64)]),
         "gcnn_store_delta": (i32, [vp, vp, i64, P(f64)]),
         "gcnn_store_set_targets": (i32, [vp, vp, i64]),
@@ -167,6 +169,19 @@ def _dev_ptr(t, dtype=None):
 
 
 # ---------------------------------------------------------------- store
+
+def _c_paths(paths):
+    arr = (ctypes.c_char_p * max(len(paths), 1))()
+    for k, p in enumerate(paths):
+        arr[k] = os.fsencode(p)
+    return arr
+
+
+def store_pack(paths, out_path: str, n_threads: int = 1) -> None:
+    """Pack per-graph files (gcnn_store_pack) into one store file."""
+    arr = _c_paths(paths)
+    _check(lib.gcnn_store_pack(ctypes.cast(arr, ctypes.c_void_p), len(paths), os.fsencode(out_path), int(n_threads)))
+
 
 class Store:
     """Packed graph store (gcnn_store_*)."""
@@ -349,6 +364,13 @@ class Context:
         ids = np.ascontiguousarray(ids, np.int64)
         b = BatchStruct()
         _check(lib.gcnn_collate(self._h, store.handle, _np_ptr(ids), len(ids), ctypes.byref(b)))
+        return Batch(b, self)
+
+    def collate_files(self, paths) -> Batch:
+        """Collate graphs straight from per-graph files (gcnn_collate_files)."""
+        arr = _c_paths(paths)
+        b = BatchStruct()
+        _check(lib.gcnn_collate_files(self._h, ctypes.cast(arr, ctypes.c_void_p), len(paths), ctypes.byref(b)))
         return Batch(b, self)
 
     def set_order(self, store: Store, order) -> None:

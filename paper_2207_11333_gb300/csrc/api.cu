@@ -471,6 +471,21 @@ int gcnn_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t 
   return ctx_collate(c, st, ids, n, out);
 }
 
+int gcnn_collate_files(gcnn_ctx *c, const char *const *paths, int32_t n, gcnn_batch *out) {
+  if (!c || !out || n < 0 || (n > 0 && !paths)) return set_error(GCNN_EINVAL, "collate_files: bad arguments");
+  for (int32_t g = 0; g < n; ++g)
+    if (!paths[g]) return set_error(GCNN_EINVAL, "collate_files: null path");
+  return ctx_collate_files(c, paths, n, out);
+}
+
+int gcnn_store_pack(const char *const *paths, int64_t n_files, const char *out_path, int32_t n_threads) {
+  if (!out_path || n_files < 0 || (n_files > 0 && !paths) || n_threads < 1 || n_threads > 256)
+    return set_error(GCNN_EINVAL, "store_pack: bad arguments");
+  for (int64_t q = 0; q < n_files; ++q)
+    if (!paths[q]) return set_error(GCNN_EINVAL, "store_pack: null path");
+  return store_pack(paths, n_files, out_path, n_threads);
+}
+
 int gcnn_set_order(gcnn_ctx *c, const gcnn_store *st, const int64_t *order, int64_t n) {
   if (!c || !st || !order || n < 1) return set_error(GCNN_EINVAL, "set_order: bad arguments");
   if (!st->dev) return set_error(GCNN_ESTATE, "set_order needs a device-resident store");

@@ -2,6 +2,7 @@
 // data-loading phase, Sec. 4 and Fig. 5), either straight from a device-
 // resident store or through pinned staging memory and one host-to-device copy.
 #include <cstring>
+#include <vector>
 
 #include "context.h"
 
@@ -49,6 +50,54 @@ int claim_stage(gcnn_ctx *c, int q) {
   return GCNN_OK;
 }
 
+// Gather n graphs into a mini-store in pinned staging memory (node_ptr,
+// edge_ptr, y, types, edges, bond features), copy it to the device in one
+// transfer and collate it.  fill(g, types, edges, y, attr) writes graph g's
+// slices at the given destinations and returns its (nodes, edges) through
+// the sizes(g) call made first.
+template <class Sizes, class Fill>
+int collate_staged(gcnn_ctx *c, int32_t n, int64_t N, int64_t E, int F, Sizes sizes, Fill fill, gcnn_batch *out) {
+  const int q = c->stage_i;
+  c->stage_i ^= 1;
+  GCNN_TRY(claim_stage(c, q));
+  char *h = c->stage_host[q];
+  size_t o = 0;
+  const size_t o_np = o; o = align_up(o + 8 * (size_t)(n + 1), 16);
+  const size_t o_ep = o; o = align_up(o + 8 * (size_t)(n + 1), 16);
+  const size_t o_y = o;  o = align_up(o + 4 * (size_t)n, 16);
+  const size_t o_t = o;  o = align_up(o + (size_t)N, 16);
+  const size_t o_e = o;  o = align_up(o + 2 * (size_t)E, 16);
+  const size_t o_a = o;  o = align_up(o + 4 * (size_t)E * F, 16);
+  if (o > c->stage_bytes) return set_error(GCNN_EINVAL, "staging buffer too small");
+  int64_t *np = reinterpret_cast<int64_t *>(h + o_np), *ep = reinterpret_cast<int64_t *>(h + o_ep);
+  float *y = reinterpret_cast<float *>(h + o_y), *at = reinterpret_cast<float *>(h + o_a);
+  uint8_t *ty = reinterpret_cast<uint8_t *>(h + o_t), *ed = reinterpret_cast<uint8_t *>(h + o_e);
+  np[0] = 0;
+  ep[0] = 0;
+  for (int32_t g = 0; g < n; ++g) {
+    int64_t nn = 0, ne = 0;
+    sizes(g, &nn, &ne);
+    if (np[g] + nn > N || ep[g] + ne > E) return set_error(GCNN_EINVAL, "collate: graph sizes changed while staging");
+    fill(g, ty + np[g], ed + 2 * ep[g], y + g, at + ep[g] * F);
+    np[g + 1] = np[g] + nn;
+    ep[g + 1] = ep[g] + ne;
+  }
+  GCNN_CUDA_TRY(cudaMemcpyAsync(c->stage_dev, h, o, cudaMemcpyHostToDevice, c->stream));
+  GCNN_CUDA_TRY(cudaEventRecord(c->stage_ev[q], c->stream));
+  c->stage_used[q] = true;
+  const char *d = c->stage_dev;
+  StoreView v{reinterpret_cast<const int64_t *>(d + o_np), reinterpret_cast<const int64_t *>(d + o_ep),
+              reinterpret_cast<const uint8_t *>(d + o_t), reinterpret_cast<const uint8_t *>(d + o_e),
+              reinterpret_cast<const float *>(d + o_y), F > 0 ? reinterpret_cast<const float *>(d + o_a) : nullptr, F};
+  {
+    PhaseScope ps(c, GCNN_PHASE_COLLATE);
+    GCNN_TRY(launch_collate(n, nullptr, v, c->bb, c->scal_tab, c->Nc, c->Ec, c->err, c->stream));
+  }
+  fill_batch(c, n, N, E, out);
+  c->have_fwd = false;
+  return GCNN_OK;
+}
+
 }  // namespace
 
 int ctx_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n, gcnn_batch *out) {
@@ -57,62 +106,71 @@ int ctx_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n
   GCNN_TRY(check_caps(c, n, 0, 0));
   GCNN_TRY(store_batch_size(st, ids, n, &N, &E));
   GCNN_TRY(check_caps(c, n, N, E));
+  if (!st->dev) {
+    // gather the graphs' slices into a mini-store in pinned memory, one copy
+    const int F = st->F;
+    auto sizes = [&](int32_t g, int64_t *nn, int64_t *ne) {
+      const int64_t id = ids[g];
+      *nn = st->node_ptr[id + 1] - st->node_ptr[id];
+      *ne = st->edge_ptr[id + 1] - st->edge_ptr[id];
+    };
+    auto fill = [&](int32_t g, uint8_t *ty, uint8_t *ed, float *y, float *at) {
+      const int64_t id = ids[g];
+      const int64_t nn = st->node_ptr[id + 1] - st->node_ptr[id], ne = st->edge_ptr[id + 1] - st->edge_ptr[id];
+      memcpy(ty, st->types + st->node_ptr[id], (size_t)nn);
+      memcpy(ed, st->edges + 2 * st->edge_ptr[id], 2 * (size_t)ne);
+      if (F > 0) memcpy(at, st->eattr + st->edge_ptr[id] * F, sizeof(float) * (size_t)ne * F);
+      *y = st->y[id];
+    };
+    return collate_staged(c, n, N, E, F, sizes, fill, out);
+  }
+  // resident store: only the graph ids travel
   const int q = c->stage_i;
   c->stage_i ^= 1;
   GCNN_TRY(claim_stage(c, q));
   char *h = c->stage_host[q];
-  if (st->dev) {
-    // resident store: only the graph ids travel
-    memcpy(h, ids, sizeof(int64_t) * (size_t)n);
-    if (n > 0)
-      GCNN_CUDA_TRY(cudaMemcpyAsync(c->ids_dev, h, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
-    GCNN_CUDA_TRY(cudaEventRecord(c->stage_ev[q], c->stream));
-    c->stage_used[q] = true;
+  memcpy(h, ids, sizeof(int64_t) * (size_t)n);
+  if (n > 0)
+    GCNN_CUDA_TRY(cudaMemcpyAsync(c->ids_dev, h, sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, c->stream));
+  GCNN_CUDA_TRY(cudaEventRecord(c->stage_ev[q], c->stream));
+  c->stage_used[q] = true;
+  {
     PhaseScope ps(c, GCNN_PHASE_COLLATE);
     GCNN_TRY(launch_collate(n, c->ids_dev, store_device_view(st), c->bb, c->scal_tab, c->Nc, c->Ec, c->err,
                             c->stream));
-  } else {
-    // gather the graphs' slices into a mini-store in pinned memory, one copy
-    size_t o = 0;
-    const size_t o_np = o; o = align_up(o + 8 * (size_t)(n + 1), 16);
-    const size_t o_ep = o; o = align_up(o + 8 * (size_t)(n + 1), 16);
-    const size_t o_y = o;  o = align_up(o + 4 * (size_t)n, 16);
-    const size_t o_t = o;  o = align_up(o + (size_t)N, 16);
-    const size_t o_e = o;  o = align_up(o + 2 * (size_t)E, 16);
-    const int F = st->F;
-    const size_t o_a = o;  o = align_up(o + 4 * (size_t)E * F, 16);
-    if (o > c->stage_bytes) return set_error(GCNN_EINVAL, "staging buffer too small");
-    float *at = reinterpret_cast<float *>(h + o_a);
-    int64_t *np = reinterpret_cast<int64_t *>(h + o_np), *ep = reinterpret_cast<int64_t *>(h + o_ep);
-    float *y = reinterpret_cast<float *>(h + o_y);
-    uint8_t *ty = reinterpret_cast<uint8_t *>(h + o_t), *ed = reinterpret_cast<uint8_t *>(h + o_e);
-    np[0] = 0;
-    ep[0] = 0;
-    for (int32_t g = 0; g < n; ++g) {
-      const int64_t id = ids[g];
-      const int64_t nn = st->node_ptr[id + 1] - st->node_ptr[id];
-      const int64_t ne = st->edge_ptr[id + 1] - st->edge_ptr[id];
-      memcpy(ty + np[g], st->types + st->node_ptr[id], (size_t)nn);
-      memcpy(ed + 2 * ep[g], st->edges + 2 * st->edge_ptr[id], 2 * (size_t)ne);
-      if (F > 0) memcpy(at + ep[g] * F, st->eattr + st->edge_ptr[id] * F, sizeof(float) * (size_t)ne * F);
-      y[g] = st->y[id];
-      np[g + 1] = np[g] + nn;
-      ep[g + 1] = ep[g] + ne;
-    }
-    GCNN_CUDA_TRY(cudaMemcpyAsync(c->stage_dev, h, o, cudaMemcpyHostToDevice, c->stream));
-    GCNN_CUDA_TRY(cudaEventRecord(c->stage_ev[q], c->stream));
-    c->stage_used[q] = true;
-    const char *d = c->stage_dev;
-    StoreView v{reinterpret_cast<const int64_t *>(d + o_np), reinterpret_cast<const int64_t *>(d + o_ep),
-                reinterpret_cast<const uint8_t *>(d + o_t), reinterpret_cast<const uint8_t *>(d + o_e),
-                reinterpret_cast<const float *>(d + o_y), F > 0 ? reinterpret_cast<const float *>(d + o_a) : nullptr,
-                F};
-    PhaseScope ps(c, GCNN_PHASE_COLLATE);
-    GCNN_TRY(launch_collate(n, nullptr, v, c->bb, c->scal_tab, c->Nc, c->Ec, c->err, c->stream));
   }
   fill_batch(c, n, N, E, out);
   c->have_fwd = false;
   return GCNN_OK;
+}
+
+int ctx_collate_files(gcnn_ctx *c, const char *const *paths, int32_t n, gcnn_batch *out) {
+  // one read per file, in order (the per-graph-file loading path)
+  std::vector<GraphFile> files((size_t)n);
+  int64_t N = 0, E = 0;
+  GCNN_TRY(check_caps(c, n, 0, 0));
+  for (int32_t g = 0; g < n; ++g) {
+    GCNN_TRY(read_graph_file(paths[g], &files[(size_t)g]));
+    if (files[(size_t)g].F != c->cfg.edge_features)
+      return set_error(GCNN_EINVAL, "%s has %d bond features per edge, the model %d", paths[g], files[(size_t)g].F,
+                       c->cfg.edge_features);
+    N += files[(size_t)g].n;
+    E += files[(size_t)g].e;
+  }
+  GCNN_TRY(check_caps(c, n, N, E));
+  const int F = c->cfg.edge_features;
+  auto sizes = [&](int32_t g, int64_t *nn, int64_t *ne) {
+    *nn = files[(size_t)g].n;
+    *ne = files[(size_t)g].e;
+  };
+  auto fill = [&](int32_t g, uint8_t *ty, uint8_t *ed, float *y, float *at) {
+    const GraphFile &f = files[(size_t)g];
+    memcpy(ty, f.types, (size_t)f.n);
+    memcpy(ed, f.edges, 2 * (size_t)f.e);
+    if (F > 0) memcpy(at, f.attr, sizeof(float) * (size_t)f.e * F);
+    *y = f.y;
+  };
+  return collate_staged(c, n, N, E, F, sizes, fill, out);
 }
 
 int ctx_collate_range(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count, gcnn_batch *out) {

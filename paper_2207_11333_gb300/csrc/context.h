@@ -109,6 +109,7 @@ class PhaseScope {
 };
 
 int ctx_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n, gcnn_batch *out);
+int ctx_collate_files(gcnn_ctx *c, const char *const *paths, int32_t n, gcnn_batch *out);
 int ctx_collate_range(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count, gcnn_batch *out);
 int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train);
 int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, double *loss_accum);

@@ -1,6 +1,8 @@
 // Packed graph store (host side).
 #pragma once
 
+#include <vector>
+
 #include "kernels.cuh"
 
 struct gcnn_store {
@@ -22,6 +24,17 @@ struct gcnn_store {
 };
 
 namespace gcnn {
+// One graph read from a per-graph file (gcnn_store_pack's input format).
+struct GraphFile {
+  std::vector<uint8_t> buf;  // the whole file
+  int n = 0, e = 0, F = 0;
+  float y = 0.f;
+  const uint8_t *types = nullptr, *edges = nullptr;
+  const float *attr = nullptr;
+};
+int read_graph_file(const char *path, GraphFile *out);
+int store_pack(const char *const *paths, int64_t n_files, const char *out_path, int n_threads);
+
 const char *last_error();
 int store_open(const char *path, gcnn_store **out);
 int store_close(gcnn_store *st);

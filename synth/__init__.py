@@ -21,11 +21,13 @@ paper's schema of one global array per graph attribute, Section 4, Table 1):
     64      i64         byte offset of edges     (u8[2E], local (src, dst) pairs)
     72      i64         byte offset of y         (f32[G])
     80      i64         file size in bytes
-    88      i64         F  bond features per edge      (version 2 only)
-    96      i64         byte offset of edge_attr (f32[E][F], version 2 only)
+    88      i64         F  bond features per edge      (version 2 only; may be 0)
+    96      i64         byte offset of edge_attr (f32[E][F], version 2, F > 0)
+    104     i64         byte offset of node_y    (f32[N], version 2; 0 = none)
     88..127 zero otherwise
 Version 2 adds the edges' features (Table 1's edge attributes), one row per
-stored directed edge in store order.
+stored directed edge in store order, and node-level targets (Table 1's y at
+node level), one per atom.
 Every array starts on a 64-byte boundary.  Node and edge ids inside a graph
 are local (0..n-1), so a graph is a contiguous slice of each array.
 """
@@ -179,6 +181,7 @@ class GraphSet:
     edges: np.ndarray     # uint8 [E, 2]  local (src, dst)
     y: np.ndarray         # float32 [G]
     eattr: np.ndarray | None = None   # float32 [E, F] bond features (store version 2)
+    ynode: np.ndarray | None = None   # float32 [N] node-level targets (store version 2)
 
     @property
     def F(self) -> int:
@@ -211,8 +214,13 @@ class GraphSet:
         if self.eattr is not None:
             eattr = (np.concatenate([self.eattr[self.edge_ptr[g]:self.edge_ptr[g + 1]] for g in ids]) if len(ids)
                      else np.zeros((0, self.F), np.float32))
+        ynode = None
+        if self.ynode is not None:
+            ynode = (np.concatenate([self.ynode[self.node_ptr[g]:self.node_ptr[g + 1]] for g in ids]) if len(ids)
+                     else np.zeros(0, np.float32))
         return GraphSet(node_ptr, edge_ptr, np.ascontiguousarray(types), np.ascontiguousarray(edges), self.y[ids].copy(),
-                        None if eattr is None else np.ascontiguousarray(eattr))
+                        None if eattr is None else np.ascontiguousarray(eattr),
+                        None if ynode is None else np.ascontiguousarray(ynode))
 
 
 def bond_features(seed: int, gs: GraphSet, F: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
@@ -263,12 +271,38 @@ def _align(x: int, a: int = 64) -> int:
     return (x + a - 1) // a * a
 
 
+GRAPH_MAGIC = b"GCNNGRF1"
+
+
+def write_graph_files(directory: str, gs: GraphSet, ids=None) -> list:
+    """One file per graph (the layout a packed store replaces); returns the paths.
+    Format: magic, int32 n, e, F, float32 y, uint8 types[n], uint8 edges[e][2],
+    zero padding to 4 bytes, float32 edge_attr[e][F]."""
+    os.makedirs(directory, exist_ok=True)
+    paths = []
+    for g in (range(gs.n_graphs) if ids is None else ids):
+        n0, n1 = int(gs.node_ptr[g]), int(gs.node_ptr[g + 1])
+        e0, e1 = int(gs.edge_ptr[g]), int(gs.edge_ptr[g + 1])
+        n, e, F = n1 - n0, e1 - e0, gs.F
+        head = GRAPH_MAGIC + np.array([n, e, F], "<i4").tobytes() + np.array([gs.y[g]], "<f4").tobytes()
+        body = gs.types[n0:n1].tobytes() + np.ascontiguousarray(gs.edges[e0:e1], np.uint8).tobytes()
+        pad = b"\0" * ((-(24 + len(body))) % 4)
+        attr = np.ascontiguousarray(gs.eattr[e0:e1], "<f4").tobytes() if F else b""
+        path = os.path.join(directory, f"g{g:07d}.gcg")
+        with open(path, "wb") as f:
+            f.write(head + body + pad + attr)
+        paths.append(path)
+    return paths
+
+
 def write_store(path: str, gs: GraphSet) -> None:
     """Write a GraphSet as one packed store file (layout in the module docstring)."""
     G, N, E, F = gs.n_graphs, gs.n_nodes, gs.n_edges, gs.F
+    v2 = gs.eattr is not None or gs.ynode is not None
     offs = []
     pos = HEADER_BYTES
-    sizes = [(G + 1) * 8, (G + 1) * 8, N, 2 * E, 4 * G] + ([4 * E * F] if gs.eattr is not None else [])
+    sizes = [(G + 1) * 8, (G + 1) * 8, N, 2 * E, 4 * G] + ([4 * E * F] if gs.eattr is not None else [0]) + \
+        ([4 * N] if gs.ynode is not None else [0])
     for nbytes in sizes:
         pos = _align(pos)
         offs.append(pos)
@@ -277,16 +311,18 @@ def write_store(path: str, gs: GraphSet) -> None:
     buf = np.zeros(total, np.uint8)
     hdr = np.zeros(HEADER_BYTES, np.uint8)
     hdr[0:8] = np.frombuffer(STORE_MAGIC, np.uint8)
-    hdr[8:16] = np.array([1 if gs.eattr is None else 2, N_TYPES], "<u4").view(np.uint8)
+    hdr[8:16] = np.array([2 if v2 else 1, N_TYPES], "<u4").view(np.uint8)
     hdr[16:88] = np.array([G, N, E] + offs[:5] + [total], "<i8").view(np.uint8)
-    if gs.eattr is not None:
-        hdr[88:104] = np.array([F, offs[5]], "<i8").view(np.uint8)
+    if v2:
+        hdr[88:112] = np.array([F, offs[5] if F else 0, offs[6] if gs.ynode is not None else 0],
+                               "<i8").view(np.uint8)
     buf[:HEADER_BYTES] = hdr
     arrays = [np.ascontiguousarray(gs.node_ptr, "<i8"), np.ascontiguousarray(gs.edge_ptr, "<i8"),
               np.ascontiguousarray(gs.types, np.uint8), np.ascontiguousarray(gs.edges, np.uint8).reshape(-1),
               np.ascontiguousarray(gs.y, "<f4")]
-    if gs.eattr is not None:
-        arrays.append(np.ascontiguousarray(gs.eattr, "<f4").reshape(-1))
+    arrays.append(np.ascontiguousarray(gs.eattr, "<f4").reshape(-1) if gs.eattr is not None
+                  else np.zeros(0, np.uint8))
+    arrays.append(np.ascontiguousarray(gs.ynode, "<f4") if gs.ynode is not None else np.zeros(0, np.uint8))
     for off, arr in zip(offs, arrays):
         b = arr.view(np.uint8).reshape(-1)
         buf[off:off + b.size] = b

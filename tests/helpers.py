@@ -33,7 +33,7 @@ def graph_set(seed: int, G: int, lo: int, hi: int, y_seed: int | None = 99) -> s
 
 
 def to_store(gs: synth.GraphSet) -> oracle.Store:
-    return oracle.store_from_arrays(gs.node_ptr, gs.edge_ptr, gs.types, gs.edges, gs.y, gs.eattr)
+    return oracle.store_from_arrays(gs.node_ptr, gs.edge_ptr, gs.types, gs.edges, gs.y, gs.eattr, gs.ynode)
 
 
 def oracle_batch(gs: synth.GraphSet, ids=None, delta: float | None = None):

@@ -396,6 +396,116 @@ def pin_bond_features_permutation_invariance():
     assert rel_norm(oracle.forward(d, p, b2), pred[order]) < 1e-12
 
 
+def _node_model(seed: int, H: int, L: int, weight: float = 1.0):
+    d = oracle.Dims(H=H, L=L, NH=1, node_weight=weight)
+    base = synth.init_params(seed, H, L).astype(np.float64)
+    head = synth.init_params(seed + 100, H, 1).astype(np.float64)    # reuse a head block's draws
+    hs = H * H + 2 * H + 1
+    pad = np.zeros((base.size + 3) // 4 * 4 - base.size)
+    return d, np.concatenate([base, pad, head[-hs:]])
+
+
+def _with_node_targets(gs, seed=51):
+    gs.ynode = synth.uniform(seed, 0, gs.n_nodes, -1.0, 1.0).astype(np.float32)
+    return gs
+
+
+def pin_node_head_weight_zero():
+    """Node-loss weight 0: the trunk and graph-head gradients equal those of the model
+    without a node head, and the node head's own gradients vanish."""
+    d, p = _node_model(3, 8, 2, weight=0.0)
+    d0 = oracle.Dims(H=8, L=2)
+    n0 = oracle.param_count(d0)
+    gs = _with_node_targets(graph_set(9, 8, 5, 18))
+    _, b, _ = oracle_batch(gs)
+    l, g, _, _ = oracle.backward(d, p, b)
+    l0, g0, _, _ = oracle.backward(d0, p[:n0], b)
+    assert l == l0 and np.array_equal(g[:n0], g0) and not np.any(g[n0:])
+
+
+def pin_node_head_constant_output():
+    """W1n = 0: every atom predicts c = w2n . ReLU(b1n) + b2n, the node loss is
+    mean((c - y_i)^2) and its gradient w.r.t. b2n is weight * 2 mean(c - y_i)."""
+    d, p = _node_model(4, 8, 1, weight=0.75)
+    V = oracle.split_params(d, p)
+    V["w1n"][:] = 0.0
+    gs = _with_node_targets(graph_set(11, 7, 5, 15))
+    _, b, _ = oracle_batch(gs)
+    pred, predn = oracle.forward(d, p, b, want_nodes=True)
+    c = float(np.maximum(V["b1n"], 0.0) @ V["w2n"] + V["b2n"][0])
+    assert np.allclose(predn, c, rtol=0, atol=1e-14)
+    loss, grad, _, _ = oracle.backward(d, p, b)
+    yn = b.ynode.astype(np.float64)
+    graph_mse = np.mean((pred - b.y.astype(np.float64)) ** 2)
+    assert abs(loss - (graph_mse + 0.75 * np.mean((c - yn) ** 2))) < 1e-12 * loss
+    G = oracle.split_params(d, grad)
+    assert abs(G["b2n"][0] - 0.75 * 2.0 * np.mean(c - yn)) < 1e-12
+
+
+def pin_node_head_autograd():
+    """With a node head, every gradient equals torch autograd (FP64)."""
+    d, p = _node_model(5, 8, 2, weight=0.5)
+    gs = _with_node_targets(graph_set(23, 6, 5, 12))
+    gs.y = synth.uniform_targets(24, 0, gs.n_graphs, 1, 10)
+    _, b, _ = oracle_batch(gs)
+    x0 = synth.normal(25, 0, b.N * d.H).reshape(b.N, d.H)
+    loss, grad, dx0, _ = oracle.backward(d, p, b, x0=x0)
+    rloss, rgrad, rdx0, _ = torch_ref.loss_and_grads(d, p, b, x0)
+    assert abs(loss - rloss) <= 1e-12 * abs(rloss)
+    views, rviews = oracle.split_params(d, grad), oracle.split_params(d, rgrad)
+    for k in views:
+        if k != "emb":
+            assert rel_norm(views[k], rviews[k]) < 1e-10, k
+    assert rel_norm(dx0, rdx0) < 1e-10
+
+
+def pin_node_head_finite_differences():
+    """Central differences of the multitask loss w.r.t. the node head and the last layer."""
+    d, p = _node_model(6, 6, 1, weight=1.3)
+    gs = _with_node_targets(graph_set(26, 8, 5, 12))
+    gs.y = synth.uniform_targets(27, 0, gs.n_graphs, 1, 10)
+    _, b, _ = oracle_batch(gs)
+    x0 = synth.normal(28, 0, b.N * d.H).reshape(b.N, d.H)
+    loss0, grad, _, _ = oracle.backward(d, p, b, x0=x0)
+    n0 = oracle.param_count(oracle.Dims(H=d.H, L=d.L))
+    coords = np.concatenate([np.arange((n0 + 3) // 4 * 4, p.size), np.arange(d.T * d.H, d.T * d.H + 40)])
+    h = 1e-6
+    fd = np.empty(len(coords))
+    for n, k in enumerate(coords):
+        q = p.copy()
+        q[k] += h
+        lp = oracle.backward(d, q, b, x0=x0)[0]
+        q[k] -= 2 * h
+        lm = oracle.backward(d, q, b, x0=x0)[0]
+        fd[n] = (lp - lm) / (2 * h)
+    floor = 20 * np.finfo(np.float64).eps * abs(loss0) / h
+    assert np.all(np.abs(fd - grad[coords]) <= 1e-6 * np.abs(grad[coords]) + floor)
+
+
+def pin_node_head_permutation_equivariance():
+    """Relabelling atoms permutes the node-level predictions the same way."""
+    d, p = _node_model(7, 8, 2)
+    gs = graph_set(29, 6, 5, 14)
+    _, b, _ = oracle_batch(gs)
+    _, predn = oracle.forward(d, p, b, want_nodes=True)
+    rng = np.random.default_rng(4)
+    graphs, perms = [], []
+    for g in range(gs.n_graphs):
+        n = int(gs.node_ptr[g + 1] - gs.node_ptr[g])
+        perm = rng.permutation(n)
+        t = np.empty(n, np.uint8)
+        t[perm] = gs.types[gs.node_ptr[g]:gs.node_ptr[g + 1]]
+        e = gs.edges[gs.edge_ptr[g]:gs.edge_ptr[g + 1]].astype(np.int64)
+        graphs.append((t.tolist(), [(perm[u], perm[v]) for u, v in e[::2]]))
+        perms.append(perm + int(gs.node_ptr[g]))
+    _, b2, _ = oracle_batch(custom_set(graphs))
+    _, predn2 = oracle.forward(d, p, b2, want_nodes=True)
+    assert rel_norm(predn2[np.concatenate(perms)], predn) < 1e-12
+
+
+NODE_PINS = [pin_node_head_weight_zero, pin_node_head_constant_output, pin_node_head_autograd,
+             pin_node_head_finite_differences, pin_node_head_permutation_equivariance]
+
 BOND_PINS = [pin_bond_features_collated_with_their_edge, pin_bond_features_zero_weights,
              pin_bond_features_constant_is_bias_shift, pin_bond_features_autograd,
              pin_bond_features_finite_differences, pin_bond_features_permutation_invariance]
@@ -404,4 +514,4 @@ ALL_PINS = [pin_collation_lexsort, pin_sum_is_dense_adjacency_matmul, pin_aggreg
             pin_scalers_cycle_closed_form, pin_scalers_star_closed_form, pin_permutation_invariance,
             pin_pool_of_constant_graph, pin_constant_messages, pin_gradients_autograd,
             pin_gradients_autograd_continuous, pin_finite_differences, pin_adam_first_step,
-            pin_adamw_decay, pin_mse_gradient] + BOND_PINS
+            pin_adamw_decay, pin_mse_gradient] + BOND_PINS + NODE_PINS

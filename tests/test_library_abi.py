@@ -106,3 +106,28 @@ def test_store_with_bond_features(tmp_path):
     gs.eattr = np.zeros((gs.n_edges, 17), np.float32)
     with pytest.raises(g.GcnnError, match="EFORMAT"):
         g.Store(_bad_store(tmp_path, gs, "too_many"))
+
+
+@pytest.mark.parametrize("F", [0, 3])
+def test_pack_per_graph_files_matches_store_writer(tmp_path, F):
+    """gcnn_store_pack of one file per graph writes the same bytes as the store
+    writer, whatever the thread count; a bad file is named in the error."""
+    import paper_2207_11333_gb300 as g
+    gs = synth.molecules_uniform(8, 40, 3, 30)
+    gs.y = synth.uniform_targets(9, 0, 40, 1, 10)
+    if F:
+        gs.eattr = synth.bond_features(10, gs, F)
+    paths = synth.write_graph_files(str(tmp_path / "files"), gs)
+    ref = str(tmp_path / "ref.gcnn")
+    synth.write_store(ref, gs)
+    want = open(ref, "rb").read()
+    for threads in (1, 3, 8):
+        out = str(tmp_path / f"packed{threads}.gcnn")
+        g.store_pack(paths, out, threads)
+        assert open(out, "rb").read() == want
+    st = g.Store(str(tmp_path / "packed8.gcnn"))
+    assert (st.n_graphs, st.edge_features) == (40, F)
+    bad = open(paths[7], "rb").read()
+    open(paths[7], "wb").write(bad[:-1])
+    with pytest.raises(g.GcnnError, match="g0000007"):
+        g.store_pack(paths, str(tmp_path / "x.gcnn"), 4)

@@ -40,6 +40,10 @@ MUTATIONS = {
                                  "eattr[p * F + f] = st_eattr[p * F + f];"),
     "bond_attr_left_behind_by_sort": ("col[b + 1] = col[b]; pos_sid[b + 1] = pos_sid[b]; --b;",
                                       "col[b + 1] = col[b]; --b;"),
+    "node_loss_over_graphs": ("dpredn[i] = N > 0 ? node_weight * 2.0 * r / (double)N : 0.0;",
+                              "dpredn[i] = N > 0 ? node_weight * 2.0 * r / (double)G : 0.0;"),
+    "node_head_no_relu": ("out += (z > 0.0 ? z : 0.0) * w2[c];", "out += z * w2[c];"),
+    "node_head_grad_not_into_trunk": ("dx[i * H + k] += w1[(int64_t)k * Hh + c] * dz;", ";"),
 }
 
 

@@ -34,11 +34,17 @@ def _views(d, p):
         k = (k + 3) // 4 * 4          # bond rows start at a multiple of 4 floats
         for l in range(L):
             take(f"edge_w{l}", (d.F, H))
+    if getattr(d, "NH", 0):
+        k = (k + 3) // 4 * 4          # node head likewise
+        take("w1n", (H, Hh))
+        take("b1n", (Hh,))
+        take("w2n", (Hh,))
+        take("b2n", (1,))
     return out
 
 
 def forward(d, params: torch.Tensor, b, x0: torch.Tensor | None = None, eps: float = 1e-5,
-            layers: list | None = None):
+            layers: list | None = None, nodes: list | None = None):
     """Predictions (G,) for a collated batch ``b`` (oracle.Batch) -- autograd-able."""
     W = _views(d, params)
     H = d.H
@@ -76,15 +82,21 @@ def forward(d, params: torch.Tensor, b, x0: torch.Tensor | None = None, eps: flo
     gid = torch.from_numpy(b.graph_id.astype(np.int64))
     cnt = torch.bincount(gid, minlength=b.G).double().clamp(min=1).unsqueeze(1)
     g = torch.zeros(b.G, H, dtype=x.dtype).index_add(0, gid, x) / cnt
+    if nodes is not None and getattr(d, "NH", 0):       # node-level head, no pooling
+        nodes.append(torch.relu(x @ W["w1n"] + W["b1n"]) @ W["w2n"] + W["b2n"])
     return torch.relu(g @ W["w1"] + W["b1"]) @ W["w2"] + W["b2"]
 
 
 def loss_and_grads(d, params_np, b, x0_np=None, eps: float = 1e-5):
     p = torch.tensor(params_np, dtype=torch.float64, requires_grad=True)
     x0 = None if x0_np is None else torch.tensor(x0_np, dtype=torch.float64, requires_grad=True)
-    pred = forward(d, p, b, x0, eps)
+    nodes = []
+    pred = forward(d, p, b, x0, eps, nodes=nodes)
     y = torch.from_numpy(b.y.astype(np.float64))
     loss = torch.mean((pred - y) ** 2)
+    if nodes:
+        yn = torch.from_numpy(b.ynode.astype(np.float64))
+        loss = loss + d.node_weight * torch.mean((nodes[0] - yn) ** 2)
     loss.backward()
     return (float(loss.detach()), p.grad.numpy().copy(), None if x0 is None else x0.grad.numpy().copy(),
             pred.detach().numpy().copy())
