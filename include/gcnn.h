@@ -36,6 +36,9 @@
  *   g             = mean of x^L over the graph's nodes
  *   yhat          = w2 . ReLU(W1 g + b1) + b2
  *   loss          = (1/G) sum_g (yhat_g - y_g)^2
+ *   optional node-level head (config node_head), on every atom of x^L:
+ *   yhat_i        = w2n . ReLU(W1n x_i + b1n) + b2n
+ *   loss         += node_loss_weight (1/N) sum_i (yhat_i - y_i)^2
  * with std = sqrt(ReLU(var) + std_eps), var two-pass; d_i = 0 gives zero
  * aggregates; the scalers use max(d_i, 1); min/max ties share the gradient
  * equally; ReLU'(0) = 0.
@@ -51,6 +54,8 @@
  *   head: w1[H][Hh], b1[Hh], w2[Hh], b2[1]
  *   with F bond features: 0..3 unused floats up to the next multiple of 4,
  *   then per layer edge_w[F][H] (the bond rows of W_M)
+ *   with the node head: 0..3 unused floats up to the next multiple of 4,
+ *   then w1n[H][Hh], b1n[Hh], w2n[Hh], b2n[1]
  */
 #ifndef GCNN_H_
 #define GCNN_H_
@@ -96,8 +101,9 @@ int gcnn_version(void);
  * array (the single-file analogue of the paper's schema, Sec. 4, Table 1):
  * node_ptr[G+1], edge_ptr[G+1] (int64 offsets), types[N] (uint8 atom type),
  * edges[E][2] (uint8 local source, destination), y[G] (float32 target);
- * version-2 files add edge_attr[E][F] (float32 bond features, F <= 16), and
- * both directions of a bond must carry bitwise-equal features.
+ * version-2 files may add edge_attr[E][F] (float32 bond features, F <= 16;
+ * both directions of a bond must carry bitwise-equal features) and node_y[N]
+ * (float32 node-level targets).
  * Graphs must have 1..255 nodes and at most 1024 directed edges, local ids
  * < n; each undirected bond is stored as two directed edges.  The file is
  * validated once at open (GCNN_EFORMAT on any violation).  A store is
@@ -113,6 +119,8 @@ int gcnn_store_close(gcnn_store *st);
 int gcnn_store_info(const gcnn_store *st, int64_t *n_graphs, int64_t *n_nodes, int64_t *n_edges);
 /* Bond features per edge (0 for a version-1 store). */
 int gcnn_store_edge_features(const gcnn_store *st, int32_t *n_features);
+/* Whether the store carries node-level targets (1) or not (0). */
+int gcnn_store_has_node_targets(const gcnn_store *st, int32_t *has);
 /* Node and edge totals of the batch graph_ids[0..n) (host ids). */
 int gcnn_store_batch_size(const gcnn_store *st, const int64_t *graph_ids, int64_t n,
                           int64_t *n_nodes, int64_t *n_edges);
@@ -163,6 +171,11 @@ typedef struct gcnn_config {
   int32_t edge_features;  /* F bond features per edge, 0..16 (0); a store fed
                              to the context must carry exactly F           */
   int32_t reserved0;
+  int32_t node_head;      /* 1: add the node-level head (Sec. 3.1 node-level
+                             properties; Table 1 node-level y); the store
+                             must carry node targets; head_hidden % 4 == 0 */
+  int32_t reserved1;
+  double node_loss_weight;  /* weight of the node-level MSE in the loss (1) */
 } gcnn_config;
 
 typedef struct gcnn_ctx gcnn_ctx;
@@ -212,6 +225,8 @@ typedef struct gcnn_batch {
   const float *edge_attr;   /* (device) [E] rows of bond features per edge
                                slot, row stride F rounded up to a multiple
                                of 4 floats (NULL when F = 0)                  */
+  const float *node_y;      /* (device) [N] node-level targets (NULL without
+                               the node head)                                 */
 } gcnn_batch;
 
 /* Collate graphs graph_ids[0..n_graphs) (host ids) of `st` on the device.
@@ -238,12 +253,15 @@ int gcnn_batch_export(gcnn_ctx *ctx, const gcnn_batch *b, int32_t *node_off, int
 
 /* ------------------------------------------------------------------ training */
 /* Forward pass; pred (device, G floats) may be NULL.  train = 1 keeps what
- * backward needs. */
+ * backward needs (with the node head it also forms the node-level loss
+ * gradient from the batch's node targets). */
 int gcnn_forward(gcnn_ctx *ctx, const gcnn_batch *b, float *pred, int train);
 /* Backward of the last forward(train = 1) on the same batch.  dpred (device,
  * G) = dL/dyhat, or NULL for the MSE loss against the batch targets.
  * Gradients overwrite the context's gradient buffer.  loss_accum (device,
- * 3 doubles, may be NULL): += sum (yhat-y)^2, += sum |yhat-y|, += G. */
+ * 3 doubles, 5 with the node head, may be NULL): += sum (yhat-y)^2,
+ * += sum |yhat-y|, += G, then += sum over atoms (yhat_i-y_i)^2, += N.  The
+ * node-level loss always uses the batch's node targets (dpred is graph-level). */
 int gcnn_backward(gcnn_ctx *ctx, const gcnn_batch *b, const float *dpred, double *loss_accum);
 /* AdamW step over all parameters with learning rate lr. */
 int gcnn_step(gcnn_ctx *ctx, float lr);
@@ -252,6 +270,9 @@ int gcnn_step(gcnn_ctx *ctx, float lr);
 int gcnn_train_step(gcnn_ctx *ctx, const gcnn_batch *b, float lr, double *loss_accum);
 /* Copy x^l (l = 0..L, N x H floats) of the last forward to host.  Sync. */
 int gcnn_get_activation(gcnn_ctx *ctx, int32_t layer, float *dst, int64_t n);
+/* Copy the node-level predictions (N floats) of the last forward to host;
+ * GCNN_ESTATE without the node head.  Synchronous. */
+int gcnn_get_node_predictions(gcnn_ctx *ctx, float *dst, int64_t n);
 
 /* ------------------------------------------------------------------ timing
  * Per-phase device time of the step (the paper's load / forward / backward /
@@ -326,7 +347,9 @@ enum {
   GCNN_K_STEP_END = 22,         /* marker after a train step (timeline on only) */
   GCNN_K_AGG_BWD_FUSED = 23,    /* aggregation backward over whole graphs      */
   GCNN_K_AGG_BWD_CHUNKS = 24,   /* its partition of the batch into chunks      */
-  GCNN_NKERNEL = 25
+  GCNN_K_NODE_PRED = 25,        /* node-level head: outputs and loss gradient  */
+  GCNN_K_NODE_GRAD = 26,        /* node-level head: w2n, b2n and loss sums     */
+  GCNN_NKERNEL = 27
 };
 int gcnn_timeline_enable(gcnn_ctx *ctx, int32_t capacity);
 int gcnn_timeline_read(gcnn_ctx *ctx, int32_t *ids, int64_t *t_ns, int32_t max, int32_t *n);

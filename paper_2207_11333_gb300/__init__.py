@@ -28,7 +28,7 @@ KERNELS = {1: "collate_scan", 2: "collate_graph", 3: "embed", 4: "embed_bwd", 5:
            7: "agg_bwd_gather", 8: "gemm_tc_partial", 9: "gemm_tc_c", 10: "gemm_tc_d3", 11: "gemm_tc_reduce",
            12: "gemm_simt", 13: "gemm_simt_reduce", 14: "pool_fwd", 15: "pool_bwd", 16: "head_graph",
            17: "head_grad", 18: "colsum", 19: "adam", 20: "cast_bf16", 21: "pack_layer", 22: "step_end",
-           23: "agg_bwd_fused", 24: "agg_bwd_chunks"}
+           23: "agg_bwd_fused", 24: "agg_bwd_chunks", 25: "node_pred", 26: "node_grad"}
 
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EFORMAT", -5: "EDEVICE", -6: "ETIMEDOUT",
            -7: "EAGAIN", -8: "ESTATE"}
@@ -46,14 +46,15 @@ class Config(ctypes.Structure):
                 ("max_edges", ctypes.c_int32), ("precision", ctypes.c_int32), ("recompute", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("delta", ctypes.c_double), ("std_eps", ctypes.c_double),
                 ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("adam_eps", ctypes.c_double),
-                ("weight_decay", ctypes.c_double), ("edge_features", ctypes.c_int32), ("reserved0", ctypes.c_int32)]
+                ("weight_decay", ctypes.c_double), ("edge_features", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("node_head", ctypes.c_int32), ("reserved1", ctypes.c_int32), ("node_loss_weight", ctypes.c_double)]
 
 
 class BatchStruct(ctypes.Structure):
     _fields_ = [("n_graphs", ctypes.c_int32), ("n_nodes", ctypes.c_int32), ("n_edges", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)] + [(n, ctypes.c_void_p) for n in (
                     "node_off", "edge_off", "graph_id", "row_ptr", "col", "rev", "deg", "amp", "att", "types", "y",
-                    "edge_attr")]
+                    "edge_attr", "node_y")]
 
 
 class ServeConfig(ctypes.Structure):
@@ -80,6 +81,8 @@ def _load() -> ctypes.CDLL:
         "gcnn_store_close": (i32, [vp]),
         "gcnn_store_info": (i32, [vp, P(i64), P(i64), P(i64)]),
         "gcnn_store_edge_features": (i32, [vp, P(i32)]),
+        "gcnn_store_has_node_targets": (i32, [vp, P(i32)]),
+        "gcnn_get_node_predictions": (i32, [vp, vp, i64]),
         "gcnn_store_pack": (i32, [vp, i64, ctypes.c_char_p, i32]),
         "gcnn_collate_files": (i32, [vp, vp, i32, vp]),
         "gcnn_store_batch_size": (i32, [vp, vp, i64, P(i64), P(i64)]),
@@ -195,6 +198,8 @@ class Store:
         f = ctypes.c_int32()
         _check(lib.gcnn_store_edge_features(self._h, ctypes.byref(f)))
         self.edge_features = f.value
+        _check(lib.gcnn_store_has_node_targets(self._h, ctypes.byref(f)))
+        self.has_node_targets = bool(f.value)
 
     @property
     def handle(self):
@@ -291,7 +296,7 @@ class Batch:
         spec = {"node_off": (G + 1, torch.int32), "edge_off": (G + 1, torch.int32), "graph_id": (N, torch.int32),
                 "row_ptr": (N + 1, torch.int32), "col": (E, torch.int32), "rev": (E, torch.int32),
                 "deg": (N, torch.int32), "amp": (N, torch.float32), "att": (N, torch.float32),
-                "types": (N, torch.uint8), "y": (G, torch.float32)}[name]
+                "types": (N, torch.uint8), "y": (G, torch.float32), "node_y": (N, torch.float32)}[name]
         return _wrap_device(getattr(self.s, name), spec[0], spec[1])
 
 
@@ -435,6 +440,12 @@ class Context:
     def activations(self, batch: Batch) -> list[np.ndarray]:
         self._last_nodes = batch.n_nodes
         return [self.activation(l) for l in range(self.cfg.layers + 1)]
+
+    def node_predictions(self, batch: Batch) -> np.ndarray:
+        """Node-level outputs of the last forward (node head), N floats."""
+        out = np.empty(batch.n_nodes, np.float32)
+        _check(lib.gcnn_get_node_predictions(self._h, _np_ptr(out), batch.n_nodes))
+        return out
 
 
 # ---------------------------------------------------------------- operators

@@ -49,9 +49,9 @@ int64_t layer_size_of(int64_t H) { return 2 * H * H + H + 16 * H * H + H; }
 int64_t param_count_of(const gcnn_config &c) {
   const int64_t H = c.hidden, Hh = c.head_hidden;
   const int64_t base = (int64_t)c.n_types * H + (int64_t)c.layers * layer_size_of(H) + H * Hh + 2 * Hh + 1;
-  if (c.edge_features == 0) return base;
-  // bond rows start at a multiple of 4 floats (16-byte rows for vector loads)
-  return (base + 3) / 4 * 4 + (int64_t)c.layers * c.edge_features * H;
+  // bond rows, then the node head, each from a multiple of 4 floats (16-byte rows)
+  const int64_t trunk = c.edge_features == 0 ? base : (base + 3) / 4 * 4 + (int64_t)c.layers * c.edge_features * H;
+  return c.node_head ? (trunk + 3) / 4 * 4 + H * Hh + 2 * Hh + 1 : trunk;
 }
 
 int check_config(const gcnn_config *c) {
@@ -71,6 +71,9 @@ int check_config(const gcnn_config *c) {
   if (!(c->delta > 0.0) || !(c->std_eps >= 0.0)) return set_error(GCNN_EINVAL, "delta must be > 0, std_eps >= 0");
   if (c->edge_features < 0 || c->edge_features > 16)
     return set_error(GCNN_EINVAL, "edge_features must be in [0, 16] (got %d)", c->edge_features);
+  if (c->node_head != 0 && c->node_head != 1) return set_error(GCNN_EINVAL, "node_head must be 0 or 1");
+  if (c->node_head && (c->head_hidden % 4 || !(c->node_loss_weight >= 0.0)))
+    return set_error(GCNN_EINVAL, "node head: head_hidden must be a multiple of 4 and node_loss_weight >= 0");
   return GCNN_OK;
 }
 
@@ -88,7 +91,8 @@ int make_scaler_table(gcnn_ctx *c) {
 size_t stage_bytes_of(int Gc, int Nc, int Ec, int F) {
   // mini-store: node_ptr, edge_ptr (i64 [G+1]), y (f32 [G]), types (u8 [N]), edges (u8 [2E]),
   // bond features (f32 [E][F]), ids
-  return 3 * 8 * (size_t)(Gc + 1) + 4 * (size_t)Gc + (size_t)Nc + 2 * (size_t)Ec + 4 * (size_t)Ec * F + 5 * 64;
+  // (+ node targets f32 [N])
+  return 3 * 8 * (size_t)(Gc + 1) + 4 * (size_t)Gc + 5 * (size_t)Nc + 2 * (size_t)Ec + 4 * (size_t)Ec * F + 6 * 64;
 }
 
 void destroy_ctx(gcnn_ctx *c) {
@@ -177,6 +181,12 @@ int gcnn_store_edge_features(const gcnn_store *st, int32_t *f) {
   return GCNN_OK;
 }
 
+int gcnn_store_has_node_targets(const gcnn_store *st, int32_t *has) {
+  if (!st || !has) return set_error(GCNN_EINVAL, "null argument");
+  *has = st->ynode != nullptr;
+  return GCNN_OK;
+}
+
 int gcnn_store_batch_size(const gcnn_store *st, const int64_t *ids, int64_t n, int64_t *nn, int64_t *ne) {
   if (!st || (!ids && n > 0) || n < 0 || !nn || !ne) return set_error(GCNN_EINVAL, "store_batch_size: bad arguments");
   return store_batch_size(st, ids, n, nn, ne);
@@ -210,6 +220,7 @@ int gcnn_config_default(gcnn_config *cfg, int32_t hidden, int32_t layers, int32_
   cfg->beta2 = 0.999;
   cfg->adam_eps = 1e-8;
   cfg->weight_decay = 0.0;
+  cfg->node_loss_weight = 1.0;
   return GCNN_OK;
 }
 
@@ -243,6 +254,11 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
     wsf = std::max(wsf, gemm_simt_workspace_floats(n, h, 3 * h));
     if (cfg->edge_features > 0)  // bond rows of W_M: e^T dm over the edges
       wsf = std::max(wsf, gemm_simt_workspace_floats(cfg->edge_features, h, (int)Ec));
+    if (cfg->node_head) {  // node head: x W1n, dz W1n^T, [x ; 1]^T dz
+      wsf = std::max(wsf, gemm_simt_workspace_floats(n, (int)Hh, h));
+      wsf = std::max(wsf, gemm_simt_workspace_floats(n, h, (int)Hh));
+      wsf = std::max(wsf, gemm_simt_workspace_floats(h + 1, (int)Hh, n));
+    }
     if (cfg->precision == GCNN_PREC_BF16) {
       const int r64 = (h + 63) / 64 * 64, r3 = (3 * h + 63) / 64 * 64, r16 = (16 * h + 63) / 64 * 64;
       wsf = std::max(wsf, gemm_tc_workspace_floats(n, 2 * h, r64));
@@ -267,6 +283,9 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   const size_t o_dims = cv.take<int>(4), o_ids = cv.take<int64_t>(Gc);
   const int F4 = (cfg->edge_features + 3) & ~3;  // 16-byte rows of bond features
   const size_t o_eattr = cv.take<float>((size_t)Ec * F4);
+  const size_t NHn = cfg->node_head ? Nc : 0;  // node head buffers
+  const size_t o_ynode = cv.take<float>(NHn), o_zn = cv.take<float>(NHn * Hh), o_dzn = cv.take<float>(NHn * Hh);
+  const size_t o_predn = cv.take<float>(NHn), o_dpredn = cv.take<float>(NHn), o_dxn = cv.take<float>(NHn * H);
   c->stage_bytes = stage_bytes_of((int)Gc, (int)Nc, (int)Ec, cfg->edge_features);
   const size_t o_stage = cv.take<char>(c->stage_bytes);
   const size_t o_xs = cv.take<float>((L + 1) * Nc * H), o_pq = cv.take<float>(L * Nc * 2 * H);
@@ -307,6 +326,11 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   c->bb.dims = (int *)(b + o_dims); c->ids_dev = (int64_t *)(b + o_ids);
   c->bb.eattr = cfg->edge_features > 0 ? (float *)(b + o_eattr) : nullptr;
   c->bb.eattr_ld = F4;
+  if (cfg->node_head) {
+    c->bb.ynode = (float *)(b + o_ynode);
+    c->zn = (float *)(b + o_zn); c->dzn = (float *)(b + o_dzn); c->predn = (float *)(b + o_predn);
+    c->dpredn = (float *)(b + o_dpredn); c->dxn = (float *)(b + o_dxn);
+  }
   c->stage_dev = b + o_stage;
   c->xs = (float *)(b + o_xs); c->PQ = (float *)(b + o_pq); c->agg = fp32_agg ? (float *)(b + o_agg) : nullptr;
   c->pooled = (float *)(b + o_pool); c->z1 = (float *)(b + o_z1); c->pred = (float *)(b + o_pred);
@@ -650,6 +674,14 @@ int gcnn_get_activation(gcnn_ctx *c, int32_t layer, float *dst, int64_t n) {
 }
 
 // ---------------------------------------------------------------- timing
+int gcnn_get_node_predictions(gcnn_ctx *c, float *dst, int64_t n) {
+  if (!c || !dst) return set_error(GCNN_EINVAL, "get_node_predictions: bad arguments");
+  if (!c->predn) return set_error(GCNN_ESTATE, "get_node_predictions: the model has no node-level head");
+  if (n != (int64_t)c->fwd_N) return set_error(GCNN_EINVAL, "get_node_predictions: expected N floats");
+  GCNN_CUDA_TRY(cudaMemcpyAsync(dst, c->predn, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  return sync(c);
+}
+
 int gcnn_profile_enable(gcnn_ctx *c, int enable) {
   if (!c) return set_error(GCNN_EINVAL, "null context");
   c->prof_on = enable != 0;

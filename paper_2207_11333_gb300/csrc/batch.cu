@@ -28,11 +28,14 @@ void fill_batch(const gcnn_ctx *c, int G, int64_t N, int64_t E, gcnn_batch *out)
   out->types = c->bb.types;
   out->y = c->bb.y;
   out->edge_attr = c->cfg.edge_features > 0 ? c->bb.eattr : nullptr;
+  out->node_y = c->bb.ynode;
 }
 
 int check_features(const gcnn_ctx *c, const gcnn_store *st) {
   if (st->F != c->cfg.edge_features)
     return set_error(GCNN_EINVAL, "store has %d bond features per edge, the model %d", st->F, c->cfg.edge_features);
+  if (c->cfg.node_head && !st->ynode)
+    return set_error(GCNN_EINVAL, "the model has a node-level head but the store carries no node targets");
   return GCNN_OK;
 }
 
@@ -51,10 +54,10 @@ int claim_stage(gcnn_ctx *c, int q) {
 }
 
 // Gather n graphs into a mini-store in pinned staging memory (node_ptr,
-// edge_ptr, y, types, edges, bond features), copy it to the device in one
-// transfer and collate it.  fill(g, types, edges, y, attr) writes graph g's
-// slices at the given destinations and returns its (nodes, edges) through
-// the sizes(g) call made first.
+// edge_ptr, y, types, edges, bond features, node targets), copy it to the
+// device in one transfer and collate it.  sizes(g) gives graph g's (nodes,
+// edges); fill(g, types, edges, y, attr, ynode) writes its slices at the
+// given destinations (ynode is nullptr without the node head).
 template <class Sizes, class Fill>
 int collate_staged(gcnn_ctx *c, int32_t n, int64_t N, int64_t E, int F, Sizes sizes, Fill fill, gcnn_batch *out) {
   const int q = c->stage_i;
@@ -68,9 +71,12 @@ int collate_staged(gcnn_ctx *c, int32_t n, int64_t N, int64_t E, int F, Sizes si
   const size_t o_t = o;  o = align_up(o + (size_t)N, 16);
   const size_t o_e = o;  o = align_up(o + 2 * (size_t)E, 16);
   const size_t o_a = o;  o = align_up(o + 4 * (size_t)E * F, 16);
+  const bool yn_on = c->bb.ynode != nullptr;
+  const size_t o_yn = o; o = align_up(o + (yn_on ? 4 * (size_t)N : 0), 16);
   if (o > c->stage_bytes) return set_error(GCNN_EINVAL, "staging buffer too small");
   int64_t *np = reinterpret_cast<int64_t *>(h + o_np), *ep = reinterpret_cast<int64_t *>(h + o_ep);
   float *y = reinterpret_cast<float *>(h + o_y), *at = reinterpret_cast<float *>(h + o_a);
+  float *yn = reinterpret_cast<float *>(h + o_yn);
   uint8_t *ty = reinterpret_cast<uint8_t *>(h + o_t), *ed = reinterpret_cast<uint8_t *>(h + o_e);
   np[0] = 0;
   ep[0] = 0;
@@ -78,7 +84,7 @@ int collate_staged(gcnn_ctx *c, int32_t n, int64_t N, int64_t E, int F, Sizes si
     int64_t nn = 0, ne = 0;
     sizes(g, &nn, &ne);
     if (np[g] + nn > N || ep[g] + ne > E) return set_error(GCNN_EINVAL, "collate: graph sizes changed while staging");
-    fill(g, ty + np[g], ed + 2 * ep[g], y + g, at + ep[g] * F);
+    fill(g, ty + np[g], ed + 2 * ep[g], y + g, at + ep[g] * F, yn_on ? yn + np[g] : nullptr);
     np[g + 1] = np[g] + nn;
     ep[g + 1] = ep[g] + ne;
   }
@@ -88,7 +94,8 @@ int collate_staged(gcnn_ctx *c, int32_t n, int64_t N, int64_t E, int F, Sizes si
   const char *d = c->stage_dev;
   StoreView v{reinterpret_cast<const int64_t *>(d + o_np), reinterpret_cast<const int64_t *>(d + o_ep),
               reinterpret_cast<const uint8_t *>(d + o_t), reinterpret_cast<const uint8_t *>(d + o_e),
-              reinterpret_cast<const float *>(d + o_y), F > 0 ? reinterpret_cast<const float *>(d + o_a) : nullptr, F};
+              reinterpret_cast<const float *>(d + o_y), F > 0 ? reinterpret_cast<const float *>(d + o_a) : nullptr, F,
+              yn_on ? reinterpret_cast<const float *>(d + o_yn) : nullptr};
   {
     PhaseScope ps(c, GCNN_PHASE_COLLATE);
     GCNN_TRY(launch_collate(n, nullptr, v, c->bb, c->scal_tab, c->Nc, c->Ec, c->err, c->stream));
@@ -114,12 +121,13 @@ int ctx_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n
       *nn = st->node_ptr[id + 1] - st->node_ptr[id];
       *ne = st->edge_ptr[id + 1] - st->edge_ptr[id];
     };
-    auto fill = [&](int32_t g, uint8_t *ty, uint8_t *ed, float *y, float *at) {
+    auto fill = [&](int32_t g, uint8_t *ty, uint8_t *ed, float *y, float *at, float *yn) {
       const int64_t id = ids[g];
       const int64_t nn = st->node_ptr[id + 1] - st->node_ptr[id], ne = st->edge_ptr[id + 1] - st->edge_ptr[id];
       memcpy(ty, st->types + st->node_ptr[id], (size_t)nn);
       memcpy(ed, st->edges + 2 * st->edge_ptr[id], 2 * (size_t)ne);
       if (F > 0) memcpy(at, st->eattr + st->edge_ptr[id] * F, sizeof(float) * (size_t)ne * F);
+      if (yn) memcpy(yn, st->ynode + st->node_ptr[id], sizeof(float) * (size_t)nn);
       *y = st->y[id];
     };
     return collate_staged(c, n, N, E, F, sizes, fill, out);
@@ -148,6 +156,7 @@ int ctx_collate_files(gcnn_ctx *c, const char *const *paths, int32_t n, gcnn_bat
   // one read per file, in order (the per-graph-file loading path)
   std::vector<GraphFile> files((size_t)n);
   int64_t N = 0, E = 0;
+  if (c->cfg.node_head) return set_error(GCNN_EINVAL, "per-graph files carry no node targets (node head)");
   GCNN_TRY(check_caps(c, n, 0, 0));
   for (int32_t g = 0; g < n; ++g) {
     GCNN_TRY(read_graph_file(paths[g], &files[(size_t)g]));
@@ -163,7 +172,7 @@ int ctx_collate_files(gcnn_ctx *c, const char *const *paths, int32_t n, gcnn_bat
     *nn = files[(size_t)g].n;
     *ne = files[(size_t)g].e;
   };
-  auto fill = [&](int32_t g, uint8_t *ty, uint8_t *ed, float *y, float *at) {
+  auto fill = [&](int32_t g, uint8_t *ty, uint8_t *ed, float *y, float *at, float *) {
     const GraphFile &f = files[(size_t)g];
     memcpy(ty, f.types, (size_t)f.n);
     memcpy(ed, f.edges, 2 * (size_t)f.e);

@@ -110,6 +110,7 @@ collate_graph_kernel(int G, const int64_t *__restrict__ ids, StoreView st, Batch
   for (int v = lane; v < n; v += 32) {
     b.types[noff + v] = st.types[np0 + v];
     b.graph_id[noff + v] = g;
+    if (b.ynode) b.ynode[noff + v] = st.ynode[np0 + v];
   }
   bool bad = false;
   for (int k = lane; k < e; k += 32) {

@@ -50,6 +50,9 @@ struct gcnn_ctx {
   float *dg = nullptr;
   float *dH = nullptr, *dX = nullptr, *dagg = nullptr, *dPQ = nullptr, *dm = nullptr;
   int *chunks = nullptr;  // work partition of the fused aggregation backward
+  // node-level head: pre-activations, their gradient, outputs, output
+  // gradients and the gradient it sends to the last layer's atoms
+  float *zn = nullptr, *dzn = nullptr, *predn = nullptr, *dpredn = nullptr, *dxn = nullptr;
   float *dPQ2 = nullptr;  // BF16: second [dP | dQ] buffer, alternating by layer
   unsigned *tickets = nullptr;  // zero-initialised completion counters of single-launch reductions
 

@@ -15,6 +15,7 @@ struct StoreView {
   const float *y;           // [G]
   const float *eattr;       // [E][F] bond features (F = 0: nullptr)
   int F;
+  const float *ynode;       // [N] node-level targets or nullptr
 };
 
 // Writable batch arrays in the context arena.
@@ -25,6 +26,7 @@ struct BatchBuf {
   int *dims;  // {G, N, E, 0}
   float *eattr;  // [E][eattr_ld] bond features in slot order (F = 0: unused)
   int eattr_ld;  // row stride: F rounded up to a multiple of 4 (16-byte rows)
+  float *ynode;  // [N] node-level targets (node head only, else nullptr)
 };
 
 // Collate graphs ids[0..G) (ids == nullptr: graphs 0..G-1) of `st`.
@@ -100,8 +102,24 @@ struct HeadArgs {
   uint16_t *D3;
   int ld3;
   const float *h, *amp, *att;
+  const float *dx_add;  // nullable: N x H added to the pooling gradient (node-level head)
 };
 int launch_head_graph(HeadArgs a, bool fwd, bool bwd, cudaStream_t s);
+// Node-level head on the last layer's atoms (zn = x W1n + b1n from a GEMM):
+// pred_n = ReLU(zn) . w2n + b2n per atom; with train, dpred_n = weight * 2
+// (pred_n - y_n) / N and dzn = [zn > 0] dpred_n w2n.
+struct NodeHeadArgs {
+  int n_cap, Hh;
+  DevDims dims;
+  const float *zn, *w2n, *b2n, *y;
+  float *pred, *dpred, *dzn;
+  float weight;
+};
+int launch_node_pred(const NodeHeadArgs &a, bool train, cudaStream_t s);
+// Node head gradients of w2n (Hh) and b2n (1) into grad_w2n[0 .. Hh], summed
+// over atoms in a fixed order, and the FP64 loss sums (squared error, count)
+// into loss_accum (nullable) as entries 3 and 4.
+int launch_node_grad(const NodeHeadArgs &a, float *grad_w2n, double *loss_accum, cudaStream_t s);
 // Head parameter gradients (w1, b1, w2, b2, contiguous in layout order) summed
 // over the batch's graphs, and the FP64 loss sums into loss_accum (nullable).
 struct HeadGradArgs {

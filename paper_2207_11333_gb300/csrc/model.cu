@@ -28,6 +28,15 @@ float *head_ptr(float *base, const gcnn_ctx *c) {
   return base + (int64_t)c->T * c->H + (int64_t)c->L * c->layer_size;
 }
 
+// node-level head w1n[H][Hh], b1n[Hh], w2n[Hh], b2n: after the bond rows (or
+// the graph head), from the next multiple of 4 floats
+float *node_head_ptr(float *base, const gcnn_ctx *c) {
+  const int64_t H = c->H, F = c->cfg.edge_features;
+  const int64_t head_end = (int64_t)c->T * H + (int64_t)c->L * c->layer_size + H * c->Hh + 2 * c->Hh + 1;
+  const int64_t trunk = F == 0 ? head_end : (head_end + 3) / 4 * 4 + (int64_t)c->L * F * H;
+  return base + (trunk + 3) / 4 * 4;
+}
+
 Seg seg(int begin, const float *ptr, int ld, const float *rowscale = nullptr,
         const float *mask = nullptr) {
   return Seg{begin, ptr, ld, rowscale, mask};
@@ -68,6 +77,18 @@ HeadArgs head_args(gcnn_ctx *c, int G, const float *dpred_in) {
     a.D3 = c->G5[0]; a.ld3 = 5 * c->H;
     a.h = xs_at(c, c->L); a.amp = c->bb.amp; a.att = c->bb.att;
   }
+  a.dx_add = c->cfg.node_head ? c->dxn : nullptr;  // formed by the forward (train)
+  return a;
+}
+
+NodeHeadArgs node_args(gcnn_ctx *c, int Ngrid) {
+  const float *w = node_head_ptr(c->params, c);
+  const int64_t HHh = (int64_t)c->H * c->Hh;
+  NodeHeadArgs a{};
+  a.n_cap = Ngrid; a.Hh = c->Hh; a.dims = DevDims{c->bb.dims};
+  a.zn = c->zn; a.w2n = w + HHh + c->Hh; a.b2n = w + HHh + 2 * c->Hh; a.y = c->bb.ynode;
+  a.pred = c->predn; a.dpred = c->dpredn; a.dzn = c->dzn;
+  a.weight = (float)c->cfg.node_loss_weight;
   return a;
 }
 
@@ -88,6 +109,56 @@ int gemm_bond_rows(gcnn_ctx *c, int Egrid, float *g_edge_w) {
   d.B.nseg = 1; d.B.seg[0] = seg(0, c->dm, c->H);
   d.C = g_edge_w; d.ldc = c->H;
   return gemm(c, d);
+}
+
+// Node-level head forward on the last layer (zn = x W1n + b1n, then the
+// per-atom output); with train also its loss gradient and dxn = dzn W1n^T,
+// which the graph head's backward adds to the pooling gradient.
+int node_head_forward(gcnn_ctx *c, int Ngrid, bool train) {
+  const int H = c->H, Hh = c->Hh;
+  const float *w = node_head_ptr(c->params, c);
+  {
+    GemmDesc d = blank();
+    d.M = Ngrid; d.N = Hh; d.K = H; d.node_dim = kNodeM;
+    d.a_kcontig = true; d.b_ncontig = true;
+    d.A.nseg = 1; d.A.seg[0] = seg(0, xs_at(c, c->L), H);
+    d.B.nseg = 1; d.B.seg[0] = seg(0, w, Hh);
+    d.C = c->zn; d.ldc = Hh; d.bias = w + (int64_t)H * Hh; d.bias_n = Hh;
+    GCNN_TRY(gemm(c, d));
+  }
+  {
+    PhaseScope ps(c, GCNN_PHASE_HEAD);
+    GCNN_TRY(launch_node_pred(node_args(c, Ngrid), train, c->stream));
+  }
+  if (train) {
+    GemmDesc d = blank();
+    d.M = Ngrid; d.N = H; d.K = Hh; d.node_dim = kNodeM;
+    d.a_kcontig = true; d.b_ncontig = false;
+    d.A.nseg = 1; d.A.seg[0] = seg(0, c->dzn, Hh);
+    d.B.nseg = 1; d.B.seg[0] = seg(0, w, Hh);
+    d.C = c->dxn; d.ldc = H;
+    GCNN_TRY(gemm(c, d));
+  }
+  return GCNN_OK;
+}
+
+// Node-level head parameter gradients: [x ; 1]^T dzn -> W1n and b1n, then
+// w2n, b2n and the node loss sums.
+int node_head_backward(gcnn_ctx *c, int Ngrid, double *loss_accum) {
+  const int H = c->H, Hh = c->Hh;
+  float *gw = node_head_ptr(c->grads, c);
+  GemmDesc d = blank();
+  d.M = H + 1; d.N = Hh; d.K = Ngrid; d.node_dim = kNodeK;
+  d.a_kcontig = false; d.b_ncontig = true;
+  d.A.nseg = 2;
+  d.A.seg[0] = seg(0, xs_at(c, c->L), H);
+  d.A.seg[1] = seg(H, nullptr, 0);
+  d.B.nseg = 1; d.B.seg[0] = seg(0, c->dzn, Hh);
+  d.C = gw; d.ldc = Hh;
+  GCNN_TRY(gemm(c, d));
+  PhaseScope ps(c, GCNN_PHASE_HEAD);
+  GCNN_TRY(launch_node_grad(node_args(c, Ngrid), gw + (int64_t)H * Hh + Hh, loss_accum, c->stream));
+  return GCNN_OK;
 }
 
 int tc(gcnn_ctx *c, const TcDesc &d) {
@@ -362,6 +433,7 @@ int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train) {
     if (bf) GCNN_TRY(tc_update(c, Ngrid, l));
     else GCNN_TRY(gemm_update(c, Ngrid, l));
   }
+  if (c->cfg.node_head) GCNN_TRY(node_head_forward(c, Ngrid, train));
   PhaseScope ps(c, GCNN_PHASE_HEAD);
   GCNN_TRY(launch_head_graph(head_args(c, G, nullptr), true, train && c->fuse_head, c->stream));
   return GCNN_OK;
@@ -370,6 +442,7 @@ int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train) {
 int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, double *loss_accum) {
   const int H = c->H;
   DevDims dims{c->bb.dims};
+  if (c->cfg.node_head) GCNN_TRY(node_head_backward(c, Ngrid, loss_accum));
   {
     PhaseScope ps(c, GCNN_PHASE_HEAD);
     if (!c->fuse_head) GCNN_TRY(launch_head_graph(head_args(c, G, dpred), false, true, c->stream));

@@ -341,6 +341,8 @@ int gcnn_serve_create(const gcnn_ctx *model, const gcnn_serve_config *cfg, gcnn_
   sc.precision = cfg->precision;
   sc.recompute = 1;  // inference: one aggregate buffer is enough
   sc.flags |= GCNN_FLAG_ROW_INVARIANT;
+  sc.node_head = 0;  // screening serves the graph-level prediction; the node head's
+                     // parameters follow all others, so the prefix is the graph model
   s->slots.resize(cfg->n_slots);
   int rc = GCNN_OK;
   for (Slot &sl : s->slots) {
@@ -352,7 +354,7 @@ int gcnn_serve_create(const gcnn_ctx *model, const gcnn_serve_config *cfg, gcnn_
     }
     rc = gcnn_create(&sc, sl.stream, &sl.ctx);
     if (rc != GCNN_OK) break;
-    rc = gcnn_set_params(sl.ctx, model->params, model->P, 1);
+    rc = gcnn_set_params(sl.ctx, model->params, sl.ctx->P, 1);
     if (rc != GCNN_OK) break;
     sl.exec.assign(cfg->n_buckets, nullptr);
   }

@@ -272,7 +272,11 @@ __global__ void __launch_bounds__(kHeadThreads) head_graph_kernel(HeadArgs a) {
     const int H4 = H >> 2;
     for (int q = tid; q < nn * H4; q += kHeadThreads) {
       const int i = n0 + q / H4, c = (q % H4) * 4;
-      const float4 d = make_float4(sv[c] / n, sv[c + 1] / n, sv[c + 2] / n, sv[c + 3] / n);
+      float4 d = make_float4(sv[c] / n, sv[c + 1] / n, sv[c + 2] / n, sv[c + 3] / n);
+      if (a.dx_add) {  // the node-level head's gradient on the same atoms
+        const float4 e = ld4(a.dx_add + (size_t)i * H + c);
+        d = make_float4(d.x + e.x, d.y + e.y, d.z + e.z, d.w + e.w);
+      }
       st4(a.dx + (size_t)i * H + c, d);
       if (a.D3) {
         const float4 m = ld4(a.h + (size_t)i * H + c);
@@ -373,6 +377,71 @@ __global__ void __launch_bounds__(kRedThreads) head_grad_kernel(HeadGradArgs a) 
         a.loss_accum[1] += sae;
         a.loss_accum[2] += (double)G;
       }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- node head
+// One warp per atom: pred = ReLU(zn) . w2n + b2n (lanes over the Hh columns,
+// fixed-order butterfly), then the loss gradient and dzn.
+constexpr int kNodeWarps = 8;
+
+__global__ void __launch_bounds__(kNodeWarps * 32) node_pred_kernel(NodeHeadArgs a, bool train) {
+  pdl_entry(GCNN_K_NODE_PRED);
+  const int N = min(a.n_cap, a.dims.nodes(a.n_cap));
+  const int i = blockIdx.x * kNodeWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i >= N) return;  // warp-uniform
+  const float *z = a.zn + (size_t)i * a.Hh;
+  float acc = 0.f;
+  for (int c = lane; c < a.Hh; c += 32) acc += fmaxf(z[c], 0.f) * a.w2n[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  const float p = acc + a.b2n[0];
+  if (lane == 0) a.pred[i] = p;
+  if (!train) return;
+  const float dp = a.weight * 2.f * (p - a.y[i]) / (float)N;
+  if (lane == 0) a.dpred[i] = dp;
+  float *dz = a.dzn + (size_t)i * a.Hh;
+  for (int c = lane; c < a.Hh; c += 32) dz[c] = z[c] > 0.f ? dp * a.w2n[c] : 0.f;
+}
+
+// w2n for columns blockIdx.x * 32 + lane (atoms strided over the 8 warps, then
+// the warps' partials in order); the last block: b2n and the loss sums.
+__global__ void __launch_bounds__(kRedThreads) node_grad_kernel(NodeHeadArgs a, float *grad, double *accum) {
+  pdl_entry(GCNN_K_NODE_GRAD);
+  __shared__ float part[kRedThreads / 32][33];
+  __shared__ double redd[kRedThreads / 32];
+  __shared__ float redf[kRedThreads / 32];
+  const int N = min(a.n_cap, a.dims.nodes(a.n_cap));
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if ((int)blockIdx.x < gridDim.x - 1) {
+    const int c = blockIdx.x * 32 + lane;
+    float s = 0.f;
+    if (c < a.Hh)
+      for (int i = w; i < N; i += kRedThreads / 32) s += fmaxf(a.zn[(size_t)i * a.Hh + c], 0.f) * a.dpred[i];
+    part[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && c < a.Hh) {
+      float t = part[0][lane];
+      for (int q = 1; q < kRedThreads / 32; ++q) t += part[q][lane];
+      grad[c] = t;
+    }
+    return;
+  }
+  double se = 0.0;
+  float db = 0.f;
+  for (int i = tid; i < N; i += kRedThreads) {
+    const float r = a.pred[i] - a.y[i];
+    se += (double)r * (double)r;
+    db += a.dpred[i];
+  }
+  const double sse = block_sum<kRedThreads>(se, redd);
+  const float sdb = block_sum<kRedThreads>(db, redf);
+  if (tid == 0) {
+    grad[a.Hh] = sdb;
+    if (accum) {
+      accum[3] += sse;
+      accum[4] += (double)N;
     }
   }
 }
@@ -585,6 +654,18 @@ int launch_head_grad(const HeadGradArgs &a, cudaStream_t s) {
   if (a.g_cap <= 0) return GCNN_OK;
   dim3 grid(ceil_div(a.Hh, kHT), ceil_div(a.H, kHT) + 1);
   GCNN_TRY(launch(head_grad_kernel, grid, kRedThreads, 0, s, a));
+  return GCNN_OK;
+}
+
+int launch_node_pred(const NodeHeadArgs &a, bool train, cudaStream_t s) {
+  if (a.n_cap <= 0) return GCNN_OK;
+  GCNN_TRY(launch(node_pred_kernel, ceil_div(a.n_cap, kNodeWarps), kNodeWarps * 32, 0, s, a, train));
+  return GCNN_OK;
+}
+
+int launch_node_grad(const NodeHeadArgs &a, float *grad_w2n, double *loss_accum, cudaStream_t s) {
+  if (a.n_cap <= 0) return GCNN_OK;
+  GCNN_TRY(launch(node_grad_kernel, ceil_div(a.Hh, 32) + 1, kRedThreads, 0, s, a, grad_w2n, loss_accum));
   return GCNN_OK;
 }
 

@@ -34,8 +34,9 @@ struct Header {
   uint32_t version, n_types;
   int64_t G, N, E, o_node_ptr, o_edge_ptr, o_types, o_edges, o_y, size;
   int64_t F, o_eattr;  // version 2: bond features per edge and their offset
+  int64_t o_ynode;     // version 2: node-level targets (0: none)
 };
-static_assert(sizeof(Header) == 104, "store header layout");
+static_assert(sizeof(Header) == 112, "store header layout");
 constexpr int kMaxEdgeFeatures = 16;
 
 bool range_ok(int64_t off, int64_t bytes, int64_t size) {
@@ -106,6 +107,7 @@ int store_open(const char *path, gcnn_store **out) {
   if (h.version == 1) {
     h.F = 0;
     h.o_eattr = 0;
+    h.o_ynode = 0;
   }
   fseek(f, 0, SEEK_END);
   const long long fsize = ftell(f);
@@ -114,7 +116,8 @@ int store_open(const char *path, gcnn_store **out) {
       !range_ok(h.o_types, h.N, h.size) || !range_ok(h.o_edges, 2 * h.E, h.size) ||
       !range_ok(h.o_y, 4 * h.G, h.size) || h.o_node_ptr % 8 || h.o_edge_ptr % 8 || h.o_y % 4 || h.F < 0 ||
       h.F > kMaxEdgeFeatures || (h.F > 0 && (h.E > INT64_MAX / (4 * h.F) || !range_ok(h.o_eattr, 4 * h.E * h.F, h.size) ||
-                                             h.o_eattr % 16))) {
+                                             h.o_eattr % 16)) ||
+      (h.o_ynode != 0 && (!range_ok(h.o_ynode, 4 * h.N, h.size) || h.o_ynode % 4))) {
     fclose(f);
     return set_error(GCNN_EFORMAT, "store_open: inconsistent header in %s", path);
   }
@@ -139,13 +142,14 @@ int store_open(const char *path, gcnn_store **out) {
   st->G = h.G; st->N = h.N; st->E = h.E; st->n_types = h.n_types;
   st->off_node_ptr = h.o_node_ptr; st->off_edge_ptr = h.o_edge_ptr; st->off_types = h.o_types;
   st->off_edges = h.o_edges; st->off_y = h.o_y;
-  st->F = (int32_t)h.F; st->off_eattr = h.o_eattr;
+  st->F = (int32_t)h.F; st->off_eattr = h.o_eattr; st->off_ynode = h.o_ynode;
   st->node_ptr = reinterpret_cast<const int64_t *>(b + h.o_node_ptr);
   st->edge_ptr = reinterpret_cast<const int64_t *>(b + h.o_edge_ptr);
   st->types = reinterpret_cast<const uint8_t *>(b + h.o_types);
   st->edges = reinterpret_cast<const uint8_t *>(b + h.o_edges);
   st->y = reinterpret_cast<float *>(b + h.o_y);
   st->eattr = h.F > 0 ? reinterpret_cast<const float *>(b + h.o_eattr) : nullptr;
+  st->ynode = h.o_ynode ? reinterpret_cast<float *>(b + h.o_ynode) : nullptr;
   int rc = got == st->bytes ? validate(st) : set_error(GCNN_EFORMAT, "store_open: short read");
   if (rc != GCNN_OK) {
     store_close(st);
@@ -188,7 +192,8 @@ StoreView store_device_view(const gcnn_store *st) {
                    reinterpret_cast<const uint8_t *>(b + st->off_types),
                    reinterpret_cast<const uint8_t *>(b + st->off_edges),
                    reinterpret_cast<const float *>(b + st->off_y),
-                   st->F > 0 ? reinterpret_cast<const float *>(b + st->off_eattr) : nullptr, st->F};
+                   st->F > 0 ? reinterpret_cast<const float *>(b + st->off_eattr) : nullptr, st->F,
+                   st->off_ynode ? reinterpret_cast<const float *>(b + st->off_ynode) : nullptr};
 }
 
 int store_batch_size(const gcnn_store *st, const int64_t *ids, int64_t n, int64_t *nn, int64_t *ne) {

@@ -13,12 +13,14 @@ struct gcnn_store {
   uint32_t n_types = 0;
   int32_t F = 0;  // bond features per edge (version 2)
   int64_t off_node_ptr = 0, off_edge_ptr = 0, off_types = 0, off_edges = 0, off_y = 0, off_eattr = 0;
+  int64_t off_ynode = 0;  // 0: no node-level targets
   const int64_t *node_ptr = nullptr;
   const int64_t *edge_ptr = nullptr;
   const uint8_t *types = nullptr;
   const uint8_t *edges = nullptr;
   float *y = nullptr;
   const float *eattr = nullptr;  // [E][F]
+  float *ynode = nullptr;        // [N] node-level targets or nullptr
   void *dev = nullptr;  // device mirror of the whole file, or nullptr
   int dev_id = -1;
 };

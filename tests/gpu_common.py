@@ -18,10 +18,11 @@ def write_both(gs: synth.GraphSet, tmpdir: str | None = None):
     return path, oracle.read_store(path)
 
 
-def context(H, L, G, N, E, delta, recompute=False, precision=0, Hh=None, F=0):
+def context(H, L, G, N, E, delta, recompute=False, precision=0, Hh=None, F=0, node_head=0, node_weight=1.0):
     import paper_2207_11333_gb300 as g
     cfg = g.make_config(H, L, G, N, E, delta=delta, recompute=int(recompute), precision=precision,
-                        head_hidden=H if Hh is None else Hh, edge_features=F)
+                        head_hidden=H if Hh is None else Hh, edge_features=F, node_head=node_head,
+                        node_loss_weight=node_weight)
     return g.Context(cfg)
 
 
