@@ -117,9 +117,11 @@ int gcnn_store_open(const char *path, gcnn_store **out);
 int gcnn_store_close(gcnn_store *st);
 /* Totals of the whole store. */
 int gcnn_store_info(const gcnn_store *st, int64_t *n_graphs, int64_t *n_nodes, int64_t *n_edges);
-/* Bond features per edge (0 for a version-1 store). */
+/* Bond features per edge, 0 for a version-1 store (Table 1's edge
+ * attributes).  Never fails on a valid store. */
 int gcnn_store_edge_features(const gcnn_store *st, int32_t *n_features);
-/* Whether the store carries node-level targets (1) or not (0). */
+/* Whether the store carries node-level targets, 1, or not, 0 (Table 1's
+ * node-level y).  Never fails on a valid store. */
 int gcnn_store_has_node_targets(const gcnn_store *st, int32_t *has);
 /* Node and edge totals of the batch graph_ids[0..n) (host ids). */
 int gcnn_store_batch_size(const gcnn_store *st, const int64_t *graph_ids, int64_t n,
@@ -270,8 +272,10 @@ int gcnn_step(gcnn_ctx *ctx, float lr);
 int gcnn_train_step(gcnn_ctx *ctx, const gcnn_batch *b, float lr, double *loss_accum);
 /* Copy x^l (l = 0..L, N x H floats) of the last forward to host.  Sync. */
 int gcnn_get_activation(gcnn_ctx *ctx, int32_t layer, float *dst, int64_t n);
-/* Copy the node-level predictions (N floats) of the last forward to host;
- * GCNN_ESTATE without the node head.  Synchronous. */
+/* Copy the node-level predictions (Sec. 3.1 atom-level properties; N floats,
+ * atom order of the batch) of the last forward to host memory dst (caller-
+ * owned); GCNN_ESTATE without the node head, GCNN_EINVAL unless n = N.
+ * Synchronous. */
 int gcnn_get_node_predictions(gcnn_ctx *ctx, float *dst, int64_t n);
 
 /* ------------------------------------------------------------------ timing

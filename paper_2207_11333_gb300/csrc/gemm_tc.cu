@@ -387,12 +387,16 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.a)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.b)) : "memory");
   }
-  pdl_entry(EPI == kEpiPartial ? GCNN_K_GEMM_TC_PARTIAL : (EPI == kEpiC ? GCNN_K_GEMM_TC_C : GCNN_K_GEMM_TC_D3));
+  // the batch sizes come from the collator, many launches before this one
   const Sizes sz = actual_sizes(d, dims);
   const int M = sz.M, K = sz.K, N = d.N;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int z = blockIdx.z;
-  if (m0 >= M) return;  // block-uniform, before any barrier wait or TMEM use
+  const int kid = EPI == kEpiPartial ? GCNN_K_GEMM_TC_PARTIAL : (EPI == kEpiC ? GCNN_K_GEMM_TC_C : GCNN_K_GEMM_TC_D3);
+  if (m0 >= M) {  // block-uniform, before any barrier wait or TMEM use
+    pdl_entry(kid);
+    return;
+  }
   const int kbeg = z * kps;
   const int kend = min(K, kbeg + kps);
   const int nk = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
@@ -400,6 +404,33 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
   const int b_atoms = (BN + 63) / 64;
   const uint32_t a_bytes = kATileBytes;
   const uint32_t b_bytes = d.B.mn_major ? (uint32_t)b_atoms * kMnAtomBytes : (uint32_t)BN * BK * 2;
+  auto load_a = [&](int s, int k0) {
+    uint8_t *a_tile = smem + s * kStageBytes;
+    if (!d.A.mn_major) {
+      tma_load_2d(smem_u32(a_tile), &maps.a, k0, m0, &full[s]);
+    } else {
+      tma_load_2d(smem_u32(a_tile), &maps.a, m0, k0, &full[s]);
+      tma_load_2d(smem_u32(a_tile + kMnAtomBytes), &maps.a, m0 + 64, k0, &full[s]);
+    }
+  };
+  auto load_b = [&](int s, int k0) {
+    uint8_t *b_tile = smem + s * kStageBytes + kATileBytes;
+    if (!d.B.mn_major) {
+      tma_load_2d(smem_u32(b_tile), &maps.b, k0, n0, &full[s]);
+    } else {
+      for (int j = 0; j < b_atoms; ++j)
+        tma_load_2d(smem_u32(b_tile + j * kMnAtomBytes), &maps.b, n0 + 64 * j, k0, &full[s]);
+    }
+  };
+  // the stable operand's first stages go out before the dependency wait
+  const int pre = d.stable != kStableNone ? min(nk, STAGES) : 0;
+  if (tid == 0)
+    for (int kt = 0; kt < pre; ++kt) {
+      mbar_expect_tx(&full[kt], a_bytes + b_bytes);
+      if (d.stable == kStableA) load_a(kt, kbeg + kt * BK);
+      else load_b(kt, kbeg + kt * BK);
+    }
+  pdl_entry(kid);
 
   if (warp == 0) tmem_alloc(tmem_slot, ncols);
   fence_before_sync();
@@ -416,22 +447,15 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
           atomicOr(flag, 1u);
           break;
         }
-        uint8_t *a_tile = smem + s * kStageBytes;
-        uint8_t *b_tile = a_tile + kATileBytes;
         const int k0 = kbeg + kt * BK;
+        if (kt < pre) {  // the other operand of a stage started before the wait
+          if (d.stable == kStableA) load_b(s, k0);
+          else load_a(s, k0);
+          continue;
+        }
         mbar_expect_tx(&full[s], a_bytes + b_bytes);
-        if (!d.A.mn_major) {
-          tma_load_2d(smem_u32(a_tile), &maps.a, k0, m0, &full[s]);
-        } else {
-          tma_load_2d(smem_u32(a_tile), &maps.a, m0, k0, &full[s]);
-          tma_load_2d(smem_u32(a_tile + kMnAtomBytes), &maps.a, m0 + 64, k0, &full[s]);
-        }
-        if (!d.B.mn_major) {
-          tma_load_2d(smem_u32(b_tile), &maps.b, k0, n0, &full[s]);
-        } else {
-          for (int j = 0; j < b_atoms; ++j)
-            tma_load_2d(smem_u32(b_tile + j * kMnAtomBytes), &maps.b, n0 + 64 * j, k0, &full[s]);
-        }
+        load_a(s, k0);
+        load_b(s, k0);
       }
     }
   } else if (warp == 1) {

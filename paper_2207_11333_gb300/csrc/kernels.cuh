@@ -231,11 +231,20 @@ struct TcEpilogue {
   const float *amp, *att;
 };
 
+// Operand not written by the kernel launched just before on the same stream:
+// its first pipeline stages are loaded before the dependency wait of
+// programmatic dependent launch, overlapping the previous kernel's tail.  A
+// kernel starts only once its predecessor has passed its own wait, so every
+// earlier kernel is complete by then; only the immediate predecessor's
+// outputs must wait.
+enum TcStable { kStableNone = 0, kStableA = 1, kStableB = 2 };
+
 struct TcDesc {
   int M, N, K;         // K: multiple of 64 (padded) or, with node_dim == kNodeK, the node capacity
   NodeDim node_dim;
   TcMat A, B;
   TcEpilogue ep;
+  TcStable stable;
 };
 
 int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned *err, cudaStream_t s);

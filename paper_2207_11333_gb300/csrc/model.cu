@@ -261,6 +261,7 @@ int tc_message(gcnn_ctx *c, int Ngrid, int l) {
   d.M = Ngrid; d.N = 2 * H; d.K = pad64(H); d.node_dim = kNodeM;
   d.A = mat(X_at(c, l), X_ld(c), Ngrid, H, false);
   d.B = mat(wb_of(c, w.msg_w), 2 * H, H, 2 * H, true);
+  d.stable = kStableB;  // the weights; x_l comes from the kernel just before
   d.ep.C = pq_at(c, l); d.ep.ldc = 2 * H; d.ep.bias = w.msg_b; d.ep.bias_n = H;
   return tc(c, d);
 }
@@ -275,6 +276,7 @@ int tc_update(gcnn_ctx *c, int Ngrid, int l) {
   d.M = Ngrid; d.N = H; d.K = pad64(16 * H); d.node_dim = kNodeM;
   d.A = mat(U_at(c, l), 16 * H, Ngrid, 16 * H, false);
   d.B = mat(wb_of(c, w.upd_w), H, 16 * H, H, true);
+  d.stable = kStableB;  // the weights; the aggregates come from the kernel just before
   d.ep.C = xs_at(c, l + 1); d.ep.ldc = H; d.ep.bias = w.upd_b; d.ep.bias_n = H; d.ep.relu = true;
   if (l + 1 < c->L) { d.ep.C16 = X_at(c, l + 1); d.ep.ld16 = X_ld(c); }
   return tc(c, d);
@@ -318,6 +320,8 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
     d.M = 16 * H; d.N = H; d.K = Ngrid; d.node_dim = kNodeK;
     d.A = mat(U_at(c, l), 16 * H, Ngrid, 16 * H, true);
     d.B = mat(G + 2 * H, 5 * H, Ngrid, H, true);
+    // the forward's operand, unless recomputed just before
+    d.stable = c->cfg.recompute ? kStableNone : kStableA;
     d.ep.C = gw.upd_w; d.ep.ldc = H;
     GCNN_TRY(tc_on(c, d, lane));
   }
@@ -326,6 +330,7 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
     d.M = Ngrid; d.N = kAgg * H; d.K = pad64(3 * H); d.node_dim = kNodeM;
     d.A = mat(G, 5 * H, Ngrid, 3 * H, false);
     d.B = mat(Wd_at(c, l), 3 * H, kAgg * H, 3 * H, false);
+    d.stable = kStableB;
     d.ep.C = c->dagg; d.ep.ldc = kAgg * H;
     GCNN_TRY(tc(c, d));
   }
@@ -347,6 +352,7 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
     d.M = H; d.N = 2 * H; d.K = Ngrid; d.node_dim = kNodeK;
     d.A = mat(X_at(c, l), X_ld(c), Ngrid, H, true);
     d.B = mat(G + 3 * H, 5 * H, Ngrid, 2 * H, true);
+    d.stable = kStableA;  // x_l from the forward; [dP | dQ] from the aggregation backward
     d.ep.C = gw.msg_w; d.ep.ldc = 2 * H;
     GCNN_TRY(tc_on(c, d, lane));
     // bias gradients: db_U = sum of dpre, db_M = sum of dP (FP32, fixed order)
@@ -362,6 +368,7 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
     d.M = Ngrid; d.N = H; d.K = pad64(3 * H); d.node_dim = kNodeM;
     d.A = mat(G + 2 * H, 5 * H, Ngrid, 3 * H, false);
     d.B = mat(Wx_at(c, l), 3 * H, H, 3 * H, false);
+    d.stable = kStableB;
     d.ep.C = c->dX; d.ep.ldc = H;
     if (l > 0) {
       d.ep.D3 = c->G5[cur ^ 1]; d.ep.ld3 = 5 * H;

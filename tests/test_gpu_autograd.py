@@ -177,3 +177,19 @@ def test_composed_layer_against_oracle():
     assert abs(loss.item() - oloss) < 1e-5 * oloss
     for name, t in (("msg_w0", msg_w), ("msg_b0", msg_b), ("upd_w0", upd_w), ("upd_b0", upd_b)):
         assert rel_norm(t.grad.cpu().numpy(), og[name]) < 1e-4, name
+
+
+def test_aggregate_function_with_graph_offsets():
+    """The Function's backward over whole graphs (fused on a batch of 900 molecules)
+    equals the pair's."""
+    from paper_2207_11333_gb300.autograd import aggregate
+    b, delta, rp, col, rev, node_off, _ = _graph(seed=18, G=900, lo=3, hi=60)
+    H = 8
+    gen = torch.Generator(device="cuda").manual_seed(6)
+    PQ = torch.randn(b.N, 2 * H, device="cuda", generator=gen)
+    W = torch.randn(b.N, 5 * H, device="cuda", generator=gen)
+    x1 = PQ.clone().requires_grad_(True)
+    x2 = PQ.clone().requires_grad_(True)
+    (aggregate(x1, rp, col, rev) * W).sum().backward()
+    (aggregate(x2, rp, col, rev, 1e-5, node_off) * W).sum().backward()
+    assert torch.equal(x1.grad, x2.grad)
