@@ -562,6 +562,42 @@ def loading_study(g, n_graphs: int = 20_000, batches: int = 60):
     return out
 
 
+def variants_study(g, wl: Workload, flush, precision: str, steps: int = 200, warmup: int = 10):
+    """The next rows of the path on the same workload and step: bond features (F = 4 per
+    edge in the message, Sec. 3.1 / Table 1 edge attributes) and the node-level head
+    (Sec. 3.1 node-level properties), alone and together; train graphs/s from the same
+    per-step CUDA events as the headline value."""
+    import torch
+    from types import SimpleNamespace
+    gs = dataset()
+    gs.y = wl.y
+    gs.eattr = synth.bond_features(SEED_DATA + 400, gs, 4, -1.0, 1.0)
+    gs.ynode = synth.uniform(SEED_DATA + 401, 0, gs.n_nodes, -1.0, 1.0).astype(np.float32)
+    path = os.path.join(wl.tmp, "variants.gcnn")
+    synth.write_store(path, gs)
+    st = g.Store(path)
+    st.to_device()
+    vw = SimpleNamespace(st=st, nb=wl.nb, n_train=wl.n_train)
+    prec = g.PREC_BF16 if precision == "bf16" else g.PREC_FP32
+    out = {"precision": precision, "steps": steps}
+    for name, F, nh in (("bond_features_4", 4, 0), ("node_head", 0, 1), ("both", 4, 1)):
+        ctx = g.Context(g.make_config(H, L, BATCH, wl.Nc, wl.Ec, delta=wl.delta, precision=prec, edge_features=F,
+                                      node_head=nh))
+        p = synth.init_params(SEED_STUDENT, H, L, F=F)
+        if nh:  # node head block: from a multiple of 4 floats, drawn like a graph head
+            p = np.concatenate([p, np.zeros((p.size + 3) // 4 * 4 - p.size, np.float32),
+                                synth.init_params(SEED_STUDENT + 1, H, 1)[-(H * H + 2 * H + 1):]])
+        ctx.set_params(p)
+        ctx.set_order(st, wl.order)
+        acc = torch.zeros(5, dtype=torch.float64, device="cuda")
+        r = timed_steps(ctx, vw, steps, warmup, flush, acc)
+        ctx.check()
+        ctx.close()
+        out[name] = {"graphs_per_s": r["value"], "ms_per_step": 1e3 * r["dev_s"] / steps}
+    st.close()
+    return out
+
+
 def recompute_study(g, precision: str, steps: int = 20):
     """Per-layer recompute at H = 256, L = 6, 1024 graphs of 3-51 atoms per batch:
     step time and device memory with and without it."""
@@ -816,7 +852,8 @@ def run_ours(args):
     if args.studies and world == 1:
         for key, fn in (("aggregate_large_batch", lambda: aggregate_large(g)),
                         ("recompute", lambda: recompute_study(g, args.precision)),
-                        ("data_loading", lambda: loading_study(g))):
+                        ("data_loading", lambda: loading_study(g)),
+                        ("next_rows", lambda: variants_study(g, wl, flush, args.precision))):
             try:
                 line[key] = fn()
             except Exception as e:  # noqa: BLE001
