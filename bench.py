@@ -571,16 +571,19 @@ def variants_study(g, wl: Workload, flush, precision: str, steps: int = 200, war
     from types import SimpleNamespace
     gs = dataset()
     gs.y = wl.y
-    gs.eattr = synth.bond_features(SEED_DATA + 400, gs, 4, -1.0, 1.0)
     gs.ynode = synth.uniform(SEED_DATA + 401, 0, gs.n_nodes, -1.0, 1.0).astype(np.float32)
-    path = os.path.join(wl.tmp, "variants.gcnn")
-    synth.write_store(path, gs)
-    st = g.Store(path)
-    st.to_device()
-    vw = SimpleNamespace(st=st, nb=wl.nb, n_train=wl.n_train)
+    stores = {}
+    for F in (0, 4):  # node targets, without and with bond features
+        gs.eattr = synth.bond_features(SEED_DATA + 400, gs, 4, -1.0, 1.0) if F else None
+        path = os.path.join(wl.tmp, f"variants_{F}.gcnn")
+        synth.write_store(path, gs)
+        stores[F] = g.Store(path)
+        stores[F].to_device()
     prec = g.PREC_BF16 if precision == "bf16" else g.PREC_FP32
     out = {"precision": precision, "steps": steps}
     for name, F, nh in (("bond_features_4", 4, 0), ("node_head", 0, 1), ("both", 4, 1)):
+        st = stores[F]
+        vw = SimpleNamespace(st=st, nb=wl.nb, n_train=wl.n_train)
         ctx = g.Context(g.make_config(H, L, BATCH, wl.Nc, wl.Ec, delta=wl.delta, precision=prec, edge_features=F,
                                       node_head=nh))
         p = synth.init_params(SEED_STUDENT, H, L, F=F)
@@ -594,7 +597,8 @@ def variants_study(g, wl: Workload, flush, precision: str, steps: int = 200, war
         ctx.check()
         ctx.close()
         out[name] = {"graphs_per_s": r["value"], "ms_per_step": 1e3 * r["dev_s"] / steps}
-    st.close()
+    for st in stores.values():
+        st.close()
     return out
 
 
