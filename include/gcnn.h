@@ -353,7 +353,8 @@ enum {
   GCNN_K_AGG_BWD_CHUNKS = 24,   /* its partition of the batch into chunks      */
   GCNN_K_NODE_PRED = 25,        /* node-level head: outputs and loss gradient  */
   GCNN_K_NODE_GRAD = 26,        /* node-level head: w2n, b2n and loss sums     */
-  GCNN_NKERNEL = 27
+  GCNN_K_BOND_GRAD = 27,        /* gradient of the bond rows of W_M            */
+  GCNN_NKERNEL = 28
 };
 int gcnn_timeline_enable(gcnn_ctx *ctx, int32_t capacity);
 int gcnn_timeline_read(gcnn_ctx *ctx, int32_t *ids, int64_t *t_ns, int32_t max, int32_t *n);

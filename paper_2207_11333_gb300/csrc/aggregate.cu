@@ -97,9 +97,22 @@ __device__ __forceinline__ bool gather_first(const float *__restrict__ PQ, const
     const float4 q = ld4(PQ + (size_t)(ok ? j[k] : i) * 2 * H + H + c);
     mc[k] = ok ? add4(P, q) : P;
   }
-  if (EDGE) {
+  if (EDGE) {  // bond_term for the kCache edges, each W_E row loaded once
+    const int ld = (b.F + 3) & ~3;
+    float4 r[kCache];
 #pragma unroll
-    for (int k = 0; k < kCache; ++k) mc[k] = add4(mc[k], bond_term(b, H, min(r0 + k, r1 - 1), c));
+    for (int k = 0; k < kCache; ++k) r[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int f = 0; f < b.F; ++f) {
+      const float4 w = ld4(b.w + (size_t)f * H + c);
+#pragma unroll
+      for (int k = 0; k < kCache; ++k) {
+        const float a = b.attr[(size_t)min(r0 + k, r1 - 1) * ld + f];
+        r[k].x = fmaf(a, w.x, r[k].x); r[k].y = fmaf(a, w.y, r[k].y);
+        r[k].z = fmaf(a, w.z, r[k].z); r[k].w = fmaf(a, w.w, r[k].w);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kCache; ++k) mc[k] = add4(mc[k], r[k]);
   }
   return bad;
 }
@@ -444,7 +457,62 @@ aggregate_bwd_gather_kernel(int n_cap, int e_cap, int H, DevDims dims,
   if (dPQ16) st_bf16x4(dPQ16 + (size_t)j * ld16 + H + c, q.x, q.y, q.z, q.w);
 }
 
+// Bond rows' gradient dW_E[f][c] = sum over the batch's edge slots r of
+// eattr[r][f] dm[r][c] (dm at reverse slots; both directions of a bond carry
+// the same features, so slot r pairs with its own features).  Block x sums
+// the float4 column 4x over all slots (threads strided over slots, then the
+// warps' partials in order): a fixed order, deterministic.
+constexpr int kBondThreads = 256, kMaxBondF = 16;
+
+__global__ void __launch_bounds__(kBondThreads)
+bond_grad_kernel(int e_cap, int H, int F, int ld, DevDims dims, const float *__restrict__ eattr,
+                 const float *__restrict__ dm, float *__restrict__ out) {
+  pdl_entry(GCNN_K_BOND_GRAD);
+  __shared__ float4 part[kBondThreads / 32][kMaxBondF];
+  const int E = min(e_cap, dims.edges(e_cap));
+  const int c = blockIdx.x * 4, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float4 acc[kMaxBondF];
+#pragma unroll
+  for (int f = 0; f < kMaxBondF; ++f) acc[f] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int r = threadIdx.x; r < E; r += kBondThreads) {
+    const float4 g = ld4(dm + (size_t)r * H + c);
+#pragma unroll
+    for (int f = 0; f < kMaxBondF; ++f)
+      if (f < F) {
+        const float a = eattr[(size_t)r * ld + f];
+        acc[f].x = fmaf(a, g.x, acc[f].x); acc[f].y = fmaf(a, g.y, acc[f].y);
+        acc[f].z = fmaf(a, g.z, acc[f].z); acc[f].w = fmaf(a, g.w, acc[f].w);
+      }
+  }
+#pragma unroll
+  for (int f = 0; f < kMaxBondF; ++f) {
+    if (f < F) {
+      float4 v = acc[f];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o); v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+        v.z += __shfl_xor_sync(0xffffffffu, v.z, o); v.w += __shfl_xor_sync(0xffffffffu, v.w, o);
+      }
+      if (lane == 0) part[w][f] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < F) {
+    float4 t = part[0][threadIdx.x];
+    for (int q = 1; q < kBondThreads / 32; ++q) t = add4(t, part[q][threadIdx.x]);
+    st4(out + (size_t)threadIdx.x * H + c, t);
+  }
+}
+
 }  // namespace
+
+int launch_bond_grad(int n_edges, int H, int F, int ld, DevDims dims, const float *eattr, const float *dm, float *out,
+                     cudaStream_t s) {
+  if (F <= 0) return GCNN_OK;
+  if (F > kMaxBondF || H % 4 || ld % 4 || ld < F) return set_error(GCNN_EINVAL, "bond_grad: bad sizes");
+  GCNN_TRY(launch(bond_grad_kernel, H / 4, kBondThreads, 0, s, std::max(n_edges, 0), H, F, ld, dims, eattr, dm, out));
+  return GCNN_OK;
+}
 
 int launch_aggregate_fwd(int n_nodes, int H, DevDims dims, const int *row_ptr, const int *col,
                          const float *PQ, float *agg, float eps, unsigned *err, cudaStream_t s,

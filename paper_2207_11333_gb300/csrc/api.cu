@@ -252,8 +252,6 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
     wsf = std::max(wsf, gemm_simt_workspace_floats(n, kAgg * h, 3 * h));
     wsf = std::max(wsf, gemm_simt_workspace_floats(h + 1, 2 * h, n));
     wsf = std::max(wsf, gemm_simt_workspace_floats(n, h, 3 * h));
-    if (cfg->edge_features > 0)  // bond rows of W_M: e^T dm over the edges
-      wsf = std::max(wsf, gemm_simt_workspace_floats(cfg->edge_features, h, (int)Ec));
     if (cfg->node_head) {  // node head: x W1n, dz W1n^T, [x ; 1]^T dz
       wsf = std::max(wsf, gemm_simt_workspace_floats(n, (int)Hh, h));
       wsf = std::max(wsf, gemm_simt_workspace_floats(n, h, (int)Hh));

@@ -69,6 +69,11 @@ int launch_aggregate_bwd_graphs(int n_graphs, int n_nodes, int n_edges, int H, D
                                 float eps, unsigned *err, cudaStream_t s, uint16_t *dPQ16 = nullptr, int ld16 = 0,
                                 const float *eattr = nullptr, const float *wE = nullptr, int F = 0);
 int aggregate_chunk_capacity(int n_edges);
+// Bond rows' gradient out[f][c] (F x H) = sum over edge slots of eattr[r][f]
+// (row stride ld) times dm[r][c] (E x H, the per-edge message gradients at
+// reverse slots); fixed-order sums.
+int launch_bond_grad(int n_edges, int H, int F, int ld, DevDims dims, const float *eattr, const float *dm, float *out,
+                     cudaStream_t s);
 bool aggregate_bwd_uses_fused(int n_edges);
 
 // ---------------------------------------------------------------- small.cu

@@ -102,13 +102,9 @@ int gemm(gcnn_ctx *c, const GemmDesc &d) {
 // bond carry the same features (checked when the store is opened), so slot r
 // pairs dm[r] with eattr[r].
 int gemm_bond_rows(gcnn_ctx *c, int Egrid, float *g_edge_w) {
-  GemmDesc d = blank();
-  d.M = c->cfg.edge_features; d.N = c->H; d.K = Egrid; d.node_dim = kEdgeK;
-  d.a_kcontig = false; d.b_ncontig = true;
-  d.A.nseg = 1; d.A.seg[0] = seg(0, c->bb.eattr, c->bb.eattr_ld);
-  d.B.nseg = 1; d.B.seg[0] = seg(0, c->dm, c->H);
-  d.C = g_edge_w; d.ldc = c->H;
-  return gemm(c, d);
+  PhaseScope ps(c, GCNN_PHASE_AGG_BWD);
+  return launch_bond_grad(Egrid, c->H, c->cfg.edge_features, c->bb.eattr_ld, DevDims{c->bb.dims}, c->bb.eattr, c->dm,
+                          g_edge_w, c->stream);
 }
 
 // Node-level head forward on the last layer (zn = x W1n + b1n, then the
@@ -301,7 +297,12 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
   const float *pq = pq_at(c, l), *h = xs_at(c, l + 1);
   float *agg = agg_at(c, l);
   uint16_t *G = c->G5[cur];
-  const Lane lane = ov ? Lane{c->side, &c->ws_side} : Lane{c->stream, &c->ws};
+  // the weight-gradient GEMMs plan with the side lane's half-SM cap in both
+  // modes, so the overlapped and the serial backward pick the same split-K
+  // plans and give the same results bit for bit
+  GemmWorkspace capped = c->ws;
+  capped.max_ctas = std::max(1, num_sms() / 2);
+  const Lane lane = ov ? Lane{c->side, &c->ws_side} : Lane{c->stream, &capped};
   cudaEvent_t fork = ov ? c->side_ev[3 * l] : nullptr, mid = ov ? c->side_ev[3 * l + 1] : nullptr;
   cudaEvent_t done = ov ? c->side_ev[3 * l + 2] : nullptr;
   if (c->cfg.recompute) {

@@ -164,6 +164,15 @@ constexpr int kHeadThreads = 512;
 // optionally also as the BF16 blocks [amp g | att g | g], g = dx [h > 0].
 // W1 is staged in shared memory, rk rows at a time.
 
+__device__ __forceinline__ void cp_async16(float *dst_smem, const float *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+               "l"(src)
+               : "memory");
+}
+
+// partials of the one-chunk path: at most kHeadThreads float4
+constexpr int kHeadRed = kHeadThreads;
+
 template <bool kFwd, bool kBwd>
 __global__ void __launch_bounds__(kHeadThreads) head_graph_kernel(HeadArgs a) {
   pdl_entry(GCNN_K_HEAD_GRAPH);
@@ -193,7 +202,66 @@ __global__ void __launch_bounds__(kHeadThreads) head_graph_kernel(HeadArgs a) {
     __syncthreads();
     staged = ch;
   };
-  if (kFwd) {
+  // one chunk of W1 and whole float4 columns: W1 arrives by asynchronous copies
+  // while the graph is pooled, and pooling and z1 use every thread (float4
+  // column x row segment, partials summed in segment order)
+  const bool one = nchunks == 1 && (Hh & 3) == 0;
+  if (kFwd && one) {
+    float4 *part4 = reinterpret_cast<float4 *>(sd + Hh);  // kHeadRed float4
+    const int H4 = H >> 2, Hh4 = Hh >> 2;
+    for (int q = tid; q < H * Hh4; q += kHeadThreads) cp_async16(Ws + 4 * q, a.w1 + 4 * (size_t)q);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    staged = 0;
+    const int R = max(1, kHeadThreads / H4);
+    if (tid < R * H4) {
+      const int c4 = tid % H4;
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int i = n0 + tid / H4; i < n1; i += R) acc = add4(acc, ld4(a.x + (size_t)i * H + 4 * c4));
+      part4[tid] = acc;
+    }
+    __syncthreads();
+    for (int c4 = tid; c4 < H4; c4 += kHeadThreads) {
+      float4 v = part4[c4];
+      for (int r = 1; r < R; ++r) v = add4(v, part4[r * H4 + c4]);
+      if (nn > 0) {
+        const float inv = (float)nn;
+        v = make_float4(v.x / inv, v.y / inv, v.z / inv, v.w / inv);
+      }
+      st4(sv + 4 * c4, v);
+      st4(a.pooled + (size_t)gr * H + 4 * c4, v);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    const int S = max(1, kHeadThreads / Hh4), kper = (H + S - 1) / S;
+    if (tid < S * Hh4) {
+      const int c4 = tid % Hh4, seg = tid / Hh4, k1 = min(H, (seg + 1) * kper);
+      float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k = seg * kper; k < k1; ++k) {
+        const float gk = sv[k];
+        const float4 w = ld4(Ws + (size_t)k * Hh + 4 * c4);
+        acc.x = fmaf(gk, w.x, acc.x); acc.y = fmaf(gk, w.y, acc.y);
+        acc.z = fmaf(gk, w.z, acc.z); acc.w = fmaf(gk, w.w, acc.w);
+      }
+      part4[tid] = acc;
+    }
+    __syncthreads();
+    for (int c4 = tid; c4 < Hh4; c4 += kHeadThreads) {
+      float4 v = make_float4(a.b1[4 * c4], a.b1[4 * c4 + 1], a.b1[4 * c4 + 2], a.b1[4 * c4 + 3]);
+      for (int sg = 0; sg < S; ++sg) v = add4(v, part4[sg * Hh4 + c4]);
+      st4(sz + 4 * c4, v);
+    }
+    __syncthreads();
+    float part = 0.f;
+    for (int c = tid; c < Hh; c += kHeadThreads) {
+      a.z1[(size_t)gr * Hh + c] = sz[c];
+      part += fmaxf(sz[c], 0.f) * a.w2[c];
+    }
+    const float s = block_sum<kHeadThreads>(part, red);
+    if (tid == 0) {
+      s_pred = s + a.b2[0];
+      a.pred[gr] = s_pred;
+    }
+  } else if (kFwd) {
     for (int k = tid; k < H; k += kHeadThreads) {
       float s4[4] = {0.f, 0.f, 0.f, 0.f};
       int i = n0;
@@ -627,10 +695,13 @@ constexpr int kHeadSmemFloats = 40 * 1024;  // 160 KB: W1 rows plus pooled / z1 
 template <bool F, bool B>
 int head_graph(HeadArgs a, cudaStream_t s) {
   static bool configured = false;
-  const size_t bytes = sizeof(float) * ((size_t)a.rk * a.Hh + a.H + 2 * (size_t)a.Hh);
+  // the one-chunk forward also keeps kHeadRed float4 partials
+  const bool one = a.rk >= a.H && a.Hh % 4 == 0;
+  const size_t bytes =
+      sizeof(float) * ((size_t)a.rk * a.Hh + a.H + 2 * (size_t)a.Hh) + (one ? sizeof(float4) * kHeadRed : 0);
   if (!configured) {
     GCNN_CUDA_TRY(cudaFuncSetAttribute(head_graph_kernel<F, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(float) * kHeadSmemFloats)));
+                                       (int)(sizeof(float) * kHeadSmemFloats + sizeof(float4) * kHeadRed)));
     configured = true;
   }
   GCNN_TRY(launch(head_graph_kernel<F, B>, a.g_cap, kHeadThreads, bytes, s, a));

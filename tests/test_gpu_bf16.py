@@ -7,7 +7,7 @@ import torch
 
 import oracle
 import workloads
-from gpu_common import context, oracle_step, write_both
+from gpu_common import oracle_step, write_both
 from helpers import rel_norm
 
 pytestmark = pytest.mark.gpu
@@ -15,12 +15,13 @@ pytestmark = pytest.mark.gpu
 BF16_FWD_TOL = 2e-2
 
 
-def _run(tmp_path, precision, G=64, lo=5, hi=30, H=32, L=2, recompute=False):
+def _run(tmp_path, precision, G=64, lo=5, hi=30, H=32, L=2, recompute=False, serial=False):
     import paper_2207_11333_gb300 as g
     d, gs, delta, student = workloads.small_parity(G=G, lo=lo, hi=hi, H=H, L=L)
     path, ost = write_both(gs, str(tmp_path))
     st = g.Store(path)
-    ctx = context(H, L, G, int(gs.n_nodes), int(gs.n_edges), delta, precision=precision, recompute=recompute)
+    ctx = g.Context(g.make_config(H, L, G, int(gs.n_nodes), int(gs.n_edges), delta=delta, precision=precision,
+                                  recompute=int(recompute), head_hidden=H, flags=g.FLAG_SERIAL if serial else 0))
     ctx.set_params(student)
     b = ctx.collate(st, np.arange(G))
     pred = torch.empty(G, device="cuda")
@@ -61,16 +62,21 @@ def test_bf16_matches_fp32_path(tmp_path):
 
 @pytest.mark.parametrize("G,hi", [(64, 30), (900, 60)])
 def test_bf16_recompute_identical(tmp_path, G, hi):
+    """Recompute (a one-stream backward) against the stored path, both with its
+    default overlapped backward and on one stream: identical bit for bit."""
     import paper_2207_11333_gb300 as g
     _, _, _, p1, _, g1 = _run(tmp_path, g.PREC_BF16, G=G, lo=3, hi=hi, recompute=False)
     _, _, _, p2, _, g2 = _run(tmp_path, g.PREC_BF16, G=G, lo=3, hi=hi, recompute=True)
+    _, _, _, p3, _, g3 = _run(tmp_path, g.PREC_BF16, G=G, lo=3, hi=hi, recompute=False, serial=True)
     assert np.array_equal(p1, p2) and np.array_equal(g1, g2)
+    assert np.array_equal(p1, p3) and np.array_equal(g1, g3)
 
 
 def test_overlapped_backward_matches_serial(tmp_path):
     """The BF16 backward's weight-gradient work on a second stream (default)
     gives the same gradients and parameters, bit for bit, as the serial step
-    (GCNN_FLAG_SERIAL), over captured train steps and an eager backward."""
+    (GCNN_FLAG_SERIAL), over captured train steps and an eager backward: the
+    weight-gradient GEMMs plan with the same half-SM cap in both modes."""
     import paper_2207_11333_gb300 as g
     G, H, L = 96, 64, 3
     d, gs, delta, student = workloads.small_parity(G=G, lo=3, hi=51, H=H, L=L)
