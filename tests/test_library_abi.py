@@ -131,3 +131,19 @@ def test_pack_per_graph_files_matches_store_writer(tmp_path, F):
     open(paths[7], "wb").write(bad[:-1])
     with pytest.raises(g.GcnnError, match="g0000007"):
         g.store_pack(paths, str(tmp_path / "x.gcnn"), 4)
+
+
+def test_store_with_node_targets(tmp_path):
+    """Version-2 stores may carry node-level targets (with or without bond features);
+    the library reports them and the oracle reads them back."""
+    import paper_2207_11333_gb300 as g
+    gs = synth.molecules_uniform(12, 9, 3, 20)
+    gs.ynode = synth.uniform(13, 0, gs.n_nodes, -1.0, 1.0).astype(np.float32)
+    for F in (0, 2):
+        gs.eattr = synth.bond_features(14, gs, F) if F else None
+        path = _bad_store(tmp_path, gs, f"ynode{F}")
+        st = g.Store(path)
+        assert st.has_node_targets and st.edge_features == F
+        ost = oracle.read_store(path)
+        assert np.array_equal(ost.ynode, gs.ynode)
+    assert not g.Store(_bad_store(tmp_path, synth.molecules_uniform(12, 3, 3, 9), "plain2")).has_node_targets
