@@ -560,7 +560,7 @@ int launch_aggregate_bwd_graphs(int n_graphs, int n_nodes, int n_edges, int H, D
                                 const int *row_ptr, const int *col, const int *rev, const float *PQ,
                                 const float *agg, const float *dagg, float *dPQ, float *scratch, int *chunks,
                                 float eps, unsigned *err, cudaStream_t s, uint16_t *dPQ16, int ld16,
-                                const float *eattr, const float *wE, int F) {
+                                const float *eattr, const float *wE, int F, bool make_chunks) {
   if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
   if (n_nodes <= 0 || n_graphs <= 0) return GCNN_OK;
   // with bond features the per-edge gradients are kept: their weight gradient reads them
@@ -582,8 +582,9 @@ int launch_aggregate_bwd_graphs(int n_graphs, int n_nodes, int n_edges, int H, D
   const int H4 = H / 4;
   const int slices = ceil_div(kChunkSlots * H4 * 16, kFusedSmem);
   const int cs4 = ceil_div(H4, slices);
-  GCNN_TRY(launch(aggregate_chunk_kernel, ceil_div(n_graphs + 1, kThreads), kThreads, 0, s, n_graphs, n_nodes,
-                  n_chunks, kChunkEdges, dims, node_off, row_ptr, chunks, err));
+  if (make_chunks)
+    GCNN_TRY(launch(aggregate_chunk_kernel, ceil_div(n_graphs + 1, kThreads), kThreads, 0, s, n_graphs, n_nodes,
+                    n_chunks, kChunkEdges, dims, node_off, row_ptr, chunks, err));
   GCNN_TRY(launch(agg ? aggregate_bwd_fused_kernel<true> : aggregate_bwd_fused_kernel<false>,
                   dim3(n_chunks, ceil_div(H4, cs4)), kFusedThreads,
                   (size_t)kChunkSlots * cs4 * 16, s, n_graphs, n_nodes, n_edges, (const int *)chunks, cs4,

@@ -116,6 +116,8 @@ void destroy_ctx(gcnn_ctx *c) {
   if (c->lr_pinned) cudaFreeHost(c->lr_pinned);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->opt) cudaStreamDestroy(c->opt);
+  if (c->opt_ev) cudaEventDestroy(c->opt_ev);
   for (cudaEvent_t e : c->side_ev) cudaEventDestroy(e);
   if (c->order_dev) cudaFree(c->order_dev);
   if (c->dmem) cudaFree(c->dmem);
@@ -362,8 +364,10 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   if (rc == GCNN_OK && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     rc = set_error(GCNN_ECUDA, "cannot create the capture stream");
   if (rc == GCNN_OK && side) {
-    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess)
-      rc = set_error(GCNN_ECUDA, "cannot create the side stream");
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->opt, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->opt_ev, cudaEventDisableTiming) != cudaSuccess)
+      rc = set_error(GCNN_ECUDA, "cannot create the side streams");
     for (int q = 0; q < 3 * c->L + 1 && rc == GCNN_OK; ++q) {
       cudaEvent_t ev = nullptr;
       if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
@@ -598,10 +602,12 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
       return set_error(GCNN_ECUDA, "begin capture: %s", cudaGetErrorString(e));
     }
     c->fuse_head = true;
+    c->fuse_step = true;
     int rc = ctx_forward(c, G, Ng, Eg, true);
     if (rc == GCNN_OK) rc = ctx_backward(c, G, Ng, Eg, nullptr, loss_accum);
     c->fuse_head = false;
     if (rc == GCNN_OK) rc = ctx_step(c);
+    c->fuse_step = false;
     e = cudaStreamEndCapture(c->stream, &graph);
     c->stream = user;
     c->capturing = false;

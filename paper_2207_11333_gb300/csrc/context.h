@@ -14,6 +14,8 @@ struct gcnn_ctx {
   cudaStream_t side = nullptr;        // BF16 backward: weight-gradient work off the critical path
   std::vector<cudaEvent_t> side_ev;   // 3 per layer: fork, aggregate gradient done, side work done;
                                       // then one for the head gradients
+  cudaStream_t opt = nullptr;         // train step: early AdamW updates of layers L-1 .. 1
+  cudaEvent_t opt_ev = nullptr;       // their completion
   int device = 0;
   int H = 0, L = 0, T = 0, Hh = 0;
   int64_t P = 0;       // parameter count
@@ -84,6 +86,7 @@ struct gcnn_ctx {
   int last_step_kernels = 0;
   bool capturing = false;
   bool fuse_head = false;  // train step: head backward runs inside the forward's head kernel
+  bool fuse_step = false;  // train step: the optimiser follows the backward in the same graph
 
   // per-phase event timing (gcnn_profile_enable)
   bool prof_on = false;

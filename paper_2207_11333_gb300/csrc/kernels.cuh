@@ -63,11 +63,14 @@ int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const in
 // aggregate_chunk_capacity(n_edges) ints.  Smaller batches, and batches
 // with bond features (whose weight gradient reads the per-edge gradients in
 // scratch), take the edge + gather pair above.  Same result either way, bitwise.
+// make_chunks = false reuses the partition that a previous call on the same
+// batch and sizes wrote to `chunks`.
 int launch_aggregate_bwd_graphs(int n_graphs, int n_nodes, int n_edges, int H, DevDims dims, const int *node_off,
                                 const int *row_ptr, const int *col, const int *rev, const float *PQ,
                                 const float *agg, const float *dagg, float *dPQ, float *scratch, int *chunks,
                                 float eps, unsigned *err, cudaStream_t s, uint16_t *dPQ16 = nullptr, int ld16 = 0,
-                                const float *eattr = nullptr, const float *wE = nullptr, int F = 0);
+                                const float *eattr = nullptr, const float *wE = nullptr, int F = 0,
+                                bool make_chunks = true);
 int aggregate_chunk_capacity(int n_edges);
 // Bond rows' gradient out[f][c] (F x H) = sum over edge slots of eattr[r][f]
 // (row stride ld) times dm[r][c] (E x H, the per-edge message gradients at
@@ -136,17 +139,24 @@ struct HeadGradArgs {
 };
 int launch_head_grad(const HeadGradArgs &a, cudaStream_t s);
 
-// AdamW over n floats.  state[0] is the step counter (advanced by the kernel),
-// ticket a zero-initialised device word.  With wb non-null the updated
-// parameters are also written as BF16 (flat copy wb, and the packed backward
-// operands wpack of every layer when non-null).
+// AdamW over the parameters [b0, b0 + n0) and [b1, b1 + n1) of the flat
+// arrays (b0, n0 and b1 multiples of 4; n1 any).  state[0] is the step
+// counter: every launch uses the bias corrections of step state[0] + 1, and a
+// launch with `advance` set (the last of a step; ticket a zero-initialised
+// device word) moves it on once all its blocks are done.  With wb non-null the
+// updated parameters are also written as BF16 (flat copy wb, and the packed
+// backward operands wpack of every layer when non-null).  max_blocks caps the
+// grid (0: up to 8 blocks per SM).
 struct AdamPack {
   int H, L;
   long long layers_begin, layer_size;
 };
-int launch_adam(int64_t n, float *param, const float *grad, float *m, float *v, int *state, unsigned *ticket,
-                const float *lr, float beta1, float beta2, float eps, float wd, uint16_t *wb, uint16_t *wpack,
-                AdamPack pk, cudaStream_t s);
+struct AdamSpan {
+  long long b0, n0, b1, n1;
+};
+int launch_adam(AdamSpan span, bool advance, int max_blocks, float *param, const float *grad, float *m, float *v,
+                int *state, unsigned *ticket, const float *lr, float beta1, float beta2, float eps, float wd,
+                uint16_t *wb, uint16_t *wpack, AdamPack pk, cudaStream_t s);
 
 // ---------------------------------------------------------------- gemm_simt.cu
 // C = op(A) . op(B) in FP32 on CUDA cores (FFMA), with operands assembled on

@@ -183,6 +183,20 @@ bool overlapped(const gcnn_ctx *c) {
 
 bool bf16(const gcnn_ctx *c) { return c->cfg.precision == GCNN_PREC_BF16; }
 
+// In a train step whose BF16 backward overlaps, the AdamW update of layer
+// l + 1 runs on the side lane while the main stream works on layer l (layer
+// l + 1's gradients and its last use of its weights are then complete); the
+// step's final update covers the rest.  AdamW is elementwise, so the result is
+// the same bit for bit.
+bool layers_updated_early(const gcnn_ctx *c) { return c->fuse_step && bf16(c) && overlapped(c); }
+
+int adam(gcnn_ctx *c, AdamSpan sp, bool advance, int max_blocks, cudaStream_t s) {
+  const AdamPack pk{c->H, c->L, (long long)c->T * c->H, (long long)c->layer_size};
+  return launch_adam(sp, advance, max_blocks, c->params, c->grads, c->adam_m, c->adam_v, c->opt_state, c->tickets,
+                     c->lr_dev, (float)c->cfg.beta1, (float)c->cfg.beta2, (float)c->cfg.adam_eps,
+                     (float)c->cfg.weight_decay, c->wb, c->wpack, pk, s);
+}
+
 // BF16 views
 // [x_l | scaled aggregates] operand of layer l (one shared buffer with recompute)
 uint16_t *U_at(const gcnn_ctx *c, int l) {
@@ -326,6 +340,15 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
     d.ep.C = gw.upd_w; d.ep.ldc = H;
     GCNN_TRY(tc_on(c, d, lane));
   }
+  // layer l + 1 on a third stream, joined at the end of the backward: its
+  // gradients are complete at `done` of l + 1, its dx before `fork`; one
+  // block per SM leaves room for the GEMMs of the other two streams
+  if (ov && l + 1 < c->L && layers_updated_early(c)) {
+    GCNN_CUDA_TRY(cudaStreamWaitEvent(c->opt, fork, 0));
+    GCNN_CUDA_TRY(cudaStreamWaitEvent(c->opt, c->side_ev[3 * (l + 1) + 2], 0));
+    const long long b = (long long)c->T * H + (long long)(l + 1) * c->layer_size;
+    GCNN_TRY(adam(c, AdamSpan{b, c->layer_size, 0, 0}, false, num_sms(), c->opt));
+  }
   {  // dagg = [amp g | att g | g] [W_amp ; W_att ; W_id]^T
     TcDesc d = tblank();
     d.M = Ngrid; d.N = kAgg * H; d.K = pad64(3 * H); d.node_dim = kNodeM;
@@ -337,10 +360,12 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
   }
   {
     PhaseScope ps(c, GCNN_PHASE_AGG_BWD);
+    // layers run from L - 1 down: the first one cuts the batch into chunks, the rest reuse them
     GCNN_TRY(launch_aggregate_bwd_graphs(Gn, Ngrid, Egrid, H, dims, c->bb.node_off, c->bb.row_ptr, c->bb.col,
                                          c->bb.rev, pq, agg, c->dagg, dPQ, c->dm, c->chunks,
                                          (float)c->cfg.std_eps, c->err, c->stream, G + 3 * H, 5 * H, c->bb.eattr,
-                                         layer_ptrs(c->params, c, l).edge_w, c->cfg.edge_features));
+                                         layer_ptrs(c->params, c, l).edge_w, c->cfg.edge_features,
+                                         l == c->L - 1));
   }
   // before the next layer's aggregation backward reuses dm
   if (c->cfg.edge_features > 0) GCNN_TRY(gemm_bond_rows(c, Egrid, gw.edge_w));
@@ -478,6 +503,10 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
     }
     // every gradient is complete before the embedding gradient and the optimiser
     if (ov) GCNN_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->side_ev[2], 0));
+    if (c->L > 1 && layers_updated_early(c)) {
+      GCNN_CUDA_TRY(cudaEventRecord(c->opt_ev, c->opt));
+      GCNN_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->opt_ev, 0));
+    }
   }
   for (int l = bf16(c) ? -1 : c->L - 1; l >= 0; --l) {
     LayerW w = layer_ptrs(c->params, c, l);
@@ -526,7 +555,7 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
       GCNN_TRY(launch_aggregate_bwd_graphs(G, Ngrid, Egrid, H, dims, c->bb.node_off, c->bb.row_ptr, c->bb.col,
                                            c->bb.rev, pq, agg, c->dagg, c->dPQ, c->dm, c->chunks,
                                            (float)c->cfg.std_eps, c->err, c->stream, nullptr, 0, c->bb.eattr,
-                                           w.edge_w, c->cfg.edge_features));
+                                           w.edge_w, c->cfg.edge_features, l == c->L - 1));
     }
     if (c->cfg.edge_features > 0) GCNN_TRY(gemm_bond_rows(c, Egrid, gw.edge_w));
     // dW_M (H x 2H) and db_M: [x ; 1]^T dPQ  (bias row keeps the first H columns)
@@ -565,11 +594,12 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
 
 int ctx_step(gcnn_ctx *c) {
   PhaseScope ps(c, GCNN_PHASE_ADAM);
-  const AdamPack pk{c->H, c->L, (long long)c->T * c->H, (long long)c->layer_size};
-  GCNN_TRY(launch_adam(c->P, c->params, c->grads, c->adam_m, c->adam_v, c->opt_state, c->tickets, c->lr_dev,
-                       (float)c->cfg.beta1, (float)c->cfg.beta2, (float)c->cfg.adam_eps, (float)c->cfg.weight_decay,
-                       c->wb, c->wpack, pk, c->stream));
-  return GCNN_OK;
+  const long long lb = (long long)c->T * c->H, le = lb + (long long)c->L * c->layer_size;
+  // after a train step's overlapped backward only the embedding, layer 0 and
+  // the parameters after the layers remain; otherwise everything
+  const AdamSpan sp = layers_updated_early(c) ? AdamSpan{0, lb + c->layer_size, le, (long long)c->P - le}
+                                              : AdamSpan{0, 0, 0, (long long)c->P};
+  return adam(c, sp, true, 0, c->stream);
 }
 
 int ctx_refresh_bf16(gcnn_ctx *c) {

@@ -546,27 +546,26 @@ __device__ __forceinline__ long long packed_index(long long i, const AdamPack &k
   return base + n * 3u * H + ((blk + 2u) % 3u) * H + c;
 }
 
-// AdamW over the flat FP32 parameters.  The step counter state[0] is read by
-// every block and advanced by the last block to finish (ticket), so the
-// update of step t uses the bias corrections of t = state[0] + 1.  Optionally
-// writes the BF16 copies of the updated parameters (flat and packed).
+// AdamW over two spans of the flat FP32 parameters.  The step counter
+// state[0] is read by every block, so the update of step t uses the bias
+// corrections of t = state[0] + 1; with `advance` the last block to finish
+// (ticket) moves it on.  Optionally writes the BF16 copies of the updated
+// parameters (flat and packed).
 __global__ void __launch_bounds__(kThreads)
-adam_kernel(int64_t n, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+adam_kernel(AdamSpan sp, int advance, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
             float *__restrict__ v, int *__restrict__ state, unsigned *__restrict__ ticket,
             const float *__restrict__ lrp, float b1, float b2, float eps, float wd, uint16_t *__restrict__ wb,
             uint16_t *__restrict__ wpack, AdamPack pk) {
   pdl_entry(GCNN_K_ADAM);
-  __shared__ float s_c[2];
-  const int t = state[0] + 1;
-  if (threadIdx.x == 0) {
-    s_c[0] = (float)(1.0 / (1.0 - pow((double)b1, (double)t)));
-    s_c[1] = (float)(1.0 / (1.0 - pow((double)b2, (double)t)));
-  }
-  __syncthreads();
-  const float c1 = s_c[0], c2 = s_c[1], lr = lrp[0];
-  const int64_t n4 = n / 4;
+  // bias corrections 1 / (1 - beta^t) in FP32 in every thread: an FP64 pow
+  // per block costs microseconds on this part's narrow FP64 pipe, and every
+  // warp of the block waited for it
+  const float t = (float)(state[0] + 1);
+  const float c1 = 1.f / (1.f - powf(b1, t)), c2 = 1.f / (1.f - powf(b2, t)), lr = lrp[0];
+  const int64_t q0 = sp.n0 / 4, n4 = q0 + sp.n1 / 4;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n4; r += stride) {
+    const int64_t q = (r < q0 ? sp.b0 + 4 * r : sp.b1 + 4 * (r - q0)) / 4;  // float4 index
     float4 P = ld4(p + 4 * q), Gv = ld4(g + 4 * q), Mv = ld4(m + 4 * q), V = ld4(v + 4 * q);
     adam_one(P.x, Gv.x, Mv.x, V.x, lr, c1, c2, b1, b2, eps, wd);
     adam_one(P.y, Gv.y, Mv.y, V.y, lr, c1, c2, b1, b2, eps, wd);
@@ -581,14 +580,15 @@ adam_kernel(int64_t n, float *__restrict__ p, const float *__restrict__ g, float
       if (d >= 0) st_bf16x4(wpack + d, P.x, P.y, P.z, P.w);
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x < (int)(n - 4 * n4)) {
-    const int64_t k = 4 * n4 + threadIdx.x;
+  if (blockIdx.x == 0 && threadIdx.x < (int)(sp.n1 % 4)) {
+    const int64_t k = sp.b1 + sp.n1 / 4 * 4 + threadIdx.x;
     float P = p[k], M = m[k], V = v[k];
     adam_one(P, g[k], M, V, lr, c1, c2, b1, b2, eps, wd);
     p[k] = P; m[k] = M; v[k] = V;
     if (wb) wb[k] = (uint16_t)(bf16x2(P, 0.f) & 0xFFFFu);
   }
   // the last block to finish advances the step counter
+  if (!advance) return;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -740,13 +740,16 @@ int launch_node_grad(const NodeHeadArgs &a, float *grad_w2n, double *loss_accum,
   return GCNN_OK;
 }
 
-int launch_adam(int64_t n, float *param, const float *grad, float *m, float *v, int *state, unsigned *ticket,
-                const float *lr, float beta1, float beta2, float eps, float wd, uint16_t *wb, uint16_t *wpack,
-                AdamPack pk, cudaStream_t s) {
-  if (n <= 0) return GCNN_OK;
-  const int blocks = (int)std::min<int64_t>((n / 4 + kThreads - 1) / kThreads + 1, (int64_t)num_sms() * 8);
-  GCNN_TRY(launch(adam_kernel, blocks, kThreads, 0, s, n, param, grad, m, v, state, ticket, lr, beta1, beta2, eps, wd,
-                  wb, wpack, pk));
+int launch_adam(AdamSpan span, bool advance, int max_blocks, float *param, const float *grad, float *m, float *v,
+                int *state, unsigned *ticket, const float *lr, float beta1, float beta2, float eps, float wd,
+                uint16_t *wb, uint16_t *wpack, AdamPack pk, cudaStream_t s) {
+  if (span.b0 % 4 || span.n0 % 4 || span.b1 % 4 || span.n0 < 0 || span.n1 < 0)
+    return set_error(GCNN_EINVAL, "adam: spans must start and the first must end on multiples of 4");
+  if (span.n0 + span.n1 <= 0) return GCNN_OK;
+  const int64_t cap = max_blocks > 0 ? max_blocks : (int64_t)num_sms() * 8;
+  const int blocks = (int)std::min<int64_t>(((span.n0 + span.n1) / 4 + kThreads - 1) / kThreads + 1, cap);
+  GCNN_TRY(launch(adam_kernel, blocks, kThreads, 0, s, span, advance ? 1 : 0, param, grad, m, v, state, ticket, lr,
+                  beta1, beta2, eps, wd, wb, wpack, pk));
   return GCNN_OK;
 }
 

@@ -76,7 +76,10 @@ def test_overlapped_backward_matches_serial(tmp_path):
     """The BF16 backward's weight-gradient work on a second stream (default)
     gives the same gradients and parameters, bit for bit, as the serial step
     (GCNN_FLAG_SERIAL), over captured train steps and an eager backward: the
-    weight-gradient GEMMs plan with the same half-SM cap in both modes."""
+    weight-gradient GEMMs plan with the same half-SM cap in both modes.  In the
+    overlapped train steps the AdamW updates of layers L-1 .. 1 run on the
+    second stream during the backward, the serial ones update everything at the
+    end: the step counter and the parameters still agree."""
     import paper_2207_11333_gb300 as g
     G, H, L = 96, 64, 3
     d, gs, delta, student = workloads.small_parity(G=G, lo=3, hi=51, H=H, L=L)
