@@ -317,44 +317,68 @@ __global__ void __launch_bounds__(kHeadThreads) head_graph_kernel(HeadArgs a) {
       sd[c] = d;
       a.dz1[(size_t)gr * Hh + c] = d;
     }
-    // dg = W1 dz1, chunks in reverse order (the forward's last chunk is still staged)
-    const int warp = tid >> 5, lane = tid & 31;
+    // dg = W1 dz1, chunks in reverse order (the forward's last chunk is still
+    // staged): one thread per row of W1, four running sums over float4
+    // columns (16-byte aligned when Hh is a multiple of 4)
     for (int ch = nchunks - 1; ch >= 0; --ch) {
       if (staged != ch) stage(ch);
       else __syncthreads();
       const int k0 = ch * rk, rows = min(rk, H - k0);
-      for (int k = warp; k < rows; k += kHeadThreads / 32) {
-        float acc = 0.f;
-        for (int c = lane; c < Hh; c += 32) acc += Ws[(size_t)k * Hh + c] * sd[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
-          sv[k0 + k] = acc;
-          a.dg[(size_t)gr * H + k0 + k] = acc;
+      for (int k = tid; k < rows; k += kHeadThreads) {
+        const float *w = Ws + (size_t)k * Hh;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int c = 0;
+        if ((Hh & 3) == 0) {
+#pragma unroll 4
+          for (; c < Hh; c += 4) {
+            const float4 wv = ld4(w + c), dv = ld4(sd + c);
+            s0 = fmaf(wv.x, dv.x, s0); s1 = fmaf(wv.y, dv.y, s1);
+            s2 = fmaf(wv.z, dv.z, s2); s3 = fmaf(wv.w, dv.w, s3);
+          }
         }
+        for (; c < Hh; ++c) s0 = fmaf(w[c], sd[c], s0);
+        const float acc = (s0 + s1) + (s2 + s3);
+        sv[k0 + k] = acc;
+        a.dg[(size_t)gr * H + k0 + k] = acc;
       }
     }
     __syncthreads();
-    // mean pooling backward on the graph's nodes
+    // mean pooling backward on the graph's nodes, four items per thread at a
+    // time: every load of the four before any store
     const float n = (float)nn;
-    const int H4 = H >> 2;
-    for (int q = tid; q < nn * H4; q += kHeadThreads) {
-      const int i = n0 + q / H4, c = (q % H4) * 4;
-      float4 d = make_float4(sv[c] / n, sv[c + 1] / n, sv[c + 2] / n, sv[c + 3] / n);
-      if (a.dx_add) {  // the node-level head's gradient on the same atoms
-        const float4 e = ld4(a.dx_add + (size_t)i * H + c);
-        d = make_float4(d.x + e.x, d.y + e.y, d.z + e.z, d.w + e.w);
+    const int H4 = H >> 2, items = nn * H4;
+    constexpr int U = 4;
+    for (int q0 = tid; q0 < items; q0 += U * kHeadThreads) {
+      float4 e[U], m[U];
+      float am[U], at[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = min(q0 + u * kHeadThreads, items - 1);  // a valid item; only real ones are stored
+        const int i = n0 + q / H4, c = (q % H4) * 4;
+        e[u] = a.dx_add ? ld4(a.dx_add + (size_t)i * H + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (a.D3) {
+          m[u] = ld4(a.h + (size_t)i * H + c);
+          am[u] = a.amp[i];
+          at[u] = a.att[i];
+        }
       }
-      st4(a.dx + (size_t)i * H + c, d);
-      if (a.D3) {
-        const float4 m = ld4(a.h + (size_t)i * H + c);
-        const float gx = m.x > 0.f ? d.x : 0.f, gy = m.y > 0.f ? d.y : 0.f;
-        const float gz = m.z > 0.f ? d.z : 0.f, gw = m.w > 0.f ? d.w : 0.f;
-        const float am = a.amp[i], at = a.att[i];
-        uint16_t *o = a.D3 + (size_t)i * a.ld3 + c;
-        st_bf16x4(o, am * gx, am * gy, am * gz, am * gw);
-        st_bf16x4(o + H, at * gx, at * gy, at * gz, at * gw);
-        st_bf16x4(o + 2 * H, gx, gy, gz, gw);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = q0 + u * kHeadThreads;
+        if (q >= items) break;
+        const int i = n0 + q / H4, c = (q % H4) * 4;
+        // plus the node-level head's gradient on the same atoms, if any
+        float4 d = make_float4(sv[c] / n, sv[c + 1] / n, sv[c + 2] / n, sv[c + 3] / n);
+        if (a.dx_add) d = make_float4(d.x + e[u].x, d.y + e[u].y, d.z + e[u].z, d.w + e[u].w);
+        st4(a.dx + (size_t)i * H + c, d);
+        if (a.D3) {
+          const float gx = m[u].x > 0.f ? d.x : 0.f, gy = m[u].y > 0.f ? d.y : 0.f;
+          const float gz = m[u].z > 0.f ? d.z : 0.f, gw = m[u].w > 0.f ? d.w : 0.f;
+          uint16_t *o = a.D3 + (size_t)i * a.ld3 + c;
+          st_bf16x4(o, am[u] * gx, am[u] * gy, am[u] * gz, am[u] * gw);
+          st_bf16x4(o + H, at[u] * gx, at[u] * gy, at[u] * gz, at[u] * gw);
+          st_bf16x4(o + 2 * H, gx, gy, gz, gw);
+        }
       }
     }
   }
