@@ -184,10 +184,11 @@ bool overlapped(const gcnn_ctx *c) {
 bool bf16(const gcnn_ctx *c) { return c->cfg.precision == GCNN_PREC_BF16; }
 
 // In a train step whose BF16 backward overlaps, the AdamW update of layer
-// l + 1 runs on the side lane while the main stream works on layer l (layer
-// l + 1's gradients and its last use of its weights are then complete); the
-// step's final update covers the rest.  AdamW is elementwise, so the result is
-// the same bit for bit.
+// l + 1 runs on a third stream while the main stream works on layer l (layer
+// l + 1's gradients and its last use of its weights are then complete), and
+// layer 0 with the parameters after the layers runs there beside the
+// embedding gradient; the step's final update covers the embedding table.
+// AdamW is elementwise, so the result is the same bit for bit.
 bool layers_updated_early(const gcnn_ctx *c) { return c->fuse_step && bf16(c) && overlapped(c); }
 
 int adam(gcnn_ctx *c, AdamSpan sp, bool advance, int max_blocks, cudaStream_t s) {
@@ -503,9 +504,14 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
     }
     // every gradient is complete before the embedding gradient and the optimiser
     if (ov) GCNN_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->side_ev[2], 0));
-    if (c->L > 1 && layers_updated_early(c)) {
+    if (layers_updated_early(c)) {
+      // layer 0 and the head, bond rows and node head: every gradient but the
+      // embedding's is complete here
+      GCNN_CUDA_TRY(cudaEventRecord(c->opt_ev, c->stream));
+      GCNN_CUDA_TRY(cudaStreamWaitEvent(c->opt, c->opt_ev, 0));
+      const long long lb = (long long)c->T * H, le = lb + (long long)c->L * c->layer_size;
+      GCNN_TRY(adam(c, AdamSpan{lb, c->layer_size, le, (long long)c->P - le}, false, 0, c->opt));
       GCNN_CUDA_TRY(cudaEventRecord(c->opt_ev, c->opt));
-      GCNN_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->opt_ev, 0));
     }
   }
   for (int l = bf16(c) ? -1 : c->L - 1; l >= 0; --l) {
@@ -589,16 +595,17 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
   // embedding: dEmb[t] = sum of dx0 over nodes of type t
   PhaseScope ps(c, GCNN_PHASE_EMBED_BWD);
   GCNN_TRY(launch_embed_bwd(Ngrid, H, dims, c->bb.types, c->dH, c->T, c->grads, c->stream));
+  // the third stream's updates join before the step's final one
+  if (bf16(c) && layers_updated_early(c)) GCNN_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->opt_ev, 0));
   return GCNN_OK;
 }
 
 int ctx_step(gcnn_ctx *c) {
   PhaseScope ps(c, GCNN_PHASE_ADAM);
   const long long lb = (long long)c->T * c->H, le = lb + (long long)c->L * c->layer_size;
-  // after a train step's overlapped backward only the embedding, layer 0 and
-  // the parameters after the layers remain; otherwise everything
-  const AdamSpan sp = layers_updated_early(c) ? AdamSpan{0, lb + c->layer_size, le, (long long)c->P - le}
-                                              : AdamSpan{0, 0, 0, (long long)c->P};
+  // after a train step's overlapped backward only the embedding table
+  // remains; otherwise everything
+  const AdamSpan sp = layers_updated_early(c) ? AdamSpan{0, lb, 0, 0} : AdamSpan{0, 0, 0, (long long)c->P};
   return adam(c, sp, true, 0, c->stream);
 }
 
