@@ -117,3 +117,32 @@ def test_node_head_needs_node_targets(tmp_path):
         ctx.collate(st, np.arange(8))
     srv = g.Server(ctx, n_slots=1, buckets=(1024,), max_graphs=64)   # graph-level screening still serves
     srv.close()
+
+
+@pytest.mark.parametrize("L,F", [(1, 0), (2, 4)])
+def test_bf16_overlapped_train_steps_match_serial(tmp_path, L, F):
+    """BF16 train steps with the node head (and bond features): the overlapped
+    step, whose AdamW updates of the layers, the head, the bond rows and the node
+    head run on a third stream during the backward, equals the serial step (one
+    update at the end) bit for bit, parameters and loss sums; L = 1 has no
+    per-layer early update, only layer 0's beside the embedding gradient."""
+    import paper_2207_11333_gb300 as g
+    d, gs, p = _workload(G=96, lo=3, hi=40, H=32, L=L, F=F)
+    path, _ = write_both(gs, str(tmp_path))
+    st = g.Store(path)
+    delta = st.delta()
+    res = []
+    for flags in (0, g.FLAG_SERIAL):
+        ctx = g.Context(g.make_config(d.H, L, gs.n_graphs, gs.n_nodes, gs.n_edges, delta=delta,
+                                      precision=g.PREC_BF16, flags=flags, head_hidden=d.H, edge_features=F,
+                                      node_head=1, node_loss_weight=W))
+        ctx.set_params(p)
+        acc = torch.zeros(5, dtype=torch.float64, device="cuda")
+        for k in range(3):
+            ids = np.random.default_rng(k).permutation(gs.n_graphs)
+            ctx.train_step(ctx.collate(st, ids), 1e-3, acc)
+        res.append((ctx.get_params(), acc.cpu().numpy()))
+        ctx.check()
+        ctx.close()
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
