@@ -267,8 +267,12 @@ int gcnn_forward(gcnn_ctx *ctx, const gcnn_batch *b, float *pred, int train);
 int gcnn_backward(gcnn_ctx *ctx, const gcnn_batch *b, const float *dpred, double *loss_accum);
 /* AdamW step over all parameters with learning rate lr. */
 int gcnn_step(gcnn_ctx *ctx, float lr);
-/* forward(train) + backward(MSE) + step; replays a captured CUDA graph per
- * batch graph count after the first call with that count. */
+/* forward(train) + backward(MSE) + step (Sec. 3.2, Fig. 3: one training
+ * iteration); replays a captured CUDA graph per batch graph count after the
+ * first call with that count.  With BF16 GEMMs and the overlapped backward, the
+ * graph runs the weight gradients on a second stream and each layer's AdamW
+ * update on a third as soon as that layer's gradients are complete; the result
+ * equals forward + backward + step bit for bit. */
 int gcnn_train_step(gcnn_ctx *ctx, const gcnn_batch *b, float lr, double *loss_accum);
 /* Copy x^l (l = 0..L, N x H floats) of the last forward to host.  Sync. */
 int gcnn_get_activation(gcnn_ctx *ctx, int32_t layer, float *dst, int64_t n);
