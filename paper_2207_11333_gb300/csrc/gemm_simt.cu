@@ -32,7 +32,6 @@ __device__ __forceinline__ Sizes actual_sizes(const GemmDesc &d, DevDims dims) {
   Sizes s{d.M, d.K};
   if (d.node_dim == kNodeM) s.M = min(d.M, dims.nodes(d.M));
   if (d.node_dim == kNodeK) s.K = min(d.K, dims.nodes(d.K));
-  if (d.node_dim == kEdgeK) s.K = min(d.K, dims.edges(d.K));
   return s;
 }
 

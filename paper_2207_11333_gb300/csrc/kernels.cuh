@@ -178,10 +178,9 @@ struct Operand {
   int nseg;
 };
 
-// Which GEMM dimension runs over the batch's nodes (read from DevDims).
-// which GEMM dimension runs over the batch's nodes (or, kEdgeK, edges), so
-// that its extent is read from the device-side batch sizes
-enum NodeDim { kNodeNone = 0, kNodeM = 1, kNodeK = 2, kEdgeK = 3 };
+// Which GEMM dimension runs over the batch's nodes, so that its extent is
+// read from the device-side batch sizes (DevDims)
+enum NodeDim { kNodeNone = 0, kNodeM = 1, kNodeK = 2 };
 
 struct GemmDesc {
   int M, N, K;          // K: capacity when node_dim == kNodeK
