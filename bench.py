@@ -187,7 +187,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     step(order[:2], 1)
     per_graph = (time.perf_counter() - t0) / 2
-    budget = 150.0
+    budget = args.ref_seconds
     gps = int(max(1, min(BATCH, budget / max(per_graph * (args.steps + args.warmup), 1e-9))))
     pos = 2
     for w in range(args.warmup):
@@ -911,6 +911,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="host-time budget of the reference arm's warm-up and timed steps")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="seconds of Poisson load per arrival rate for the serving measurement (0: skip)")
     ap.add_argument("--serve-rates", default="200,1000,2000", help="arrival rates, requests/s")
