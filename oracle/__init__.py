@@ -9,7 +9,7 @@ step of the method, each citing the paper section it follows).  This file
 only marshals numpy arrays and reads the packed store file with its own
 reader.
 
-Parity pins (tests/test_oracle_pins.py): dense-adjacency matmul for the sum
+Parity pins (tests/oracle_pins.py, run by tests/test_oracle_pins.py): dense-adjacency matmul for the sum
 aggregator, torch.scatter_reduce for all five aggregators, closed forms of the
 degree scalers on cycles and stars, node-permutation invariance, pooling of a
 constant graph, central finite differences of every gradient, torch autograd
@@ -71,6 +71,10 @@ def load(path: str) -> ctypes.CDLL:
     L.oracle_backward.argtypes = [i32, i32, i32, i32, i32, i32, vp, i64, i64, i64] + [vp] * 11 + [dbl, dbl] + [vp] * 6
     L.oracle_adam.restype = None
     L.oracle_adam.argtypes = [i64, vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, dbl]
+    L.oracle_aggregate_op.restype = None
+    L.oracle_aggregate_op.argtypes = [i64, i32, vp, vp, dbl, vp]
+    L.oracle_aggregate_bwd_op.restype = None
+    L.oracle_aggregate_bwd_op.argtypes = [i64, i32, vp, vp, vp, vp, vp]
     return L
 
 
@@ -256,6 +260,34 @@ def adam(theta, grad, m, v, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, wd=0.0)
     for a in (theta, grad, m, v):
         assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
     lib().oracle_adam(theta.size, _p(theta), _p(grad), _p(m), _p(v), t, lr, b1, b2, eps, wd)
+
+
+# ------------------------------------------------------------------ operators
+
+def aggregate_op(row_ptr, m, eps: float = 1e-5):
+    """The aggregation step alone on given per-edge messages m (E, H), slots
+    grouped by destination through row_ptr (N+1): (N, 5H) [sum, mean, min,
+    max, std] in FP64 (oracle_aggregate_op)."""
+    rp = np.ascontiguousarray(row_ptr, np.int32)
+    m = np.ascontiguousarray(m, np.float64)
+    N, H = rp.size - 1, m.shape[1]
+    agg = np.zeros((N, N_AGG * H), np.float64)
+    lib().oracle_aggregate_op(N, H, _p(rp), _p(m), eps, _p(agg))
+    return agg
+
+
+def aggregate_bwd_op(row_ptr, m, agg, dagg):
+    """dL/dm (E, H) per edge slot from dL/dagg (N, 5H) and the forward's agg
+    (oracle_aggregate_bwd_op): min/max ties share, std via (m - mean)/(d std)."""
+    rp = np.ascontiguousarray(row_ptr, np.int32)
+    m = np.ascontiguousarray(m, np.float64)
+    agg = np.ascontiguousarray(agg, np.float64)
+    dagg = np.ascontiguousarray(dagg, np.float64)
+    N, H = rp.size - 1, m.shape[1]
+    assert agg.shape == (N, N_AGG * H) and dagg.shape == (N, N_AGG * H)
+    dm = np.zeros_like(m)
+    lib().oracle_aggregate_bwd_op(N, H, _p(rp), _p(m), _p(agg), _p(dagg), _p(dm))
+    return dm
 
 
 def split_params(d: Dims, p):

@@ -301,6 +301,48 @@ static void aggregate(const net_t *n, const double *m, double *agg) {
   }
 }
 
+/*
+ * Backward of the five aggregators (Sec. 3.1): the gradient dm[e] of the
+ * loss w.r.t. every message m[e] into node i, given the forward's agg[i]
+ * (sum, mean, min, max, std) and the incoming dagg[i]:
+ *   sum: 1 ; mean: 1/d ; min / max: 1 / (number of tied extrema) at each
+ *   extremum, 0 elsewhere ; std = sqrt(var + eps): (m - mean) / (d std)
+ *   (0 when var = 0, where the derivative of the ReLU is taken as 0).
+ */
+static void aggregate_backward(const net_t *n, const double *msg, const double *agg, const double *dagg,
+                               double *dm) {
+  int H = n->H;
+  const int32_t *row_ptr = n->row_ptr;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n->N; ++i) {
+    int32_t r0 = row_ptr[i], r1 = row_ptr[i + 1];
+    if (r1 == r0) continue;
+    double d = (double)(r1 - r0);
+    const double *a = agg + i * NAGG * H;
+    const double *da = dagg + i * NAGG * H;
+    for (int c = 0; c < H; ++c) {
+      double mean = a[1 * H + c], mn = a[2 * H + c], mx = a[3 * H + c], sd = a[4 * H + c];
+      double var = 0.0;
+      int nmin = 0, nmax = 0;
+      for (int32_t e = r0; e < r1; ++e) {
+        double v = msg[(int64_t)e * H + c];
+        var += (v - mean) * (v - mean);
+        nmin += (v == mn);
+        nmax += (v == mx);
+      }
+      var /= d;
+      for (int32_t e = r0; e < r1; ++e) {
+        double v = msg[(int64_t)e * H + c];
+        double g = da[0 * H + c] + da[1 * H + c] / d;      /* sum, mean */
+        if (v == mn) g += da[2 * H + c] / nmin;            /* min, ties share */
+        if (v == mx) g += da[3 * H + c] / nmax;            /* max, ties share */
+        if (var > 0.0) g += da[4 * H + c] * (v - mean) / (d * sd);  /* std */
+        dm[(int64_t)e * H + c] = g;
+      }
+    }
+  }
+}
+
 /* u_i = [x_i ; id*agg_i ; amp_i*agg_i ; att_i*agg_i]  (16H) */
 static void update_input(const net_t *n, const double *x, const double *agg, int64_t i, double *u) {
   int H = n->H;
@@ -612,34 +654,7 @@ int oracle_backward(int H, int L, int T, int Hh, int F, int NHd, const double *p
 
     /* aggregators -> per-edge message gradients */
     messages(&n, &w, x, f.msg);
-#pragma omp parallel for schedule(static)
-    for (int64_t i = 0; i < N; ++i) {
-      int32_t r0 = row_ptr[i], r1 = row_ptr[i + 1];
-      if (r1 == r0) continue;
-      double d = (double)(r1 - r0);
-      const double *a = agg + i * NAGG * H;
-      const double *da = dagg + i * NAGG * H;
-      for (int c = 0; c < H; ++c) {
-        double mean = a[1 * H + c], mn = a[2 * H + c], mx = a[3 * H + c], sd = a[4 * H + c];
-        double var = 0.0;
-        int nmin = 0, nmax = 0;
-        for (int32_t e = r0; e < r1; ++e) {
-          double v = f.msg[(int64_t)e * H + c];
-          var += (v - mean) * (v - mean);
-          nmin += (v == mn);
-          nmax += (v == mx);
-        }
-        var /= d;
-        for (int32_t e = r0; e < r1; ++e) {
-          double v = f.msg[(int64_t)e * H + c];
-          double g = da[0 * H + c] + da[1 * H + c] / d;      /* sum, mean */
-          if (v == mn) g += da[2 * H + c] / nmin;            /* min, ties share */
-          if (v == mx) g += da[3 * H + c] / nmax;            /* max, ties share */
-          if (var > 0.0) g += da[4 * H + c] * (v - mean) / (d * sd);  /* std */
-          dm[(int64_t)e * H + c] = g;
-        }
-      }
-    }
+    aggregate_backward(&n, f.msg, agg, dagg, dm);
 
     /* message layer: m_ij = b_M + W_M^T [x_i ; x_j ; e_ij], edge e = (j -> i) in row i */
     for (int c = 0; c < H; ++c) {
@@ -702,6 +717,33 @@ int oracle_backward(int H, int L, int T, int Hh, int F, int NHd, const double *p
   fwd_free(&f);
   free(pred); free(dpred); free(dx); free(dxn); free(dpre); free(dagg); free(dm); free(dg); free(tsrc); free(dpredn);
   return 0;
+}
+
+/* ------------------------------------------------------------ operators */
+
+/*
+ * The aggregation step alone (Sec. 3.1), on given messages: m[E][H] holds
+ * the message of every edge slot, the slots of node i being
+ * row_ptr[i]..row_ptr[i+1]-1.  agg[N][5H] receives [sum, mean, min, max,
+ * std] per node (all 0 for a node without in-edges).
+ */
+void oracle_aggregate_op(int64_t N, int H, const int32_t *row_ptr, const double *m, double eps, double *agg) {
+  net_t n;
+  memset(&n, 0, sizeof(n));
+  n.N = N; n.H = H; n.row_ptr = row_ptr; n.eps = eps;
+  aggregate(&n, m, agg);
+}
+
+/*
+ * Its backward: dm[E][H] = dL/dm for every edge slot from dagg[N][5H] and
+ * the forward's agg (oracle_aggregate_op of the same messages).
+ */
+void oracle_aggregate_bwd_op(int64_t N, int H, const int32_t *row_ptr, const double *m, const double *agg,
+                             const double *dagg, double *dm) {
+  net_t n;
+  memset(&n, 0, sizeof(n));
+  n.N = N; n.H = H; n.row_ptr = row_ptr;
+  aggregate_backward(&n, m, agg, dagg, dm);
 }
 
 /*

@@ -1,6 +1,8 @@
 """Shared test fixtures: seeded graph sets, oracle batches, error measures."""
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 import oracle
@@ -58,3 +60,98 @@ def custom_set(graphs) -> synth.GraphSet:
     return synth.GraphSet(np.array(node_ptr, np.int64), np.array(edge_ptr, np.int64),
                           np.array(types, np.uint8), np.array(edges, np.uint8).reshape(-1, 2),
                           np.zeros(len(graphs), np.float32))
+
+
+def star_and_dense_set(seed: int = 41, ks=(5, 8, 16, 64, 254), dense: int = 6, max_deg: int = 16):
+    """Stars K_{1,k} (centre in-degree k, leaves 1; leaf types cycle over the 7
+    atom types, so the centre sees groups of equal messages: ties) followed by
+    `dense` molecule-shaped graphs of 20-60 atoms with degrees up to max_deg
+    (2.5 bonds per atom, so many atoms have more than 4 neighbours).  Every
+    graph stays within the store's limits (255 atoms, 1,024 directed edges)."""
+    graphs = [([1] + [j % 7 for j in range(k)], [(0, j) for j in range(1, k + 1)]) for k in ks]
+    stars = custom_set(graphs)
+    if not dense:
+        return stars
+    mol = synth.make_graphs(seed, synth.node_counts_uniform(seed, 0, dense, 20, 60), max_deg=max_deg,
+                            edge_factor=2.5)
+    t = [(stars.types[stars.node_ptr[g]:stars.node_ptr[g + 1]].tolist(),
+          [tuple(e) for e in stars.edges[stars.edge_ptr[g]:stars.edge_ptr[g + 1]:2].tolist()])
+         for g in range(stars.n_graphs)]
+    t += [(mol.types[mol.node_ptr[g]:mol.node_ptr[g + 1]].tolist(),
+           [tuple(e) for e in mol.edges[mol.edge_ptr[g]:mol.edge_ptr[g + 1]:2].tolist()])
+          for g in range(mol.n_graphs)]
+    return custom_set(t)
+
+
+# Gates of the parity tests (relative errors, R13: normwise and max elementwise)
+FP32_FWD_TOL = 1e-5     # FP32 forward: predictions and every layer's activations
+FP32_GRAD_TOL = 1e-4    # FP32 gradients: every parameter tensor
+BF16_FWD_TOL = 2e-2     # BF16-GEMM forward, normwise
+BF16_U = 2.0 ** -8      # unit roundoff of bfloat16 (8 significant bits, round to nearest)
+
+
+def bf16_fwd_bound(L: int) -> float:
+    """First-order forward error of the BF16-GEMM path: every BF16 GEMM rounds
+    both operands once (relative error <= u each, FP32 accumulation adds
+    K 2^-24 <= 2e-4, negligible), so one GEMM output carries <= 2u; a forward
+    pass chains 2 GEMMs per layer (message, update) and the errors add:
+    2u * 2L."""
+    return 2 * BF16_U * 2 * L
+
+
+def bf16_grad_bound(L: int, kappa: float = 1.0) -> float:
+    """Normwise bound for a parameter gradient of the BF16-GEMM path against the
+    FP64 oracle, from two error sources (neither taken from a measurement):
+
+    rounding along the path: <= 2u per BF16 GEMM output, at most 4L + 1 of
+      them between the loss and a weight gradient (2L forward, 2 per layer
+      of the backward above the tensor, the weight-gradient GEMM itself),
+      amplified by kappa = ||yhat|| / ||yhat - y|| (>= 1) because the loss
+      gradient is the residual yhat - y;
+    decisions: the ReLU masks and the min/max routes are decided on forward
+      values that carry <= e = bf16_fwd_bound(L) relative error; an entry
+      whose margin is below e can flip, which with margins of density <= 1
+      near 0 is a fraction <= e of the entries, and a flip moves at most the
+      entry's own gradient (twice its square in the norm): sqrt(2 e).
+    """
+    return 2 * BF16_U * (4 * L + 1) * max(1.0, kappa) + math.sqrt(2 * bf16_fwd_bound(L))
+
+
+def residual_kappa(pred, y) -> float:
+    """kappa = ||yhat|| / ||yhat - y|| (at least 1) from the oracle's predictions."""
+    pred = np.asarray(pred, np.float64)
+    r = np.linalg.norm(pred - np.asarray(y, np.float64))
+    return max(1.0, float(np.linalg.norm(pred) / r)) if r > 0 else float("inf")
+
+
+class Gates:
+    """Collects relative errors of many tensors, prints them all, and fails
+    once at the end with every tensor that broke its gate."""
+
+    def __init__(self, title: str):
+        self.title = title
+        self.rows = []
+
+    def check(self, name, a, b, norm_tol: float, elem_tol: float | None = None):
+        b64 = np.asarray(b, np.float64)
+        if b64.size and np.max(np.abs(b64)) == 0.0:
+            en = float(np.max(np.abs(np.asarray(a, np.float64))))     # an exactly-zero reference
+            self.rows.append((name, en, en, norm_tol, elem_tol, en <= 0.0))
+            return
+        en = rel_norm(a, b)
+        em = rel_max(a, b) if elem_tol is not None else float("nan")
+        ok = en < norm_tol and (elem_tol is None or em < elem_tol)
+        self.rows.append((name, en, em, norm_tol, elem_tol, ok))
+
+    def report(self) -> str:
+        lines = [f"{self.title}: tensor, normwise, elementwise, gates"]
+        for name, en, em, nt, et, ok in self.rows:
+            lines.append(f"  {name:12s} {en:9.2e} {em:9.2e}  <{nt:.0e}" + (f" <{et:.0e}" if et else "") +
+                         ("" if ok else "  FAIL"))
+        return "\n".join(lines)
+
+    def assert_all(self):
+        text = self.report()
+        print(text)
+        bad = [r[0] for r in self.rows if not r[5]]
+        assert not bad, f"gates broken by {bad}\n{text}"

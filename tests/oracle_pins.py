@@ -16,7 +16,7 @@ import torch
 import oracle
 import synth
 import torch_ref
-from helpers import custom_set, graph_set, oracle_batch, rel_max, rel_norm
+from helpers import custom_set, graph_set, oracle_batch, rel_max, rel_norm, star_and_dense_set
 
 EPS = 1e-5
 
@@ -503,6 +503,73 @@ def pin_node_head_permutation_equivariance():
     assert rel_norm(predn2[np.concatenate(perms)], predn) < 1e-12
 
 
+def _torch_aggregators(m, row_ptr, eps=EPS):
+    """[sum, mean, min, max, std] of per-slot messages by scatter_reduce (FP64, autograd-able)."""
+    N = len(row_ptr) - 1
+    deg = np.diff(row_ptr)
+    dst = torch.from_numpy(np.repeat(np.arange(N), deg)).long()
+    idx = dst.unsqueeze(1).expand(-1, m.shape[1])
+    z = torch.zeros(N, m.shape[1], dtype=m.dtype)
+    s = z.scatter_reduce(0, idx, m, "sum", include_self=False)
+    mean = z.scatter_reduce(0, idx, m, "mean", include_self=False)
+    mn = z.scatter_reduce(0, idx, m, "amin", include_self=False)
+    mx = z.scatter_reduce(0, idx, m, "amax", include_self=False)
+    d = torch.from_numpy(np.maximum(deg, 1).astype(np.float64)).unsqueeze(1)
+    var = z.index_add(0, dst, m * m) / d - mean * mean       # E[m^2] - E[m]^2
+    sd = torch.sqrt(torch.relu(var) + eps)
+    has = torch.from_numpy((deg > 0).astype(np.float64)).unsqueeze(1)
+    return torch.cat([s, mean, mn, mx, sd], 1) * has
+
+
+def pin_aggregate_operator_high_degree():
+    """The aggregation operator and its per-edge backward against torch
+    scatter_reduce + autograd on stars K_{1,k} (k up to 254) and molecules with
+    degrees up to 16: continuous messages, and messages on a grid of 1/16 where
+    min/max tie among many edges (autograd of amax/amin shares the gradient
+    equally among ties, the rule the oracle states).  On the grid P is an odd
+    and Q an even multiple of 1/16, so no message is 0: torch's amax/amin
+    backward would count the 0 it starts from as one more tie."""
+    gs = star_and_dense_set()
+    _, b, _ = oracle_batch(gs)
+    assert b.deg.max() == 254 and np.sum(b.deg > 4) > 20
+    H = 6
+    rng = np.random.default_rng(3)
+    dst = np.repeat(np.arange(b.N), b.deg)
+    for grid in (False, True):
+        if grid:   # m_e = P_i + Q_j, odd multiples of 1/16: exact, with ties, never 0
+            P, Q = (2 * rng.integers(-8, 8, (b.N, H)) + 1) / 16.0, 2 * rng.integers(-3, 3, (b.N, H)) / 16.0
+        else:
+            P, Q = rng.standard_normal((b.N, H)), rng.standard_normal((b.N, H))
+        m = P[dst] + Q[b.col]
+        agg = oracle.aggregate_op(b.row_ptr, m)
+        mt = torch.tensor(m, requires_grad=True)
+        ref = _torch_aggregators(mt, b.row_ptr)
+        assert rel_norm(agg, ref.detach().numpy()) < 1e-12
+        assert rel_max(agg, ref.detach().numpy()) < 1e-10
+        dagg = rng.standard_normal((b.N, 5 * H))
+        (ref * torch.tensor(dagg)).sum().backward()
+        dm = oracle.aggregate_bwd_op(b.row_ptr, m, agg, dagg)
+        assert rel_norm(dm, mt.grad.numpy()) < 1e-10, grid
+        assert rel_max(dm, mt.grad.numpy()) < 1e-8, grid
+
+
+def pin_gradients_autograd_high_degree():
+    """Model gradients equal torch autograd (FP64) on stars and high-degree molecules
+    (rows longer than any fixed cache of edges), with atom-type embeddings (ties)."""
+    d, p = _model(3, 8, 2)
+    gs = star_and_dense_set(ks=(5, 9, 17, 40), dense=4)
+    gs.y = synth.uniform_targets(5, 0, gs.n_graphs, 1.0, 10.0)
+    st, b, _ = oracle_batch(gs)
+    assert b.deg.max() == 40
+    loss, grad, _, pred = oracle.backward(d, p, b)
+    rloss, rgrad, _, rpred = torch_ref.loss_and_grads(d, p, b)
+    assert abs(loss - rloss) <= 1e-12 * abs(rloss)
+    assert rel_norm(pred, rpred) < 1e-12
+    views, rviews = oracle.split_params(d, grad), oracle.split_params(d, rgrad)
+    for k in views:
+        assert rel_norm(views[k], rviews[k]) < 1e-10, k
+
+
 NODE_PINS = [pin_node_head_weight_zero, pin_node_head_constant_output, pin_node_head_autograd,
              pin_node_head_finite_differences, pin_node_head_permutation_equivariance]
 
@@ -514,4 +581,5 @@ ALL_PINS = [pin_collation_lexsort, pin_sum_is_dense_adjacency_matmul, pin_aggreg
             pin_scalers_cycle_closed_form, pin_scalers_star_closed_form, pin_permutation_invariance,
             pin_pool_of_constant_graph, pin_constant_messages, pin_gradients_autograd,
             pin_gradients_autograd_continuous, pin_finite_differences, pin_adam_first_step,
-            pin_adamw_decay, pin_mse_gradient] + BOND_PINS + NODE_PINS
+            pin_adamw_decay, pin_mse_gradient, pin_aggregate_operator_high_degree,
+            pin_gradients_autograd_high_degree] + BOND_PINS + NODE_PINS
