@@ -111,6 +111,7 @@ struct HeadArgs {
   int ld3;
   const float *h, *amp, *att;
   const float *dx_add;  // nullable: N x H added to the pooling gradient (node-level head)
+  const float *loss_scale;  // nullable: device scalar multiplying dL/dyhat of the MSE (1 when null)
 };
 int launch_head_graph(HeadArgs a, bool fwd, bool bwd, cudaStream_t s);
 // Node-level head on the last layer's atoms (zn = x W1n + b1n from a GEMM):
@@ -122,6 +123,7 @@ struct NodeHeadArgs {
   const float *zn, *w2n, *b2n, *y;
   float *pred, *dpred, *dzn;
   float weight;
+  const float *loss_scale;  // nullable: device scalar multiplying the node-level loss gradient
 };
 int launch_node_pred(const NodeHeadArgs &a, bool train, cudaStream_t s);
 // Node head gradients of w2n (Hh) and b2n (1) into grad_w2n[0 .. Hh], summed
@@ -155,7 +157,7 @@ struct AdamSpan {
   long long b0, n0, b1, n1;
 };
 int launch_adam(AdamSpan span, bool advance, int max_blocks, float *param, const float *grad, float *m, float *v,
-                int *state, unsigned *ticket, const float *lr, float beta1, float beta2, float eps, float wd,
+                int *state, unsigned *ticket, const float *lr, double beta1, double beta2, float eps, float wd,
                 uint16_t *wb, uint16_t *wpack, AdamPack pk, cudaStream_t s);
 
 // ---------------------------------------------------------------- gemm_simt.cu

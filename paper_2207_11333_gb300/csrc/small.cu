@@ -306,7 +306,8 @@ __global__ void __launch_bounds__(kHeadThreads) head_graph_kernel(HeadArgs a) {
     __syncthreads();
     if (tid == 0) {
       const float r = s_pred - a.y[gr];
-      const float dp = a.dpred_in ? a.dpred_in[gr] : 2.f * r / (float)G;
+      // the MSE gradient times the loss scale (data-parallel weighting, 1 alone)
+      const float dp = a.dpred_in ? a.dpred_in[gr] : (2.f * r / (float)G) * (a.loss_scale ? a.loss_scale[0] : 1.f);
       a.dpred[gr] = dp;
       s_dp = dp;
     }
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(kNodeWarps * 32) node_pred_kernel(NodeHeadArgs
   const float p = acc + a.b2n[0];
   if (lane == 0) a.pred[i] = p;
   if (!train) return;
-  const float dp = a.weight * 2.f * (p - a.y[i]) / (float)N;
+  const float dp = (a.weight * 2.f * (p - a.y[i]) / (float)N) * (a.loss_scale ? a.loss_scale[0] : 1.f);
   if (lane == 0) a.dpred[i] = dp;
   float *dz = a.dzn + (size_t)i * a.Hh;
   for (int c = lane; c < a.Hh; c += 32) dz[c] = z[c] > 0.f ? dp * a.w2n[c] : 0.f;
@@ -539,11 +540,17 @@ __global__ void __launch_bounds__(kRedThreads) node_grad_kernel(NodeHeadArgs a, 
 }
 
 // ---------------------------------------------------------------- AdamW
+// Moment decays beta and their complements 1 - beta, each rounded once to
+// FP32 from double: 1 - (float)0.999 would carry a 1.3e-5 relative error.
+struct AdamBetas {
+  float b1, omb1, b2, omb2;
+};
+
 __device__ __forceinline__ void adam_one(float &p, float g, float &m, float &v, float lr, float c1,
-                                         float c2, float b1, float b2, float eps, float wd) {
+                                         float c2, const AdamBetas &bt, float eps, float wd) {
   if (wd > 0.f) p -= lr * wd * p;
-  m = b1 * m + (1.f - b1) * g;
-  v = b2 * v + (1.f - b2) * g * g;
+  m = bt.b1 * m + bt.omb1 * g;
+  v = bt.b2 * v + bt.omb2 * (g * g);
   p -= lr * (m * c1) / (sqrtf(v * c2) + eps);
 }
 
@@ -578,23 +585,25 @@ __device__ __forceinline__ long long packed_index(long long i, const AdamPack &k
 __global__ void __launch_bounds__(kThreads)
 adam_kernel(AdamSpan sp, int advance, float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
             float *__restrict__ v, int *__restrict__ state, unsigned *__restrict__ ticket,
-            const float *__restrict__ lrp, float b1, float b2, float eps, float wd, uint16_t *__restrict__ wb,
+            const float *__restrict__ lrp, AdamBetas bt, float eps, float wd, uint16_t *__restrict__ wb,
             uint16_t *__restrict__ wpack, AdamPack pk) {
   pdl_entry(GCNN_K_ADAM);
-  // bias corrections 1 / (1 - beta^t) in FP32 in every thread: an FP64 pow
-  // per block costs microseconds on this part's narrow FP64 pipe, and every
-  // warp of the block waited for it
+  // bias corrections 1 / (1 - beta^t) in FP32 in every thread (an FP64 pow
+  // per block costs microseconds on this part's narrow FP64 pipe).  1 - beta^t
+  // is formed as -expm1(t log1p(-(1 - beta))) from the complement: the
+  // difference of two rounded numbers near 1 is never taken, which with
+  // beta2 = 0.999 would cost ~1e-7 / (1 - beta2^t) relative error
   const float t = (float)(state[0] + 1);
-  const float c1 = 1.f / (1.f - powf(b1, t)), c2 = 1.f / (1.f - powf(b2, t)), lr = lrp[0];
+  const float c1 = -1.f / expm1f(t * log1pf(-bt.omb1)), c2 = -1.f / expm1f(t * log1pf(-bt.omb2)), lr = lrp[0];
   const int64_t q0 = sp.n0 / 4, n4 = q0 + sp.n1 / 4;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n4; r += stride) {
     const int64_t q = (r < q0 ? sp.b0 + 4 * r : sp.b1 + 4 * (r - q0)) / 4;  // float4 index
     float4 P = ld4(p + 4 * q), Gv = ld4(g + 4 * q), Mv = ld4(m + 4 * q), V = ld4(v + 4 * q);
-    adam_one(P.x, Gv.x, Mv.x, V.x, lr, c1, c2, b1, b2, eps, wd);
-    adam_one(P.y, Gv.y, Mv.y, V.y, lr, c1, c2, b1, b2, eps, wd);
-    adam_one(P.z, Gv.z, Mv.z, V.z, lr, c1, c2, b1, b2, eps, wd);
-    adam_one(P.w, Gv.w, Mv.w, V.w, lr, c1, c2, b1, b2, eps, wd);
+    adam_one(P.x, Gv.x, Mv.x, V.x, lr, c1, c2, bt, eps, wd);
+    adam_one(P.y, Gv.y, Mv.y, V.y, lr, c1, c2, bt, eps, wd);
+    adam_one(P.z, Gv.z, Mv.z, V.z, lr, c1, c2, bt, eps, wd);
+    adam_one(P.w, Gv.w, Mv.w, V.w, lr, c1, c2, bt, eps, wd);
     st4(p + 4 * q, P);
     st4(m + 4 * q, Mv);
     st4(v + 4 * q, V);
@@ -607,7 +616,7 @@ adam_kernel(AdamSpan sp, int advance, float *__restrict__ p, const float *__rest
   if (blockIdx.x == 0 && threadIdx.x < (int)(sp.n1 % 4)) {
     const int64_t k = sp.b1 + sp.n1 / 4 * 4 + threadIdx.x;
     float P = p[k], M = m[k], V = v[k];
-    adam_one(P, g[k], M, V, lr, c1, c2, b1, b2, eps, wd);
+    adam_one(P, g[k], M, V, lr, c1, c2, bt, eps, wd);
     p[k] = P; m[k] = M; v[k] = V;
     if (wb) wb[k] = (uint16_t)(bf16x2(P, 0.f) & 0xFFFFu);
   }
@@ -765,15 +774,16 @@ int launch_node_grad(const NodeHeadArgs &a, float *grad_w2n, double *loss_accum,
 }
 
 int launch_adam(AdamSpan span, bool advance, int max_blocks, float *param, const float *grad, float *m, float *v,
-                int *state, unsigned *ticket, const float *lr, float beta1, float beta2, float eps, float wd,
+                int *state, unsigned *ticket, const float *lr, double beta1, double beta2, float eps, float wd,
                 uint16_t *wb, uint16_t *wpack, AdamPack pk, cudaStream_t s) {
   if (span.b0 % 4 || span.n0 % 4 || span.b1 % 4 || span.n0 < 0 || span.n1 < 0)
     return set_error(GCNN_EINVAL, "adam: spans must start and the first must end on multiples of 4");
   if (span.n0 + span.n1 <= 0) return GCNN_OK;
   const int64_t cap = max_blocks > 0 ? max_blocks : (int64_t)num_sms() * 8;
   const int blocks = (int)std::min<int64_t>(((span.n0 + span.n1) / 4 + kThreads - 1) / kThreads + 1, cap);
+  const AdamBetas bt{(float)beta1, (float)(1.0 - beta1), (float)beta2, (float)(1.0 - beta2)};
   GCNN_TRY(launch(adam_kernel, blocks, kThreads, 0, s, span, advance ? 1 : 0, param, grad, m, v, state, ticket, lr,
-                  beta1, beta2, eps, wd, wb, wpack, pk));
+                  bt, eps, wd, wb, wpack, pk));
   return GCNN_OK;
 }
 

@@ -1,6 +1,8 @@
 """BF16 tensor-core GEMM path (tcgen05) against the FP64 oracle: forward within
-2e-2 relative (normwise) per output and per layer; gradient errors stated and
-bounded; the BF16 and FP32 paths agree to BF16 accuracy."""
+2e-2 relative (normwise) per output and per layer, predictions also
+elementwise; gradients within the BF16 error bound derived in tests/helpers.py
+(bf16_grad_bound: operand rounding along the GEMM chain plus ReLU / min-max
+decision flips); the BF16 and FP32 paths agree to BF16 accuracy."""
 import numpy as np
 import pytest
 import torch
@@ -8,11 +10,9 @@ import torch
 import oracle
 import workloads
 from gpu_common import oracle_step, write_both
-from helpers import rel_norm
+from helpers import BF16_FWD_TOL, Gates, bf16_grad_bound, rel_norm, residual_kappa
 
 pytestmark = pytest.mark.gpu
-
-BF16_FWD_TOL = 2e-2
 
 
 def _run(tmp_path, precision, G=64, lo=5, hi=30, H=32, L=2, recompute=False, serial=False):
@@ -43,13 +43,15 @@ def test_bf16_forward_and_gradients(tmp_path, G, lo, hi, H, L):
     d, student, ob, pred, acts, grads = _run(tmp_path, g.PREC_BF16, G, lo, hi, H, L)
     opred, oxs, _, _ = oracle.forward(d, student.astype(np.float64), ob, want_layers=True)
     _, ograd, _, _ = oracle_step(d, student, ob)
-    assert rel_norm(pred, opred) < BF16_FWD_TOL, rel_norm(pred, opred)
+    gates = Gates(f"bf16 G = {G}, H = {H}, L = {L}")
+    gates.check("pred", pred, opred, BF16_FWD_TOL)
     for l in range(1, d.L + 1):
-        assert rel_norm(acts[l], oxs[l]) < BF16_FWD_TOL, (l, rel_norm(acts[l], oxs[l]))
+        gates.check(f"x{l}", acts[l], oxs[l], BF16_FWD_TOL)
     gv, ov = oracle.split_params(d, grads), oracle.split_params(d, ograd)
-    errs = {k: rel_norm(gv[k], ov[k]) for k in ov if np.linalg.norm(ov[k]) > 0}
-    print("bf16 gradient rel errors:", {k: f"{v:.2e}" for k, v in errs.items()})
-    assert max(errs.values()) < 0.1, errs
+    bound = bf16_grad_bound(d.L, residual_kappa(opred, ob.y))
+    for k in ov:
+        gates.check(k, gv[k], ov[k], bound, elementwise=False)
+    gates.assert_all()
 
 
 def test_bf16_matches_fp32_path(tmp_path):
@@ -57,7 +59,7 @@ def test_bf16_matches_fp32_path(tmp_path):
     _, _, _, p16, a16, g16 = _run(tmp_path, g.PREC_BF16)
     _, _, _, p32, a32, g32 = _run(tmp_path, g.PREC_FP32)
     assert rel_norm(p16, p32) < BF16_FWD_TOL
-    assert rel_norm(g16, g32) < 0.1
+    assert rel_norm(g16, g32) < bf16_grad_bound(2)
 
 
 @pytest.mark.parametrize("G,hi", [(64, 30), (900, 60)])
