@@ -231,7 +231,9 @@ typedef struct gcnn_batch {
                                the node head)                                 */
 } gcnn_batch;
 
-/* Collate graphs graph_ids[0..n_graphs) (host ids) of `st` on the device.
+/* Collate graphs graph_ids[0..n_graphs) (host ids) of `st` on the device: the
+ * disjoint union of the molecules as one graph (Sec. 3.2: a mini-batch of
+ * graphs; Sec. 4, Table 1: per-graph slices of the global arrays).
  * Resident store: the collator reads the device copy; otherwise the graphs'
  * slices are gathered into pinned staging memory and copied in one transfer.
  * GCNN_EINVAL if the batch exceeds the context's capacities. */
@@ -254,19 +256,57 @@ int gcnn_batch_export(gcnn_ctx *ctx, const gcnn_batch *b, int32_t *node_off, int
                       float *att, uint8_t *types, float *y);
 
 /* ------------------------------------------------------------------ training */
-/* Forward pass; pred (device, G floats) may be NULL.  train = 1 keeps what
- * backward needs (with the node head it also forms the node-level loss
- * gradient from the batch's node targets). */
+/* Forward pass (Sec. 3.1: embedding, L PNA message-passing layers, global
+ * mean pooling, FC head; Fig. 3's forward phase); pred (device, G floats) may
+ * be NULL.  train = 1 keeps what backward needs (with the node head it also
+ * forms the node-level loss gradient from the batch's node targets). */
 int gcnn_forward(gcnn_ctx *ctx, const gcnn_batch *b, float *pred, int train);
-/* Backward of the last forward(train = 1) on the same batch.  dpred (device,
+/* Backward of the last forward(train = 1) on the same batch (Sec. 3.2, Fig. 3:
+ * the MSE loss and its gradients w.r.t. every parameter).  dpred (device,
  * G) = dL/dyhat, or NULL for the MSE loss against the batch targets.
  * Gradients overwrite the context's gradient buffer.  loss_accum (device,
  * 3 doubles, 5 with the node head, may be NULL): += sum (yhat-y)^2,
  * += sum |yhat-y|, += G, then += sum over atoms (yhat_i-y_i)^2, += N.  The
  * node-level loss always uses the batch's node targets (dpred is graph-level). */
 int gcnn_backward(gcnn_ctx *ctx, const gcnn_batch *b, const float *dpred, double *loss_accum);
-/* AdamW step over all parameters with learning rate lr. */
+/* AdamW step over all parameters with learning rate lr (Sec. 3.2, Fig. 3: the
+ * optimizer update of one training iteration; Sec. 5.1: AdamW). */
 int gcnn_step(gcnn_ctx *ctx, float lr);
+
+/* ------------------------------------------------------- data parallelism
+ * Sec. 4 (Fig. 4): distributed data parallelism replicates the model on every
+ * GPU, gives each process its own graphs and averages the gradients with an
+ * all-reduce before every optimizer step.  The library does not talk to other
+ * processes; these calls let the caller run that exchange with its own
+ * communicator (NCCL through torch.distributed in the Python package), bucket
+ * by bucket while the backward is still running.
+ *
+ * gcnn_set_loss_scale: multiply dL/dyhat of the graph-level MSE by graph_scale
+ * and the node-level loss gradient by node_scale in every later backward and
+ * train step (both 1 after gcnn_create).  With graph_scale = G_r / G (this
+ * process's graphs over all processes' graphs of the step) and node_scale =
+ * N_r / N (atoms likewise), the sum over processes of the gradients is the
+ * gradient of the whole step's mean loss.  Not applied to a caller-given dpred.
+ * Synchronises the context's stream when a value changes.  GCNN_EINVAL for a
+ * negative or non-finite scale. */
+int gcnn_set_loss_scale(gcnn_ctx *ctx, float graph_scale, float node_scale);
+/* Number of gradient buckets: L + 2.  Bucket l < L is conv layer l's
+ * parameters; bucket L the head, bond rows and node head; bucket L + 1 the
+ * embedding table.  Buckets are disjoint and together cover the flat buffer. */
+int gcnn_grad_buckets(const gcnn_ctx *ctx, int32_t *n_buckets);
+/* Float offset and count of bucket k in the flat gradient buffer. */
+int gcnn_grad_bucket(const gcnn_ctx *ctx, int32_t k, int64_t *offset, int64_t *count);
+/* Make `stream` (a caller's cudaStream_t) wait until bucket k's gradients of
+ * the last gcnn_backward are final.  Layer buckets complete during the
+ * backward, from the last layer to the first; buckets L and L + 1 when it
+ * ends.  Valid after gcnn_backward, not after gcnn_train_step (whose graph
+ * applies AdamW itself).  Enqueues a wait only; never blocks the host. */
+int gcnn_grad_wait(gcnn_ctx *ctx, int32_t k, void *stream);
+/* Device address of the flat FP32 gradient buffer (gcnn_param_count floats,
+ * owned by the context, valid until gcnn_destroy).  A caller that reduces the
+ * gradients in place does so between gcnn_backward and gcnn_step, on streams
+ * ordered after gcnn_grad_wait and before the context's stream resumes. */
+int gcnn_grads_device(gcnn_ctx *ctx, float **grads);
 /* forward(train) + backward(MSE) + step (Sec. 3.2, Fig. 3: one training
  * iteration); replays a captured CUDA graph per batch graph count after the
  * first call with that count.  With BF16 GEMMs and the overlapped backward, the

@@ -107,6 +107,11 @@ def _load() -> ctypes.CDLL:
         "gcnn_forward": (i32, [vp, P(BatchStruct), vp, i32]),
         "gcnn_backward": (i32, [vp, P(BatchStruct), vp, vp]),
         "gcnn_step": (i32, [vp, f32]),
+        "gcnn_set_loss_scale": (i32, [vp, f32, f32]),
+        "gcnn_grad_buckets": (i32, [vp, P(i32)]),
+        "gcnn_grad_bucket": (i32, [vp, i32, P(i64), P(i64)]),
+        "gcnn_grad_wait": (i32, [vp, i32, vp]),
+        "gcnn_grads_device": (i32, [vp, P(vp)]),
         "gcnn_train_step": (i32, [vp, P(BatchStruct), f32, vp]),
         "gcnn_get_activation": (i32, [vp, i32, vp, i64]),
         "gcnn_profile_enable": (i32, [vp, i32]),
@@ -354,6 +359,33 @@ class Context:
 
     def reset_optimizer(self) -> None:
         _check(lib.gcnn_reset_optimizer(self._h))
+
+    # data parallelism (Sec. 4): hooks for an exchange of the gradients
+    def set_loss_scale(self, graph_scale: float, node_scale: float = 1.0) -> None:
+        _check(lib.gcnn_set_loss_scale(self._h, float(graph_scale), float(node_scale)))
+
+    def grad_buckets(self) -> list[tuple[int, int]]:
+        """(offset, count) of every gradient bucket: layers 0..L-1, head (+ bond
+        rows, node head), embedding."""
+        n = ctypes.c_int32()
+        _check(lib.gcnn_grad_buckets(self._h, ctypes.byref(n)))
+        out = []
+        for k in range(n.value):
+            o, c = ctypes.c_int64(), ctypes.c_int64()
+            _check(lib.gcnn_grad_bucket(self._h, k, ctypes.byref(o), ctypes.byref(c)))
+            out.append((o.value, c.value))
+        return out
+
+    def grad_wait(self, bucket: int, stream) -> None:
+        """Order `stream` (torch stream or raw handle) after bucket's final gradients."""
+        _check(lib.gcnn_grad_wait(self._h, int(bucket), _stream(stream)))
+
+    def grads_tensor(self):
+        """Zero-copy torch view of the flat FP32 gradient buffer on the device."""
+        import torch
+        p = ctypes.c_void_p()
+        _check(lib.gcnn_grads_device(self._h, ctypes.byref(p)))
+        return _wrap_device(p.value, self.n_params, torch.float32)
 
     def save(self, path: str) -> None:
         _check(lib.gcnn_save(self._h, path.encode()))

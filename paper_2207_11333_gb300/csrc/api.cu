@@ -114,6 +114,8 @@ void destroy_ctx(gcnn_ctx *c) {
     if (c->stage_ev[q]) cudaEventDestroy(c->stage_ev[q]);
   }
   if (c->lr_pinned) cudaFreeHost(c->lr_pinned);
+  if (c->scale_pinned) cudaFreeHost(c->scale_pinned);
+  for (cudaEvent_t e : c->grad_ev) cudaEventDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->opt) cudaStreamDestroy(c->opt);
@@ -274,7 +276,7 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   Carve cv;
   const size_t o_params = cv.take<float>(c->P), o_grads = cv.take<float>(c->P);
   const size_t o_m = cv.take<float>(c->P), o_v = cv.take<float>(c->P);
-  const size_t o_opt = cv.take<int>(16), o_lr = cv.take<float>(4);
+  const size_t o_opt = cv.take<int>(16), o_lr = cv.take<float>(4), o_ls = cv.take<float>(4);
   const size_t o_tab = cv.take<float>(2 * (kMaxGraphEdges + 1)), o_err = cv.take<unsigned>(4);
   const size_t o_node_off = cv.take<int>(Gc + 1), o_edge_off = cv.take<int>(Gc + 1);
   const size_t o_gid = cv.take<int>(Nc), o_rp = cv.take<int>(Nc + 1), o_col = cv.take<int>(Ec);
@@ -317,7 +319,7 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   char *b = c->dmem;
   c->params = (float *)(b + o_params); c->grads = (float *)(b + o_grads);
   c->adam_m = (float *)(b + o_m); c->adam_v = (float *)(b + o_v);
-  c->opt_state = (int *)(b + o_opt); c->lr_dev = (float *)(b + o_lr);
+  c->opt_state = (int *)(b + o_opt); c->lr_dev = (float *)(b + o_lr); c->loss_scale = (float *)(b + o_ls);
   c->scal_tab = (float *)(b + o_tab); c->err = (unsigned *)(b + o_err);
   c->bb.node_off = (int *)(b + o_node_off); c->bb.edge_off = (int *)(b + o_edge_off);
   c->bb.graph_id = (int *)(b + o_gid); c->bb.row_ptr = (int *)(b + o_rp); c->bb.col = (int *)(b + o_col);
@@ -376,8 +378,21 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
         c->side_ev.push_back(ev);
     }
   }
-  if (rc == GCNN_OK && cudaMallocHost(&c->lr_pinned, sizeof(float)) != cudaSuccess)
+  if (rc == GCNN_OK && (cudaMallocHost(&c->lr_pinned, sizeof(float)) != cudaSuccess ||
+                        cudaMallocHost(&c->scale_pinned, 2 * sizeof(float)) != cudaSuccess))
     rc = set_error(GCNN_ENOMEM, "cannot allocate pinned memory");
+  if (rc == GCNN_OK) {  // loss-gradient scales start at 1 (a single process)
+    const float one[2] = {1.f, 1.f};
+    if (cudaMemcpy(c->loss_scale, one, sizeof(one), cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = set_error(GCNN_ECUDA, "cannot initialise the loss scale");
+  }
+  for (int q = 0; q <= c->L && rc == GCNN_OK; ++q) {  // gradient buckets' completion events
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+      rc = set_error(GCNN_ECUDA, "cannot create events");
+    else
+      c->grad_ev.push_back(ev);
+  }
   if (rc == GCNN_OK) rc = make_scaler_table(c);
   if (rc == GCNN_OK) (void)num_sms();  // cache the SM count outside any capture
   if (rc != GCNN_OK) {
@@ -568,6 +583,60 @@ int gcnn_backward(gcnn_ctx *c, const gcnn_batch *b, const float *dpred, double *
   if (!c->have_fwd || c->fwd_G != b->n_graphs || c->fwd_N != b->n_nodes)
     return set_error(GCNN_ESTATE, "backward needs a forward(train=1) on the same batch");
   return ctx_backward(c, b->n_graphs, grid_nodes(c, b), grid_edges(c, b), dpred, loss_accum);
+}
+
+int gcnn_set_loss_scale(gcnn_ctx *c, float graph_scale, float node_scale) {
+  if (!c) return set_error(GCNN_EINVAL, "null context");
+  if (!std::isfinite(graph_scale) || !std::isfinite(node_scale) || graph_scale < 0.f || node_scale < 0.f)
+    return set_error(GCNN_EINVAL, "loss scales must be finite and >= 0");
+  if (graph_scale != c->scale_host[0] || node_scale != c->scale_host[1]) {
+    c->scale_pinned[0] = graph_scale;
+    c->scale_pinned[1] = node_scale;
+    GCNN_CUDA_TRY(cudaMemcpyAsync(c->loss_scale, c->scale_pinned, 2 * sizeof(float), cudaMemcpyHostToDevice,
+                                  c->stream));
+    // the pinned source must stay valid until the copy ran
+    GCNN_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->scale_host[0] = graph_scale;
+    c->scale_host[1] = node_scale;
+  }
+  return GCNN_OK;
+}
+
+int gcnn_grad_buckets(const gcnn_ctx *c, int32_t *n_buckets) {
+  if (!c || !n_buckets) return set_error(GCNN_EINVAL, "null argument");
+  *n_buckets = c->L + 2;
+  return GCNN_OK;
+}
+
+int gcnn_grad_bucket(const gcnn_ctx *c, int32_t k, int64_t *offset, int64_t *count) {
+  if (!c || !offset || !count) return set_error(GCNN_EINVAL, "null argument");
+  const int64_t lb = (int64_t)c->T * c->H, le = lb + (int64_t)c->L * c->layer_size;
+  if (k >= 0 && k < c->L) {
+    *offset = lb + (int64_t)k * c->layer_size;
+    *count = c->layer_size;
+  } else if (k == c->L) {
+    *offset = le;
+    *count = c->P - le;
+  } else if (k == c->L + 1) {
+    *offset = 0;
+    *count = lb;
+  } else {
+    return set_error(GCNN_EINVAL, "bucket %d out of range 0..%d", k, c->L + 1);
+  }
+  return GCNN_OK;
+}
+
+int gcnn_grad_wait(gcnn_ctx *c, int32_t k, void *stream) {
+  if (!c) return set_error(GCNN_EINVAL, "null context");
+  if (k < 0 || k > c->L + 1) return set_error(GCNN_EINVAL, "bucket %d out of range 0..%d", k, c->L + 1);
+  GCNN_CUDA_TRY(cudaStreamWaitEvent(static_cast<cudaStream_t>(stream), c->grad_ev[std::min(k, c->L)], 0));
+  return GCNN_OK;
+}
+
+int gcnn_grads_device(gcnn_ctx *c, float **grads) {
+  if (!c || !grads) return set_error(GCNN_EINVAL, "null argument");
+  *grads = c->grads;
+  return GCNN_OK;
 }
 
 int gcnn_step(gcnn_ctx *c, float lr) {

@@ -28,6 +28,8 @@ struct gcnn_ctx {
   float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
   int *opt_state = nullptr;  // [0] step, [1..2] bias-correction factors (float bits)
   float *lr_dev = nullptr;
+  float *loss_scale = nullptr;  // [0] graph-level, [1] node-level loss-gradient scale (1, 1)
+  std::vector<cudaEvent_t> grad_ev;  // L + 1: layer l's gradients final; [L]: every gradient
   float *scal_tab = nullptr;  // 2 * (kMaxGraphEdges + 1)
   unsigned *err = nullptr;
 
@@ -72,6 +74,8 @@ struct gcnn_ctx {
   int fwd_G = 0, fwd_N = 0, fwd_E = 0;
   float lr_host = -1.f;
   float *lr_pinned = nullptr;
+  float scale_host[2] = {1.f, 1.f};
+  float *scale_pinned = nullptr;  // 2 floats
   struct ProfEvent {
     int phase;
     cudaEvent_t a, b;

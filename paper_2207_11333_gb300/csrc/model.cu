@@ -78,6 +78,7 @@ HeadArgs head_args(gcnn_ctx *c, int G, const float *dpred_in) {
     a.h = xs_at(c, c->L); a.amp = c->bb.amp; a.att = c->bb.att;
   }
   a.dx_add = c->cfg.node_head ? c->dxn : nullptr;  // formed by the forward (train)
+  a.loss_scale = c->loss_scale;
   return a;
 }
 
@@ -89,7 +90,18 @@ NodeHeadArgs node_args(gcnn_ctx *c, int Ngrid) {
   a.zn = c->zn; a.w2n = w + HHh + c->Hh; a.b2n = w + HHh + 2 * c->Hh; a.y = c->bb.ynode;
   a.pred = c->predn; a.dpred = c->dpredn; a.dzn = c->dzn;
   a.weight = (float)c->cfg.node_loss_weight;
+  a.loss_scale = c->loss_scale + 1;
   return a;
+}
+
+// Record that the gradients of bucket k (layer k, or every gradient for
+// k = L) are final once the work queued so far on stream s has run, for
+// callers that start their exchange of a bucket early (gcnn_grad_wait).  Not
+// while a train step is being captured: its graph runs AdamW itself.
+int mark_grads_ready(gcnn_ctx *c, int k, cudaStream_t s) {
+  if (c->capturing || k < 0 || k >= (int)c->grad_ev.size()) return GCNN_OK;
+  GCNN_CUDA_TRY(cudaEventRecord(c->grad_ev[k], s));
+  return GCNN_OK;
 }
 
 int gemm(gcnn_ctx *c, const GemmDesc &d) {
@@ -194,7 +206,7 @@ bool layers_updated_early(const gcnn_ctx *c) { return c->fuse_step && bf16(c) &&
 int adam(gcnn_ctx *c, AdamSpan sp, bool advance, int max_blocks, cudaStream_t s) {
   const AdamPack pk{c->H, c->L, (long long)c->T * c->H, (long long)c->layer_size};
   return launch_adam(sp, advance, max_blocks, c->params, c->grads, c->adam_m, c->adam_v, c->opt_state, c->tickets,
-                     c->lr_dev, (float)c->cfg.beta1, (float)c->cfg.beta2, (float)c->cfg.adam_eps,
+                     c->lr_dev, c->cfg.beta1, c->cfg.beta2, (float)c->cfg.adam_eps,
                      (float)c->cfg.weight_decay, c->wb, c->wpack, pk, s);
 }
 
@@ -390,6 +402,7 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
     GCNN_CUDA_TRY(cudaEventRecord(done, lane.s));
     if (l + 1 < c->L) GCNN_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->side_ev[3 * (l + 1) + 2], 0));
   }
+  GCNN_TRY(mark_grads_ready(c, l, lane.s));
   {  // dx = [g | dP | dQ] [W_x | A | B]^T ; the next layer's masked, scaled BF16 gradient
     TcDesc d = tblank();
     d.M = Ngrid; d.N = H; d.K = pad64(3 * H); d.node_dim = kNodeM;
@@ -576,6 +589,7 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
       d.C = gw.msg_w; d.ldc = 2 * H; d.last_row_cols = H;
       GCNN_TRY(gemm(c, d));
     }
+    GCNN_TRY(mark_grads_ready(c, l, c->stream));
     // dx = (dh * [h > 0]) W_x^T + [dP | dQ] [A | B]^T
     {
       GemmDesc d = blank();
@@ -597,7 +611,7 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
   GCNN_TRY(launch_embed_bwd(Ngrid, H, dims, c->bb.types, c->dH, c->T, c->grads, c->stream));
   // the third stream's updates join before the step's final one
   if (bf16(c) && layers_updated_early(c)) GCNN_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->opt_ev, 0));
-  return GCNN_OK;
+  return mark_grads_ready(c, c->L, c->stream);  // every gradient is final here
 }
 
 int ctx_step(gcnn_ctx *c) {
