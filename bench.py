@@ -159,6 +159,24 @@ def oracle_graphs_per_s(path: str, order: np.ndarray, budget_s: float):
                       f"FP64 collation + fwd + bwd + AdamW each, {t:.1f} s, OpenMP over nodes on {cores} host cores"}
 
 
+def oracle_single_thread(path: str, order: np.ndarray, budget_s: float):
+    """The same oracle timing on one host thread: a child process with
+    OMP_NUM_THREADS=1 (the OpenMP runtime reads it when the oracle loads)."""
+    np.save(os.path.join(os.path.dirname(path), "order.npy"), order[:4096])
+    code = ("import json, sys, numpy as np; sys.path.insert(0, %r); import bench; "
+            "o = np.load(%r); print(json.dumps(bench.oracle_graphs_per_s(%r, o, %r)))"
+            % (ROOT, os.path.join(os.path.dirname(path), "order.npy"), path, budget_s))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=budget_s * 4 + 120)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["cores"] = 1
+    out["sample"] = out["sample"].replace(f"on {len(os.sched_getaffinity(0))} host cores", "on 1 host thread")
+    return out
+
+
 def run_reference(args):
     """Reference arm: the FP64 oracle on the host cores, bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -240,10 +258,15 @@ def measured_peaks():
 
 
 class Workload:
-    """The 200k-graph store (device-resident), its teacher targets, the epoch order, capacities."""
+    """The 200k-graph store (device-resident), its teacher targets, the epoch order, capacities.
 
-    def __init__(self, g, rank: int, world: int = 1):
+    One process: the seeded epoch order in batches of 128.  Data parallel (ddp):
+    the package's ShardedSampler over the same graphs, 128 per process and step,
+    and capacities that cover every process's share."""
+
+    def __init__(self, g, rank: int, world: int = 1, ddp: bool = False):
         gs = dataset()
+        self.counts = np.diff(gs.node_ptr)[:N_TRAIN]
         self.tmp = tempfile.mkdtemp(prefix="gcnn_bench_")
         self.path = os.path.join(self.tmp, "train.gcnn")
         synth.write_store(self.path, gs)
@@ -252,11 +275,19 @@ class Workload:
         self.delta = self.st.delta(np.arange(N_TRAIN))
         self.y = make_targets(g, self.st, self.delta, N_TRAIN + N_HELDOUT)
         self.st.set_targets(self.y)
-        # replicas take disjoint shards of one seeded epoch order
-        self.order = np.ascontiguousarray(epoch_order(0)[rank::world])
+        self.sampler = None
+        if ddp:
+            from paper_2207_11333_gb300.ddp import ShardedSampler
+            self.sampler = ShardedSampler(N_TRAIN, BATCH, world, rank, SEED_ORDER, node_counts=self.counts)
+            shards = [self.sampler.shard(k).ids for k in range(len(self.sampler))]
+            self.order = np.concatenate(shards)
+            sizes = [self.st.batch_size(ids) for ids in shards]
+        else:
+            self.order = np.ascontiguousarray(epoch_order(0))
         self.n_train = len(self.order)
         self.nb = (self.n_train + BATCH - 1) // BATCH
-        sizes = [self.st.batch_size(self.order[i * BATCH:(i + 1) * BATCH]) for i in range(self.nb)]
+        if not ddp:
+            sizes = [self.st.batch_size(self.order[i * BATCH:(i + 1) * BATCH]) for i in range(self.nb)]
         self.Nc = (max(s[0] for s in sizes) + 255) // 256 * 256
         self.Ec = (max(s[1] for s in sizes) + 511) // 512 * 512
 
@@ -312,19 +343,77 @@ def timed_steps(ctx, wl, steps, warmup, flush, loss_acc, dist=None, gpu_index=No
             "kernels_per_step": ctx.step_kernel_count() + 2}
 
 
+def timed_ddp_steps(g, ctx, wl, steps, warmup, flush, loss_acc, dist, gpu_index, store=None, e2e=False):
+    """Data-parallel steps (Sec. 4, Fig. 4) through the package's DataParallelTrainer:
+    per process its share of every global batch, collated from the store, the
+    loss gradient scaled by that share, the backward, each gradient bucket
+    all-reduced over NCCL as soon as it is final, then AdamW.  Device time per
+    step from CUDA events (L2 flushed between steps, outside the events), the
+    maximum over processes; with e2e, wall clock of the steps from a host store
+    with every step's loss read back to the host."""
+    import torch
+    from paper_2207_11333_gb300.ddp import DataParallelTrainer
+    tr = DataParallelTrainer(ctx, store or wl.st, wl.sampler)
+    n_steps = len(wl.sampler)
+    for k in range(warmup):
+        tr.step(k % n_steps, LR, loss_acc)
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_index) if (gpu_index is not None and not e2e) else None
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    pinned = torch.zeros(3, dtype=torch.float64).pin_memory()
+    graphs = h2d = 0
+    mine = []
+    t_wall = time.perf_counter()
+    for k in range(steps):
+        if not e2e:
+            flush.zero_()
+        evs[k][0].record()
+        sh = tr.step((warmup + k) % n_steps, LR, loss_acc)
+        evs[k][1].record()
+        if e2e:
+            pinned.copy_(loss_acc, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            assert math.isfinite(float(pinned[0]))
+            mine.append(sh.ids)
+        graphs += sum(sh.graphs)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    for ids in mine:        # bytes staged and copied per step: offsets, targets, types, local edges
+        n_atoms, n_edges = wl.st.batch_size(ids)
+        h2d += 16 * (len(ids) + 1) + 4 * len(ids) + n_atoms + 2 * n_edges
+    clocks = sampler.stop() if sampler else None
+    dev_s = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+    t = torch.tensor([dev_s, wall], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_s, wall = float(t[0]), float(t[1])
+    out = {"value": graphs / (wall if e2e else dev_s), "dev_s": dev_s, "graphs": float(graphs), "wall_s": wall,
+           "clocks": clocks, "h2d_bytes_per_step": h2d / steps}
+    # kernels per step from the library's kernel timeline over one more step
+    ctx.timeline_enable(4096)
+    ctx.timeline_read()
+    tr.step(0, LR, loss_acc)
+    torch.cuda.synchronize()
+    ids, _ = ctx.timeline_read()
+    ctx.timeline_enable(0)
+    out["kernels_per_step"] = len(ids)
+    return out
+
+
 def gemm_traffic():
-    """DRAM bytes per GEMM launch from the committed ncu summary, or None when
-    the GEMM kernel's source has changed since those counters were taken."""
+    """DRAM bytes per GEMM launch from the committed ncu record
+    (profiles/tma_gemm_bf16_train_step_200k.json), or None when the GEMM
+    kernel's source has changed since those counters were taken."""
     import hashlib
-    import re
     try:
-        with open(os.path.join(ROOT, "profiles", "tma_gemm_bf16_train_step_200k.md")) as f:
-            m = re.search(r"bench: kernel=tma_gemm source_sha256=([0-9a-f]{64}) dram_bytes_per_launch=(\d+)", f.read())
-        with open(os.path.join(ROOT, "paper_2207_11333_gb300", "csrc", "gemm_tc.cu"), "rb") as f:
+        with open(os.path.join(ROOT, "profiles", "tma_gemm_bf16_train_step_200k.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
             src = hashlib.sha256(f.read()).hexdigest()
-    except OSError:
+    except (OSError, ValueError, KeyError):
         return None
-    return float(m.group(2)) if m and m.group(1) == src else None
+    return float(rec["dram_bytes_per_launch"]) if rec.get("source_sha256") == src else None
 
 
 def kernel_profile(g, wl, n_steps, warmup, flush, loss_acc, precision):
@@ -824,12 +913,19 @@ def run_ours(args):
     torch.cuda.set_device(local)
     import paper_2207_11333_gb300 as g
 
+    ddp = world > 1 or args.ddp
+    if ddp and dist is None:    # --ddp at one process: the data-parallel path in a group of one
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{os.environ.get('MASTER_PORT', '29533')}",
+                                rank=0, world_size=1)
     t_setup = time.perf_counter()
-    wl = Workload(g, rank, world)
+    wl = Workload(g, rank, world, ddp)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > 129 MB L2
     loss_acc = torch.zeros(3, dtype=torch.float64, device="cuda")
     log(f"[bench] setup {time.perf_counter() - t_setup:.1f}s, capacity N={wl.Nc} E={wl.Ec}, delta={wl.delta:.6f}")
 
+    if ddp:
+        return run_ddp(g, wl, args, world, rank, local, dist, flush, loss_acc)
     ctx = make_ctx(g, wl, args.precision)
     r = timed_steps(ctx, wl, args.steps, args.warmup, flush, loss_acc, dist, local)
     line = {"metric": METRIC, "value": r["value"], "unit": "graphs/s", "n_gpus": world, "steps": args.steps,
@@ -888,6 +984,7 @@ def run_ours(args):
         try:
             os.environ.setdefault("OMP_NUM_THREADS", str(len(os.sched_getaffinity(0))))
             line["cpu_baseline"] = oracle_graphs_per_s(wl.path, wl.order, budget_s=args.cpu_seconds)
+            line["cpu_baseline"]["single_thread"] = oracle_single_thread(wl.path, wl.order, args.cpu_seconds / 2)
         except Exception as e:  # noqa: BLE001
             line["cpu_baseline"] = {"error": repr(e)}
     if rank == 0:
@@ -895,6 +992,44 @@ def run_ours(args):
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+    return 0
+
+
+def run_ddp(g, wl, args, world, rank, local, dist, flush, loss_acc):
+    """The bench line of the data-parallel step: world processes, one GPU each,
+    128 graphs per process and step, gradients all-reduced every step."""
+    import torch
+    prec = g.PREC_BF16 if args.precision == "bf16" else g.PREC_FP32
+    ctx = g.Context(g.make_config(H, L, BATCH, wl.Nc, wl.Ec, delta=wl.delta, precision=prec))
+    ctx.set_params(synth.init_params(SEED_STUDENT, H, L))
+    r = timed_ddp_steps(g, ctx, wl, args.steps, args.warmup, flush, loss_acc, dist, local)
+    line = {"metric": METRIC, "value": r["value"], "unit": "graphs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * r["dev_s"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.precision == "bf16" else "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "graphs": N_TRAIN, "batch_graphs_per_gpu": BATCH, "hidden": H,
+                       "layers": L, "head": "200-200-1", "precision": args.precision,
+                       "parallelism": f"ddp x{world}: gradient all-reduce (NCCL) per layer bucket, overlapped "
+                                      "with the backward; eager launches (no captured graph)",
+                       "l2": "256 MB buffer written between steps, outside the per-step CUDA events",
+                       "wall_ms_per_step_incl_flush": 1e3 * r["wall_s"] / args.steps},
+            "clocks": r["clocks"], "gpu_launches": r["kernels_per_step"] * args.steps}
+    if not args.no_e2e:
+        try:
+            sh = g.Store(wl.path)           # host-resident twin: pinned staging + H2D per step
+            sh.set_targets(wl.y)
+            e = timed_ddp_steps(g, ctx, wl, args.steps, args.warmup, flush, loss_acc, dist, None, store=sh, e2e=True)
+            line["e2e"] = {"value": e["value"], "unit": "graphs/s", "h2d_bytes_per_step": e["h2d_bytes_per_step"],
+                           "d2h_bytes_per_step": 24,
+                           "path": "DataParallelTrainer from a host store; every step's loss read back"}
+        except Exception as ex:  # noqa: BLE001
+            line["e2e"] = {"error": repr(ex)}
+    ctx.check()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.barrier()
+    dist.destroy_process_group()
     return 0
 
 
@@ -909,6 +1044,8 @@ def main():
     ap.add_argument("--compare", choices=["none", "fp32", "bf16"], default="fp32",
                     help="also time this path on the same workload (default: the plain FP32 path)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ddp", action="store_true",
+                    help="data-parallel steps (gradient all-reduce) also at one GPU; always on for N > 1")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=150.0,
