@@ -814,12 +814,13 @@ def serve_rates(g, model_ctx, pool, rates, seconds, precision):
     prec = g.PREC_BF16 if precision == "bf16" else g.PREC_FP32
     srv = g.Server(model_ctx, n_slots=4, buckets=(1024, 4096, 16384, 65536), max_graphs=4096, precision=prec,
                    queue_nodes=1 << 22)
-    warm = srv.submit(*g.request_arrays(pool, 0, 4096))   # captures the bucket graphs
+    warm = srv.submit(*g.request_arrays(pool, 0, 4096))   # every bucket's graph is captured at creation
     srv.wait(warm)
     for b in (1, 60, 300):
         srv.wait(srv.submit(*g.request_arrays(pool, 0, b)))
     out = []
     for r_i, lam in enumerate(rates):
+        tm0 = srv.timing()
         t_arr, size, start = arrival_schedule(lam, seconds, pool.n_graphs, SEED_SERVE + r_i)
         pending, lat, mols, refused = [], [], 0, 0
         i = 0
@@ -847,7 +848,18 @@ def serve_rates(g, model_ctx, pool, rates, seconds, precision):
             if not still and i < len(t_arr):
                 time.sleep(max(0.0, min(0.001, t_arr[i] - (time.perf_counter() - t0))))
         elapsed = time.perf_counter() - t0
-        out.append(summarize(lat, mols, elapsed, len(t_arr), refused, lam))
+        res = summarize(lat, mols, elapsed, len(t_arr), refused, lam)
+        tm1 = srv.timing()
+        nb = max(1, tm1["batches"] - tm0["batches"])
+        res["batches"] = tm1["batches"] - tm0["batches"]
+        res["atoms_per_batch"] = (tm1["atoms"] - tm0["atoms"]) / nb
+        res["scheduler_us_per_batch"] = (tm1["host_us"] - tm0["host_us"]) / nb
+        res["device_us_per_batch"] = (tm1["device_us"] - tm0["device_us"]) / nb
+        # fraction of the wall time the scheduler thread spent forming and
+        # launching batches, and the mean number of batches on the device
+        res["scheduler_busy"] = (tm1["host_us"] - tm0["host_us"]) / (1e6 * elapsed)
+        res["device_batches_in_flight"] = (tm1["device_us"] - tm0["device_us"]) / (1e6 * elapsed)
+        out.append(res)
     stats = srv.stats()
     srv.close()
     return out, stats
@@ -893,12 +905,33 @@ def run_serving(g, model_ctx, delta, params, args):
     synth.write_store(path, pool)
     rates = [float(x) for x in args.serve_rates.split(",")]
     res, stats = serve_rates(g, model_ctx, pool, rates, args.serve_seconds, args.precision)
-    base = baseline_rates(g, params, delta, path, pool, rates, args.serve_seconds)
+    base_s = min(args.serve_seconds, args.baseline_seconds)
+    base = baseline_rates(g, params, delta, path, pool, rates, base_s)
     return {"workload": "Poisson arrivals; 1-4096 molecules per request (log-uniform), 5-80 atoms each; "
-                        f"{args.serve_seconds:g} s per rate",
+                        f"{args.serve_seconds:g} s per rate (baseline {base_s:g} s per rate)",
             "server": {"precision": args.precision, "slots": 4, "buckets_nodes": [1024, 4096, 16384, 65536],
                        "rates": res, "totals": stats},
             "baseline_fp32_one_request_per_launch": {"rates": base}}
+
+
+def serving_study(args):
+    """The serving configuration alone: a student trained for a few hundred steps
+    of the training workload serves Poisson traffic at every rate of
+    --serve-rates for --serve-seconds each, beside the FP32 one-request-per-launch
+    path; one JSON line."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_2207_11333_gb300 as g
+    wl = Workload(g, 0, 1)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    loss_acc = torch.zeros(3, dtype=torch.float64, device="cuda")
+    ctx = make_ctx(g, wl, args.precision)
+    timed_steps(ctx, wl, args.steps, args.warmup, flush, loss_acc)
+    trained = ctx.get_params()
+    out = run_serving(g, ctx, wl.delta, trained, args)
+    ctx.close()
+    print(json.dumps({"study": "serving", "trained_steps": args.steps + args.warmup, **out}), flush=True)
+    return 0
 
 
 def run_ours(args):
@@ -1052,8 +1085,10 @@ def main():
                     help="host-time budget of the reference arm's warm-up and timed steps")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="seconds of Poisson load per arrival rate for the serving measurement (0: skip)")
-    ap.add_argument("--serve-rates", default="200,1000,2000", help="arrival rates, requests/s")
-    ap.add_argument("--study", choices=["none", "precision", "aggregate", "loading"], default="none",
+    ap.add_argument("--serve-rates", default="50,200,500,1000,2000", help="arrival rates, requests/s")
+    ap.add_argument("--baseline-seconds", type=float, default=20.0,
+                    help="seconds per rate of the one-request-per-launch FP32 baseline (at most --serve-seconds)")
+    ap.add_argument("--study", choices=["none", "precision", "aggregate", "loading", "serving"], default="none",
                     help="precision: train FP32 and BF16 for --epochs and compare held-out MAE; aggregate: the "
                          "aggregation operators alone on --molecules molecules, --reps timed launches each "
                          "(no bench line)")
@@ -1080,6 +1115,8 @@ def main():
         import paper_2207_11333_gb300 as g
         print(json.dumps({"study": "loading", **loading_study(g)}), flush=True)
         return 0
+    if args.study == "serving":
+        return serving_study(args)
     if args.study == "aggregate":
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

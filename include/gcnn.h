@@ -446,8 +446,8 @@ typedef struct gcnn_request {
 } gcnn_request;
 
 /* Create a server for the model in `model` (its current parameters are copied
- * to every slot; later changes to `model` are not seen).  Starts the
- * scheduler thread.  Requests carry no bond features: a model with
+ * to every slot; later changes to `model` are not seen).  Captures every
+ * slot's forward graph for every bucket, then starts the scheduler thread.  Requests carry no bond features: a model with
  * edge_features > 0 is refused (GCNN_EINVAL). */
 int gcnn_serve_create(const gcnn_ctx *model, const gcnn_serve_config *cfg, gcnn_server **out);
 /* Queue a request (the library copies it; the caller may free it on return).
@@ -464,6 +464,13 @@ int gcnn_serve_wait(gcnn_server *srv, uint64_t ticket, float *out, double *laten
  * submissions refused. */
 int gcnn_serve_stats(gcnn_server *srv, int64_t *requests, int64_t *molecules, int64_t *batches,
                      int64_t *refused);
+/* Time spent since creation, summed over batches: host_us, the scheduler's
+ * time forming and launching batches (packing, copies, graph launches);
+ * device_us, each batch's device time from its input copy to its output copy
+ * (batches on different slots overlap, so this can exceed wall time); atoms,
+ * the batches' atoms; batches, their number.  Measurement support: it says
+ * whether the host or the device limits a saturated server. */
+int gcnn_serve_timing(gcnn_server *srv, double *host_us, double *device_us, double *atoms, int64_t *batches);
 /* Stop the scheduler (finishing batches in flight) and free everything. */
 int gcnn_serve_destroy(gcnn_server *srv);
 

@@ -127,6 +127,7 @@ def _load() -> ctypes.CDLL:
         "gcnn_serve_wait": (i32, [vp, ctypes.c_uint64, vp, P(f64), i64]),
         "gcnn_serve_stats": (i32, [vp, P(i64), P(i64), P(i64), P(i64)]),
         "gcnn_serve_destroy": (i32, [vp]),
+        "gcnn_serve_timing": (i32, [vp, P(f64), P(f64), P(f64), P(i64)]),
         "gcnn_op_aggregate_fwd": (i32, [i32, i32, vp, vp, vp, vp, f32, vp]),
         "gcnn_op_aggregate_bwd": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, f32, vp]),
         "gcnn_op_aggregate_bwd_graphs": (i32, [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, f32, vp]),
@@ -588,6 +589,12 @@ class Server:
         v = [ctypes.c_int64() for _ in range(4)]
         _check(lib.gcnn_serve_stats(self._h, *[ctypes.byref(x) for x in v]))
         return dict(zip(("requests", "molecules", "batches", "refused"), (x.value for x in v)))
+
+    def timing(self) -> dict:
+        """Host scheduler time, device time and atoms summed over batches (gcnn_serve_timing)."""
+        h, d, a, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        _check(lib.gcnn_serve_timing(self._h, ctypes.byref(h), ctypes.byref(d), ctypes.byref(a), ctypes.byref(n)))
+        return {"host_us": h.value, "device_us": d.value, "atoms": a.value, "batches": n.value}
 
     def close(self) -> None:
         if self._h:

@@ -11,9 +11,10 @@
 //     across batches) up to the largest bucket and the slot's molecule and
 //     edge capacities, picks the smallest bucket that fits, writes the batch
 //     as a packed mini-store into pinned memory, and enqueues on its own
-//     stream: one host-to-device copy, the device collator, the captured
-//     forward graph of that bucket, and one device-to-host copy of the
-//     predictions, followed by its completion event.
+//     stream: one host-to-device copy, the device collator, the forward graph
+//     of that bucket (captured for every slot and bucket at creation), and one
+//     device-to-host copy of the predictions, followed by its completion
+//     event.
 // Slots run with GCNN_FLAG_ROW_INVARIANT, so results do not depend on which
 // molecules share a batch.
 #include <algorithm>
@@ -57,12 +58,13 @@ struct Piece {
 struct Slot {
   gcnn_ctx *ctx = nullptr;
   cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t start = nullptr, done = nullptr;  // around the batch's device work (timed)
   float *pin_out = nullptr;
   bool busy = false;
   std::vector<Piece> pieces;
   int graphs = 0;
-  std::vector<cudaGraphExec_t> exec;  // per bucket, captured lazily
+  int64_t atoms = 0;
+  std::vector<cudaGraphExec_t> exec;  // per bucket, captured at creation
 };
 
 }  // namespace
@@ -81,6 +83,9 @@ struct gcnn_server {
   int fatal = GCNN_OK;
   char fatal_msg[256] = "";
   int64_t n_requests = 0, n_molecules = 0, n_batches = 0, n_refused = 0;
+  // scheduler time forming and launching batches (host), device time from the
+  // batch's input copy to its output copy, and atoms, summed over batches
+  double host_us = 0.0, device_us = 0.0, atoms = 0.0;
   std::thread worker;
   int device = 0;
 };
@@ -154,12 +159,19 @@ void form_batch(gcnn_server *s, Slot &sl, int64_t *nodes, int64_t *edges) {
   *edges = E;
 }
 
+// Edge grid of bucket b: the slot's edge capacity in proportion to the
+// bucket's node capacity (at least 512)
+int bucket_edges(const gcnn_server *s, const gcnn_ctx *c, int b) {
+  const int64_t top = s->cfg.bucket_nodes[s->cfg.n_buckets - 1];
+  const int Eg = std::min(c->Ec, (int)((int64_t)s->cfg.bucket_nodes[b] * s->max_edges / top + 512));
+  return std::max(Eg, 512);
+}
+
 int launch_batch(gcnn_server *s, Slot &sl, int64_t N, int64_t E) {
   gcnn_ctx *c = sl.ctx;
   const int G = sl.graphs;
   int b = 0;
   while (b < s->cfg.n_buckets - 1 && s->cfg.bucket_nodes[b] < N) ++b;
-  const int Ng = s->cfg.bucket_nodes[b];
   // packed mini-store in the slot context's pinned staging buffer (free: the
   // slot's previous batch has completed)
   char *h = c->stage_host[0];
@@ -186,20 +198,18 @@ int launch_batch(gcnn_server *s, Slot &sl, int64_t N, int64_t E) {
       ep[g + 1] = ep[g] + r->n_edges[m];
     }
   }
+  GCNN_CUDA_TRY(cudaEventRecord(sl.start, sl.stream));
   GCNN_CUDA_TRY(cudaMemcpyAsync(c->stage_dev, h, o, cudaMemcpyHostToDevice, sl.stream));
   const char *d = c->stage_dev;
   StoreView v{reinterpret_cast<const int64_t *>(d + o_np), reinterpret_cast<const int64_t *>(d + o_ep),
               reinterpret_cast<const uint8_t *>(d + o_t), reinterpret_cast<const uint8_t *>(d + o_e),
               reinterpret_cast<const float *>(d + o_y)};
   GCNN_TRY(launch_collate(G, nullptr, v, c->bb, c->scal_tab, c->Nc, c->Ec, c->err, sl.stream));
-  if (!sl.exec[b]) {
-    const int Eg = std::min(c->Ec, (int)((int64_t)Ng * s->max_edges / s->cfg.bucket_nodes[s->cfg.n_buckets - 1] + 512));
-    GCNN_TRY(capture_forward(c, s->cfg.max_graphs, Ng, std::max(Eg, 512), &sl.exec[b]));
-  }
   GCNN_CUDA_TRY(cudaGraphLaunch(sl.exec[b], sl.stream));
   GCNN_CUDA_TRY(cudaMemcpyAsync(sl.pin_out, c->pred, sizeof(float) * G, cudaMemcpyDeviceToHost, sl.stream));
   GCNN_CUDA_TRY(cudaEventRecord(sl.done, sl.stream));
   sl.busy = true;
+  sl.atoms = N;
   return GCNN_OK;
 }
 
@@ -221,6 +231,9 @@ void retire(gcnn_server *s, Slot &sl) {
   sl.pieces.clear();
   sl.busy = false;
   s->n_batches += 1;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, sl.start, sl.done) == cudaSuccess) s->device_us += 1e3 * ms;
+  s->atoms += (double)sl.atoms;
   s->done_cv.notify_all();
 }
 
@@ -252,7 +265,13 @@ void worker_loop(gcnn_server *s) {
         form_batch(s, sl, &N, &E);
       }
       if (sl.graphs == 0) break;
+      const auto t0 = Clock::now();
       const int rc = launch_batch(s, sl, N, E);
+      const double us = std::chrono::duration<double, std::micro>(Clock::now() - t0).count();
+      {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->host_us += us;
+      }
       progressed = true;
       if (rc != GCNN_OK) {
         std::lock_guard<std::mutex> lock(s->mu);
@@ -306,6 +325,7 @@ void destroy_server(gcnn_server *s) {
     for (auto e : sl.exec)
       if (e) cudaGraphExecDestroy(e);
     if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.start) cudaEventDestroy(sl.start);
     if (sl.pin_out) cudaFreeHost(sl.pin_out);
     if (sl.ctx) gcnn_destroy(sl.ctx);
     if (sl.stream) cudaStreamDestroy(sl.stream);
@@ -347,7 +367,7 @@ int gcnn_serve_create(const gcnn_ctx *model, const gcnn_serve_config *cfg, gcnn_
   int rc = GCNN_OK;
   for (Slot &sl : s->slots) {
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&sl.done) != cudaSuccess || cudaEventCreate(&sl.start) != cudaSuccess ||
         cudaMallocHost(&sl.pin_out, sizeof(float) * cfg->max_graphs) != cudaSuccess) {
       rc = set_error(GCNN_ENOMEM, "serve_create: stream / event / pinned allocation failed");
       break;
@@ -356,7 +376,12 @@ int gcnn_serve_create(const gcnn_ctx *model, const gcnn_serve_config *cfg, gcnn_
     if (rc != GCNN_OK) break;
     rc = gcnn_set_params(sl.ctx, model->params, sl.ctx->P, 1);
     if (rc != GCNN_OK) break;
+    // every bucket's forward graph is captured now, so that no request
+    // waits for a capture
     sl.exec.assign(cfg->n_buckets, nullptr);
+    for (int b = 0; b < cfg->n_buckets && rc == GCNN_OK; ++b)
+      rc = capture_forward(sl.ctx, cfg->max_graphs, cfg->bucket_nodes[b], bucket_edges(s, sl.ctx, b), &sl.exec[b]);
+    if (rc != GCNN_OK) break;
   }
   if (rc != GCNN_OK) {
     destroy_server(s);
@@ -446,6 +471,16 @@ int gcnn_serve_stats(gcnn_server *s, int64_t *requests, int64_t *molecules, int6
   if (molecules) *molecules = s->n_molecules;
   if (batches) *batches = s->n_batches;
   if (refused) *refused = s->n_refused;
+  return GCNN_OK;
+}
+
+int gcnn_serve_timing(gcnn_server *s, double *host_us, double *device_us, double *atoms, int64_t *batches) {
+  if (!s) return set_error(GCNN_EINVAL, "serve_timing: null server");
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (host_us) *host_us = s->host_us;
+  if (device_us) *device_us = s->device_us;
+  if (atoms) *atoms = s->atoms;
+  if (batches) *batches = s->n_batches;
   return GCNN_OK;
 }
 
