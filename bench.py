@@ -809,10 +809,10 @@ def summarize(lat_us, molecules, elapsed, offered, refused, lam):
             "p99_ms": pct(0.99), "elapsed_s": elapsed}
 
 
-def serve_rates(g, model_ctx, pool, rates, seconds, precision):
+def serve_rates(g, model_ctx, pool, rates, seconds, precision, slots=4):
     """Continuous-batching server under Poisson load."""
     prec = g.PREC_BF16 if precision == "bf16" else g.PREC_FP32
-    srv = g.Server(model_ctx, n_slots=4, buckets=(1024, 4096, 16384, 65536), max_graphs=4096, precision=prec,
+    srv = g.Server(model_ctx, n_slots=slots, buckets=(1024, 4096, 16384, 65536), max_graphs=4096, precision=prec,
                    queue_nodes=1 << 22)
     warm = srv.submit(*g.request_arrays(pool, 0, 4096))   # every bucket's graph is captured at creation
     srv.wait(warm)
@@ -904,12 +904,12 @@ def run_serving(g, model_ctx, delta, params, args):
     path = os.path.join(tmp, "pool.gcnn")
     synth.write_store(path, pool)
     rates = [float(x) for x in args.serve_rates.split(",")]
-    res, stats = serve_rates(g, model_ctx, pool, rates, args.serve_seconds, args.precision)
+    res, stats = serve_rates(g, model_ctx, pool, rates, args.serve_seconds, args.precision, args.serve_slots)
     base_s = min(args.serve_seconds, args.baseline_seconds)
     base = baseline_rates(g, params, delta, path, pool, rates, base_s)
     return {"workload": "Poisson arrivals; 1-4096 molecules per request (log-uniform), 5-80 atoms each; "
                         f"{args.serve_seconds:g} s per rate (baseline {base_s:g} s per rate)",
-            "server": {"precision": args.precision, "slots": 4, "buckets_nodes": [1024, 4096, 16384, 65536],
+            "server": {"precision": args.precision, "slots": args.serve_slots, "buckets_nodes": [1024, 4096, 16384, 65536],
                        "rates": res, "totals": stats},
             "baseline_fp32_one_request_per_launch": {"rates": base}}
 
@@ -1086,6 +1086,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="seconds of Poisson load per arrival rate for the serving measurement (0: skip)")
     ap.add_argument("--serve-rates", default="50,200,500,1000,2000", help="arrival rates, requests/s")
+    ap.add_argument("--serve-slots", type=int, default=4, help="server slots (batches in flight)")
     ap.add_argument("--baseline-seconds", type=float, default=20.0,
                     help="seconds per rate of the one-request-per-launch FP32 baseline (at most --serve-seconds)")
     ap.add_argument("--study", choices=["none", "precision", "aggregate", "loading", "serving"], default="none",

@@ -297,10 +297,11 @@ int gcnn_grad_buckets(const gcnn_ctx *ctx, int32_t *n_buckets);
 /* Float offset and count of bucket k in the flat gradient buffer. */
 int gcnn_grad_bucket(const gcnn_ctx *ctx, int32_t k, int64_t *offset, int64_t *count);
 /* Make `stream` (a caller's cudaStream_t) wait until bucket k's gradients of
- * the last gcnn_backward are final.  Layer buckets complete during the
- * backward, from the last layer to the first; buckets L and L + 1 when it
- * ends.  Valid after gcnn_backward, not after gcnn_train_step (whose graph
- * applies AdamW itself).  Enqueues a wait only; never blocks the host. */
+ * the last backward are final.  Layer buckets complete during the backward,
+ * from the last layer to the first; buckets L and L + 1 when it ends.  Valid
+ * after gcnn_backward, not after gcnn_train_step (whose graph
+ * applies AdamW itself); after gcnn_forward_backward too.  Enqueues a wait
+ * only; never blocks the host. */
 int gcnn_grad_wait(gcnn_ctx *ctx, int32_t k, void *stream);
 /* Device address of the flat FP32 gradient buffer (gcnn_param_count floats,
  * owned by the context, valid until gcnn_destroy).  A caller that reduces the
@@ -314,6 +315,13 @@ int gcnn_grads_device(gcnn_ctx *ctx, float **grads);
  * update on a third as soon as that layer's gradients are complete; the result
  * equals forward + backward + step bit for bit. */
 int gcnn_train_step(gcnn_ctx *ctx, const gcnn_batch *b, float lr, double *loss_accum);
+/* forward(train) + backward(MSE) without the optimizer step, replayed from a
+ * captured CUDA graph per batch graph count like gcnn_train_step: the first
+ * half of a data-parallel step.  The graph records the gradient buckets'
+ * completion events (gcnn_grad_wait works on them after this call returns);
+ * the caller exchanges the gradients and then calls gcnn_step.  Results equal
+ * gcnn_forward + gcnn_backward. */
+int gcnn_forward_backward(gcnn_ctx *ctx, const gcnn_batch *b, double *loss_accum);
 /* Copy x^l (l = 0..L, N x H floats) of the last forward to host.  Sync. */
 int gcnn_get_activation(gcnn_ctx *ctx, int32_t layer, float *dst, int64_t n);
 /* Copy the node-level predictions (Sec. 3.1 atom-level properties; N floats,

@@ -113,6 +113,7 @@ def _load() -> ctypes.CDLL:
         "gcnn_grad_wait": (i32, [vp, i32, vp]),
         "gcnn_grads_device": (i32, [vp, P(vp)]),
         "gcnn_train_step": (i32, [vp, P(BatchStruct), f32, vp]),
+        "gcnn_forward_backward": (i32, [vp, P(BatchStruct), vp]),
         "gcnn_get_activation": (i32, [vp, i32, vp, i64]),
         "gcnn_profile_enable": (i32, [vp, i32]),
         "gcnn_profile_read": (i32, [vp, vp, vp]),
@@ -432,6 +433,10 @@ class Context:
 
     def train_step(self, batch: Batch, lr: float, loss_accum=None) -> None:
         _check(lib.gcnn_train_step(self._h, ctypes.byref(batch.s), lr, _dev_ptr(loss_accum)))
+
+    def forward_backward(self, batch: Batch, loss_accum=None) -> None:
+        """Captured forward + backward without the optimizer (gcnn_forward_backward)."""
+        _check(lib.gcnn_forward_backward(self._h, ctypes.byref(batch.s), _dev_ptr(loss_accum)))
 
     def profile(self, enable: bool) -> None:
         _check(lib.gcnn_profile_enable(self._h, int(enable)))

@@ -645,15 +645,16 @@ int gcnn_step(gcnn_ctx *c, float lr) {
   return ctx_step(c);
 }
 
-int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_accum) {
-  if (!c) return set_error(GCNN_EINVAL, "null context");
-  GCNN_TRY(same_batch(c, b));
-  GCNN_TRY(set_lr(c, lr));
+namespace {
+// Replay (capturing it on first use) the graph of one training step on batch
+// b: forward + backward, followed by AdamW when with_step.  Without the step,
+// the backward's gradient-bucket events are external nodes of the graph.
+int run_step_graph(gcnn_ctx *c, const gcnn_batch *b, double *loss_accum, bool with_step) {
   const int G = b->n_graphs;
   const int Ng = grid_nodes(c, b), Eg = grid_edges(c, b);
   // with profiling on, a separate graph carries event-record nodes around
   // every phase; each of its replays is synchronised and accumulated
-  auto key = std::make_tuple(G, Ng, Eg, (const double *)loss_accum, c->prof_on);
+  auto key = std::make_tuple(G, Ng, Eg, (const double *)loss_accum, c->prof_on, with_step);
   auto it = c->graphs.find(key);
   if (it == c->graphs.end()) {
     // capture on the context's private stream (the legacy default stream
@@ -663,23 +664,26 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
     cudaStream_t user = c->stream;
     c->stream = c->cap_stream;
     c->capturing = true;
+    c->cap_grad_events = !with_step;
     c->cap_ev.clear();
     cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
       c->stream = user;
       c->capturing = false;
+      c->cap_grad_events = false;
       return set_error(GCNN_ECUDA, "begin capture: %s", cudaGetErrorString(e));
     }
     c->fuse_head = true;
-    c->fuse_step = true;
+    c->fuse_step = with_step;
     int rc = ctx_forward(c, G, Ng, Eg, true);
     if (rc == GCNN_OK) rc = ctx_backward(c, G, Ng, Eg, nullptr, loss_accum);
     c->fuse_head = false;
-    if (rc == GCNN_OK) rc = ctx_step(c);
+    if (rc == GCNN_OK && with_step) rc = ctx_step(c);
     c->fuse_step = false;
     e = cudaStreamEndCapture(c->stream, &graph);
     c->stream = user;
     c->capturing = false;
+    c->cap_grad_events = false;
     std::vector<gcnn_ctx::ProfEvent> ev;
     ev.swap(c->cap_ev);
     auto drop_events = [&ev] {
@@ -691,10 +695,12 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
     if (rc != GCNN_OK) {
       if (graph) cudaGraphDestroy(graph);
       drop_events();
+      cudaGetLastError();  // a failed capture must not fail later calls
       return rc;
     }
     if (e != cudaSuccess) {
       drop_events();
+      cudaGetLastError();
       return set_error(GCNN_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
     }
     size_t n_nodes = 0;
@@ -736,6 +742,20 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
   c->have_fwd = true;
   c->fwd_G = b->n_graphs; c->fwd_N = b->n_nodes; c->fwd_E = b->n_edges;
   return GCNN_OK;
+}
+}  // namespace
+
+int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_accum) {
+  if (!c) return set_error(GCNN_EINVAL, "null context");
+  GCNN_TRY(same_batch(c, b));
+  GCNN_TRY(set_lr(c, lr));
+  return run_step_graph(c, b, loss_accum, true);
+}
+
+int gcnn_forward_backward(gcnn_ctx *c, const gcnn_batch *b, double *loss_accum) {
+  if (!c) return set_error(GCNN_EINVAL, "null context");
+  GCNN_TRY(same_batch(c, b));
+  return run_step_graph(c, b, loss_accum, false);
 }
 
 int gcnn_get_activation(gcnn_ctx *c, int32_t layer, float *dst, int64_t n) {

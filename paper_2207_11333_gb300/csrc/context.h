@@ -85,8 +85,10 @@ struct gcnn_ctx {
     int kernels;
     std::vector<ProfEvent> ev;  // profiling graphs: event-record nodes around each phase
   };
-  // key: grid (graphs, node bucket, edge bucket), loss accumulator, profiling graph
-  std::map<std::tuple<int, int, int, const double *, bool>, Graph> graphs;
+  // key: grid (graphs, node bucket, edge bucket), loss accumulator, profiling
+  // graph, and whether the graph ends with the optimizer step
+  std::map<std::tuple<int, int, int, const double *, bool, bool>, Graph> graphs;
+  bool cap_grad_events = false;  // capturing forward + backward: record the bucket events externally
   int last_step_kernels = 0;
   bool capturing = false;
   bool fuse_head = false;  // train step: head backward runs inside the forward's head kernel

@@ -96,10 +96,15 @@ NodeHeadArgs node_args(gcnn_ctx *c, int Ngrid) {
 
 // Record that the gradients of bucket k (layer k, or every gradient for
 // k = L) are final once the work queued so far on stream s has run, for
-// callers that start their exchange of a bucket early (gcnn_grad_wait).  Not
-// while a train step is being captured: its graph runs AdamW itself.
+// callers that start their exchange of a bucket early (gcnn_grad_wait).  In a
+// captured forward + backward the record is an external event node of the
+// graph; a captured train step runs AdamW itself and records nothing.
 int mark_grads_ready(gcnn_ctx *c, int k, cudaStream_t s) {
-  if (c->capturing || k < 0 || k >= (int)c->grad_ev.size()) return GCNN_OK;
+  if (k < 0 || k >= (int)c->grad_ev.size()) return GCNN_OK;
+  if (c->capturing) {
+    if (c->cap_grad_events) GCNN_CUDA_TRY(cudaEventRecordWithFlags(c->grad_ev[k], s, cudaEventRecordExternal));
+    return GCNN_OK;
+  }
   GCNN_CUDA_TRY(cudaEventRecord(c->grad_ev[k], s));
   return GCNN_OK;
 }
@@ -398,11 +403,12 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
     PhaseScope ps(c, GCNN_PHASE_GEMM);
     GCNN_TRY(launch_colsum2(Ngrid, H, H, dims, c->dH, H, h, H, dPQ, 2 * H, gw.upd_b, gw.msg_b, lane.s));
   }
+  // layer l's gradients are final: before `done`, which the main stream joins
+  GCNN_TRY(mark_grads_ready(c, l, lane.s));
   if (ov) {
     GCNN_CUDA_TRY(cudaEventRecord(done, lane.s));
     if (l + 1 < c->L) GCNN_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->side_ev[3 * (l + 1) + 2], 0));
   }
-  GCNN_TRY(mark_grads_ready(c, l, lane.s));
   {  // dx = [g | dP | dQ] [W_x | A | B]^T ; the next layer's masked, scaled BF16 gradient
     TcDesc d = tblank();
     d.M = Ngrid; d.N = H; d.K = pad64(3 * H); d.node_dim = kNodeM;

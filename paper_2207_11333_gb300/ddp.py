@@ -13,7 +13,8 @@ across GPUs, gloo on the host):
   process reads its own portion of the data).
 - DataParallelTrainer: per step, the process's share is collated, its loss
   gradient scaled by its share of the step's graphs (and atoms, for the
-  node-level loss), the backward enqueued, and each gradient bucket (one per
+  node-level loss), the forward and backward launched (one captured graph),
+  and each gradient bucket (one per
   conv layer, then the head and the embedding) all-reduced on a separate
   stream as soon as the library reports it final (gcnn_grad_wait), while the
   backward of the layers below still runs.  The optimizer step then waits for
@@ -90,9 +91,12 @@ class DataParallelTrainer:
     initialised).
     """
 
-    def __init__(self, ctx, store, sampler: ShardedSampler, group=None):
+    def __init__(self, ctx, store, sampler: ShardedSampler, group=None, captured: bool = True):
         import torch.distributed as dist
         self.ctx, self.store, self.sampler, self.group = ctx, store, sampler, group
+        # forward + backward from one captured graph (gcnn_forward_backward)
+        # when the context offers it, else the eager calls
+        self.captured = captured and hasattr(ctx, "forward_backward")
         self.dist = dist if dist.is_available() and dist.is_initialized() else None
         self.world = self.dist.get_world_size(group) if self.dist else 1
         if self.world != sampler.W:
@@ -132,8 +136,11 @@ class DataParallelTrainer:
         sh = self.sampler.shard(step)
         b = self.ctx.collate(self.store, sh.ids)
         self.ctx.set_loss_scale(*sh.scales(self.rank))
-        self.ctx.forward(b, train=True)
-        self.ctx.backward(b, None, loss_accum)
+        if self.captured:
+            self.ctx.forward_backward(b, loss_accum)
+        else:
+            self.ctx.forward(b, train=True)
+            self.ctx.backward(b, None, loss_accum)
         self.exchange()
         self.ctx.step(lr)
         return sh

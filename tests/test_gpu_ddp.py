@@ -8,7 +8,7 @@
 - DataParallelTrainer in a process group of one over NCCL: the bucketed
   all-reduce on its own stream, ordered after gcnn_grad_wait, and the AdamW
   step after it give the same parameters, bit for bit, as the plain eager
-  steps.
+  steps, with the forward + backward from one captured graph and eager.
 - Two processes share the GPU with gloo (the all-reduce goes through host
   memory; no kernel waits on another process): both end with identical
   parameters, which match the oracle's steps on the whole global batches.
@@ -114,17 +114,48 @@ def test_trainer_in_a_group_of_one_over_nccl(tmp_path):
         plain.step(lr)
     dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{_free_port()}", rank=0, world_size=1)
     try:
-        ctx = _ctx(gs, delta, precision=1)
-        ctx.set_params(p)
-        tr = DataParallelTrainer(ctx, st, sampler)
-        assert tr.dist is not None and tr.comm is not None
-        for s in range(steps):
-            tr.step(s, lr)
-        torch.cuda.synchronize()
-        assert np.array_equal(ctx.get_params(), plain.get_params())
-        ctx.check()
+        for captured in (True, False):      # one graph per forward + backward, or eager calls
+            ctx = _ctx(gs, delta, precision=1)
+            ctx.set_params(p)
+            tr = DataParallelTrainer(ctx, st, sampler, captured=captured)
+            assert tr.dist is not None and tr.comm is not None and tr.captured == captured
+            for s in range(steps):
+                tr.step(s, lr)
+            torch.cuda.synchronize()
+            assert np.array_equal(ctx.get_params(), plain.get_params()), captured
+            ctx.check()
+            ctx.close()
     finally:
         dist.destroy_process_group()
+
+
+def test_forward_backward_graph_then_step_equals_train_step(tmp_path):
+    """gcnn_forward_backward (captured, bucket events as external graph nodes)
+    followed by gcnn_step gives the parameters of gcnn_train_step bit for bit,
+    FP32 and BF16, and a stream can wait on every bucket afterwards."""
+    import paper_2207_11333_gb300 as g
+    d, gs, p = _workload()
+    path, _ = write_both(gs, str(tmp_path))
+    st = g.Store(path)
+    delta = st.delta()
+    for precision in (0, 1):
+        a, b2 = _ctx(gs, delta, precision), _ctx(gs, delta, precision)
+        a.set_params(p)
+        b2.set_params(p)
+        side = torch.cuda.Stream()
+        for k in range(3):
+            ids = np.random.default_rng(k).permutation(gs.n_graphs)[:40]
+            a.train_step(a.collate(st, ids), 1e-3)
+            bb = b2.collate(st, ids)
+            b2.forward_backward(bb)
+            for bucket in range(len(b2.grad_buckets())):
+                b2.grad_wait(bucket, side)
+            torch.cuda.current_stream().wait_stream(side)
+            b2.step(1e-3)
+        torch.cuda.synchronize()
+        assert np.array_equal(a.get_params(), b2.get_params()), precision
+        a.check()
+        b2.check()
 
 
 def _rank_main(rank, world, port, path, q):

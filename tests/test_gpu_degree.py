@@ -93,17 +93,23 @@ def _model_workload(big: bool, F: int, H: int, L: int, seed: int = 52):
     return d, gs, synth.init_params(seed + 3, H, L, F=F)
 
 
-@pytest.mark.parametrize("precision,F,big", [(0, 0, False), (0, 4, False), (1, 0, False), (1, 4, False),
-                                             (0, 0, True), (1, 0, True)],
-                         ids=["fp32", "fp32-bonds", "bf16", "bf16-bonds", "fp32-fused", "bf16-fused"])
-def test_model_high_degree_vs_oracle(tmp_path, precision, F, big):
+@pytest.mark.parametrize("precision,F,big,recompute",
+                         [(0, 0, False, False), (0, 4, False, False), (1, 0, False, False), (1, 4, False, False),
+                          (0, 0, True, False), (1, 0, True, False), (0, 0, False, True), (1, 4, False, True),
+                          (0, 0, True, True)],
+                         ids=["fp32", "fp32-bonds", "bf16", "bf16-bonds", "fp32-fused", "bf16-fused",
+                              "fp32-recompute", "bf16-bonds-recompute", "fp32-fused-recompute"])
+def test_model_high_degree_vs_oracle(tmp_path, precision, F, big, recompute):
+    """Per-layer recompute (the aggregates are dropped after the forward and
+    recomputed in the backward) takes the stored-statistics branch of the
+    FP32 backward and the shared-buffer path of the BF16 one."""
     H, L = (8, 2) if big else (32, 2)
     d, gs, p = _model_workload(big, F, H, L)
     path, ost = write_both(gs, str(tmp_path))
     import paper_2207_11333_gb300 as g
     st = g.Store(path)
     delta = st.delta()
-    ctx = context(H, L, gs.n_graphs, gs.n_nodes, gs.n_edges, delta, precision=precision, F=F)
+    ctx = context(H, L, gs.n_graphs, gs.n_nodes, gs.n_edges, delta, precision=precision, F=F, recompute=recompute)
     ctx.set_params(p)
     ids = np.arange(gs.n_graphs)
     b = ctx.collate(st, ids)
@@ -118,7 +124,8 @@ def test_model_high_degree_vs_oracle(tmp_path, precision, F, big):
     opred, oxs, _, _ = oracle.forward(d, p.astype(np.float64), ob, want_layers=True)
     _, ograd, _, _ = oracle.backward(d, p.astype(np.float64), ob)
     gv, ov = oracle.split_params(d, grads), oracle.split_params(d, ograd)
-    gates = Gates(f"high-degree model, {'bf16' if precision else 'fp32'}, F = {F}, {'fused' if big else 'pair'}")
+    gates = Gates(f"high-degree model, {'bf16' if precision else 'fp32'}, F = {F}, {'fused' if big else 'pair'}, "
+                  f"recompute = {recompute}")
     if precision == 0:
         gates.check("pred", pred.cpu().numpy(), opred, FP32_FWD_TOL)
         for l in range(1, L + 1):
