@@ -440,7 +440,11 @@ typedef struct gcnn_serve_config {
   int32_t bucket_nodes[8];    /* ascending node capacities, e.g. 1k,4k,16k,64k   */
   int32_t max_graphs;         /* molecules per batch                             */
   int32_t precision;          /* GCNN_PREC_FP32 or GCNN_PREC_BF16                */
-  int64_t queue_nodes;        /* admission limit: atoms queued and not started   */
+  int64_t queue_nodes;        /* atoms of the device request pool: admission is
+                                 refused while admitted requests hold it (their
+                                 atoms and four edges per atom, until all their
+                                 molecules are done); clamped to half of the
+                                 device memory left after the slots' arenas   */
 } gcnn_serve_config;
 
 typedef struct gcnn_request {
@@ -458,8 +462,10 @@ typedef struct gcnn_request {
  * slot's forward graph for every bucket, then starts the scheduler thread.  Requests carry no bond features: a model with
  * edge_features > 0 is refused (GCNN_EINVAL). */
 int gcnn_serve_create(const gcnn_ctx *model, const gcnn_serve_config *cfg, gcnn_server **out);
-/* Queue a request (the library copies it; the caller may free it on return).
- * GCNN_EAGAIN: admission refused (queue full), retry later. */
+/* Queue a request: its atom types and bonds are copied into the server's
+ * device request pool before this returns (the caller may free it then).
+ * GCNN_EAGAIN: admission refused (no room in the pool), retry later;
+ * GCNN_EINVAL: malformed, or larger than the whole pool. */
 int gcnn_serve_submit(gcnn_server *srv, const gcnn_request *req, uint64_t *ticket);
 /* Non-blocking: GCNN_EAGAIN until every molecule of the request is done;
  * then writes n_mol predictions to out (host), the latency from submit to

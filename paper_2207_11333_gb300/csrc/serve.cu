@@ -1,17 +1,24 @@
 // Inference server: continuous batching of screening requests (Sec. 1 and
 // Sec. 6: the trained GCNN as a fast surrogate over streams of molecules).
 //
-// submit() validates and copies a request into host memory and queues it;
-// admission is refused (GCNN_EAGAIN) while the atoms waiting to start would
-// exceed queue_nodes.  One scheduler thread loops over the slots:
+// submit() validates a request, reserves room for its atoms and edges in a
+// device-resident request pool (two FIFO rings in device memory, sized at
+// creation from queue_nodes and from the free device memory reported by
+// cudaMemGetInfo once the slots' arenas are allocated), copies its atom types
+// and bonds there and queues it.  Admission is refused (GCNN_EAGAIN) while
+// the pool has no contiguous room for the request: admission is by device
+// memory.  A request's room is released once all its molecules are done,
+// in submission order.  One scheduler thread loops over the slots:
 //   - a busy slot whose completion event fired is retired: its predictions
 //     (pinned memory) are scattered to their requests, finished requests are
 //     stamped and waiters woken;
 //   - a free slot takes queued molecules in FIFO order (splitting requests
 //     across batches) up to the largest bucket and the slot's molecule and
-//     edge capacities, picks the smallest bucket that fits, writes the batch
-//     as a packed mini-store into pinned memory, and enqueues on its own
-//     stream: one host-to-device copy, the device collator, the forward graph
+//     edge capacities, and only while they lie contiguously in the pool,
+//     picks the smallest bucket that fits, writes the molecules' atom and
+//     edge offsets into pinned memory, and enqueues on its own stream: one
+//     host-to-device copy of the offsets, the device collator reading the
+//     molecules straight from the pool, the forward graph
 //     of that bucket (captured for every slot and bucket at creation), and one
 //     device-to-host copy of the predictions, followed by its completion
 //     event.
@@ -41,7 +48,7 @@ struct Request {
   int n_mol = 0;
   std::vector<int32_t> n_nodes, n_edges;
   std::vector<int64_t> node_off, edge_off;  // prefix sums into types / edges
-  std::vector<uint8_t> types, edges;
+  int64_t pool_a = 0, pool_e = 0;            // first atom / edge of the request in the pool
   std::vector<float> out;
   int next = 0;          // first molecule not yet placed in a batch
   int remaining = 0;     // molecules not yet finished
@@ -67,6 +74,48 @@ struct Slot {
   std::vector<cudaGraphExec_t> exec;  // per bucket, captured at creation
 };
 
+// A FIFO ring over [0, cap) of one pool array: allocations are contiguous,
+// taken at the head (skipping the end of the array when a request does not
+// fit before it) and released from the tail in allocation order.
+struct Ring {
+  int64_t cap = 0, head = 0, tail = 0, used = 0;
+  // start of `need` contiguous free units, and the units skipped at the end
+  // of the array to reach it; false when there is no room
+  bool fits(int64_t need, int64_t *start, int64_t *skip) const {
+    if (need > cap) return false;
+    if (used == 0) {
+      *start = 0;
+      *skip = 0;
+      return true;
+    }
+    if (head > tail || (head == tail && used == 0)) {  // live [tail, head)
+      if (cap - head >= need) { *start = head; *skip = 0; return true; }
+      if (tail >= need) { *start = 0; *skip = cap - head; return true; }
+      return false;
+    }
+    if (head < tail && tail - head >= need) { *start = head; *skip = 0; return true; }  // live wraps
+    return false;
+  }
+  void take(int64_t start, int64_t skip, int64_t need) {
+    if (used == 0) tail = start;
+    used += skip + need;
+    head = start + need;
+  }
+  void release(int64_t units, int64_t next_tail) {
+    used -= units;
+    tail = next_tail;
+    if (used == 0) head = tail = 0;
+  }
+};
+
+// One request's room in both rings: each region starts where the ring's head
+// stood (so it includes the units skipped to reach the array's start).
+struct Alloc {
+  uint64_t ticket;  // the request's (requests are freed once polled)
+  int64_t a_region, a_units, e_region, e_units;
+  bool done;
+};
+
 }  // namespace
 
 struct gcnn_server {
@@ -77,6 +126,13 @@ struct gcnn_server {
   std::condition_variable work_cv, done_cv;
   std::deque<Request *> pending;
   std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
+  // device request pool: atom types and local edge pairs of admitted requests
+  uint8_t *pool_types = nullptr, *pool_edges = nullptr;
+  float *zeros = nullptr;  // [max_graphs] targets of the collator (unused by serving)
+  Ring ring_a, ring_e;     // atoms, edges
+  std::deque<Alloc> allocs;
+  cudaStream_t copy_stream = nullptr;
+  std::mutex copy_mu;
   uint64_t next_ticket = 1;
   int64_t queued_nodes = 0;
   std::atomic<bool> stop{false};
@@ -136,8 +192,11 @@ void form_batch(gcnn_server *s, Slot &sl, int64_t *nodes, int64_t *edges) {
   int64_t N = 0, E = 0;
   int G = 0;
   sl.pieces.clear();
+  int64_t next_a = -1, next_e = -1;  // where the batch's next molecule must lie in the pool
   while (!s->pending.empty() && G < s->cfg.max_graphs) {
     Request *r = s->pending.front();
+    const int64_t a0 = r->pool_a + r->node_off[r->next], e0 = r->pool_e + r->edge_off[r->next];
+    if (next_a >= 0 && (a0 != next_a || e0 != next_e)) break;  // not contiguous (the pool wrapped)
     int take = 0;
     while (r->next + take < r->n_mol && G + take < s->cfg.max_graphs) {
       const int m = r->next + take;
@@ -150,6 +209,9 @@ void form_batch(gcnn_server *s, Slot &sl, int64_t *nodes, int64_t *edges) {
     sl.pieces.push_back(Piece{r, r->next, take});
     for (int m = r->next; m < r->next + take; ++m) s->queued_nodes -= r->n_nodes[m];
     r->next += take;
+    const int last = r->next - 1;
+    next_a = r->pool_a + r->node_off[last] + r->n_nodes[last];
+    next_e = r->pool_e + r->edge_off[last] + r->n_edges[last];
     G += take;
     if (r->next == r->n_mol) s->pending.pop_front();
     else break;  // batch full
@@ -172,38 +234,34 @@ int launch_batch(gcnn_server *s, Slot &sl, int64_t N, int64_t E) {
   const int G = sl.graphs;
   int b = 0;
   while (b < s->cfg.n_buckets - 1 && s->cfg.bucket_nodes[b] < N) ++b;
-  // packed mini-store in the slot context's pinned staging buffer (free: the
-  // slot's previous batch has completed)
+  // the batch's molecules lie contiguously in the pool: only their atom and
+  // edge offsets (relative to the first molecule) go to the device, through
+  // the slot context's pinned staging buffer (free: its previous batch has
+  // completed)
   char *h = c->stage_host[0];
   size_t o = 0;
   const size_t o_np = o; o = align16(o + 8 * (size_t)(G + 1));
   const size_t o_ep = o; o = align16(o + 8 * (size_t)(G + 1));
-  const size_t o_y = o;  o = align16(o + 4 * (size_t)G);
-  const size_t o_t = o;  o = align16(o + (size_t)N);
-  const size_t o_e = o;  o = align16(o + 2 * (size_t)E);
   if (o > c->stage_bytes) return set_error(GCNN_EINVAL, "serve: staging too small");
   int64_t *np = reinterpret_cast<int64_t *>(h + o_np), *ep = reinterpret_cast<int64_t *>(h + o_ep);
-  float *y = reinterpret_cast<float *>(h + o_y);
-  uint8_t *ty = reinterpret_cast<uint8_t *>(h + o_t), *ed = reinterpret_cast<uint8_t *>(h + o_e);
-  np[0] = 0;
-  ep[0] = 0;
+  const Request *r0 = sl.pieces.front().r;
+  const int64_t base_a = r0->pool_a + r0->node_off[sl.pieces.front().first];
+  const int64_t base_e = r0->pool_e + r0->edge_off[sl.pieces.front().first];
   int g = 0;
   for (const Piece &p : sl.pieces) {
     const Request *r = p.r;
     for (int m = p.first; m < p.first + p.count; ++m, ++g) {
-      memcpy(ty + np[g], r->types.data() + r->node_off[m], (size_t)r->n_nodes[m]);
-      memcpy(ed + 2 * ep[g], r->edges.data() + 2 * r->edge_off[m], 2 * (size_t)r->n_edges[m]);
-      y[g] = 0.f;
-      np[g + 1] = np[g] + r->n_nodes[m];
-      ep[g + 1] = ep[g] + r->n_edges[m];
+      np[g] = r->pool_a + r->node_off[m] - base_a;
+      ep[g] = r->pool_e + r->edge_off[m] - base_e;
     }
   }
+  np[G] = N;
+  ep[G] = E;
   GCNN_CUDA_TRY(cudaEventRecord(sl.start, sl.stream));
   GCNN_CUDA_TRY(cudaMemcpyAsync(c->stage_dev, h, o, cudaMemcpyHostToDevice, sl.stream));
   const char *d = c->stage_dev;
   StoreView v{reinterpret_cast<const int64_t *>(d + o_np), reinterpret_cast<const int64_t *>(d + o_ep),
-              reinterpret_cast<const uint8_t *>(d + o_t), reinterpret_cast<const uint8_t *>(d + o_e),
-              reinterpret_cast<const float *>(d + o_y)};
+              s->pool_types + base_a, s->pool_edges + 2 * base_e, s->zeros};
   GCNN_TRY(launch_collate(G, nullptr, v, c->bb, c->scal_tab, c->Nc, c->Ec, c->err, sl.stream));
   GCNN_CUDA_TRY(cudaGraphLaunch(sl.exec[b], sl.stream));
   GCNN_CUDA_TRY(cudaMemcpyAsync(sl.pin_out, c->pred, sizeof(float) * G, cudaMemcpyDeviceToHost, sl.stream));
@@ -211,6 +269,20 @@ int launch_batch(gcnn_server *s, Slot &sl, int64_t N, int64_t E) {
   sl.busy = true;
   sl.atoms = N;
   return GCNN_OK;
+}
+
+// Mark request r's pool room free and return every free room at the front
+// of the allocation order to the rings (caller holds s->mu).
+void release_pool(gcnn_server *s, Request *r) {
+  for (Alloc &a : s->allocs)
+    if (a.ticket == r->ticket) a.done = true;
+  while (!s->allocs.empty() && s->allocs.front().done) {
+    const Alloc a = s->allocs.front();
+    s->allocs.pop_front();
+    const Alloc *next = s->allocs.empty() ? nullptr : &s->allocs.front();
+    s->ring_a.release(a.a_units, next ? next->a_region : 0);
+    s->ring_e.release(a.e_units, next ? next->e_region : 0);
+  }
 }
 
 void retire(gcnn_server *s, Slot &sl) {
@@ -227,6 +299,7 @@ void retire(gcnn_server *s, Slot &sl) {
       r->t_done = now;
       s->n_requests += 1;
     }
+    if (r->remaining == 0) release_pool(s, r);
   }
   sl.pieces.clear();
   sl.busy = false;
@@ -321,6 +394,10 @@ int validate(const gcnn_server *s, const gcnn_request *q, int64_t *nodes) {
 }
 
 void destroy_server(gcnn_server *s) {
+  if (s->pool_types) cudaFree(s->pool_types);
+  if (s->pool_edges) cudaFree(s->pool_edges);
+  if (s->zeros) cudaFree(s->zeros);
+  if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
   for (Slot &sl : s->slots) {
     for (auto e : sl.exec)
       if (e) cudaGraphExecDestroy(e);
@@ -383,6 +460,29 @@ int gcnn_serve_create(const gcnn_ctx *model, const gcnn_serve_config *cfg, gcnn_
       rc = capture_forward(sl.ctx, cfg->max_graphs, cfg->bucket_nodes[b], bucket_edges(s, sl.ctx, b), &sl.exec[b]);
     if (rc != GCNN_OK) break;
   }
+  // the request pool: queue_nodes atoms and four edges per atom (plus one
+  // largest molecule), within half of the device memory left once the slots'
+  // arenas are allocated
+  if (rc == GCNN_OK) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) rc = set_error(GCNN_ECUDA, "serve_create: cudaMemGetInfo");
+    int64_t atoms = cfg->queue_nodes;
+    const int64_t budget = (int64_t)(free_b / 2);
+    if (rc == GCNN_OK && atoms + 2 * (4 * atoms + kMaxGraphEdges) > budget) atoms = (budget - 2 * kMaxGraphEdges) / 9;
+    if (rc == GCNN_OK && atoms < kMaxGraphNodes)
+      rc = set_error(GCNN_ENOMEM, "serve_create: no device memory left for the request pool");
+    if (rc == GCNN_OK) {
+      s->ring_a.cap = atoms;
+      s->ring_e.cap = 4 * atoms + kMaxGraphEdges;
+      s->cfg.queue_nodes = atoms;
+      if (cudaMalloc(&s->pool_types, (size_t)s->ring_a.cap) != cudaSuccess ||
+          cudaMalloc(&s->pool_edges, 2 * (size_t)s->ring_e.cap) != cudaSuccess ||
+          cudaMalloc(&s->zeros, sizeof(float) * cfg->max_graphs) != cudaSuccess ||
+          cudaMemset(s->zeros, 0, sizeof(float) * cfg->max_graphs) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        rc = set_error(GCNN_ENOMEM, "serve_create: request pool allocation failed");
+    }
+  }
   if (rc != GCNN_OK) {
     destroy_server(s);
     return rc;
@@ -397,7 +497,8 @@ int gcnn_serve_submit(gcnn_server *s, const gcnn_request *q, uint64_t *ticket) {
   int64_t nodes = 0;
   GCNN_TRY(validate(s, q, &nodes));
   if (nodes > s->cfg.queue_nodes)
-    return set_error(GCNN_EINVAL, "serve_submit: request of %lld atoms exceeds queue_nodes", (long long)nodes);
+    return set_error(GCNN_EINVAL, "serve_submit: request of %lld atoms exceeds the pool's %lld", (long long)nodes,
+                     (long long)s->cfg.queue_nodes);
   auto r = std::make_unique<Request>();
   r->n_mol = q->n_mol;
   r->n_nodes.assign(q->n_nodes, q->n_nodes + q->n_mol);
@@ -411,24 +512,54 @@ int gcnn_serve_submit(gcnn_server *s, const gcnn_request *q, uint64_t *ticket) {
     nn += q->n_nodes[m];
     ne += q->n_edges[m];
   }
-  r->types.assign(q->types, q->types + nn);
-  r->edges.assign(q->edges, q->edges + 2 * ne);
+  if (ne > s->ring_e.cap)
+    return set_error(GCNN_EINVAL, "serve_submit: request of %lld edges exceeds the pool's %lld", (long long)ne,
+                     (long long)s->ring_e.cap);
   r->out.assign(q->n_mol, 0.f);
   r->remaining = q->n_mol;
   r->t_submit = Clock::now();
+  Request *rp = r.get();
   {
+    // room in the device pool (admission by device memory)
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->fatal != GCNN_OK) return set_error(s->fatal, "%s", s->fatal_msg);
     if (s->stop.load()) return set_error(GCNN_ESTATE, "serve_submit: server is stopping");
-    if (s->queued_nodes + nodes > s->cfg.queue_nodes) {
+    int64_t a0 = 0, askip = 0, e0 = 0, eskip = 0;
+    if (!s->ring_a.fits(nn, &a0, &askip) || !s->ring_e.fits(ne, &e0, &eskip)) {
       s->n_refused += 1;
-      return set_error(GCNN_EAGAIN, "serve_submit: queue full (%lld atoms waiting)", (long long)s->queued_nodes);
+      return set_error(GCNN_EAGAIN, "serve_submit: request pool full (%lld of %lld atoms held)",
+                       (long long)s->ring_a.used, (long long)s->ring_a.cap);
     }
     r->ticket = s->next_ticket++;
     *ticket = r->ticket;
-    s->queued_nodes += nodes;
-    s->pending.push_back(r.get());
+    s->allocs.push_back(Alloc{r->ticket, s->ring_a.head, askip + nn, s->ring_e.head, eskip + ne, false});
+    s->ring_a.take(a0, askip, nn);
+    s->ring_e.take(e0, eskip, ne);
+    rp->pool_a = a0;
+    rp->pool_e = e0;
     s->reqs.emplace(r->ticket, std::move(r));
+  }
+  // the atom types and bonds go to the reserved room before the scheduler can
+  // see the request (the room belongs to no batch until then)
+  cudaError_t ce;
+  {
+    std::lock_guard<std::mutex> lock(s->copy_mu);
+    ce = cudaMemcpyAsync(s->pool_types + rp->pool_a, q->types, (size_t)nn, cudaMemcpyHostToDevice, s->copy_stream);
+    if (ce == cudaSuccess && ne > 0)
+      ce = cudaMemcpyAsync(s->pool_edges + 2 * rp->pool_e, q->edges, 2 * (size_t)ne, cudaMemcpyHostToDevice,
+                           s->copy_stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->copy_stream);
+  }
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (ce != cudaSuccess) {
+      s->fatal = GCNN_ECUDA;
+      snprintf(s->fatal_msg, sizeof(s->fatal_msg), "serve: request copy failed: %s", cudaGetErrorString(ce));
+      fail_all(s, GCNN_ECUDA);
+      return set_error(GCNN_ECUDA, "%s", s->fatal_msg);
+    }
+    s->queued_nodes += nodes;
+    s->pending.push_back(rp);
   }
   s->work_cv.notify_one();
   return GCNN_OK;

@@ -108,3 +108,43 @@ def test_concurrent_submitters(model):
     for k in range(6):
         assert np.array_equal(results[k], whole[100 * k:100 * k + 100])
     srv.close()
+
+
+def test_request_pool_wraps_and_releases_in_order(model):
+    """The device request pool is a ring: with room for 2,500 atoms and a
+    stream of requests of up to ~1,500 atoms, rooms wrap around the end of the
+    pool many times, batches stop where the pool wraps, and refused requests
+    are admitted again once earlier ones are done and released.  Every
+    prediction equals, bit for bit, that of a server whose pool never wraps."""
+    g, gs, ost, delta, ctx, p, d = model
+    small = g.Server(ctx, n_slots=2, buckets=(2048,), max_graphs=64, queue_nodes=2500)
+    large = g.Server(ctx, n_slots=2, buckets=(2048,), max_graphs=64)
+    rng = np.random.default_rng(7)
+    spans, pos = [], 0
+    for _ in range(40):
+        n = int(rng.integers(3, 30))
+        if pos + n > 600:
+            pos = 0
+        spans.append((pos, n))
+        pos += n
+    want = [large.wait(large.submit(*g.request_arrays(gs, a, n)))[0] for a, n in spans]
+    outstanding, got, refusals, atoms = [], {}, 0, 0
+    for k, (a, n) in enumerate(spans):
+        req = g.request_arrays(gs, a, n)
+        atoms += int(np.sum(req[0]))
+        while True:
+            t = small.submit(*req)
+            if t is not None:
+                outstanding.append((k, t))
+                break
+            refusals += 1
+            k0, t0 = outstanding.pop(0)          # the oldest request frees its room first
+            got[k0] = small.wait(t0)[0]
+    for k0, t0 in outstanding:
+        got[k0] = small.wait(t0)[0]
+    assert atoms > 6 * 2500 and refusals > 0
+    for k in range(len(spans)):
+        assert np.array_equal(got[k], want[k]), k
+    assert small.stats()["refused"] == refusals
+    small.close()
+    large.close()
