@@ -42,6 +42,7 @@ LR = 1e-3
 METRIC = "train graphs/s"
 WORKLOAD = "PNA GCNN training step: 200k synthetic molecular graphs (3-51 nodes, mean 18), 6 layers x 200, batch 128"
 SM_COUNT, FP32_LANES_PER_SM = 152, 128
+BM_ROWS, SM_CLOCK_HZ = 128, 2.07e9   # tensor-core GEMM tile rows; maximum SM clock
 
 
 def log(*a):
@@ -914,6 +915,40 @@ def run_serving(g, model_ctx, delta, params, args):
             "baseline_fp32_one_request_per_launch": {"rates": base}}
 
 
+def gemm_study(args):
+    """Where a BF16 GEMM launch's time goes (gcnn_gemm_study): the step's six GEMM
+    shapes for a batch of --atoms atoms at H = 200, under the planner's plan and
+    under every plan of its search space; and the update shape's time against K
+    without split-K, fitted per tile width as fixed + per-64-wide-k-tile cost."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import paper_2207_11333_gb300 as g
+    plans = g.gemm_study(args.atoms, H, 0)
+    shapes = {}
+    for name in g.GEMM_SHAPES:
+        rows = [r for r in plans if r["shape"] == name]
+        own = next(r for r in rows if r["planner"])
+        best = min(rows, key=lambda r: r["us"])
+        pick = lambda r: {k: r[k] for k in ("BN", "ntiles", "splits", "cluster", "us")}
+        shapes[name] = {"planner": pick(own), "fastest": pick(best), "plans_timed": len(rows),
+                        "planner_over_fastest": own["us"] / best["us"]}
+    sweep = g.gemm_study(args.atoms, H, 1)
+    fits = {}
+    for bn in sorted({r["BN"] for r in sweep}):
+        pts = [(r["K"] / 64.0, r["us"]) for r in sweep if r["BN"] == bn and r["K"] >= 1024]
+        x = np.array([p[0] for p in pts]); y = np.array([p[1] for p in pts])
+        slope, icpt = np.polyfit(x, y, 1)
+        mac_per_cycle = BM_ROWS * bn * 64 / (slope * 1e-6 * SM_CLOCK_HZ)
+        fits[str(bn)] = {"us_per_k_tile": float(slope), "fixed_us": float(icpt),
+                         "mac_per_cycle_per_sm": float(mac_per_cycle),
+                         "times_us": {str(r["K"]): r["us"] for r in sweep if r["BN"] == bn}}
+    print(json.dumps({"study": "gemm", "atoms": args.atoms, "hidden": H, "shapes": shapes,
+                      "update_k_sweep_no_split": fits,
+                      "note": "us per launch, best of 5 replays of a 20-launch CUDA graph; k-tile = 64 of K; "
+                              "MAC/cycle at 2070 MHz for a 128-row tile"}), flush=True)
+    return 0
+
+
 def serving_study(args):
     """The serving configuration alone: a student trained for a few hundred steps
     of the training workload serves Poisson traffic at every rate of
@@ -1089,11 +1124,13 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4, help="server slots (batches in flight)")
     ap.add_argument("--baseline-seconds", type=float, default=20.0,
                     help="seconds per rate of the one-request-per-launch FP32 baseline (at most --serve-seconds)")
-    ap.add_argument("--study", choices=["none", "precision", "aggregate", "loading", "serving"], default="none",
+    ap.add_argument("--study", choices=["none", "precision", "aggregate", "loading", "serving", "gemm"],
+                    default="none",
                     help="precision: train FP32 and BF16 for --epochs and compare held-out MAE; aggregate: the "
                          "aggregation operators alone on --molecules molecules, --reps timed launches each "
                          "(no bench line)")
     ap.add_argument("--molecules", type=int, default=60_000, help="batch of the aggregation study")
+    ap.add_argument("--atoms", type=int, default=2304, help="batch atoms of the GEMM study (128 molecules of 18)")
     ap.add_argument("--reps", type=int, default=5, help="timed launches per operator in the aggregation study")
     ap.add_argument("--epochs", type=int, default=10)
     ap.add_argument("--lr", type=float, default=1e-4, help="learning rate of the precision study")
@@ -1118,6 +1155,8 @@ def main():
         return 0
     if args.study == "serving":
         return serving_study(args)
+    if args.study == "gemm":
+        return gemm_study(args)
     if args.study == "aggregate":
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

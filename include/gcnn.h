@@ -418,6 +418,22 @@ int gcnn_timeline_read(gcnn_ctx *ctx, int32_t *ids, int64_t *t_ns, int32_t max, 
  * paper operation: measurement support.  GCNN_EINVAL for iters < 1. */
 int gcnn_ffma_peak(int32_t iters, double *tflops);
 
+/* Timing study of the BF16 tensor-core GEMMs of one training step, for a
+ * batch of n_atoms atoms and hidden width `hidden` (a multiple of 8, at most
+ * 256), on the calling thread's device; synchronous.  Six shapes: 0 message
+ * (x [A | B]), 1 update (U W_U), 2 dW_U, 3 dagg, 4 dW_M, 5 dx (dW_U and dW_M
+ * limited to half the SMs, as on the backward's second stream).  Each time is
+ * the best of five replays of a CUDA graph of 20 launches, in microseconds per
+ * launch.  mode 0: per shape, the planner's own plan (flag 1), then every plan
+ * of its search space: tile width BN (16..256), K-splits, cluster or partial
+ * buffer.  mode 1: the update shape at K = 64 .. 16 hidden without split-K,
+ * at tile widths 32, 64, 112, 128, 208 and 256.  Each result row is 8
+ * doubles: shape, BN, n-tiles, splits, cluster (0/1), K, microseconds, planner
+ * flag; rows beyond max_rows are dropped.  Not a paper operation: measurement
+ * support.  GCNN_EINVAL for bad sizes; GCNN_EDEVICE if a wait timed out. */
+int gcnn_gemm_study(int32_t n_atoms, int32_t hidden, int32_t mode, double *rows, int32_t max_rows,
+                    int32_t *n_rows);
+
 /* ------------------------------------------------------------------ serving
  * Inference server for the screening use of the trained model (Sec. 1:
  * surrogate screening over streaming molecules; Sec. 6).  Requests of any

@@ -120,6 +120,7 @@ def _load() -> ctypes.CDLL:
         "gcnn_step_kernel_count": (i32, [vp, P(i32)]),
         "gcnn_timeline_enable": (i32, [vp, i32]),
         "gcnn_ffma_peak": (i32, [i32, P(f64)]),
+        "gcnn_gemm_study": (i32, [i32, i32, i32, vp, i32, P(i32)]),
         "gcnn_timeline_read": (i32, [vp, vp, vp, i32, P(i32)]),
         "gcnn_memory": (i32, [vp, P(i64)]),
         "gcnn_serve_create": (i32, [vp, P(ServeConfig), P(vp)]),
@@ -253,6 +254,18 @@ def ffma_peak(iters: int = 4096) -> float:
     t = ctypes.c_double()
     _check(lib.gcnn_ffma_peak(int(iters), ctypes.byref(t)))
     return t.value
+
+
+GEMM_SHAPES = ("message", "update", "dW_U", "dagg", "dW_M", "dx")
+
+
+def gemm_study(n_atoms: int, hidden: int, mode: int = 0, max_rows: int = 4096) -> list[dict]:
+    """Timing study of the training step's BF16 GEMMs (gcnn_gemm_study): one dict per timed plan."""
+    rows = np.zeros((max_rows, 8), np.float64)
+    n = ctypes.c_int32()
+    _check(lib.gcnn_gemm_study(int(n_atoms), int(hidden), int(mode), _np_ptr(rows), max_rows, ctypes.byref(n)))
+    return [{"shape": GEMM_SHAPES[int(r[0])], "BN": int(r[1]), "ntiles": int(r[2]), "splits": int(r[3]),
+             "cluster": bool(r[4]), "K": int(r[5]), "us": float(r[6]), "planner": bool(r[7])} for r in rows[:n.value]]
 
 
 def make_config(hidden: int, layers: int, max_graphs: int, max_nodes: int, max_edges: int, **kw) -> Config:

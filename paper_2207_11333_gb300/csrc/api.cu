@@ -846,6 +846,15 @@ int gcnn_timeline_enable(gcnn_ctx *c, int32_t capacity) {
   return GCNN_OK;
 }
 
+int gcnn_gemm_study(int32_t n_atoms, int32_t hidden, int32_t mode, double *rows, int32_t max_rows,
+                    int32_t *n_rows) {
+  if (!n_rows) return set_error(GCNN_EINVAL, "gemm_study: null argument");
+  int n = 0;
+  const int rc = gemm_tc_study(n_atoms, hidden, mode, rows, max_rows, &n);
+  *n_rows = n;
+  return rc;
+}
+
 int gcnn_ffma_peak(int32_t iters, double *tflops) {
   if (iters < 1 || !tflops) return set_error(GCNN_EINVAL, "ffma_peak: iters must be >= 1");
   float *out = nullptr;

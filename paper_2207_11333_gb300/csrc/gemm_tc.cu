@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "kernels.cuh"
 
@@ -795,7 +796,10 @@ int launch_gemm(void (*kernel)(P...), dim3 grid, int cz, cudaStream_t s, A &&...
 
 }  // namespace
 
-int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned *err, cudaStream_t s) {
+namespace {
+// One GEMM with the planner's plan, or with `force` (measurement: gcnn_gemm_study).
+int run_planned(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned *err, cudaStream_t s,
+                const Plan *force, Plan *used) {
   if (d.M <= 0 || d.N <= 0 || d.K < 0) return GCNN_OK;
   const TcEpilogue &e = d.ep;
   if (d.N % 8 || (e.C && (e.ldc % 4 || reinterpret_cast<uintptr_t>(e.C) % 16)) ||
@@ -806,7 +810,9 @@ int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
   GCNN_TRY(configure());
   const double out_bytes = (e.C ? 4.0 : 0.0) + (e.C16 ? 2.0 : 0.0) + (e.D3 ? 10.0 : 0.0);
   Plan plan = choose(d.M, d.N, d.K, ws.max_splits, ws.max_ctas, out_bytes, d.B.mn_major, e.D3 != nullptr);
+  if (force) plan = *force;
   if (plan.splits > 1 && !plan.cluster && (size_t)plan.splits * d.M * d.N > ws.floats) plan.splits = 1;
+  if (used) *used = plan;
   const int BN = plan.BN, ntiles = plan.ntiles, splits = plan.splits;
   const int ktiles = (d.K + BK - 1) / BK;
   TcMaps maps;
@@ -828,9 +834,193 @@ int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
   return GCNN_OK;
 }
 
+}  // namespace
+
+int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned *err, cudaStream_t s) {
+  return run_planned(d, dims, ws, err, s, nullptr, nullptr);
+}
+
 size_t gemm_tc_workspace_floats(int M, int N, int K) {
   const int sp = max_splits_of(M, K);
   return sp > 1 ? (size_t)sp * M * N : 0;
+}
+
+// ---------------------------------------------------------------- study
+// Timing of the training step's six BF16 GEMM shapes for n_atoms rows and
+// hidden H (measurement support; gcnn_gemm_study documents the modes and the
+// rows).  Operands are arbitrary BF16 values in device buffers of the step's
+// layouts; each time is the best of five replays of a graph of 20 launches.
+namespace {
+struct StudyShape {
+  int id;
+  TcDesc d;
+  int max_ctas;
+};
+
+int study_time(const StudyShape &sh, DevDims dims, const GemmWorkspace &ws, unsigned *err, cudaStream_t s,
+               const Plan *force, Plan *used, double *us) {
+  for (int i = 0; i < 3; ++i) GCNN_TRY(run_planned(sh.d, dims, ws, err, s, force, used));
+  GCNN_CUDA_TRY(cudaStreamSynchronize(s));
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  GCNN_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int rc = GCNN_OK;
+  for (int i = 0; i < 20 && rc == GCNN_OK; ++i) rc = run_planned(sh.d, dims, ws, err, s, force, nullptr);
+  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (rc != GCNN_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc != GCNN_OK ? rc : set_error(GCNN_ECUDA, "gemm study: capture failed");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double best = 1e30;
+  if (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess || cudaGraphLaunch(ge, s) != cudaSuccess)
+    rc = set_error(GCNN_ECUDA, "gemm study: graph set-up failed");
+  for (int k = 0; k < 5 && rc == GCNN_OK; ++k) {
+    float ms = 0.f;
+    if (cudaEventRecord(e0, s) != cudaSuccess || cudaGraphLaunch(ge, s) != cudaSuccess ||
+        cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      rc = set_error(GCNN_ECUDA, "gemm study: timing failed");
+    best = std::min(best, 1e3 * ms / 20.0);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (ge) cudaGraphExecDestroy(ge);
+  cudaGraphDestroy(g);
+  *us = best;
+  return rc;
+}
+}  // namespace
+
+int gemm_tc_study(int n_atoms, int H, int mode, double *rows, int max_rows, int *n_rows) {
+  *n_rows = 0;
+  if (n_atoms < 1 || H < 8 || H % 8 || H > 256 || (mode != 0 && mode != 1) || !rows || max_rows < 1)
+    return set_error(GCNN_EINVAL, "gemm study: bad arguments (hidden a multiple of 8, at most 256)");
+  GCNN_TRY(configure());
+  const int Ng = (n_atoms + 255) / 256 * 256, K3 = (3 * H + 63) / 64 * 64, KH = (H + 63) / 64 * 64;
+  const size_t wsf = (size_t)32 * 16 * H * H + (size_t)32 * Ng * 5 * H;
+  uint16_t *U = nullptr, *G5 = nullptr, *W = nullptr, *D3 = nullptr;
+  float *C = nullptr, *F = nullptr, *ws_p = nullptr;
+  int *dd = nullptr;
+  unsigned *err = nullptr;
+  cudaStream_t s = nullptr;
+  int rc = GCNN_OK;
+  const size_t nU = (size_t)Ng * 16 * H, nG = (size_t)Ng * 5 * H, nW = (size_t)36 * H * H;
+  if (cudaMalloc(&U, 2 * nU) != cudaSuccess || cudaMalloc(&G5, 2 * nG) != cudaSuccess ||
+      cudaMalloc(&W, 2 * nW) != cudaSuccess || cudaMalloc(&D3, 2 * nG) != cudaSuccess ||
+      cudaMalloc(&C, 4 * nG) != cudaSuccess || cudaMalloc(&F, 4 * ((size_t)Ng * H + 2 * Ng + 5 * H)) != cudaSuccess ||
+      cudaMalloc(&ws_p, 4 * wsf) != cudaSuccess || cudaMalloc(&dd, 16) != cudaSuccess ||
+      cudaMalloc(&err, 4) != cudaSuccess || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+    rc = set_error(GCNN_ENOMEM, "gemm study: allocation failed");
+  if (rc == GCNN_OK) {
+    const int hd[4] = {1, n_atoms, 0, 0};
+    // BF16 0x3c00..0x3c3f (about 0.008-0.016) and FP32 0.5 everywhere: finite outputs
+    if (cudaMemset(U, 0x3c, 2 * nU) != cudaSuccess || cudaMemset(G5, 0x3c, 2 * nG) != cudaSuccess ||
+        cudaMemset(W, 0x3c, 2 * nW) != cudaSuccess || cudaMemset(F, 0, 4 * ((size_t)Ng * H + 2 * Ng + 5 * H)) != cudaSuccess ||
+        cudaMemset(err, 0, 4) != cudaSuccess || cudaMemcpy(dd, hd, 16, cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = set_error(GCNN_ECUDA, "gemm study: initialisation failed");
+  }
+  // weights: message [H][2H], update [16H][H], dagg's [5H][3H], dx's [H][3H]
+  const uint16_t *Wm = W, *Wu = W + 2 * H * H, *Wd = W + 18 * H * H, *Wx = W + 33 * H * H;
+  float *mask = F, *amp = F + (size_t)Ng * H, *att = amp + Ng, *bias = att + Ng;
+  std::vector<StudyShape> shapes;
+  auto M = [](const uint16_t *p, int ld, int r, int c, bool mn) { return TcMat{p, ld, r, c, mn}; };
+  {  // 0: message, x [A | B] + b
+    TcDesc d{}; d.M = Ng; d.N = 2 * H; d.K = KH; d.node_dim = kNodeM;
+    d.A = M(U, 16 * H, Ng, H, false); d.B = M(Wm, 2 * H, H, 2 * H, true); d.stable = kStableB;
+    d.ep.C = C; d.ep.ldc = 2 * H; d.ep.bias = bias; d.ep.bias_n = H;
+    shapes.push_back({0, d, 0});
+  }
+  {  // 1: update, ReLU(U W_U + b) in FP32 and BF16
+    TcDesc d{}; d.M = Ng; d.N = H; d.K = 16 * H; d.node_dim = kNodeM;
+    d.A = M(U, 16 * H, Ng, 16 * H, false); d.B = M(Wu, H, 16 * H, H, true); d.stable = kStableB;
+    d.ep.C = C; d.ep.ldc = H; d.ep.bias = bias; d.ep.bias_n = H; d.ep.relu = true; d.ep.C16 = D3; d.ep.ld16 = H;
+    shapes.push_back({1, d, 0});
+  }
+  {  // 2: dW_U = U^T g (side stream: half the SMs)
+    TcDesc d{}; d.M = 16 * H; d.N = H; d.K = Ng; d.node_dim = kNodeK;
+    d.A = M(U, 16 * H, Ng, 16 * H, true); d.B = M(G5 + 2 * H, 5 * H, Ng, H, true); d.stable = kStableA;
+    d.ep.C = C; d.ep.ldc = H;
+    shapes.push_back({2, d, std::max(1, num_sms() / 2)});
+  }
+  {  // 3: dagg = [amp g | att g | g] Wd^T
+    TcDesc d{}; d.M = Ng; d.N = 5 * H; d.K = K3; d.node_dim = kNodeM;
+    d.A = M(G5, 5 * H, Ng, 3 * H, false); d.B = M(Wd, 3 * H, 5 * H, 3 * H, false); d.stable = kStableB;
+    d.ep.C = C; d.ep.ldc = 5 * H;
+    shapes.push_back({3, d, 0});
+  }
+  {  // 4: dW_M = x^T [dP | dQ] (side stream)
+    TcDesc d{}; d.M = H; d.N = 2 * H; d.K = Ng; d.node_dim = kNodeK;
+    d.A = M(U, 16 * H, Ng, H, true); d.B = M(G5 + 3 * H, 5 * H, Ng, 2 * H, true); d.stable = kStableA;
+    d.ep.C = C; d.ep.ldc = 2 * H;
+    shapes.push_back({4, d, std::max(1, num_sms() / 2)});
+  }
+  {  // 5: dx = [g | dP | dQ] Wx^T with the masked, scaled BF16 blocks
+    TcDesc d{}; d.M = Ng; d.N = H; d.K = K3; d.node_dim = kNodeM;
+    d.A = M(G5 + 2 * H, 5 * H, Ng, 3 * H, false); d.B = M(Wx, 3 * H, H, 3 * H, false); d.stable = kStableB;
+    d.ep.C = C; d.ep.ldc = H; d.ep.D3 = D3; d.ep.ld3 = 5 * H; d.ep.mask = mask; d.ep.ldm = H; d.ep.amp = amp;
+    d.ep.att = att;
+    shapes.push_back({5, d, 0});
+  }
+  const DevDims dims{dd};
+  auto emit = [&](int shape, const Plan &p, int K, double us, int is_default) {
+    if (*n_rows >= max_rows) return;
+    double *r = rows + 8 * (size_t)(*n_rows)++;
+    r[0] = shape; r[1] = p.BN; r[2] = p.ntiles; r[3] = p.splits; r[4] = p.cluster ? 1 : 0; r[5] = K; r[6] = us;
+    r[7] = is_default;
+  };
+  for (const StudyShape &sh : shapes) {
+    if (rc != GCNN_OK) break;
+    const GemmWorkspace w{ws_p, wsf, 32, sh.max_ctas};
+    const int sms = sh.max_ctas > 0 ? sh.max_ctas : num_sms();
+    if (mode == 0) {  // the planner's plan, then every plan of the planner's search space
+      Plan used{};
+      double us = 0.0;
+      rc = study_time(sh, dims, w, err, s, nullptr, &used, &us);
+      if (rc == GCNN_OK) emit(sh.id, used, sh.d.K, us, 1);
+      const int mt = (sh.d.M + BM - 1) / BM, kt = (sh.d.K + BK - 1) / BK;
+      for (int bn = 16; bn <= kMaxBN && rc == GCNN_OK; bn += 16) {
+        const int nt = (sh.d.N + bn - 1) / bn;
+        if (nt > 1 && bn * (nt - 1) >= sh.d.N) continue;
+        for (int sp = 1; sp <= std::min(kt, 8) && rc == GCNN_OK; ++sp) {
+          if (mt * nt * sp > sms) break;
+          for (int cl = 0; cl <= 1 && rc == GCNN_OK; ++cl) {
+            if (cl && (sp < 2 || sp > kMaxCluster || mt * nt > g_capacity[sh.d.ep.D3 ? 1 : 0][sp])) continue;
+            if (!cl && sp > 1 && (size_t)sp * sh.d.M * sh.d.N > wsf) continue;
+            const Plan f{bn, nt, sp, cl == 1};
+            rc = study_time(sh, dims, w, err, s, &f, &used, &us);
+            if (rc == GCNN_OK) emit(sh.id, used, sh.d.K, us, 0);
+          }
+        }
+      }
+    } else if (sh.id == 1) {  // the update shape: time against K at tile widths without split
+      for (int bn : {32, 64, 112, 128, 208, 256}) {
+        const int nt = (sh.d.N + bn - 1) / bn;
+        for (int k = 64; k <= sh.d.K && rc == GCNN_OK; k = k < 512 ? 2 * k : k + 512) {
+          StudyShape t = sh;
+          t.d.K = k;
+          t.d.A.cols = std::min(sh.d.A.cols, k);
+          t.d.B.rows = std::min(sh.d.B.rows, k);
+          const Plan f{bn, nt, 1, false};
+          Plan used{};
+          double us = 0.0;
+          rc = study_time(t, dims, w, err, s, &f, &used, &us);
+          if (rc == GCNN_OK) emit(sh.id, used, k, us, 0);
+        }
+      }
+    }
+  }
+  unsigned herr = 0;
+  if (rc == GCNN_OK && (cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost) != cudaSuccess || herr))
+    rc = set_error(GCNN_EDEVICE, "gemm study: device error word 0x%x", herr);
+  if (s) cudaStreamSynchronize(s);
+  for (void *p : {(void *)U, (void *)G5, (void *)W, (void *)D3, (void *)C, (void *)F, (void *)ws_p, (void *)dd,
+                  (void *)err})
+    if (p) cudaFree(p);
+  if (s) cudaStreamDestroy(s);
+  return rc;
 }
 
 // ---------------------------------------------------------------- casts

@@ -265,6 +265,8 @@ struct TcDesc {
 
 int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned *err, cudaStream_t s);
 size_t gemm_tc_workspace_floats(int M, int N, int K);
+// Timing study of the training step's BF16 GEMM shapes (gcnn_gemm_study).
+int gemm_tc_study(int n_atoms, int H, int mode, double *rows, int max_rows, int *n_rows);
 // dst[i] = bf16(src[i]) (round to nearest even)
 int launch_cast_bf16(int64_t n, const float *src, uint16_t *dst, cudaStream_t s);
 // BF16 weight layouts of one layer for the backward GEMMs (see gemm_tc.cu)

@@ -106,3 +106,20 @@ def test_overlapped_backward_matches_serial(tmp_path):
     assert np.array_equal(res[0][0], res[1][0])
     assert np.array_equal(res[0][1], res[1][1])
     assert np.array_equal(res[0][2], res[1][2])
+
+
+def test_gemm_study_times_every_shape():
+    """gcnn_gemm_study (measurement support) times the six GEMM shapes of a step
+    under the planner's plan and under its search space, and the update shape
+    against K; a bad size is refused."""
+    import paper_2207_11333_gb300 as g
+    rows = g.gemm_study(512, 32, 0)
+    for name in g.GEMM_SHAPES:
+        mine = [r for r in rows if r["shape"] == name]
+        assert sum(r["planner"] for r in mine) == 1 and len(mine) > 1, name
+        assert all(0.0 < r["us"] < 1e4 for r in mine)
+    sweep = g.gemm_study(512, 32, 1)
+    assert {r["BN"] for r in sweep} == {32, 64, 112, 128, 208, 256}
+    assert all(r["shape"] == "update" and r["splits"] == 1 for r in sweep)
+    with pytest.raises(g.GcnnError, match="EINVAL"):
+        g.gemm_study(512, 30, 0)
