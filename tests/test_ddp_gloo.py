@@ -12,6 +12,7 @@ import os
 import socket
 
 import numpy as np
+import pytest
 import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
@@ -171,3 +172,68 @@ def test_sampler_and_buckets_on_the_host():
     assert len(s2) == 0                      # a tail of fewer graphs than processes is dropped
     s[0].set_epoch(1)
     assert not np.array_equal(s[0].order, s[1].order)
+
+
+def _post_and_exit(q, msg):
+    """Deliver msg, then end the process without the process group's shutdown
+    (which would wait on the departed peer)."""
+    q.put(msg)
+    q.close()
+    q.join_thread()
+    os._exit(0)
+
+
+DROP_TIMEOUT_S = 4.0
+
+
+def _dropout_main(rank, world, port, q, how):
+    import datetime
+    import time
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=DROP_TIMEOUT_S))
+    d, gs, st, delta, p = _data()
+    sampler = ShardedSampler(G_ALL, LOCAL_BATCH, world, rank, seed=11, node_counts=np.diff(gs.node_ptr))
+    ctx = OracleContext(d, st, delta, p)
+    tr = DataParallelTrainer(ctx, None, sampler)
+    tr.step(0, 1e-3)
+    if rank == 1:                       # leaves between steps, nothing in flight
+        if how == "stalls":             # alive, but never joins the next exchange
+            time.sleep(3 * DROP_TIMEOUT_S)
+        _post_and_exit(q, (1, "left", 0.0, 0.0, ""))
+    before = ctx.p.copy()
+    t0 = time.monotonic()
+    try:
+        tr.step(1, 1e-3)
+        msg = (0, "no error", time.monotonic() - t0, 0.0, "")
+    except RuntimeError as e:
+        msg = (0, "error", time.monotonic() - t0, float(np.max(np.abs(ctx.p - before))), str(e)[:200])
+    _post_and_exit(q, msg)
+
+
+@pytest.mark.parametrize("how", ["exits", "stalls"])
+def test_rank_that_drops_out_fails_the_next_exchange_on_the_host(how):
+    """A rank leaves between steps (fault injected on the host): it exits, or it
+    stays alive and never joins the next exchange.  The other rank's next step
+    raises on the host, at once when the peer's connection closes and after the
+    process group's timeout when it stalls, and leaves its parameters as they
+    were: the optimizer step never runs on a partial sum."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_dropout_main, args=(r, 2, port, q, how)) for r in range(2)]
+    for pr in procs:
+        pr.start()
+    res = {}
+    for _ in procs:
+        r, what, secs, moved, why = q.get(timeout=120)
+        res[r] = (what, secs, moved, why)
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    assert res[1][0] == "left"
+    what, secs, moved, why = res[0]
+    assert what == "error", res[0]
+    assert secs < (1.0 if how == "exits" else 3 * DROP_TIMEOUT_S), res[0]
+    if how == "stalls":
+        assert secs >= 0.9 * DROP_TIMEOUT_S, res[0]
+    assert moved == 0.0
