@@ -54,8 +54,9 @@ def dataset():
     return gs
 
 
-def epoch_order(epoch: int = 0) -> np.ndarray:
-    return np.random.default_rng(SEED_ORDER + 1000 * epoch).permutation(N_TRAIN).astype(np.int64)
+def epoch_order(epoch: int = 0, replicate: int = 0) -> np.ndarray:
+    seed = SEED_ORDER + 1000 * epoch + 100_000 * replicate
+    return np.random.default_rng(seed).permutation(N_TRAIN).astype(np.int64)
 
 
 def gemm_flops(n_nodes: int) -> float:
@@ -735,12 +736,14 @@ def recompute_study(g, precision: str, steps: int = 20):
 
 
 # ------------------------------------------------------------------ precision study
-def precision_study(g, epochs: int, lr: float):
+def precision_study(g, epochs: int, lr: float, seeds: int = 1):
     """FP32 and BF16 paths trained from the same initial parameters on the same epoch
     orders of the 200k-graph set, the learning rate decayed over the run by a half
     cosine from `lr` to zero (so that the last epochs settle instead of moving with
-    the step size); training MSE per epoch and MAE on the held-out 20k, with the
-    mean over the last three epochs as the comparison figure."""
+    the step size); training MSE per epoch and MAE on the held-out 20k.  With
+    seeds > 1 the pair is trained again from other initial parameters and epoch
+    orders, and the comparison figure is the relative difference of the two
+    paths' final held-out MAE, averaged over the seeds, with its standard error."""
     import torch
     wl = Workload(g, 0, 1)
     held = np.arange(N_TRAIN, N_TRAIN + N_HELDOUT, dtype=np.int64)
@@ -749,18 +752,19 @@ def precision_study(g, epochs: int, lr: float):
     Ec = max(wl.Ec, (max(s[1] for s in hs) + 511) // 512 * 512)
     y_held = wl.y[held].astype(np.float64)
     out = {"epochs": epochs, "train_graphs": N_TRAIN, "heldout_graphs": N_HELDOUT, "batch": BATCH, "lr": lr,
-           "lr_schedule": "half cosine from lr to 0 over all steps"}
+           "lr_schedule": "half cosine from lr to 0 over all steps", "seeds": seeds}
     steps_per_epoch = (N_TRAIN + BATCH - 1) // BATCH
     total = epochs * steps_per_epoch
-    for prec in ("fp32", "bf16"):
+
+    def train(prec, r):
         c = g.Context(g.make_config(H, L, BATCH, Nc, Ec, delta=wl.delta,
                                     precision=g.PREC_BF16 if prec == "bf16" else g.PREC_FP32))
-        c.set_params(synth.init_params(SEED_STUDENT, H, L))
+        c.set_params(synth.init_params(SEED_STUDENT + 100 * r, H, L))
         pred = torch.empty(N_HELDOUT, device="cuda")
         hist = []
         t0 = time.perf_counter()
         for ep in range(epochs):
-            order = epoch_order(ep)
+            order = epoch_order(ep, r)
             c.set_order(wl.st, order)
             acc = torch.zeros(3, dtype=torch.float64, device="cuda")
             for j, i in enumerate(range(0, N_TRAIN, BATCH)):
@@ -773,10 +777,18 @@ def precision_study(g, epochs: int, lr: float):
             err = pred.cpu().numpy().astype(np.float64) - y_held
             hist.append({"epoch": ep + 1, "train_mse": a[0] / a[2], "train_mae": a[1] / a[2],
                          "heldout_mae": float(np.mean(np.abs(err))), "heldout_rmse": float(np.sqrt(np.mean(err ** 2)))})
-            log(f"[precision] {prec} epoch {ep + 1}: {hist[-1]}")
+            log(f"[precision] seed {r} {prec} epoch {ep + 1}: {hist[-1]}")
         c.check()
-        out[prec] = {"history": hist, "seconds": time.perf_counter() - t0}
         c.close()
+        return {"history": hist, "seconds": time.perf_counter() - t0}
+
+    reps = []
+    for r in range(seeds):
+        run = {p: train(p, r) for p in ("fp32", "bf16")}
+        if r == 0:
+            out.update(run)
+        f32, f16 = run["fp32"]["history"][-1]["heldout_mae"], run["bf16"]["history"][-1]["heldout_mae"]
+        reps.append({"seed": r, "fp32_heldout_mae": f32, "bf16_heldout_mae": f16, "rel_diff": (f16 - f32) / f32})
     h32, h16 = out["fp32"]["history"], out["bf16"]["history"]
     out["final_train_mse_rel_diff"] = (h16[-1]["train_mse"] - h32[-1]["train_mse"]) / h32[-1]["train_mse"]
     out["final_heldout_mae_rel_diff"] = (h16[-1]["heldout_mae"] - h32[-1]["heldout_mae"]) / h32[-1]["heldout_mae"]
@@ -784,6 +796,12 @@ def precision_study(g, epochs: int, lr: float):
     out["best_heldout_mae_rel_diff"] = (b16 - b32) / b32
     m32, m16 = (float(np.mean([h["heldout_mae"] for h in hh[-3:]])) for hh in (h32, h16))
     out["last3_heldout_mae"] = {"fp32": m32, "bf16": m16, "rel_diff": (m16 - m32) / m32}
+    d = np.array([x["rel_diff"] for x in reps])
+    out["replicates"] = reps
+    out["final_heldout_mae_rel_diff_over_seeds"] = {
+        "mean": float(d.mean()), "std_err": float(d.std(ddof=1) / np.sqrt(len(d))) if len(d) > 1 else None,
+        "fp32_mean": float(np.mean([x["fp32_heldout_mae"] for x in reps])),
+        "bf16_mean": float(np.mean([x["bf16_heldout_mae"] for x in reps]))}
     return out
 
 
@@ -1133,6 +1151,7 @@ def main():
     ap.add_argument("--atoms", type=int, default=2304, help="batch atoms of the GEMM study (128 molecules of 18)")
     ap.add_argument("--reps", type=int, default=5, help="timed launches per operator in the aggregation study")
     ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--seeds", type=int, default=1, help="precision study: initial parameters and orders to repeat over")
     ap.add_argument("--lr", type=float, default=1e-4, help="learning rate of the precision study")
     ap.add_argument("--no-studies", dest="studies", action="store_false",
                     help="skip the large-batch aggregation and recompute measurements")
@@ -1145,7 +1164,7 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         import paper_2207_11333_gb300 as g
-        print(json.dumps({"study": "precision", **precision_study(g, args.epochs, args.lr)}), flush=True)
+        print(json.dumps({"study": "precision", **precision_study(g, args.epochs, args.lr, args.seeds)}), flush=True)
         return 0
     if args.study == "loading":
         import torch
