@@ -961,7 +961,7 @@ def gemm_study(args):
                          "mac_per_cycle_per_sm": float(mac_per_cycle),
                          "times_us": {str(r["K"]): r["us"] for r in sweep if r["BN"] == bn}}
     print(json.dumps({"study": "gemm", "atoms": args.atoms, "hidden": H, "shapes": shapes,
-                      "update_k_sweep_no_split": fits,
+                      "update_k_sweep_no_split": fits, "plans": plans,
                       "note": "us per launch, best of 5 replays of a 20-launch CUDA graph; k-tile = 64 of K; "
                               "MAC/cycle at 2070 MHz for a 128-row tile"}), flush=True)
     return 0

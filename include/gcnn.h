@@ -422,12 +422,13 @@ int gcnn_ffma_peak(int32_t iters, double *tflops);
  * batch of n_atoms atoms and hidden width `hidden` (a multiple of 8, at most
  * 256), on the calling thread's device; synchronous.  Six shapes: 0 message
  * (x [A | B]), 1 update (U W_U), 2 dW_U, 3 dagg, 4 dW_M, 5 dx (dW_U and dW_M
- * limited to half the SMs, as on the backward's second stream).  Each time is
- * the best of five replays of a CUDA graph of 20 launches, in microseconds per
- * launch.  mode 0: per shape, the planner's own plan (flag 1), then every plan
- * of its search space: tile width BN (16..256), K-splits, cluster or partial
- * buffer.  mode 1: the update shape at K = 64 .. 16 hidden without split-K,
- * at tile widths 32, 64, 112, 128, 208 and 256.  Each result row is 8
+ * with the CTA limit of the backward's second stream).
+ * Each time is the best of five replays of a CUDA graph of 20 launches, in
+ * microseconds per launch.  mode 0: per shape, the planner's own plan (flag
+ * 1), then every plan of its search space: tile width BN (16..128), K-splits,
+ * cluster or partial buffer, up to two CTAs per SM.  mode 1: the update shape
+ * at K = 64 .. 16 hidden without split-K, at tile widths 32, 64, 112 and 128.
+ * Each result row is 8
  * doubles: shape, BN, n-tiles, splits, cluster (0/1), K, microseconds, planner
  * flag; rows beyond max_rows are dropped.  Not a paper operation: measurement
  * support.  GCNN_EINVAL for bad sizes; GCNN_EDEVICE if a wait timed out. */

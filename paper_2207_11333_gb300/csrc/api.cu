@@ -345,10 +345,7 @@ int gcnn_create(const gcnn_config *cfg, void *stream, gcnn_ctx **out) {
   if (side) {
     c->ws_side = c->ws;
     c->ws_side.partial = (float *)(b + o_ws2);
-    // side GEMMs take at most half the SMs, leaving the rest to the
-    // data-gradient chain they overlap (best of 38 / 50 / 60 / 76 / 100 /
-    // 120 / all on the bench workload)
-    c->ws_side.max_ctas = std::max(1, num_sms() / 2);
+    c->ws_side.max_ctas = side_gemm_ctas();
     c->dPQ2 = (float *)(b + o_dPQ2);
   }
   if (bf) {

@@ -12,7 +12,8 @@
 // the batch's true node count inside the array are cleared in shared memory
 // before the MMA when K runs over nodes.
 //
-// Roles (256 threads, one 128 x BN output tile per CTA, BN <= 256):
+// Roles (256 threads, one 128 x BN output tile per CTA, BN <= 128; two CTAs
+// fit one SM, whose tensor core then runs both CTAs' MMAs side by side):
 //   warp 0   one lane issues the TMA loads of a stage after the stage's
 //            "empty" barrier fired, with the byte count on its "full" barrier
 //   warp 1   waits "full", issues four tcgen05.mma (K = 16 each) and commits
@@ -35,10 +36,19 @@
 namespace gcnn {
 namespace {
 
-constexpr int BM = 128, BK = 64, STAGES = 4, kThreads = 256;
-constexpr int kMaxBN = 256;
+constexpr int BM = 128, BK = 64, STAGES = 3, kThreads = 256;
+constexpr int kMaxBN = 128;
+// Co-resident CTAs per SM: about 100 KB of shared memory and at most 128
+// registers per thread each.  One CTA issues its MMAs at a latency-bound rate
+// well below the SM's tensor throughput for tiles up to 128 wide; a second
+// CTA on the same SM, from another stream's GEMM or from the next wave of a
+// large grid, nearly doubles the SM's rate.  A launch is planned for at most
+// one CTA per SM: within one short launch a second CTA per SM only adds its
+// fixed costs (measured).
+constexpr int kCtasPerSm = 2;
+constexpr int kDrain = 4;  // 8-column TMEM loads in flight per thread in the epilogue (register budget)
 constexpr int kATileBytes = BM * BK * 2;        // 16 KB
-constexpr int kBTileBytes = kMaxBN * BK * 2;    // 32 KB
+constexpr int kBTileBytes = kMaxBN * BK * 2;    // 16 KB
 constexpr int kStageBytes = kATileBytes + kBTileBytes;
 // masked-gradient epilogue: ReLU-mask bits (8 words per tile row) and the
 // tile rows' degree scalers, prefetched during the main loop
@@ -362,7 +372,7 @@ __device__ __forceinline__ void clear_k_rows(uint8_t *tile, int atoms, int from,
 // cluster; the split-K partial tiles are summed through distributed shared
 // memory instead of a partial buffer and a reduction kernel.
 template <int EPI, bool CL>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
 tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, float *__restrict__ partial, int splits,
                 int kps, int BN, unsigned *err) {
   extern __shared__ uint8_t smem_raw[];
@@ -542,22 +552,22 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
       const int r = 32 * (warp & 3) + lane;
       const int groups = BN / 8, half = (groups + 1) / 2;
       const int g0 = warp < 4 ? 0 : half, g1 = warp < 4 ? half : groups;
-      for (int gb = g0; gb < g1; gb += 8) {
-        uint32_t v[8][8];
-        const int cnt = min(8, g1 - gb);
+      for (int gb = g0; gb < g1; gb += kDrain) {
+        uint32_t v[kDrain][8];
+        const int cnt = min(kDrain, g1 - gb);
         if (nk > 0) {
 #pragma unroll
-          for (int u = 0; u < 8; ++u)
+          for (int u = 0; u < kDrain; ++u)
             if (u < cnt) tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((gb + u) * 8), v[u]);
           tmem_wait_ld();
         } else {
 #pragma unroll
-          for (int u = 0; u < 8; ++u)
+          for (int u = 0; u < kDrain; ++u)
 #pragma unroll
             for (int q = 0; q < 8; ++q) v[u][q] = 0u;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < kDrain; ++u) {
           if (u >= cnt) break;
           float *p = S + (size_t)r * RS + (gb + u) * 8;
           *reinterpret_cast<uint4 *>(p) = make_uint4(v[u][0], v[u][1], v[u][2], v[u][3]);
@@ -715,9 +725,9 @@ struct Plan {
 // tiles in global memory (a separate kernel) or, with the splits of a tile
 // in one cluster, reads of the other CTAs' staged tiles (~50 GB/s per SM) and
 // two cluster barriers, each CTA then storing its share of the rows.  Among
-// widths BN (multiple of 16, <= 256) and splits whose grid fits one wave (one
-// CTA per SM; clusters within their co-resident capacity), take the smallest
-// estimate; grids larger than a wave use the widest tiles and no split.
+// widths BN (multiple of 16, <= 128) and splits whose grid fits one CTA per
+// SM (clusters within their co-resident capacity), take the smallest
+// estimate; grids larger than that use the widest tiles and no split.
 // out_bytes: epilogue bytes per output element; b_mn: B tiles are MN-major
 // (loaded in 64-column atoms); d3: masked-gradient epilogue.
 Plan choose(int M, int N, int K, int max_splits, int max_ctas, double out_bytes, bool b_mn, bool d3) {
@@ -811,6 +821,8 @@ int run_planned(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
   const double out_bytes = (e.C ? 4.0 : 0.0) + (e.C16 ? 2.0 : 0.0) + (e.D3 ? 10.0 : 0.0);
   Plan plan = choose(d.M, d.N, d.K, ws.max_splits, ws.max_ctas, out_bytes, d.B.mn_major, e.D3 != nullptr);
   if (force) plan = *force;
+  if (plan.BN < 16 || plan.BN > kMaxBN || plan.BN % 16 || plan.ntiles < 1 || plan.splits < 1)
+    return set_error(GCNN_EINVAL, "tc gemm: tile width must be a multiple of 16 in [16, %d]", kMaxBN);
   if (plan.splits > 1 && !plan.cluster && (size_t)plan.splits * d.M * d.N > ws.floats) plan.splits = 1;
   if (used) *used = plan;
   const int BN = plan.BN, ntiles = plan.ntiles, splits = plan.splits;
@@ -839,6 +851,10 @@ int run_planned(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
 int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned *err, cudaStream_t s) {
   return run_planned(d, dims, ws, err, s, nullptr, nullptr);
 }
+
+// One CTA per SM: with two CTA slots per SM the second stream's GEMM and the
+// main stream's run side by side on every SM instead of splitting the SMs.
+int side_gemm_ctas() { return num_sms(); }
 
 size_t gemm_tc_workspace_floats(int M, int N, int K) {
   const int sp = max_splits_of(M, K);
@@ -939,11 +955,11 @@ int gemm_tc_study(int n_atoms, int H, int mode, double *rows, int max_rows, int 
     d.ep.C = C; d.ep.ldc = H; d.ep.bias = bias; d.ep.bias_n = H; d.ep.relu = true; d.ep.C16 = D3; d.ep.ld16 = H;
     shapes.push_back({1, d, 0});
   }
-  {  // 2: dW_U = U^T g (side stream: half the SMs)
+  {  // 2: dW_U = U^T g (side stream)
     TcDesc d{}; d.M = 16 * H; d.N = H; d.K = Ng; d.node_dim = kNodeK;
     d.A = M(U, 16 * H, Ng, 16 * H, true); d.B = M(G5 + 2 * H, 5 * H, Ng, H, true); d.stable = kStableA;
     d.ep.C = C; d.ep.ldc = H;
-    shapes.push_back({2, d, std::max(1, num_sms() / 2)});
+    shapes.push_back({2, d, side_gemm_ctas()});
   }
   {  // 3: dagg = [amp g | att g | g] Wd^T
     TcDesc d{}; d.M = Ng; d.N = 5 * H; d.K = K3; d.node_dim = kNodeM;
@@ -955,7 +971,7 @@ int gemm_tc_study(int n_atoms, int H, int mode, double *rows, int max_rows, int 
     TcDesc d{}; d.M = H; d.N = 2 * H; d.K = Ng; d.node_dim = kNodeK;
     d.A = M(U, 16 * H, Ng, H, true); d.B = M(G5 + 3 * H, 5 * H, Ng, 2 * H, true); d.stable = kStableA;
     d.ep.C = C; d.ep.ldc = 2 * H;
-    shapes.push_back({4, d, std::max(1, num_sms() / 2)});
+    shapes.push_back({4, d, side_gemm_ctas()});
   }
   {  // 5: dx = [g | dP | dQ] Wx^T with the masked, scaled BF16 blocks
     TcDesc d{}; d.M = Ng; d.N = H; d.K = K3; d.node_dim = kNodeM;
@@ -996,7 +1012,7 @@ int gemm_tc_study(int n_atoms, int H, int mode, double *rows, int max_rows, int 
         }
       }
     } else if (sh.id == 1) {  // the update shape: time against K at tile widths without split
-      for (int bn : {32, 64, 112, 128, 208, 256}) {
+      for (int bn : {32, 64, 112, 128}) {
         const int nt = (sh.d.N + bn - 1) / bn;
         for (int k = 64; k <= sh.d.K && rc == GCNN_OK; k = k < 512 ? 2 * k : k + 512) {
           StudyShape t = sh;

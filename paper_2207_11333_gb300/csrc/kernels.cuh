@@ -264,6 +264,10 @@ struct TcDesc {
 };
 
 int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned *err, cudaStream_t s);
+// CTA limit of the weight-gradient GEMMs, which run on the backward's second
+// stream beside the data-gradient chain (the same limit in the serial backward,
+// so that both pick the same plans)
+int side_gemm_ctas();
 size_t gemm_tc_workspace_floats(int M, int N, int K);
 // Timing study of the training step's BF16 GEMM shapes (gcnn_gemm_study).
 int gemm_tc_study(int n_atoms, int H, int mode, double *rows, int max_rows, int *n_rows);

@@ -329,11 +329,11 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
   const float *pq = pq_at(c, l), *h = xs_at(c, l + 1);
   float *agg = agg_at(c, l);
   uint16_t *G = c->G5[cur];
-  // the weight-gradient GEMMs plan with the side lane's half-SM cap in both
+  // the weight-gradient GEMMs plan with the side lane's CTA limit in both
   // modes, so the overlapped and the serial backward pick the same split-K
   // plans and give the same results bit for bit
   GemmWorkspace capped = c->ws;
-  capped.max_ctas = std::max(1, num_sms() / 2);
+  capped.max_ctas = side_gemm_ctas();
   const Lane lane = ov ? Lane{c->side, &c->ws_side} : Lane{c->stream, &capped};
   cudaEvent_t fork = ov ? c->side_ev[3 * l] : nullptr, mid = ov ? c->side_ev[3 * l + 1] : nullptr;
   cudaEvent_t done = ov ? c->side_ev[3 * l + 2] : nullptr;
