@@ -1096,7 +1096,8 @@ def run_ddp(g, wl, args, world, rank, local, dist, flush, loss_acc):
             "config": {"workload": WORKLOAD, "graphs": N_TRAIN, "batch_graphs_per_gpu": BATCH, "hidden": H,
                        "layers": L, "head": "200-200-1", "precision": args.precision,
                        "parallelism": f"ddp x{world}: gradient all-reduce (NCCL) per layer bucket, overlapped "
-                                      "with the backward; eager launches (no captured graph)",
+                                      "with the backward; forward + backward from one captured graph, the "
+                                      "all-reduces and AdamW launched after it",
                        "l2": "256 MB buffer written between steps, outside the per-step CUDA events",
                        "wall_ms_per_step_incl_flush": 1e3 * r["wall_s"] / args.steps},
             "clocks": r["clocks"], "gpu_launches": r["kernels_per_step"] * args.steps}
