@@ -129,14 +129,34 @@ __global__ void __launch_bounds__(kThreads, 4)
 aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row_ptr,
                      const int *__restrict__ col, const float *__restrict__ PQ,
                      float *__restrict__ agg, float eps, unsigned *err, uint16_t *__restrict__ S16, int ld16,
-                     const float *__restrict__ amp, const float *__restrict__ att, Bonds bonds) {
-  pdl_entry(GCNN_K_AGG_FWD);
+                     const float *__restrict__ amp, const float *__restrict__ att, Bonds bonds, int early) {
   const int H4 = H >> 2;
-  const int N = min(n_cap, dims.nodes(n_cap));
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // the batch's sizes, the row's CSR range and its first sources (and the
+  // degree scalers) come from the collator; with `early` they are read
+  // before the dependency wait, overlapping the previous kernel's tail
+  int N = 0, i = 0, c = 0, r0 = 0, r1 = 0;
+  int j[kCache];
+  float s_amp = 0.f, s_att = 0.f;
+  auto load_row = [&]() {
+    N = min(n_cap, dims.nodes(n_cap));
+    if (t >= (long long)N * H4) return;
+    i = (int)(t / H4);
+    c = (int)(t % H4) * 4;
+    r0 = row_ptr[i];
+    r1 = row_ptr[i + 1];
+    if (r1 > r0 && r0 >= 0)
+#pragma unroll
+      for (int k = 0; k < kCache; ++k) j[k] = col[min(r0 + k, r1 - 1)];
+    if (B16) {
+      s_amp = amp[i];
+      s_att = att[i];
+    }
+  };
+  if (early) load_row();
+  pdl_entry(GCNN_K_AGG_FWD);
+  if (!early) load_row();
   if (t >= (long long)N * H4) return;
-  const int i = (int)(t / H4), c = (int)(t % H4) * 4;
-  const int r0 = row_ptr[i], r1 = row_ptr[i + 1];
   const int d = r1 - r0;
   float *out = F32 ? agg + (size_t)i * kAgg * H + c : nullptr;
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -151,10 +171,7 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
   }
   // every load of the row is issued before the arithmetic: the first kCache
   // sources (indices clamped into the row, so short rows repeat their last
-  // edge and use only the first d), then P and the gathered Q rows
-  int j[kCache];
-#pragma unroll
-  for (int k = 0; k < kCache; ++k) j[k] = col[min(r0 + k, r1 - 1)];
+  // edge and use only the first d; read above), then P and the gathered Q rows
   const float4 P = ld4(PQ + (size_t)i * 2 * H + c);
   float4 mc[kCache];
   if (gather_first<EDGE>(PQ, j, i, N, H, c, P, mc, bonds, r0, r1)) flag(err, kErrIndex);
@@ -192,7 +209,7 @@ aggregate_fwd_kernel(int n_cap, int H, DevDims dims, const int *__restrict__ row
   }
   if (B16) {  // scaler-major: identity, amplification, attenuation
     const float4 vv[kAgg] = {s, mean, mn, mx, sd};
-    const float sc[kScalers] = {1.f, amp[i], att[i]};
+    const float sc[kScalers] = {1.f, s_amp, s_att};
     uint16_t *o = S16 + (size_t)i * ld16 + c;
 #pragma unroll
     for (int q = 0; q < kScalers; ++q)
@@ -213,6 +230,27 @@ __device__ __forceinline__ float route(float m, float base, float mn, float cmin
 
 constexpr int kEdgeThreads = 128;  // five blocks of 128 per SM at this kernel's register count
 
+// CSR range of node i's row and the sources and reverse slots of its first
+// kCache edges (clamped into the row); the slots are read only for a valid range.
+struct RowIdx {
+  int r0, r1;
+  int j[kCache], re[kCache];
+};
+
+__device__ __forceinline__ RowIdx load_row_idx(int i, int E, const int *__restrict__ row_ptr,
+                                               const int *__restrict__ col, const int *__restrict__ rev) {
+  RowIdx x;
+  x.r0 = row_ptr[i];
+  x.r1 = row_ptr[i + 1];
+  if (x.r1 > x.r0 && x.r0 >= 0 && x.r1 <= E)
+#pragma unroll
+    for (int k = 0; k < kCache; ++k) {
+      x.j[k] = col[min(x.r0 + k, x.r1 - 1)];
+      x.re[k] = rev[min(x.r0 + k, x.r1 - 1)];
+    }
+  return x;
+}
+
 // Backward of one (node i, 4 channels at c): recomputes the row's messages,
 // takes the forward's statistics (stored in agg, or recomputed in the
 // forward's order when agg is null), routes dagg to every edge of the row
@@ -220,13 +258,13 @@ constexpr int kEdgeThreads = 128;  // five blocks of 128 per SM at this kernel's
 // STATS: 1 = statistics stored in agg, 0 = recomputed, -1 = decided at run
 // time by agg != null (one code path for both, fewer registers)
 template <int STATS, bool EDGE, class ToSlot>
-__device__ __forceinline__ float4 node_backward(int i, int c, int H, int N, int E, const int *__restrict__ row_ptr,
+__device__ __forceinline__ float4 node_backward(int i, int c, int H, int N, int E, const RowIdx &ix,
                                                 const int *__restrict__ col, const int *__restrict__ rev,
                                                 const float *__restrict__ PQ, const float *__restrict__ agg,
                                                 const float *__restrict__ dagg, float eps, unsigned *err,
                                                 const Bonds &bonds, ToSlot to_slot) {
   const bool STORED = STATS < 0 ? agg != nullptr : STATS == 1;
-  const int r0 = row_ptr[i], r1 = row_ptr[i + 1];
+  const int r0 = ix.r0, r1 = ix.r1;
   const int d = r1 - r0;
   float4 dP = make_float4(0.f, 0.f, 0.f, 0.f);
   if (d <= 0 || r0 < 0 || r1 > E) {
@@ -235,14 +273,10 @@ __device__ __forceinline__ float4 node_backward(int i, int c, int H, int N, int 
   }
   const float df = (float)d;
   // all loads of the row first (as in the forward): sources and reverse slots
-  // of the first kCache edges (clamped into the row), P, the stored statistics,
-  // the incoming gradient and the gathered Q rows
-  int j[kCache], re[kCache];
-#pragma unroll
-  for (int k = 0; k < kCache; ++k) {
-    j[k] = col[min(r0 + k, r1 - 1)];
-    re[k] = rev[min(r0 + k, r1 - 1)];
-  }
+  // of the first kCache edges (clamped into the row; in ix), P, the stored
+  // statistics, the incoming gradient and the gathered Q rows
+  const int(&j)[kCache] = ix.j;
+  const int(&re)[kCache] = ix.re;
   const float4 P = ld4(PQ + (size_t)i * 2 * H + c);
   float4 mean, mn, mx, sd;
   if (STORED) {
@@ -320,15 +354,23 @@ aggregate_bwd_edge_kernel(int n_cap, int e_cap, int H, DevDims dims, const int *
                           const float *__restrict__ PQ, const float *__restrict__ agg,
                           const float *__restrict__ dagg, float *__restrict__ dPQ,
                           float *__restrict__ dm, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16, float eps,
-                          Bonds bonds) {
-  pdl_entry(GCNN_K_AGG_BWD_EDGE);
+                          Bonds bonds, int early) {
   const int H4 = H >> 2;
-  const int N = min(n_cap, dims.nodes(n_cap));
-  const int E = min(e_cap, dims.edges(e_cap));
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // sizes and the row's indices (collator) before the dependency wait with `early`
+  int N = 0, E = 0;
+  RowIdx ix{};
+  auto load = [&]() {
+    N = min(n_cap, dims.nodes(n_cap));
+    E = min(e_cap, dims.edges(e_cap));
+    if (t < (long long)N * H4) ix = load_row_idx((int)(t / H4), E, row_ptr, col, rev);
+  };
+  if (early) load();
+  pdl_entry(GCNN_K_AGG_BWD_EDGE);
+  if (!early) load();
   if (t >= (long long)N * H4) return;
   const int i = (int)(t / H4), c = (int)(t % H4) * 4;
-  const float4 dP = node_backward<-1, EDGE>(i, c, H, N, E, row_ptr, col, rev, PQ, agg, dagg, eps, err, bonds,
+  const float4 dP = node_backward<-1, EDGE>(i, c, H, N, E, ix, col, rev, PQ, agg, dagg, eps, err, bonds,
                                              [&](int r, float4 g) {
     if (r >= 0 && r < E) st4(dm + (size_t)r * H + c, g);
     else flag(err, kErrIndex);
@@ -411,7 +453,8 @@ aggregate_bwd_fused_kernel(int g_cap, int n_cap, int e_cap, const int *__restric
   const int rows = kFusedThreads / w, row = threadIdx.x / w, cc = threadIdx.x % w, c = (c0 + cc) * 4;
   const int n_end = row < rows ? n1 : n0;
   for (int i = n0 + row; i < n_end; i += rows) {
-    const float4 dP = node_backward<STORED ? 1 : 0, false>(i, c, H, N, E, row_ptr, col, rev, PQ, agg, dagg, eps, err,
+    const float4 dP = node_backward<STORED ? 1 : 0, false>(i, c, H, N, E, load_row_idx(i, E, row_ptr, col, rev), col,
+                                                           rev, PQ, agg, dagg, eps, err,
                                                            Bonds{nullptr, nullptr, 0}, [&](int r, float4 g) {
       if (r < e0 || r >= e1) flag(err, kErrIndex);  // an edge leaving the graph
       else if (in_smem) s_dm[(r - e0) * cs4 + cc] = g;
@@ -440,15 +483,25 @@ aggregate_bwd_fused_kernel(int g_cap, int n_cap, int e_cap, const int *__restric
 __global__ void __launch_bounds__(kThreads)
 aggregate_bwd_gather_kernel(int n_cap, int e_cap, int H, DevDims dims,
                             const int *__restrict__ row_ptr, const float *__restrict__ dm,
-                            float *__restrict__ dPQ, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16) {
-  pdl_entry(GCNN_K_AGG_BWD_GATHER);
+                            float *__restrict__ dPQ, unsigned *err, uint16_t *__restrict__ dPQ16, int ld16,
+                            int early) {
   const int H4 = H >> 2;
-  const int N = min(n_cap, dims.nodes(n_cap));
-  const int E = min(e_cap, dims.edges(e_cap));
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // sizes and the row's range (collator) before the dependency wait with `early`
+  int N = 0, E = 0, r0 = 0, r1 = 0;
+  auto load = [&]() {
+    N = min(n_cap, dims.nodes(n_cap));
+    E = min(e_cap, dims.edges(e_cap));
+    if (t < (long long)N * H4) {
+      r0 = row_ptr[t / H4];
+      r1 = row_ptr[t / H4 + 1];
+    }
+  };
+  if (early) load();
+  pdl_entry(GCNN_K_AGG_BWD_GATHER);
+  if (!early) load();
   if (t >= (long long)N * H4) return;
   const int j = (int)(t / H4), c = (int)(t % H4) * 4;
-  int r0 = row_ptr[j], r1 = row_ptr[j + 1];
   if (r1 < r0 || r0 < 0 || r1 > E) { flag(err, kErrIndex); r1 = r0; }
   float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
@@ -517,36 +570,37 @@ int launch_bond_grad(int n_edges, int H, int F, int ld, DevDims dims, const floa
 int launch_aggregate_fwd(int n_nodes, int H, DevDims dims, const int *row_ptr, const int *col,
                          const float *PQ, float *agg, float eps, unsigned *err, cudaStream_t s,
                          uint16_t *S16, int ld16, const float *amp, const float *att, const float *eattr,
-                         const float *wE, int F) {
+                         const float *wE, int F, bool idx_early) {
   if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
   if (F < 0 || (F > 0 && (!eattr || !wE))) return set_error(GCNN_EINVAL, "aggregate: bond features without data");
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
   using K = void (*)(int, int, DevDims, const int *, const int *, const float *, float *, float, unsigned *,
-                     uint16_t *, int, const float *, const float *, Bonds);
+                     uint16_t *, int, const float *, const float *, Bonds, int);
   static const K table[8] = {aggregate_fwd_kernel<false, false, false>, aggregate_fwd_kernel<false, true, false>,
                              aggregate_fwd_kernel<true, false, false>,  aggregate_fwd_kernel<true, true, false>,
                              aggregate_fwd_kernel<false, false, true>,  aggregate_fwd_kernel<false, true, true>,
                              aggregate_fwd_kernel<true, false, true>,   aggregate_fwd_kernel<true, true, true>};
   const K kernel = table[(F > 0 ? 4 : 0) + (agg ? 2 : 0) + (S16 ? 1 : 0)];
   GCNN_TRY(launch(kernel, ceil_div(work, kThreads), kThreads, 0, s, n_nodes, H, dims, row_ptr, col, PQ, agg, eps, err,
-                  S16, ld16, amp, att, Bonds{eattr, wE, F}));
+                  S16, ld16, amp, att, Bonds{eattr, wE, F}, idx_early ? 1 : 0));
   return GCNN_OK;
 }
 
 int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const int *row_ptr,
                          const int *col, const int *rev, const float *PQ, const float *agg,
                          const float *dagg, float *dPQ, float *scratch, float eps, unsigned *err,
-                         cudaStream_t s, uint16_t *dPQ16, int ld16, const float *eattr, const float *wE, int F) {
+                         cudaStream_t s, uint16_t *dPQ16, int ld16, const float *eattr, const float *wE, int F,
+                         bool idx_early) {
   if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
   if (F < 0 || (F > 0 && (!eattr || !wE))) return set_error(GCNN_EINVAL, "aggregate: bond features without data");
   if (n_nodes <= 0) return GCNN_OK;
   const long long work = (long long)n_nodes * (H / 4);
   GCNN_TRY(launch(F > 0 ? aggregate_bwd_edge_kernel<true> : aggregate_bwd_edge_kernel<false>, ceil_div(work, kEdgeThreads),
                   kEdgeThreads, 0, s, n_nodes, n_edges, H, dims, row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, err,
-                  dPQ16, ld16, eps, Bonds{eattr, wE, F}));
+                  dPQ16, ld16, eps, Bonds{eattr, wE, F}, idx_early ? 1 : 0));
   GCNN_TRY(launch(aggregate_bwd_gather_kernel, ceil_div(work, kThreads), kThreads, 0, s, n_nodes, n_edges, H, dims,
-                  row_ptr, (const float *)scratch, dPQ, err, dPQ16, ld16));
+                  row_ptr, (const float *)scratch, dPQ, err, dPQ16, ld16, idx_early ? 1 : 0));
   return GCNN_OK;
 }
 
@@ -560,13 +614,13 @@ int launch_aggregate_bwd_graphs(int n_graphs, int n_nodes, int n_edges, int H, D
                                 const int *row_ptr, const int *col, const int *rev, const float *PQ,
                                 const float *agg, const float *dagg, float *dPQ, float *scratch, int *chunks,
                                 float eps, unsigned *err, cudaStream_t s, uint16_t *dPQ16, int ld16,
-                                const float *eattr, const float *wE, int F, bool make_chunks) {
+                                const float *eattr, const float *wE, int F, bool make_chunks, bool idx_early) {
   if (H <= 0 || H % 4) return set_error(GCNN_EINVAL, "aggregate: hidden must be a positive multiple of 4");
   if (n_nodes <= 0 || n_graphs <= 0) return GCNN_OK;
   // with bond features the per-edge gradients are kept: their weight gradient reads them
   if (F > 0 || !aggregate_bwd_uses_fused(n_edges))
     return launch_aggregate_bwd(n_nodes, n_edges, H, dims, row_ptr, col, rev, PQ, agg, dagg, dPQ, scratch, eps, err, s,
-                                dPQ16, ld16, eattr, wE, F);
+                                dPQ16, ld16, eattr, wE, F, idx_early);
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {

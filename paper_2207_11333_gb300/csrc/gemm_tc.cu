@@ -219,17 +219,39 @@ __device__ __forceinline__ float4 ld_cluster4(uint32_t a, int rank) {
   return v;
 }
 
-// Element p of the staged tile summed over the cluster's `ranks` CTAs in rank
-// order (the K-splits of one output tile), or the CTA's own value.
-__device__ __forceinline__ float4 tile_sum(const float *p, int ranks) {
-  if (ranks == 1) return *reinterpret_cast<const float4 *>(p);
-  const uint32_t a = smem_u32(p);
-  float4 s = ld_cluster4(a, 0);
-  for (int z = 1; z < ranks; ++z) {
-    const float4 t = ld_cluster4(a, z);
-    s.x += t.x; s.y += t.y; s.z += t.z; s.w += t.w;
+// Rows r0, r0 + 8, r0 + 16, r0 + 24 (those below re) of the staged tile at
+// column cn, each summed over the cluster's `ranks` CTAs in rank order (the
+// K-splits of one output tile), or the CTA's own rows.  The four rows' loads
+// from rank z + 1 are issued before the sums of rank z, so a warp waits for
+// one remote-load latency per rank, not one per row and rank; the order of
+// the additions, and so every result bit, does not depend on this.
+__device__ __forceinline__ void rows_sum4(const float *S, int RS, int r0, int re, int cn, int ranks, float4 v[4]) {
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (ranks == 1) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      v[u] = r0 + 8 * u < re ? *reinterpret_cast<const float4 *>(S + (size_t)(r0 + 8 * u) * RS + cn) : zero;
+    return;
   }
-  return s;
+  uint32_t a[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) a[u] = smem_u32(S + (size_t)(r0 + 8 * u) * RS + cn);
+  float4 t[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    v[u] = r0 + 8 * u < re ? ld_cluster4(a[u], 0) : zero;
+    t[u] = r0 + 8 * u < re ? ld_cluster4(a[u], 1) : zero;
+  }
+  for (int z = 1; z < ranks; ++z) {
+    float4 n[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) n[u] = (z + 1 < ranks && r0 + 8 * u < re) ? ld_cluster4(a[u], z + 1) : zero;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      v[u].x += t[u].x; v[u].y += t[u].y; v[u].z += t[u].z; v[u].w += t[u].w;
+      t[u] = n[u];
+    }
+  }
 }
 
 // ---------------------------------------------------------------- tile stores
@@ -277,10 +299,7 @@ __device__ __forceinline__ void store_c(const float *S, int RS, int rb, int re, 
         if (n + q < e.bias_n) b[q] = e.bias[n + q];
     for (int r0 = rb + warp; r0 < re; r0 += 32) {
       float4 v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        v[u] = r0 + 8 * u < re ? tile_sum(S + (size_t)(r0 + 8 * u) * RS + cn, ranks)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
+      rows_sum4(S, RS, r0, re, cn, ranks, v);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (r0 + 8 * u >= re) break;
@@ -312,14 +331,13 @@ __device__ __forceinline__ void store_d3(const float *S, int RS, int rb, int re,
       float4 v[4];
       uint32_t mk[4];
       float am[4], at[4];
+      rows_sum4(S, RS, r0, re, cn, ranks, v);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int r = r0 + 8 * u;
-        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
         mk[u] = 0u;
         am[u] = at[u] = 0.f;
         if (r < re) {
-          v[u] = tile_sum(S + (size_t)r * RS + cn, ranks);
           mk[u] = mbits[r * kMaskWords + word] >> shift;
           am[u] = s_amp[r];
           at[u] = s_att[r];

@@ -42,11 +42,15 @@ int launch_collate(int G, const int64_t *ids, StoreView st, BatchBuf b, const fl
 // update GEMM.
 // With F > 0 the message carries the bond term sum_f eattr[e][f] wE[f]
 // (eattr: E rows of stride round_up(F, 4) in slot order, wE: F x H).
+// idx_early: the sizes in dims, the CSR arrays and the degree scalers were
+// written at least two launches before this one on the stream (the model's
+// own launch sequences after the collator), so the kernels read them before
+// their dependency wait; false for arrays a caller may just have written.
 int launch_aggregate_fwd(int n_nodes, int H, DevDims dims, const int *row_ptr, const int *col,
                          const float *PQ, float *agg, float eps, unsigned *err, cudaStream_t s,
                          uint16_t *S16 = nullptr, int ld16 = 0, const float *amp = nullptr,
                          const float *att = nullptr, const float *eattr = nullptr, const float *wE = nullptr,
-                         int F = 0);
+                         int F = 0, bool idx_early = false);
 // dPQ from dagg; scratch is E x H (per-edge message gradients).  With agg
 // null the forward's statistics are recomputed from the messages in the
 // forward kernel's order (bit-identical).
@@ -54,7 +58,7 @@ int launch_aggregate_bwd(int n_nodes, int n_edges, int H, DevDims dims, const in
                          const int *col, const int *rev, const float *PQ, const float *agg,
                          const float *dagg, float *dPQ, float *scratch, float eps, unsigned *err,
                          cudaStream_t s, uint16_t *dPQ16 = nullptr, int ld16 = 0, const float *eattr = nullptr,
-                         const float *wE = nullptr, int F = 0);
+                         const float *wE = nullptr, int F = 0, bool idx_early = false);
 
 // The same gradient for a batch of whole graphs (node_off: G + 1 offsets;
 // no edge leaves its graph).  Batches of at least 2 x SMs x 128 edges take the
@@ -70,7 +74,7 @@ int launch_aggregate_bwd_graphs(int n_graphs, int n_nodes, int n_edges, int H, D
                                 const float *agg, const float *dagg, float *dPQ, float *scratch, int *chunks,
                                 float eps, unsigned *err, cudaStream_t s, uint16_t *dPQ16 = nullptr, int ld16 = 0,
                                 const float *eattr = nullptr, const float *wE = nullptr, int F = 0,
-                                bool make_chunks = true);
+                                bool make_chunks = true, bool idx_early = false);
 int aggregate_chunk_capacity(int n_edges);
 // Bond rows' gradient out[f][c] (F x H) = sum over edge slots of eattr[r][f]
 // (row stride ld) times dm[r][c] (E x H, the per-edge message gradients at

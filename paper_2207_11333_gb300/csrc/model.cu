@@ -341,7 +341,7 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
     PhaseScope ps(c, GCNN_PHASE_AGG_FWD);
     GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq, agg, (float)c->cfg.std_eps, c->err,
                                   c->stream, U_at(c, l) + H, 16 * H, c->bb.amp, c->bb.att, c->bb.eattr,
-                                  layer_ptrs(c->params, c, l).edge_w, c->cfg.edge_features));
+                                  layer_ptrs(c->params, c, l).edge_w, c->cfg.edge_features, true));
     GCNN_TRY(stage_x(c, Ngrid, l));
   }
   if (ov) {
@@ -383,7 +383,7 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
                                          c->bb.rev, pq, agg, c->dagg, dPQ, c->dm, c->chunks,
                                          (float)c->cfg.std_eps, c->err, c->stream, G + 3 * H, 5 * H, c->bb.eattr,
                                          layer_ptrs(c->params, c, l).edge_w, c->cfg.edge_features,
-                                         l == c->L - 1));
+                                         l == c->L - 1, true));
   }
   // before the next layer's aggregation backward reuses dm
   if (c->cfg.edge_features > 0) GCNN_TRY(gemm_bond_rows(c, Egrid, gw.edge_w));
@@ -481,7 +481,7 @@ int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train) {
       GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq_at(c, l), agg_at(c, l),
                                     (float)c->cfg.std_eps, c->err, c->stream, bf ? U_at(c, l) + H : nullptr,
                                     16 * H, c->bb.amp, c->bb.att, c->bb.eattr, layer_ptrs(c->params, c, l).edge_w,
-                                    c->cfg.edge_features));
+                                    c->cfg.edge_features, true));
     }
     if (bf) GCNN_TRY(tc_update(c, Ngrid, l));
     else GCNN_TRY(gemm_update(c, Ngrid, l));
@@ -542,7 +542,7 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
       PhaseScope ps(c, GCNN_PHASE_AGG_FWD);
       GCNN_TRY(launch_aggregate_fwd(Ngrid, H, dims, c->bb.row_ptr, c->bb.col, pq, agg,
                                     (float)c->cfg.std_eps, c->err, c->stream, nullptr, 0, nullptr, nullptr,
-                                    c->bb.eattr, w.edge_w, c->cfg.edge_features));
+                                    c->bb.eattr, w.edge_w, c->cfg.edge_features, true));
     }
     // dW_U (16H x H) and db_U: [x ; agg ; amp agg ; att agg ; 1]^T (dh * [h > 0])
     {
@@ -580,7 +580,7 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
       GCNN_TRY(launch_aggregate_bwd_graphs(G, Ngrid, Egrid, H, dims, c->bb.node_off, c->bb.row_ptr, c->bb.col,
                                            c->bb.rev, pq, agg, c->dagg, c->dPQ, c->dm, c->chunks,
                                            (float)c->cfg.std_eps, c->err, c->stream, nullptr, 0, c->bb.eattr,
-                                           w.edge_w, c->cfg.edge_features, l == c->L - 1));
+                                           w.edge_w, c->cfg.edge_features, l == c->L - 1, true));
     }
     if (c->cfg.edge_features > 0) GCNN_TRY(gemm_bond_rows(c, Egrid, gw.edge_w));
     // dW_M (H x 2H) and db_M: [x ; 1]^T dPQ  (bias row keeps the first H columns)

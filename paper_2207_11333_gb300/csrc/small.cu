@@ -175,7 +175,6 @@ constexpr int kHeadRed = kHeadThreads;
 
 template <bool kFwd, bool kBwd>
 __global__ void __launch_bounds__(kHeadThreads) head_graph_kernel(HeadArgs a) {
-  pdl_entry(GCNN_K_HEAD_GRAPH);
   extern __shared__ float sm[];
   __shared__ float red[kHeadThreads / 32];
   __shared__ float s_pred, s_dp;
@@ -184,12 +183,27 @@ __global__ void __launch_bounds__(kHeadThreads) head_graph_kernel(HeadArgs a) {
   float *sv = Ws + (size_t)rk * Hh;   // H: pooled features, later dg
   float *sz = sv + H;                 // Hh: z1
   float *sd = sz + Hh;                // Hh: dz1
-  const int G = min(a.g_cap, a.dims.graphs(a.g_cap));
   const int gr = blockIdx.x;
-  if (gr >= G) return;  // block-uniform
   const int tid = threadIdx.x;
-  const int n0 = a.node_off[gr], n1 = a.node_off[gr + 1], nn = n1 - n0;
   const int nchunks = (H + rk - 1) / rk;
+  // one chunk of W1 and whole float4 columns: W1 arrives by asynchronous copies
+  // while the graph is pooled
+  const bool one = nchunks == 1 && (Hh & 3) == 0;
+  // Before the dependency wait: W1 is a parameter (written by the optimizer
+  // or by a host copy, never by the kernel just before this one, which is a
+  // GEMM of the last layer) and the graph offsets come from the collator, so
+  // the copy of W1 and the offsets' loads overlap the previous kernel's tail.
+  if (kFwd && one) {
+    for (int q = tid; q < H * (Hh >> 2); q += kHeadThreads) cp_async16(Ws + 4 * q, a.w1 + 4 * (size_t)q);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  const int G = min(a.g_cap, a.dims.graphs(a.g_cap));
+  const int n0 = gr < G ? a.node_off[gr] : 0, n1 = gr < G ? a.node_off[gr + 1] : 0, nn = n1 - n0;
+  pdl_entry(GCNN_K_HEAD_GRAPH);
+  if (gr >= G) {  // block-uniform
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    return;
+  }
   int staged = -1;
   auto stage = [&](int ch) {  // rows [ch * rk, ...) of W1 into Ws
     __syncthreads();
@@ -202,15 +216,11 @@ __global__ void __launch_bounds__(kHeadThreads) head_graph_kernel(HeadArgs a) {
     __syncthreads();
     staged = ch;
   };
-  // one chunk of W1 and whole float4 columns: W1 arrives by asynchronous copies
-  // while the graph is pooled, and pooling and z1 use every thread (float4
-  // column x row segment, partials summed in segment order)
-  const bool one = nchunks == 1 && (Hh & 3) == 0;
+  // one chunk: pooling and z1 use every thread (float4 column x row segment,
+  // partials summed in segment order) while W1 arrives
   if (kFwd && one) {
     float4 *part4 = reinterpret_cast<float4 *>(sd + Hh);  // kHeadRed float4
     const int H4 = H >> 2, Hh4 = Hh >> 2;
-    for (int q = tid; q < H * Hh4; q += kHeadThreads) cp_async16(Ws + 4 * q, a.w1 + 4 * (size_t)q);
-    asm volatile("cp.async.commit_group;" ::: "memory");
     staged = 0;
     const int R = max(1, kHeadThreads / H4);
     if (tid < R * H4) {
