@@ -521,17 +521,9 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
       cur ^= 1;
       std::swap(c->dH, c->dX);
     }
-    // every gradient is complete before the embedding gradient and the optimiser
-    if (ov) GCNN_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->side_ev[2], 0));
-    if (layers_updated_early(c)) {
-      // layer 0 and the head, bond rows and node head: every gradient but the
-      // embedding's is complete here
-      GCNN_CUDA_TRY(cudaEventRecord(c->opt_ev, c->stream));
-      GCNN_CUDA_TRY(cudaStreamWaitEvent(c->opt, c->opt_ev, 0));
-      const long long lb = (long long)c->T * H, le = lb + (long long)c->L * c->layer_size;
-      GCNN_TRY(adam(c, AdamSpan{lb, c->layer_size, le, (long long)c->P - le}, false, 0, c->opt));
-      GCNN_CUDA_TRY(cudaEventRecord(c->opt_ev, c->opt));
-    }
+    // the third stream's updates of layers L-1 .. 1 (each launched during the
+    // backward of the layer below it) join the main stream below
+    if (layers_updated_early(c) && c->L >= 2) GCNN_CUDA_TRY(cudaEventRecord(c->opt_ev, c->opt));
   }
   for (int l = bf16(c) ? -1 : c->L - 1; l >= 0; --l) {
     LayerW w = layer_ptrs(c->params, c, l);
@@ -612,20 +604,30 @@ int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, d
     }
     std::swap(c->dH, c->dX);
   }
-  // embedding: dEmb[t] = sum of dx0 over nodes of type t
-  PhaseScope ps(c, GCNN_PHASE_EMBED_BWD);
-  GCNN_TRY(launch_embed_bwd(Ngrid, H, dims, c->bb.types, c->dH, c->T, c->grads, c->stream));
-  // the third stream's updates join before the step's final one
-  if (bf16(c) && layers_updated_early(c)) GCNN_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->opt_ev, 0));
+  // embedding: dEmb[t] = sum of dx0 over nodes of type t; it needs only the
+  // main stream's dx, so it runs beside the second stream's last layer
+  {
+    PhaseScope ps(c, GCNN_PHASE_EMBED_BWD);
+    GCNN_TRY(launch_embed_bwd(Ngrid, H, dims, c->bb.types, c->dH, c->T, c->grads, c->stream));
+  }
+  if (bf16(c) && overlapped(c)) {
+    // every gradient is complete before the optimiser: layer 0's weight
+    // gradients and the head's on the second stream, and the third stream's
+    // updates join here
+    GCNN_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->side_ev[2], 0));
+    if (layers_updated_early(c) && c->L >= 2) GCNN_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->opt_ev, 0));
+  }
   return mark_grads_ready(c, c->L, c->stream);  // every gradient is final here
 }
 
 int ctx_step(gcnn_ctx *c) {
   PhaseScope ps(c, GCNN_PHASE_ADAM);
   const long long lb = (long long)c->T * c->H, le = lb + (long long)c->L * c->layer_size;
-  // after a train step's overlapped backward only the embedding table
-  // remains; otherwise everything
-  const AdamSpan sp = layers_updated_early(c) ? AdamSpan{0, lb, 0, 0} : AdamSpan{0, 0, 0, (long long)c->P};
+  // after a train step's overlapped backward the embedding table, layer 0
+  // and the parameters after the layers remain (layers L-1 .. 1 were updated
+  // on the third stream); otherwise everything
+  const AdamSpan sp = layers_updated_early(c) ? AdamSpan{0, lb + c->layer_size, le, (long long)c->P - le}
+                                              : AdamSpan{0, 0, 0, (long long)c->P};
   return adam(c, sp, true, 0, c->stream);
 }
 
