@@ -307,11 +307,17 @@ def batch_at(ctx, wl: Workload, k: int):
     return ctx.collate_range(wl.st, i * BATCH, min(BATCH, wl.n_train - i * BATCH))
 
 
+def train_at(ctx, wl: Workload, k: int, loss_acc):
+    """Training step k: collation of batch k of the epoch order and the step in one graph launch."""
+    i = k % wl.nb
+    return ctx.train_step_range(wl.st, i * BATCH, min(BATCH, wl.n_train - i * BATCH), LR, loss_acc)
+
+
 def timed_steps(ctx, wl, steps, warmup, flush, loss_acc, dist=None, gpu_index=None):
     """Device time of `steps` training steps (per-step CUDA events, L2 flushed between steps)."""
     import torch
     for k in range(warmup):
-        ctx.train_step(batch_at(ctx, wl, k), LR, loss_acc)
+        train_at(ctx, wl, k, loss_acc)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -324,8 +330,7 @@ def timed_steps(ctx, wl, steps, warmup, flush, loss_acc, dist=None, gpu_index=No
     for k in range(steps):
         flush.zero_()
         evs[k][0].record()
-        b = batch_at(ctx, wl, warmup + k)
-        ctx.train_step(b, LR, loss_acc)
+        b = train_at(ctx, wl, warmup + k, loss_acc)
         evs[k][1].record()
         graphs += b.n_graphs
     torch.cuda.synchronize()
@@ -341,8 +346,9 @@ def timed_steps(ctx, wl, steps, warmup, flush, loss_acc, dist=None, gpu_index=No
         dev_s, total = float(tmax.item()), float(gsum.item())
     else:
         total = float(graphs)
+    # the collation's two kernels are part of the step's graph
     return {"value": total / dev_s, "dev_s": dev_s, "graphs": total, "wall_s": wall, "clocks": clocks,
-            "kernels_per_step": ctx.step_kernel_count() + 2}
+            "kernels_per_step": ctx.step_kernel_count()}
 
 
 def timed_ddp_steps(g, ctx, wl, steps, warmup, flush, loss_acc, dist, gpu_index, store=None, e2e=False):
@@ -429,8 +435,8 @@ def kernel_profile(g, wl, n_steps, warmup, flush, loss_acc, precision):
     stream (GCNN_FLAG_SERIAL, same kernels and launch shapes).  The library
     appends a one-thread marker kernel after the step while the timeline is
     on, so the optimiser (the step's last kernel) is timed too, with the
-    graph's completion latency included; the collation kernels run before
-    the graph launch, so their durations include that host gap.  Phases
+    graph's completion latency included; the collation kernels are the
+    graph's first launches (gcnn_train_step_range).  Phases
     follow the launch order: collation, forward (embedding through the head
     and loss), backward (head gradient through the embedding gradient) and
     the optimiser."""
@@ -438,7 +444,7 @@ def kernel_profile(g, wl, n_steps, warmup, flush, loss_acc, precision):
     from collections import Counter, defaultdict
     ctx = make_ctx(g, wl, precision, g.FLAG_SERIAL)
     for k in range(warmup):
-        ctx.train_step(batch_at(ctx, wl, k), LR, loss_acc)
+        train_at(ctx, wl, k, loss_acc)
     torch.cuda.synchronize()
     ctx.timeline_enable(256 * n_steps)
     ctx.timeline_read()
@@ -446,8 +452,7 @@ def kernel_profile(g, wl, n_steps, warmup, flush, loss_acc, precision):
     dur, cnt, ph = defaultdict(float), Counter(), defaultdict(float)
     for k in range(n_steps):
         flush.zero_()
-        b = batch_at(ctx, wl, warmup + k)
-        ctx.train_step(b, LR, loss_acc)
+        b = train_at(ctx, wl, warmup + k, loss_acc)
         torch.cuda.synchronize()
         ids, t = ctx.timeline_read()
         phase = "collate"

@@ -315,6 +315,20 @@ int gcnn_grads_device(gcnn_ctx *ctx, float **grads);
  * update on a third as soon as that layer's gradients are complete; the result
  * equals forward + backward + step bit for bit. */
 int gcnn_train_step(gcnn_ctx *ctx, const gcnn_batch *b, float lr, double *loss_accum);
+/* gcnn_collate_range(first, count) + gcnn_train_step in one captured CUDA
+ * graph (Sec. 3.2, Fig. 3: loading, forward, backward and optimizer of one
+ * training iteration): the collation of order[first .. first+count) (the
+ * order set by gcnn_set_order, resident store) is the graph's first launch,
+ * so the device goes from batch assembly into the forward without a host
+ * round trip between two submissions.  The graph is captured per graph count
+ * and size bucket on first use; a later call with another `first` updates the
+ * collation's arguments in the instantiated graph (launches already queued
+ * keep theirs).  Results equal gcnn_collate_range + gcnn_train_step bit for
+ * bit.  out (nullable) receives the batch's device views, valid as after
+ * gcnn_collate_range.  GCNN_ESTATE without gcnn_set_order on `st`,
+ * GCNN_EINVAL for a range outside the order or beyond the capacities. */
+int gcnn_train_step_range(gcnn_ctx *ctx, const gcnn_store *st, int64_t first, int32_t count, float lr,
+                          double *loss_accum, gcnn_batch *out);
 /* forward(train) + backward(MSE) without the optimizer step, replayed from a
  * captured CUDA graph per batch graph count like gcnn_train_step: the first
  * half of a data-parallel step.  The graph records the gradient buckets'

@@ -113,6 +113,7 @@ def _load() -> ctypes.CDLL:
         "gcnn_grad_wait": (i32, [vp, i32, vp]),
         "gcnn_grads_device": (i32, [vp, P(vp)]),
         "gcnn_train_step": (i32, [vp, P(BatchStruct), f32, vp]),
+        "gcnn_train_step_range": (i32, [vp, vp, i64, i32, f32, vp, P(BatchStruct)]),
         "gcnn_forward_backward": (i32, [vp, P(BatchStruct), vp]),
         "gcnn_get_activation": (i32, [vp, i32, vp, i64]),
         "gcnn_profile_enable": (i32, [vp, i32]),
@@ -446,6 +447,13 @@ class Context:
 
     def train_step(self, batch: Batch, lr: float, loss_accum=None) -> None:
         _check(lib.gcnn_train_step(self._h, ctypes.byref(batch.s), lr, _dev_ptr(loss_accum)))
+
+    def train_step_range(self, store: Store, first: int, count: int, lr: float, loss_accum=None) -> Batch:
+        """Collation of order[first:first+count] and one training step in one graph (gcnn_train_step_range)."""
+        b = BatchStruct()
+        _check(lib.gcnn_train_step_range(self._h, store.handle, first, count, lr, _dev_ptr(loss_accum),
+                                         ctypes.byref(b)))
+        return Batch(b, self)
 
     def forward_backward(self, batch: Batch, loss_accum=None) -> None:
         """Captured forward + backward without the optimizer (gcnn_forward_backward)."""

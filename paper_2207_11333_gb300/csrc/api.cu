@@ -99,6 +99,7 @@ void destroy_ctx(gcnn_ctx *c) {
   if (!c) return;
   for (auto &kv : c->graphs) {
     cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
     for (auto &pe : kv.second.ev) {
       cudaEventDestroy(pe.a);
       cudaEventDestroy(pe.b);
@@ -646,13 +647,25 @@ namespace {
 // Replay (capturing it on first use) the graph of one training step on batch
 // b: forward + backward, followed by AdamW when with_step.  Without the step,
 // the backward's gradient-bucket events are external nodes of the graph.
-int run_step_graph(gcnn_ctx *c, const gcnn_batch *b, double *loss_accum, bool with_step) {
+// With range_st, the graph begins with the collation of graphs
+// order[range_first .. + b->n_graphs) of the device-resident order (b then
+// describes that batch before it is collated); a replay for another range
+// of the same sizes updates the collation's two kernel nodes.
+int run_step_graph(gcnn_ctx *c, const gcnn_batch *b, double *loss_accum, bool with_step,
+                   const gcnn_store *range_st = nullptr, int64_t range_first = 0) {
   const int G = b->n_graphs;
   const int Ng = grid_nodes(c, b), Eg = grid_edges(c, b);
   // with profiling on, a separate graph carries event-record nodes around
   // every phase; each of its replays is synchronised and accumulated
-  auto key = std::make_tuple(G, Ng, Eg, (const double *)loss_accum, c->prof_on, with_step);
+  auto key = std::make_tuple(G, Ng, Eg, (const double *)loss_accum, c->prof_on, with_step, range_st != nullptr);
   auto it = c->graphs.find(key);
+  if (it != c->graphs.end() && range_st &&
+      (it->second.range_store != range_st || it->second.range_first != range_first)) {
+    GCNN_TRY(ctx_range_update(c, range_st, range_first, G, it->second.exec, it->second.scan_node,
+                              it->second.graph_node));
+    it->second.range_store = range_st;
+    it->second.range_first = range_first;
+  }
   if (it == c->graphs.end()) {
     // capture on the context's private stream (the legacy default stream
     // cannot be captured); the graph is then launched on the caller's stream
@@ -672,7 +685,8 @@ int run_step_graph(gcnn_ctx *c, const gcnn_batch *b, double *loss_accum, bool wi
     }
     c->fuse_head = true;
     c->fuse_step = with_step;
-    int rc = ctx_forward(c, G, Ng, Eg, true);
+    int rc = range_st ? ctx_range_launch(c, range_st, range_first, G) : GCNN_OK;
+    if (rc == GCNN_OK) rc = ctx_forward(c, G, Ng, Eg, true);
     if (rc == GCNN_OK) rc = ctx_backward(c, G, Ng, Eg, nullptr, loss_accum);
     c->fuse_head = false;
     if (rc == GCNN_OK && with_step) rc = ctx_step(c);
@@ -704,20 +718,44 @@ int run_step_graph(gcnn_ctx *c, const gcnn_batch *b, double *loss_accum, bool wi
     cudaGraphGetNodes(graph, nullptr, &n_nodes);
     std::vector<cudaGraphNode_t> nodes(n_nodes);
     int kernels = 0;
+    cudaGraphNode_t scan_node = nullptr, graph_node = nullptr;
     if (n_nodes && cudaGraphGetNodes(graph, nodes.data(), &n_nodes) == cudaSuccess) {
       for (auto nd : nodes) {
         cudaGraphNodeType t;
-        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+        if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+        ++kernels;
+        cudaKernelNodeParams kp{};
+        if (range_st && cudaGraphKernelNodeGetParams(nd, &kp) == cudaSuccess) {
+          const int kind = collate_node_kind(kp.func);
+          if (kind == 1) scan_node = nd;
+          if (kind == 2) graph_node = nd;
+        }
       }
+    }
+    cudaGetLastError();
+    if (range_st && (!scan_node || !graph_node)) {
+      cudaGraphDestroy(graph);
+      drop_events();
+      return set_error(GCNN_ECUDA, "train step: the captured collation nodes were not found");
     }
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
+    // a graph whose collation nodes are updated later stays alive with its exec
+    if (!range_st || e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      graph = nullptr;
+    }
     if (e != cudaSuccess) {
       drop_events();
       return set_error(GCNN_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     }
-    it = c->graphs.emplace(key, gcnn_ctx::Graph{exec, kernels, std::move(ev)}).first;
+    gcnn_ctx::Graph entry{exec, kernels, std::move(ev)};
+    entry.graph = graph;
+    entry.scan_node = scan_node;
+    entry.graph_node = graph_node;
+    entry.range_store = range_st;
+    entry.range_first = range_first;
+    it = c->graphs.emplace(key, std::move(entry)).first;
   }
   GCNN_CUDA_TRY(cudaGraphLaunch(it->second.exec, c->stream));
   bool tl_on;
@@ -747,6 +785,18 @@ int gcnn_train_step(gcnn_ctx *c, const gcnn_batch *b, float lr, double *loss_acc
   GCNN_TRY(same_batch(c, b));
   GCNN_TRY(set_lr(c, lr));
   return run_step_graph(c, b, loss_accum, true);
+}
+
+int gcnn_train_step_range(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count, float lr,
+                          double *loss_accum, gcnn_batch *out) {
+  if (!c || !st || count < 1) return set_error(GCNN_EINVAL, "train_step_range: bad arguments");
+  gcnn_batch b{};
+  GCNN_TRY(ctx_range_prepare(c, st, first, count, &b));
+  GCNN_TRY(set_lr(c, lr));
+  c->have_fwd = false;
+  GCNN_TRY(run_step_graph(c, &b, loss_accum, true, st, first));
+  if (out) *out = b;
+  return GCNN_OK;
 }
 
 int gcnn_forward_backward(gcnn_ctx *c, const gcnn_batch *b, double *loss_accum) {

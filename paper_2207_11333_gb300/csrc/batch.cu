@@ -182,7 +182,7 @@ int ctx_collate_files(gcnn_ctx *c, const char *const *paths, int32_t n, gcnn_bat
   return collate_staged(c, n, N, E, F, sizes, fill, out);
 }
 
-int ctx_collate_range(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count, gcnn_batch *out) {
+int ctx_range_prepare(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count, gcnn_batch *out) {
   if (!c->order_dev || c->order_store != st) return set_error(GCNN_ESTATE, "collate_range: call gcnn_set_order first");
   if (!st->dev) return set_error(GCNN_ESTATE, "collate_range needs a device-resident store");
   if (first < 0 || first + count > (int64_t)c->order_host.size())
@@ -192,10 +192,25 @@ int ctx_collate_range(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t 
   GCNN_TRY(check_caps(c, count, 0, 0));
   GCNN_TRY(store_batch_size(st, c->order_host.data() + first, count, &N, &E));
   GCNN_TRY(check_caps(c, count, N, E));
-  PhaseScope ps(c, GCNN_PHASE_COLLATE);
-  GCNN_TRY(launch_collate(count, c->order_dev + first, store_device_view(st), c->bb, c->scal_tab, c->Nc, c->Ec,
-                          c->err, c->stream));
   fill_batch(c, count, N, E, out);
+  return GCNN_OK;
+}
+
+int ctx_range_launch(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count) {
+  PhaseScope ps(c, GCNN_PHASE_COLLATE);
+  return launch_collate(count, c->order_dev + first, store_device_view(st), c->bb, c->scal_tab, c->Nc, c->Ec, c->err,
+                        c->stream);
+}
+
+int ctx_range_update(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count, cudaGraphExec_t exec,
+                     cudaGraphNode_t scan_node, cudaGraphNode_t graph_node) {
+  return collate_set_nodes(exec, scan_node, graph_node, count, c->order_dev + first, store_device_view(st), c->bb,
+                           c->scal_tab, c->Nc, c->Ec, c->err);
+}
+
+int ctx_collate_range(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count, gcnn_batch *out) {
+  GCNN_TRY(ctx_range_prepare(c, st, first, count, out));
+  GCNN_TRY(ctx_range_launch(c, st, first, count));
   c->have_fwd = false;
   return GCNN_OK;
 }

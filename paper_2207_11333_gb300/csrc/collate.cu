@@ -175,6 +175,32 @@ int launch_collate(int G, const int64_t *ids, StoreView st, BatchBuf b, const fl
   return GCNN_OK;
 }
 
+int collate_node_kind(const void *func) {
+  if (func == reinterpret_cast<const void *>(collate_scan_kernel)) return 1;
+  if (func == reinterpret_cast<const void *>(collate_graph_kernel)) return 2;
+  return 0;
+}
+
+int collate_set_nodes(cudaGraphExec_t exec, cudaGraphNode_t scan_node, cudaGraphNode_t graph_node, int G,
+                      const int64_t *ids, StoreView st, BatchBuf b, const float *scal_tab, int cap_nodes,
+                      int cap_edges, unsigned *err) {
+  if (G <= 0) return set_error(GCNN_EINVAL, "collate: a captured collation needs at least one graph");
+  void *scan_args[] = {&G, &ids, &st, &b, &cap_nodes, &cap_edges, &err};
+  cudaKernelNodeParams p{};
+  p.func = reinterpret_cast<void *>(collate_scan_kernel);
+  p.gridDim = dim3(1);
+  p.blockDim = dim3(kScanThreads);
+  p.kernelParams = scan_args;
+  GCNN_CUDA_TRY(cudaGraphExecKernelNodeSetParams(exec, scan_node, &p));
+  void *graph_args[] = {&G, &ids, &st, &b, &scal_tab, &cap_nodes, &cap_edges, &err};
+  p.func = reinterpret_cast<void *>(collate_graph_kernel);
+  p.gridDim = dim3(ceil_div(G, kGraphWarps));
+  p.blockDim = dim3(kGraphWarps * 32);
+  p.kernelParams = graph_args;
+  GCNN_CUDA_TRY(cudaGraphExecKernelNodeSetParams(exec, graph_node, &p));
+  return GCNN_OK;
+}
+
 GCNN_TIMELINE_ATTACH(collate)
 
 }  // namespace gcnn

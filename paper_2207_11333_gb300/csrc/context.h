@@ -84,10 +84,18 @@ struct gcnn_ctx {
     cudaGraphExec_t exec;
     int kernels;
     std::vector<ProfEvent> ev;  // profiling graphs: event-record nodes around each phase
+    // graphs that begin with the collation of a range of the device-resident
+    // order: the captured graph (its nodes address the instantiated one), the
+    // collation's two kernel nodes and the range they were last set to
+    cudaGraph_t graph = nullptr;
+    cudaGraphNode_t scan_node = nullptr, graph_node = nullptr;
+    const gcnn_store *range_store = nullptr;
+    int64_t range_first = -1;
   };
   // key: grid (graphs, node bucket, edge bucket), loss accumulator, profiling
-  // graph, and whether the graph ends with the optimizer step
-  std::map<std::tuple<int, int, int, const double *, bool, bool>, Graph> graphs;
+  // graph, whether the graph ends with the optimizer step, and whether it
+  // begins with the collation of a range of the device-resident order
+  std::map<std::tuple<int, int, int, const double *, bool, bool, bool>, Graph> graphs;
   bool cap_grad_events = false;  // capturing forward + backward: record the bucket events externally
   int last_step_kernels = 0;
   bool capturing = false;
@@ -123,6 +131,14 @@ class PhaseScope {
 int ctx_collate(gcnn_ctx *c, const gcnn_store *st, const int64_t *ids, int32_t n, gcnn_batch *out);
 int ctx_collate_files(gcnn_ctx *c, const char *const *paths, int32_t n, gcnn_batch *out);
 int ctx_collate_range(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count, gcnn_batch *out);
+// gcnn_collate_range in parts: checks and host-side sizes of the range (out
+// receives the batch views), the collation launches on c->stream, and the
+// update of a captured collation's two kernel nodes to another range of the
+// same graph count
+int ctx_range_prepare(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count, gcnn_batch *out);
+int ctx_range_launch(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count);
+int ctx_range_update(gcnn_ctx *c, const gcnn_store *st, int64_t first, int32_t count, cudaGraphExec_t exec,
+                     cudaGraphNode_t scan_node, cudaGraphNode_t graph_node);
 int ctx_forward(gcnn_ctx *c, int G, int Ngrid, int Egrid, bool train);
 int ctx_backward(gcnn_ctx *c, int G, int Ngrid, int Egrid, const float *dpred, double *loss_accum);
 int ctx_step(gcnn_ctx *c);

@@ -225,6 +225,8 @@ __device__ __forceinline__ float4 ld_cluster4(uint32_t a, int rank) {
 // from rank z + 1 are issued before the sums of rank z, so a warp waits for
 // one remote-load latency per rank, not one per row and rank; the order of
 // the additions, and so every result bit, does not depend on this.
+// LEAN (register-capped kernels): one rank's loads at a time.
+template <bool LEAN>
 __device__ __forceinline__ void rows_sum4(const float *S, int RS, int r0, int re, int cn, int ranks, float4 v[4]) {
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   if (ranks == 1) {
@@ -236,6 +238,20 @@ __device__ __forceinline__ void rows_sum4(const float *S, int RS, int r0, int re
   uint32_t a[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) a[u] = smem_u32(S + (size_t)(r0 + 8 * u) * RS + cn);
+  if (LEAN) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = r0 + 8 * u < re ? ld_cluster4(a[u], 0) : zero;
+    for (int z = 1; z < ranks; ++z) {
+      float4 t[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) t[u] = r0 + 8 * u < re ? ld_cluster4(a[u], z) : zero;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        v[u].x += t[u].x; v[u].y += t[u].y; v[u].z += t[u].z; v[u].w += t[u].w;
+      }
+    }
+    return;
+  }
   float4 t[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -285,6 +301,7 @@ __device__ __forceinline__ void store_partial(const float *S, int RS, int rows, 
 
 // C (FP32) and / or C16 (BF16) with optional bias and ReLU, tile rows [rb, re)
 // summed over `ranks` cluster CTAs
+template <bool LEAN>
 __device__ __forceinline__ void store_c(const float *S, int RS, int rb, int re, int ranks, int BN, int N, int m0,
                                         int n0, const TcEpilogue e, int warp, int lane) {
 #pragma unroll 1
@@ -299,7 +316,7 @@ __device__ __forceinline__ void store_c(const float *S, int RS, int rb, int re, 
         if (n + q < e.bias_n) b[q] = e.bias[n + q];
     for (int r0 = rb + warp; r0 < re; r0 += 32) {
       float4 v[4];
-      rows_sum4(S, RS, r0, re, cn, ranks, v);
+      rows_sum4<LEAN>(S, RS, r0, re, cn, ranks, v);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (r0 + 8 * u >= re) break;
@@ -331,7 +348,7 @@ __device__ __forceinline__ void store_d3(const float *S, int RS, int rb, int re,
       float4 v[4];
       uint32_t mk[4];
       float am[4], at[4];
-      rows_sum4(S, RS, r0, re, cn, ranks, v);
+      rows_sum4<false>(S, RS, r0, re, cn, ranks, v);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int r = r0 + 8 * u;
@@ -389,8 +406,12 @@ __device__ __forceinline__ void clear_k_rows(uint8_t *tile, int atoms, int from,
 // CL: the grid's z dimension (K-splits of one output tile) is a thread-block
 // cluster; the split-K partial tiles are summed through distributed shared
 // memory instead of a partial buffer and a reduction kernel.
-template <int EPI, bool CL>
-__global__ void __launch_bounds__(kThreads, kCtasPerSm)
+// LEAN: at most 80 registers per thread (3 CTAs' worth of the register
+// file): the weight-gradient GEMMs, which run on the backward's second stream
+// beside the memory-bound aggregation backward, leave that kernel more of the
+// SM's registers for its loads in flight.  Same arithmetic and order.
+template <int EPI, bool CL, bool LEAN>
+__global__ void __launch_bounds__(kThreads, LEAN ? 3 : kCtasPerSm)
 tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, float *__restrict__ partial, int splits,
                 int kps, int BN, unsigned *err) {
   extern __shared__ uint8_t smem_raw[];
@@ -607,7 +628,7 @@ tma_gemm_kernel(const __grid_constant__ TcMaps maps, TcDesc d, DevDims dims, flo
       if constexpr (EPI == kEpiPartial)
         store_partial(S, RS, rows, BN, N, m0, n0, partial + (size_t)z * d.M * N, warp, lane);
       else if constexpr (EPI == kEpiC)
-        store_c(S, RS, rb, re, ranks, BN, N, m0, n0, d.ep, warp, lane);
+        store_c<LEAN>(S, RS, rb, re, ranks, BN, N, m0, n0, d.ep, warp, lane);
       else
         store_d3(S, RS, rb, re, ranks, BN, N, m0, n0, d.ep, mbits, s_amp, s_att, warp, lane);
     }
@@ -679,10 +700,10 @@ int make_map(CUtensorMap *m, const TcMat &a, int box_rows) {
 
 constexpr int kMaxCluster = 6;  // largest split-K cluster (co-resident capacity falls beyond)
 
-template <int EPI, bool CL>
+template <int EPI, bool CL, bool LEAN = false>
 void set_smem_attr(int *rc) {
   if (*rc == GCNN_OK &&
-      cudaFuncSetAttribute(tma_gemm_kernel<EPI, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
+      cudaFuncSetAttribute(tma_gemm_kernel<EPI, CL, LEAN>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
           cudaSuccess)
     *rc = set_error(GCNN_ECUDA, "tc gemm: cannot set the shared-memory size");
 }
@@ -702,7 +723,7 @@ int cluster_capacity_of(int size) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, (void *)tma_gemm_kernel<EPI, true>, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, (void *)tma_gemm_kernel<EPI, true, false>, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -722,6 +743,9 @@ int configure() {
     set_smem_attr<kEpiD3, false>(&rc);
     set_smem_attr<kEpiC, true>(&rc);
     set_smem_attr<kEpiD3, true>(&rc);
+    set_smem_attr<kEpiPartial, false, true>(&rc);
+    set_smem_attr<kEpiC, false, true>(&rc);
+    set_smem_attr<kEpiC, true, true>(&rc);
     for (int sz = 2; sz <= kMaxCluster && rc == GCNN_OK; ++sz) {
       g_capacity[0][sz] = cluster_capacity_of<kEpiC>(sz);
       g_capacity[1][sz] = cluster_capacity_of<kEpiD3>(sz);
@@ -850,12 +874,16 @@ int run_planned(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned
   GCNN_TRY(make_map(&maps.b, d.B, d.B.mn_major ? 64 : BN));
   const int kps = (ktiles + splits - 1) / splits * BK;
   dim3 grid(ntiles, (d.M + BM - 1) / BM, splits);
+  // the masked-gradient epilogue has no register-capped form
+  const bool lean = d.lean && !e.D3;
   if (splits > 1 && plan.cluster) {
-    auto kernel = e.D3 ? tma_gemm_kernel<kEpiD3, true> : tma_gemm_kernel<kEpiC, true>;
+    auto kernel = e.D3 ? tma_gemm_kernel<kEpiD3, true, false>
+                       : (lean ? tma_gemm_kernel<kEpiC, true, true> : tma_gemm_kernel<kEpiC, true, false>);
     return launch_gemm(kernel, grid, splits, s, maps, d, dims, (float *)nullptr, splits, kps, BN, err);
   }
-  auto kernel = splits > 1 ? tma_gemm_kernel<kEpiPartial, false>
-                           : (e.D3 ? tma_gemm_kernel<kEpiD3, false> : tma_gemm_kernel<kEpiC, false>);
+  auto kernel = splits > 1 ? (lean ? tma_gemm_kernel<kEpiPartial, false, true> : tma_gemm_kernel<kEpiPartial, false, false>)
+                           : (e.D3 ? tma_gemm_kernel<kEpiD3, false, false>
+                                   : (lean ? tma_gemm_kernel<kEpiC, false, true> : tma_gemm_kernel<kEpiC, false, false>));
   GCNN_TRY(launch_gemm(kernel, grid, 1, s, maps, d, dims, splits > 1 ? ws.partial : nullptr, splits, kps, BN, err));
   if (splits > 1) {
     const long long work = (long long)d.M * (d.N / 8);
@@ -976,7 +1004,7 @@ int gemm_tc_study(int n_atoms, int H, int mode, double *rows, int max_rows, int 
   {  // 2: dW_U = U^T g (side stream)
     TcDesc d{}; d.M = 16 * H; d.N = H; d.K = Ng; d.node_dim = kNodeK;
     d.A = M(U, 16 * H, Ng, 16 * H, true); d.B = M(G5 + 2 * H, 5 * H, Ng, H, true); d.stable = kStableA;
-    d.ep.C = C; d.ep.ldc = H;
+    d.ep.C = C; d.ep.ldc = H; d.lean = true;
     shapes.push_back({2, d, side_gemm_ctas()});
   }
   {  // 3: dagg = [amp g | att g | g] Wd^T
@@ -988,7 +1016,7 @@ int gemm_tc_study(int n_atoms, int H, int mode, double *rows, int max_rows, int 
   {  // 4: dW_M = x^T [dP | dQ] (side stream)
     TcDesc d{}; d.M = H; d.N = 2 * H; d.K = Ng; d.node_dim = kNodeK;
     d.A = M(U, 16 * H, Ng, H, true); d.B = M(G5 + 3 * H, 5 * H, Ng, 2 * H, true); d.stable = kStableA;
-    d.ep.C = C; d.ep.ldc = 2 * H;
+    d.ep.C = C; d.ep.ldc = 2 * H; d.lean = true;
     shapes.push_back({4, d, side_gemm_ctas()});
   }
   {  // 5: dx = [g | dP | dQ] Wx^T with the masked, scaled BF16 blocks

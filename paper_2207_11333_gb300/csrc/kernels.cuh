@@ -34,6 +34,14 @@ struct BatchBuf {
 // (d = 0..kMaxGraphEdges).
 int launch_collate(int G, const int64_t *ids, StoreView st, BatchBuf b, const float *scal_tab,
                    int cap_nodes, int cap_edges, unsigned *err, cudaStream_t s);
+// For a collation captured in a CUDA graph: 1 or 2 when `func` is the kernel
+// of its scan or its per-graph launch (0 otherwise), and the update of those
+// two nodes of an instantiated graph to the arguments of another batch of the
+// same graph count G.
+int collate_node_kind(const void *func);
+int collate_set_nodes(cudaGraphExec_t exec, cudaGraphNode_t scan_node, cudaGraphNode_t graph_node, int G,
+                      const int64_t *ids, StoreView st, BatchBuf b, const float *scal_tab, int cap_nodes,
+                      int cap_edges, unsigned *err);
 
 // ---------------------------------------------------------------- aggregate.cu
 // agg[i] = [sum, mean, min, max, std](P_i + Q_j, j in N(i)); PQ is N x 2H.
@@ -265,6 +273,9 @@ struct TcDesc {
   TcMat A, B;
   TcEpilogue ep;
   TcStable stable;
+  // at most 80 registers per thread (the weight-gradient GEMMs beside the
+  // aggregation backward); ignored with the masked-gradient epilogue
+  bool lean;
 };
 
 int run_gemm_tc(const TcDesc &d, DevDims dims, const GemmWorkspace &ws, unsigned *err, cudaStream_t s);

@@ -356,6 +356,7 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
     // the forward's operand, unless recomputed just before
     d.stable = c->cfg.recompute ? kStableNone : kStableA;
     d.ep.C = gw.upd_w; d.ep.ldc = H;
+    d.lean = true;
     GCNN_TRY(tc_on(c, d, lane));
   }
   // layer l + 1 on a third stream, joined at the end of the backward: its
@@ -398,6 +399,7 @@ int tc_backward_layer(gcnn_ctx *c, int Gn, int Ngrid, int Egrid, int l, int cur,
     d.B = mat(G + 3 * H, 5 * H, Ngrid, 2 * H, true);
     d.stable = kStableA;  // x_l from the forward; [dP | dQ] from the aggregation backward
     d.ep.C = gw.msg_w; d.ep.ldc = 2 * H;
+    d.lean = true;
     GCNN_TRY(tc_on(c, d, lane));
     // bias gradients: db_U = sum of dpre, db_M = sum of dP (FP32, fixed order)
     PhaseScope ps(c, GCNN_PHASE_GEMM);
