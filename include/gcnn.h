@@ -373,8 +373,10 @@ int gcnn_profile_read(gcnn_ctx *ctx, double *ms, int64_t *launches);
 /* Device bytes held by the context (parameters, optimiser state, batch,
  * activations and workspace; one allocation made by gcnn_create). */
 int gcnn_memory(const gcnn_ctx *ctx, int64_t *arena_bytes);
-/* Kernels in the CUDA graph of the most recent gcnn_train_step (0 if it ran
- * eagerly); the collation of a batch adds 2 more. */
+/* Kernels in the CUDA graph of the most recent gcnn_train_step or
+ * gcnn_train_step_range (0 if it ran eagerly; the latter's count includes its
+ * collation); a separate collation of a batch adds 1 more launch for at most
+ * 1024 graphs, 2 beyond. */
 int gcnn_step_kernel_count(gcnn_ctx *ctx, int32_t *n);
 
 /* Kernel timeline.  While enabled, block 0 of every kernel of the library
@@ -420,6 +422,7 @@ enum {
   GCNN_K_NODE_PRED = 25,        /* node-level head: outputs and loss gradient  */
   GCNN_K_NODE_GRAD = 26,        /* node-level head: w2n, b2n and loss sums     */
   GCNN_K_BOND_GRAD = 27,        /* gradient of the bond rows of W_M            */
+  GCNN_K_COLLATE = 28,          /* collation of <= 1024 graphs in one launch   */
   GCNN_NKERNEL = 28
 };
 int gcnn_timeline_enable(gcnn_ctx *ctx, int32_t capacity);

@@ -28,7 +28,8 @@ KERNELS = {1: "collate_scan", 2: "collate_graph", 3: "embed", 4: "embed_bwd", 5:
            7: "agg_bwd_gather", 8: "gemm_tc_partial", 9: "gemm_tc_c", 10: "gemm_tc_d3", 11: "gemm_tc_reduce",
            12: "gemm_simt", 13: "gemm_simt_reduce", 14: "pool_fwd", 15: "pool_bwd", 16: "head_graph",
            17: "head_grad", 18: "colsum", 19: "adam", 20: "cast_bf16", 21: "pack_layer", 22: "step_end",
-           23: "agg_bwd_fused", 24: "agg_bwd_chunks", 25: "node_pred", 26: "node_grad", 27: "bond_grad"}
+           23: "agg_bwd_fused", 24: "agg_bwd_chunks", 25: "node_pred", 26: "node_grad", 27: "bond_grad",
+           28: "collate"}
 
 _ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "EFORMAT", -5: "EDEVICE", -6: "ETIMEDOUT",
            -7: "EAGAIN", -8: "ESTATE"}

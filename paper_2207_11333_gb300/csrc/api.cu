@@ -727,13 +727,14 @@ int run_step_graph(gcnn_ctx *c, const gcnn_batch *b, double *loss_accum, bool wi
         cudaKernelNodeParams kp{};
         if (range_st && cudaGraphKernelNodeGetParams(nd, &kp) == cudaSuccess) {
           const int kind = collate_node_kind(kp.func);
-          if (kind == 1) scan_node = nd;
+          if (kind == 1 || kind == 3) scan_node = nd;
           if (kind == 2) graph_node = nd;
         }
       }
     }
     cudaGetLastError();
-    if (range_st && (!scan_node || !graph_node)) {
+    // one launch for a batch of at most 1024 graphs, a scan and a per-graph launch beyond
+    if (range_st && (!scan_node || (G > 1024 && !graph_node))) {
       cudaGraphDestroy(graph);
       drop_events();
       return set_error(GCNN_ECUDA, "train step: the captured collation nodes were not found");

@@ -35,9 +35,11 @@ struct BatchBuf {
 int launch_collate(int G, const int64_t *ids, StoreView st, BatchBuf b, const float *scal_tab,
                    int cap_nodes, int cap_edges, unsigned *err, cudaStream_t s);
 // For a collation captured in a CUDA graph: 1 or 2 when `func` is the kernel
-// of its scan or its per-graph launch (0 otherwise), and the update of those
-// two nodes of an instantiated graph to the arguments of another batch of the
-// same graph count G.
+// of its scan or its per-graph launch, 3 for the single launch of a batch of
+// at most 1024 graphs (0 otherwise); and the update of those nodes of an
+// instantiated graph (scan_node: the scan or the single launch; graph_node:
+// the per-graph launch, unused for a single launch) to the arguments of
+// another batch of the same graph count G.
 int collate_node_kind(const void *func);
 int collate_set_nodes(cudaGraphExec_t exec, cudaGraphNode_t scan_node, cudaGraphNode_t graph_node, int G,
                       const int64_t *ids, StoreView st, BatchBuf b, const float *scal_tab, int cap_nodes,

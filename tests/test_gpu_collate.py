@@ -40,6 +40,37 @@ def test_collate_bit_exact(resident, tmp_path):
     ctx.check()
 
 
+@pytest.mark.parametrize("resident", [False, True])
+def test_collate_bit_exact_around_the_single_launch_limit(resident, tmp_path):
+    """Batches of up to 1024 graphs are collated by one launch whose blocks each
+    scan the whole batch's counts; larger ones by a scan launch and a per-graph
+    launch.  Both sides of the limit, and a range of the device-resident order,
+    match the oracle's collation bit for bit."""
+    import paper_2207_11333_gb300 as g
+    gs = synth.molecules_uniform(21, 3000, 1, 30)
+    gs.y = synth.uniform_targets(22, 0, 3000, 1, 10)
+    path, ost = write_both(gs, str(tmp_path))
+    st = g.Store(path)
+    if resident:
+        st.to_device()
+    delta = st.delta()
+    ctx = context(32, 1, 2500, 2500 * 30, 2500 * 80, delta)
+    rng = np.random.default_rng(23)
+    for n in (1023, 1024, 1025, 2500):
+        ids = rng.permutation(3000)[:n]
+        gb = ctx.collate(st, ids)
+        ob = oracle.collate(ost, ids, delta)
+        assert (gb.n_graphs, gb.n_nodes, gb.n_edges) == (ob.G, ob.N, ob.E)
+        _compare(gb, ob)
+    if resident:
+        order = rng.permutation(3000)
+        ctx.set_order(st, order)
+        for first, n in ((100, 1024), (400, 1800)):
+            gb = ctx.collate_range(st, first, n)
+            _compare(gb, oracle.collate(ost, order[first:first + n], delta))
+    ctx.check()
+
+
 def test_collate_edge_cases(tmp_path):
     import paper_2207_11333_gb300 as g
     from helpers import custom_set

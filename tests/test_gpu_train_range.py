@@ -73,3 +73,41 @@ def test_train_step_range_rejects_bad_ranges(tmp_path):
     ctx.train_step_range(st, 16, 64, 1e-3)
     ctx.check()
     ctx.close()
+
+
+def test_train_step_range_beyond_the_single_launch_collation(tmp_path):
+    """Batches of more than 1024 graphs are collated by two launches: both of
+    the graph's collation nodes move to the next range."""
+    import paper_2207_11333_gb300 as g
+    import synth
+    n_total, G, H, L = 2400, 1100, 32, 1
+    gs = synth.molecules_uniform(31, n_total, 2, 12)
+    gs.y = synth.uniform_targets(32, 0, n_total, 1.0, 10.0)
+    path, _ = write_both(gs, str(tmp_path))
+    st = g.Store(path)
+    st.to_device()
+    delta = st.delta()
+    student = synth.init_params(3, H, L)
+    order = np.random.default_rng(33).permutation(n_total)
+    res = []
+    for ranged in (False, True):
+        ctx = g.Context(g.make_config(H, L, G, int(gs.n_nodes), int(gs.n_edges), delta=delta, head_hidden=H))
+        ctx.set_params(student)
+        ctx.set_order(st, order)
+        acc = torch.zeros(3, dtype=torch.float64, device="cuda")
+        exports = []
+        for first in (0, 1100, 0):
+            if ranged:
+                b = ctx.train_step_range(st, first, G, 1e-3, acc)
+            else:
+                b = ctx.collate_range(st, first, G)
+                ctx.train_step(b, 1e-3, acc)
+            exports.append(b.export())
+        res.append((ctx.get_params(), acc.cpu().numpy(), exports))
+        ctx.check()
+        ctx.close()
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
+    for x, y in zip(res[0][2], res[1][2]):
+        for k in x:
+            assert np.array_equal(x[k], y[k]), k
