@@ -219,82 +219,105 @@ __device__ __forceinline__ float4 ld_cluster4(uint32_t a, int rank) {
   return v;
 }
 
-// Rows r0, r0 + 8, r0 + 16, r0 + 24 (those below re) of the staged tile at
-// column cn, each summed over the cluster's `ranks` CTAs in rank order (the
+// Rows r0, r0 + rs, r0 + 2 rs, r0 + 3 rs (those below re) of the staged tile
+// at column cn, each summed over the cluster's `ranks` CTAs in rank order (the
 // K-splits of one output tile), or the CTA's own rows.  The four rows' loads
 // from rank z + 1 are issued before the sums of rank z, so a warp waits for
 // one remote-load latency per rank, not one per row and rank; the order of
 // the additions, and so every result bit, does not depend on this.
 // LEAN (register-capped kernels): one rank's loads at a time.
 template <bool LEAN>
-__device__ __forceinline__ void rows_sum4(const float *S, int RS, int r0, int re, int cn, int ranks, float4 v[4]) {
+__device__ __forceinline__ void rows_sum4(const float *S, int RS, int r0, int rs, int re, int cn, int ranks,
+                                          float4 v[4]) {
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   if (ranks == 1) {
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      v[u] = r0 + 8 * u < re ? *reinterpret_cast<const float4 *>(S + (size_t)(r0 + 8 * u) * RS + cn) : zero;
+      v[u] = r0 + rs * u < re ? *reinterpret_cast<const float4 *>(S + (size_t)(r0 + rs * u) * RS + cn) : zero;
     return;
   }
   uint32_t a[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) a[u] = smem_u32(S + (size_t)(r0 + 8 * u) * RS + cn);
-  if (LEAN) {
+  for (int u = 0; u < 4; ++u) a[u] = smem_u32(S + (size_t)(r0 + rs * u) * RS + cn);
+  if constexpr (LEAN) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = r0 + 8 * u < re ? ld_cluster4(a[u], 0) : zero;
+    for (int u = 0; u < 4; ++u) v[u] = r0 + rs * u < re ? ld_cluster4(a[u], 0) : zero;
     for (int z = 1; z < ranks; ++z) {
       float4 t[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) t[u] = r0 + 8 * u < re ? ld_cluster4(a[u], z) : zero;
+      for (int u = 0; u < 4; ++u) t[u] = r0 + rs * u < re ? ld_cluster4(a[u], z) : zero;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         v[u].x += t[u].x; v[u].y += t[u].y; v[u].z += t[u].z; v[u].w += t[u].w;
       }
     }
-    return;
-  }
-  float4 t[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    v[u] = r0 + 8 * u < re ? ld_cluster4(a[u], 0) : zero;
-    t[u] = r0 + 8 * u < re ? ld_cluster4(a[u], 1) : zero;
-  }
-  for (int z = 1; z < ranks; ++z) {
-    float4 n[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) n[u] = (z + 1 < ranks && r0 + 8 * u < re) ? ld_cluster4(a[u], z + 1) : zero;
+  } else {
+    float4 t[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      v[u].x += t[u].x; v[u].y += t[u].y; v[u].z += t[u].z; v[u].w += t[u].w;
-      t[u] = n[u];
+      v[u] = r0 + rs * u < re ? ld_cluster4(a[u], 0) : zero;
+      t[u] = r0 + rs * u < re ? ld_cluster4(a[u], 1) : zero;
+    }
+    for (int z = 1; z < ranks; ++z) {
+      float4 n[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) n[u] = (z + 1 < ranks && r0 + rs * u < re) ? ld_cluster4(a[u], z + 1) : zero;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        v[u].x += t[u].x; v[u].y += t[u].y; v[u].z += t[u].z; v[u].w += t[u].w;
+        t[u] = n[u];
+      }
     }
   }
 }
 
 // ---------------------------------------------------------------- tile stores
 // The FP32 tile staged in shared memory (row pitch RS floats) goes to global
-// memory row by row: warp w takes rows w, w + 8, ...; lane l the 4-column
-// slices 4l and 128 + 4l.  Four rows per batch, every load of a batch issued
-// before its stores.  One routine per epilogue kind keeps each kernel
+// memory row by row.  A row's BN columns take lpr lanes of a warp, 4 columns
+// each (lpr the smallest power of two covering BN / 4), so one warp
+// instruction covers rpi = 32 / lpr rows: narrow tiles keep every lane busy.
+// Slot q = rpi w + (lane / lpr) of warp w takes rows q, q + 8 rpi, q + 16 rpi,
+// q + 24 rpi as one batch (every load of a batch issued before its stores),
+// then the next 32 rpi rows.  One routine per epilogue kind keeps each kernel
 // instantiation's store loop small.
 enum EpiKind { kEpiPartial = 0, kEpiC = 1, kEpiD3 = 2 };
+
+struct StoreLanes {
+  int cn;     // first column of this lane's 4-column slice
+  int slot;   // first row, relative to the range's start
+  int rs;     // rows between the batch's four rows (8 rpi)
+};
+
+// WIDE: one row per warp instruction whatever BN (the register-capped
+// kernels, which the narrower layout would make spill)
+template <bool WIDE = false>
+__device__ __forceinline__ StoreLanes store_lanes(int BN, int warp, int lane) {
+  int lpr = 32;
+  if (!WIDE)
+    while (lpr > 1 && 4 * (lpr / 2) >= BN) lpr /= 2;
+  const int rpi = 32 / lpr;
+  return StoreLanes{4 * (lane % lpr), rpi * warp + lane / lpr, 8 * rpi};
+}
 
 // split-K partial tile: P[row][n] (pitch N), no epilogue
 __device__ __forceinline__ void store_partial(const float *S, int RS, int rows, int BN, int N, int m0, int n0,
                                               float *__restrict__ P, int warp, int lane) {
+  const StoreLanes sl = store_lanes(BN, warp, lane);
+  const int rs = sl.rs;
 #pragma unroll 1
   for (int h = 0; h < 2; ++h) {
-    const int cn = 128 * h + 4 * lane;
+    const int cn = 128 * h + sl.cn;
     if (cn >= BN || n0 + cn >= N) continue;
     float *dst = P + (size_t)m0 * N + n0 + cn;
-    for (int r0 = warp; r0 < rows; r0 += 32) {
+    for (int r0 = sl.slot; r0 < rows; r0 += 4 * rs) {
       float4 v[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        v[u] = r0 + 8 * u < rows ? *reinterpret_cast<const float4 *>(S + (size_t)(r0 + 8 * u) * RS + cn)
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[u] = r0 + rs * u < rows ? *reinterpret_cast<const float4 *>(S + (size_t)(r0 + rs * u) * RS + cn)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        if (r0 + 8 * u < rows) *reinterpret_cast<float4 *>(dst + (size_t)(r0 + 8 * u) * N) = v[u];
+        if (r0 + rs * u < rows) *reinterpret_cast<float4 *>(dst + (size_t)(r0 + rs * u) * N) = v[u];
     }
   }
 }
@@ -304,9 +327,11 @@ __device__ __forceinline__ void store_partial(const float *S, int RS, int rows, 
 template <bool LEAN>
 __device__ __forceinline__ void store_c(const float *S, int RS, int rb, int re, int ranks, int BN, int N, int m0,
                                         int n0, const TcEpilogue e, int warp, int lane) {
+  const StoreLanes sl = store_lanes<LEAN>(BN, warp, lane);
+  const int rs = sl.rs;
 #pragma unroll 1
   for (int h = 0; h < 2; ++h) {
-    const int cn = 128 * h + 4 * lane;
+    const int cn = 128 * h + sl.cn;
     const int n = n0 + cn;
     if (cn >= BN || n >= N) continue;
     float b[4] = {0.f, 0.f, 0.f, 0.f};
@@ -314,13 +339,13 @@ __device__ __forceinline__ void store_c(const float *S, int RS, int rb, int re, 
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (n + q < e.bias_n) b[q] = e.bias[n + q];
-    for (int r0 = rb + warp; r0 < re; r0 += 32) {
+    for (int r0 = rb + sl.slot; r0 < re; r0 += 4 * rs) {
       float4 v[4];
-      rows_sum4<LEAN>(S, RS, r0, re, cn, ranks, v);
+      rows_sum4<LEAN>(S, RS, r0, rs, re, cn, ranks, v);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (r0 + 8 * u >= re) break;
-        const size_t row = (size_t)(m0 + r0 + 8 * u);
+        if (r0 + rs * u >= re) break;
+        const size_t row = (size_t)(m0 + r0 + rs * u);
         float4 x = make_float4(v[u].x + b[0], v[u].y + b[1], v[u].z + b[2], v[u].w + b[3]);
         if (e.relu) {
           x.x = fmaxf(x.x, 0.f); x.y = fmaxf(x.y, 0.f); x.z = fmaxf(x.z, 0.f); x.w = fmaxf(x.w, 0.f);
@@ -338,20 +363,22 @@ __device__ __forceinline__ void store_c(const float *S, int RS, int rb, int re, 
 __device__ __forceinline__ void store_d3(const float *S, int RS, int rb, int re, int ranks, int BN, int N, int m0,
                                          int n0, const TcEpilogue e, const uint32_t *mbits, const float *s_amp,
                                          const float *s_att, int warp, int lane) {
+  const StoreLanes sl = store_lanes(BN, warp, lane);
+  const int rs = sl.rs;
 #pragma unroll 1
   for (int h = 0; h < 2; ++h) {
-    const int cn = 128 * h + 4 * lane;
+    const int cn = 128 * h + sl.cn;
     const int n = n0 + cn;
     if (cn >= BN || n >= N) continue;
     const int word = cn / 32, shift = cn % 32;
-    for (int r0 = rb + warp; r0 < re; r0 += 32) {
+    for (int r0 = rb + sl.slot; r0 < re; r0 += 4 * rs) {
       float4 v[4];
       uint32_t mk[4];
       float am[4], at[4];
-      rows_sum4<false>(S, RS, r0, re, cn, ranks, v);
+      rows_sum4<false>(S, RS, r0, rs, re, cn, ranks, v);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int r = r0 + 8 * u;
+        const int r = r0 + rs * u;
         mk[u] = 0u;
         am[u] = at[u] = 0.f;
         if (r < re) {
@@ -362,8 +389,8 @@ __device__ __forceinline__ void store_d3(const float *S, int RS, int rb, int re,
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (r0 + 8 * u >= re) break;
-        const size_t row = (size_t)(m0 + r0 + 8 * u);
+        if (r0 + rs * u >= re) break;
+        const size_t row = (size_t)(m0 + r0 + rs * u);
         const float4 x = v[u];
         if (e.C) *reinterpret_cast<float4 *>(e.C + row * e.ldc + n) = x;
         const float gx = (mk[u] & 1u) ? x.x : 0.f, gy = (mk[u] & 2u) ? x.y : 0.f;
