@@ -659,12 +659,15 @@ int run_step_graph(gcnn_ctx *c, const gcnn_batch *b, double *loss_accum, bool wi
   // every phase; each of its replays is synchronised and accumulated
   auto key = std::make_tuple(G, Ng, Eg, (const double *)loss_accum, c->prof_on, with_step, range_st != nullptr);
   auto it = c->graphs.find(key);
+  // the collation's arguments name the store and the uploaded order's address
+  // (gcnn_set_order may have replaced the order since the last launch)
+  const int64_t *range_ids = range_st ? c->order_dev + range_first : nullptr;
   if (it != c->graphs.end() && range_st &&
-      (it->second.range_store != range_st || it->second.range_first != range_first)) {
+      (it->second.range_store != range_st || it->second.range_ids != range_ids)) {
     GCNN_TRY(ctx_range_update(c, range_st, range_first, G, it->second.exec, it->second.scan_node,
                               it->second.graph_node));
     it->second.range_store = range_st;
-    it->second.range_first = range_first;
+    it->second.range_ids = range_ids;
   }
   if (it == c->graphs.end()) {
     // capture on the context's private stream (the legacy default stream
@@ -755,7 +758,7 @@ int run_step_graph(gcnn_ctx *c, const gcnn_batch *b, double *loss_accum, bool wi
     entry.scan_node = scan_node;
     entry.graph_node = graph_node;
     entry.range_store = range_st;
-    entry.range_first = range_first;
+    entry.range_ids = range_ids;
     it = c->graphs.emplace(key, std::move(entry)).first;
   }
   GCNN_CUDA_TRY(cudaGraphLaunch(it->second.exec, c->stream));

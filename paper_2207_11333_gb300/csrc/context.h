@@ -86,11 +86,11 @@ struct gcnn_ctx {
     std::vector<ProfEvent> ev;  // profiling graphs: event-record nodes around each phase
     // graphs that begin with the collation of a range of the device-resident
     // order: the captured graph (its nodes address the instantiated one), the
-    // collation's two kernel nodes and the range they were last set to
+    // collation's kernel nodes, and the store and id list they were last set to
     cudaGraph_t graph = nullptr;
     cudaGraphNode_t scan_node = nullptr, graph_node = nullptr;
     const gcnn_store *range_store = nullptr;
-    int64_t range_first = -1;
+    const int64_t *range_ids = nullptr;
   };
   // key: grid (graphs, node bucket, edge bucket), loss accumulator, profiling
   // graph, whether the graph ends with the optimizer step, and whether it

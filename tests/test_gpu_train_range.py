@@ -1,8 +1,9 @@
 """gcnn_train_step_range: the collation of a range of the device-resident order
 captured in the same CUDA graph as the training step.  Consecutive ranges
 (the graph's collation nodes updated between launches, a smaller last batch
-with a graph of its own, and a return to the first range) give the parameters,
-loss sums and batches of gcnn_collate_range + gcnn_train_step bit for bit."""
+with a graph of its own, a return to the first range, and a new order
+uploaded between two launches) give the parameters, loss sums and batches of
+gcnn_collate_range + gcnn_train_step bit for bit."""
 import numpy as np
 import pytest
 import torch
@@ -23,7 +24,9 @@ def _trained(g, st, gs, delta, student, precision, ranged):
     ctx.set_order(st, np.random.default_rng(5).permutation(300))
     acc = torch.zeros(3, dtype=torch.float64, device="cuda")
     batches = []
-    for first, count in RANGES:
+    for k, (first, count) in enumerate(RANGES):
+        if k == len(RANGES) - 2:   # a new order: the cached graph must read the new id list
+            ctx.set_order(st, np.random.default_rng(6).permutation(300))
         if ranged:
             b = ctx.train_step_range(st, first, count, 1e-3, acc)
         else:
