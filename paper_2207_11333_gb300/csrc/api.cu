@@ -737,7 +737,7 @@ int run_step_graph(gcnn_ctx *c, const gcnn_batch *b, double *loss_accum, bool wi
     }
     cudaGetLastError();
     // one launch for a batch of at most 1024 graphs, a scan and a per-graph launch beyond
-    if (range_st && (!scan_node || (G > 1024 && !graph_node))) {
+    if (range_st && (!scan_node || (G > kCollateOneLaunchGraphs && !graph_node))) {
       cudaGraphDestroy(graph);
       drop_events();
       return set_error(GCNN_ECUDA, "train step: the captured collation nodes were not found");

@@ -184,7 +184,7 @@ collate_graph_kernel(int G, const int64_t *__restrict__ ids, StoreView st, Batch
 // same offsets) before its dependency wait, since it reads only the store and
 // the id list; then it writes the scan's outputs for its own graphs (block 0
 // also the totals and the device-side sizes) and collates them.
-constexpr int kFusedGraphs = 1024;
+constexpr int kFusedGraphs = kCollateOneLaunchGraphs;
 
 __global__ void __launch_bounds__(kGraphWarps * 32)
 collate_small_kernel(int G, const int64_t *__restrict__ ids, StoreView st, BatchBuf b,

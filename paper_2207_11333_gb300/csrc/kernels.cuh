@@ -40,6 +40,7 @@ int launch_collate(int G, const int64_t *ids, StoreView st, BatchBuf b, const fl
 // instantiated graph (scan_node: the scan or the single launch; graph_node:
 // the per-graph launch, unused for a single launch) to the arguments of
 // another batch of the same graph count G.
+constexpr int kCollateOneLaunchGraphs = 1024;  // batches up to this size: one collation launch
 int collate_node_kind(const void *func);
 int collate_set_nodes(cudaGraphExec_t exec, cudaGraphNode_t scan_node, cudaGraphNode_t graph_node, int G,
                       const int64_t *ids, StoreView st, BatchBuf b, const float *scal_tab, int cap_nodes,
