@@ -36,9 +36,28 @@ constexpr int kMaxTypes = 16;
 constexpr int kRedThreads = 256;
 constexpr int kEmbBwdThreads = 512;   // one block per 4-column slice: nodes strided over the block
 constexpr int kColsumThreads = 1024;
+constexpr int kColsumWidth = 32;    // columns per CTA of the bias sums
+constexpr int kColsumMaxRanks = 8;  // CTAs of a cluster (row ranges), portable size
 
 __device__ __forceinline__ float4 add4(float4 a, float4 b) {
   return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// barrier over every thread of the cluster's CTAs (release / acquire)
+__device__ __forceinline__ void colsum_cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// 16 bytes at shared-memory address a of the cluster's CTA `rank`
+__device__ __forceinline__ float4 colsum_ld_cluster4(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  float4 v;
+  asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(r)
+               : "memory");
+  return v;
 }
 
 // Butterfly sum over the warp (fixed order; every lane gets the total).
@@ -643,43 +662,77 @@ adam_kernel(AdamSpan sp, int advance, float *__restrict__ p, const float *__rest
 }
 
 // out0[c] = sum_i a0[i][c] [mask[i][c] > 0] for c < cols0 and out1[c] =
-// sum_i a1[i][c] for c < cols1: one block per 4-column slice of [a0 | a1],
-// nodes strided over the block's threads, fixed-order reduction.
+// sum_i a1[i][c] for c < cols1 (the bias gradients).  The columns of
+// [a0 | a1] go in groups of 32 (blockIdx.x): eight lanes of a warp read one
+// row's 128 bytes, so a warp covers four rows per load.  The rows are cut into
+// gridDim.y contiguous ranges, one per CTA of a cluster.  Fixed order
+// throughout: each thread adds its rows in increasing order, the four rows of
+// a warp by butterfly, the warps in index order, and the cluster's CTAs in
+// rank order (distributed shared memory), so the sums are bit-reproducible.
 __global__ void __launch_bounds__(kColsumThreads)
-colsum_kernel(int n_cap, int cols0, DevDims dims, const float *__restrict__ a0, int ld0,
+colsum_kernel(int n_cap, int cols0, int cols, DevDims dims, const float *__restrict__ a0, int ld0,
               const float *__restrict__ mask, int ldm, const float *__restrict__ a1, int ld1,
               float *__restrict__ out0, float *__restrict__ out1) {
   pdl_entry(GCNN_K_COLSUM);
-  __shared__ float4 sh[kColsumThreads / 32];
+  constexpr int kWarps = kColsumThreads / 32, kRowsPerPass = kColsumThreads / 8;
+  __shared__ float4 sh[kWarps][8];
+  __shared__ float4 part[8];
   const int N = min(n_cap, dims.nodes(n_cap));
-  const int c = blockIdx.x * 4;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, q = lane & 7;
+  const int c = blockIdx.x * kColsumWidth + 4 * q;
   const bool first = c < cols0;
+  const int seg = (N + (int)gridDim.y - 1) / (int)gridDim.y;
+  const int i0 = (int)blockIdx.y * seg, i1 = min(N, i0 + seg);
   float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-  for (int i = threadIdx.x; i < N; i += kColsumThreads) {
-    float4 x;
-    if (first) {
-      x = ld4(a0 + (size_t)i * ld0 + c);
-      if (mask) {
-        const float4 mk = ld4(mask + (size_t)i * ldm + c);
-        x.x = mk.x > 0.f ? x.x : 0.f;
-        x.y = mk.y > 0.f ? x.y : 0.f;
-        x.z = mk.z > 0.f ? x.z : 0.f;
-        x.w = mk.w > 0.f ? x.w : 0.f;
+  if (c < cols) {
+    const float *src = first ? a0 + c : a1 + (c - cols0);
+    const int ld = first ? ld0 : ld1;
+    const float *mk = first ? mask : nullptr;
+    for (int i = i0 + (threadIdx.x >> 3); i < i1; i += 4 * kRowsPerPass) {
+      float4 x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = i + u * kRowsPerPass;
+        if (r < i1) {
+          x[u] = ld4(src + (size_t)r * ld);
+          if (mk) {
+            const float4 m = ld4(mk + (size_t)r * ldm + c);
+            x[u].x = m.x > 0.f ? x[u].x : 0.f;
+            x[u].y = m.y > 0.f ? x[u].y : 0.f;
+            x[u].z = m.z > 0.f ? x[u].z : 0.f;
+            x[u].w = m.w > 0.f ? x[u].w : 0.f;
+          }
+        }
       }
-    } else {
-      x = ld4(a1 + (size_t)i * ld1 + (c - cols0));
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (i + u * kRowsPerPass < i1) acc = add4(acc, x[u]);
     }
-    acc = add4(acc, x);
   }
-  acc = warp_sum4(acc);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+#pragma unroll
+  for (int o = 8; o < 32; o <<= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, o);
+    acc.w += __shfl_xor_sync(0xffffffffu, acc.w, o);
+  }
+  if (lane < 8) sh[w][lane] = acc;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float4 sum = sh[0];
-    for (int q = 1; q < kColsumThreads / 32; ++q) sum = add4(sum, sh[q]);
+  if (threadIdx.x < 8) {
+    float4 sum = sh[0][threadIdx.x];
+#pragma unroll
+    for (int k = 1; k < kWarps; ++k) sum = add4(sum, sh[k][threadIdx.x]);
+    part[threadIdx.x] = sum;
+  }
+  colsum_cluster_sync();
+  if (blockIdx.y == 0 && threadIdx.x < 8 && c < cols) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(&part[threadIdx.x]);
+    float4 sum = colsum_ld_cluster4(a, 0);
+    for (int k = 1; k < (int)gridDim.y; ++k) sum = add4(sum, colsum_ld_cluster4(a, k));
     st4(first ? out0 + c : out1 + (c - cols0), sum);
   }
+  // no CTA leaves while rank 0 may still read its partial sums
+  colsum_cluster_sync();
 }
 
 }  // namespace
@@ -690,8 +743,29 @@ int launch_colsum2(int n_cap, int cols0, int cols1, DevDims dims, const float *a
   if (cols <= 0 || n_cap <= 0) return GCNN_OK;
   if (cols0 % 4 || cols1 % 4 || ld0 % 4 || ld1 % 4 || (mask && ldm % 4))
     return set_error(GCNN_EINVAL, "colsum: widths and strides must be multiples of 4");
-  GCNN_TRY(launch(colsum_kernel, cols / 4, kColsumThreads, 0, s, n_cap, cols0, dims, a0, ld0, mask, ldm, a1, ld1, out0,
-                  out1));
+  // about one CTA per SM: the column groups times the row ranges of a cluster
+  const int groups = (int)ceil_div(cols, kColsumWidth);
+  const int ranks = std::max(1, std::min(kColsumMaxRanks, num_sms() / groups));
+  cudaLaunchAttribute attr[2];
+  int n = 0;
+  attr[n].id = cudaLaunchAttributeClusterDimension;
+  attr[n].val.clusterDim.x = 1;
+  attr[n].val.clusterDim.y = (unsigned)ranks;
+  attr[n].val.clusterDim.z = 1;
+  ++n;
+  if (pdl_enabled(s)) {
+    attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)groups, (unsigned)ranks);
+  cfg.blockDim = dim3(kColsumThreads);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = n;
+  GCNN_CUDA_TRY(cudaLaunchKernelEx(&cfg, colsum_kernel, n_cap, cols0, cols, dims, a0, ld0, mask, ldm, a1, ld1, out0,
+                                   out1));
   return GCNN_OK;
 }
 
