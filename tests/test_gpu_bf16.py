@@ -34,10 +34,12 @@ def _run(tmp_path, precision, G=64, lo=5, hi=30, H=32, L=2, recompute=False, ser
     return d, student, ob, pred.cpu().numpy(), acts, grads
 
 
-# the last case has more than 2 x 152 x 128 edges: its aggregation backward runs
-# fused over chunks of whole graphs and writes the BF16 [dP | dQ] operand there
+# the case of 900 graphs has more than 2 x 152 x 128 edges: its aggregation
+# backward runs fused over chunks of whole graphs and writes the BF16 [dP | dQ]
+# operand there; at H = 256 the bias sums cover 2H = 512 columns, 16 groups of 32
+# (13 at H = 200, the last one partly filled)
 @pytest.mark.parametrize("G,lo,hi,H,L", [(64, 5, 30, 32, 2), (13, 3, 51, 200, 2), (150, 3, 51, 64, 3),
-                                         (900, 3, 60, 32, 2)])
+                                         (900, 3, 60, 32, 2), (40, 3, 30, 256, 1)])
 def test_bf16_forward_and_gradients(tmp_path, G, lo, hi, H, L):
     import paper_2207_11333_gb300 as g
     d, student, ob, pred, acts, grads = _run(tmp_path, g.PREC_BF16, G, lo, hi, H, L)
