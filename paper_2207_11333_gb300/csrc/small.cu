@@ -669,6 +669,8 @@ adam_kernel(AdamSpan sp, int advance, float *__restrict__ p, const float *__rest
 // throughout: each thread adds its rows in increasing order, the four rows of
 // a warp by butterfly, the warps in index order, and the cluster's CTAs in
 // rank order (distributed shared memory), so the sums are bit-reproducible.
+// The launch makes the cluster (1, gridDim.y, 1), so a CTA's rank in its
+// cluster is blockIdx.y and rank 0 writes the group's sums.
 __global__ void __launch_bounds__(kColsumThreads)
 colsum_kernel(int n_cap, int cols0, int cols, DevDims dims, const float *__restrict__ a0, int ld0,
               const float *__restrict__ mask, int ldm, const float *__restrict__ a1, int ld1,
